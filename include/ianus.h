@@ -1,0 +1,300 @@
+/*
+ * ianus.h -- C ABI of the GB300 spin-glass Monte Carlo library (libianus.so).
+ *
+ * The library runs the checkerboard Metropolis / heat-bath sweep of the
+ * lattice spin models of "Simulating spin systems on IANUS, an FPGA-based
+ * computer" (Sec. 2 and Sec. 3.1 of the paper):
+ *
+ *   - the 3D (and 2D) Edwards-Anderson +-J Ising spin glass, Eq. (2) with
+ *     x_i = 1, h_i = 0, J_ij = +-1 i.i.d. (Sec. 2.1);
+ *   - a q = 4 Potts glass H = -sum_<ij> J_ij delta(s_i, s_j), J_ij = +-1,
+ *     a J-weighted variant of the glassy Potts model of Eq. (3);
+ *
+ * with single-spin Metropolis and heat-bath updates (Sec. 2.2), the
+ * two-colour (bipartite) parallel update (Sec. 3.1), integer look-up-table
+ * acceptance against 32-bit random numbers (Sec. 3.2, Sec. 3.3), energy,
+ * magnetisation and replica-overlap measurements (Sec. 4.1) and parallel
+ * tempering, which Sec. 2.2 names as a required add-on without giving rules.
+ *
+ * All signatures use plain C types and pointers.  Host pointers are owned by
+ * the caller.  Every entry point returns an ianus_status and never aborts,
+ * exits or prints.  Every device operation is enqueued on the lattice's CUDA
+ * stream; the calls documented as synchronous synchronise that stream only.
+ *
+ * ------------------------------------------------------------------------
+ * Lattice, colours, bonds (Sec. 2.1; Sec. 3.1)
+ * ------------------------------------------------------------------------
+ *   D in {2,3}, side L even and >= 2, N = L^D sites, periodic boundaries.
+ *   Site index i = x + L*(y + L*z)  (z = 0 when D = 2).
+ *   Colour c(i) = (x + y + z) mod 2.  A sweep updates every colour-0 site,
+ *   then every colour-1 site; no bond joins two sites of the same colour.
+ *   Bonds are stored as forward bonds J_d(i) joining i and i + e_d
+ *   (d = 0..D-1, periodic); the backward bond of i along d is J_d(i - e_d).
+ *   For L = 2 the forward and backward neighbour coincide but the two bonds
+ *   are distinct.
+ *
+ * Configurations.  A lattice object holds n_samples disorder samples; each
+ * sample has n_temps * n_replicas spin configurations ("slots") that share
+ * the sample's couplings.  Slot sigma = tslot * n_replicas + a, where a is the
+ * replica index and tslot the temperature index the slot started at.  With
+ * n_temps > 1 the slots of one chain (sample s, replica a) exchange
+ * temperatures by parallel tempering; a configuration keeps its slot (and
+ * its random stream) and only its temperature label moves.
+ *
+ * Ising encoding.  Spin bit b = (1 - s)/2 (1 means s = -1); coupling bit
+ * c = (1 - J)/2.  Bond (i,j) is unsatisfied (J s_i s_j = -1) iff
+ * b_i ^ b_j ^ c_ij = 1.  u_i = number of unsatisfied bonds at i (0..2D).
+ *   Metropolis flip cost  dE_i = 4D - 4 u_i.
+ *   Heat-bath local field x_i = s_i h_i = 2D - 2 u_i.
+ *   Total energy E = -sum_bonds J s s = 2U - D N, U = unsatisfied bonds.
+ *
+ * ------------------------------------------------------------------------
+ * Random stream (replaces the Parisi-Rapuano wheel of Sec. 3.3, Eq. (5))
+ * ------------------------------------------------------------------------
+ *   Generator: Philox4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw,
+ *   "Parallel random numbers: as easy as 1, 2, 3", SC'11).  Key
+ *   (k0,k1) = (seed & 0xffffffff, seed >> 32); counter (c0,c1,c2,c3);
+ *   output (x0,x1,x2,x3).  Every random number is a function of the seed and
+ *   of its coordinates only, so results do not depend on memory layout,
+ *   kernel choice, launch shape or on how sweeps are split across calls.
+ *   Tags: SPIN = 1, J = 2, INIT = 3, POTTS = 4, PINIT = 5, PT = 6.
+ *   Sample s lives in group g = s >> 6 at lane l = s & 63.
+ *
+ *   Ising update random r(s, sigma, i, t), t = absolute sweep index:
+ *     for plane pair m = 0..15:
+ *       (x0..x3) = Philox(key, c0 = i, c1 = t & 0xffffffff,
+ *                         c2 = (SPIN << 28) | (m << 24) | (sigma << 12) | g,
+ *                         c3 = t >> 32)
+ *       W[2m] = x0 | x1 << 32,  W[2m+1] = x2 | x3 << 32
+ *     r = sum_{p=0..31} bit_l(W[p]) << (31 - p)      (plane 0 is the MSB)
+ *   Deciding r < T from the most significant plane down and stopping at the
+ *   first plane where r and T differ gives the same decision.
+ *
+ *   Couplings: J_d(i) of sample s is -1 iff bit l of (x0 | x1 << 32) of
+ *     Philox(key, c0 = i, c1 = d, c2 = (J << 28) | g, c3 = 0) is set.
+ *     (IANUS_DISORDER_FERRO: every J = +1.)  Both models use this stream.
+ *   Initial Ising spin of (s, sigma, i): s = -1 iff bit l of (x0 | x1 << 32)
+ *     of Philox(key, c0 = i, c1 = 0, c2 = (INIT << 28) | (sigma << 12) | g,
+ *     c3 = 0) is set.
+ *   Potts update random: r = x_{s & 3} of Philox(key, c0 = i,
+ *     c1 = t & 0xffffffff, c2 = (POTTS << 28) | (sigma << 16) | (s >> 2),
+ *     c3 = t >> 32).
+ *   Potts initial state: x_{s & 3} >> 30 of Philox(key, c0 = i, c1 = 0,
+ *     c2 = (PINIT << 28) | (sigma << 16) | (s >> 2), c3 = 0).
+ *   Parallel-tempering random for chain (s, a), temperature pair k, swap
+ *     step tau: x_{s & 3} of Philox(key, c0 = k, c1 = tau & 0xffffffff,
+ *     c2 = (PT << 28) | (a << 16) | (s >> 2), c3 = tau >> 32).
+ *   Field limits: slots < 4096, groups < 4096, samples < 2^18.
+ *
+ * ------------------------------------------------------------------------
+ * Acceptance tables (the look-up table of Sec. 3.2, 32-bit randoms Sec. 3.3)
+ * ------------------------------------------------------------------------
+ *   Built once per beta on the host in IEEE double precision, in exactly
+ *   this order, with std::exp, std::ldexp and std::floor; values lie in
+ *   [0, 2^32] and the decision is (uint64)r < T, so a probability p is
+ *   applied as floor(2^32 p) / 2^32.
+ *   Metropolis (Sec. 2.2): dE <= 0 always flips (no random compare);
+ *     for dE in {4, 8, 12} (2D: {4, 8}):
+ *     T_M(dE) = floor(ldexp(exp(-beta * dE), 32)); flip iff r < T_M(dE).
+ *   Heat bath (Sec. 2.2, Eq. (4)), x = s_i h_i in {-2D, ..., 2D} step 2:
+ *     T_H(x) = floor(ldexp(1.0 / (1.0 + exp(-2.0 * beta * x)), 32));
+ *     keep s_i iff r < T_H(x), else flip.  This is Eq. (4) written for the
+ *     current spin value, so a gauge transformation maps trajectories onto
+ *     each other bit for bit.
+ *   Potts heat bath, n_k = sum_j J_ij [s_j == k] in -6..6:
+ *     w_k = exp(beta * n_k); S0 = w0; S1 = S0 + w1; S2 = S1 + w2;
+ *     Z = S2 + w3; T_k = floor(ldexp(S_k / Z, 32)) for k = 0, 1, 2;
+ *     new state = smallest k in 0..2 with r < T_k, else 3.
+ *   Parallel tempering (pair k of temperatures k and k+1):
+ *     db = beta[k] - beta[k+1]; energies of the configurations at
+ *     temperatures k and k+1 are E_A and E_B, d = E_B - E_A (a multiple of 4
+ *     in the +-J model); swap iff db * d <= 0, else iff
+ *     r < T_PT(k, |d|) = floor(ldexp(exp(-|db| * |d|), 32)).  This is the
+ *     usual acceptance min(1, exp(db * (E_A - E_B))).  Pairs are visited for
+ *     k = 0 .. n_temps-2 in ascending order within one swap step.
+ *
+ * Measurements (Sec. 4.1): exact int64 values.
+ *   Ising: E = -sum_bonds J s s, M = sum_i s_i, Q = sum_i s_i^0 s_i^1.
+ *   Potts: E = -sum_bonds J delta(s_i, s_j); "magnetisation" = the four
+ *     state counts n_k; Q = sum_i delta(s_i^0, s_i^1).
+ */
+#ifndef IANUS_H
+#define IANUS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define IANUS_ABI_VERSION 1u
+
+typedef struct ianus_lattice ianus_lattice; /* opaque, library-owned */
+
+typedef enum {
+  IANUS_OK = 0,
+  IANUS_EINVAL = 1,      /* invalid argument or configuration            */
+  IANUS_ENOMEM = 2,      /* device or host allocation failed              */
+  IANUS_ECUDA = 3,       /* a CUDA runtime call failed                    */
+  IANUS_ETIMEOUT = 4,    /* a bounded device wait expired                 */
+  IANUS_EUNSUPPORTED = 5,/* valid request this build does not implement   */
+  IANUS_ESTATE = 6       /* lattice is in an error state / bad state blob */
+} ianus_status;
+
+typedef enum { IANUS_EA_PM_J = 0, IANUS_POTTS4_J = 1 } ianus_model;
+typedef enum { IANUS_METROPOLIS = 0, IANUS_HEATBATH = 1 } ianus_algo;
+typedef enum {
+  IANUS_LAYOUT_AUTO = 0,   /* BITS64 for Ising, U8X4 for Potts              */
+  IANUS_LAYOUT_I8 = 1,     /* Ising: one int8 per spin (the plain kernel)   */
+  IANUS_LAYOUT_BITS64 = 2, /* Ising: one uint64 per site holds 64 samples   */
+  IANUS_LAYOUT_U8X4 = 3    /* Potts: one uint32 per site holds 4 samples    */
+} ianus_layout;
+typedef enum { IANUS_DISORDER_PM_J = 0, IANUS_DISORDER_FERRO = 1 } ianus_disorder;
+
+typedef struct {
+  uint32_t abi_version;     /* must equal IANUS_ABI_VERSION                 */
+  int32_t model;            /* ianus_model                                  */
+  int32_t dim;              /* 2 or 3                                       */
+  int32_t L;                /* even, >= 2                                   */
+  int32_t n_samples;        /* disorder samples, >= 1                       */
+  int32_t n_replicas;       /* real replicas per sample and temperature     */
+  int32_t n_temps;          /* temperatures; > 1 enables parallel tempering */
+  int32_t layout;           /* ianus_layout                                 */
+  int32_t disorder;         /* ianus_disorder                               */
+  uint32_t series_capacity; /* rows kept by the device measurement series   */
+  uint64_t seed;
+  void* device_buffer;      /* optional caller-owned device memory, >= ianus_required_bytes */
+  size_t device_buffer_bytes;
+  void* cuda_stream;        /* cudaStream_t; NULL = the legacy default stream */
+} ianus_config;
+
+/* Device bytes a lattice with this configuration uses (state, couplings,
+ * tables, series).  Returns 0 for an invalid configuration.  Host only. */
+size_t ianus_required_bytes(const ianus_config* cfg);
+
+/* Validates cfg, takes device memory (cfg->device_buffer if non-NULL, which
+ * the caller keeps alive until ianus_destroy; else cudaMalloc), and fills
+ * the couplings and the initial configuration from the seed on the device
+ * (Sec. 2.1: quenched J_ij; initial state from the INIT/PINIT streams).
+ * Sweep and swap counters start at 0, temperatures at the identity order.
+ * Errors: EINVAL (bad cfg, out NULL, buffer too small), ENOMEM, ECUDA,
+ * EUNSUPPORTED (e.g. Potts with layout I8/BITS64).  On error *out = NULL. */
+ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out);
+
+/* Runs nsweeps full sweeps (Sec. 2.2: every site once; Sec. 3.1: colour 0
+ * then colour 1) of Metropolis or heat bath (algo) at inverse temperatures
+ * beta[0..n_temps-1] (host array, indexed by temperature, not slot).
+ * Acceptance tables are rebuilt on the host when beta or algo changes and
+ * uploaded on the lattice stream.  If measure_every > 0, E, M and Q are
+ * appended to the device series after every sweep whose absolute sweep
+ * count is a multiple of measure_every.  Asynchronous.  Errors: EINVAL
+ * (NULL, beta not finite or negative, algo out of range), EUNSUPPORTED
+ * (Potts Metropolis), ECUDA, ESTATE. */
+ianus_status ianus_sweep(ianus_lattice* lat, int32_t algo, const double* beta,
+                         uint64_t nsweeps, uint32_t measure_every);
+
+/* One parallel-tempering swap step (Sec. 2.2 names PT; rules in the header
+ * comment above): measures the exact energies on the device, then every
+ * chain (sample, replica) visits its temperature pairs in ascending order.
+ * Uses the beta array of the last ianus_sweep.  Asynchronous.  Errors:
+ * EINVAL (n_temps == 1 or no prior sweep), EUNSUPPORTED (Potts), ECUDA. */
+ianus_status ianus_pt_swap(ianus_lattice* lat);
+
+/* Fused loop: repeats { ianus_sweep(swap_every sweeps, measure_every);
+ * ianus_pt_swap } until nsweeps sweeps are done (nsweeps must be a multiple
+ * of swap_every).  Same results as the separate calls. */
+ianus_status ianus_sweep_pt(ianus_lattice* lat, int32_t algo, const double* beta,
+                            uint64_t nsweeps, uint32_t swap_every,
+                            uint32_t measure_every);
+
+/* Measures the current configuration (Sec. 4.1 observables) and copies it
+ * to host arrays (any may be NULL).  Synchronous.  Layouts, indexed by
+ * temperature k (not slot):
+ *   energy        int64 [n_samples][n_temps][n_replicas]
+ *   magnetisation int64 [n_samples][n_temps][n_replicas]      (Ising)
+ *                 int64 [n_samples][n_temps][n_replicas][4]   (Potts counts)
+ *   overlap       int64 [n_samples][n_temps]  (replicas 0 and 1; needs
+ *                 n_replicas >= 2, else EINVAL when non-NULL). */
+ianus_status ianus_measure(ianus_lattice* lat, int64_t* energy,
+                           int64_t* magnetisation, int64_t* overlap);
+
+/* Copies the device measurement series to the host.  Synchronous.  Row r
+ * holds the absolute sweep count in sweep[r] and arrays laid out as in
+ * ianus_measure; energy row r starts at energy + r * S*K*R, etc.  At most
+ * cap_rows rows (the oldest kept rows first) are written; *n_rows receives
+ * the number written.  If more rows were recorded than series_capacity,
+ * only the last series_capacity are kept.  clear != 0 empties the series
+ * afterwards. */
+ianus_status ianus_read_series(ianus_lattice* lat, uint64_t* sweep,
+                               int64_t* energy, int64_t* magnetisation,
+                               int64_t* overlap, size_t cap_rows,
+                               size_t* n_rows, int32_t clear);
+
+/* Spins of every slot in natural site order: int8 [n_samples][slots][N]
+ * with slots = n_temps * n_replicas; Ising values +-1, Potts 0..3.
+ * Synchronous. */
+ianus_status ianus_get_spins_i8(ianus_lattice* lat, int8_t* host);
+/* Overwrites every slot's spins from the same layout (Ising values must be
+ * +-1, Potts 0..3; else EINVAL).  Asynchronous w.r.t. the device. */
+ianus_status ianus_set_spins_i8(ianus_lattice* lat, const int8_t* host);
+/* Couplings: int8 [n_samples][dim][N], J_d(i) in {+1,-1}.  Synchronous. */
+ianus_status ianus_get_couplings_i8(ianus_lattice* lat, int8_t* host);
+/* Overwrites the couplings (values must be +-1).  Used for gauge tests. */
+ianus_status ianus_set_couplings_i8(ianus_lattice* lat, const int8_t* host);
+
+/* Parallel-tempering state: slot_at int32 [n_samples][n_replicas][n_temps]
+ * (the temperature slot tslot holding temperature k), accepted uint64
+ * [n_samples][n_replicas][n_temps-1] (swaps accepted per pair so far),
+ * *swap_steps = number of swap steps done.  Any pointer may be NULL.
+ * Synchronous. */
+ianus_status ianus_get_pt_state(ianus_lattice* lat, int32_t* slot_at,
+                                uint64_t* accepted, uint64_t* swap_steps);
+
+/* Absolute number of sweeps done so far. */
+ianus_status ianus_get_sweeps(ianus_lattice* lat, uint64_t* sweeps);
+
+/* Checkpoint (Sec. 4.1: configurations dumped to the host).  The blob holds
+ * a versioned header with the configuration, sweep and swap counters, the
+ * temperature permutation, the couplings and the spins.  With host_buf NULL,
+ * *n receives the size needed.  Synchronous.  ianus_set_state restores a
+ * blob taken from a lattice of the same configuration (else ESTATE) and
+ * clears a previous error state. */
+ianus_status ianus_get_state(ianus_lattice* lat, void* host_buf, size_t cap,
+                             size_t* n);
+ianus_status ianus_set_state(ianus_lattice* lat, const void* host_buf,
+                             size_t n);
+
+/* Blocks until all work queued for the lattice is done and reports a device
+ * error recorded by a kernel (ETIMEOUT) or the CUDA runtime (ECUDA). */
+ianus_status ianus_synchronize(ianus_lattice* lat);
+
+/* Frees what the lattice allocated.  NULL is accepted.  The caller-owned
+ * device buffer, if any, is not freed. */
+ianus_status ianus_destroy(ianus_lattice* lat);
+
+/* Static, NUL-terminated description of a status code. */
+const char* ianus_status_string(int32_t status);
+
+/* ---- Host-only table builders (the look-up tables of Sec. 3.2).  These
+ * need no GPU; tests compare them with an independent builder. ---- */
+
+/* Metropolis (algo 0): out[j] = T_M(4 (j+1)) for j = 0..dim-1 (dE = 4, 8,
+ * 12 in 3D).  Heat bath (algo 1): out[j] = T_H(-2 dim + 2 j) for
+ * j = 0..2 dim.  Values in [0, 2^32].  n = capacity of out.  Returns the
+ * count written, or 0 on bad arguments. */
+size_t ianus_table_ising(int32_t dim, int32_t algo, double beta, uint64_t* out,
+                         size_t n);
+/* Potts heat bath: out[idx*3 + k] = T_k(n0..n3), idx = (((n0+6)*13 + n1+6)
+ * *13 + n2+6)*13 + n3+6, for all 13^4 tuples (also unreachable ones).
+ * n must be >= 3 * 13^4.  Returns the count written or 0. */
+size_t ianus_table_potts(double beta, uint64_t* out, size_t n);
+/* PT: out[m-1] = T_PT(|d| = 4 m) = floor(ldexp(exp(-|db| * 4m), 32)) for
+ * m = 1..n, db = beta_k - beta_k1.  Returns n, or 0 on bad arguments. */
+size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IANUS_H */

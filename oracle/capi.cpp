@@ -1,0 +1,150 @@
+/*
+ * capi.cpp -- extern "C" entry points of the oracle for ctypes.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).  Built into liboracle.so, which
+ * only the tests, the smoke check and the CPU-baseline leg of bench.py load.
+ */
+#include <cstring>
+#include <vector>
+
+#include "oracle.h"
+
+using namespace oracle;
+
+extern "C" {
+
+void* oracle_create(int model, int q, int dim, int L, const int32_t* sample_ids, int n_ids, int R,
+                    int K, uint64_t seed, int ferro) {
+  if (dim < 1 || dim > 3 || L < 2 || (L & 1) || n_ids < 1 || R < 1 || K < 1 || q < 2) return nullptr;
+  State* st = new State();
+  std::vector<int> ids(sample_ids, sample_ids + n_ids);
+  init_state(*st, model, q, dim, L, ids, R, K, seed, ferro);
+  return st;
+}
+
+void oracle_destroy(void* h) { delete static_cast<State*>(h); }
+
+void oracle_sweep(void* h, int algo, const double* beta, uint64_t nsweeps, uint32_t measure_every,
+                  int nthreads) {
+  run_sweeps(*static_cast<State*>(h), algo, beta, nsweeps, measure_every, nthreads);
+}
+
+void oracle_pt_swap(void* h, const double* beta) { pt_swap(*static_cast<State*>(h), beta); }
+
+void oracle_measure(void* h, int64_t* E, int64_t* M, int64_t* Q) {
+  measure_all(*static_cast<State*>(h), E, M, Q);
+}
+
+uint64_t oracle_sweeps(void* h) { return static_cast<State*>(h)->sweeps; }
+
+size_t oracle_series_rows(void* h) { return static_cast<State*>(h)->ser_sweep.size(); }
+
+/* Copies all rows; caller sizes arrays from oracle_series_rows. */
+void oracle_series(void* h, uint64_t* sweep, int64_t* E, int64_t* M, int64_t* Q) {
+  State* st = static_cast<State*>(h);
+  if (sweep) std::memcpy(sweep, st->ser_sweep.data(), st->ser_sweep.size() * 8);
+  if (E) std::memcpy(E, st->ser_E.data(), st->ser_E.size() * 8);
+  if (M) std::memcpy(M, st->ser_M.data(), st->ser_M.size() * 8);
+  if (Q) std::memcpy(Q, st->ser_Q.data(), st->ser_Q.size() * 8);
+}
+
+void oracle_series_clear(void* h) {
+  State* st = static_cast<State*>(h);
+  st->ser_sweep.clear();
+  st->ser_E.clear();
+  st->ser_M.clear();
+  st->ser_Q.clear();
+}
+
+/* spins int8 [n_ids][slots][N] */
+void oracle_get_spins(void* h, int8_t* out) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples)
+    for (auto& v : smp.spin) {
+      std::memcpy(out + o, v.data(), v.size());
+      o += v.size();
+    }
+}
+
+void oracle_set_spins(void* h, const int8_t* in) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples) {
+    for (auto& v : smp.spin) {
+      std::memcpy(v.data(), in + o, v.size());
+      o += v.size();
+    }
+    for (size_t sl = 0; sl < smp.spin.size(); ++sl) smp.E_run[sl] = energy(*st, smp, (int)sl);
+  }
+}
+
+/* couplings int8 [n_ids][D][N] */
+void oracle_get_couplings(void* h, int8_t* out) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples) {
+    std::memcpy(out + o, smp.J.data(), smp.J.size());
+    o += smp.J.size();
+  }
+}
+
+void oracle_set_couplings(void* h, const int8_t* in) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples) {
+    std::memcpy(smp.J.data(), in + o, smp.J.size());
+    o += smp.J.size();
+    for (size_t sl = 0; sl < smp.spin.size(); ++sl) smp.E_run[sl] = energy(*st, smp, (int)sl);
+  }
+}
+
+/* slot_at int32 [n_ids][R][K], accepted uint64 [n_ids][R][K-1] */
+void oracle_get_pt(void* h, int32_t* slot_at, uint64_t* accepted, uint64_t* steps) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0, p = 0;
+  for (auto& smp : st->samples)
+    for (int a = 0; a < st->R; ++a) {
+      for (int k = 0; k < st->K; ++k)
+        if (slot_at) slot_at[o++] = smp.slot_at[a][k];
+      for (int k = 0; k + 1 < st->K; ++k)
+        if (accepted) accepted[p++] = smp.accepted[a][k];
+    }
+  if (steps) *steps = st->steps;
+}
+
+/* max over configurations of |E_run - E recomputed from scratch| */
+int64_t oracle_bookkeeping_error(void* h) {
+  State* st = static_cast<State*>(h);
+  int64_t worst = 0;
+  for (auto& smp : st->samples)
+    for (size_t sl = 0; sl < smp.spin.size(); ++sl) {
+      int64_t diff = smp.E_run[sl] - energy(*st, smp, (int)sl);
+      if (diff < 0) diff = -diff;
+      if (diff > worst) worst = diff;
+    }
+  return worst;
+}
+
+void oracle_philox(const uint32_t* ctr, const uint32_t* key, uint32_t* out) {
+  philox4x32_10(ctr, key, out);
+}
+
+uint32_t oracle_ising_random(uint64_t seed, int sample, int slot, uint32_t site, uint64_t sweep) {
+  return ising_random(seed, sample, slot, site, sweep);
+}
+uint32_t oracle_potts_random(uint64_t seed, int sample, int slot, uint32_t site, uint64_t sweep) {
+  return potts_random(seed, sample, slot, site, sweep);
+}
+uint32_t oracle_pt_random(uint64_t seed, int sample, int replica, int pair, uint64_t step) {
+  return pt_random(seed, sample, replica, pair, step);
+}
+uint64_t oracle_table_metropolis(double beta, int dE) { return table_metropolis(beta, dE); }
+uint64_t oracle_table_heatbath(double beta, int x) { return table_heatbath(beta, x); }
+void oracle_table_potts(double beta, int q, const int32_t* n, uint64_t* T) {
+  std::vector<int> nn(n, n + q);
+  table_potts(beta, q, nn.data(), T);
+}
+uint64_t oracle_table_pt(double dbeta_abs, int64_t dabs) { return table_pt(dbeta_abs, dabs); }
+
+}  // extern "C"

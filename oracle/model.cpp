@@ -1,0 +1,316 @@
+/*
+ * model.cpp -- the oracle's lattice, Hamiltonians, sweeps, measurements and
+ * parallel tempering.  Plain site loops, no blocking, no bit tricks.
+ *
+ * TEST INFRASTRUCTURE ONLY (see oracle.h).
+ */
+#include "oracle.h"
+
+#include <algorithm>
+#include <thread>
+
+namespace oracle {
+
+/* ---- geometry: periodic D-dimensional cubic lattice (Sec. 2.1) ---- */
+
+void site_coords(const State& st, uint32_t i, int* x) {
+  for (int d = 0; d < st.D; ++d) {
+    x[d] = (int)(i % (uint32_t)st.L);
+    i /= (uint32_t)st.L;
+  }
+}
+
+static uint32_t site_index(const State& st, const int* x) {
+  uint32_t i = 0;
+  for (int d = st.D - 1; d >= 0; --d) i = i * (uint32_t)st.L + (uint32_t)x[d];
+  return i;
+}
+
+uint32_t neighbour(const State& st, uint32_t i, int d, int dir) {
+  int x[3];
+  site_coords(st, i, x);
+  x[d] = (x[d] + dir + st.L) % st.L;
+  return site_index(st, x);
+}
+
+/* Sec. 3.1: the lattice is bipartite; colour = parity of the coordinate sum. */
+int colour(const State& st, uint32_t i) {
+  int x[3];
+  site_coords(st, i, x);
+  int sum = 0;
+  for (int d = 0; d < st.D; ++d) sum += x[d];
+  return sum % 2;
+}
+
+/* ---- set-up: quenched couplings and initial configurations ---- */
+
+void init_state(State& st, int model, int q, int D, int L, const std::vector<int>& sample_ids,
+                int R, int K, uint64_t seed, int ferro) {
+  st.model = model;
+  st.q = q;
+  st.D = D;
+  st.L = L;
+  st.N = 1;
+  for (int d = 0; d < D; ++d) st.N *= L;
+  st.R = R;
+  st.K = K;
+  st.seed = seed;
+  st.sweeps = 0;
+  st.steps = 0;
+  st.samples.clear();
+  const int slots = K * R;
+  for (int s : sample_ids) {
+    Sample smp;
+    smp.s = s;
+    smp.J.assign((size_t)D * st.N, 1);
+    for (int d = 0; d < D; ++d)
+      for (uint32_t i = 0; i < (uint32_t)st.N; ++i)
+        smp.J[(size_t)d * st.N + i] = (ferro || !coupling_bit(seed, s, d, i)) ? 1 : -1;
+    smp.spin.assign(slots, std::vector<int8_t>(st.N));
+    for (int sl = 0; sl < slots; ++sl)
+      for (uint32_t i = 0; i < (uint32_t)st.N; ++i)
+        smp.spin[sl][i] = model == 0 ? (ising_init_bit(seed, s, sl, i) ? -1 : 1)
+                                     : (int8_t)(potts_init_state(seed, s, sl, i) % q);
+    smp.slot_at.assign(R, std::vector<int>(K));
+    for (int a = 0; a < R; ++a)
+      for (int k = 0; k < K; ++k) smp.slot_at[a][k] = k;
+    smp.accepted.assign(R, std::vector<uint64_t>(K > 1 ? K - 1 : 0, 0));
+    st.samples.push_back(smp);
+  }
+  for (auto& smp : st.samples) {
+    smp.E_run.assign(slots, 0);
+    for (int sl = 0; sl < slots; ++sl) smp.E_run[sl] = energy(st, smp, sl);
+  }
+}
+
+/* ---- observables (Sec. 4.1) ---- */
+
+/* Eq. (2) with x_i = 1, h_i = 0: E = -sum over bonds of J_ij s_i s_j.
+ * Potts: E = -sum over bonds of J_ij delta(s_i, s_j).  Every bond is counted
+ * once, as the forward bond of its lower end along d. */
+int64_t energy(const State& st, const Sample& smp, int slot) {
+  const std::vector<int8_t>& s = smp.spin[slot];
+  int64_t E = 0;
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i)
+    for (int d = 0; d < st.D; ++d) {
+      uint32_t j = neighbour(st, i, d, +1);
+      int J = smp.J[(size_t)d * st.N + i];
+      if (st.model == 0)
+        E -= (int64_t)J * s[i] * s[j];
+      else
+        E -= (s[i] == s[j]) ? J : 0;
+    }
+  return E;
+}
+
+int64_t magnetisation(const State& st, const Sample& smp, int slot) {
+  int64_t M = 0;
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) M += smp.spin[slot][i];
+  return M;
+}
+
+void potts_counts(const State& st, const Sample& smp, int slot, int64_t* counts) {
+  for (int k = 0; k < st.q; ++k) counts[k] = 0;
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) counts[smp.spin[slot][i]] += 1;
+}
+
+/* Sec. 4.1 overlap between two real replicas of one sample (times N). */
+int64_t overlap(const State& st, const Sample& smp, int slot_a, int slot_b) {
+  int64_t Q = 0;
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+    if (st.model == 0)
+      Q += (int64_t)smp.spin[slot_a][i] * smp.spin[slot_b][i];
+    else
+      Q += (smp.spin[slot_a][i] == smp.spin[slot_b][i]) ? 1 : 0;
+  }
+  return Q;
+}
+
+/* ---- one sweep (Sec. 2.2), colour 0 then colour 1 (Sec. 3.1) ---- */
+
+void sweep_ising(const State& st, Sample& smp, int slot, int algo, double beta, uint64_t t) {
+  std::vector<int8_t>& s = smp.spin[slot];
+  const int D = st.D;
+  for (int c = 0; c < 2; ++c) {
+    for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+      if (colour(st, i) != c) continue;
+      /* u = number of unsatisfied bonds (J s_i s_j = -1) at site i */
+      int u = 0;
+      for (int d = 0; d < D; ++d) {
+        uint32_t jf = neighbour(st, i, d, +1);
+        uint32_t jb = neighbour(st, i, d, -1);
+        int Jf = smp.J[(size_t)d * st.N + i];
+        int Jb = smp.J[(size_t)d * st.N + jb];
+        if (Jf * s[i] * s[jf] == -1) ++u;
+        if (Jb * s[i] * s[jb] == -1) ++u;
+      }
+      const int dE = 4 * D - 4 * u; /* energy change if s_i flips */
+      const uint32_t r = ising_random(st.seed, smp.s, slot, i, t);
+      bool flip;
+      if (algo == 0) {
+        /* Metropolis: dE <= 0 is always taken; else with prob exp(-beta dE) */
+        flip = (dE <= 0) || ((uint64_t)r < table_metropolis(beta, dE));
+      } else {
+        /* heat bath, Eq. (4) for the current value: keep with prob
+         * 1/(1+exp(-2 beta x)), x = s_i h_i = 2D - 2u */
+        const int x = 2 * D - 2 * u;
+        flip = !((uint64_t)r < table_heatbath(beta, x));
+      }
+      if (flip) {
+        s[i] = (int8_t)-s[i];
+        smp.E_run[slot] += dE;
+      }
+    }
+  }
+}
+
+void sweep_potts(const State& st, Sample& smp, int slot, double beta, uint64_t t) {
+  std::vector<int8_t>& s = smp.spin[slot];
+  const int q = st.q;
+  std::vector<int> n(q);
+  std::vector<uint64_t> T(q - 1);
+  for (int c = 0; c < 2; ++c) {
+    for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+      if (colour(st, i) != c) continue;
+      /* n_k = sum_j J_ij [s_j == k]: minus the local energy of state k */
+      std::fill(n.begin(), n.end(), 0);
+      for (int d = 0; d < st.D; ++d) {
+        uint32_t jf = neighbour(st, i, d, +1);
+        uint32_t jb = neighbour(st, i, d, -1);
+        n[s[jf]] += smp.J[(size_t)d * st.N + i];
+        n[s[jb]] += smp.J[(size_t)d * st.N + jb];
+      }
+      table_potts(beta, q, n.data(), T.data());
+      const uint32_t r = potts_random(st.seed, smp.s, slot, i, t);
+      int knew = q - 1;
+      for (int k = 0; k < q - 1; ++k)
+        if ((uint64_t)r < T[k]) {
+          knew = k;
+          break;
+        }
+      smp.E_run[slot] += n[s[i]] - n[knew];
+      s[i] = (int8_t)knew;
+    }
+  }
+}
+
+/* ---- measurement rows, indexed by temperature k (not slot) ---- */
+
+void measure_all(const State& st, int64_t* E, int64_t* M, int64_t* Q) {
+  const int K = st.K, R = st.R, q = st.q;
+  for (size_t si = 0; si < st.samples.size(); ++si) {
+    const Sample& smp = st.samples[si];
+    for (int k = 0; k < K; ++k) {
+      for (int a = 0; a < R; ++a) {
+        const int slot = smp.slot_at[a][k] * R + a;
+        const size_t row = (si * K + k) * R + a;
+        if (E) E[row] = energy(st, smp, slot);
+        if (M) {
+          if (st.model == 0)
+            M[row] = magnetisation(st, smp, slot);
+          else
+            potts_counts(st, smp, slot, M + row * q);
+        }
+      }
+      if (Q && R >= 2) {
+        const int sa = smp.slot_at[0][k] * R + 0;
+        const int sb = smp.slot_at[1][k] * R + 1;
+        Q[si * K + k] = overlap(st, smp, sa, sb);
+      }
+    }
+  }
+}
+
+static void append_row(State& st) {
+  const size_t S = st.samples.size();
+  const size_t nEM = S * st.K * st.R;
+  const size_t nM = st.model == 0 ? nEM : nEM * st.q;
+  const size_t nQ = S * st.K;
+  size_t e0 = st.ser_E.size(), m0 = st.ser_M.size(), q0 = st.ser_Q.size();
+  st.ser_E.resize(e0 + nEM);
+  st.ser_M.resize(m0 + nM);
+  st.ser_Q.resize(q0 + nQ, 0);
+  st.ser_sweep.push_back(st.sweeps);
+  measure_all(st, &st.ser_E[e0], &st.ser_M[m0], st.R >= 2 ? &st.ser_Q[q0] : nullptr);
+}
+
+/* nsweeps sweeps of every configuration; each configuration uses the beta
+ * of the temperature its slot currently holds.  Configurations are
+ * independent between swap steps, so samples are spread over threads; every
+ * sweep of every configuration is the plain serial loop above. */
+void run_sweeps(State& st, int algo, const double* beta, uint64_t nsweeps, uint32_t measure_every,
+                int nthreads) {
+  const int R = st.R, K = st.K;
+  uint64_t done = 0;
+  while (done < nsweeps) {
+    /* advance to the next measurement point (or the end) */
+    uint64_t chunk = nsweeps - done;
+    if (measure_every) {
+      uint64_t to_next = measure_every - (st.sweeps % measure_every);
+      chunk = std::min(chunk, to_next);
+    }
+    const uint64_t t0 = st.sweeps;
+    auto work = [&](size_t first, size_t stride) {
+      for (size_t si = first; si < st.samples.size(); si += stride) {
+        Sample& smp = st.samples[si];
+        for (int a = 0; a < R; ++a)
+          for (int k = 0; k < K; ++k) {
+            const int tslot = smp.slot_at[a][k];
+            const int slot = tslot * R + a;
+            for (uint64_t t = t0; t < t0 + chunk; ++t) {
+              if (st.model == 0)
+                sweep_ising(st, smp, slot, algo, beta[k], t);
+              else
+                sweep_potts(st, smp, slot, beta[k], t);
+            }
+          }
+      }
+    };
+    int nt = std::max(1, std::min<int>(nthreads, (int)st.samples.size()));
+    if (nt == 1) {
+      work(0, 1);
+    } else {
+      std::vector<std::thread> th;
+      for (int w = 0; w < nt; ++w) th.emplace_back(work, (size_t)w, (size_t)nt);
+      for (auto& x : th) x.join();
+    }
+    st.sweeps += chunk;
+    done += chunk;
+    if (measure_every && st.sweeps % measure_every == 0) append_row(st);
+  }
+}
+
+/* Parallel tempering swap step: for every chain (sample, replica) and for
+ * k = 0..K-2 in order, exchange the temperatures of the configurations at k
+ * and k+1 with probability min(1, exp((beta_k - beta_k+1)(E_k - E_k+1))). */
+void pt_swap(State& st, const double* beta) {
+  const int R = st.R, K = st.K;
+  for (auto& smp : st.samples) {
+    for (int a = 0; a < R; ++a) {
+      for (int k = 0; k + 1 < K; ++k) {
+        const int A = smp.slot_at[a][k], B = smp.slot_at[a][k + 1];
+        const int64_t EA = energy(st, smp, A * R + a);
+        const int64_t EB = energy(st, smp, B * R + a);
+        const int64_t d = EB - EA;
+        const double db = beta[k] - beta[k + 1];
+        bool swap;
+        if (d == 0 || db == 0.0 || ((d > 0) != (db > 0.0))) {
+          swap = true; /* db * d <= 0: the exchange does not lower the weight */
+        } else {
+          const uint32_t r = pt_random(st.seed, smp.s, a, k, st.steps);
+          const double dba = db > 0 ? db : -db;
+          const int64_t dabs = d > 0 ? d : -d;
+          swap = (uint64_t)r < table_pt(dba, dabs);
+        }
+        if (swap) {
+          smp.slot_at[a][k] = B;
+          smp.slot_at[a][k + 1] = A;
+          smp.accepted[a][k] += 1;
+        }
+      }
+    }
+  }
+  st.steps += 1;
+}
+
+}  // namespace oracle
