@@ -1,0 +1,304 @@
+"""GB300 checkerboard Monte Carlo for the EA +-J spin glass and the q=4 Potts glass.
+
+Thin ctypes binding over ``libianus.so`` (C ABI in ``include/ianus.h``).  This
+module only marshals arguments: every step of the sweep, the measurements and
+the parallel-tempering swaps run in the library's CUDA kernels.  PyTorch is
+used for device memory (the lattice state lives in a ``torch.uint8`` CUDA
+tensor handed to the library) and for the current CUDA stream.
+
+There is no CPU fallback: if the library cannot be built or loaded, or no
+CUDA device is present, constructing a :class:`Lattice` raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ABI_VERSION = 1
+
+EA_PM_J, POTTS4_J = 0, 1
+METROPOLIS, HEATBATH = 0, 1
+LAYOUT_AUTO, LAYOUT_I8, LAYOUT_BITS64, LAYOUT_U8X4 = 0, 1, 2, 3
+DISORDER_PM_J, DISORDER_FERRO = 0, 1
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = range(7)
+
+_MODELS = {"ea": EA_PM_J, "potts": POTTS4_J}
+_ALGOS = {"metropolis": METROPOLIS, "heatbath": HEATBATH}
+_LAYOUTS = {"auto": LAYOUT_AUTO, "i8": LAYOUT_I8, "bits64": LAYOUT_BITS64, "u8x4": LAYOUT_U8X4}
+
+EXPORTS = [
+    "ianus_required_bytes", "ianus_lattice_create", "ianus_sweep", "ianus_pt_swap", "ianus_sweep_pt",
+    "ianus_measure", "ianus_read_series", "ianus_get_spins_i8", "ianus_set_spins_i8", "ianus_get_couplings_i8",
+    "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
+    "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
+    "ianus_table_pt",
+]
+
+
+class IanusConfig(C.Structure):
+    _fields_ = [
+        ("abi_version", C.c_uint32),
+        ("model", C.c_int32),
+        ("dim", C.c_int32),
+        ("L", C.c_int32),
+        ("n_samples", C.c_int32),
+        ("n_replicas", C.c_int32),
+        ("n_temps", C.c_int32),
+        ("layout", C.c_int32),
+        ("disorder", C.c_int32),
+        ("series_capacity", C.c_uint32),
+        ("seed", C.c_uint64),
+        ("device_buffer", C.c_void_p),
+        ("device_buffer_bytes", C.c_size_t),
+        ("cuda_stream", C.c_void_p),
+    ]
+
+
+class IanusError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True):
+    """Load libianus.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise ImportError(f"libianus.so not built at {_build.LIB}")
+    L = C.CDLL(_build.LIB)
+    vp, i32, u32, u64, sz, dp = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_size_t, C.POINTER(C.c_double)
+    cfgp = C.POINTER(IanusConfig)
+    sig = {
+        "ianus_required_bytes": (sz, [cfgp]),
+        "ianus_lattice_create": (i32, [cfgp, C.POINTER(vp)]),
+        "ianus_sweep": (i32, [vp, i32, dp, u64, u32]),
+        "ianus_pt_swap": (i32, [vp]),
+        "ianus_sweep_pt": (i32, [vp, i32, dp, u64, u32, u32]),
+        "ianus_measure": (i32, [vp, vp, vp, vp]),
+        "ianus_read_series": (i32, [vp, vp, vp, vp, vp, sz, C.POINTER(sz), i32]),
+        "ianus_get_spins_i8": (i32, [vp, vp]),
+        "ianus_set_spins_i8": (i32, [vp, vp]),
+        "ianus_get_couplings_i8": (i32, [vp, vp]),
+        "ianus_set_couplings_i8": (i32, [vp, vp]),
+        "ianus_get_pt_state": (i32, [vp, vp, vp, C.POINTER(u64)]),
+        "ianus_get_sweeps": (i32, [vp, C.POINTER(u64)]),
+        "ianus_get_state": (i32, [vp, vp, sz, C.POINTER(sz)]),
+        "ianus_set_state": (i32, [vp, vp, sz]),
+        "ianus_synchronize": (i32, [vp]),
+        "ianus_destroy": (i32, [vp]),
+        "ianus_status_string": (C.c_char_p, [i32]),
+        "ianus_table_ising": (sz, [i32, i32, C.c_double, vp, sz]),
+        "ianus_table_potts": (sz, [C.c_double, vp, sz]),
+        "ianus_table_pt": (sz, [C.c_double, C.c_double, vp, sz]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(st: int) -> str:
+    return lib().ianus_status_string(st).decode()
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise IanusError(st, what)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def table_ising(dim: int, algo: int, beta: float) -> np.ndarray:
+    out = np.zeros(8, dtype=np.uint64)
+    n = lib().ianus_table_ising(dim, algo, beta, _ptr(out), 8)
+    return out[:n]
+
+
+def table_potts(beta: float) -> np.ndarray:
+    out = np.zeros(3 * 13 ** 4, dtype=np.uint64)
+    n = lib().ianus_table_potts(beta, _ptr(out), out.size)
+    if n != out.size:
+        raise ValueError("bad beta")
+    return out.reshape(13, 13, 13, 13, 3)
+
+
+def table_pt(beta_k: float, beta_k1: float, n: int) -> np.ndarray:
+    out = np.zeros(n, dtype=np.uint64)
+    lib().ianus_table_pt(beta_k, beta_k1, _ptr(out), n)
+    return out
+
+
+class Lattice:
+    """A batch of lattices: n_samples disorder samples x n_temps x n_replicas.
+
+    The device state is held in a torch CUDA byte tensor (``self.buffer``);
+    all work is enqueued on ``stream`` (default: torch's current stream).
+    """
+
+    def __init__(self, model="ea", dim=3, L=16, n_samples=1, n_replicas=1, n_temps=1, seed=0,
+                 layout="auto", ferro=False, series_capacity=0, stream=None, device=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("paper_0704_3573_gb300 needs a CUDA device (no CPU fallback)")
+        self._lib = lib()
+        self.model = _MODELS[model] if isinstance(model, str) else int(model)
+        self.dim, self.L = dim, L
+        self.N = L ** dim
+        self.S, self.R, self.K = n_samples, n_replicas, n_temps
+        self.mq = 4 if self.model == POTTS4_J else 1
+        dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        if stream is None:
+            stream = torch.cuda.current_stream(dev)
+        self.stream = stream
+        cfg = IanusConfig()
+        cfg.abi_version = ABI_VERSION
+        cfg.model = self.model
+        cfg.dim, cfg.L = dim, L
+        cfg.n_samples, cfg.n_replicas, cfg.n_temps = n_samples, n_replicas, n_temps
+        cfg.layout = _LAYOUTS[layout] if isinstance(layout, str) else int(layout)
+        cfg.disorder = DISORDER_FERRO if ferro else DISORDER_PM_J
+        cfg.series_capacity = series_capacity
+        cfg.seed = seed & 0xFFFFFFFFFFFFFFFF
+        nbytes = self._lib.ianus_required_bytes(C.byref(cfg))
+        if nbytes == 0:
+            raise IanusError(EINVAL, "ianus_required_bytes")
+        with torch.cuda.device(dev):
+            self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        cfg.device_buffer = self.buffer.data_ptr()
+        cfg.device_buffer_bytes = nbytes
+        cfg.cuda_stream = stream.cuda_stream
+        self.cfg = cfg
+        self._h = C.c_void_p()
+        with torch.cuda.device(dev):
+            _check(self._lib.ianus_lattice_create(C.byref(cfg), C.byref(self._h)), "ianus_lattice_create")
+        self.device = dev
+
+    # ---- lifetime ----
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ianus_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- the hot path ----
+    def _beta(self, beta) -> np.ndarray:
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(beta, dtype=np.float64), (self.K,)))
+
+    def sweep(self, algo, beta, nsweeps: int, measure_every: int = 0):
+        a = _ALGOS[algo] if isinstance(algo, str) else int(algo)
+        b = self._beta(beta)
+        _check(self._lib.ianus_sweep(self._h, a, b.ctypes.data_as(C.POINTER(C.c_double)), nsweeps, measure_every),
+               "ianus_sweep")
+
+    def pt_swap(self):
+        _check(self._lib.ianus_pt_swap(self._h), "ianus_pt_swap")
+
+    def sweep_pt(self, algo, beta, nsweeps: int, swap_every: int, measure_every: int = 0):
+        a = _ALGOS[algo] if isinstance(algo, str) else int(algo)
+        b = self._beta(beta)
+        _check(self._lib.ianus_sweep_pt(self._h, a, b.ctypes.data_as(C.POINTER(C.c_double)), nsweeps, swap_every,
+                                        measure_every), "ianus_sweep_pt")
+
+    # ---- observables ----
+    def measure(self, overlap: bool | None = None):
+        """(E [S,K,R], M [S,K,R] or [S,K,R,4], Q [S,K] or None), exact int64."""
+        S, K, R = self.S, self.K, self.R
+        E = np.zeros((S, K, R), dtype=np.int64)
+        M = np.zeros((S, K, R) if self.mq == 1 else (S, K, R, 4), dtype=np.int64)
+        want_q = (R >= 2) if overlap is None else overlap
+        Q = np.zeros((S, K), dtype=np.int64) if want_q else None
+        _check(self._lib.ianus_measure(self._h, _ptr(E), _ptr(M), _ptr(Q)), "ianus_measure")
+        return E, M, Q
+
+    def series(self, clear: bool = False, max_rows: int = 1 << 20):
+        S, K, R = self.S, self.K, self.R
+        cap = min(max_rows, self.cfg.series_capacity or 1024)
+        sw = np.zeros(cap, dtype=np.uint64)
+        E = np.zeros((cap, S, K, R), dtype=np.int64)
+        M = np.zeros((cap, S, K, R) if self.mq == 1 else (cap, S, K, R, 4), dtype=np.int64)
+        Q = np.zeros((cap, S, K), dtype=np.int64) if R >= 2 else None
+        n = C.c_size_t()
+        _check(self._lib.ianus_read_series(self._h, _ptr(sw), _ptr(E), _ptr(M), _ptr(Q), cap, C.byref(n),
+                                           int(clear)), "ianus_read_series")
+        k = n.value
+        return sw[:k], E[:k], M[:k], (Q[:k] if Q is not None else None)
+
+    def spins(self) -> np.ndarray:
+        out = np.zeros((self.S, self.K * self.R, self.N), dtype=np.int8)
+        _check(self._lib.ianus_get_spins_i8(self._h, _ptr(out)), "ianus_get_spins_i8")
+        return out
+
+    def set_spins(self, a):
+        a = np.ascontiguousarray(a, dtype=np.int8).reshape(self.S, self.K * self.R, self.N)
+        _check(self._lib.ianus_set_spins_i8(self._h, _ptr(a)), "ianus_set_spins_i8")
+
+    def couplings(self) -> np.ndarray:
+        out = np.zeros((self.S, self.dim, self.N), dtype=np.int8)
+        _check(self._lib.ianus_get_couplings_i8(self._h, _ptr(out)), "ianus_get_couplings_i8")
+        return out
+
+    def set_couplings(self, a):
+        a = np.ascontiguousarray(a, dtype=np.int8).reshape(self.S, self.dim, self.N)
+        _check(self._lib.ianus_set_couplings_i8(self._h, _ptr(a)), "ianus_set_couplings_i8")
+
+    def pt_state(self):
+        S, R, K = self.S, self.R, self.K
+        slot_at = np.zeros((S, R, K), dtype=np.int32)
+        acc = np.zeros((S, R, max(K - 1, 0)), dtype=np.uint64)
+        steps = C.c_uint64()
+        _check(self._lib.ianus_get_pt_state(self._h, _ptr(slot_at), _ptr(acc) if K > 1 else None, C.byref(steps)),
+               "ianus_get_pt_state")
+        return slot_at, acc, steps.value
+
+    @property
+    def sweeps(self) -> int:
+        v = C.c_uint64()
+        _check(self._lib.ianus_get_sweeps(self._h, C.byref(v)), "ianus_get_sweeps")
+        return v.value
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t()
+        _check(self._lib.ianus_get_state(self._h, None, 0, C.byref(n)), "ianus_get_state")
+        buf = np.zeros(n.value, dtype=np.uint8)
+        _check(self._lib.ianus_get_state(self._h, _ptr(buf), n.value, C.byref(n)), "ianus_get_state")
+        return buf.tobytes()
+
+    def set_state(self, blob: bytes):
+        buf = np.frombuffer(blob, dtype=np.uint8).copy()
+        _check(self._lib.ianus_set_state(self._h, _ptr(buf), buf.size), "ianus_set_state")
+
+    def synchronize(self):
+        _check(self._lib.ianus_synchronize(self._h), "ianus_synchronize")

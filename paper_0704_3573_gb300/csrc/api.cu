@@ -1,0 +1,654 @@
+// api.cu -- the extern "C" entry points of libianus.so (declared and
+// documented in include/ianus.h): lattice set-up, the sweep loop
+// (Sec. 2.2 sweeps of the two-colour update of Sec. 3.1), acceptance-table
+// uploads (Sec. 3.2), measurements (Sec. 4.1), parallel tempering,
+// checkpoints and error reporting.  Host logic only; all per-site work runs
+// in the kernels of k_plain.cu, k_msc.cu, k_potts.cu and k_pt.cu.
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "lattice.h"
+
+using namespace ianus;
+
+namespace {
+
+constexpr uint32_t kDefaultSeries = 1024;
+constexpr uint32_t kPtCapMax = 4096;
+constexpr uint64_t kStateMagic = 0x31534e4149ull;  // "IANS1"
+
+struct Sizes {
+  int model, D, L, S, R, K, slots, layout, G, Q4, mq;
+  uint32_t N, cap, pt_cap;
+  size_t off_spins, off_J, off_thr, off_tp, off_ptab, off_pttab, off_ptsign, off_slot, off_temp, off_acc_pt,
+      off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, total;
+  size_t spins_bytes, J_bytes;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Validates cfg and lays out the device buffer.  Returns IANUS_OK or an error.
+int plan(const ianus_config* c, Sizes& z) {
+  if (!c) return IANUS_EINVAL;
+  if (c->abi_version != IANUS_ABI_VERSION) return IANUS_EINVAL;
+  if (c->model != IANUS_EA_PM_J && c->model != IANUS_POTTS4_J) return IANUS_EINVAL;
+  if (c->dim != 2 && c->dim != 3) return IANUS_EINVAL;
+  if (c->L < 2 || (c->L & 1) || c->L > 4096) return IANUS_EINVAL;
+  if (c->n_samples < 1 || c->n_samples >= (1 << 18)) return IANUS_EINVAL;
+  if (c->n_replicas < 1 || c->n_temps < 1) return IANUS_EINVAL;
+  if ((long long)c->n_replicas * c->n_temps >= 4096) return IANUS_EINVAL;
+  if (c->disorder != IANUS_DISORDER_PM_J && c->disorder != IANUS_DISORDER_FERRO) return IANUS_EINVAL;
+  uint64_t N = 1;
+  for (int d = 0; d < c->dim; ++d) N *= (uint64_t)c->L;
+  if (N >= (1ull << 31)) return IANUS_EINVAL;
+  int layout = c->layout;
+  if (layout == IANUS_LAYOUT_AUTO) layout = c->model == IANUS_EA_PM_J ? IANUS_LAYOUT_BITS64 : IANUS_LAYOUT_U8X4;
+  if (layout < IANUS_LAYOUT_I8 || layout > IANUS_LAYOUT_U8X4) return IANUS_EINVAL;
+  if (c->model == IANUS_EA_PM_J && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
+  if (c->model == IANUS_POTTS4_J && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
+  z.model = c->model;
+  z.D = c->dim;
+  z.L = c->L;
+  z.S = c->n_samples;
+  z.R = c->n_replicas;
+  z.K = c->n_temps;
+  z.slots = z.R * z.K;
+  z.layout = layout;
+  z.N = (uint32_t)N;
+  z.G = (z.S + 63) / 64;
+  z.Q4 = (z.S + 3) / 4;
+  z.mq = c->model == IANUS_POTTS4_J ? 4 : 1;
+  z.cap = c->series_capacity ? c->series_capacity : kDefaultSeries;
+  z.pt_cap = z.K > 1 ? (uint32_t)std::min<uint64_t>((uint64_t)z.D * N / 2 + 1, kPtCapMax) : 0;
+  if (layout == IANUS_LAYOUT_I8) {
+    z.spins_bytes = (size_t)z.slots * z.S * N;
+    z.J_bytes = (size_t)z.S * z.D * N;
+  } else if (layout == IANUS_LAYOUT_BITS64) {
+    z.spins_bytes = (size_t)z.G * z.slots * N * 8;
+    z.J_bytes = (size_t)z.G * z.D * N * 8;
+  } else {
+    z.spins_bytes = (size_t)z.slots * z.Q4 * N * 4;
+    z.J_bytes = (size_t)z.Q4 * z.D * N * 4;
+  }
+  const size_t SKR = (size_t)z.S * z.K * z.R;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o += align256(bytes);
+    return at;
+  };
+  z.off_spins = take(z.spins_bytes);
+  z.off_J = take(z.J_bytes);
+  z.off_thr = take((size_t)z.K * kMaxClasses * 8);
+  z.off_tp = take(layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
+  z.off_ptab = take(layout == IANUS_LAYOUT_U8X4 ? (size_t)z.K * 65536 * 16 : 0);
+  z.off_pttab = take((size_t)std::max(z.K - 1, 0) * z.pt_cap * 8);
+  z.off_ptsign = take((size_t)std::max(z.K - 1, 1));
+  z.off_slot = take((size_t)z.S * z.R * z.K * 4 * 2);  // slot_at then temp_of
+  z.off_temp = z.off_slot + (size_t)z.S * z.R * z.K * 4;
+  z.off_acc_pt = take((size_t)z.S * z.R * std::max(z.K - 1, 1) * 8);
+  z.off_acc = take((size_t)z.S * z.slots * kAccStride * 8);
+  z.off_oE = take(SKR * 8);
+  z.off_oM = take(SKR * z.mq * 8);
+  z.off_oQ = take((size_t)z.S * z.K * 8);
+  z.off_sw = take((size_t)z.cap * 8);
+  z.off_sE = take((size_t)z.cap * SKR * 8);
+  z.off_sM = take((size_t)z.cap * SKR * z.mq * 8);
+  z.off_sQ = take((size_t)z.cap * z.S * z.K * 8);
+  z.off_err = take(8);
+  z.total = o;
+  return IANUS_OK;
+}
+
+// A failure code usable as the return value of both the int helpers and the
+// ianus_status entry points.
+struct Fail {
+  int v;
+  operator int() const { return v; }
+  operator ianus_status() const { return (ianus_status)v; }
+};
+
+Fail fail(Lattice* lat, int st) {
+  if (lat && st == IANUS_ECUDA) lat->sticky = IANUS_ESTATE;
+  return Fail{st};
+}
+
+#define CK(expr)                                     \
+  do {                                               \
+    cudaError_t e_ = (expr);                         \
+    if (e_ != cudaSuccess) return fail(lat, IANUS_ECUDA); \
+  } while (0)
+
+bool beta_ok(const double* beta, int K) {
+  for (int k = 0; k < K; ++k)
+    if (!std::isfinite(beta[k]) || beta[k] < 0.0) return false;
+  return true;
+}
+
+// Rebuild and upload the acceptance tables for (algo, beta).
+int upload_tables(Lattice* lat, int algo, const double* beta) {
+  const int K = lat->K;
+  if (lat->model == IANUS_EA_PM_J) {
+    std::vector<uint64_t> thr((size_t)K * kMaxClasses);
+    for (int k = 0; k < K; ++k) class_thresholds(lat->D, algo, beta[k], &thr[(size_t)k * kMaxClasses]);
+    CK(cudaMemcpyAsync(lat->thr, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, lat->stream));
+    if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
+  } else {
+    if (beta_ok(beta, K)) {
+      for (int k = 0; k < K; ++k)
+        if (beta[k] > 100.0) return IANUS_EINVAL;  // exp(6 beta) must stay finite
+    }
+    std::vector<uint64_t> flat(3u * 28561u);
+    std::vector<uint4> tab((size_t)K * 65536);
+    std::memset(tab.data(), 0, tab.size() * sizeof(uint4));
+    for (int k = 0; k < K; ++k) {
+      table_potts(beta[k], flat.data(), flat.size());
+      size_t idx = 0;
+      for (int n0 = 0; n0 < 13; ++n0)
+        for (int n1 = 0; n1 < 13; ++n1)
+          for (int n2 = 0; n2 < 13; ++n2)
+            for (int n3 = 0; n3 < 13; ++n3, ++idx) {
+              const uint32_t key = (uint32_t)n0 | ((uint32_t)n1 << 4) | ((uint32_t)n2 << 8) | ((uint32_t)n3 << 12);
+              uint4 e;
+              const uint64_t t0 = flat[3 * idx], t1 = flat[3 * idx + 1], t2 = flat[3 * idx + 2];
+              e.x = (uint32_t)t0;
+              e.y = (uint32_t)t1;
+              e.z = (uint32_t)t2;
+              e.w = (t0 >= kTwo32 ? 1u : 0u) | (t1 >= kTwo32 ? 2u : 0u) | (t2 >= kTwo32 ? 4u : 0u);
+              tab[(size_t)k * 65536 + key] = e;
+            }
+    }
+    CK(cudaMemcpyAsync(lat->ptab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice, lat->stream));
+  }
+  if (K > 1) {
+    // PT tables: T(m) for |d| = 4m until the first zero (or the largest
+    // possible |d|/4 = D N / 2).
+    std::vector<uint64_t> pt((size_t)(K - 1) * lat->pt_cap, 0);
+    std::vector<int8_t> sign((size_t)K - 1);
+    uint32_t len = 1;
+    const uint64_t mmax = (uint64_t)lat->D * lat->N / 2;
+    for (int k = 0; k + 1 < K; ++k) {
+      const double db = beta[k] - beta[k + 1];
+      sign[k] = db > 0 ? 1 : (db < 0 ? -1 : 0);
+      if (sign[k] == 0) continue;
+      std::vector<uint64_t> col(lat->pt_cap);
+      table_pt(beta[k], beta[k + 1], col.data(), col.size());
+      uint32_t m = 0;
+      while (m < lat->pt_cap && m < mmax && col[m] != 0) ++m;
+      if (m == lat->pt_cap && m < mmax) return IANUS_EUNSUPPORTED;  // temperatures too close for the table
+      for (uint32_t q = 0; q < m; ++q) pt[(size_t)k * lat->pt_cap + q] = col[q];
+      len = std::max(len, m);
+    }
+    lat->pt_len = lat->pt_cap;  // rows are stored with stride pt_cap; zeros end each row
+    (void)len;
+    CK(cudaMemcpyAsync(lat->pttab, pt.data(), pt.size() * 8, cudaMemcpyHostToDevice, lat->stream));
+    CK(cudaMemcpyAsync(lat->pt_sign, sign.data(), sign.size(), cudaMemcpyHostToDevice, lat->stream));
+  }
+  lat->beta.assign(beta, beta + K);
+  lat->algo = algo;
+  lat->tables_ok = true;
+  return IANUS_OK;
+}
+
+int measure_into(Lattice* lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q) {
+  want_q = want_q && lat->R >= 2;
+  if (lat->layout == IANUS_LAYOUT_I8)
+    CK(launch_measure_i8(*lat, want_q));
+  else if (lat->layout == IANUS_LAYOUT_BITS64)
+    CK(launch_measure_bits(*lat, want_q));
+  else
+    CK(launch_measure_potts(*lat, want_q));
+  CK(launch_finalize(*lat, E, M, Q, sweep_out, want_q));
+  return IANUS_OK;
+}
+
+int record_row(Lattice* lat) {
+  const size_t SKR = (size_t)lat->S * lat->K * lat->R;
+  const size_t row = (size_t)(lat->ser_count % lat->cap);
+  int st = measure_into(lat, lat->ser_E + row * SKR, lat->ser_M + row * SKR * lat->mq,
+                        lat->ser_Q + row * (size_t)lat->S * lat->K, lat->ser_sweep + row, 1);
+  if (st) return st;
+  lat->ser_count += 1;
+  return IANUS_OK;
+}
+
+int one_sweep(Lattice* lat, int inv) {
+  const uint64_t t = lat->sweeps;
+  for (int c = 0; c < 2; ++c) {
+    if (lat->layout == IANUS_LAYOUT_I8)
+      CK(launch_sweep_i8(*lat, c, t, inv));
+    else if (lat->layout == IANUS_LAYOUT_BITS64)
+      CK(launch_sweep_bits(*lat, c, t, inv));
+    else
+      CK(launch_sweep_potts(*lat, c, t));
+  }
+  lat->sweeps += 1;
+  return IANUS_OK;
+}
+
+bool same_beta(const Lattice* lat, const double* beta) {
+  if ((int)lat->beta.size() != lat->K) return false;
+  for (int k = 0; k < lat->K; ++k)
+    if (std::memcmp(&lat->beta[k], &beta[k], sizeof(double)) != 0) return false;
+  return true;
+}
+
+int do_pt_swap(Lattice* lat) {
+  int st = measure_into(lat, nullptr, nullptr, nullptr, nullptr, 0);
+  if (st) return st;
+  CK(launch_pt_swap(*lat));
+  lat->steps += 1;
+  if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
+  return IANUS_OK;
+}
+
+struct StateHeader {
+  uint64_t magic;
+  uint32_t version, model, dim, L, S, R, K, layout, disorder, pad;
+  uint64_t seed, sweeps, steps, spins_bytes, J_bytes;
+};
+
+}  // namespace
+
+extern "C" {
+
+size_t ianus_required_bytes(const ianus_config* cfg) {
+  Sizes z;
+  if (plan(cfg, z) != IANUS_OK) return 0;
+  return z.total;
+}
+
+ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) {
+  if (!out) return IANUS_EINVAL;
+  *out = nullptr;
+  Sizes z;
+  int st = plan(cfg, z);
+  if (st) return (ianus_status)st;
+  Lattice* lat = new (std::nothrow) Lattice();
+  if (!lat) return IANUS_ENOMEM;
+  lat->cfg = *cfg;
+  lat->model = z.model;
+  lat->D = z.D;
+  lat->L = z.L;
+  lat->S = z.S;
+  lat->R = z.R;
+  lat->K = z.K;
+  lat->slots = z.slots;
+  lat->layout = z.layout;
+  lat->G = z.G;
+  lat->Q4 = z.Q4;
+  lat->N = z.N;
+  lat->mq = z.mq;
+  lat->cap = z.cap;
+  lat->pt_cap = z.pt_cap;
+  lat->pt_len = z.pt_cap;
+  lat->geom.D = z.D;
+  lat->geom.L = z.L;
+  lat->geom.h = z.L / 2;
+  lat->geom.N = z.N;
+  lat->geom.half = z.N / 2;
+  lat->stream = (cudaStream_t)cfg->cuda_stream;
+  lat->keys = make_keys(cfg->seed);
+  lat->algo = -1;
+  lat->bytes = z.total;
+  if (cfg->device_buffer) {
+    if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {
+      delete lat;
+      return IANUS_EINVAL;
+    }
+    lat->base = (uint8_t*)cfg->device_buffer;
+    lat->owns_buffer = false;
+  } else {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, z.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      delete lat;
+      return e == cudaErrorMemoryAllocation ? IANUS_ENOMEM : IANUS_ECUDA;
+    }
+    lat->base = (uint8_t*)p;
+    lat->owns_buffer = true;
+  }
+  uint8_t* b = lat->base;
+  lat->spins = b + z.off_spins;
+  lat->J = b + z.off_J;
+  lat->thr = (uint64_t*)(b + z.off_thr);
+  lat->tp = (uint64_t*)(b + z.off_tp);
+  lat->ptab = (uint4*)(b + z.off_ptab);
+  lat->pttab = (uint64_t*)(b + z.off_pttab);
+  lat->pt_sign = (int8_t*)(b + z.off_ptsign);
+  lat->slot_at = (int32_t*)(b + z.off_slot);
+  lat->temp_of = (int32_t*)(b + z.off_temp);
+  lat->accepted = (uint64_t*)(b + z.off_acc_pt);
+  lat->acc = (int64_t*)(b + z.off_acc);
+  lat->out_E = (int64_t*)(b + z.off_oE);
+  lat->out_M = (int64_t*)(b + z.off_oM);
+  lat->out_Q = (int64_t*)(b + z.off_oQ);
+  lat->ser_sweep = (uint64_t*)(b + z.off_sw);
+  lat->ser_E = (int64_t*)(b + z.off_sE);
+  lat->ser_M = (int64_t*)(b + z.off_sM);
+  lat->ser_Q = (int64_t*)(b + z.off_sQ);
+  lat->err = (uint32_t*)(b + z.off_err);
+
+  auto bail = [&](int code) {
+    if (lat->owns_buffer) cudaFree(lat->base);
+    delete lat;
+    return (ianus_status)code;
+  };
+  if (cudaMemsetAsync(lat->base, 0, z.total, lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
+  {
+    std::vector<int32_t> perm((size_t)z.S * z.R * z.K);
+    for (size_t c = 0; c < perm.size(); ++c) perm[c] = (int32_t)(c % z.K);
+    if (cudaMemcpyAsync(lat->slot_at, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, lat->stream) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(lat->temp_of, perm.data(), perm.size() * 4, cudaMemcpyHostToDevice, lat->stream) !=
+            cudaSuccess)
+      return bail(IANUS_ECUDA);
+  }
+  const int ferro = cfg->disorder == IANUS_DISORDER_FERRO;
+  cudaError_t e;
+  if (lat->layout == IANUS_LAYOUT_I8)
+    e = launch_init_i8(*lat, ferro);
+  else if (lat->layout == IANUS_LAYOUT_BITS64)
+    e = launch_init_bits(*lat, ferro);
+  else
+    e = launch_init_potts(*lat, ferro);
+  if (e != cudaSuccess || cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
+  *out = reinterpret_cast<ianus_lattice*>(lat);
+  return IANUS_OK;
+}
+
+#define GET_LAT(h)                                          \
+  Lattice* lat = reinterpret_cast<Lattice*>(h);             \
+  if (!lat) return IANUS_EINVAL;                            \
+  if (lat->sticky) return (ianus_status)lat->sticky;
+
+ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uint64_t nsweeps,
+                         uint32_t measure_every) {
+  GET_LAT(h);
+  if (!beta || (algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH)) return IANUS_EINVAL;
+  if (!beta_ok(beta, lat->K)) return IANUS_EINVAL;
+  if (lat->model == IANUS_POTTS4_J && algo == IANUS_METROPOLIS) return IANUS_EUNSUPPORTED;
+  if (!lat->tables_ok || lat->algo != algo || !same_beta(lat, beta)) {
+    int st = upload_tables(lat, algo, beta);
+    if (st) return (ianus_status)st;
+  }
+  const int inv = algo == IANUS_HEATBATH;
+  for (uint64_t n = 0; n < nsweeps; ++n) {
+    int st = one_sweep(lat, inv);
+    if (st) return (ianus_status)st;
+    if (measure_every && lat->sweeps % measure_every == 0) {
+      st = record_row(lat);
+      if (st) return (ianus_status)st;
+    }
+  }
+  return IANUS_OK;
+}
+
+ianus_status ianus_pt_swap(ianus_lattice* h) {
+  GET_LAT(h);
+  if (lat->K < 2 || !lat->tables_ok) return IANUS_EINVAL;
+  if (lat->model != IANUS_EA_PM_J) return IANUS_EUNSUPPORTED;
+  return (ianus_status)do_pt_swap(lat);
+}
+
+ianus_status ianus_sweep_pt(ianus_lattice* h, int32_t algo, const double* beta, uint64_t nsweeps,
+                            uint32_t swap_every, uint32_t measure_every) {
+  GET_LAT(h);
+  if (swap_every == 0 || nsweeps % swap_every != 0) return IANUS_EINVAL;
+  if (lat->K < 2) return IANUS_EINVAL;
+  if (lat->model != IANUS_EA_PM_J) return IANUS_EUNSUPPORTED;
+  for (uint64_t n = 0; n < nsweeps; n += swap_every) {
+    ianus_status st = ianus_sweep(h, algo, beta, swap_every, measure_every);
+    if (st) return st;
+    st = ianus_pt_swap(h);
+    if (st) return st;
+  }
+  return IANUS_OK;
+}
+
+ianus_status ianus_measure(ianus_lattice* h, int64_t* energy, int64_t* magnetisation, int64_t* overlap) {
+  GET_LAT(h);
+  if (overlap && lat->R < 2) return IANUS_EINVAL;
+  int st = measure_into(lat, lat->out_E, lat->out_M, lat->out_Q, nullptr, overlap != nullptr);
+  if (st) return (ianus_status)st;
+  const size_t SKR = (size_t)lat->S * lat->K * lat->R;
+  if (energy) CK(cudaMemcpyAsync(energy, lat->out_E, SKR * 8, cudaMemcpyDeviceToHost, lat->stream));
+  if (magnetisation)
+    CK(cudaMemcpyAsync(magnetisation, lat->out_M, SKR * lat->mq * 8, cudaMemcpyDeviceToHost, lat->stream));
+  if (overlap)
+    CK(cudaMemcpyAsync(overlap, lat->out_Q, (size_t)lat->S * lat->K * 8, cudaMemcpyDeviceToHost, lat->stream));
+  CK(cudaStreamSynchronize(lat->stream));
+  return IANUS_OK;
+}
+
+ianus_status ianus_read_series(ianus_lattice* h, uint64_t* sweep, int64_t* energy, int64_t* magnetisation,
+                               int64_t* overlap, size_t cap_rows, size_t* n_rows, int32_t clear) {
+  GET_LAT(h);
+  const uint64_t first = std::max<uint64_t>(lat->ser_first, lat->ser_count > lat->cap ? lat->ser_count - lat->cap : 0);
+  uint64_t n = lat->ser_count - first;
+  if (n > cap_rows) n = cap_rows;
+  const size_t SKR = (size_t)lat->S * lat->K * lat->R, SK = (size_t)lat->S * lat->K;
+  for (uint64_t r = 0; r < n; ++r) {
+    const size_t pos = (size_t)((first + r) % lat->cap);
+    if (sweep) CK(cudaMemcpyAsync(sweep + r, lat->ser_sweep + pos, 8, cudaMemcpyDeviceToHost, lat->stream));
+    if (energy) CK(cudaMemcpyAsync(energy + r * SKR, lat->ser_E + pos * SKR, SKR * 8, cudaMemcpyDeviceToHost, lat->stream));
+    if (magnetisation)
+      CK(cudaMemcpyAsync(magnetisation + r * SKR * lat->mq, lat->ser_M + pos * SKR * lat->mq, SKR * lat->mq * 8,
+                         cudaMemcpyDeviceToHost, lat->stream));
+    if (overlap && lat->R >= 2)
+      CK(cudaMemcpyAsync(overlap + r * SK, lat->ser_Q + pos * SK, SK * 8, cudaMemcpyDeviceToHost, lat->stream));
+  }
+  CK(cudaStreamSynchronize(lat->stream));
+  if (n_rows) *n_rows = (size_t)n;
+  if (clear) lat->ser_first = lat->ser_count;
+  return IANUS_OK;
+}
+
+static ianus_status staged_get(Lattice* lat, int8_t* host, size_t bytes,
+                               cudaError_t (*fn)(Lattice&, int8_t*)) {
+  int8_t* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ENOMEM;
+  }
+  cudaError_t e = fn(*lat, d);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(host, d, bytes, cudaMemcpyDeviceToHost, lat->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+  cudaFree(d);
+  return e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
+}
+
+static ianus_status staged_set(Lattice* lat, const int8_t* host, size_t bytes,
+                               cudaError_t (*fn)(Lattice&, const int8_t*)) {
+  int8_t* d = nullptr;
+  if (cudaMalloc(&d, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ENOMEM;
+  }
+  cudaError_t e = cudaMemcpyAsync(d, host, bytes, cudaMemcpyHostToDevice, lat->stream);
+  if (e == cudaSuccess) e = fn(*lat, d);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+  cudaFree(d);
+  return e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
+}
+
+ianus_status ianus_get_spins_i8(ianus_lattice* h, int8_t* host) {
+  GET_LAT(h);
+  if (!host) return IANUS_EINVAL;
+  const size_t bytes = (size_t)lat->S * lat->slots * lat->N;
+  auto fn = lat->layout == IANUS_LAYOUT_I8 ? launch_get_spins_i8
+            : lat->layout == IANUS_LAYOUT_BITS64 ? launch_get_spins_bits : launch_get_spins_potts;
+  return staged_get(lat, host, bytes, fn);
+}
+
+ianus_status ianus_set_spins_i8(ianus_lattice* h, const int8_t* host) {
+  GET_LAT(h);
+  if (!host) return IANUS_EINVAL;
+  const size_t bytes = (size_t)lat->S * lat->slots * lat->N;
+  for (size_t i = 0; i < bytes; ++i) {
+    const int v = host[i];
+    if (lat->model == IANUS_EA_PM_J ? (v != 1 && v != -1) : (v < 0 || v > 3)) return IANUS_EINVAL;
+  }
+  auto fn = lat->layout == IANUS_LAYOUT_I8 ? launch_set_spins_i8
+            : lat->layout == IANUS_LAYOUT_BITS64 ? launch_set_spins_bits : launch_set_spins_potts;
+  return staged_set(lat, host, bytes, fn);
+}
+
+ianus_status ianus_get_couplings_i8(ianus_lattice* h, int8_t* host) {
+  GET_LAT(h);
+  if (!host) return IANUS_EINVAL;
+  const size_t bytes = (size_t)lat->S * lat->D * lat->N;
+  auto fn = lat->layout == IANUS_LAYOUT_I8 ? launch_get_couplings_i8
+            : lat->layout == IANUS_LAYOUT_BITS64 ? launch_get_couplings_bits : launch_get_couplings_potts;
+  return staged_get(lat, host, bytes, fn);
+}
+
+ianus_status ianus_set_couplings_i8(ianus_lattice* h, const int8_t* host) {
+  GET_LAT(h);
+  if (!host) return IANUS_EINVAL;
+  const size_t bytes = (size_t)lat->S * lat->D * lat->N;
+  for (size_t i = 0; i < bytes; ++i)
+    if (host[i] != 1 && host[i] != -1) return IANUS_EINVAL;
+  auto fn = lat->layout == IANUS_LAYOUT_I8 ? launch_set_couplings_i8
+            : lat->layout == IANUS_LAYOUT_BITS64 ? launch_set_couplings_bits : launch_set_couplings_potts;
+  return staged_set(lat, host, bytes, fn);
+}
+
+ianus_status ianus_get_pt_state(ianus_lattice* h, int32_t* slot_at, uint64_t* accepted, uint64_t* swap_steps) {
+  GET_LAT(h);
+  const size_t n = (size_t)lat->S * lat->R * lat->K;
+  if (slot_at) CK(cudaMemcpyAsync(slot_at, lat->slot_at, n * 4, cudaMemcpyDeviceToHost, lat->stream));
+  if (accepted && lat->K > 1)
+    CK(cudaMemcpyAsync(accepted, lat->accepted, (size_t)lat->S * lat->R * (lat->K - 1) * 8, cudaMemcpyDeviceToHost,
+                       lat->stream));
+  CK(cudaStreamSynchronize(lat->stream));
+  if (swap_steps) *swap_steps = lat->steps;
+  return IANUS_OK;
+}
+
+ianus_status ianus_get_sweeps(ianus_lattice* h, uint64_t* sweeps) {
+  GET_LAT(h);
+  if (!sweeps) return IANUS_EINVAL;
+  *sweeps = lat->sweeps;
+  return IANUS_OK;
+}
+
+ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_t* n) {
+  GET_LAT(h);
+  Sizes z;
+  plan(&lat->cfg, z);
+  const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
+  const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
+  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes;
+  if (n) *n = need;
+  if (!host_buf) return IANUS_OK;
+  if (cap < need) return IANUS_EINVAL;
+  StateHeader hd{};
+  hd.magic = kStateMagic;
+  hd.version = IANUS_ABI_VERSION;
+  hd.model = (uint32_t)lat->model;
+  hd.dim = (uint32_t)lat->D;
+  hd.L = (uint32_t)lat->L;
+  hd.S = (uint32_t)lat->S;
+  hd.R = (uint32_t)lat->R;
+  hd.K = (uint32_t)lat->K;
+  hd.layout = (uint32_t)lat->layout;
+  hd.disorder = (uint32_t)lat->cfg.disorder;
+  hd.seed = lat->cfg.seed;
+  hd.sweeps = lat->sweeps;
+  hd.steps = lat->steps;
+  hd.spins_bytes = z.spins_bytes;
+  hd.J_bytes = z.J_bytes;
+  uint8_t* o = (uint8_t*)host_buf;
+  std::memcpy(o, &hd, sizeof hd);
+  o += sizeof hd;
+  CK(cudaMemcpyAsync(o, lat->slot_at, perm, cudaMemcpyDeviceToHost, lat->stream));
+  o += perm;
+  CK(cudaMemcpyAsync(o, lat->temp_of, perm, cudaMemcpyDeviceToHost, lat->stream));
+  o += perm;
+  CK(cudaMemcpyAsync(o, lat->accepted, accb, cudaMemcpyDeviceToHost, lat->stream));
+  o += accb;
+  CK(cudaMemcpyAsync(o, lat->J, z.J_bytes, cudaMemcpyDeviceToHost, lat->stream));
+  o += z.J_bytes;
+  CK(cudaMemcpyAsync(o, lat->spins, z.spins_bytes, cudaMemcpyDeviceToHost, lat->stream));
+  CK(cudaStreamSynchronize(lat->stream));
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
+  Lattice* lat = reinterpret_cast<Lattice*>(h);
+  if (!lat || !host_buf) return IANUS_EINVAL;
+  Sizes z;
+  plan(&lat->cfg, z);
+  const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
+  const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
+  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes;
+  if (n < need) return IANUS_ESTATE;
+  StateHeader hd;
+  std::memcpy(&hd, host_buf, sizeof hd);
+  if (hd.magic != kStateMagic || hd.version != IANUS_ABI_VERSION || hd.model != (uint32_t)lat->model ||
+      hd.dim != (uint32_t)lat->D || hd.L != (uint32_t)lat->L || hd.S != (uint32_t)lat->S ||
+      hd.R != (uint32_t)lat->R || hd.K != (uint32_t)lat->K || hd.layout != (uint32_t)lat->layout ||
+      hd.seed != lat->cfg.seed || hd.spins_bytes != z.spins_bytes || hd.J_bytes != z.J_bytes)
+    return IANUS_ESTATE;
+  const uint8_t* in = (const uint8_t*)host_buf + sizeof hd;
+  lat->sticky = 0;
+  CK(cudaMemcpyAsync(lat->slot_at, in, perm, cudaMemcpyHostToDevice, lat->stream));
+  in += perm;
+  CK(cudaMemcpyAsync(lat->temp_of, in, perm, cudaMemcpyHostToDevice, lat->stream));
+  in += perm;
+  CK(cudaMemcpyAsync(lat->accepted, in, accb, cudaMemcpyHostToDevice, lat->stream));
+  in += accb;
+  CK(cudaMemcpyAsync(lat->J, in, z.J_bytes, cudaMemcpyHostToDevice, lat->stream));
+  in += z.J_bytes;
+  CK(cudaMemcpyAsync(lat->spins, in, z.spins_bytes, cudaMemcpyHostToDevice, lat->stream));
+  CK(cudaMemsetAsync(lat->err, 0, 4, lat->stream));
+  CK(cudaStreamSynchronize(lat->stream));
+  lat->sweeps = hd.sweeps;
+  lat->steps = hd.steps;
+  lat->tables_ok = false;  // per-lane planes depend on the restored permutation
+  return IANUS_OK;
+}
+
+ianus_status ianus_synchronize(ianus_lattice* h) {
+  GET_LAT(h);
+  CK(cudaStreamSynchronize(lat->stream));
+  uint32_t err = 0;
+  CK(cudaMemcpy(&err, lat->err, 4, cudaMemcpyDeviceToHost));
+  if (err & ERR_TIMEOUT) {
+    lat->sticky = IANUS_ESTATE;
+    return IANUS_ETIMEOUT;
+  }
+  if (err) {
+    lat->sticky = IANUS_ESTATE;
+    return IANUS_ESTATE;
+  }
+  return IANUS_OK;
+}
+
+ianus_status ianus_destroy(ianus_lattice* h) {
+  Lattice* lat = reinterpret_cast<Lattice*>(h);
+  if (!lat) return IANUS_OK;
+  cudaStreamSynchronize(lat->stream);
+  if (lat->owns_buffer) cudaFree(lat->base);
+  delete lat;
+  return IANUS_OK;
+}
+
+const char* ianus_status_string(int32_t status) {
+  switch (status) {
+    case IANUS_OK: return "ok";
+    case IANUS_EINVAL: return "invalid argument";
+    case IANUS_ENOMEM: return "out of memory";
+    case IANUS_ECUDA: return "CUDA runtime error";
+    case IANUS_ETIMEOUT: return "bounded device wait expired";
+    case IANUS_EUNSUPPORTED: return "unsupported configuration";
+    case IANUS_ESTATE: return "lattice in error state or bad state blob";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,112 @@
+// common.cuh -- device-side definitions shared by the library's kernels:
+// the counter-based random stream, lattice geometry and launch parameters.
+//
+// Everything here follows the definitions stated in include/ianus.h:
+// Philox4x32-10 (Salmon et al., SC'11) replaces the paper's Parisi-Rapuano
+// wheel (Sec. 3.3, Eq. (5)); the lattice and checkerboard are those of
+// Sec. 2.1 and Sec. 3.1.
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace ianus {
+
+enum : uint32_t { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6 };
+
+// Round keys of Philox4x32-10 for one seed: k[r] = key + r * (W0, W1) mod 2^32.
+// Passed by value inside kernel parameters so that the XOR with the round key
+// reads the constant bank.
+struct PhiloxKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+inline PhiloxKeys make_keys(uint64_t seed) {
+  PhiloxKeys K;
+  uint32_t a = (uint32_t)(seed & 0xffffffffu), b = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    K.k0[r] = a;
+    K.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return K;
+}
+
+// One Philox4x32-10 block: ten rounds of two 32x32->64 products; the high
+// halves are XORed with the other counter words and the round key.
+__device__ __forceinline__ uint4 philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          const PhiloxKeys& K) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Geometry of a periodic D-dimensional cube (D = 2 or 3) of even side L.
+// Natural site index i = x + L*(y + L*z).  The checkerboard-split index puts
+// the sites of one colour in one row (y, z) next to each other:
+//   split(x, y, z) = (2*(y + L*z) + colour) * (L/2) + x/2.
+struct Geom {
+  int D, L, h;    // h = L/2
+  uint32_t N;     // L^D
+  uint32_t half;  // N/2 sites per colour
+};
+
+__host__ __device__ __forceinline__ uint32_t split_index(const Geom& g, int x, int y, int z) {
+  const int c = (x + y + z) & 1;
+  const uint32_t row = (uint32_t)y + (uint32_t)g.L * (uint32_t)z;
+  return (2u * row + (uint32_t)c) * (uint32_t)g.h + (uint32_t)(x >> 1);
+}
+
+// Colour-c word w of the split layout -> coordinates and the split indices of
+// the site and of its 2D neighbours (which all have colour 1-c).
+struct Nbr {
+  uint32_t self;
+  uint32_t site;     // natural index (drives the random stream)
+  uint32_t xp, xm;   // x+1, x-1
+  uint32_t yp, ym;
+  uint32_t zp, zm;
+};
+
+__device__ __forceinline__ Nbr split_neighbours(const Geom& g, int c, uint32_t w) {
+  const uint32_t h = (uint32_t)g.h, L = (uint32_t)g.L;
+  const uint32_t row = w / h, k = w - row * h;
+  const uint32_t y = row % L, z = row / L;  // z = 0 for D = 2 (row < L)
+  const uint32_t xpar = (uint32_t)(c ^ (int)(y + z)) & 1u;
+  const uint32_t x = 2u * k + xpar;
+  const uint32_t oc = 1u - (uint32_t)c;
+  Nbr n;
+  n.self = (2u * row + (uint32_t)c) * h + k;
+  n.site = x + L * (y + L * z);
+  const uint32_t base_o = (2u * row + oc) * h;
+  const uint32_t kp = xpar ? (k + 1u == h ? 0u : k + 1u) : k;  // (x+1)/2 mod h
+  const uint32_t km = xpar ? k : (k == 0u ? h - 1u : k - 1u);  // (x-1)/2 mod h
+  n.xp = base_o + kp;
+  n.xm = base_o + km;
+  const uint32_t yp = (y + 1u == L) ? 0u : y + 1u, ym = (y == 0u) ? L - 1u : y - 1u;
+  n.yp = (2u * (yp + L * z) + oc) * h + k;
+  n.ym = (2u * (ym + L * z) + oc) * h + k;
+  if (g.D == 3) {
+    const uint32_t zp = (z + 1u == L) ? 0u : z + 1u, zm = (z == 0u) ? L - 1u : z - 1u;
+    n.zp = (2u * (y + L * zp) + oc) * h + k;
+    n.zm = (2u * (y + L * zm) + oc) * h + k;
+  } else {
+    n.zp = n.zm = 0u;
+  }
+  return n;
+}
+
+// Device error word bits (read by ianus_synchronize).
+enum : uint32_t { ERR_BOUNDS = 1u, ERR_PT_PARITY = 2u, ERR_TIMEOUT = 4u };
+
+}  // namespace ianus

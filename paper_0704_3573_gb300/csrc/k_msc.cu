@@ -1,0 +1,505 @@
+// k_msc.cu -- the bit-sliced multispin layout (IANUS_LAYOUT_BITS64).
+//
+// A 64-bit word holds one site of 64 independent disorder samples (lane l =
+// sample mod 64), the multi-sample idea of Sec. 4.1.1 carried to a GPU word,
+// with an independent random stream per sample.  Words of one colour are
+// stored next to each other (checkerboard-split order, Sec. 3.1), so the own
+// word, the 2D neighbour words and the coupling words of a warp are
+// contiguous loads.
+//
+// Update cell (Sec. 3.2) in bit-sliced form, per word:
+//   e_j = b_i ^ b_j ^ c_ij                    unsatisfied-bond bits (2D words)
+//   (u2,u1,u0) = carry-save adder tree of the e_j  (u = 0..2D per lane)
+//   m_u = lanes whose count is u              (class masks)
+//   threshold bit-plane p: t_p = OR_u (m_u & TP[u][p])
+//   lazy compare from the most significant plane: lanes stay undecided while
+//   their random bit equals the threshold bit; lt collects r < T.
+//   flip = lt ^ inv (Metropolis: inv = 0; heat bath: inv = ~0)
+// TP[u][p] are 64-bit lane masks, so every lane can carry its own threshold
+// (parallel tempering moves temperatures per sample).
+#include <algorithm>
+
+#include "lattice.h"
+
+namespace ianus {
+
+namespace {
+
+constexpr int kBlock = 256;
+
+struct BitsParams {
+  uint64_t* spins;        // [G][slots][N]
+  const uint64_t* J;      // [G][D][N]
+  const uint64_t* tp;     // [G][slots][kPlanes][kMaxClasses]
+  Geom geom;
+  int G, R, K, slots;
+  int colour;
+  uint32_t t_lo, t_hi;
+  uint32_t words_per_block;  // colour-c words handled by one block (multiple of kBlock)
+  PhiloxKeys keys;
+};
+
+template <int D>
+__device__ __forceinline__ void count_unsat(const uint64_t* e, uint64_t& u0, uint64_t& u1, uint64_t& u2) {
+  // full adder on three bit-vectors
+  const uint64_t sa = e[0] ^ e[1] ^ e[2];
+  const uint64_t ca = (e[0] & e[1]) | (e[0] & e[2]) | (e[1] & e[2]);
+  if (D == 3) {
+    const uint64_t sb = e[3] ^ e[4] ^ e[5];
+    const uint64_t cb = (e[3] & e[4]) | (e[3] & e[5]) | (e[4] & e[5]);
+    u0 = sa ^ sb;
+    const uint64_t k = sa & sb;
+    u1 = ca ^ cb ^ k;
+    u2 = (ca & cb) | (ca & k) | (cb & k);
+  } else {
+    u0 = sa ^ e[3];
+    const uint64_t k = sa & e[3];
+    u1 = ca ^ k;
+    u2 = ca & k;
+  }
+}
+
+// ALGO 0 = Metropolis (only classes u < D need a random number),
+// ALGO 1 = heat bath (all 2D+1 classes).
+template <int D, int ALGO, int RT>
+__global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
+  constexpr int NC = (ALGO == 0) ? D : 2 * D + 1;  // classes that take a random
+  extern __shared__ uint64_t sm_tp[];             // [R][kPlanes][kMaxClasses]
+  const int R = RT > 0 ? RT : p.R;
+  const int gt = blockIdx.y;  // g * K + tslot
+  const int g = gt / p.K, tslot = gt - g * p.K;
+  // stage this block's threshold planes
+  {
+    const uint64_t* src = p.tp + ((size_t)g * p.slots + (size_t)tslot * R) * kPlanes * kMaxClasses;
+    for (int k = threadIdx.x; k < R * kPlanes * kMaxClasses; k += kBlock) sm_tp[k] = src[k];
+  }
+  __syncthreads();
+  const Geom geom = p.geom;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = p.J + (size_t)g * D * N;
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
+    const Nbr n = split_neighbours(geom, p.colour, w);
+    uint64_t jw[2 * D];
+    jw[0] = __ldg(Jg + n.self);
+    jw[1] = __ldg(Jg + n.xm);
+    jw[2] = __ldg(Jg + N + n.self);
+    jw[3] = __ldg(Jg + N + n.ym);
+    if (D == 3) {
+      jw[4] = __ldg(Jg + 2u * N + n.self);
+      jw[5] = __ldg(Jg + 2u * N + n.zm);
+    }
+#pragma unroll 1
+    for (int a = 0; a < R; ++a) {
+      const int sigma = tslot * R + a;
+      uint64_t* sp = p.spins + ((size_t)g * p.slots + sigma) * N;
+      const uint64_t b = sp[n.self];
+      uint64_t e[2 * D];
+      e[0] = b ^ sp[n.xp] ^ jw[0];
+      e[1] = b ^ sp[n.xm] ^ jw[1];
+      e[2] = b ^ sp[n.yp] ^ jw[2];
+      e[3] = b ^ sp[n.ym] ^ jw[3];
+      if (D == 3) {
+        e[4] = b ^ sp[n.zp] ^ jw[4];
+        e[5] = b ^ sp[n.zm] ^ jw[5];
+      }
+      uint64_t u0, u1, u2;
+      count_unsat<D>(e, u0, u1, u2);
+      uint64_t m[2 * D + 1];
+#pragma unroll
+      for (int u = 0; u <= 2 * D; ++u)
+        m[u] = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
+      const uint64_t* tpa = sm_tp + (size_t)a * kPlanes * kMaxClasses;
+      uint64_t always = 0;
+#pragma unroll
+      for (int u = 0; u <= 2 * D; ++u) always |= m[u] & tpa[32 * kMaxClasses + u];
+      uint64_t lt = always;
+      uint64_t und = ~always;
+      if (ALGO == 0) {
+        // Metropolis: dE <= 0 (u >= D) always flips; those lanes are in `always`.
+        uint64_t need = 0;
+#pragma unroll
+        for (int u = 0; u < D; ++u) need |= m[u];
+        und &= need;
+      }
+      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
+#pragma unroll 1
+      for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
+        const uint4 x = philox10(n.site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
+                                    : ((uint64_t)x.z | ((uint64_t)x.w << 32));
+          const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * kMaxClasses;
+          uint64_t tb = 0;
+#pragma unroll
+          for (int u = 0; u < NC; ++u) tb |= m[u] & row[u];
+          lt |= und & ~r & tb;
+          und &= ~(r ^ tb);
+        }
+      }
+      const uint64_t flip = (ALGO == 0) ? lt : ~lt;
+      if (flip) sp[n.self] = b ^ flip;
+    }
+  }
+}
+
+// ---- initialisation: one Philox block gives the word of 64 samples ----
+
+__global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int slots, int ferro,
+                            PhiloxKeys keys) {
+  const uint64_t total = (uint64_t)G * geom.N;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = (uint32_t)(idx / geom.N), i = (uint32_t)(idx - (uint64_t)g * geom.N);
+    const uint32_t L = (uint32_t)geom.L;
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint32_t j = split_index(geom, x, y, z);
+    for (int d = 0; d < geom.D; ++d) {
+      const uint4 r = philox10(i, (uint32_t)d, (TAG_J << 28) | g, 0u, keys);
+      J[((size_t)g * geom.D + d) * geom.N + j] = ferro ? 0ull : ((uint64_t)r.x | ((uint64_t)r.y << 32));
+    }
+    for (int sg = 0; sg < slots; ++sg) {
+      const uint4 r = philox10(i, 0u, (TAG_INIT << 28) | ((uint32_t)sg << 12) | g, 0u, keys);
+      spins[((size_t)g * slots + sg) * geom.N + j] = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    }
+  }
+}
+
+// ---- threshold planes: TP[g][sigma][p][u], bit l = bit (31-p) of T of the
+// temperature sample 64g+l holds in slot sigma; plane 32 = (T == 2^32). ----
+
+__global__ void k_build_planes(uint64_t* tp, const uint64_t* thr, const int32_t* temp_of, int G, int S, int R,
+                               int K, int slots) {
+  const int total = G * slots * kMaxClasses;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int u = idx % kMaxClasses, rest = idx / kMaxClasses;
+    const int sigma = rest % slots, g = rest / slots;
+    const int tslot = sigma / R, a = sigma - tslot * R;
+    uint64_t planes[kPlanes];
+    for (int q = 0; q < kPlanes; ++q) planes[q] = 0;
+    for (int l = 0; l < 64; ++l) {
+      const int s = 64 * g + l;
+      const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
+      const uint64_t T = thr[(size_t)k * kMaxClasses + u];
+      if (T >= kTwo32) {
+        planes[32] |= 1ull << l;
+      } else {
+        for (int q = 0; q < 32; ++q)
+          if ((T >> (31 - q)) & 1ull) planes[q] |= 1ull << l;
+      }
+    }
+    for (int q = 0; q < kPlanes; ++q) tp[(((size_t)g * slots + sigma) * kPlanes + q) * kMaxClasses + u] = planes[q];
+  }
+}
+
+// ---- measurements: per-lane counts with vertical (bit-sliced) counters ----
+//
+// Per site and configuration: unsatisfied forward bonds U (E = 2U - D N) and
+// spin-down count B (M = N - 2B).  Each thread adds its masks into 8-plane vertical counters
+// over up to kMeasIters sites, then the warp transposes them with ballots and
+// lane l of the sample group gets its total by an atomic add.
+
+constexpr int kCtr = 8;
+constexpr int kMeasIters = 64;  // 3 increments per site (3D): 192 < 256
+
+__device__ __forceinline__ void ctr_add(uint64_t* c, uint64_t x) {
+#pragma unroll
+  for (int k = 0; k < kCtr; ++k) {
+    const uint64_t t = c[k] & x;
+    c[k] ^= x;
+    x = t;
+  }
+}
+
+// Warp-wide per-lane totals of a vertical counter; thread t receives the
+// totals of sample lanes t and t+32.
+__device__ __forceinline__ void ctr_flush(const uint64_t* c, long long& lo, long long& hi) {
+  const int lane = threadIdx.x & 31;
+  lo = hi = 0;
+#pragma unroll
+  for (int k = 0; k < kCtr; ++k) {
+    const uint32_t wl = (uint32_t)c[k], wh = (uint32_t)(c[k] >> 32);
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+      const uint32_t bl = __ballot_sync(0xffffffffu, (wl >> j) & 1u);
+      const uint32_t bh = __ballot_sync(0xffffffffu, (wh >> j) & 1u);
+      if (lane == j) {
+        lo += (long long)__popc(bl) << k;
+        hi += (long long)__popc(bh) << k;
+      }
+    }
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restrict__ spins,
+                                                         const uint64_t* __restrict__ J, int64_t* acc,
+                                                         Geom geom, int S, int R, int K, int slots) {
+  const int gt = blockIdx.y;  // g * slots + sigma
+  const int g = gt / slots, sigma = gt - g * slots;
+  const uint32_t N = geom.N, L = (uint32_t)geom.L, h = (uint32_t)geom.h;
+  const uint64_t* Jg = J + (size_t)g * D * N;
+  const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
+  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
+  const int lane = threadIdx.x & 31;
+  uint64_t cu[kCtr], cb[kCtr];
+#pragma unroll
+  for (int k = 0; k < kCtr; ++k) cu[k] = cb[k] = 0;
+  for (int it = 0; it < kMeasIters; ++it) {
+    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+    if (j < N) {
+      // split index j -> row, colour, k -> coordinates
+      const uint32_t rc = j / h, k = j - rc * h;
+      const uint32_t row = rc >> 1, c = rc & 1u;
+      const uint32_t y = row % L, z = row / L;
+      const uint32_t x = 2u * k + ((c ^ (y + z)) & 1u);
+      const uint64_t bi = sp[j];
+      const uint32_t xp = (x + 1u == L) ? 0u : x + 1u;
+      const uint32_t yp = (y + 1u == L) ? 0u : y + 1u;
+      ctr_add(cu, bi ^ sp[split_index(geom, (int)xp, (int)y, (int)z)] ^ Jg[j]);
+      ctr_add(cu, bi ^ sp[split_index(geom, (int)x, (int)yp, (int)z)] ^ Jg[N + j]);
+      if (D == 3) {
+        const uint32_t zp = (z + 1u == L) ? 0u : z + 1u;
+        ctr_add(cu, bi ^ sp[split_index(geom, (int)x, (int)y, (int)zp)] ^ Jg[2u * N + j]);
+      }
+      ctr_add(cb, bi);
+    }
+  }
+  long long lo, hi;
+  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
+  ctr_flush(cu, lo, hi);
+  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 0], (unsigned long long)lo);
+  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 0], (unsigned long long)hi);
+  ctr_flush(cb, lo, hi);
+  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 1], (unsigned long long)lo);
+  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 1], (unsigned long long)hi);
+}
+
+// Overlap at temperature k between replicas 0 and 1 (Sec. 4.1).  After
+// parallel-tempering swaps the configuration holding temperature k differs
+// per sample, so the word of replica a at temperature k is assembled lane by
+// lane: W_a = OR_t (sel[a][t] & spins[t*R + a]), sel[a][t] = lanes whose
+// temperature k sits in slot t.  X = popcount per lane of W_0 ^ W_1,
+// Q = N - 2X, stored in acc[s][k*R][6].
+__global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restrict__ spins,
+                                                         const int32_t* __restrict__ slot_at, int64_t* acc,
+                                                         uint32_t N, int S, int R, int K, int slots) {
+  extern __shared__ uint64_t sel[];  // [2][K]
+  const int gk = blockIdx.y;
+  const int g = gk / K, k = gk - g * K;
+  for (int t = threadIdx.x; t < 2 * K; t += kBlock) {
+    const int a = t / K, ts = t - a * K;
+    uint64_t m = 0;
+    for (int l = 0; l < 64; ++l) {
+      const int s = 64 * g + l;
+      const int at = s < S ? slot_at[((size_t)s * R + a) * K + k] : k;
+      if (at == ts) m |= 1ull << l;
+    }
+    sel[t] = m;
+  }
+  __syncthreads();
+  const uint64_t* sg = spins + (size_t)g * slots * N;
+  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
+  const int lane = threadIdx.x & 31;
+  uint64_t cx[kCtr];
+#pragma unroll
+  for (int q = 0; q < kCtr; ++q) cx[q] = 0;
+  for (int it = 0; it < kMeasIters; ++it) {
+    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+    if (j < N) {
+      uint64_t w0 = 0, w1 = 0;
+      for (int t = 0; t < K; ++t) {
+        const uint64_t m0 = sel[t], m1 = sel[K + t];
+        if (m0) w0 |= m0 & sg[((size_t)t * R + 0) * N + j];
+        if (m1) w1 |= m1 & sg[((size_t)t * R + 1) * N + j];
+      }
+      ctr_add(cx, w0 ^ w1);
+    }
+  }
+  long long lo, hi;
+  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
+  ctr_flush(cx, lo, hi);
+  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + (size_t)k * R) * kAccStride + 6], (unsigned long long)lo);
+  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + (size_t)k * R) * kAccStride + 6], (unsigned long long)hi);
+}
+
+// ---- layout conversions (natural int8 <-> bit-sliced split words) ----
+
+__global__ void k_get_spins_bits(const uint64_t* spins, int8_t* out, Geom geom, int S, int slots) {
+  const uint64_t total = (uint64_t)S * slots * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const uint64_t rest = idx / geom.N;
+    const int sg = (int)(rest % slots), s = (int)(rest / slots);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint64_t w = spins[((size_t)(s >> 6) * slots + sg) * geom.N + split_index(geom, x, y, z)];
+    out[idx] = ((w >> (s & 63)) & 1ull) ? -1 : 1;
+  }
+}
+
+__global__ void k_set_spins_bits(uint64_t* spins, const int8_t* in, Geom geom, int S, int G, int slots) {
+  const uint64_t total = (uint64_t)G * slots * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const uint64_t rest = idx / geom.N;
+    const int sg = (int)(rest % slots), g = (int)(rest / slots);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    uint64_t* wp = &spins[((size_t)g * slots + sg) * geom.N + split_index(geom, x, y, z)];
+    uint64_t w = *wp;
+    for (int l = 0; l < 64; ++l) {
+      const int s = 64 * g + l;
+      if (s >= S) break;
+      const uint64_t bit = in[((size_t)s * slots + sg) * geom.N + i] < 0 ? 1ull : 0ull;
+      w = (w & ~(1ull << l)) | (bit << l);
+    }
+    *wp = w;
+  }
+}
+
+__global__ void k_get_couplings_bits(const uint64_t* J, int8_t* out, Geom geom, int S) {
+  const uint64_t total = (uint64_t)S * geom.D * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const uint64_t rest = idx / geom.N;
+    const int d = (int)(rest % geom.D), s = (int)(rest / geom.D);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint64_t w = J[((size_t)(s >> 6) * geom.D + d) * geom.N + split_index(geom, x, y, z)];
+    out[idx] = ((w >> (s & 63)) & 1ull) ? -1 : 1;
+  }
+}
+
+__global__ void k_set_couplings_bits(uint64_t* J, const int8_t* in, Geom geom, int S, int G) {
+  const uint64_t total = (uint64_t)G * geom.D * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const uint64_t rest = idx / geom.N;
+    const int d = (int)(rest % geom.D), g = (int)(rest / geom.D);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    uint64_t* wp = &J[((size_t)g * geom.D + d) * geom.N + split_index(geom, x, y, z)];
+    uint64_t w = *wp;
+    for (int l = 0; l < 64; ++l) {
+      const int s = 64 * g + l;
+      if (s >= S) break;
+      const uint64_t bit = in[((size_t)s * geom.D + d) * geom.N + i] < 0 ? 1ull : 0ull;
+      w = (w & ~(1ull << l)) | (bit << l);
+    }
+    *wp = w;
+  }
+}
+
+inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 152u * 16u) {
+  uint64_t g = (total + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g == 0) g = 1;
+  return (unsigned)g;
+}
+
+template <int D, int ALGO>
+cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
+  if (lat.R == 1)
+    k_sweep_bits<D, ALGO, 1><<<grid, kBlock, smem, lat.stream>>>(p);
+  else if (lat.R == 2)
+    k_sweep_bits<D, ALGO, 2><<<grid, kBlock, smem, lat.stream>>>(p);
+  else
+    k_sweep_bits<D, ALGO, 0><<<grid, kBlock, smem, lat.stream>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_init_bits(Lattice& lat, int ferro) {
+  k_init_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>((uint64_t*)lat.spins, (uint64_t*)lat.J,
+                                                                          lat.geom, lat.G, lat.slots, ferro, lat.keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_planes(Lattice& lat) {
+  k_build_planes<<<grid_for((uint64_t)lat.G * lat.slots * kMaxClasses, 128), 128, 0, lat.stream>>>(
+      lat.tp, lat.thr, lat.temp_of, lat.G, lat.S, lat.R, lat.K, lat.slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
+  BitsParams p;
+  p.spins = (uint64_t*)lat.spins;
+  p.J = (const uint64_t*)lat.J;
+  p.tp = lat.tp;
+  p.geom = lat.geom;
+  p.G = lat.G;
+  p.R = lat.R;
+  p.K = lat.K;
+  p.slots = lat.slots;
+  p.colour = colour;
+  p.t_lo = (uint32_t)(t & 0xffffffffu);
+  p.t_hi = (uint32_t)(t >> 32);
+  p.keys = lat.keys;
+  // blocks per (group, temperature slot): enough to fill the GPU ~4 deep
+  const uint32_t half = lat.geom.half;
+  const uint32_t gts = (uint32_t)(lat.G * lat.K);
+  uint32_t target_blocks = (152u * 8u + gts - 1) / gts;
+  uint32_t wpb = (half + target_blocks - 1) / target_blocks;
+  wpb = ((wpb + kBlock - 1) / kBlock) * kBlock;
+  if (wpb < (uint32_t)kBlock) wpb = kBlock;
+  p.words_per_block = wpb;
+  dim3 grid((half + wpb - 1) / wpb, gts);
+  const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
+  const int algo = inv ? 1 : 0;
+  if (lat.D == 3)
+    return algo ? sweep_dispatch<3, 1>(lat, p, grid, smem) : sweep_dispatch<3, 0>(lat, p, grid, smem);
+  return algo ? sweep_dispatch<2, 1>(lat, p, grid, smem) : sweep_dispatch<2, 0>(lat, p, grid, smem);
+}
+
+cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
+  cudaError_t e = cudaMemsetAsync(lat.acc, 0, (size_t)lat.S * lat.slots * kAccStride * sizeof(int64_t), lat.stream);
+  if (e != cudaSuccess) return e;
+  const uint32_t per_block = kBlock * kMeasIters;
+  dim3 grid((lat.N + per_block - 1) / per_block, (unsigned)(lat.G * lat.slots));
+  if (lat.D == 3)
+    k_measure_bits<3><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
+                                                        lat.geom, lat.S, lat.R, lat.K, lat.slots);
+  else
+    k_measure_bits<2><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
+                                                        lat.geom, lat.S, lat.R, lat.K, lat.slots);
+  if (want_q && lat.R >= 2) {
+    dim3 gq((lat.N + per_block - 1) / per_block, (unsigned)(lat.G * lat.K));
+    k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(
+        (const uint64_t*)lat.spins, lat.slot_at, lat.acc, lat.N, lat.S, lat.R, lat.K, lat.slots);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out) {
+  k_get_spins_bits<<<grid_for((uint64_t)lat.S * lat.slots * lat.N), 256, 0, lat.stream>>>(
+      (const uint64_t*)lat.spins, dev_out, lat.geom, lat.S, lat.slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_spins_bits(Lattice& lat, const int8_t* dev_in) {
+  k_set_spins_bits<<<grid_for((uint64_t)lat.G * lat.slots * lat.N), 256, 0, lat.stream>>>(
+      (uint64_t*)lat.spins, dev_in, lat.geom, lat.S, lat.G, lat.slots);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_couplings_bits(Lattice& lat, int8_t* dev_out) {
+  k_get_couplings_bits<<<grid_for((uint64_t)lat.S * lat.D * lat.N), 256, 0, lat.stream>>>(
+      (const uint64_t*)lat.J, dev_out, lat.geom, lat.S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_couplings_bits(Lattice& lat, const int8_t* dev_in) {
+  k_set_couplings_bits<<<grid_for((uint64_t)lat.G * lat.D * lat.N), 256, 0, lat.stream>>>(
+      (uint64_t*)lat.J, dev_in, lat.geom, lat.S, lat.G);
+  return cudaGetLastError();
+}
+
+}  // namespace ianus

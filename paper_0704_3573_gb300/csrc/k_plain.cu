@@ -1,0 +1,287 @@
+// k_plain.cu -- the plain one-byte-per-spin layout (IANUS_LAYOUT_I8).
+//
+// One thread updates one site of the active colour of one configuration
+// (Sec. 3.1: all sites of one colour are independent).  The update cell of
+// Sec. 3.2 becomes: count the unsatisfied bonds u among the 2D bonds, look
+// up the class threshold T(u), compare against the site's 32-bit random
+// number, write the new spin.  The random number is produced lazily, two
+// bit-planes per Philox call, from the most significant bit down, and the
+// comparison stops at the first plane where r and T differ.
+#include <algorithm>
+
+#include "lattice.h"
+
+namespace ianus {
+
+namespace {
+
+struct I8Params {
+  int8_t* spins;            // [slots][S][N]
+  const int8_t* J;          // [S][D][N]
+  const uint64_t* thr;      // [K][kMaxClasses]
+  const int32_t* temp_of;   // [S][R][K]
+  int S, R, K, slots, L;
+  uint32_t N, half;
+  int colour, inv;
+  uint32_t t_lo, t_hi;
+  PhiloxKeys keys;
+};
+
+// r < T for the random r of (sample, slot, site, sweep), decided from the
+// most significant plane down.  T in [0, 2^32].
+__device__ __forceinline__ bool lazy_less(uint64_t T, const I8Params& p, int s, int sigma, uint32_t site) {
+  if (T >= kTwo32) return true;
+  const uint32_t T32 = (uint32_t)T;
+  const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
+  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+#pragma unroll 1
+  for (uint32_t m = 0; m < 16u; ++m) {
+    const uint4 x = philox10(site, p.t_lo, c2base | (m << 24), p.t_hi, p.keys);
+    const uint32_t w0 = lane < 32u ? (x.x >> lane) : (x.y >> (lane - 32u));
+    const uint32_t w1 = lane < 32u ? (x.z >> lane) : (x.w >> (lane - 32u));
+    const uint32_t r0 = w0 & 1u, t0 = (T32 >> (31u - 2u * m)) & 1u;
+    if (r0 != t0) return r0 < t0;
+    const uint32_t r1 = w1 & 1u, t1 = (T32 >> (30u - 2u * m)) & 1u;
+    if (r1 != t1) return r1 < t1;
+  }
+  return false;  // r == T
+}
+
+template <int D>
+__global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
+  const uint64_t total = (uint64_t)p.slots * p.S * p.half;
+  const uint32_t L = (uint32_t)p.L, h = L / 2u;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lat = (uint32_t)(idx / p.half);
+    const uint32_t w = (uint32_t)(idx - (uint64_t)lat * p.half);
+    const int sigma = (int)(lat / (uint32_t)p.S);
+    const int s = (int)(lat - (uint32_t)sigma * (uint32_t)p.S);
+    const uint32_t row = w / h, k = w - row * h;
+    const uint32_t y = row % L, z = row / L;
+    const uint32_t x = 2u * k + ((uint32_t)(p.colour ^ (int)(y + z)) & 1u);
+    const uint32_t i = x + L * (y + L * z);
+    int8_t* sp = p.spins + (size_t)lat * p.N;
+    const int8_t* Jp = p.J + (size_t)s * D * p.N;
+    const int si = sp[i];
+    // neighbours along each axis (periodic)
+    const uint32_t xp = (x + 1u == L ? 0u : x + 1u) + L * (y + L * z);
+    const uint32_t xm = (x == 0u ? L - 1u : x - 1u) + L * (y + L * z);
+    const uint32_t yp = x + L * ((y + 1u == L ? 0u : y + 1u) + L * z);
+    const uint32_t ym = x + L * ((y == 0u ? L - 1u : y - 1u) + L * z);
+    int u = 0;
+    u += (Jp[i] * si * sp[xp]) < 0;
+    u += (Jp[xm] * si * sp[xm]) < 0;
+    u += (Jp[p.N + i] * si * sp[yp]) < 0;
+    u += (Jp[p.N + ym] * si * sp[ym]) < 0;
+    if (D == 3) {
+      const uint32_t zp = x + L * (y + L * (z + 1u == L ? 0u : z + 1u));
+      const uint32_t zm = x + L * (y + L * (z == 0u ? L - 1u : z - 1u));
+      u += (Jp[2u * p.N + i] * si * sp[zp]) < 0;
+      u += (Jp[2u * p.N + zm] * si * sp[zm]) < 0;
+    }
+    const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+    const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
+    const uint64_t T = p.thr[(size_t)kt * kMaxClasses + u];
+    const bool less = lazy_less(T, p, s, sigma, i);
+    if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
+  }
+}
+
+struct InitParams {
+  int8_t* spins;
+  int8_t* J;
+  int S, D, slots;
+  uint32_t N;
+  int ferro;
+  PhiloxKeys keys;
+};
+
+__device__ __forceinline__ uint32_t lane_bit(const uint4& x, uint32_t lane) {
+  return (lane < 32u ? (x.x >> lane) : (x.y >> (lane - 32u))) & 1u;
+}
+
+__global__ void k_init_i8(const InitParams p) {
+  const uint64_t total = (uint64_t)p.S * p.N;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = (uint32_t)(idx / p.N), i = (uint32_t)(idx - (uint64_t)s * p.N);
+    const uint32_t g = s >> 6, lane = s & 63u;
+    for (int d = 0; d < p.D; ++d) {
+      const uint4 x = philox10(i, (uint32_t)d, (TAG_J << 28) | g, 0u, p.keys);
+      p.J[((size_t)s * p.D + d) * p.N + i] = (p.ferro || !lane_bit(x, lane)) ? 1 : -1;
+    }
+    for (int sg = 0; sg < p.slots; ++sg) {
+      const uint4 x = philox10(i, 0u, (TAG_INIT << 28) | ((uint32_t)sg << 12) | g, 0u, p.keys);
+      p.spins[((size_t)sg * p.S + s) * p.N + i] = lane_bit(x, lane) ? -1 : 1;
+    }
+  }
+}
+
+// Block per configuration: E = -sum_bonds J s s and M = sum s (Sec. 4.1).
+template <int D>
+__global__ void __launch_bounds__(256) k_measure_i8(const int8_t* __restrict__ spins,
+                                                    const int8_t* __restrict__ J, int64_t* acc, int S,
+                                                    int R, int slots, int L, uint32_t N) {
+  __shared__ long long red[3][8];
+  for (uint32_t lat = blockIdx.x; lat < (uint32_t)(slots * S); lat += gridDim.x) {
+    const int sigma = (int)(lat / (uint32_t)S), s = (int)(lat - (uint32_t)sigma * S);
+    const int8_t* sp = spins + (size_t)lat * N;
+    const int8_t* Jp = J + (size_t)s * D * N;
+    long long e = 0, m = 0;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+      const uint32_t x = i % (uint32_t)L, y = (i / (uint32_t)L) % (uint32_t)L;
+      const uint32_t z = D == 3 ? i / ((uint32_t)L * (uint32_t)L) : 0u;
+      const int si = sp[i];
+      const uint32_t xp = (x + 1u == (uint32_t)L ? 0u : x + 1u) + (uint32_t)L * (y + (uint32_t)L * z);
+      const uint32_t yp = x + (uint32_t)L * ((y + 1u == (uint32_t)L ? 0u : y + 1u) + (uint32_t)L * z);
+      e -= Jp[i] * si * sp[xp];
+      e -= Jp[N + i] * si * sp[yp];
+      if (D == 3) {
+        const uint32_t zp = x + (uint32_t)L * (y + (uint32_t)L * (z + 1u == (uint32_t)L ? 0u : z + 1u));
+        e -= Jp[2u * N + i] * si * sp[zp];
+      }
+      m += si;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      e += __shfl_down_sync(0xffffffffu, e, off);
+      m += __shfl_down_sync(0xffffffffu, m, off);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[0][wid] = e;
+      red[1][wid] = m;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long E = 0, M = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        E += red[0][w];
+        M += red[1][w];
+      }
+      int64_t* a = acc + ((size_t)s * slots + sigma) * kAccStride;
+      a[0] = E;
+      a[1] = M;
+    }
+    __syncthreads();
+  }
+}
+
+// Block per (sample, temperature k): Q = sum_i s_i^0 s_i^1 between the
+// configurations of replicas 0 and 1 that currently hold temperature k
+// (Sec. 4.1 overlap).  Stored in acc[s][k*R][6].
+__global__ void __launch_bounds__(256) k_overlap_i8(const int8_t* __restrict__ spins, const int32_t* slot_at,
+                                                    int64_t* acc, int S, int R, int K, int slots, uint32_t N) {
+  __shared__ long long red[8];
+  for (uint32_t sk = blockIdx.x; sk < (uint32_t)(S * K); sk += gridDim.x) {
+    const int s = (int)(sk / (uint32_t)K), k = (int)(sk - (uint32_t)s * K);
+    const int s0 = slot_at[((size_t)s * R + 0) * K + k] * R + 0;
+    const int s1 = slot_at[((size_t)s * R + 1) * K + k] * R + 1;
+    const int8_t* a0 = spins + ((size_t)s0 * S + s) * N;
+    const int8_t* a1 = spins + ((size_t)s1 * S + s) * N;
+    long long q = 0;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += a0[i] * a1[i];
+    for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long Q = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Q += red[w];
+      acc[((size_t)s * slots + (size_t)k * R) * kAccStride + 6] = Q;
+    }
+    __syncthreads();
+  }
+}
+
+// natural-order conversions: device [S][slots][N] <-> [slots][S][N]
+__global__ void k_copy_spins_i8(int8_t* spins, int8_t* out, const int8_t* in, int S, int slots, uint32_t N) {
+  const uint64_t total = (uint64_t)S * slots * N;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t i = idx % N, rest = idx / N;
+    const uint64_t sg = rest % slots, s = rest / slots;
+    int8_t* v = spins + (sg * S + s) * N + i;
+    if (out) out[idx] = *v;
+    else *v = in[idx];
+  }
+}
+
+inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 152u * 16u) {
+  uint64_t g = (total + block - 1) / block;
+  if (g > cap) g = cap;
+  if (g == 0) g = 1;
+  return (unsigned)g;
+}
+
+}  // namespace
+
+cudaError_t launch_init_i8(Lattice& lat, int ferro) {
+  InitParams p{(int8_t*)lat.spins, (int8_t*)lat.J, lat.S, lat.D, lat.slots, lat.N, ferro, lat.keys};
+  k_init_i8<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
+  I8Params p;
+  p.spins = (int8_t*)lat.spins;
+  p.J = (const int8_t*)lat.J;
+  p.thr = lat.thr;
+  p.temp_of = lat.temp_of;
+  p.S = lat.S;
+  p.R = lat.R;
+  p.K = lat.K;
+  p.slots = lat.slots;
+  p.L = lat.L;
+  p.N = lat.N;
+  p.half = lat.N / 2;
+  p.colour = colour;
+  p.inv = inv;
+  p.t_lo = (uint32_t)(t & 0xffffffffu);
+  p.t_hi = (uint32_t)(t >> 32);
+  p.keys = lat.keys;
+  const uint64_t total = (uint64_t)lat.slots * lat.S * p.half;
+  const unsigned grid = grid_for(total, 256, 152u * 8u);
+  if (lat.D == 3)
+    k_sweep_i8<3><<<grid, 256, 0, lat.stream>>>(p);
+  else
+    k_sweep_i8<2><<<grid, 256, 0, lat.stream>>>(p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
+  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)lat.slots * lat.S, 152u * 8u);
+  if (lat.D == 3)
+    k_measure_i8<3><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.acc,
+                                                   lat.S, lat.R, lat.slots, lat.L, lat.N);
+  else
+    k_measure_i8<2><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.acc,
+                                                   lat.S, lat.R, lat.slots, lat.L, lat.N);
+  if (want_q && lat.R >= 2) {
+    const unsigned gq = (unsigned)std::min<uint64_t>((uint64_t)lat.S * lat.K, 152u * 8u);
+    k_overlap_i8<<<gq, 256, 0, lat.stream>>>((const int8_t*)lat.spins, lat.slot_at, lat.acc, lat.S, lat.R, lat.K,
+                                            lat.slots, lat.N);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_spins_i8(Lattice& lat, int8_t* dev_out) {
+  k_copy_spins_i8<<<grid_for((uint64_t)lat.S * lat.slots * lat.N), 256, 0, lat.stream>>>(
+      (int8_t*)lat.spins, dev_out, nullptr, lat.S, lat.slots, lat.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_spins_i8(Lattice& lat, const int8_t* dev_in) {
+  k_copy_spins_i8<<<grid_for((uint64_t)lat.S * lat.slots * lat.N), 256, 0, lat.stream>>>(
+      (int8_t*)lat.spins, nullptr, dev_in, lat.S, lat.slots, lat.N);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out) {
+  return cudaMemcpyAsync(dev_out, lat.J, (size_t)lat.S * lat.D * lat.N, cudaMemcpyDeviceToDevice, lat.stream);
+}
+
+cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in) {
+  return cudaMemcpyAsync(lat.J, dev_in, (size_t)lat.S * lat.D * lat.N, cudaMemcpyDeviceToDevice, lat.stream);
+}
+
+}  // namespace ianus

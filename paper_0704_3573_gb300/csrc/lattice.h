@@ -1,0 +1,110 @@
+// lattice.h -- host-side definition of a lattice object and the kernel
+// launchers each translation unit provides.  Internal to libianus.so.
+#pragma once
+#include <cstddef>
+#include <algorithm>
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ianus.h"
+#include "common.cuh"
+
+namespace ianus {
+
+constexpr int kMaxClasses = 8;   // u = 0..2D (7 in 3D), padded
+constexpr int kPlanes = 33;      // 32 threshold bit-planes + the "always" mask
+constexpr int kAccStride = 8;    // int64 accumulators per (sample, slot)
+constexpr uint64_t kTwo32 = 1ull << 32;
+
+struct Lattice {
+  ianus_config cfg;
+  int model, D, L, S, R, K, slots, layout;
+  int G;        // 64-sample groups (BITS64)
+  int Q4;       // 4-sample quads (U8X4)
+  uint32_t N;
+  Geom geom;
+  cudaStream_t stream;
+  bool owns_buffer;
+  uint8_t* base;
+  size_t bytes;
+
+  // device arrays (carved from base)
+  void* spins;          // I8: int8 [slots][S][N]; BITS64: u64 [G][slots][N]; U8X4: u32 [slots][Q4][N]
+  void* J;              // I8: int8 [S][D][N];     BITS64: u64 [G][D][N];     U8X4: u32 [Q4][D][N]
+  uint64_t* thr;        // Ising: u64 [K][kMaxClasses] threshold per class u
+  uint64_t* tp;         // BITS64: u64 [G][slots][kMaxClasses][kPlanes]
+  uint4* ptab;          // Potts: uint4 [K][65536]
+  uint64_t* pttab;      // PT: u64 [K-1][pt_len], T_PT(|d| = 4m) at m-1
+  int8_t* pt_sign;      // PT: sign of beta[k] - beta[k+1], [K-1]
+  int32_t* slot_at;     // [S][R][K]
+  int32_t* temp_of;     // [S][R][K]
+  uint64_t* accepted;   // [S][R][K-1]
+  int64_t* acc;         // [S][slots][kAccStride] measurement accumulators
+  int64_t* out_E;       // [S][K][R]
+  int64_t* out_M;       // [S][K][R][mq]
+  int64_t* out_Q;       // [S][K]
+  uint64_t* ser_sweep;  // [cap]
+  int64_t* ser_E;       // [cap][S*K*R]
+  int64_t* ser_M;       // [cap][S*K*R*mq]
+  int64_t* ser_Q;       // [cap][S*K]
+  uint32_t* err;        // device error word
+
+  int mq;               // magnetisation entries per configuration (1 Ising, 4 Potts)
+  uint32_t cap;         // series capacity
+  uint64_t ser_count;   // rows recorded so far (ring position = ser_count % cap)
+  uint64_t ser_first;   // first row still readable
+  uint32_t pt_len;      // entries per PT pair table (<= pt_cap)
+  uint32_t pt_cap;      // allocated entries per pair
+  uint64_t sweeps;      // absolute sweep counter
+  uint64_t steps;       // PT swap steps done
+  PhiloxKeys keys;
+  std::vector<double> beta;  // last beta array (tables are valid for it)
+  int algo;                  // last algo; -1 = none
+  bool tables_ok;
+  bool pt_tables_ok;
+  int sticky;                // sticky error status (ESTATE after a failure)
+  int variant;               // kernel variant knob (tuner), 0 = default
+};
+
+// ---- host table builders (tables.cpp) ----
+size_t table_ising(int dim, int algo, double beta, uint64_t* out, size_t n);
+size_t table_potts(double beta, uint64_t* out, size_t n);
+size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
+// Threshold per class u = 0..2D for the unified rule "flip iff (r < T) != inv":
+// Metropolis: u < D -> T_M(4D - 4u), u >= D -> 2^32 (always); inv = 0.
+// Heat bath: T_H(2D - 2u), inv = 1 (keep iff r < T).
+void class_thresholds(int dim, int algo, double beta, uint64_t* thr /*[kMaxClasses]*/);
+
+// ---- launchers; each returns cudaGetLastError() of its launches ----
+// I8 (k_plain.cu)
+cudaError_t launch_init_i8(Lattice& lat, int ferro);
+cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv);
+cudaError_t launch_measure_i8(Lattice& lat, int want_q);
+cudaError_t launch_get_spins_i8(Lattice& lat, int8_t* dev_out);       // [S][slots][N]
+cudaError_t launch_set_spins_i8(Lattice& lat, const int8_t* dev_in);
+cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out);   // [S][D][N]
+cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in);
+// BITS64 (k_msc.cu)
+cudaError_t launch_init_bits(Lattice& lat, int ferro);
+cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
+cudaError_t launch_measure_bits(Lattice& lat, int want_q);
+cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
+cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_spins_bits(Lattice& lat, const int8_t* dev_in);
+cudaError_t launch_get_couplings_bits(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_couplings_bits(Lattice& lat, const int8_t* dev_in);
+// U8X4 Potts (k_potts.cu)
+cudaError_t launch_init_potts(Lattice& lat, int ferro);
+cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t);
+cudaError_t launch_measure_potts(Lattice& lat, int want_q);
+cudaError_t launch_get_spins_potts(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_spins_potts(Lattice& lat, const int8_t* dev_in);
+cudaError_t launch_get_couplings_potts(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_couplings_potts(Lattice& lat, const int8_t* dev_in);
+// shared (k_pt.cu)
+cudaError_t launch_finalize(Lattice& lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q);
+cudaError_t launch_pt_swap(Lattice& lat);
+
+}  // namespace ianus

@@ -1,0 +1,85 @@
+// tables.cpp -- host construction of the integer acceptance tables: the
+// look-up table the update cell indexes with its local energy (Sec. 3.2),
+// compared against a 32-bit random number (Sec. 3.3).  Probabilities are
+// those of Sec. 2.2: Metropolis exp(-beta dE), heat bath Eq. (4), evaluated
+// in IEEE double precision exactly as stated in include/ianus.h and stored
+// as floor(2^32 p) in [0, 2^32].
+#include <cmath>
+#include <cstdint>
+
+#include "lattice.h"
+
+namespace ianus {
+
+static uint64_t to_threshold(double p) { return (uint64_t)std::floor(std::ldexp(p, 32)); }
+
+size_t table_ising(int dim, int algo, double beta, uint64_t* out, size_t n) {
+  if ((dim != 2 && dim != 3) || !out || !(beta >= 0.0) || !std::isfinite(beta)) return 0;
+  if (algo == IANUS_METROPOLIS) {
+    if (n < (size_t)dim) return 0;
+    for (int j = 0; j < dim; ++j) out[j] = to_threshold(std::exp(-beta * (double)(4 * (j + 1))));
+    return (size_t)dim;
+  }
+  if (algo == IANUS_HEATBATH) {
+    if (n < (size_t)(2 * dim + 1)) return 0;
+    for (int j = 0; j <= 2 * dim; ++j) {
+      const int x = -2 * dim + 2 * j;
+      out[j] = to_threshold(1.0 / (1.0 + std::exp(-2.0 * beta * (double)x)));
+    }
+    return (size_t)(2 * dim + 1);
+  }
+  return 0;
+}
+
+void class_thresholds(int dim, int algo, double beta, uint64_t* thr) {
+  for (int u = 0; u < kMaxClasses; ++u) thr[u] = 0;
+  if (algo == IANUS_METROPOLIS) {
+    for (int u = 0; u <= 2 * dim; ++u) {
+      const int dE = 4 * dim - 4 * u;
+      thr[u] = dE <= 0 ? kTwo32 : to_threshold(std::exp(-beta * (double)dE));
+    }
+  } else {
+    for (int u = 0; u <= 2 * dim; ++u) {
+      const int x = 2 * dim - 2 * u;
+      thr[u] = to_threshold(1.0 / (1.0 + std::exp(-2.0 * beta * (double)x)));
+    }
+  }
+}
+
+size_t table_potts(double beta, uint64_t* out, size_t n) {
+  const size_t need = 3u * 13u * 13u * 13u * 13u;
+  if (!out || n < need || !(beta >= 0.0) || !std::isfinite(beta)) return 0;
+  size_t idx = 0;
+  for (int n0 = -6; n0 <= 6; ++n0)
+    for (int n1 = -6; n1 <= 6; ++n1)
+      for (int n2 = -6; n2 <= 6; ++n2)
+        for (int n3 = -6; n3 <= 6; ++n3) {
+          const double w0 = std::exp(beta * (double)n0), w1 = std::exp(beta * (double)n1);
+          const double w2 = std::exp(beta * (double)n2), w3 = std::exp(beta * (double)n3);
+          const double S0 = w0, S1 = S0 + w1, S2 = S1 + w2, Z = S2 + w3;
+          out[idx++] = to_threshold(S0 / Z);
+          out[idx++] = to_threshold(S1 / Z);
+          out[idx++] = to_threshold(S2 / Z);
+        }
+  return need;
+}
+
+size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n) {
+  if (!out || !std::isfinite(beta_k) || !std::isfinite(beta_k1)) return 0;
+  double db = beta_k - beta_k1;
+  if (db < 0) db = -db;
+  for (size_t m = 1; m <= n; ++m) out[m - 1] = to_threshold(std::exp(-db * (double)(4 * m)));
+  return n;
+}
+
+}  // namespace ianus
+
+extern "C" {
+size_t ianus_table_ising(int32_t dim, int32_t algo, double beta, uint64_t* out, size_t n) {
+  return ianus::table_ising(dim, algo, beta, out, n);
+}
+size_t ianus_table_potts(double beta, uint64_t* out, size_t n) { return ianus::table_potts(beta, out, n); }
+size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n) {
+  return ianus::table_pt(beta_k, beta_k1, out, n);
+}
+}

@@ -1,0 +1,276 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Everything is integer work, so the bar is bit-exact: couplings, initial
+states, spins after every sweep, integer energies, magnetisations, overlaps,
+PT permutations and acceptance counts.  Sizes span several thread blocks and
+ragged tails (odd sample counts crossing the 64-lane and 4-lane packing,
+L = 2 where forward and backward neighbours coincide).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import HEATBATH, METROPOLIS, MODEL_ISING, MODEL_POTTS, Oracle
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x0704357300000000
+
+
+def _pair(ianus, model="ea", dim=3, L=4, S=1, R=1, K=1, seed=SEED, layout="auto", ferro=False, ids=None):
+    lat = ianus.Lattice(model=model, dim=dim, L=L, n_samples=S, n_replicas=R, n_temps=K, seed=seed,
+                        layout=layout, ferro=ferro, series_capacity=4096)
+    ids = list(range(S)) if ids is None else ids
+    orc = Oracle(model=MODEL_ISING if model == "ea" else MODEL_POTTS, dim=dim, L=L, sample_ids=ids,
+                 n_replicas=R, n_temps=K, seed=seed, ferro=ferro)
+    return lat, orc, ids
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+@pytest.mark.parametrize("dim,L,S,R", [(3, 2, 1, 1), (3, 4, 70, 2), (2, 6, 3, 2), (3, 8, 130, 1), (2, 2, 65, 2)])
+def test_init_matches_oracle(ianus, layout, dim, L, S, R):
+    lat, orc, _ = _pair(ianus, dim=dim, L=L, S=S, R=R, layout=layout)
+    assert np.array_equal(lat.couplings(), orc.couplings())
+    assert np.array_equal(lat.spins(), orc.spins())
+
+
+@pytest.mark.parametrize("dim,L,S,R", [(3, 2, 1, 2), (3, 4, 9, 2), (2, 6, 5, 2), (3, 6, 3, 1)])
+def test_potts_init_matches_oracle(ianus, dim, L, S, R):
+    lat, orc, _ = _pair(ianus, model="potts", dim=dim, L=L, S=S, R=R)
+    assert np.array_equal(lat.couplings(), orc.couplings())
+    assert np.array_equal(lat.spins(), orc.spins())
+
+
+CASES = [(3, 2, 1, 1), (3, 4, 3, 2), (2, 4, 65, 1), (3, 6, 70, 2), (2, 8, 2, 2), (3, 8, 1, 1), (2, 2, 5, 2)]
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+@pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
+@pytest.mark.parametrize("dim,L,S,R", CASES)
+def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
+    lat, orc, _ = _pair(ianus, dim=dim, L=L, S=S, R=R, layout=layout, seed=SEED + 17 * L + S)
+    beta = 0.85
+    for _ in range(6):
+        lat.sweep(algo, beta, 1)
+        orc.sweep(algo, beta, 1)
+        assert np.array_equal(lat.spins(), orc.spins())
+    E, M, Q = lat.measure()
+    Eo, Mo, Qo = orc.measure()
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo)
+    if R >= 2:
+        assert np.array_equal(Q, Qo)
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+def test_series_matches_oracle(ianus, layout):
+    lat, orc, _ = _pair(ianus, dim=3, L=6, S=67, R=2, layout=layout)
+    lat.sweep(HEATBATH, 1.0, 23, measure_every=5)
+    orc.sweep(HEATBATH, 1.0, 23, measure_every=5)
+    sw, E, M, Q = lat.series()
+    swo, Eo, Mo, Qo = orc.series()
+    assert list(sw) == list(swo) == [5, 10, 15, 20]
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo) and np.array_equal(Q, Qo)
+
+
+@pytest.mark.parametrize("beta", [0.0, 40.0])
+def test_extreme_temperatures(ianus, beta):
+    """beta = 0 (T_H = 2^31 everywhere, Metropolis always flips) and a
+    beta so large that T_M = 0 and T_H reaches 2^32."""
+    for layout in ("i8", "bits64"):
+        for algo in (METROPOLIS, HEATBATH):
+            lat, orc, _ = _pair(ianus, dim=3, L=4, S=66, R=1, layout=layout)
+            lat.sweep(algo, beta, 3)
+            orc.sweep(algo, beta, 3)
+            assert np.array_equal(lat.spins(), orc.spins()), (layout, algo)
+
+
+def test_plain_and_bitsliced_agree(ianus):
+    """The stream is defined per (sample, slot, site, sweep), not per layout."""
+    a = ianus.Lattice(dim=3, L=8, n_samples=40, n_replicas=2, seed=5, layout="i8")
+    b = ianus.Lattice(dim=3, L=8, n_samples=40, n_replicas=2, seed=5, layout="bits64")
+    for algo in (METROPOLIS, HEATBATH):
+        a.sweep(algo, 0.7, 5)
+        b.sweep(algo, 0.7, 5)
+        assert np.array_equal(a.spins(), b.spins())
+        for x, y in zip(a.measure(), b.measure()):
+            assert np.array_equal(x, y)
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+def test_split_sweeps_and_checkpoint(ianus, layout):
+    a = ianus.Lattice(dim=3, L=6, n_samples=5, n_replicas=2, seed=9, layout=layout)
+    a.sweep(HEATBATH, 0.9, 7)
+    blob = a.get_state()
+    a.sweep(HEATBATH, 0.9, 5)
+    b = ianus.Lattice(dim=3, L=6, n_samples=5, n_replicas=2, seed=9, layout=layout)
+    b.set_state(blob)
+    assert b.sweeps == 7
+    b.sweep(HEATBATH, 0.9, 2)
+    b.sweep(HEATBATH, 0.9, 3)
+    assert np.array_equal(a.spins(), b.spins())
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+def test_gauge_invariance_on_gpu(ianus, layout):
+    L, dim, S = 6, 3, 3
+    N = L ** dim
+    a = ianus.Lattice(dim=dim, L=L, n_samples=S, n_replicas=2, seed=21, layout=layout)
+    b = ianus.Lattice(dim=dim, L=L, n_samples=S, n_replicas=2, seed=21, layout=layout)
+    rng = np.random.default_rng(4)
+    eps = rng.choice([-1, 1], size=(S, N)).astype(np.int8)
+    J = a.couplings()
+    x = np.arange(N) % L
+    y = (np.arange(N) // L) % L
+    z = np.arange(N) // (L * L)
+    fwd = [((x + 1) % L) + L * (y + L * z), x + L * (((y + 1) % L) + L * z), x + L * (y + L * ((z + 1) % L))]
+    Jg = J.copy()
+    for d in range(dim):
+        Jg[:, d, :] = eps * J[:, d, :] * eps[:, fwd[d]]
+    b.set_couplings(Jg)
+    b.set_spins(a.spins() * eps[:, None, :])
+    for algo in (METROPOLIS, HEATBATH):
+        a.sweep(algo, 0.8, 4)
+        b.sweep(algo, 0.8, 4)
+        assert np.array_equal(b.spins(), a.spins() * eps[:, None, :])
+        Ea, _, Qa = a.measure()
+        Eb, _, Qb = b.measure()
+        assert np.array_equal(Ea, Eb) and np.array_equal(Qa, Qb)
+
+
+@pytest.mark.parametrize("dim,L,S,R", [(3, 2, 1, 2), (3, 4, 9, 2), (2, 6, 6, 2), (3, 8, 5, 1)])
+def test_potts_sweep_bit_exact(ianus, dim, L, S, R):
+    lat, orc, _ = _pair(ianus, model="potts", dim=dim, L=L, S=S, R=R, seed=SEED + 3)
+    for beta in (0.5, 1.25):
+        for _ in range(4):
+            lat.sweep(HEATBATH, beta, 1)
+            orc.sweep(HEATBATH, beta, 1)
+            assert np.array_equal(lat.spins(), orc.spins())
+    E, M, Q = lat.measure()
+    Eo, Mo, Qo = orc.measure()
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo)
+    if R >= 2:
+        assert np.array_equal(Q, Qo)
+
+
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+@pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
+def test_parallel_tempering_matches_oracle(ianus, layout, algo):
+    K = 5
+    beta = [1.0 / (0.7 + 0.9 * k / (K - 1)) for k in range(K)]
+    lat, orc, _ = _pair(ianus, dim=3, L=4, S=67, R=2, K=K, layout=layout, seed=SEED + 40)
+    for _ in range(6):
+        lat.sweep(algo, beta, 3)
+        orc.sweep(algo, beta, 3)
+        lat.pt_swap()
+        orc.pt_swap(beta)
+        sa, acc, steps = lat.pt_state()
+        sao, acco, stepso = orc.pt_state()
+        assert np.array_equal(sa, sao) and np.array_equal(acc, acco) and steps == stepso
+        assert np.array_equal(lat.spins(), orc.spins())
+    assert acc.sum() > 0
+    E, M, Q = lat.measure()
+    Eo, Mo, Qo = orc.measure()
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo) and np.array_equal(Q, Qo)
+
+
+def test_sweep_pt_fused_equals_separate(ianus):
+    K = 4
+    beta = [1.2, 1.0, 0.8, 0.6]
+    a = ianus.Lattice(dim=3, L=4, n_samples=10, n_replicas=2, n_temps=K, seed=3)
+    b = ianus.Lattice(dim=3, L=4, n_samples=10, n_replicas=2, n_temps=K, seed=3)
+    a.sweep_pt(METROPOLIS, beta, 20, swap_every=5)
+    for _ in range(4):
+        b.sweep(METROPOLIS, beta, 5)
+        b.pt_swap()
+    assert np.array_equal(a.spins(), b.spins())
+    assert np.array_equal(a.pt_state()[0], b.pt_state()[0])
+
+
+def test_errors_are_reported_not_raised_in_kernels(ianus):
+    lat = ianus.Lattice(dim=3, L=4, n_samples=2)
+    with pytest.raises(ianus.IanusError) as e:
+        lat.sweep(METROPOLIS, -1.0, 1)
+    assert e.value.status == ianus.EINVAL
+    with pytest.raises(ianus.IanusError):
+        lat.pt_swap()  # one temperature
+    p = ianus.Lattice(model="potts", dim=3, L=4, n_samples=2)
+    with pytest.raises(ianus.IanusError) as e:
+        p.sweep(METROPOLIS, 1.0, 1)
+    assert e.value.status == ianus.EUNSUPPORTED
+    lat.synchronize()
+
+
+# ---------------- BASELINE-sized workloads ----------------
+
+def test_cfg0_full_run(ianus):
+    """3D EA L=16, one sample, Metropolis T=1.1, 1000 sweeps, E and M after
+    every sweep: the whole series bit-exact against the oracle."""
+    seed = SEED + 0
+    beta = 1.0 / 1.1
+    for layout in ("i8", "bits64"):
+        lat = ianus.Lattice(dim=3, L=16, n_samples=1, seed=seed, layout=layout, series_capacity=1000)
+        lat.sweep(METROPOLIS, beta, 1000, measure_every=1)
+        orc = Oracle(dim=3, L=16, sample_ids=[0], seed=seed)
+        orc.sweep(METROPOLIS, beta, 1000, measure_every=1)
+        sw, E, M, _ = lat.series()
+        swo, Eo, Mo, _ = orc.series()
+        assert len(sw) == 1000
+        assert np.array_equal(sw, swo) and np.array_equal(E, Eo) and np.array_equal(M, Mo)
+        assert np.array_equal(lat.spins(), orc.spins())
+
+
+def test_cfg1_full_size_sampled(ianus):
+    """L=64, 256 samples x 2 replicas, heat bath T=1.0 on the GPU in the bench
+    launch configuration; samples 0, 63, 64, 255 checked against the oracle."""
+    seed = SEED + 1
+    lat = ianus.Lattice(dim=3, L=64, n_samples=256, n_replicas=2, seed=seed, layout="bits64")
+    lat.sweep(HEATBATH, 1.0, 10, measure_every=5)
+    ids = [0, 63, 64, 255]
+    orc = Oracle(dim=3, L=64, sample_ids=ids, n_replicas=2, seed=seed)
+    orc.sweep(HEATBATH, 1.0, 10, measure_every=5, nthreads=8)
+    sp = lat.spins()
+    assert np.array_equal(sp[ids], orc.spins())
+    sw, E, M, Q = lat.series()
+    swo, Eo, Mo, Qo = orc.series()
+    assert np.array_equal(E[:, ids], Eo) and np.array_equal(Q[:, ids], Qo) and np.array_equal(M[:, ids], Mo)
+    # every sample: energy from the series equals the energy of the read-back state
+    E_now, _, _ = lat.measure()
+    assert np.array_equal(E_now, E[-1])
+
+
+def test_cfg2_full_size_sampled(ianus):
+    """L=32, 32 temperatures in [0.7, 1.6], 64 samples x 2 replicas,
+    Metropolis with a device PT swap every 10 sweeps; samples 0 and 37."""
+    seed = SEED + 2
+    K = 32
+    beta = [1.0 / (0.7 + 0.9 * k / 31) for k in range(K)]
+    lat = ianus.Lattice(dim=3, L=32, n_samples=64, n_replicas=2, n_temps=K, seed=seed, layout="bits64")
+    ids = [0, 37]
+    orc = Oracle(dim=3, L=32, sample_ids=ids, n_replicas=2, n_temps=K, seed=seed)
+    for _ in range(2):
+        lat.sweep(METROPOLIS, beta, 10)
+        lat.pt_swap()
+        orc.sweep(METROPOLIS, beta, 10, nthreads=2)
+        orc.pt_swap(beta)
+    sa, acc, _ = lat.pt_state()
+    sao, acco, _ = orc.pt_state()
+    assert np.array_equal(sa[ids], sao) and np.array_equal(acc[ids], acco)
+    assert np.array_equal(lat.spins()[ids], orc.spins())
+    E, _, _ = lat.measure()
+    Eo, _, _ = orc.measure()
+    assert np.array_equal(E[ids], Eo)
+
+
+def test_cfg3_full_size_sampled(ianus):
+    """Potts q=4, L=32, 128 samples x 2 replicas, heat bath T=0.8."""
+    seed = SEED + 3
+    lat = ianus.Lattice(model="potts", dim=3, L=32, n_samples=128, n_replicas=2, seed=seed)
+    lat.sweep(HEATBATH, 1.0 / 0.8, 10, measure_every=10)
+    ids = [0, 127]
+    orc = Oracle(model=MODEL_POTTS, dim=3, L=32, sample_ids=ids, n_replicas=2, seed=seed)
+    orc.sweep(HEATBATH, 1.0 / 0.8, 10, measure_every=10, nthreads=2)
+    assert np.array_equal(lat.spins()[ids], orc.spins())
+    _, E, M, Q = lat.series()
+    _, Eo, Mo, Qo = orc.series()
+    assert np.array_equal(E[:, ids], Eo) and np.array_equal(M[:, ids], Mo) and np.array_equal(Q[:, ids], Qo)
