@@ -1,0 +1,411 @@
+#!/usr/bin/env python3
+"""Benchmark: spin updates/ns of the batched bit-sliced checkerboard sweep.
+
+Workload (one GPU): 3D Edwards-Anderson +-J glass, L = 64 periodic, 256
+disorder samples x 2 real replicas packed 64 samples per uint64 word, heat
+bath at T = 1.0, energy and replica overlap measured every 10 sweeps.  One
+step is a block of 100 sweeps with its 10 measurements; the default 100
+steps are the workload's full 10^4 sweeps.  Inputs are synthetic and seeded
+(couplings and initial spins drawn on the device from the counter-based
+stream).
+
+Printed JSON line (rank 0): value = spin updates/ns of the device-resident
+run; e2e = the same through the C ABI with the state uploaded from pinned
+host memory and the measurement series read back every step; plain = the
+one-byte-per-spin kernel on the same workload; roofline = the dominant
+sweep kernel against the integer-issue peak; cpu_baseline = the CPU oracle on
+a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle instead (the only reference this
+method has: the paper ships no code).
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes as C
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "spin updates/ns (3D EA ±J, batched vs plain, bit-exact); p50/p99 job latency"
+UNIT = "spin updates/ns"
+L, S, R = 64, 256, 2
+T = 1.0
+SWEEPS_PER_STEP = 100
+MEASURE_EVERY = 10
+SEED = 0x0704357300000001
+WORKLOAD = ("3D EA +-J, L=64 periodic, 256 samples x 2 replicas (64 samples per uint64), heat bath T=1.0, "
+            "E and Q every 10 sweeps; step = 100 sweeps")
+SM_COUNT = 152
+SM_MAX_MHZ = 2070.0
+
+
+def config_dict(ws: int) -> dict:
+    return {"workload": WORKLOAD, "L": L, "samples_per_gpu": S, "replicas": R, "T": T,
+            "sweeps_per_step": SWEEPS_PER_STEP, "measure_every": MEASURE_EVERY,
+            "l2": "flushed between timed steps (256 MiB write)",
+            "parallelism": f"dp{ws}: independent sample batches per GPU, no collective"}
+
+
+def expected_plane_pairs(lanes: int = 64) -> float:
+    """E[plane pairs a 64-lane word needs]: a lane is undecided after k planes
+    with probability 2^-k exactly (uniform r), the word while any lane is."""
+    return sum(1.0 - (1.0 - 4.0 ** (-m)) ** lanes for m in range(16))
+
+
+def algorithmic_ops_per_word_hb3d(R_: int = 2) -> float:
+    """32-bit integer operations one heat-bath update of a 64-lane site word
+    needs in 3D (loads, 6 unsatisfied bits, adder tree, 7 class masks, per
+    plane: threshold bits and compare, per plane pair: one Philox4x32-10
+    block, write-back).  64-bit logic counts as two 32-bit operations."""
+    fixed = (7 + 6.0 / R_) + 12 + 16 + 14 + 3
+    per_plane = 14 + 4
+    per_pair = 10 * 4 + 1
+    return fixed + expected_plane_pairs() * (2 * per_plane + per_pair)
+
+
+# ---------------- distributed helpers ----------------
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------- clocks ----------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------- CPU oracle ----------------
+
+def oracle_rate(nthreads: int, sweeps: int, seed: int = SEED):
+    """The oracle as it stands on nthreads samples (2 replicas each) of the
+    workload; returns (updates/ns, wall seconds, updates)."""
+    import oracle
+
+    ids = list(range(nthreads))
+    o = oracle.Oracle(dim=3, L=L, sample_ids=ids, n_replicas=R, seed=seed)
+    t0 = time.perf_counter()
+    o.sweep(oracle.HEATBATH, 1.0 / T, sweeps, measure_every=MEASURE_EVERY, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    upd = nthreads * R * L ** 3 * sweeps
+    return upd / (dt * 1e9), dt, upd
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+
+    oracle.build()
+    cores = os.cpu_count() or 1
+    nthr = max(1, min(cores, 16))
+    ids = list(range(nthr))
+    o = oracle.Oracle(dim=3, L=L, sample_ids=ids, n_replicas=R, seed=SEED)
+    for _ in range(args.warmup):
+        o.sweep(oracle.HEATBATH, 1.0 / T, 1, nthreads=nthr)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.sweep(oracle.HEATBATH, 1.0 / T, 1, measure_every=1, nthreads=nthr)
+        times.append(time.perf_counter() - t0)
+    upd_step = nthr * R * L ** 3
+    total = sum(times)
+    value = upd_step * args.steps / (total * 1e9)
+    sample = f"{nthr} samples x {R} replicas of the L=64 workload, 1 sweep + E/Q per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
+        "config": config_dict(ws),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------- GPU arm ----------------
+
+def run_gpu(args, ws, rank, local):
+    import torch
+
+    import paper_0704_3573_gb300 as ianus
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream(dev)
+    seed = SEED + 0x100000 * rank  # each rank: its own independent batch of samples
+    beta = 1.0 / T
+    upd_step = S * R * L ** 3 * SWEEPS_PER_STEP
+    flush = torch.empty(256 * 2 ** 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=seed, layout="bits64",
+                        series_capacity=4096, stream=stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            lat.sweep(ianus.HEATBATH, beta, SWEEPS_PER_STEP, MEASURE_EVERY)
+    torch.cuda.synchronize()
+    lat.series(clear=True)
+
+    # ---- device-resident timed region ----
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier(ws)
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(k & 0xFF)  # evict the 40 MiB working set from L2
+            ev[k][0].record(stream)
+            lat.sweep(ianus.HEATBATH, beta, SWEEPS_PER_STEP, MEASURE_EVERY)
+            ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    dev_s = max_over_ranks(dev_s, ws)
+    value = ws * upd_step * args.steps / (dev_s * 1e9)
+    lat.synchronize()
+    n_rows = len(lat.series()[0])
+
+    # ---- dominant kernel: colour half-sweeps alone, timed on the same stream ----
+    nsw = 200
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        flush.fill_(1)
+        a0.record(stream)
+        lat.sweep(ianus.HEATBATH, beta, nsw, 0)
+        a1.record(stream)
+    torch.cuda.synchronize()
+    kern_s = a0.elapsed_time(a1) / 1e3 / (2 * nsw)
+    words_per_launch = (S // 64) * R * L ** 3 // 2
+    ops_word = algorithmic_ops_per_word_hb3d(R)
+    achieved = ops_word * words_per_launch / kern_s / 1e12  # Tops/s
+    probe = probe_peak()
+    peak = probe["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if probe else None
+    roofline = {
+        "bound": "alu", "kernel": "k_sweep_bits<3,HB,R=2>", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+        "frac": (achieved / peak) if peak else None, "traffic": None,
+        "ops_per_word": ops_word, "words_per_launch": words_per_launch, "launch_us": kern_s * 1e6,
+        "peak_source": "probe lop3.b32 ops/clk/SM x 152 SMs x 2070 MHz" if probe else None,
+        "probe": probe,
+    }
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = run_e2e(ianus, lat, stream, args, ws)
+
+    # ---- plain one-byte-per-spin kernel on the same workload ----
+    plain = None
+    if args.plain_steps > 0:
+        del lat
+        torch.cuda.empty_cache()
+        pl = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=seed, layout="i8", stream=stream)
+        with torch.cuda.stream(stream):
+            pl.sweep(ianus.HEATBATH, beta, 2, 0)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nps = args.plain_steps * MEASURE_EVERY
+        with torch.cuda.stream(stream):
+            flush.fill_(2)
+            p0.record(stream)
+            pl.sweep(ianus.HEATBATH, beta, nps, MEASURE_EVERY)
+            p1.record(stream)
+        torch.cuda.synchronize()
+        ps = p0.elapsed_time(p1) / 1e3
+        pv = S * R * L ** 3 * nps / (ps * 1e9)
+        plain = {"value": pv, "unit": UNIT, "layout": "i8 (one byte per spin)", "sweeps": nps,
+                 "speedup_bitsliced_over_plain": value / ws / pv}
+        del pl
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        oracle.build()
+        nthr = max(1, min(os.cpu_count() or 1, 16))
+        rate, dt, upd = oracle_rate(nthr, args.cpu_sweeps)
+        cpu = {"value": rate, "unit": UNIT, "cores": nthr, "kind": "oracle",
+               "sample": f"samples 0..{nthr - 1} x {R} replicas, {args.cpu_sweeps} sweeps of the L=64 workload "
+                         f"({upd} updates, {dt:.1f} s wall)"}
+
+    launches = args.steps * (2 * SWEEPS_PER_STEP + 3 * (SWEEPS_PER_STEP // MEASURE_EVERY))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": config_dict(ws),
+        "wall_s": wall, "series_rows": n_rows, "gpu_launches": launches, "clocks": clk, "roofline": roofline,
+        "e2e": e2e, "plain": plain, "cpu_baseline": cpu,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def probe_peak():
+    import paper_0704_3573_gb300.build as b
+
+    try:
+        P = C.CDLL(b.PROBE_LIB)
+        P.ianus_probe_int.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
+        out = {}
+        for kind, name in ((0, "lop3_per_clk_sm"), (1, "imad_wide_per_clk_sm"), (2, "philox_mix_per_clk_sm"),
+                           (3, "philox_blocks_per_clk_sm")):
+            v = C.c_double()
+            if P.ianus_probe_int(kind, 4, C.byref(v)) != 0:
+                return None
+            out[name] = v.value
+        return out
+    except OSError:
+        return None
+
+
+def run_e2e(ianus, lat, stream, args, ws):
+    """Per step: upload the state blob from pinned host memory (set_state),
+    run the 100-sweep block, read the measurement series into pinned host
+    arrays.  All through the C ABI."""
+    import torch
+
+    L_ = lat._lib
+    n = C.c_size_t()
+    L_.ianus_get_state(lat._h, None, 0, C.byref(n))
+    blob = torch.empty(n.value, dtype=torch.uint8, pin_memory=True)
+    assert L_.ianus_get_state(lat._h, C.c_void_p(blob.data_ptr()), n.value, C.byref(n)) == 0
+    rows = SWEEPS_PER_STEP // MEASURE_EVERY
+    SK, SKR = S, S * R
+    sw = torch.empty(rows, dtype=torch.int64, pin_memory=True)
+    E = torch.empty(rows * SKR, dtype=torch.int64, pin_memory=True)
+    M = torch.empty(rows * SKR, dtype=torch.int64, pin_memory=True)
+    Q = torch.empty(rows * SK, dtype=torch.int64, pin_memory=True)
+    beta = (C.c_double * 1)(1.0 / T)
+    nrow = C.c_size_t()
+    steps = max(3, min(args.steps, args.e2e_steps))
+    times = []
+    for k in range(steps + 1):
+        t0 = time.perf_counter()
+        st = L_.ianus_set_state(lat._h, C.c_void_p(blob.data_ptr()), n.value)
+        st |= L_.ianus_sweep(lat._h, ianus.HEATBATH, beta, SWEEPS_PER_STEP, MEASURE_EVERY)
+        st |= L_.ianus_read_series(lat._h, C.c_void_p(sw.data_ptr()), C.c_void_p(E.data_ptr()),
+                                   C.c_void_p(M.data_ptr()), C.c_void_p(Q.data_ptr()), rows, C.byref(nrow), 1)
+        dt = time.perf_counter() - t0
+        assert st == 0 and nrow.value == rows
+        if k > 0:  # first iteration re-uploads tables after set_state
+            times.append(dt)
+    t = max_over_ranks(sum(times), ws)
+    return {"value": ws * S * R * L ** 3 * SWEEPS_PER_STEP * len(times) / (t * 1e9), "unit": UNIT,
+            "h2d_bytes_per_step": int(n.value), "d2h_bytes_per_step": int(rows * (8 + 8 * (2 * SKR + SK))),
+            "steps": len(times), "what": "set_state (pinned H2D) + 100 sweeps + read_series (pinned D2H)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ianus", choices=["ianus", "reference"])
+    ap.add_argument("--plain-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        import __graft_entry__
+
+        __graft_entry__.build()
+        run_gpu(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -19,6 +19,8 @@ LIB = os.path.join(HERE, "libianus.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
 SOURCES = ["api.cu", "k_plain.cu", "k_msc.cu", "k_potts.cu", "k_pt.cu", "tables.cpp"]
+PROBE_SOURCES = ["probe.cu"]
+PROBE_LIB = os.path.join(HERE, "libianus_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2", "--expt-relaxed-constexpr"]
 
@@ -33,15 +35,19 @@ def nvcc() -> str:
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
     files.append(os.path.join(INCLUDE, "ianus.h"))
+    files.append(os.path.join(INCLUDE, "ianus_probe.h"))
     files.append(os.path.abspath(__file__))
     return files
 
 
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(f) <= t for f in _deps())
+    for lib in (LIB, PROBE_LIB):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not all(os.path.getmtime(f) <= t for f in _deps()):
+            return False
+    return True
 
 
 def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = False) -> str:
@@ -61,20 +67,22 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
         return obj, r.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(SOURCES) + len(PROBE_SOURCES)) as ex:
+        results = list(ex.map(compile_one, SOURCES + PROBE_SOURCES))
     if verbose or ptxas_verbose:
         for (obj, err) in results:
             if err.strip():
                 print(f"== {os.path.basename(obj)}\n{err}")
-    tmp = LIB + f".tmp{os.getpid()}"
     cuda_lib = os.path.join(os.path.dirname(os.path.dirname(cc)), "lib64")
-    cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *[o for o, _ in results],
-           "-Xlinker", f"-rpath={cuda_lib}"]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    objs = [o for o, _ in results]
+    for lib, n in ((LIB, len(SOURCES)), (PROBE_LIB, None)):
+        part = objs[:n] if n is not None else objs[len(SOURCES):]
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [cc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *part, "-Xlinker", f"-rpath={cuda_lib}"]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 
