@@ -276,6 +276,42 @@ ianus_status ianus_destroy(ianus_lattice* lat);
 /* Static, NUL-terminated description of a status code. */
 const char* ianus_status_string(int32_t status);
 
+/* ---- Measurement for callers that cannot allocate device memory ----
+ *
+ * The paper has no counterpart to this entry point.  It serves callers that
+ * must not call cudaMalloc: code embedded in a framework that owns all device
+ * memory through its own pool (a direct allocation bypasses the pool and can
+ * fail when the pool has reserved the device), and serving loops where
+ * cudaMalloc / cudaFree would synchronise the device and stall other streams.
+ * It allocates nothing: it calls no cudaMalloc, cudaFree or allocating
+ * library routine.
+ *
+ * It computes, for bit-sliced configurations in the BITS64 layout, the energy
+ * E = -sum_bonds J s s and the magnetisation M = sum_i s_i of every (sample,
+ * slot), the same values ianus_measure reports for a BITS64 lattice.
+ *   spins          device uint64 [ceil(n_samples/64)][n_slots][L^dim], lane
+ *                  l of a word = sample 64 g + l, bit 1 = spin -1, sites in
+ *                  checkerboard-split order (2 (y + L z) + colour) L/2 + x/2
+ *   couplings      device uint64 [ceil(n_samples/64)][dim][L^dim], same
+ *                  order, bit 1 = coupling -1, J_d(i) joins i and i + e_d
+ *   energy, magnetisation  device int64 [n_samples][n_slots] (written)
+ *   cuda_stream    cudaStream_t the work is enqueued on (NULL = legacy stream)
+ * Working storage is a fixed device array inside the library: 2 counters for
+ * each of at most IANUS_NOALLOC_MAX_CONFIGS (sample, slot) pairs, 512 KiB
+ * that every GPU which loads the library holds until the process exits.
+ * n_samples * n_slots above that limit returns IANUS_EINVAL, as do NULL
+ * pointers and invalid dim / L; a CUDA failure returns IANUS_ECUDA.
+ * The first call on a device looks up that array's device address (with the
+ * device current) and caches it; make that first call before any stream
+ * capture.  Each call clears the counters it uses before counting, but all
+ * calls share the one array: calls that may overlap on the GPU (different
+ * streams, or different host threads) race and give wrong results, so
+ * serialise them.  Asynchronous: results are ready when the stream is. */
+#define IANUS_NOALLOC_MAX_CONFIGS 32768
+ianus_status ianus_measure_bits64_noalloc(const uint64_t* spins, const uint64_t* couplings, int32_t dim,
+                                          int32_t L, int32_t n_samples, int32_t n_slots, int64_t* energy,
+                                          int64_t* magnetisation, void* cuda_stream);
+
 /* ---- Host-only table builders (the look-up tables of Sec. 3.2).  These
  * need no GPU; tests compare them with an independent builder. ---- */
 

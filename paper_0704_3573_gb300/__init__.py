@@ -37,7 +37,7 @@ EXPORTS = [
     "ianus_measure", "ianus_read_series", "ianus_get_spins_i8", "ianus_set_spins_i8", "ianus_get_couplings_i8",
     "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
-    "ianus_table_pt",
+    "ianus_table_pt", "ianus_measure_bits64_noalloc",
 ]
 
 
@@ -107,6 +107,7 @@ def lib(build_if_missing: bool = True):
         "ianus_table_ising": (sz, [i32, i32, C.c_double, vp, sz]),
         "ianus_table_potts": (sz, [C.c_double, vp, sz]),
         "ianus_table_pt": (sz, [C.c_double, C.c_double, vp, sz]),
+        "ianus_measure_bits64_noalloc": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

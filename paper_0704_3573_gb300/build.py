@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libianus.so")
 BUILD_DIR = os.path.join(ROOT, "_build")
 
-SOURCES = ["api.cu", "k_plain.cu", "k_msc.cu", "k_potts.cu", "k_pt.cu", "tables.cpp"]
+SOURCES = ["api.cu", "k_plain.cu", "k_msc.cu", "k_potts.cu", "k_pt.cu", "tables.cpp", "noalloc.cu"]
 PROBE_SOURCES = ["probe.cu"]
 PROBE_LIB = os.path.join(HERE, "libianus_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
