@@ -269,6 +269,12 @@ ianus_status ianus_set_state(ianus_lattice* lat, const void* host_buf,
  * error recorded by a kernel (ETIMEOUT) or the CUDA runtime (ECUDA). */
 ianus_status ianus_synchronize(ianus_lattice* lat);
 
+/* Kernel variant for the bit-sliced sweep (results are identical; only speed
+ * differs): 0 = automatic (lane-uniform threshold tables when n_temps == 1,
+ * per-lane threshold bit-planes otherwise), 1 = always per-lane bit-planes.
+ * EINVAL for other values. */
+ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
+
 /* Frees what the lattice allocated.  NULL is accepted.  The caller-owned
  * device buffer, if any, is not freed. */
 ianus_status ianus_destroy(ianus_lattice* lat);

@@ -37,7 +37,7 @@ EXPORTS = [
     "ianus_measure", "ianus_read_series", "ianus_get_spins_i8", "ianus_set_spins_i8", "ianus_get_couplings_i8",
     "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
-    "ianus_table_pt", "ianus_measure_bits64_noalloc",
+    "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant",
 ]
 
 
@@ -108,6 +108,7 @@ def lib(build_if_missing: bool = True):
         "ianus_table_potts": (sz, [C.c_double, vp, sz]),
         "ianus_table_pt": (sz, [C.c_double, C.c_double, vp, sz]),
         "ianus_measure_bits64_noalloc": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp]),
+        "ianus_set_variant": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -300,6 +301,10 @@ class Lattice:
     def set_state(self, blob: bytes):
         buf = np.frombuffer(blob, dtype=np.uint8).copy()
         _check(self._lib.ianus_set_state(self._h, _ptr(buf), buf.size), "ianus_set_state")
+
+    def set_variant(self, variant: int):
+        """0 = automatic kernel choice, 1 = per-lane threshold planes (tests)."""
+        _check(self._lib.ianus_set_variant(self._h, variant), "ianus_set_variant")
 
     def synchronize(self):
         _check(self._lib.ianus_synchronize(self._h), "ianus_synchronize")

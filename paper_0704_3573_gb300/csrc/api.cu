@@ -81,7 +81,7 @@ int plan(const ianus_config* c, Sizes& z) {
   };
   z.off_spins = take(z.spins_bytes);
   z.off_J = take(z.J_bytes);
-  z.off_thr = take((size_t)z.K * kMaxClasses * 8);
+  z.off_thr = take((size_t)z.K * kMaxClasses * 8 + sizeof(UniformLut));  // class thresholds, then the uniform tables
   z.off_tp = take(layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
   z.off_ptab = take(layout == IANUS_LAYOUT_U8X4 ? (size_t)z.K * 65536 * 16 : 0);
   z.off_pttab = take((size_t)std::max(z.K - 1, 0) * z.pt_cap * 8);
@@ -135,6 +135,25 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     for (int k = 0; k < K; ++k) class_thresholds(lat->D, algo, beta[k], &thr[(size_t)k * kMaxClasses]);
     CK(cudaMemcpyAsync(lat->thr, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, lat->stream));
     if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
+    lat->ulut_ok = false;
+    if (K == 1) {
+      UniformLut u{};
+      const int nclass = 2 * lat->D + 1;
+      uint32_t always = 0, cmp = 0;
+      for (int c = 0; c < nclass; ++c) {
+        const uint64_t T = thr[c];
+        if (T >= kTwo32) always |= 1u << c;
+        else if (algo == IANUS_HEATBATH || c < lat->D) cmp |= 1u << c;
+        for (int q = 0; q < 32; ++q)
+          if (T < kTwo32 && ((T >> (31 - q)) & 1ull)) u.t[q] |= (uint8_t)(1u << c);
+      }
+      u.always = (uint8_t)always;
+      u.need = (uint8_t)cmp;
+      lat->ulut = u;
+      CK(cudaMemcpyAsync(lat->thr + (size_t)K * kMaxClasses, &lat->ulut, sizeof(UniformLut), cudaMemcpyHostToDevice,
+                         lat->stream));
+      lat->ulut_ok = true;
+    }
   } else {
     if (beta_ok(beta, K)) {
       for (int k = 0; k < K; ++k)
@@ -287,6 +306,11 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->geom.D = z.D;
   lat->geom.L = z.L;
   lat->geom.h = z.L / 2;
+  lat->geom.lh = lat->geom.lL = 0;
+  if ((z.L & (z.L - 1)) == 0) {  // power of two: shift-based index arithmetic
+    while ((1 << lat->geom.lL) < z.L) ++lat->geom.lL;
+    lat->geom.lh = lat->geom.lL - 1;
+  }
   lat->geom.N = z.N;
   lat->geom.half = z.N / 2;
   lat->stream = (cudaStream_t)cfg->cuda_stream;
@@ -626,6 +650,13 @@ ianus_status ianus_synchronize(ianus_lattice* h) {
     lat->sticky = IANUS_ESTATE;
     return IANUS_ESTATE;
   }
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
+  GET_LAT(h);
+  if (variant < 0 || variant > 1) return IANUS_EINVAL;
+  lat->variant = variant;
   return IANUS_OK;
 }
 

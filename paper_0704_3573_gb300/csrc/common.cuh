@@ -60,6 +60,7 @@ struct Geom {
   int D, L, h;    // h = L/2
   uint32_t N;     // L^D
   uint32_t half;  // N/2 sites per colour
+  int lh, lL;     // log2(h), log2(L) when L is a power of two (else 0)
 };
 
 __host__ __device__ __forceinline__ uint32_t split_index(const Geom& g, int x, int y, int z) {
@@ -78,10 +79,21 @@ struct Nbr {
   uint32_t zp, zm;
 };
 
-__device__ __forceinline__ Nbr split_neighbours(const Geom& g, int c, uint32_t w) {
+template <bool P2>
+__device__ __forceinline__ Nbr split_neighbours_t(const Geom& g, int c, uint32_t w) {
   const uint32_t h = (uint32_t)g.h, L = (uint32_t)g.L;
-  const uint32_t row = w / h, k = w - row * h;
-  const uint32_t y = row % L, z = row / L;  // z = 0 for D = 2 (row < L)
+  uint32_t row, k, y, z;
+  if (P2) {  // L a power of two: shifts and masks
+    row = w >> g.lh;
+    k = w & (h - 1u);
+    y = row & (L - 1u);
+    z = row >> g.lL;
+  } else {
+    row = w / h;
+    k = w - row * h;
+    y = row % L;
+    z = row / L;  // z = 0 for D = 2 (row < L)
+  }
   const uint32_t xpar = (uint32_t)(c ^ (int)(y + z)) & 1u;
   const uint32_t x = 2u * k + xpar;
   const uint32_t oc = 1u - (uint32_t)c;
@@ -104,6 +116,42 @@ __device__ __forceinline__ Nbr split_neighbours(const Geom& g, int c, uint32_t w
     n.zp = n.zm = 0u;
   }
   return n;
+}
+
+__device__ __forceinline__ Nbr split_neighbours(const Geom& g, int c, uint32_t w) {
+  return split_neighbours_t<false>(g, c, w);
+}
+
+// Runtime-selected three-input logic on 64-bit words: out = f(a, b, c) with
+// f given by the 8-bit truth table `lut` (bit a*4 + b*2 + c), as one lop3.b32
+// per 32-bit half.  lop3 takes its table as an immediate, so the table picks
+// a case of a switch; callers keep `lut` warp-uniform so the branch does not
+// diverge.  MASK bounds the cases the caller can pass.
+#define IANUS_LOP3_CASE(n)                                                                       \
+  case (n):                                                                                      \
+    asm("lop3.b32 %0, %2, %3, %4, %5;\n\tlop3.b32 %1, %6, %7, %8, %5;"                        \
+        : "=r"(lo), "=r"(hi)                                                                     \
+        : "r"(al), "r"(bl), "r"(cl), "n"(n), "r"(ah), "r"(bh), "r"(ch));                        \
+    break;
+#define IANUS_LOP3_4(n) IANUS_LOP3_CASE(n) IANUS_LOP3_CASE((n) + 1) IANUS_LOP3_CASE((n) + 2) IANUS_LOP3_CASE((n) + 3)
+#define IANUS_LOP3_16(n) IANUS_LOP3_4(n) IANUS_LOP3_4((n) + 4) IANUS_LOP3_4((n) + 8) IANUS_LOP3_4((n) + 12)
+#define IANUS_LOP3_64(n) IANUS_LOP3_16(n) IANUS_LOP3_16((n) + 16) IANUS_LOP3_16((n) + 32) IANUS_LOP3_16((n) + 48)
+
+template <uint32_t MASK>
+__device__ __forceinline__ uint64_t lop3_rt(uint64_t a, uint64_t b, uint64_t c, uint32_t lut) {
+  const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
+  const uint32_t bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
+  const uint32_t cl = (uint32_t)c, ch = (uint32_t)(c >> 32);
+  uint32_t lo = 0, hi = 0;
+  switch (lut & MASK) {
+    IANUS_LOP3_64(0)
+    IANUS_LOP3_64(64)
+    IANUS_LOP3_64(128)
+    IANUS_LOP3_64(192)
+    default:
+      break;
+  }
+  return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 
 // Device error word bits (read by ianus_synchronize).

@@ -61,7 +61,7 @@ __device__ __forceinline__ void count_unsat(const uint64_t* e, uint64_t& u0, uin
 
 // ALGO 0 = Metropolis (only classes u < D need a random number),
 // ALGO 1 = heat bath (all 2D+1 classes).
-template <int D, int ALGO, int RT>
+template <int D, int ALGO, int RT, bool P2>
 __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
   constexpr int NC = (ALGO == 0) ? D : 2 * D + 1;  // classes that take a random
   extern __shared__ uint64_t sm_tp[];             // [R][kPlanes][kMaxClasses]
@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
   for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
-    const Nbr n = split_neighbours(geom, p.colour, w);
+    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
     uint64_t jw[2 * D];
     jw[0] = __ldg(Jg + n.self);
     jw[1] = __ldg(Jg + n.xm);
@@ -145,6 +145,78 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
   }
 }
 
+
+// Lane-uniform thresholds (every lane of every slot at the same temperature):
+// the threshold bit of plane p is a fixed boolean function of the class
+// bits (u2, u1, u0), i.e. one lop3 whose 8-bit truth table lut.t[p] has bit
+// u = bit (31 - p) of T(u).  The same holds for the "always" lanes
+// (T = 2^32) and for the lanes that need a random at all.  The plane loop
+// runs in lockstep across the warp, so the table index is warp-uniform.
+template <int D, int ALGO, int RT, bool P2>
+__global__ void __launch_bounds__(kBlock) k_sweep_bits_uniform(const BitsParams p, const uint8_t* __restrict__ lut_t,
+                                                               uint32_t lut_always, uint32_t lut_need) {
+  constexpr uint32_t TMASK = (ALGO == 0) ? ((1u << D) - 1u) : 0x7Fu;  // classes that compare
+  constexpr int R = RT;
+  __shared__ uint8_t s_lut[32];
+  if (threadIdx.x < 32) s_lut[threadIdx.x] = lut_t[threadIdx.x];
+  __syncthreads();
+  const int gt = blockIdx.y;  // g * K + tslot
+  const int g = gt / p.K, tslot = gt - g * p.K;
+  const Geom geom = p.geom;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = p.J + (size_t)g * D * N;
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
+    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
+    uint64_t jw[2 * D];
+    jw[0] = __ldg(Jg + n.self);
+    jw[1] = __ldg(Jg + n.xm);
+    jw[2] = __ldg(Jg + N + n.self);
+    jw[3] = __ldg(Jg + N + n.ym);
+    if (D == 3) {
+      jw[4] = __ldg(Jg + 2u * N + n.self);
+      jw[5] = __ldg(Jg + 2u * N + n.zm);
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      const int sigma = tslot * R + a;
+      uint64_t* sp = p.spins + ((size_t)g * p.slots + sigma) * N;
+      const uint64_t b = sp[n.self];
+      uint64_t e[2 * D];
+      e[0] = b ^ sp[n.xp] ^ jw[0];
+      e[1] = b ^ sp[n.xm] ^ jw[1];
+      e[2] = b ^ sp[n.yp] ^ jw[2];
+      e[3] = b ^ sp[n.ym] ^ jw[3];
+      if (D == 3) {
+        e[4] = b ^ sp[n.zp] ^ jw[4];
+        e[5] = b ^ sp[n.zm] ^ jw[5];
+      }
+      uint64_t u0, u1, u2;
+      count_unsat<D>(e, u0, u1, u2);
+      uint64_t lt = 0;
+      if (lut_always) lt = lop3_rt<0x7Fu>(u2, u1, u0, lut_always);
+      uint64_t und = lop3_rt<0x7Fu>(u2, u1, u0, lut_need);
+      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
+#pragma unroll 1
+      for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
+        const uint4 x = philox10(n.site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+        const uint64_t r0 = (uint64_t)x.x | ((uint64_t)x.y << 32);
+        const uint64_t r1 = (uint64_t)x.z | ((uint64_t)x.w << 32);
+        const uint64_t t0 = lop3_rt<TMASK>(u2, u1, u0, s_lut[2u * mm]);
+        const uint64_t c0 = und & t0 & ~r0;  // decided here: r < T
+        und &= ~(r0 ^ t0);
+        const uint64_t t1 = lop3_rt<TMASK>(u2, u1, u0, s_lut[2u * mm + 1u]);
+        const uint64_t c1 = und & t1 & ~r1;
+        und &= ~(r1 ^ t1);
+        lt |= c0 | c1;
+      }
+      const uint64_t flip = (ALGO == 0) ? lt : ~lt;
+      if (flip) sp[n.self] = b ^ flip;
+    }
+  }
+}
+
 // ---- initialisation: one Philox block gives the word of 64 samples ----
 
 __global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int slots, int ferro,
@@ -197,12 +269,13 @@ __global__ void k_build_planes(uint64_t* tp, const uint64_t* thr, const int32_t*
 // ---- measurements: per-lane counts with vertical (bit-sliced) counters ----
 //
 // Per site and configuration: unsatisfied forward bonds U (E = 2U - D N) and
-// spin-down count B (M = N - 2B).  Each thread adds its masks into 8-plane vertical counters
-// over up to kMeasIters sites, then the warp transposes them with ballots and
-// lane l of the sample group gets its total by an atomic add.
+// spin-down count B (M = N - 2B).  Each thread adds its masks into 6-plane
+// vertical counters over kMeasIters sites (at most 3 increments a site:
+// 48 < 64), then the warp transposes each plane with shuffles so that thread
+// j holds bit j of every thread's plane; a popcount gives lane j's total.
 
-constexpr int kCtr = 8;
-constexpr int kMeasIters = 64;  // 3 increments per site (3D): 192 < 256
+constexpr int kCtr = 6;
+constexpr int kMeasIters = 16;
 
 __device__ __forceinline__ void ctr_add(uint64_t* c, uint64_t x) {
 #pragma unroll
@@ -213,23 +286,93 @@ __device__ __forceinline__ void ctr_add(uint64_t* c, uint64_t x) {
   }
 }
 
+// 32x32 bit transpose across the warp: afterwards thread j holds, in bit t,
+// bit j of the word thread t passed in (five butterfly exchanges).
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t M[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const uint32_t sft = 16u >> i;
+    const uint32_t y = __shfl_xor_sync(0xffffffffu, x, sft);
+    x = (lane & sft) ? ((x & ~M[i]) | ((y >> sft) & M[i])) : ((x & M[i]) | ((y << sft) & ~M[i]));
+  }
+  return x;
+}
+
 // Warp-wide per-lane totals of a vertical counter; thread t receives the
 // totals of sample lanes t and t+32.
 __device__ __forceinline__ void ctr_flush(const uint64_t* c, long long& lo, long long& hi) {
-  const int lane = threadIdx.x & 31;
   lo = hi = 0;
 #pragma unroll
   for (int k = 0; k < kCtr; ++k) {
-    const uint32_t wl = (uint32_t)c[k], wh = (uint32_t)(c[k] >> 32);
-#pragma unroll 4
-    for (int j = 0; j < 32; ++j) {
-      const uint32_t bl = __ballot_sync(0xffffffffu, (wl >> j) & 1u);
-      const uint32_t bh = __ballot_sync(0xffffffffu, (wh >> j) & 1u);
-      if (lane == j) {
-        lo += (long long)__popc(bl) << k;
-        hi += (long long)__popc(bh) << k;
+    lo += (long long)__popc(warp_transpose32((uint32_t)c[k])) << k;
+    hi += (long long)__popc(warp_transpose32((uint32_t)(c[k] >> 32))) << k;
+  }
+}
+
+__device__ __forceinline__ void acc_add(int64_t* acc, int s, int S, size_t row, int field, long long v) {
+  if (s < S) atomicAdd((unsigned long long*)&acc[row * kAccStride + field], (unsigned long long)v);
+}
+
+// One temperature (slot = replica): E and M of every replica and, with two
+// replicas, Q = N - 2X with X the disagreement count, in one pass.
+template <int D, int R>
+__global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __restrict__ spins,
+                                                            const uint64_t* __restrict__ J, int64_t* acc, Geom geom,
+                                                            int S) {
+  const int g = blockIdx.y;
+  const uint32_t N = geom.N, L = (uint32_t)geom.L, h = (uint32_t)geom.h;
+  const uint64_t* Jg = J + (size_t)g * D * N;
+  const uint64_t* sg = spins + (size_t)g * R * N;
+  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
+  uint64_t cu[R][kCtr], cb[R][kCtr], cx[kCtr];
+#pragma unroll
+  for (int k = 0; k < kCtr; ++k) {
+    cx[k] = 0;
+#pragma unroll
+    for (int a = 0; a < R; ++a) cu[a][k] = cb[a][k] = 0;
+  }
+  for (int it = 0; it < kMeasIters; ++it) {
+    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+    if (j < N) {
+      const uint32_t rc = j / h, k = j - rc * h;
+      const uint32_t row = rc >> 1, c = rc & 1u;
+      const uint32_t y = row % L, z = row / L;
+      const uint32_t x = 2u * k + ((c ^ (y + z)) & 1u);
+      const uint32_t jx = split_index(geom, (int)((x + 1u == L) ? 0u : x + 1u), (int)y, (int)z);
+      const uint32_t jy = split_index(geom, (int)x, (int)((y + 1u == L) ? 0u : y + 1u), (int)z);
+      const uint32_t jz = D == 3 ? split_index(geom, (int)x, (int)y, (int)((z + 1u == L) ? 0u : z + 1u)) : 0u;
+      const uint64_t Jx = Jg[j], Jy = Jg[N + j], Jz = D == 3 ? Jg[2u * N + j] : 0ull;
+      uint64_t b[R];
+#pragma unroll
+      for (int a = 0; a < R; ++a) {
+        const uint64_t* sp = sg + (size_t)a * N;
+        b[a] = sp[j];
+        ctr_add(cu[a], b[a] ^ sp[jx] ^ Jx);
+        ctr_add(cu[a], b[a] ^ sp[jy] ^ Jy);
+        if (D == 3) ctr_add(cu[a], b[a] ^ sp[jz] ^ Jz);
+        ctr_add(cb[a], b[a]);
       }
+      if (R == 2) ctr_add(cx, b[0] ^ b[R - 1]);
     }
+  }
+  const int lane = threadIdx.x & 31;
+  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
+  long long lo, hi;
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    ctr_flush(cu[a], lo, hi);
+    acc_add(acc, s_lo, S, (size_t)s_lo * R + a, 0, lo);
+    acc_add(acc, s_hi, S, (size_t)s_hi * R + a, 0, hi);
+    ctr_flush(cb[a], lo, hi);
+    acc_add(acc, s_lo, S, (size_t)s_lo * R + a, 1, lo);
+    acc_add(acc, s_hi, S, (size_t)s_hi * R + a, 1, hi);
+  }
+  if (R == 2) {
+    ctr_flush(cx, lo, hi);
+    acc_add(acc, s_lo, S, (size_t)s_lo * R, 6, lo);
+    acc_add(acc, s_hi, S, (size_t)s_hi * R, 6, hi);
   }
 }
 
@@ -404,15 +547,26 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
   return (unsigned)g;
 }
 
-template <int D, int ALGO>
-cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
-  if (lat.R == 1)
-    k_sweep_bits<D, ALGO, 1><<<grid, kBlock, smem, lat.stream>>>(p);
+template <int D, int ALGO, bool P2>
+cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem, bool uniform) {
+  const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
+  if (uniform && lat.R == 1)
+    k_sweep_bits_uniform<D, ALGO, 1, P2><<<grid, kBlock, 0, lat.stream>>>(p, lut_t, lat.ulut.always, lat.ulut.need);
+  else if (uniform && lat.R == 2)
+    k_sweep_bits_uniform<D, ALGO, 2, P2><<<grid, kBlock, 0, lat.stream>>>(p, lut_t, lat.ulut.always, lat.ulut.need);
+  else if (lat.R == 1)
+    k_sweep_bits<D, ALGO, 1, P2><<<grid, kBlock, smem, lat.stream>>>(p);
   else if (lat.R == 2)
-    k_sweep_bits<D, ALGO, 2><<<grid, kBlock, smem, lat.stream>>>(p);
+    k_sweep_bits<D, ALGO, 2, P2><<<grid, kBlock, smem, lat.stream>>>(p);
   else
-    k_sweep_bits<D, ALGO, 0><<<grid, kBlock, smem, lat.stream>>>(p);
+    k_sweep_bits<D, ALGO, 0, P2><<<grid, kBlock, smem, lat.stream>>>(p);
   return cudaGetLastError();
+}
+
+template <int D, int ALGO>
+cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem, bool uniform) {
+  return lat.geom.lL > 0 ? sweep_dispatch<D, ALGO, true>(lat, p, grid, smem, uniform)
+                         : sweep_dispatch<D, ALGO, false>(lat, p, grid, smem, uniform);
 }
 
 }  // namespace
@@ -454,16 +608,33 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   dim3 grid((half + wpb - 1) / wpb, gts);
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
+  // lane-uniform thresholds: one temperature, so every lane of every slot
+  // shares the class thresholds (variant 1 forces the per-lane planes)
+  const bool uniform = lat.K == 1 && lat.ulut_ok && lat.variant != 1 && (lat.R == 1 || lat.R == 2);
   if (lat.D == 3)
-    return algo ? sweep_dispatch<3, 1>(lat, p, grid, smem) : sweep_dispatch<3, 0>(lat, p, grid, smem);
-  return algo ? sweep_dispatch<2, 1>(lat, p, grid, smem) : sweep_dispatch<2, 0>(lat, p, grid, smem);
+    return algo ? sweep_dispatch2<3, 1>(lat, p, grid, smem, uniform) : sweep_dispatch2<3, 0>(lat, p, grid, smem, uniform);
+  return algo ? sweep_dispatch2<2, 1>(lat, p, grid, smem, uniform) : sweep_dispatch2<2, 0>(lat, p, grid, smem, uniform);
 }
 
 cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
   cudaError_t e = cudaMemsetAsync(lat.acc, 0, (size_t)lat.S * lat.slots * kAccStride * sizeof(int64_t), lat.stream);
   if (e != cudaSuccess) return e;
   const uint32_t per_block = kBlock * kMeasIters;
-  dim3 grid((lat.N + per_block - 1) / per_block, (unsigned)(lat.G * lat.slots));
+  const unsigned nx = (lat.N + per_block - 1) / per_block;
+  if (lat.K == 1 && (lat.R == 1 || lat.R == 2)) {
+    // one pass for E, M and (R == 2) Q; the overlap is computed either way
+    dim3 grid(nx, (unsigned)lat.G);
+    const uint64_t* sp = (const uint64_t*)lat.spins;
+    const uint64_t* J = (const uint64_t*)lat.J;
+    if (lat.D == 3)
+      lat.R == 2 ? k_measure_bits_k1<3, 2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S)
+                 : k_measure_bits_k1<3, 1><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
+    else
+      lat.R == 2 ? k_measure_bits_k1<2, 2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S)
+                 : k_measure_bits_k1<2, 1><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
+    return cudaGetLastError();
+  }
+  dim3 grid(nx, (unsigned)(lat.G * lat.slots));
   if (lat.D == 3)
     k_measure_bits<3><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
                                                         lat.geom, lat.S, lat.R, lat.K, lat.slots);
@@ -471,7 +642,7 @@ cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
     k_measure_bits<2><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
                                                         lat.geom, lat.S, lat.R, lat.K, lat.slots);
   if (want_q && lat.R >= 2) {
-    dim3 gq((lat.N + per_block - 1) / per_block, (unsigned)(lat.G * lat.K));
+    dim3 gq(nx, (unsigned)(lat.G * lat.K));
     k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(
         (const uint64_t*)lat.spins, lat.slot_at, lat.acc, lat.N, lat.S, lat.R, lat.K, lat.slots);
   }

@@ -18,6 +18,14 @@ constexpr int kPlanes = 33;      // 32 threshold bit-planes + the "always" mask
 constexpr int kAccStride = 8;    // int64 accumulators per (sample, slot)
 constexpr uint64_t kTwo32 = 1ull << 32;
 
+// Truth tables of the lane-uniform threshold path: t[p] bit u = bit (31-p)
+// of the class-u threshold; always bit u = (T(u) == 2^32); need bit u = the
+// class compares against a random number.
+struct UniformLut {
+  uint8_t t[32];
+  uint8_t always, need, pad0, pad1;
+};
+
 struct Lattice {
   ianus_config cfg;
   int model, D, L, S, R, K, slots, layout;
@@ -66,6 +74,8 @@ struct Lattice {
   bool pt_tables_ok;
   int sticky;                // sticky error status (ESTATE after a failure)
   int variant;               // kernel variant knob (tuner), 0 = default
+  UniformLut ulut;           // valid when ulut_ok (n_temps == 1)
+  bool ulut_ok;
 };
 
 // ---- host table builders (tables.cpp) ----

@@ -19,8 +19,13 @@ SEED = 0x0704357300000000
 
 
 def _pair(ianus, model="ea", dim=3, L=4, S=1, R=1, K=1, seed=SEED, layout="auto", ferro=False, ids=None):
+    variant = 0
+    if layout == "bits64-planes":  # bit-sliced kernel with per-lane threshold planes
+        layout, variant = "bits64", 1
     lat = ianus.Lattice(model=model, dim=dim, L=L, n_samples=S, n_replicas=R, n_temps=K, seed=seed,
                         layout=layout, ferro=ferro, series_capacity=4096)
+    if variant:
+        lat.set_variant(variant)
     ids = list(range(S)) if ids is None else ids
     orc = Oracle(model=MODEL_ISING if model == "ea" else MODEL_POTTS, dim=dim, L=L, sample_ids=ids,
                  n_replicas=R, n_temps=K, seed=seed, ferro=ferro)
@@ -42,10 +47,11 @@ def test_potts_init_matches_oracle(ianus, dim, L, S, R):
     assert np.array_equal(lat.spins(), orc.spins())
 
 
-CASES = [(3, 2, 1, 1), (3, 4, 3, 2), (2, 4, 65, 1), (3, 6, 70, 2), (2, 8, 2, 2), (3, 8, 1, 1), (2, 2, 5, 2)]
+CASES = [(3, 2, 1, 1), (3, 4, 3, 2), (2, 4, 65, 1), (3, 6, 70, 2), (2, 8, 2, 2), (3, 8, 1, 1), (2, 2, 5, 2),
+         (3, 10, 3, 2), (2, 12, 67, 1)]
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-planes"])
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
 @pytest.mark.parametrize("dim,L,S,R", CASES)
 def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
@@ -62,7 +68,7 @@ def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
         assert np.array_equal(Q, Qo)
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-planes"])
 def test_series_matches_oracle(ianus, layout):
     lat, orc, _ = _pair(ianus, dim=3, L=6, S=67, R=2, layout=layout)
     lat.sweep(HEATBATH, 1.0, 23, measure_every=5)
@@ -77,7 +83,7 @@ def test_series_matches_oracle(ianus, layout):
 def test_extreme_temperatures(ianus, beta):
     """beta = 0 (T_H = 2^31 everywhere, Metropolis always flips) and a
     beta so large that T_M = 0 and T_H reaches 2^32."""
-    for layout in ("i8", "bits64"):
+    for layout in ("i8", "bits64", "bits64-planes"):
         for algo in (METROPOLIS, HEATBATH):
             lat, orc, _ = _pair(ianus, dim=3, L=4, S=66, R=1, layout=layout)
             lat.sweep(algo, beta, 3)
