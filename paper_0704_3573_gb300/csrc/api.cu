@@ -154,6 +154,7 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
                          lat->stream));
       lat->ulut_ok = true;
     }
+    lat->jit = (lat->ulut_ok && lat->layout == IANUS_LAYOUT_BITS64) ? jit_kernel(*lat, algo) : nullptr;
   } else {
     if (beta_ok(beta, K)) {
       for (int k = 0; k < K; ++k)

@@ -6,9 +6,18 @@
 // wheel (Sec. 3.3, Eq. (5)); the lattice and checkerboard are those of
 // Sec. 2.1 and Sec. 3.1.
 #pragma once
+#ifndef __CUDACC_RTC__
 #include <cstdint>
 
 #include <cuda_runtime.h>
+#else  // runtime compilation (jit.cu) provides no standard headers
+typedef unsigned char uint8_t;
+typedef signed char int8_t;
+typedef unsigned int uint32_t;
+typedef int int32_t;
+typedef unsigned long long uint64_t;
+typedef long long int64_t;
+#endif
 
 namespace ianus {
 
@@ -22,6 +31,7 @@ struct PhiloxKeys {
   uint32_t k1[10];
 };
 
+#ifndef __CUDACC_RTC__
 inline PhiloxKeys make_keys(uint64_t seed) {
   PhiloxKeys K;
   uint32_t a = (uint32_t)(seed & 0xffffffffu), b = (uint32_t)(seed >> 32);
@@ -33,6 +43,7 @@ inline PhiloxKeys make_keys(uint64_t seed) {
   }
   return K;
 }
+#endif
 
 // One Philox4x32-10 block: ten rounds of two 32x32->64 products; the high
 // halves are XORed with the other counter words and the round key.
@@ -122,36 +133,39 @@ __device__ __forceinline__ Nbr split_neighbours(const Geom& g, int c, uint32_t w
   return split_neighbours_t<false>(g, c, w);
 }
 
-// Runtime-selected three-input logic on 64-bit words: out = f(a, b, c) with
-// f given by the 8-bit truth table `lut` (bit a*4 + b*2 + c), as one lop3.b32
-// per 32-bit half.  lop3 takes its table as an immediate, so the table picks
-// a case of a switch; callers keep `lut` warp-uniform so the branch does not
-// diverge.  MASK bounds the cases the caller can pass.
-#define IANUS_LOP3_CASE(n)                                                                       \
-  case (n):                                                                                      \
-    asm("lop3.b32 %0, %2, %3, %4, %5;\n\tlop3.b32 %1, %6, %7, %8, %5;"                        \
-        : "=r"(lo), "=r"(hi)                                                                     \
-        : "r"(al), "r"(bl), "r"(cl), "n"(n), "r"(ah), "r"(bh), "r"(ch));                        \
-    break;
-#define IANUS_LOP3_4(n) IANUS_LOP3_CASE(n) IANUS_LOP3_CASE((n) + 1) IANUS_LOP3_CASE((n) + 2) IANUS_LOP3_CASE((n) + 3)
-#define IANUS_LOP3_16(n) IANUS_LOP3_4(n) IANUS_LOP3_4((n) + 4) IANUS_LOP3_4((n) + 8) IANUS_LOP3_4((n) + 12)
-#define IANUS_LOP3_64(n) IANUS_LOP3_16(n) IANUS_LOP3_16((n) + 16) IANUS_LOP3_16((n) + 32) IANUS_LOP3_16((n) + 48)
+// Launch parameters of the bit-sliced sweep kernels (k_msc.cu and the
+// runtime-specialised kernel of jit_sweep.cuh).
+struct BitsParams {
+  uint64_t* spins;        // [G][slots][N]
+  const uint64_t* J;      // [G][D][N]
+  const uint64_t* tp;     // [G][slots][kPlanes][kMaxClasses] per-lane threshold planes
+  Geom geom;
+  int G, R, K, slots;
+  int colour;
+  uint32_t t_lo, t_hi;
+  uint32_t words_per_block;  // colour-c words handled by one block (multiple of the block size)
+  PhiloxKeys keys;
+};
 
-template <uint32_t MASK>
-__device__ __forceinline__ uint64_t lop3_rt(uint64_t a, uint64_t b, uint64_t c, uint32_t lut) {
-  const uint32_t al = (uint32_t)a, ah = (uint32_t)(a >> 32);
-  const uint32_t bl = (uint32_t)b, bh = (uint32_t)(b >> 32);
-  const uint32_t cl = (uint32_t)c, ch = (uint32_t)(c >> 32);
-  uint32_t lo = 0, hi = 0;
-  switch (lut & MASK) {
-    IANUS_LOP3_64(0)
-    IANUS_LOP3_64(64)
-    IANUS_LOP3_64(128)
-    IANUS_LOP3_64(192)
-    default:
-      break;
+// Number of unsatisfied bonds per lane as bit-planes (u2, u1, u0), from the
+// 2D unsatisfied-bond words e[]: a carry-save adder tree.
+template <int D>
+__device__ __forceinline__ void count_unsat(const uint64_t* e, uint64_t& u0, uint64_t& u1, uint64_t& u2) {
+  const uint64_t sa = e[0] ^ e[1] ^ e[2];
+  const uint64_t ca = (e[0] & e[1]) | (e[0] & e[2]) | (e[1] & e[2]);
+  if (D == 3) {
+    const uint64_t sb = e[3] ^ e[4] ^ e[5];
+    const uint64_t cb = (e[3] & e[4]) | (e[3] & e[5]) | (e[4] & e[5]);
+    u0 = sa ^ sb;
+    const uint64_t k = sa & sb;
+    u1 = ca ^ cb ^ k;
+    u2 = (ca & cb) | (ca & k) | (cb & k);
+  } else {
+    u0 = sa ^ e[3];
+    const uint64_t k = sa & e[3];
+    u1 = ca ^ k;
+    u2 = ca & k;
   }
-  return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 
 // Device error word bits (read by ianus_synchronize).

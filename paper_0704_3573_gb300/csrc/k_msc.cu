@@ -27,38 +27,6 @@ namespace {
 
 constexpr int kBlock = 256;
 
-struct BitsParams {
-  uint64_t* spins;        // [G][slots][N]
-  const uint64_t* J;      // [G][D][N]
-  const uint64_t* tp;     // [G][slots][kPlanes][kMaxClasses]
-  Geom geom;
-  int G, R, K, slots;
-  int colour;
-  uint32_t t_lo, t_hi;
-  uint32_t words_per_block;  // colour-c words handled by one block (multiple of kBlock)
-  PhiloxKeys keys;
-};
-
-template <int D>
-__device__ __forceinline__ void count_unsat(const uint64_t* e, uint64_t& u0, uint64_t& u1, uint64_t& u2) {
-  // full adder on three bit-vectors
-  const uint64_t sa = e[0] ^ e[1] ^ e[2];
-  const uint64_t ca = (e[0] & e[1]) | (e[0] & e[2]) | (e[1] & e[2]);
-  if (D == 3) {
-    const uint64_t sb = e[3] ^ e[4] ^ e[5];
-    const uint64_t cb = (e[3] & e[4]) | (e[3] & e[5]) | (e[4] & e[5]);
-    u0 = sa ^ sb;
-    const uint64_t k = sa & sb;
-    u1 = ca ^ cb ^ k;
-    u2 = (ca & cb) | (ca & k) | (cb & k);
-  } else {
-    u0 = sa ^ e[3];
-    const uint64_t k = sa & e[3];
-    u1 = ca ^ k;
-    u2 = ca & k;
-  }
-}
-
 // ALGO 0 = Metropolis (only classes u < D need a random number),
 // ALGO 1 = heat bath (all 2D+1 classes).
 template <int D, int ALGO, int RT, bool P2>
@@ -145,77 +113,6 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
   }
 }
 
-
-// Lane-uniform thresholds (every lane of every slot at the same temperature):
-// the threshold bit of plane p is a fixed boolean function of the class
-// bits (u2, u1, u0), i.e. one lop3 whose 8-bit truth table lut.t[p] has bit
-// u = bit (31 - p) of T(u).  The same holds for the "always" lanes
-// (T = 2^32) and for the lanes that need a random at all.  The plane loop
-// runs in lockstep across the warp, so the table index is warp-uniform.
-template <int D, int ALGO, int RT, bool P2>
-__global__ void __launch_bounds__(kBlock) k_sweep_bits_uniform(const BitsParams p, const uint8_t* __restrict__ lut_t,
-                                                               uint32_t lut_always, uint32_t lut_need) {
-  constexpr uint32_t TMASK = (ALGO == 0) ? ((1u << D) - 1u) : 0x7Fu;  // classes that compare
-  constexpr int R = RT;
-  __shared__ uint8_t s_lut[32];
-  if (threadIdx.x < 32) s_lut[threadIdx.x] = lut_t[threadIdx.x];
-  __syncthreads();
-  const int gt = blockIdx.y;  // g * K + tslot
-  const int g = gt / p.K, tslot = gt - g * p.K;
-  const Geom geom = p.geom;
-  const uint32_t N = geom.N;
-  const uint64_t* Jg = p.J + (size_t)g * D * N;
-  const uint32_t w_begin = blockIdx.x * p.words_per_block;
-  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
-  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
-    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
-    uint64_t jw[2 * D];
-    jw[0] = __ldg(Jg + n.self);
-    jw[1] = __ldg(Jg + n.xm);
-    jw[2] = __ldg(Jg + N + n.self);
-    jw[3] = __ldg(Jg + N + n.ym);
-    if (D == 3) {
-      jw[4] = __ldg(Jg + 2u * N + n.self);
-      jw[5] = __ldg(Jg + 2u * N + n.zm);
-    }
-#pragma unroll
-    for (int a = 0; a < R; ++a) {
-      const int sigma = tslot * R + a;
-      uint64_t* sp = p.spins + ((size_t)g * p.slots + sigma) * N;
-      const uint64_t b = sp[n.self];
-      uint64_t e[2 * D];
-      e[0] = b ^ sp[n.xp] ^ jw[0];
-      e[1] = b ^ sp[n.xm] ^ jw[1];
-      e[2] = b ^ sp[n.yp] ^ jw[2];
-      e[3] = b ^ sp[n.ym] ^ jw[3];
-      if (D == 3) {
-        e[4] = b ^ sp[n.zp] ^ jw[4];
-        e[5] = b ^ sp[n.zm] ^ jw[5];
-      }
-      uint64_t u0, u1, u2;
-      count_unsat<D>(e, u0, u1, u2);
-      uint64_t lt = 0;
-      if (lut_always) lt = lop3_rt<0x7Fu>(u2, u1, u0, lut_always);
-      uint64_t und = lop3_rt<0x7Fu>(u2, u1, u0, lut_need);
-      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
-#pragma unroll 1
-      for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
-        const uint4 x = philox10(n.site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
-        const uint64_t r0 = (uint64_t)x.x | ((uint64_t)x.y << 32);
-        const uint64_t r1 = (uint64_t)x.z | ((uint64_t)x.w << 32);
-        const uint64_t t0 = lop3_rt<TMASK>(u2, u1, u0, s_lut[2u * mm]);
-        const uint64_t c0 = und & t0 & ~r0;  // decided here: r < T
-        und &= ~(r0 ^ t0);
-        const uint64_t t1 = lop3_rt<TMASK>(u2, u1, u0, s_lut[2u * mm + 1u]);
-        const uint64_t c1 = und & t1 & ~r1;
-        und &= ~(r1 ^ t1);
-        lt |= c0 | c1;
-      }
-      const uint64_t flip = (ALGO == 0) ? lt : ~lt;
-      if (flip) sp[n.self] = b ^ flip;
-    }
-  }
-}
 
 // ---- initialisation: one Philox block gives the word of 64 samples ----
 
@@ -548,13 +445,8 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 }
 
 template <int D, int ALGO, bool P2>
-cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem, bool uniform) {
-  const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
-  if (uniform && lat.R == 1)
-    k_sweep_bits_uniform<D, ALGO, 1, P2><<<grid, kBlock, 0, lat.stream>>>(p, lut_t, lat.ulut.always, lat.ulut.need);
-  else if (uniform && lat.R == 2)
-    k_sweep_bits_uniform<D, ALGO, 2, P2><<<grid, kBlock, 0, lat.stream>>>(p, lut_t, lat.ulut.always, lat.ulut.need);
-  else if (lat.R == 1)
+cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
+  if (lat.R == 1)
     k_sweep_bits<D, ALGO, 1, P2><<<grid, kBlock, smem, lat.stream>>>(p);
   else if (lat.R == 2)
     k_sweep_bits<D, ALGO, 2, P2><<<grid, kBlock, smem, lat.stream>>>(p);
@@ -564,9 +456,9 @@ cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t 
 }
 
 template <int D, int ALGO>
-cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem, bool uniform) {
-  return lat.geom.lL > 0 ? sweep_dispatch<D, ALGO, true>(lat, p, grid, smem, uniform)
-                         : sweep_dispatch<D, ALGO, false>(lat, p, grid, smem, uniform);
+cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
+  return lat.geom.lL > 0 ? sweep_dispatch<D, ALGO, true>(lat, p, grid, smem)
+                         : sweep_dispatch<D, ALGO, false>(lat, p, grid, smem);
 }
 
 }  // namespace
@@ -608,12 +500,16 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   dim3 grid((half + wpb - 1) / wpb, gts);
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
-  // lane-uniform thresholds: one temperature, so every lane of every slot
-  // shares the class thresholds (variant 1 forces the per-lane planes)
-  const bool uniform = lat.K == 1 && lat.ulut_ok && lat.variant != 1 && (lat.R == 1 || lat.R == 2);
+  // lane-uniform thresholds (one temperature): the kernel specialised for
+  // them at run time; variant 1 forces the per-lane threshold planes
+  if (lat.K == 1 && lat.jit && lat.variant != 1) {
+    const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
+    void* args[] = {(void*)&p, (void*)&lut_t};
+    return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, 0, lat.stream);
+  }
   if (lat.D == 3)
-    return algo ? sweep_dispatch2<3, 1>(lat, p, grid, smem, uniform) : sweep_dispatch2<3, 0>(lat, p, grid, smem, uniform);
-  return algo ? sweep_dispatch2<2, 1>(lat, p, grid, smem, uniform) : sweep_dispatch2<2, 0>(lat, p, grid, smem, uniform);
+    return algo ? sweep_dispatch2<3, 1>(lat, p, grid, smem) : sweep_dispatch2<3, 0>(lat, p, grid, smem);
+  return algo ? sweep_dispatch2<2, 1>(lat, p, grid, smem) : sweep_dispatch2<2, 0>(lat, p, grid, smem);
 }
 
 cudaError_t launch_measure_bits(Lattice& lat, int want_q) {

@@ -76,6 +76,7 @@ struct Lattice {
   int variant;               // kernel variant knob (tuner), 0 = default
   UniformLut ulut;           // valid when ulut_ok (n_temps == 1)
   bool ulut_ok;
+  cudaKernel_t jit;          // sweep kernel specialised for ulut (null: use the per-lane planes)
 };
 
 // ---- host table builders (tables.cpp) ----
@@ -86,6 +87,10 @@ size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
 // Metropolis: u < D -> T_M(4D - 4u), u >= D -> 2^32 (always); inv = 0.
 // Heat bath: T_H(2D - 2u), inv = 1 (keep iff r < T).
 void class_thresholds(int dim, int algo, double beta, uint64_t* thr /*[kMaxClasses]*/);
+
+// Run-time specialised bit-sliced sweep for lat.ulut (jit.cu); null when
+// runtime compilation is unavailable.
+cudaKernel_t jit_kernel(const Lattice& lat, int algo);
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)

@@ -1,0 +1,45 @@
+"""The run-time specialised sweep kernel (csrc/jit_sweep.cuh) compiles with
+NVRTC for sm_103a for the parameter sets the library generates.  NVRTC needs
+no GPU, so this runs on the CPU host; the GPU parity tests then check the
+compiled kernel's results bit for bit."""
+
+import ctypes as C
+import os
+
+import pytest
+
+CSRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_0704_3573_gb300", "csrc")
+
+
+def _nvrtc():
+    for name in ("libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"):
+        try:
+            return C.CDLL(name)
+        except OSError:
+            continue
+    pytest.skip("NVRTC not available")
+
+
+@pytest.mark.parametrize("D,algo,R,P2", [(3, 1, 2, 1), (3, 0, 1, 0), (2, 1, 1, 1), (2, 0, 2, 0)])
+def test_jit_kernel_compiles_for_sm103a(D, algo, R, P2):
+    lib = _nvrtc()
+    hdrs = [open(os.path.join(CSRC, n), "rb").read() for n in ("common.cuh", "jit_sweep.cuh")]
+    luts = ",".join(str((13 * q + 5) & 0x7F) for q in range(32))
+    pre = (f"#define IANUS_JIT_D {D}\n#define IANUS_JIT_ALGO {algo}\n#define IANUS_JIT_R {R}\n"
+           f"#define IANUS_JIT_P2 {P2}\n#define IANUS_JIT_LUTS {luts}\n#define IANUS_JIT_ALWAYS 0\n"
+           f"#define IANUS_JIT_NEED 127\n#include \"jit_sweep.cuh\"\n").encode()
+    prog = C.c_void_p()
+    H = (C.c_char_p * 2)(*hdrs)
+    N = (C.c_char_p * 2)(b"common.cuh", b"jit_sweep.cuh")
+    assert lib.nvrtcCreateProgram(C.byref(prog), pre, b"ianus_jit_sweep.cu", 2, H, N) == 0
+    opts = (C.c_char_p * 2)(b"--gpu-architecture=sm_103a", b"-std=c++17")
+    rc = lib.nvrtcCompileProgram(prog, 2, opts)
+    n = C.c_size_t()
+    lib.nvrtcGetProgramLogSize(prog, C.byref(n))
+    log = C.create_string_buffer(n.value)
+    lib.nvrtcGetProgramLog(prog, log)
+    size = C.c_size_t()
+    lib.nvrtcGetCUBINSize(prog, C.byref(size))
+    lib.nvrtcDestroyProgram(C.byref(prog))
+    assert rc == 0, log.value.decode()
+    assert size.value > 1000
