@@ -64,14 +64,19 @@ def expected_plane_pairs(lanes: int = 64) -> float:
 
 
 def algorithmic_ops_per_word_hb3d(R_: int = 2) -> float:
-    """32-bit integer operations one heat-bath update of a 64-lane site word
-    needs in 3D (loads, 6 unsatisfied bits, adder tree, 7 class masks, per
-    plane: threshold bits and compare, per plane pair: one Philox4x32-10
-    block, write-back).  64-bit logic counts as two 32-bit operations."""
-    fixed = (7 + 6.0 / R_) + 12 + 16 + 14 + 3
-    per_plane = 14 + 4
-    per_pair = 10 * 4 + 1
-    return fixed + expected_plane_pairs() * (2 * per_plane + per_pair)
+    """Minimal 32-bit integer operations one 3D heat-bath update of a 64-lane
+    site word needs (64-bit logic counts as two 32-bit operations):
+      fixed: 7 spin + 6/R coupling loads, 6 unsatisfied-bond words (12), the
+        6->3 adder tree (16), the always / needs-a-random masks (one lop3
+        each, 4), write-back (3);
+      per plane: the threshold bit-plane as one lop3 of (u2, u1, u0) (2), the
+        compare (r < T decided where r and T first differ: 4);
+      per plane pair: one Philox4x32-10 block (10 rounds x (2 mad.wide +
+        2 lop3) + 1 counter word) and merging the decided-less lanes (2);
+    times the expected number of plane pairs a word needs."""
+    fixed = (7 + 6.0 / R_) + 12 + 16 + 4 + 3
+    per_pair = 10 * 4 + 1 + 2 * (2 + 4) + 2
+    return fixed + expected_plane_pairs() * per_pair
 
 
 # ---------------- distributed helpers ----------------
@@ -269,7 +274,7 @@ def run_gpu(args, ws, rank, local):
     probe = probe_peak()
     peak = probe["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if probe else None
     roofline = {
-        "bound": "alu", "kernel": "k_sweep_bits<3,HB,R=2>", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+        "bound": "alu", "kernel": "ianus_jit_sweep (3D heat bath, R=2, thresholds as lop3 immediates)", "achieved": achieved, "peak": peak, "unit": "Tops/s",
         "frac": (achieved / peak) if peak else None, "traffic": None,
         "ops_per_word": ops_word, "words_per_launch": words_per_launch, "launch_us": kern_s * 1e6,
         "peak_source": "probe lop3.b32 ops/clk/SM x 152 SMs x 2070 MHz" if probe else None,
@@ -313,17 +318,38 @@ def run_gpu(args, ws, rank, local):
                "sample": f"samples 0..{nthr - 1} x {R} replicas, {args.cpu_sweeps} sweeps of the L=64 workload "
                          f"({upd} updates, {dt:.1f} s wall)"}
 
-    launches = args.steps * (2 * SWEEPS_PER_STEP + 3 * (SWEEPS_PER_STEP // MEASURE_EVERY))
+    serving = run_serving(args) if (rank == 0 and args.serve_jobs > 0) else None
+
+    launches = args.steps * (2 * SWEEPS_PER_STEP + 2 * (SWEEPS_PER_STEP // MEASURE_EVERY))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u64", "data": "synthetic",
         "config": config_dict(ws),
         "wall_s": wall, "series_rows": n_rows, "gpu_launches": launches, "clocks": clk, "roofline": roofline,
-        "e2e": e2e, "plain": plain, "cpu_baseline": cpu,
+        "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "serving": serving,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_serving(args):
+    """The serving mix (3D/2D EA jobs of 1..64 samples, L from the listed
+    sides, T in [0.5, 2], sweeps log-uniform in [10^3, 10^5] scaled by
+    --serve-scale), Poisson arrivals at 0.8 x the capacity measured on a
+    saturated run of the first fifth of the jobs; p50/p99 latency and
+    aggregate spin updates/ns."""
+    from paper_0704_3573_gb300 import serve
+
+    jobs = serve.job_mix(args.serve_jobs, sweep_scale=args.serve_scale)
+    server = serve.Server(mem_budget=16 << 30, max_active=64, n_streams=16, chunk_sweeps=50)
+    calib = jobs[: max(10, len(jobs) // 5)]
+    rate = serve.calibrated_rate(server, calib, load=0.8)
+    _, st = server.run(serve.poisson_arrivals(jobs, rate))
+    st["arrival_rate_per_s"] = rate
+    st["sweep_scale"] = args.serve_scale
+    st["mix"] = "3D L in {8..80} / 2D L in {64..1024}, 1-64 samples, T~U[0.5,2], sweeps log-U[1e3,1e5] x scale"
+    return st
 
 
 def probe_peak():
@@ -391,6 +417,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--serve-scale", type=float, default=0.05)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()

@@ -270,8 +270,14 @@ ianus_status ianus_set_state(ianus_lattice* lat, const void* host_buf,
 ianus_status ianus_synchronize(ianus_lattice* lat);
 
 /* Kernel variant for the bit-sliced sweep (results are identical; only speed
- * differs): 0 = automatic (lane-uniform threshold tables when n_temps == 1,
- * per-lane threshold bit-planes otherwise), 1 = always per-lane bit-planes.
+ * differs).  With one temperature the thresholds are the same in every lane
+ * and the sweep kernel can be specialised for them at run time (NVRTC, a
+ * fraction of a second per new table set, cached per device).
+ *   0 = automatic: specialise lattices of >= 2^20 site words, else use the
+ *       precompiled kernel with per-lane threshold bit-planes;
+ *   1 = always the precompiled per-lane kernel;
+ *   2 = specialise whenever n_temps == 1.
+ * If run-time compilation is unavailable, the precompiled kernel runs.
  * EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
 

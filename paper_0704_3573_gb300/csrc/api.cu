@@ -154,7 +154,8 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
                          lat->stream));
       lat->ulut_ok = true;
     }
-    lat->jit = (lat->ulut_ok && lat->layout == IANUS_LAYOUT_BITS64) ? jit_kernel(*lat, algo) : nullptr;
+    lat->jit = nullptr;  // specialised lazily by the first launch that wants it
+    lat->jit_algo = -1;
   } else {
     if (beta_ok(beta, K)) {
       for (int k = 0; k < K; ++k)
@@ -317,6 +318,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->stream = (cudaStream_t)cfg->cuda_stream;
   lat->keys = make_keys(cfg->seed);
   lat->algo = -1;
+  lat->jit_algo = -1;
   lat->bytes = z.total;
   if (cfg->device_buffer) {
     if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {
@@ -656,7 +658,7 @@ ianus_status ianus_synchronize(ianus_lattice* h) {
 
 ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   GET_LAT(h);
-  if (variant < 0 || variant > 1) return IANUS_EINVAL;
+  if (variant < 0 || variant > 2) return IANUS_EINVAL;
   lat->variant = variant;
   return IANUS_OK;
 }

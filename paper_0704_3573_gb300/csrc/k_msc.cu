@@ -500,9 +500,17 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   dim3 grid((half + wpb - 1) / wpb, gts);
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
-  // lane-uniform thresholds (one temperature): the kernel specialised for
-  // them at run time; variant 1 forces the per-lane threshold planes
-  if (lat.K == 1 && lat.jit && lat.variant != 1) {
+  // Lane-uniform thresholds (one temperature): the kernel specialised for
+  // them at run time.  Variant 0 specialises lattices of at least 2^20 site
+  // words (a compile costs a fraction of a second), variant 2 always,
+  // variant 1 never.
+  const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
+  const bool want_jit = lat.K == 1 && lat.ulut_ok && (lat.variant == 2 || (lat.variant == 0 && words >= (1ull << 20)));
+  if (want_jit && lat.jit_algo != algo) {
+    lat.jit = jit_kernel(lat, algo);
+    lat.jit_algo = algo;
+  }
+  if (want_jit && lat.jit) {
     const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
     void* args[] = {(void*)&p, (void*)&lut_t};
     return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, 0, lat.stream);

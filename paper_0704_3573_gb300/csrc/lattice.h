@@ -77,6 +77,7 @@ struct Lattice {
   UniformLut ulut;           // valid when ulut_ok (n_temps == 1)
   bool ulut_ok;
   cudaKernel_t jit;          // sweep kernel specialised for ulut (null: use the per-lane planes)
+  int jit_algo;              // algorithm the specialisation was requested for; -1 = not yet
 };
 
 // ---- host table builders (tables.cpp) ----

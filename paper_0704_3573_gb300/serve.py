@@ -1,0 +1,224 @@
+"""Continuous-batching server for spin-glass Monte Carlo jobs.
+
+A job is one lattice batch (3D or 2D EA +-J glass, 1..64 disorder samples,
+one temperature, a number of sweeps, Metropolis or heat bath) whose result is
+its final energy and magnetisation per sample.  Jobs arrive over time; the
+server admits them while the device-memory budget and the number of active
+slots allow, keeps each admitted job's lattice and random-stream state
+resident on the GPU, and interleaves their sweeps: every active job receives
+its next chunk of sweeps on one of several CUDA streams as soon as its
+previous chunk has finished, so the work of different jobs overlaps on the
+device.  A finished job is measured, its memory released, and waiting jobs
+are admitted in arrival order.
+
+Results do not depend on the mix: each job owns its lattice, and every
+random number is a function of (job seed, sample, slot, site, sweep) only.
+All per-site work runs in libianus.so; this module only schedules calls.
+"""
+
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from collections import deque
+
+import numpy as np
+
+from . import HEATBATH, METROPOLIS, Lattice
+from . import lib as _lib
+
+L3D = (8, 12, 16, 24, 32, 48, 64, 80)
+L2D = (64, 128, 256, 512, 1024)
+
+
+@dataclasses.dataclass
+class Job:
+    id: int
+    dim: int
+    L: int
+    samples: int
+    T: float
+    sweeps: int
+    algo: int
+    seed: int
+    arrival: float = 0.0  # seconds after the start of the run
+
+    @property
+    def updates(self) -> int:
+        return self.samples * self.L ** self.dim * self.sweeps
+
+
+@dataclasses.dataclass
+class Result:
+    job: Job
+    energy: np.ndarray         # [samples]
+    magnetisation: np.ndarray  # [samples]
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.job.arrival
+
+
+def job_mix(n_jobs: int, seed: int = 0x0704357300000004, sweep_scale: float = 1.0, min_sweeps: int = 10,
+            L3=L3D, L2=L2D, max_samples: int = 64) -> list[Job]:
+    """The serving mix: 3D or 2D with probability 1/2, L uniform over the
+    listed sides, samples uniform in 1..64, T uniform in [0.5, 2.0], sweeps
+    log-uniform in [10^3, 10^5] (a multiple of 10, times sweep_scale),
+    Metropolis or heat bath with probability 1/2.  Seeded."""
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for i in range(n_jobs):
+        dim = 3 if rng.random() < 0.5 else 2
+        L = int(rng.choice(L3 if dim == 3 else L2))
+        samples = int(rng.integers(1, max_samples + 1))
+        T = float(rng.uniform(0.5, 2.0))
+        sweeps = int(round(10 ** rng.uniform(3, 5) / 10)) * 10
+        sweeps = max(min_sweeps, int(round(sweeps * sweep_scale / 10)) * 10)
+        algo = METROPOLIS if rng.random() < 0.5 else HEATBATH
+        jobs.append(Job(i, dim, L, samples, T, sweeps, algo, seed=(seed + 1000003 * (i + 1)) & ((1 << 64) - 1)))
+    return jobs
+
+
+def poisson_arrivals(jobs: list[Job], rate: float, seed: int = 11) -> list[Job]:
+    """Assign Poisson arrival times (rate in jobs per second)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for j in jobs:
+        t += float(rng.exponential(1.0 / rate)) if rate > 0 else 0.0
+        out.append(dataclasses.replace(j, arrival=t))
+    return out
+
+
+def footprint(job: Job) -> int:
+    """Device bytes the job's lattice needs (ianus_required_bytes)."""
+    import ctypes
+
+    from . import ABI_VERSION, IanusConfig, LAYOUT_BITS64
+
+    c = IanusConfig()
+    c.abi_version = ABI_VERSION
+    c.model, c.dim, c.L = 0, job.dim, job.L
+    c.n_samples, c.n_replicas, c.n_temps = job.samples, 1, 1
+    c.layout, c.disorder, c.series_capacity, c.seed = LAYOUT_BITS64, 0, 1, job.seed
+    return int(_lib().ianus_required_bytes(ctypes.byref(c)))
+
+
+class _Active:
+    __slots__ = ("job", "lat", "stream", "event", "done", "admitted", "footprint")
+
+
+class Server:
+    """Admission by memory and slots; chunked, stream-interleaved sweeps."""
+
+    def __init__(self, mem_budget: int = 8 << 30, max_active: int = 64, n_streams: int = 8,
+                 chunk_sweeps: int = 100):
+        import torch
+
+        self.torch = torch
+        self.mem_budget = mem_budget
+        self.max_active = max_active
+        self.chunk = chunk_sweeps
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self._rr = 0
+
+    def _admit(self, job: Job, now: float) -> _Active:
+        a = _Active()
+        a.job = job
+        a.stream = self.streams[self._rr % len(self.streams)]
+        self._rr += 1
+        a.lat = Lattice(dim=job.dim, L=job.L, n_samples=job.samples, n_replicas=1, seed=job.seed,
+                        layout="bits64", series_capacity=1, stream=a.stream)
+        a.event = None
+        a.done = 0
+        a.admitted = now
+        a.footprint = footprint(job)
+        return a
+
+    def _issue(self, a: _Active):
+        n = min(self.chunk, a.job.sweeps - a.done)
+        with self.torch.cuda.stream(a.stream):
+            a.lat.sweep(a.job.algo, 1.0 / a.job.T, n)
+            ev = self.torch.cuda.Event()
+            ev.record(a.stream)
+        a.event = ev
+        a.done += n
+
+    def run(self, jobs: list[Job], realtime: bool = True) -> tuple[list[Result], dict]:
+        """Serve jobs (sorted by arrival).  With realtime=False every job is
+        available at t=0 (a saturated queue)."""
+        torch = self.torch
+        pending = deque(sorted(jobs, key=lambda j: j.arrival))
+        active: list[_Active] = []
+        results: list[Result] = []
+        used = 0
+        t0 = time.perf_counter()
+        while pending or active:
+            now = time.perf_counter() - t0
+            # admit arrived jobs, in order, while memory and slots allow
+            while pending and len(active) < self.max_active and (not realtime or pending[0].arrival <= now):
+                fp = footprint(pending[0])
+                if used + fp > self.mem_budget and active:
+                    break
+                job = pending.popleft()
+                a = self._admit(job, now)
+                used += a.footprint
+                active.append(a)
+                self._issue(a)
+            progressed = False
+            still = []
+            for a in active:
+                if a.event is not None and not a.event.query():
+                    still.append(a)
+                    continue
+                progressed = True
+                if a.done < a.job.sweeps:
+                    self._issue(a)
+                    still.append(a)
+                    continue
+                E, M, _ = a.lat.measure(overlap=False)
+                fin = time.perf_counter() - t0
+                results.append(Result(a.job, E[:, 0, 0].copy(), M[:, 0, 0].copy(), a.admitted, fin))
+                used -= a.footprint
+                a.lat.close()
+                del a.lat
+            active = still
+            if not progressed:
+                if realtime and not active and pending:
+                    time.sleep(max(0.0, min(0.002, pending[0].arrival - (time.perf_counter() - t0))))
+                else:
+                    time.sleep(0.0002)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        lat = np.array([r.latency for r in results])
+        upd = sum(r.job.updates for r in results)
+        stats = {
+            "jobs": len(results),
+            "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+            "p99_latency_s": float(np.percentile(lat, 99)) if len(lat) else None,
+            "makespan_s": wall,
+            "updates": upd,
+            "updates_per_ns": upd / (wall * 1e9),
+        }
+        results.sort(key=lambda r: r.job.id)
+        return results, stats
+
+
+def run_alone(job: Job) -> tuple[np.ndarray, np.ndarray]:
+    """The same job on its own lattice, outside the server."""
+    lat = Lattice(dim=job.dim, L=job.L, n_samples=job.samples, n_replicas=1, seed=job.seed, layout="bits64",
+                  series_capacity=1)
+    lat.sweep(job.algo, 1.0 / job.T, job.sweeps)
+    E, M, _ = lat.measure(overlap=False)
+    lat.close()
+    return E[:, 0, 0], M[:, 0, 0]
+
+
+def calibrated_rate(server: Server, jobs: list[Job], load: float = 0.8) -> float:
+    """Arrival rate (jobs/s) at `load` times the capacity measured on a
+    saturated run of the given jobs."""
+    _, st = server.run(jobs, realtime=False)
+    return load * len(jobs) / st["makespan_s"] if st["makespan_s"] > 0 else math.inf

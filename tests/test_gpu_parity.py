@@ -22,6 +22,8 @@ def _pair(ianus, model="ea", dim=3, L=4, S=1, R=1, K=1, seed=SEED, layout="auto"
     variant = 0
     if layout == "bits64-planes":  # bit-sliced kernel with per-lane threshold planes
         layout, variant = "bits64", 1
+    elif layout == "bits64-jit":  # kernel specialised at run time for the thresholds
+        layout, variant = "bits64", 2
     lat = ianus.Lattice(model=model, dim=dim, L=L, n_samples=S, n_replicas=R, n_temps=K, seed=seed,
                         layout=layout, ferro=ferro, series_capacity=4096)
     if variant:
@@ -51,7 +53,7 @@ CASES = [(3, 2, 1, 1), (3, 4, 3, 2), (2, 4, 65, 1), (3, 6, 70, 2), (2, 8, 2, 2),
          (3, 10, 3, 2), (2, 12, 67, 1)]
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-planes"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit"])
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
 @pytest.mark.parametrize("dim,L,S,R", CASES)
 def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
@@ -68,7 +70,7 @@ def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
         assert np.array_equal(Q, Qo)
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-planes"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit"])
 def test_series_matches_oracle(ianus, layout):
     lat, orc, _ = _pair(ianus, dim=3, L=6, S=67, R=2, layout=layout)
     lat.sweep(HEATBATH, 1.0, 23, measure_every=5)
@@ -83,7 +85,7 @@ def test_series_matches_oracle(ianus, layout):
 def test_extreme_temperatures(ianus, beta):
     """beta = 0 (T_H = 2^31 everywhere, Metropolis always flips) and a
     beta so large that T_M = 0 and T_H reaches 2^32."""
-    for layout in ("i8", "bits64", "bits64-planes"):
+    for layout in ("i8", "bits64", "bits64-jit"):
         for algo in (METROPOLIS, HEATBATH):
             lat, orc, _ = _pair(ianus, dim=3, L=4, S=66, R=1, layout=layout)
             lat.sweep(algo, beta, 3)
