@@ -10,10 +10,9 @@
 // k_msc.cu).  With thresholds fixed at compile time, the threshold bit of
 // plane p for a lane of class u = (u2 u1 u0) is bit u of an 8-bit truth
 // table, which is exactly one lop3 with that table as immediate per 32 bits,
-// instead of seven AND-ORs with per-class masks.  Plane pairs 0..7 are
-// unrolled with their tables as immediates; the rare pairs 8..15 (a word is
-// still undecided after 16 planes with probability < 64 * 2^-16) use the
-// per-class masks and the tables from shared memory.
+// instead of seven AND-ORs with per-class masks.  Plane pairs 0..3 use their
+// tables as immediates; the rarer later pairs use per-class masks and the
+// tables from shared memory.
 #include "common.cuh"
 
 namespace ianus {
@@ -27,7 +26,7 @@ constexpr uint32_t kLut[32] = {IANUS_JIT_LUTS};
 constexpr uint32_t kAlways = IANUS_JIT_ALWAYS;
 constexpr uint32_t kNeed = IANUS_JIT_NEED;
 constexpr int kBlock = 256;
-constexpr int kUnrolled = 8;
+constexpr int kUnrolled = 3;  // pairs run in lockstep before queueing
 
 template <uint32_t LUT>
 __device__ __forceinline__ uint64_t lop3c(uint64_t a, uint64_t b, uint64_t c) {
@@ -69,25 +68,132 @@ __device__ __forceinline__ void pairs(Word& w, const BitsParams& p, uint32_t sit
   }
 }
 
-// Pairs kUnrolled..15 with runtime tables (lut from shared memory).
-__device__ __noinline__ void tail(Word& w, const BitsParams& p, uint32_t site, uint32_t c2, const uint8_t* lut) {
+// ---- compaction of the lazy plane loop ----
+//
+// A warp's 32 words need different numbers of plane pairs (a 64-lane word is
+// decided after ~3.9 pairs on average, the slowest of 32 words after ~6.4).
+// Pairs 0..2 run in lockstep (almost every word needs them); words still
+// undecided go to a per-warp queue in shared memory and pair 3 runs on 32
+// queued words at a time; words undecided after that go to a second queue
+// and advance one pair per round with run-time tables.  Every word is
+// written exactly once, by whichever lane finishes it; only colour-c words
+// are written during a colour-c pass, so the order does not matter.
+
+constexpr int kPhaseA = 3;
+constexpr int kWarps = kBlock / 32;
+constexpr uint32_t kQ = 64;  // queue capacity: < 32 left + <= 32 pushed
+
+struct Queue {
+  uint64_t u0[kQ], u1[kQ], u2[kQ], und[kQ], lt[kQ];
+  uint32_t self[kQ], site[kQ], tag[kQ];  // tag = replica | next pair << 1
+};
+
+struct Ctx {
+  const BitsParams* p;
+  int g, tslot;
+  const uint8_t* lut;  // shared-memory copy of the 32 tables
+};
+
+__device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
+  const uint32_t sigma = (uint32_t)(c.tslot * R) + a;
+  return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
+}
+
+__device__ __forceinline__ void finish(const Ctx& c, uint32_t self, uint32_t a, const Word& w) {
+  const BitsParams& p = *c.p;
+  uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R) + a) * p.geom.N;
+  const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
+  if (flip) sp[self] ^= flip;
+}
+
+__device__ __forceinline__ void put(Queue& q, uint32_t i, const Word& w, uint32_t self, uint32_t site, uint32_t tag) {
+  q.u0[i] = w.u0;
+  q.u1[i] = w.u1;
+  q.u2[i] = w.u2;
+  q.und[i] = w.und;
+  q.lt[i] = w.lt;
+  q.self[i] = self;
+  q.site[i] = site;
+  q.tag[i] = tag;
+}
+
+__device__ __forceinline__ void get(const Queue& q, uint32_t i, Word& w, uint32_t& self, uint32_t& site,
+                                    uint32_t& tag) {
+  w.u0 = q.u0[i];
+  w.u1 = q.u1[i];
+  w.u2 = q.u2[i];
+  w.und = q.und[i];
+  w.lt = q.lt[i];
+  self = q.self[i];
+  site = q.site[i];
+  tag = q.tag[i];
+}
+
+// Warp-wide append of the lanes with pred set; n is warp-uniform.
+__device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Word& w, uint32_t self, uint32_t site,
+                                     uint32_t tag) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t m = __ballot_sync(0xffffffffu, pred);
+  if (pred) put(q, n + __popc(m & ((1u << lane) - 1u)), w, self, site, tag);
+  n += __popc(m);
+  __syncwarp();
+}
+
+// One plane pair with run-time tables (per-lane pair index mm).
+__device__ __forceinline__ void pair_rt(Word& w, const Ctx& c, uint32_t site, uint32_t c2, uint32_t mm) {
+  const BitsParams& p = *c.p;
+  const uint4 x = philox10(site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
   uint64_t m[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
     m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
-  for (uint32_t mm = kUnrolled; mm < 16u && w.und != 0ull; ++mm) {
-    const uint4 x = philox10(site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
 #pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32)) : ((uint64_t)x.z | ((uint64_t)x.w << 32));
-      const uint32_t tab = lut[2u * mm + (uint32_t)q];
-      uint64_t tb = 0;
+  for (int q = 0; q < 2; ++q) {
+    const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32)) : ((uint64_t)x.z | ((uint64_t)x.w << 32));
+    const uint32_t tab = c.lut[2u * mm + (uint32_t)q];
+    uint64_t tb = 0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) tb |= m[u] & (0ull - (uint64_t)((tab >> u) & 1u));
-      w.lt |= w.und & tb & ~r;
-      w.und &= ~(r ^ tb);
-    }
+    for (int u = 0; u < 8; ++u) tb |= m[u] & (0ull - (uint64_t)((tab >> u) & 1u));
+    w.lt |= w.und & tb & ~r;
+    w.und &= ~(r ^ tb);
   }
+}
+
+// Pair kPhaseA for up to 32 queued words (the top `take` entries of q3).
+__device__ __forceinline__ void round3(Queue& q3, Queue& q4, uint32_t& n3, uint32_t& n4, uint32_t take,
+                                       const Ctx& c) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool has = lane < take;
+  Word w;
+  uint32_t self = 0, site = 0, tag = 0;
+  w.und = 0;
+  if (has) get(q3, n3 - take + lane, w, self, site, tag);
+  __syncwarp();
+  n3 -= take;
+  if (has) pair<kPhaseA>(w, *c.p, site, sigma_c2(c, tag & 1u));
+  const bool pend = has && w.und != 0ull;
+  push(q4, n4, pend, w, self, site, (tag & 1u) | ((uint32_t)(kPhaseA + 1) << 1));
+  if (has && !pend) finish(c, self, tag & 1u, w);
+}
+
+// One more pair (run-time tables) for up to 32 words of q4.
+__device__ __forceinline__ void round4(Queue& q4, uint32_t& n4, uint32_t take, const Ctx& c) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const bool has = lane < take;
+  Word w;
+  uint32_t self = 0, site = 0, tag = 0;
+  w.und = 0;
+  if (has) get(q4, n4 - take + lane, w, self, site, tag);
+  __syncwarp();
+  n4 -= take;
+  uint32_t mm = tag >> 1;
+  if (has) {
+    pair_rt(w, c, site, sigma_c2(c, tag & 1u), mm);
+    ++mm;
+  }
+  const bool pend = has && w.und != 0ull && mm < 16u;
+  push(q4, n4, pend, w, self, site, (tag & 1u) | (mm << 1));
+  if (has && !pend) finish(c, self, tag & 1u, w);
 }
 
 }  // namespace jit
@@ -97,50 +203,83 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock)
     ianus_jit_sweep(const ianus::BitsParams p, const uint8_t* __restrict__ lut_t) {
   using namespace ianus;
   using namespace ianus::jit;
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  Queue* queues = reinterpret_cast<Queue*>(dyn_smem);  // [kWarps][2]
   __shared__ uint8_t s_lut[32];
   if (threadIdx.x < 32) s_lut[threadIdx.x] = lut_t[threadIdx.x];
   __syncthreads();
+  const uint32_t warp = threadIdx.x >> 5;
+  Queue& q3 = queues[2 * warp];
+  Queue& q4 = queues[2 * warp + 1];
+  uint32_t n3 = 0, n4 = 0;
+  Ctx c;
+  c.p = &p;
   const int gt = blockIdx.y;  // g * K + tslot
-  const int g = gt / p.K, tslot = gt - g * p.K;
+  c.g = gt / p.K;
+  c.tslot = gt - c.g * p.K;
+  c.lut = s_lut;
   const Geom geom = p.geom;
   const uint32_t N = geom.N;
-  const uint64_t* Jg = p.J + (uint64_t)g * D * N;
+  const uint64_t* Jg = p.J + (uint64_t)c.g * D * N;
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
-  for (uint32_t wi = w_begin + threadIdx.x; wi < w_end; wi += kBlock) {
-    const Nbr n = split_neighbours_t<P2>(geom, p.colour, wi);
+  for (uint32_t base = w_begin; base < w_end; base += kBlock) {  // uniform across the block
+    const uint32_t wi = base + threadIdx.x;
+    const bool valid = wi < w_end;
+    Nbr n;
     uint64_t jw[2 * D];
-    jw[0] = __ldg(Jg + n.self);
-    jw[1] = __ldg(Jg + n.xm);
-    jw[2] = __ldg(Jg + N + n.self);
-    jw[3] = __ldg(Jg + N + n.ym);
-    if (D == 3) {
-      jw[4] = __ldg(Jg + 2u * N + n.self);
-      jw[5] = __ldg(Jg + 2u * N + n.zm);
+    if (valid) {
+      n = split_neighbours_t<P2>(geom, p.colour, wi);
+      jw[0] = __ldg(Jg + n.self);
+      jw[1] = __ldg(Jg + n.xm);
+      jw[2] = __ldg(Jg + N + n.self);
+      jw[3] = __ldg(Jg + N + n.ym);
+      if (D == 3) {
+        jw[4] = __ldg(Jg + 2u * N + n.self);
+        jw[5] = __ldg(Jg + 2u * N + n.zm);
+      }
     }
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-      const int sigma = tslot * R + a;
-      uint64_t* sp = p.spins + ((uint64_t)g * p.slots + sigma) * N;
-      const uint64_t b = sp[n.self];
-      uint64_t e[2 * D];
-      e[0] = b ^ sp[n.xp] ^ jw[0];
-      e[1] = b ^ sp[n.xm] ^ jw[1];
-      e[2] = b ^ sp[n.yp] ^ jw[2];
-      e[3] = b ^ sp[n.ym] ^ jw[3];
-      if (D == 3) {
-        e[4] = b ^ sp[n.zp] ^ jw[4];
-        e[5] = b ^ sp[n.zm] ^ jw[5];
-      }
       Word w;
-      count_unsat<D>(e, w.u0, w.u1, w.u2);
-      w.lt = kAlways ? lop3c<kAlways>(w.u2, w.u1, w.u0) : 0ull;
-      w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
-      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
-      pairs<0>(w, p, n.site, c2);
-      if (w.und != 0ull) tail(w, p, n.site, c2, s_lut);
-      const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
-      if (flip) sp[n.self] = b ^ flip;
+      w.und = 0;
+      w.lt = 0;
+      w.u0 = w.u1 = w.u2 = 0;
+      uint32_t c2 = 0;
+      if (valid) {
+        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t b = sp[n.self];
+        uint64_t e[2 * D];
+        e[0] = b ^ sp[n.xp] ^ jw[0];
+        e[1] = b ^ sp[n.xm] ^ jw[1];
+        e[2] = b ^ sp[n.yp] ^ jw[2];
+        e[3] = b ^ sp[n.ym] ^ jw[3];
+        if (D == 3) {
+          e[4] = b ^ sp[n.zp] ^ jw[4];
+          e[5] = b ^ sp[n.zm] ^ jw[5];
+        }
+        count_unsat<D>(e, w.u0, w.u1, w.u2);
+        w.lt = kAlways ? lop3c<kAlways>(w.u2, w.u1, w.u0) : 0ull;
+        w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
+        c2 = sigma_c2(c, (uint32_t)a);
+        pairs<0>(w, p, n.site, c2);
+      }
+      const bool pend = valid && w.und != 0ull;
+      push(q3, n3, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, (uint32_t)a | ((uint32_t)kPhaseA << 1));
+      if (valid && !pend) finish(c, n.self, (uint32_t)a, w);
+      while (n3 >= 32u) round3(q3, q4, n3, n4, 32u, c);
+      while (n4 >= 32u) round4(q4, n4, 32u, c);
     }
+  }
+  // Drain with partial warps.  round3 pushes at most 32 entries into q4, so
+  // it only runs while q4 holds fewer than 32 (q4 never exceeds 63 < kQ);
+  // every round4 advances its entries' pair index, which stops at 16.
+  while (n3 > 0u || n4 > 0u) {
+    if (n4 >= 32u)
+      round4(q4, n4, 32u, c);
+    else if (n3 > 0u)
+      round3(q3, q4, n3, n4, n3 < 32u ? n3 : 32u, c);
+    else
+      round4(q4, n4, n4, c);
   }
 }

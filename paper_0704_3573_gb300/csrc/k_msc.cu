@@ -513,7 +513,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   if (want_jit && lat.jit) {
     const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
     void* args[] = {(void*)&p, (void*)&lut_t};
-    return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, 0, lat.stream);
+    return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, kJitSmemBytes, lat.stream);
   }
   if (lat.D == 3)
     return algo ? sweep_dispatch2<3, 1>(lat, p, grid, smem) : sweep_dispatch2<3, 0>(lat, p, grid, smem);
