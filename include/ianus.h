@@ -273,13 +273,21 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * differs).  With one temperature the thresholds are the same in every lane
  * and the sweep kernel can be specialised for them at run time (NVRTC, a
  * fraction of a second per new table set, cached per device).
- *   0 = automatic: specialise lattices of >= 2^20 site words, else use the
- *       precompiled kernel with per-lane threshold bit-planes;
+ *   0 = automatic: the specialised lockstep kernel for lattices of >= 2^20
+ *       site words, else the precompiled kernel with per-lane threshold
+ *       bit-planes;
  *   1 = always the precompiled per-lane kernel;
- *   2 = specialise whenever n_temps == 1.
+ *   2..7 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
+ *       blocks per SM; 4..7 = per-warp queues entered after 3 or 4 plane
+ *       pairs, 3 or 4 blocks per SM (4: 3/3, 5: 4/3, 6: 3/4, 7: 4/4).
  * If run-time compilation is unavailable, the precompiled kernel runs.
  * EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
+
+/* Launch shape of the bit-sliced sweep: colour words handled by one block of
+ * 256 threads (rounded up to a multiple of 256); 0 restores the default,
+ * which sizes the grid to about 8 blocks per SM.  EINVAL above 2^24. */
+ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
 
 /* Frees what the lattice allocated.  NULL is accepted.  The caller-owned
  * device buffer, if any, is not freed. */

@@ -37,7 +37,7 @@ EXPORTS = [
     "ianus_measure", "ianus_read_series", "ianus_get_spins_i8", "ianus_set_spins_i8", "ianus_get_couplings_i8",
     "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
-    "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant",
+    "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
 ]
 
 
@@ -109,6 +109,7 @@ def lib(build_if_missing: bool = True):
         "ianus_table_pt": (sz, [C.c_double, C.c_double, vp, sz]),
         "ianus_measure_bits64_noalloc": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp]),
         "ianus_set_variant": (i32, [vp, i32]),
+        "ianus_set_block_words": (i32, [vp, u32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -303,8 +304,13 @@ class Lattice:
         _check(self._lib.ianus_set_state(self._h, _ptr(buf), buf.size), "ianus_set_state")
 
     def set_variant(self, variant: int):
-        """0 = automatic kernel choice, 1 = per-lane threshold planes (tests)."""
+        """Bit-sliced sweep kernel: 0 automatic, 1 per-lane threshold planes,
+        2..7 shapes of the kernel specialised at run time (include/ianus.h)."""
         _check(self._lib.ianus_set_variant(self._h, variant), "ianus_set_variant")
+
+    def set_block_words(self, words: int):
+        """Colour words per 256-thread block of the bit-sliced sweep (0 = default)."""
+        _check(self._lib.ianus_set_block_words(self._h, words), "ianus_set_block_words")
 
     def synchronize(self):
         _check(self._lib.ianus_synchronize(self._h), "ianus_synchronize")

@@ -319,6 +319,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->keys = make_keys(cfg->seed);
   lat->algo = -1;
   lat->jit_algo = -1;
+  lat->jit_variant = -1;
+  lat->jit_variant = -1;
   lat->bytes = z.total;
   if (cfg->device_buffer) {
     if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {
@@ -658,8 +660,15 @@ ianus_status ianus_synchronize(ianus_lattice* h) {
 
 ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   GET_LAT(h);
-  if (variant < 0 || variant > 2) return IANUS_EINVAL;
+  if (variant < 0 || variant > 7) return IANUS_EINVAL;
   lat->variant = variant;
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_block_words(ianus_lattice* h, uint32_t words_per_block) {
+  GET_LAT(h);
+  if (words_per_block > (1u << 24)) return IANUS_EINVAL;
+  lat->block_words = words_per_block;
   return IANUS_OK;
 }
 

@@ -26,7 +26,13 @@ constexpr uint32_t kLut[32] = {IANUS_JIT_LUTS};
 constexpr uint32_t kAlways = IANUS_JIT_ALWAYS;
 constexpr uint32_t kNeed = IANUS_JIT_NEED;
 constexpr int kBlock = 256;
-constexpr int kUnrolled = 3;  // pairs run in lockstep before queueing
+// IANUS_JIT_MODE 0: all plane pairs in lockstep across the warp (pairs
+// 0..7 with immediate tables, then run-time tables); 1: pairs 0..PHASEA-1 in
+// lockstep, then per-warp queues (below).  IANUS_JIT_MINB: blocks per SM the
+// register allocation must allow.
+constexpr int kMode = IANUS_JIT_MODE;
+constexpr int kPhaseA = IANUS_JIT_PHASEA;
+constexpr int kUnrolled = kMode == 0 ? 8 : kPhaseA;
 
 template <uint32_t LUT>
 __device__ __forceinline__ uint64_t lop3c(uint64_t a, uint64_t b, uint64_t c) {
@@ -79,7 +85,6 @@ __device__ __forceinline__ void pairs(Word& w, const BitsParams& p, uint32_t sit
 // written exactly once, by whichever lane finishes it; only colour-c words
 // are written during a colour-c pass, so the order does not matter.
 
-constexpr int kPhaseA = 3;
 constexpr int kWarps = kBlock / 32;
 constexpr uint32_t kQ = 64;  // queue capacity: < 32 left + <= 32 pushed
 
@@ -137,6 +142,28 @@ __device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Wor
   if (pred) put(q, n + __popc(m & ((1u << lane) - 1u)), w, self, site, tag);
   n += __popc(m);
   __syncwarp();
+}
+
+// Mode 0: the remaining pairs kUnrolled..15 of one word, run-time tables.
+__device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, uint32_t site, uint32_t c2,
+                                           const uint8_t* lut) {
+  uint64_t m[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u)
+    m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
+  for (uint32_t mm = kUnrolled; mm < 16u && w.und != 0ull; ++mm) {
+    const uint4 x = philox10(site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32)) : ((uint64_t)x.z | ((uint64_t)x.w << 32));
+      const uint32_t tab = lut[2u * mm + (uint32_t)q];
+      uint64_t tb = 0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) tb |= m[u] & (0ull - (uint64_t)((tab >> u) & 1u));
+      w.lt |= w.und & tb & ~r;
+      w.und &= ~(r ^ tb);
+    }
+  }
 }
 
 // One plane pair with run-time tables (per-lane pair index mm).
@@ -199,7 +226,7 @@ __device__ __forceinline__ void round4(Queue& q4, uint32_t& n4, uint32_t take, c
 }  // namespace jit
 }  // namespace ianus
 
-extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock)
+extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
     ianus_jit_sweep(const ianus::BitsParams p, const uint8_t* __restrict__ lut_t) {
   using namespace ianus;
   using namespace ianus::jit;
@@ -263,7 +290,12 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock)
         w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
         c2 = sigma_c2(c, (uint32_t)a);
         pairs<0>(w, p, n.site, c2);
+        if (kMode == 0) {
+          if (w.und != 0ull) tail_lockstep(w, p, n.site, c2, s_lut);
+          finish(c, n.self, (uint32_t)a, w);
+        }
       }
+      if (kMode == 0) continue;
       const bool pend = valid && w.und != 0ull;
       push(q3, n3, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, (uint32_t)a | ((uint32_t)kPhaseA << 1));
       if (valid && !pend) finish(c, n.self, (uint32_t)a, w);
@@ -271,6 +303,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock)
       while (n4 >= 32u) round4(q4, n4, 32u, c);
     }
   }
+  if (kMode == 0) return;
   // Drain with partial warps.  round3 pushes at most 32 entries into q4, so
   // it only runs while q4 holds fewer than 32 (q4 never exceeds 63 < kQ);
   // every round4 advances its entries' pair index, which stops at 16.

@@ -461,6 +461,16 @@ cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t
                          : sweep_dispatch<D, ALGO, false>(lat, p, grid, smem);
 }
 
+// Shapes of the run-time specialised sweep (variants 2..): lockstep plane
+// loop or per-warp queues entered after phase_a pairs; registers capped so
+// that min_blocks blocks of 256 threads fit on an SM.
+struct JitShape {
+  int mode, phase_a, min_blocks;
+};
+constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 3, 3}, {1, 4, 3}, {1, 3, 4}, {1, 4, 4}};
+constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
+constexpr int kAutoJitVariant = 2;
+
 }  // namespace
 
 cudaError_t launch_init_bits(Lattice& lat, int ferro) {
@@ -493,7 +503,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   const uint32_t half = lat.geom.half;
   const uint32_t gts = (uint32_t)(lat.G * lat.K);
   uint32_t target_blocks = (152u * 8u + gts - 1) / gts;
-  uint32_t wpb = (half + target_blocks - 1) / target_blocks;
+  uint32_t wpb = lat.block_words ? lat.block_words : (half + target_blocks - 1) / target_blocks;
   wpb = ((wpb + kBlock - 1) / kBlock) * kBlock;
   if (wpb < (uint32_t)kBlock) wpb = kBlock;
   p.words_per_block = wpb;
@@ -501,19 +511,27 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
   // Lane-uniform thresholds (one temperature): the kernel specialised for
-  // them at run time.  Variant 0 specialises lattices of at least 2^20 site
-  // words (a compile costs a fraction of a second), variant 2 always,
-  // variant 1 never.
+  // them at run time.  Variants (ianus_set_variant): 0 = automatic (the
+  // specialised kernel for lattices of >= 2^20 site words, else the per-lane
+  // planes), 1 = per-lane planes, 2.. = a specialised kernel shape from
+  // kJitShapes.  A compile costs a fraction of a second and is cached.
   const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
-  const bool want_jit = lat.K == 1 && lat.ulut_ok && (lat.variant == 2 || (lat.variant == 0 && words >= (1ull << 20)));
-  if (want_jit && lat.jit_algo != algo) {
-    lat.jit = jit_kernel(lat, algo);
-    lat.jit_algo = algo;
-  }
-  if (want_jit && lat.jit) {
-    const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
-    void* args[] = {(void*)&p, (void*)&lut_t};
-    return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, kJitSmemBytes, lat.stream);
+  int v = lat.variant;
+  if (v == 0) v = words >= (1ull << 20) ? kAutoJitVariant : 1;
+  const bool want_jit = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
+  if (want_jit) {
+    const JitShape& js = kJitShapes[v - 2];
+    if (lat.jit_algo != algo || lat.jit_variant != v) {
+      lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks);
+      lat.jit_algo = algo;
+      lat.jit_variant = v;
+    }
+    if (lat.jit) {
+      const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
+      void* args[] = {(void*)&p, (void*)&lut_t};
+      return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, js.mode == 1 ? kJitSmemBytes : 0,
+                              lat.stream);
+    }
   }
   if (lat.D == 3)
     return algo ? sweep_dispatch2<3, 1>(lat, p, grid, smem) : sweep_dispatch2<3, 0>(lat, p, grid, smem);

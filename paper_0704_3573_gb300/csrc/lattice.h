@@ -78,6 +78,8 @@ struct Lattice {
   bool ulut_ok;
   cudaKernel_t jit;          // sweep kernel specialised for ulut (null: use the per-lane planes)
   int jit_algo;              // algorithm the specialisation was requested for; -1 = not yet
+  int jit_variant;           // variant it was built for
+  uint32_t block_words;      // words per block of the bit-sliced sweep; 0 = heuristic
 };
 
 // ---- host table builders (tables.cpp) ----
@@ -94,7 +96,7 @@ void class_thresholds(int dim, int algo, double beta, uint64_t* thr /*[kMaxClass
 // shared memory: two per-warp queues of 64 entries (5 x 8 + 3 x 4 bytes) for
 // each of its 8 warps.
 constexpr size_t kJitSmemBytes = 8 * 2 * 64 * (5 * 8 + 3 * 4);
-cudaKernel_t jit_kernel(const Lattice& lat, int algo);
+cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks);
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)

@@ -24,6 +24,8 @@ def _pair(ianus, model="ea", dim=3, L=4, S=1, R=1, K=1, seed=SEED, layout="auto"
         layout, variant = "bits64", 1
     elif layout == "bits64-jit":  # kernel specialised at run time for the thresholds
         layout, variant = "bits64", 2
+    elif layout == "bits64-queues":  # specialised kernel with per-warp queues
+        layout, variant = "bits64", 6
     lat = ianus.Lattice(model=model, dim=dim, L=L, n_samples=S, n_replicas=R, n_temps=K, seed=seed,
                         layout=layout, ferro=ferro, series_capacity=4096)
     if variant:
@@ -53,7 +55,7 @@ CASES = [(3, 2, 1, 1), (3, 4, 3, 2), (2, 4, 65, 1), (3, 6, 70, 2), (2, 8, 2, 2),
          (3, 10, 3, 2), (2, 12, 67, 1)]
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit", "bits64-queues"])
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
 @pytest.mark.parametrize("dim,L,S,R", CASES)
 def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
@@ -70,7 +72,7 @@ def test_sweep_bit_exact_every_sweep(ianus, layout, algo, dim, L, S, R):
         assert np.array_equal(Q, Qo)
 
 
-@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit"])
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit", "bits64-queues"])
 def test_series_matches_oracle(ianus, layout):
     lat, orc, _ = _pair(ianus, dim=3, L=6, S=67, R=2, layout=layout)
     lat.sweep(HEATBATH, 1.0, 23, measure_every=5)
@@ -85,7 +87,7 @@ def test_series_matches_oracle(ianus, layout):
 def test_extreme_temperatures(ianus, beta):
     """beta = 0 (T_H = 2^31 everywhere, Metropolis always flips) and a
     beta so large that T_M = 0 and T_H reaches 2^32."""
-    for layout in ("i8", "bits64", "bits64-jit"):
+    for layout in ("i8", "bits64", "bits64-jit", "bits64-queues"):
         for algo in (METROPOLIS, HEATBATH):
             lat, orc, _ = _pair(ianus, dim=3, L=4, S=66, R=1, layout=layout)
             lat.sweep(algo, beta, 3)
@@ -282,3 +284,41 @@ def test_cfg3_full_size_sampled(ianus):
     _, E, M, Q = lat.series()
     _, Eo, Mo, Qo = orc.series()
     assert np.array_equal(E[:, ids], Eo) and np.array_equal(M[:, ids], Mo) and np.array_equal(Q[:, ids], Qo)
+
+
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
+def test_every_variant_and_launch_shape_is_bit_exact(ianus, variant):
+    """All kernel variants and several launch shapes give the same
+    trajectory (L=16: several blocks per (group, slot), ragged last block)."""
+    ref = None
+    for bw in (0, 256, 768):
+        lat = ianus.Lattice(dim=3, L=16, n_samples=100, n_replicas=2, seed=SEED + 77, layout="bits64")
+        lat.set_variant(variant)
+        lat.set_block_words(bw)
+        lat.sweep(HEATBATH, 0.9, 3)
+        lat.sweep(METROPOLIS, 1.1, 3)
+        sp = lat.spins()
+        if ref is None:
+            orc = Oracle(dim=3, L=16, sample_ids=list(range(100)), n_replicas=2, seed=SEED + 77)
+            orc.sweep(HEATBATH, 0.9, 3, nthreads=8)
+            orc.sweep(METROPOLIS, 1.1, 3, nthreads=8)
+            ref = orc.spins()
+        assert np.array_equal(sp, ref), (variant, bw)
+
+
+def test_autotuner_does_not_change_the_trajectory(ianus, tmp_path, monkeypatch):
+    from paper_0704_3573_gb300 import tune
+
+    monkeypatch.setenv("IANUS_TUNE_CACHE", str(tmp_path / "tune.json"))
+    a = ianus.Lattice(dim=3, L=16, n_samples=128, n_replicas=2, seed=SEED + 78, layout="bits64")
+    b = ianus.Lattice(dim=3, L=16, n_samples=128, n_replicas=2, seed=SEED + 78, layout="bits64")
+    a.sweep(HEATBATH, 1.0, 4)
+    b.sweep(HEATBATH, 1.0, 4)
+    best = tune.tune(a, HEATBATH, 1.0, sweeps=4, block_words=(0, 512))
+    assert best["variant"] in tune.VARIANTS and not best["cached"]
+    assert a.sweeps == 4
+    a.sweep(HEATBATH, 1.0, 5)
+    b.sweep(HEATBATH, 1.0, 5)
+    assert np.array_equal(a.spins(), b.spins())
+    again = tune.tune(a, HEATBATH, 1.0)
+    assert again["cached"] and again["variant"] == best["variant"]
