@@ -289,6 +289,14 @@ ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
  * which sizes the grid to about 8 blocks per SM.  EINVAL above 2^24. */
 ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
 
+/* Sweep blocks through CUDA graphs (default on): runs of at least 4 sweeps
+ * between measurements are replayed from graphs of up to 64 sweeps, captured
+ * on a private stream the first time each block length occurs and dropped
+ * when the tables, the variant or the launch shape change.  Captured kernels
+ * read the sweep index from a device counter, so results are identical with
+ * and without graphs.  enable = 0 launches every kernel directly. */
+ianus_status ianus_set_graphs(ianus_lattice* lat, int32_t enable);
+
 /* Frees what the lattice allocated.  NULL is accepted.  The caller-owned
  * device buffer, if any, is not freed. */
 ianus_status ianus_destroy(ianus_lattice* lat);

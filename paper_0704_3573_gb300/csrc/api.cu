@@ -23,7 +23,7 @@ struct Sizes {
   int model, D, L, S, R, K, slots, layout, G, Q4, mq;
   uint32_t N, cap, pt_cap;
   size_t off_spins, off_J, off_thr, off_tp, off_ptab, off_pttab, off_ptsign, off_slot, off_temp, off_acc_pt,
-      off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, total;
+      off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
   size_t spins_bytes, J_bytes;
 };
 
@@ -98,6 +98,7 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_sM = take((size_t)z.cap * SKR * z.mq * 8);
   z.off_sQ = take((size_t)z.cap * z.S * z.K * 8);
   z.off_err = take(8);
+  z.off_tdev = take(8);
   z.total = o;
   return IANUS_OK;
 }
@@ -120,6 +121,8 @@ Fail fail(Lattice* lat, int st) {
     cudaError_t e_ = (expr);                         \
     if (e_ != cudaSuccess) return fail(lat, IANUS_ECUDA); \
   } while (0)
+
+void drop_graphs(Lattice* lat);
 
 bool beta_ok(const double* beta, int K) {
   for (int k = 0; k < K; ++k)
@@ -210,6 +213,7 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
   lat->beta.assign(beta, beta + K);
   lat->algo = algo;
   lat->tables_ok = true;
+  drop_graphs(lat);  // captured kernels depend on the tables and the algorithm
   return IANUS_OK;
 }
 
@@ -262,6 +266,77 @@ int do_pt_swap(Lattice* lat) {
   CK(launch_pt_swap(*lat));
   lat->steps += 1;
   if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
+  return IANUS_OK;
+}
+
+// ---- CUDA graphs of sweep blocks ----
+
+void drop_graphs(Lattice* lat) {
+  if (!lat->graphs) return;
+  for (auto& kv : *lat->graphs) cudaGraphExecDestroy(kv.second);
+  lat->graphs->clear();
+}
+
+// Captures B sweeps (2B colour kernels reading the device sweep counter at
+// offsets 0..B-1) and the counter advance on a private stream.
+int build_graph(Lattice* lat, int inv, uint32_t B, cudaGraphExec_t* out) {
+  if (lat->layout == IANUS_LAYOUT_BITS64) prepare_sweep_bits(*lat, inv);  // compile before capturing
+  if (!lat->cap_stream) CK(cudaStreamCreateWithFlags(&lat->cap_stream, cudaStreamNonBlocking));
+  cudaStream_t user = lat->stream;
+  lat->stream = lat->cap_stream;
+  lat->capturing = true;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(lat->cap_stream, cudaStreamCaptureModeThreadLocal);
+  for (uint32_t s = 0; e == cudaSuccess && s < B; ++s)
+    for (int c = 0; e == cudaSuccess && c < 2; ++c) {
+      if (lat->layout == IANUS_LAYOUT_I8)
+        e = launch_sweep_i8(*lat, c, s, inv);
+      else if (lat->layout == IANUS_LAYOUT_BITS64)
+        e = launch_sweep_bits(*lat, c, s, inv);
+      else
+        e = launch_sweep_potts(*lat, c, s);
+    }
+  if (e == cudaSuccess) e = launch_advance_tick(*lat, B);
+  cudaError_t e2 = cudaStreamEndCapture(lat->cap_stream, &g);
+  lat->stream = user;
+  lat->capturing = false;
+  if (e != cudaSuccess || e2 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return IANUS_ECUDA;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  return e == cudaSuccess ? IANUS_OK : fail(lat, IANUS_ECUDA);
+}
+
+// Runs n sweeps (no measurement inside) through cached graphs of blocks of
+// up to 64 sweeps; short runs (< 4 sweeps) launch eagerly.
+int sweeps_graphed(Lattice* lat, int inv, uint64_t n) {
+  while (n > 0) {
+    const uint32_t B = (uint32_t)std::min<uint64_t>(n, 64);
+    if (B < 4 || !lat->use_graphs || !lat->graphs) {
+      for (uint32_t s = 0; s < B; ++s) {
+        int st = one_sweep(lat, inv);
+        if (st) return st;
+      }
+      lat->t_dev_valid = false;
+      n -= B;
+      continue;
+    }
+    auto it = lat->graphs->find(B);
+    if (it == lat->graphs->end()) {
+      cudaGraphExec_t ex = nullptr;
+      int st = build_graph(lat, inv, B, &ex);
+      if (st) return st;
+      it = lat->graphs->emplace(B, ex).first;
+    }
+    if (!lat->t_dev_valid) CK(launch_set_tick(*lat, lat->sweeps));
+    CK(cudaGraphLaunch(it->second, lat->stream));
+    lat->sweeps += B;
+    lat->t_dev_valid = true;  // the graph advanced the counter by B
+    n -= B;
+  }
   return IANUS_OK;
 }
 
@@ -360,9 +435,13 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->ser_M = (int64_t*)(b + z.off_sM);
   lat->ser_Q = (int64_t*)(b + z.off_sQ);
   lat->err = (uint32_t*)(b + z.off_err);
+  lat->t_dev = (uint64_t*)(b + z.off_tdev);
+  lat->use_graphs = true;
+  lat->graphs = new (std::nothrow) std::map<uint32_t, cudaGraphExec_t>();
 
   auto bail = [&](int code) {
     if (lat->owns_buffer) cudaFree(lat->base);
+    delete lat->graphs;
     delete lat;
     return (ianus_status)code;
   };
@@ -405,9 +484,13 @@ ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uin
     if (st) return (ianus_status)st;
   }
   const int inv = algo == IANUS_HEATBATH;
-  for (uint64_t n = 0; n < nsweeps; ++n) {
-    int st = one_sweep(lat, inv);
+  uint64_t left = nsweeps;
+  while (left > 0) {
+    uint64_t chunk = left;  // sweeps up to the next measurement point
+    if (measure_every) chunk = std::min<uint64_t>(chunk, measure_every - lat->sweeps % measure_every);
+    int st = sweeps_graphed(lat, inv, chunk);
     if (st) return (ianus_status)st;
+    left -= chunk;
     if (measure_every && lat->sweeps % measure_every == 0) {
       st = record_row(lat);
       if (st) return (ianus_status)st;
@@ -638,6 +721,7 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   CK(cudaStreamSynchronize(lat->stream));
   lat->sweeps = hd.sweeps;
   lat->steps = hd.steps;
+  lat->t_dev_valid = false;
   lat->tables_ok = false;  // per-lane planes depend on the restored permutation
   return IANUS_OK;
 }
@@ -661,6 +745,7 @@ ianus_status ianus_synchronize(ianus_lattice* h) {
 ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   GET_LAT(h);
   if (variant < 0 || variant > 7) return IANUS_EINVAL;
+  if (lat->variant != variant) drop_graphs(lat);
   lat->variant = variant;
   return IANUS_OK;
 }
@@ -668,7 +753,14 @@ ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
 ianus_status ianus_set_block_words(ianus_lattice* h, uint32_t words_per_block) {
   GET_LAT(h);
   if (words_per_block > (1u << 24)) return IANUS_EINVAL;
+  if (lat->block_words != words_per_block) drop_graphs(lat);
   lat->block_words = words_per_block;
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_graphs(ianus_lattice* h, int32_t enable) {
+  GET_LAT(h);
+  lat->use_graphs = enable != 0;
   return IANUS_OK;
 }
 
@@ -676,6 +768,9 @@ ianus_status ianus_destroy(ianus_lattice* h) {
   Lattice* lat = reinterpret_cast<Lattice*>(h);
   if (!lat) return IANUS_OK;
   cudaStreamSynchronize(lat->stream);
+  drop_graphs(lat);
+  delete lat->graphs;
+  if (lat->cap_stream) cudaStreamDestroy(lat->cap_stream);
   if (lat->owns_buffer) cudaFree(lat->base);
   delete lat;
   return IANUS_OK;

@@ -145,7 +145,22 @@ struct BitsParams {
   uint32_t t_lo, t_hi;
   uint32_t words_per_block;  // colour-c words handled by one block (multiple of the block size)
   PhiloxKeys keys;
+  const uint64_t* t_dev;     // non-null in captured graphs: sweep = *t_dev + t_lo
 };
+
+// The absolute sweep index of a launch: the (t_hi, t_lo) parameters, or in a
+// captured graph the device-resident counter plus the offset in t_lo.
+struct Tick {
+  uint32_t lo, hi;
+};
+
+__device__ __forceinline__ Tick sweep_tick(uint32_t t_lo, uint32_t t_hi, const uint64_t* t_dev) {
+  if (t_dev) {
+    const uint64_t t = *t_dev + (uint64_t)t_lo;
+    return Tick{(uint32_t)t, (uint32_t)(t >> 32)};
+  }
+  return Tick{t_lo, t_hi};
+}
 
 // Number of unsatisfied bonds per lane as bit-planes (u2, u1, u0), from the
 // 2D unsatisfied-bond words e[]: a carry-save adder tree.

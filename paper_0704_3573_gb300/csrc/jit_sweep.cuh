@@ -52,8 +52,8 @@ struct Word {
 
 // One plane pair with compile-time tables: planes 2M and 2M+1.
 template <int M>
-__device__ __forceinline__ void pair(Word& w, const BitsParams& p, uint32_t site, uint32_t c2) {
-  const uint4 x = philox10(site, p.t_lo, c2 | ((uint32_t)M << 24), p.t_hi, p.keys);
+__device__ __forceinline__ void pair(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
+  const uint4 x = philox10(site, tk.lo, c2 | ((uint32_t)M << 24), tk.hi, p.keys);
   const uint64_t r0 = (uint64_t)x.x | ((uint64_t)x.y << 32);
   const uint64_t r1 = (uint64_t)x.z | ((uint64_t)x.w << 32);
   const uint64_t t0 = lop3c<kLut[2 * M]>(w.u2, w.u1, w.u0);
@@ -66,11 +66,11 @@ __device__ __forceinline__ void pair(Word& w, const BitsParams& p, uint32_t site
 }
 
 template <int M>
-__device__ __forceinline__ void pairs(Word& w, const BitsParams& p, uint32_t site, uint32_t c2) {
+__device__ __forceinline__ void pairs(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
   if constexpr (M < kUnrolled) {
     if (w.und == 0ull) return;
-    pair<M>(w, p, site, c2);
-    pairs<M + 1>(w, p, site, c2);
+    pair<M>(w, p, tk, site, c2);
+    pairs<M + 1>(w, p, tk, site, c2);
   }
 }
 
@@ -97,6 +97,7 @@ struct Ctx {
   const BitsParams* p;
   int g, tslot;
   const uint8_t* lut;  // shared-memory copy of the 32 tables
+  Tick tk;
 };
 
 __device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
@@ -145,14 +146,14 @@ __device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Wor
 }
 
 // Mode 0: the remaining pairs kUnrolled..15 of one word, run-time tables.
-__device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, uint32_t site, uint32_t c2,
-                                           const uint8_t* lut) {
+__device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, const Tick tk, uint32_t site,
+                                           uint32_t c2, const uint8_t* lut) {
   uint64_t m[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
     m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
   for (uint32_t mm = kUnrolled; mm < 16u && w.und != 0ull; ++mm) {
-    const uint4 x = philox10(site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+    const uint4 x = philox10(site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
       const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32)) : ((uint64_t)x.z | ((uint64_t)x.w << 32));
@@ -169,7 +170,7 @@ __device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, uint32_
 // One plane pair with run-time tables (per-lane pair index mm).
 __device__ __forceinline__ void pair_rt(Word& w, const Ctx& c, uint32_t site, uint32_t c2, uint32_t mm) {
   const BitsParams& p = *c.p;
-  const uint4 x = philox10(site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+  const uint4 x = philox10(site, c.tk.lo, c2 | (mm << 24), c.tk.hi, p.keys);
   uint64_t m[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
@@ -197,7 +198,7 @@ __device__ __forceinline__ void round3(Queue& q3, Queue& q4, uint32_t& n3, uint3
   if (has) get(q3, n3 - take + lane, w, self, site, tag);
   __syncwarp();
   n3 -= take;
-  if (has) pair<kPhaseA>(w, *c.p, site, sigma_c2(c, tag & 1u));
+  if (has) pair<kPhaseA>(w, *c.p, c.tk, site, sigma_c2(c, tag & 1u));
   const bool pend = has && w.und != 0ull;
   push(q4, n4, pend, w, self, site, (tag & 1u) | ((uint32_t)(kPhaseA + 1) << 1));
   if (has && !pend) finish(c, self, tag & 1u, w);
@@ -245,6 +246,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
   c.g = gt / p.K;
   c.tslot = gt - c.g * p.K;
   c.lut = s_lut;
+  c.tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const Geom geom = p.geom;
   const uint32_t N = geom.N;
   const uint64_t* Jg = p.J + (uint64_t)c.g * D * N;
@@ -289,9 +291,9 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
         w.lt = kAlways ? lop3c<kAlways>(w.u2, w.u1, w.u0) : 0ull;
         w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
         c2 = sigma_c2(c, (uint32_t)a);
-        pairs<0>(w, p, n.site, c2);
+        pairs<0>(w, p, c.tk, n.site, c2);
         if (kMode == 0) {
-          if (w.und != 0ull) tail_lockstep(w, p, n.site, c2, s_lut);
+          if (w.und != 0ull) tail_lockstep(w, p, c.tk, n.site, c2, s_lut);
           finish(c, n.self, (uint32_t)a, w);
         }
       }

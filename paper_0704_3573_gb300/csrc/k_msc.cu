@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
   const Geom geom = p.geom;
   const uint32_t N = geom.N;
   const uint64_t* Jg = p.J + (size_t)g * D * N;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
   for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
@@ -94,7 +95,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
       const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
 #pragma unroll 1
       for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
-        const uint4 x = philox10(n.site, p.t_lo, c2 | (mm << 24), p.t_hi, p.keys);
+        const uint4 x = philox10(n.site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
@@ -471,7 +472,29 @@ constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 3, 3}, {1, 4, 3}, {
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 constexpr int kAutoJitVariant = 2;
 
+// The specialised kernel shape the next sweep uses (>= 2), or 1 for the
+// precompiled per-lane kernel.
+int jit_variant_for(const Lattice& lat) {
+  const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
+  int v = lat.variant;
+  if (v == 0) v = words >= (1ull << 20) ? kAutoJitVariant : 1;
+  const bool ok = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
+  return ok ? v : 1;
+}
+
 }  // namespace
+
+void prepare_sweep_bits(Lattice& lat, int inv) {
+  const int algo = inv ? 1 : 0;
+  const int v = jit_variant_for(lat);
+  if (v < 2) return;
+  if (lat.jit_algo != algo || lat.jit_variant != v) {
+    const JitShape& js = kJitShapes[v - 2];
+    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks);
+    lat.jit_algo = algo;
+    lat.jit_variant = v;
+  }
+}
 
 cudaError_t launch_init_bits(Lattice& lat, int ferro) {
   k_init_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>((uint64_t*)lat.spins, (uint64_t*)lat.J,
@@ -499,6 +522,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   p.t_lo = (uint32_t)(t & 0xffffffffu);
   p.t_hi = (uint32_t)(t >> 32);
   p.keys = lat.keys;
+  p.t_dev = lat.capturing ? lat.t_dev : nullptr;
   // blocks per (group, temperature slot): enough to fill the GPU ~4 deep
   const uint32_t half = lat.geom.half;
   const uint32_t gts = (uint32_t)(lat.G * lat.K);
@@ -515,17 +539,10 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   // specialised kernel for lattices of >= 2^20 site words, else the per-lane
   // planes), 1 = per-lane planes, 2.. = a specialised kernel shape from
   // kJitShapes.  A compile costs a fraction of a second and is cached.
-  const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
-  int v = lat.variant;
-  if (v == 0) v = words >= (1ull << 20) ? kAutoJitVariant : 1;
-  const bool want_jit = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
-  if (want_jit) {
+  const int v = jit_variant_for(lat);
+  if (v >= 2) {
     const JitShape& js = kJitShapes[v - 2];
-    if (lat.jit_algo != algo || lat.jit_variant != v) {
-      lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks);
-      lat.jit_algo = algo;
-      lat.jit_variant = v;
-    }
+    prepare_sweep_bits(lat, inv);
     if (lat.jit) {
       const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
       void* args[] = {(void*)&p, (void*)&lut_t};

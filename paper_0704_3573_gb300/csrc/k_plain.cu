@@ -25,18 +25,20 @@ struct I8Params {
   int colour, inv;
   uint32_t t_lo, t_hi;
   PhiloxKeys keys;
+  const uint64_t* t_dev;  // non-null in captured graphs
 };
 
 // r < T for the random r of (sample, slot, site, sweep), decided from the
 // most significant plane down.  T in [0, 2^32].
-__device__ __forceinline__ bool lazy_less(uint64_t T, const I8Params& p, int s, int sigma, uint32_t site) {
+__device__ __forceinline__ bool lazy_less(uint64_t T, const I8Params& p, const Tick& tk, int s, int sigma,
+                                          uint32_t site) {
   if (T >= kTwo32) return true;
   const uint32_t T32 = (uint32_t)T;
   const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
   const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
 #pragma unroll 1
   for (uint32_t m = 0; m < 16u; ++m) {
-    const uint4 x = philox10(site, p.t_lo, c2base | (m << 24), p.t_hi, p.keys);
+    const uint4 x = philox10(site, tk.lo, c2base | (m << 24), tk.hi, p.keys);
     const uint32_t w0 = lane < 32u ? (x.x >> lane) : (x.y >> (lane - 32u));
     const uint32_t w1 = lane < 32u ? (x.z >> lane) : (x.w >> (lane - 32u));
     const uint32_t r0 = w0 & 1u, t0 = (T32 >> (31u - 2u * m)) & 1u;
@@ -51,6 +53,7 @@ template <int D>
 __global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
   const uint64_t total = (uint64_t)p.slots * p.S * p.half;
   const uint32_t L = (uint32_t)p.L, h = L / 2u;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t lat = (uint32_t)(idx / p.half);
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
     const int tslot = sigma / p.R, a = sigma - tslot * p.R;
     const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
     const uint64_t T = p.thr[(size_t)kt * kMaxClasses + u];
-    const bool less = lazy_less(T, p, s, sigma, i);
+    const bool less = lazy_less(T, p, tk, s, sigma, i);
     if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
   }
 }
@@ -239,6 +242,7 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
   p.t_lo = (uint32_t)(t & 0xffffffffu);
   p.t_hi = (uint32_t)(t >> 32);
   p.keys = lat.keys;
+  p.t_dev = lat.capturing ? lat.t_dev : nullptr;
   const uint64_t total = (uint64_t)lat.slots * lat.S * p.half;
   const unsigned grid = grid_for(total, 256, 152u * 8u);
   if (lat.D == 3)

@@ -30,6 +30,7 @@ struct PottsParams {
   uint32_t t_lo, t_hi;
   uint32_t words_per_block;
   PhiloxKeys keys;
+  const uint64_t* t_dev;  // non-null in captured graphs
 };
 
 template <int D>
@@ -49,6 +50,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_potts(const PottsParams p) {
     tab[b] = p.ptab + (size_t)k * 65536u;
   }
   const uint32_t c2 = (TAG_POTTS << 28) | ((uint32_t)sigma << 16) | (uint32_t)q;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
   for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_potts(const PottsParams p) {
       nb[4] = sp[n.zp];
       nb[5] = sp[n.zm];
     }
-    const uint4 x = philox10(n.site, p.t_lo, c2, p.t_hi, p.keys);
+    const uint4 x = philox10(n.site, tk.lo, c2, tk.hi, p.keys);
     const uint32_t rr[4] = {x.x, x.y, x.z, x.w};
     uint32_t out = 0;
 #pragma unroll
@@ -324,6 +326,7 @@ cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t) {
   p.t_lo = (uint32_t)(t & 0xffffffffu);
   p.t_hi = (uint32_t)(t >> 32);
   p.keys = lat.keys;
+  p.t_dev = lat.capturing ? lat.t_dev : nullptr;
   const uint32_t half = lat.geom.half;
   const uint32_t ys = (uint32_t)(lat.slots * lat.Q4);
   uint32_t target_blocks = (152u * 8u + ys - 1) / ys;

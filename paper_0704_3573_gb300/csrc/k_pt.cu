@@ -89,7 +89,20 @@ __global__ void k_pt_swap(const int64_t* __restrict__ acc, int32_t* slot_at, int
   }
 }
 
+__global__ void k_set_tick(uint64_t* t, uint64_t v) { *t = v; }
+__global__ void k_advance_tick(uint64_t* t, uint64_t by) { *t += by; }
+
 }  // namespace
+
+cudaError_t launch_set_tick(Lattice& lat, uint64_t value) {
+  k_set_tick<<<1, 1, 0, lat.stream>>>(lat.t_dev, value);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_tick(Lattice& lat, uint64_t by) {
+  k_advance_tick<<<1, 1, 0, lat.stream>>>(lat.t_dev, by);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(Lattice& lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q) {
   const int total = lat.S * lat.K * lat.R;

@@ -4,6 +4,7 @@
 #include <cstddef>
 #include <algorithm>
 #include <cstdint>
+#include <map>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -80,6 +81,14 @@ struct Lattice {
   int jit_algo;              // algorithm the specialisation was requested for; -1 = not yet
   int jit_variant;           // variant it was built for
   uint32_t block_words;      // words per block of the bit-sliced sweep; 0 = heuristic
+  // CUDA graphs of sweep blocks: the kernels of B sweeps and a counter
+  // advance, captured once on a private stream and replayed on `stream`.
+  uint64_t* t_dev;           // device sweep counter read by captured kernels
+  bool capturing;            // launchers pass t_dev (and an offset) while true
+  bool use_graphs;
+  bool t_dev_valid;          // *t_dev == sweeps
+  cudaStream_t cap_stream;
+  std::map<uint32_t, cudaGraphExec_t>* graphs;  // by block length
 };
 
 // ---- host table builders (tables.cpp) ----
@@ -127,5 +136,10 @@ cudaError_t launch_set_couplings_potts(Lattice& lat, const int8_t* dev_in);
 // shared (k_pt.cu)
 cudaError_t launch_finalize(Lattice& lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q);
 cudaError_t launch_pt_swap(Lattice& lat);
+cudaError_t launch_set_tick(Lattice& lat, uint64_t value);
+cudaError_t launch_advance_tick(Lattice& lat, uint64_t by);
+// Compiles the specialised bit-sliced kernel if the next sweep will use it
+// (so that no compilation happens during stream capture).
+void prepare_sweep_bits(Lattice& lat, int inv);
 
 }  // namespace ianus

@@ -322,3 +322,34 @@ def test_autotuner_does_not_change_the_trajectory(ianus, tmp_path, monkeypatch):
     assert np.array_equal(a.spins(), b.spins())
     again = tune.tune(a, HEATBATH, 1.0)
     assert again["cached"] and again["variant"] == best["variant"]
+
+
+@pytest.mark.parametrize("layout,model", [("i8", "ea"), ("bits64", "ea"), ("bits64-jit", "ea"), ("auto", "potts")])
+def test_graph_replay_equals_direct_launches(ianus, layout, model):
+    """Sweep blocks replayed from captured graphs (device sweep counter) give
+    the same trajectory and series as launching every kernel directly."""
+    runs = []
+    for graphs in (True, False):
+        lat, _, _ = _pair(ianus, model=model, dim=3, L=6, S=70, R=2, layout=layout, seed=SEED + 90)
+        lat.set_graphs(graphs)
+        algo = HEATBATH
+        for n, every in ((7, 0), (69, 6), (3, 0), (64, 0), (130, 0), (12, 4)):
+            lat.sweep(algo, 0.95, n, measure_every=every)
+        runs.append((lat.spins(), lat.series(), lat.sweeps))
+    (s0, ser0, n0), (s1, ser1, n1) = runs
+    assert n0 == n1 == 285
+    assert np.array_equal(s0, s1)
+    for a, b in zip(ser0, ser1):
+        assert np.array_equal(a, b)
+
+
+def test_graphs_with_parallel_tempering(ianus):
+    K = 4
+    beta = [1.3, 1.1, 0.9, 0.7]
+    lat, orc, _ = _pair(ianus, dim=3, L=4, S=66, R=2, K=K, layout="bits64", seed=SEED + 91)
+    lat.sweep_pt(METROPOLIS, beta, 40, swap_every=10)
+    for _ in range(4):
+        orc.sweep(METROPOLIS, beta, 10)
+        orc.pt_swap(beta)
+    assert np.array_equal(lat.spins(), orc.spins())
+    assert np.array_equal(lat.pt_state()[0], orc.pt_state()[0])
