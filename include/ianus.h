@@ -297,6 +297,14 @@ ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block)
  * and without graphs.  enable = 0 launches every kernel directly. */
 ianus_status ianus_set_graphs(ianus_lattice* lat, int32_t enable);
 
+/* Resident mode for small plain lattices (default on): with layout I8, one
+ * temperature, (1 + dim) L^dim bytes <= 200 KiB, and either one replica or no
+ * measurements, each configuration is held in the shared memory of one
+ * thread block that runs all requested sweeps (the two colours separated by
+ * a block barrier, Sec. 3.1) and records E and M itself.  Same results as the
+ * launch-per-colour path.  enable = 0 turns it off. */
+ianus_status ianus_set_resident(ianus_lattice* lat, int32_t enable);
+
 /* Frees what the lattice allocated.  NULL is accepted.  The caller-owned
  * device buffer, if any, is not freed. */
 ianus_status ianus_destroy(ianus_lattice* lat);

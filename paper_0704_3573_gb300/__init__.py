@@ -38,7 +38,7 @@ EXPORTS = [
     "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
-    "ianus_set_graphs",
+    "ianus_set_graphs", "ianus_set_resident",
 ]
 
 
@@ -112,6 +112,7 @@ def lib(build_if_missing: bool = True):
         "ianus_set_variant": (i32, [vp, i32]),
         "ianus_set_block_words": (i32, [vp, u32]),
         "ianus_set_graphs": (i32, [vp, i32]),
+        "ianus_set_resident": (i32, [vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -317,6 +318,10 @@ class Lattice:
     def set_graphs(self, enable: bool):
         """Replay sweep blocks from captured CUDA graphs (default) or launch directly."""
         _check(self._lib.ianus_set_graphs(self._h, int(bool(enable))), "ianus_set_graphs")
+
+    def set_resident(self, enable: bool):
+        """Shared-memory-resident sweeps for small plain lattices (default on)."""
+        _check(self._lib.ianus_set_resident(self._h, int(bool(enable))), "ianus_set_resident")
 
     def synchronize(self):
         _check(self._lib.ianus_synchronize(self._h), "ianus_synchronize")

@@ -437,6 +437,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->err = (uint32_t*)(b + z.off_err);
   lat->t_dev = (uint64_t*)(b + z.off_tdev);
   lat->use_graphs = true;
+  lat->use_resident = true;
   lat->graphs = new (std::nothrow) std::map<uint32_t, cudaGraphExec_t>();
 
   auto bail = [&](int code) {
@@ -484,6 +485,20 @@ ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uin
     if (st) return (ianus_status)st;
   }
   const int inv = algo == IANUS_HEATBATH;
+  if (lat->use_resident && resident_i8_fits(*lat) && (lat->R == 1 || measure_every == 0) && nsweeps >= 2) {
+    // small plain lattice: whole configurations in shared memory, many sweeps per launch
+    uint64_t left = nsweeps;
+    while (left > 0) {
+      const uint32_t n = (uint32_t)std::min<uint64_t>(left, 65536);
+      CK(launch_resident_i8(*lat, inv, n, measure_every));
+      if (measure_every)  // measured sweeps t+1 in (sweeps, sweeps + n] with (t+1) % every == 0
+        lat->ser_count += (lat->sweeps + n) / measure_every - lat->sweeps / measure_every;
+      lat->sweeps += n;
+      lat->t_dev_valid = false;
+      left -= n;
+    }
+    return IANUS_OK;
+  }
   uint64_t left = nsweeps;
   while (left > 0) {
     uint64_t chunk = left;  // sweeps up to the next measurement point
@@ -761,6 +776,12 @@ ianus_status ianus_set_block_words(ianus_lattice* h, uint32_t words_per_block) {
 ianus_status ianus_set_graphs(ianus_lattice* h, int32_t enable) {
   GET_LAT(h);
   lat->use_graphs = enable != 0;
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_resident(ianus_lattice* h, int32_t enable) {
+  GET_LAT(h);
+  lat->use_resident = enable != 0;
   return IANUS_OK;
 }
 

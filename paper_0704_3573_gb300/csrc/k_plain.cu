@@ -91,6 +91,117 @@ __global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
   }
 }
 
+
+// ---- resident mode: a whole configuration in shared memory ----
+//
+// One block per configuration (n_temps == 1) keeps the spins and the
+// couplings in shared memory and runs many sweeps in one launch, with a block
+// barrier between the two colours (Sec. 3.1) instead of a kernel boundary,
+// and records E and M into the series ring after every measured sweep.  The
+// per-site update is the one of k_sweep_i8.
+
+struct ResidentParams {
+  int8_t* spins;            // [slots][S][N]
+  const int8_t* J;          // [S][D][N]
+  const uint64_t* thr;      // [1][kMaxClasses]
+  int S, R, slots, L, inv;
+  uint32_t N, half;
+  uint64_t t0;              // absolute index of the first sweep
+  uint32_t nsweeps;
+  uint32_t measure_every;   // 0 = none
+  uint64_t row0;            // series rows recorded before this launch
+  uint32_t cap;             // series capacity
+  int64_t* ser_E;           // [cap][S*R]
+  int64_t* ser_M;
+  uint64_t* ser_sweep;      // [cap]
+  PhiloxKeys keys;
+};
+
+template <int D>
+__global__ void __launch_bounds__(1024) k_resident_i8(const ResidentParams p) {
+  extern __shared__ int8_t sm[];  // spins[N], then J[D][N]
+  __shared__ long long red[2][32];
+  int8_t* sp = sm;
+  int8_t* Js = sm + p.N;
+  const uint32_t lat = blockIdx.x;  // sigma * S + s
+  const int sigma = (int)(lat / (uint32_t)p.S), s = (int)(lat - (uint32_t)sigma * (uint32_t)p.S);
+  int8_t* gsp = p.spins + (size_t)lat * p.N;
+  const int8_t* gJ = p.J + (size_t)s * D * p.N;
+  for (uint32_t i = threadIdx.x; i < p.N; i += blockDim.x) sp[i] = gsp[i];
+  for (uint32_t i = threadIdx.x; i < (uint32_t)D * p.N; i += blockDim.x) Js[i] = gJ[i];
+  __syncthreads();
+  const uint32_t L = (uint32_t)p.L, h = L / 2u;
+  I8Params q;  // the fields lazy_less reads
+  q.keys = p.keys;
+  uint32_t nmeas = 0;
+  for (uint32_t it = 0; it < p.nsweeps; ++it) {
+    const uint64_t t = p.t0 + it;
+    const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
+    for (int colour = 0; colour < 2; ++colour) {
+      for (uint32_t w = threadIdx.x; w < p.half; w += blockDim.x) {
+        const uint32_t row = w / h, k = w - row * h;
+        const uint32_t y = row % L, z = row / L;
+        const uint32_t x = 2u * k + ((uint32_t)(colour ^ (int)(y + z)) & 1u);
+        const uint32_t i = x + L * (y + L * z);
+        const int si = sp[i];
+        const uint32_t xp = (x + 1u == L ? 0u : x + 1u) + L * (y + L * z);
+        const uint32_t xm = (x == 0u ? L - 1u : x - 1u) + L * (y + L * z);
+        const uint32_t yp = x + L * ((y + 1u == L ? 0u : y + 1u) + L * z);
+        const uint32_t ym = x + L * ((y == 0u ? L - 1u : y - 1u) + L * z);
+        int u = 0;
+        u += (Js[i] * si * sp[xp]) < 0;
+        u += (Js[xm] * si * sp[xm]) < 0;
+        u += (Js[p.N + i] * si * sp[yp]) < 0;
+        u += (Js[p.N + ym] * si * sp[ym]) < 0;
+        if (D == 3) {
+          const uint32_t zp = x + L * (y + L * (z + 1u == L ? 0u : z + 1u));
+          const uint32_t zm = x + L * (y + L * (z == 0u ? L - 1u : z - 1u));
+          u += (Js[2u * p.N + i] * si * sp[zp]) < 0;
+          u += (Js[2u * p.N + zm] * si * sp[zm]) < 0;
+        }
+        const bool less = lazy_less(p.thr[u], q, tk, s, sigma, i);
+        if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
+      }
+      __syncthreads();
+    }
+    if (p.measure_every && (t + 1) % p.measure_every == 0) {
+      long long e = 0, m = 0;
+      for (uint32_t i = threadIdx.x; i < p.N; i += blockDim.x) {
+        const uint32_t x = i % L, y = (i / L) % L, z = D == 3 ? i / (L * L) : 0u;
+        const int si = sp[i];
+        e -= Js[i] * si * sp[(x + 1u == L ? 0u : x + 1u) + L * (y + L * z)];
+        e -= Js[p.N + i] * si * sp[x + L * ((y + 1u == L ? 0u : y + 1u) + L * z)];
+        if (D == 3) e -= Js[2u * p.N + i] * si * sp[x + L * (y + L * (z + 1u == L ? 0u : z + 1u))];
+        m += si;
+      }
+      for (int off = 16; off > 0; off >>= 1) {
+        e += __shfl_down_sync(0xffffffffu, e, off);
+        m += __shfl_down_sync(0xffffffffu, m, off);
+      }
+      if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = e;
+        red[1][threadIdx.x >> 5] = m;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        long long E = 0, M = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+          E += red[0][w];
+          M += red[1][w];
+        }
+        const uint64_t row = (p.row0 + nmeas) % p.cap;
+        const size_t at = (size_t)row * p.S * p.R + (size_t)s * p.R + (size_t)sigma;  // one temperature: slot = replica
+        p.ser_E[at] = E;
+        p.ser_M[at] = M;
+        if (lat == 0) p.ser_sweep[row] = t + 1;
+      }
+      __syncthreads();
+      ++nmeas;
+    }
+  }
+  for (uint32_t i = threadIdx.x; i < p.N; i += blockDim.x) gsp[i] = sp[i];
+}
+
 struct InitParams {
   int8_t* spins;
   int8_t* J;
@@ -266,6 +377,44 @@ cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
                                             lat.slots, lat.N);
   }
   return cudaGetLastError();
+}
+
+bool resident_i8_fits(const Lattice& lat) {
+  return lat.layout == IANUS_LAYOUT_I8 && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
+}
+
+cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every) {
+  ResidentParams p;
+  p.spins = (int8_t*)lat.spins;
+  p.J = (const int8_t*)lat.J;
+  p.thr = lat.thr;
+  p.S = lat.S;
+  p.R = lat.R;
+  p.slots = lat.slots;
+  p.L = lat.L;
+  p.inv = inv;
+  p.N = lat.N;
+  p.half = lat.N / 2;
+  p.t0 = lat.sweeps;
+  p.nsweeps = nsweeps;
+  p.measure_every = measure_every;
+  p.row0 = lat.ser_count;
+  p.cap = lat.cap;
+  p.ser_E = lat.ser_E;
+  p.ser_M = lat.ser_M;
+  p.ser_sweep = lat.ser_sweep;
+  p.keys = lat.keys;
+  const size_t smem = (size_t)lat.N * (1 + lat.D);
+  const unsigned blocks = (unsigned)(lat.slots * lat.S);
+  cudaError_t e;
+  if (lat.D == 3) {
+    e = cudaFuncSetAttribute(k_resident_i8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidentSmemMax);
+    if (e == cudaSuccess) k_resident_i8<3><<<blocks, 1024, smem, lat.stream>>>(p);
+  } else {
+    e = cudaFuncSetAttribute(k_resident_i8<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidentSmemMax);
+    if (e == cudaSuccess) k_resident_i8<2><<<blocks, 1024, smem, lat.stream>>>(p);
+  }
+  return e == cudaSuccess ? cudaGetLastError() : e;
 }
 
 cudaError_t launch_get_spins_i8(Lattice& lat, int8_t* dev_out) {

@@ -86,6 +86,7 @@ struct Lattice {
   uint64_t* t_dev;           // device sweep counter read by captured kernels
   bool capturing;            // launchers pass t_dev (and an offset) while true
   bool use_graphs;
+  bool use_resident;         // resident mode for small I8 lattices (default on)
   bool t_dev_valid;          // *t_dev == sweeps
   cudaStream_t cap_stream;
   std::map<uint32_t, cudaGraphExec_t>* graphs;  // by block length
@@ -112,6 +113,12 @@ cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int
 cudaError_t launch_init_i8(Lattice& lat, int ferro);
 cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv);
 cudaError_t launch_measure_i8(Lattice& lat, int want_q);
+// Resident mode (one block per configuration in shared memory, many sweeps
+// per launch, E/M written to the series ring): n_temps == 1, I8 layout,
+// (1 + D) N bytes <= kResidentSmemMax.
+constexpr size_t kResidentSmemMax = 200 * 1024;
+bool resident_i8_fits(const Lattice& lat);
+cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every);
 cudaError_t launch_get_spins_i8(Lattice& lat, int8_t* dev_out);       // [S][slots][N]
 cudaError_t launch_set_spins_i8(Lattice& lat, const int8_t* dev_in);
 cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out);   // [S][D][N]

@@ -353,3 +353,24 @@ def test_graphs_with_parallel_tempering(ianus):
         orc.pt_swap(beta)
     assert np.array_equal(lat.spins(), orc.spins())
     assert np.array_equal(lat.pt_state()[0], orc.pt_state()[0])
+
+
+@pytest.mark.parametrize("dim,L,S,every", [(3, 16, 1, 1), (3, 8, 5, 3), (2, 32, 3, 0), (3, 2, 1, 1), (3, 32, 2, 7)])
+def test_resident_mode_equals_oracle_and_eager(ianus, dim, L, S, every):
+    """Resident mode (configurations in shared memory, many sweeps per
+    launch, series written in the kernel) against the oracle and the
+    launch-per-colour path."""
+    runs = []
+    for resident in (True, False):
+        lat = ianus.Lattice(dim=dim, L=L, n_samples=S, seed=SEED + 95, layout="i8", series_capacity=100)
+        lat.set_resident(resident)
+        lat.sweep(METROPOLIS, 1.0 / 1.1, 40, measure_every=every)
+        lat.sweep(HEATBATH, 0.8, 13, measure_every=every)
+        runs.append((lat.spins(), lat.series()))
+    orc = Oracle(dim=dim, L=L, sample_ids=list(range(S)), seed=SEED + 95)
+    orc.sweep(METROPOLIS, 1.0 / 1.1, 40, measure_every=every)
+    orc.sweep(HEATBATH, 0.8, 13, measure_every=every)
+    for sp, (sw, E, M, _) in runs:
+        assert np.array_equal(sp, orc.spins())
+        swo, Eo, Mo, _ = orc.series()
+        assert np.array_equal(sw, swo) and np.array_equal(E, Eo) and np.array_equal(M, Mo)
