@@ -48,6 +48,22 @@ WORKLOAD = ("3D EA +-J, L=64 periodic, 256 samples x 2 replicas (64 samples per 
             "E and Q every 10 sweeps; step = 100 sweeps")
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
+# kernel from one ncu capture (profiles/ianus_jit_sweep_hb3d_L64_S256x2.md),
+# valid while the kernel source is unchanged (hash of the sources it is
+# compiled from).
+TRAFFIC_BYTES_PER_LAUNCH = 41970432 + 222
+TRAFFIC_SOURCE_HASH = "50f0a28cd2a1eb15"
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("common.cuh", "jit_sweep.cuh"):
+        with open(os.path.join(ROOT, "paper_0704_3573_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def config_dict(ws: int) -> dict:
@@ -273,9 +289,10 @@ def run_gpu(args, ws, rank, local):
     achieved = ops_word * words_per_launch / kern_s / 1e12  # Tops/s
     probe = probe_peak()
     peak = probe["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if probe else None
+    traffic = TRAFFIC_BYTES_PER_LAUNCH if kernel_source_hash() == TRAFFIC_SOURCE_HASH else None
     roofline = {
         "bound": "alu", "kernel": "ianus_jit_sweep (3D heat bath, R=2, thresholds as lop3 immediates)", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-        "frac": (achieved / peak) if peak else None, "traffic": None,
+        "frac": (achieved / peak) if peak else None, "traffic": traffic,
         "ops_per_word": ops_word, "words_per_launch": words_per_launch, "launch_us": kern_s * 1e6,
         "peak_source": "probe lop3.b32 ops/clk/SM x 152 SMs x 2070 MHz" if probe else None,
         "probe": probe,
@@ -319,6 +336,7 @@ def run_gpu(args, ws, rank, local):
                          f"({upd} updates, {dt:.1f} s wall)"}
 
     serving = run_serving(args) if (rank == 0 and args.serve_jobs > 0) else None
+    others = run_other_configs(args) if (rank == 0 and not args.no_others) else None
 
     launches = args.steps * (2 * SWEEPS_PER_STEP + 2 * (SWEEPS_PER_STEP // MEASURE_EVERY))
     line = {
@@ -327,10 +345,63 @@ def run_gpu(args, ws, rank, local):
         "dtype": "u64", "data": "synthetic",
         "config": config_dict(ws),
         "wall_s": wall, "series_rows": n_rows, "gpu_launches": launches, "clocks": clk, "roofline": roofline,
-        "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "serving": serving,
+        "e2e": e2e, "plain": plain, "cpu_baseline": cpu, "serving": serving, "other_workloads": others,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def run_other_configs(args):
+    """Device throughput of the other workloads (parity-test cases, not the
+    headline): L=16 single sample Metropolis T=1.1 with E/M every sweep
+    (plain layout, shared-memory-resident); L=32 parallel tempering, 32
+    temperatures in [0.7, 1.6], 64 samples x 2 replicas, Metropolis, swap every
+    10 sweeps; q=4 Potts glass L=32, 128 samples x 2 replicas, heat bath
+    T=0.8, E and Q every 10 sweeps."""
+    import torch
+
+    import paper_0704_3573_gb300 as ianus
+
+    out = {}
+    stream = torch.cuda.Stream()
+
+    def timed(fn, reps):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3
+
+    # L=16, one sample, 1000 sweeps, E and M every sweep
+    lat = ianus.Lattice(dim=3, L=16, n_samples=1, seed=SEED - 1, layout="i8", series_capacity=1000, stream=stream)
+    lat.sweep(ianus.METROPOLIS, 1 / 1.1, 10, 1)
+    sec = timed(lambda: lat.sweep(ianus.METROPOLIS, 1 / 1.1, 1000, 1), 1)
+    out["L16_single_sample_metropolis"] = {"updates_per_ns": 16 ** 3 * 1000 / (sec * 1e9), "ms_per_1000_sweeps": sec * 1e3,
+                                           "mode": "plain int8, shared-memory resident, E/M every sweep"}
+    del lat
+    # parallel tempering
+    K = 32
+    beta = [1.0 / (0.7 + 0.9 * k / 31) for k in range(K)]
+    pt = ianus.Lattice(dim=3, L=32, n_samples=64, n_replicas=2, n_temps=K, seed=SEED + 1, layout="bits64", stream=stream)
+    pt.sweep_pt(ianus.METROPOLIS, beta, 20, swap_every=10)
+    reps = 20
+    sec = timed(lambda: pt.sweep_pt(ianus.METROPOLIS, beta, 100, swap_every=10), reps)
+    upd = 64 * 2 * K * 32 ** 3 * 100 * reps
+    out["L32_pt_32temps"] = {"updates_per_ns": upd / (sec * 1e9), "ms_per_100_sweeps": sec * 1e3 / reps,
+                             "mode": "bit-sliced, per-lane threshold planes, device PT swap every 10 sweeps"}
+    del pt
+    # Potts q=4
+    po = ianus.Lattice(model="potts", dim=3, L=32, n_samples=128, n_replicas=2, seed=SEED + 2, stream=stream)
+    po.sweep(ianus.HEATBATH, 1 / 0.8, 10, 10)
+    reps = 10
+    sec = timed(lambda: po.sweep(ianus.HEATBATH, 1 / 0.8, 100, 10), reps)
+    upd = 128 * 2 * 32 ** 3 * 100 * reps
+    out["potts_L32_128x2"] = {"updates_per_ns": upd / (sec * 1e9), "ms_per_100_sweeps": sec * 1e3 / reps,
+                              "mode": "4 samples per uint32 word, heat bath, E/Q every 10 sweeps"}
+    return out
 
 
 def run_serving(args):
@@ -418,6 +489,7 @@ def main():
     ap.add_argument("--cpu-sweeps", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--serve-scale", type=float, default=0.05)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
