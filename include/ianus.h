@@ -277,9 +277,11 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       site words, else the precompiled kernel with per-lane threshold
  *       bit-planes;
  *   1 = always the precompiled per-lane kernel;
- *   2..7 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
+ *   2..9 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
  *       blocks per SM; 4..7 = per-warp queues entered after 3 or 4 plane
- *       pairs, 3 or 4 blocks per SM (4: 3/3, 5: 4/3, 6: 3/4, 7: 4/4).
+ *       pairs, 3 or 4 blocks per SM (4: 3/3, 5: 4/3, 6: 3/4, 7: 4/4); 8, 9 =
+ *       lockstep with the two replicas interleaved in one thread, 2 or 3
+ *       blocks per SM (needs two replicas; otherwise shape 2 is used).
  * If run-time compilation is unavailable, the precompiled kernel runs.
  * EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);

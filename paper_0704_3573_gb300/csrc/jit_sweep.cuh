@@ -28,11 +28,14 @@ constexpr uint32_t kNeed = IANUS_JIT_NEED;
 constexpr int kBlock = 256;
 // IANUS_JIT_MODE 0: all plane pairs in lockstep across the warp (pairs
 // 0..7 with immediate tables, then run-time tables); 1: pairs 0..PHASEA-1 in
-// lockstep, then per-warp queues (below).  IANUS_JIT_MINB: blocks per SM the
+// lockstep, then per-warp queues (below); 2 (two replicas): as 0, with the
+// two replicas' plane loops interleaved in one thread, so that two
+// independent Philox chains are in flight (a decided replica's extra block is
+// masked out by its undecided-lane word).  IANUS_JIT_MINB: blocks per SM the
 // register allocation must allow.
 constexpr int kMode = IANUS_JIT_MODE;
 constexpr int kPhaseA = IANUS_JIT_PHASEA;
-constexpr int kUnrolled = kMode == 0 ? 8 : kPhaseA;
+constexpr int kUnrolled = kMode == 1 ? kPhaseA : 8;
 
 template <uint32_t LUT>
 __device__ __forceinline__ uint64_t lop3c(uint64_t a, uint64_t b, uint64_t c) {
@@ -63,6 +66,17 @@ __device__ __forceinline__ void pair(Word& w, const BitsParams& p, const Tick& t
   const uint64_t c1 = w.und & t1 & ~r1;
   w.und &= ~(r1 ^ t1);
   w.lt |= c0 | c1;
+}
+
+template <int M>
+__device__ __forceinline__ void pairs2(Word& w0, Word& w1, const BitsParams& p, const Tick& tk, uint32_t site,
+                                       uint32_t c2a, uint32_t c2b) {
+  if constexpr (M < kUnrolled) {
+    if ((w0.und | w1.und) == 0ull) return;
+    pair<M>(w0, p, tk, site, c2a);
+    pair<M>(w1, p, tk, site, c2b);
+    pairs2<M + 1>(w0, w1, p, tk, site, c2a, c2b);
+  }
 }
 
 template <int M>
@@ -268,6 +282,34 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
         jw[5] = __ldg(Jg + 2u * N + n.zm);
       }
     }
+    if (kMode == 2 && R == 2) {
+      if (!valid) continue;
+      Word wa[2];
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t b = sp[n.self];
+        uint64_t e[2 * D];
+        e[0] = b ^ sp[n.xp] ^ jw[0];
+        e[1] = b ^ sp[n.xm] ^ jw[1];
+        e[2] = b ^ sp[n.yp] ^ jw[2];
+        e[3] = b ^ sp[n.ym] ^ jw[3];
+        if (D == 3) {
+          e[4] = b ^ sp[n.zp] ^ jw[4];
+          e[5] = b ^ sp[n.zm] ^ jw[5];
+        }
+        count_unsat<D>(e, wa[a].u0, wa[a].u1, wa[a].u2);
+        wa[a].lt = kAlways ? lop3c<kAlways>(wa[a].u2, wa[a].u1, wa[a].u0) : 0ull;
+        wa[a].und = lop3c<kNeed>(wa[a].u2, wa[a].u1, wa[a].u0);
+      }
+      const uint32_t c2a = sigma_c2(c, 0u), c2b = sigma_c2(c, 1u);
+      pairs2<0>(wa[0], wa[1], p, c.tk, n.site, c2a, c2b);
+      if (wa[0].und != 0ull) tail_lockstep(wa[0], p, c.tk, n.site, c2a, s_lut);
+      if (wa[1].und != 0ull) tail_lockstep(wa[1], p, c.tk, n.site, c2b, s_lut);
+      finish(c, n.self, 0u, wa[0]);
+      finish(c, n.self, 1u, wa[1]);
+      continue;
+    }
 #pragma unroll
     for (int a = 0; a < R; ++a) {
       Word w;
@@ -292,12 +334,12 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
         w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
         c2 = sigma_c2(c, (uint32_t)a);
         pairs<0>(w, p, c.tk, n.site, c2);
-        if (kMode == 0) {
+        if (kMode != 1) {
           if (w.und != 0ull) tail_lockstep(w, p, c.tk, n.site, c2, s_lut);
           finish(c, n.self, (uint32_t)a, w);
         }
       }
-      if (kMode == 0) continue;
+      if (kMode != 1) continue;
       const bool pend = valid && w.und != 0ull;
       push(q3, n3, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, (uint32_t)a | ((uint32_t)kPhaseA << 1));
       if (valid && !pend) finish(c, n.self, (uint32_t)a, w);
@@ -305,7 +347,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
       while (n4 >= 32u) round4(q4, n4, 32u, c);
     }
   }
-  if (kMode == 0) return;
+  if (kMode != 1) return;
   // Drain with partial warps.  round3 pushes at most 32 entries into q4, so
   // it only runs while q4 holds fewer than 32 (q4 never exceeds 63 < kQ);
   // every round4 advances its entries' pair index, which stops at 16.

@@ -468,7 +468,8 @@ cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t
 struct JitShape {
   int mode, phase_a, min_blocks;
 };
-constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 3, 3}, {1, 4, 3}, {1, 3, 4}, {1, 4, 4}};
+constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 3, 3}, {1, 4, 3}, {1, 3, 4}, {1, 4, 4},
+                                   {2, 8, 2}, {2, 8, 3}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 constexpr int kAutoJitVariant = 2;
 
@@ -478,7 +479,8 @@ int jit_variant_for(const Lattice& lat) {
   const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
   int v = lat.variant;
   if (v == 0) v = words >= (1ull << 20) ? kAutoJitVariant : 1;
-  const bool ok = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
+  bool ok = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
+  if (ok && kJitShapes[v - 2].mode == 2 && lat.R != 2) v = 2;  // the interleaved shape needs two replicas
   return ok ? v : 1;
 }
 
