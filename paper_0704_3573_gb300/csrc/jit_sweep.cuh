@@ -159,14 +159,20 @@ __device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Wor
   __syncwarp();
 }
 
-// Mode 0: the remaining pairs kUnrolled..15 of one word, run-time tables.
-__device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, const Tick tk, uint32_t site,
-                                           uint32_t c2, const uint8_t* lut) {
+// Modes 0 and 2: the remaining pairs kUnrolled..15 of one word, run-time
+// tables.  Rarely entered; the word is passed and returned by value so that
+// the caller's state never has to live in local memory.
+struct Decided {
+  uint64_t und, lt;
+};
+
+__device__ __noinline__ Decided tail_lockstep(uint64_t u0, uint64_t u1, uint64_t u2, uint64_t und, uint64_t lt,
+                                              const BitsParams& p, const Tick tk, uint32_t site, uint32_t c2,
+                                              const uint8_t* lut) {
   uint64_t m[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u)
-    m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
-  for (uint32_t mm = kUnrolled; mm < 16u && w.und != 0ull; ++mm) {
+  for (int u = 0; u < 8; ++u) m[u] = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
+  for (uint32_t mm = kUnrolled; mm < 16u && und != 0ull; ++mm) {
     const uint4 x = philox10(site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -175,9 +181,19 @@ __device__ __noinline__ void tail_lockstep(Word& w, const BitsParams& p, const T
       uint64_t tb = 0;
 #pragma unroll
       for (int u = 0; u < 8; ++u) tb |= m[u] & (0ull - (uint64_t)((tab >> u) & 1u));
-      w.lt |= w.und & tb & ~r;
-      w.und &= ~(r ^ tb);
+      lt |= und & tb & ~r;
+      und &= ~(r ^ tb);
     }
+  }
+  return Decided{und, lt};
+}
+
+__device__ __forceinline__ void finish_tail(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2,
+                                            const uint8_t* lut) {
+  if (w.und != 0ull) {
+    const Decided d = tail_lockstep(w.u0, w.u1, w.u2, w.und, w.lt, p, tk, site, c2, lut);
+    w.und = d.und;
+    w.lt = d.lt;
   }
 }
 
@@ -304,8 +320,8 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
       }
       const uint32_t c2a = sigma_c2(c, 0u), c2b = sigma_c2(c, 1u);
       pairs2<0>(wa[0], wa[1], p, c.tk, n.site, c2a, c2b);
-      if (wa[0].und != 0ull) tail_lockstep(wa[0], p, c.tk, n.site, c2a, s_lut);
-      if (wa[1].und != 0ull) tail_lockstep(wa[1], p, c.tk, n.site, c2b, s_lut);
+      finish_tail(wa[0], p, c.tk, n.site, c2a, s_lut);
+      finish_tail(wa[1], p, c.tk, n.site, c2b, s_lut);
       finish(c, n.self, 0u, wa[0]);
       finish(c, n.self, 1u, wa[1]);
       continue;
@@ -335,7 +351,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
         c2 = sigma_c2(c, (uint32_t)a);
         pairs<0>(w, p, c.tk, n.site, c2);
         if (kMode != 1) {
-          if (w.und != 0ull) tail_lockstep(w, p, c.tk, n.site, c2, s_lut);
+          finish_tail(w, p, c.tk, n.site, c2, s_lut);
           finish(c, n.self, (uint32_t)a, w);
         }
       }
