@@ -278,8 +278,9 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       bit-planes;
  *   1 = always the precompiled per-lane kernel;
  *   2..9 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
- *       blocks per SM; 4..7 = per-warp queues entered after 3 or 4 plane
- *       pairs, 3 or 4 blocks per SM (4: 3/3, 5: 4/3, 6: 3/4, 7: 4/4); 8, 9 =
+ *       blocks per SM; 4..7 = a per-warp queue of the words still undecided
+ *       after 4, 4, 3 or 5 lockstep plane pairs, finished 32 at a time, with
+ *       3, 4, 3 or 3 blocks per SM; 8, 9 =
  *       lockstep with the two replicas interleaved in one thread, 2 or 3
  *       blocks per SM (needs two replicas; otherwise shape 2 is used).
  * If run-time compilation is unavailable, the precompiled kernel runs.

@@ -28,7 +28,7 @@ constexpr uint32_t kNeed = IANUS_JIT_NEED;
 constexpr int kBlock = 256;
 // IANUS_JIT_MODE 0: all plane pairs in lockstep across the warp (pairs
 // 0..7 with immediate tables, then run-time tables); 1: pairs 0..PHASEA-1 in
-// lockstep, then per-warp queues (below); 2 (two replicas): as 0, with the
+// lockstep, then a per-warp queue (below); 2 (two replicas): as 0, with the
 // two replicas' plane loops interleaved in one thread, so that two
 // independent Philox chains are in flight (a decided replica's extra block is
 // masked out by its undecided-lane word).  IANUS_JIT_MINB: blocks per SM the
@@ -88,80 +88,9 @@ __device__ __forceinline__ void pairs(Word& w, const BitsParams& p, const Tick& 
   }
 }
 
-// ---- compaction of the lazy plane loop ----
-//
-// A warp's 32 words need different numbers of plane pairs (a 64-lane word is
-// decided after ~3.9 pairs on average, the slowest of 32 words after ~6.4).
-// Pairs 0..2 run in lockstep (almost every word needs them); words still
-// undecided go to a per-warp queue in shared memory and pair 3 runs on 32
-// queued words at a time; words undecided after that go to a second queue
-// and advance one pair per round with run-time tables.  Every word is
-// written exactly once, by whichever lane finishes it; only colour-c words
-// are written during a colour-c pass, so the order does not matter.
-
-constexpr int kWarps = kBlock / 32;
-constexpr uint32_t kQ = 64;  // queue capacity: < 32 left + <= 32 pushed
-
-struct Queue {
-  uint64_t u0[kQ], u1[kQ], u2[kQ], und[kQ], lt[kQ];
-  uint32_t self[kQ], site[kQ], tag[kQ];  // tag = replica | next pair << 1
-};
-
-struct Ctx {
-  const BitsParams* p;
-  int g, tslot;
-  const uint8_t* lut;  // shared-memory copy of the 32 tables
-  Tick tk;
-};
-
-__device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
-  const uint32_t sigma = (uint32_t)(c.tslot * R) + a;
-  return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
-}
-
-__device__ __forceinline__ void finish(const Ctx& c, uint32_t self, uint32_t a, const Word& w) {
-  const BitsParams& p = *c.p;
-  uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R) + a) * p.geom.N;
-  const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
-  if (flip) sp[self] ^= flip;
-}
-
-__device__ __forceinline__ void put(Queue& q, uint32_t i, const Word& w, uint32_t self, uint32_t site, uint32_t tag) {
-  q.u0[i] = w.u0;
-  q.u1[i] = w.u1;
-  q.u2[i] = w.u2;
-  q.und[i] = w.und;
-  q.lt[i] = w.lt;
-  q.self[i] = self;
-  q.site[i] = site;
-  q.tag[i] = tag;
-}
-
-__device__ __forceinline__ void get(const Queue& q, uint32_t i, Word& w, uint32_t& self, uint32_t& site,
-                                    uint32_t& tag) {
-  w.u0 = q.u0[i];
-  w.u1 = q.u1[i];
-  w.u2 = q.u2[i];
-  w.und = q.und[i];
-  w.lt = q.lt[i];
-  self = q.self[i];
-  site = q.site[i];
-  tag = q.tag[i];
-}
-
-// Warp-wide append of the lanes with pred set; n is warp-uniform.
-__device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Word& w, uint32_t self, uint32_t site,
-                                     uint32_t tag) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t m = __ballot_sync(0xffffffffu, pred);
-  if (pred) put(q, n + __popc(m & ((1u << lane) - 1u)), w, self, site, tag);
-  n += __popc(m);
-  __syncwarp();
-}
-
-// Modes 0 and 2: the remaining pairs kUnrolled..15 of one word, run-time
-// tables.  Rarely entered; the word is passed and returned by value so that
-// the caller's state never has to live in local memory.
+// Modes 0 and 2 (and the queued words of mode 1): pairs 8..15 of one word,
+// run-time tables.  Rarely entered; the word is passed and returned by value
+// so that the caller's state never has to live in local memory.
 struct Decided {
   uint64_t und, lt;
 };
@@ -172,7 +101,7 @@ __device__ __noinline__ Decided tail_lockstep(uint64_t u0, uint64_t u1, uint64_t
   uint64_t m[8];
 #pragma unroll
   for (int u = 0; u < 8; ++u) m[u] = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
-  for (uint32_t mm = kUnrolled; mm < 16u && und != 0ull; ++mm) {
+  for (uint32_t mm = 8; mm < 16u && und != 0ull; ++mm) {
     const uint4 x = philox10(site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -197,61 +126,98 @@ __device__ __forceinline__ void finish_tail(Word& w, const BitsParams& p, const 
   }
 }
 
-// One plane pair with run-time tables (per-lane pair index mm).
-__device__ __forceinline__ void pair_rt(Word& w, const Ctx& c, uint32_t site, uint32_t c2, uint32_t mm) {
+// ---- compaction of the lazy plane loop (mode 1) ----
+//
+// A warp's 32 words need different numbers of plane pairs (a 64-lane word is
+// decided after ~3.9 pairs on average, the slowest of 32 words after ~6.4).
+// Pairs 0..PHASEA-1 run in lockstep; the few words still undecided (about a
+// fifth after 4 pairs) are appended to a per-warp queue in shared memory, and
+// whenever 32 are queued the warp finishes them together: pairs PHASEA..7
+// in lockstep with immediate tables, then the run-time tail.  Every word is
+// written exactly once, by whichever lane finishes it; during a colour-c pass
+// only colour-c words are written, so the order does not matter.
+
+constexpr int kWarps = kBlock / 32;
+constexpr uint32_t kQ = 64;  // queue capacity: < 32 left + <= 32 pushed
+
+struct Queue {
+  uint64_t u0[kQ], u1[kQ], u2[kQ], und[kQ], lt[kQ];
+  uint32_t self[kQ], site[kQ], tag[kQ];  // tag = replica
+};
+
+struct Ctx {
+  const BitsParams* p;
+  int g, tslot;
+  const uint8_t* lut;  // shared-memory copy of the 32 tables
+  Tick tk;
+};
+
+__device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
+  const uint32_t sigma = (uint32_t)(c.tslot * R) + a;
+  return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
+}
+
+__device__ __forceinline__ void finish(const Ctx& c, uint32_t self, uint32_t a, const Word& w) {
   const BitsParams& p = *c.p;
-  const uint4 x = philox10(site, c.tk.lo, c2 | (mm << 24), c.tk.hi, p.keys);
-  uint64_t m[8];
-#pragma unroll
-  for (int u = 0; u < 8; ++u)
-    m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
-#pragma unroll
-  for (int q = 0; q < 2; ++q) {
-    const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32)) : ((uint64_t)x.z | ((uint64_t)x.w << 32));
-    const uint32_t tab = c.lut[2u * mm + (uint32_t)q];
-    uint64_t tb = 0;
-#pragma unroll
-    for (int u = 0; u < 8; ++u) tb |= m[u] & (0ull - (uint64_t)((tab >> u) & 1u));
-    w.lt |= w.und & tb & ~r;
-    w.und &= ~(r ^ tb);
+  uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R) + a) * p.geom.N;
+  const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
+  if (flip) sp[self] ^= flip;
+}
+
+// Pairs M..END-1 in lockstep with immediate tables.
+template <int M, int END>
+__device__ __forceinline__ void pairs_range(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
+  if constexpr (M < END) {
+    if (w.und == 0ull) return;
+    pair<M>(w, p, tk, site, c2);
+    pairs_range<M + 1, END>(w, p, tk, site, c2);
   }
 }
 
-// Pair kPhaseA for up to 32 queued words (the top `take` entries of q3).
-__device__ __forceinline__ void round3(Queue& q3, Queue& q4, uint32_t& n3, uint32_t& n4, uint32_t take,
-                                       const Ctx& c) {
+// Warp-wide append of the lanes with pred set; n is warp-uniform.
+__device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Word& w, uint32_t self, uint32_t site,
+                                     uint32_t tag) {
   const uint32_t lane = threadIdx.x & 31u;
-  const bool has = lane < take;
-  Word w;
-  uint32_t self = 0, site = 0, tag = 0;
-  w.und = 0;
-  if (has) get(q3, n3 - take + lane, w, self, site, tag);
+  const uint32_t m = __ballot_sync(0xffffffffu, pred);
+  if (pred) {
+    const uint32_t i = n + __popc(m & ((1u << lane) - 1u));
+    q.u0[i] = w.u0;
+    q.u1[i] = w.u1;
+    q.u2[i] = w.u2;
+    q.und[i] = w.und;
+    q.lt[i] = w.lt;
+    q.self[i] = self;
+    q.site[i] = site;
+    q.tag[i] = tag;
+  }
+  n += __popc(m);
   __syncwarp();
-  n3 -= take;
-  if (has) pair<kPhaseA>(w, *c.p, c.tk, site, sigma_c2(c, tag & 1u));
-  const bool pend = has && w.und != 0ull;
-  push(q4, n4, pend, w, self, site, (tag & 1u) | ((uint32_t)(kPhaseA + 1) << 1));
-  if (has && !pend) finish(c, self, tag & 1u, w);
 }
 
-// One more pair (run-time tables) for up to 32 words of q4.
-__device__ __forceinline__ void round4(Queue& q4, uint32_t& n4, uint32_t take, const Ctx& c) {
+// Finish the top `take` (<= 32) queued words.
+__device__ __forceinline__ void round(Queue& q, uint32_t& n, uint32_t take, const Ctx& c) {
   const uint32_t lane = threadIdx.x & 31u;
   const bool has = lane < take;
   Word w;
-  uint32_t self = 0, site = 0, tag = 0;
-  w.und = 0;
-  if (has) get(q4, n4 - take + lane, w, self, site, tag);
-  __syncwarp();
-  n4 -= take;
-  uint32_t mm = tag >> 1;
+  uint32_t self = 0, site = 0, a = 0;
+  w.u0 = w.u1 = w.u2 = w.und = w.lt = 0;
   if (has) {
-    pair_rt(w, c, site, sigma_c2(c, tag & 1u), mm);
-    ++mm;
+    const uint32_t i = n - take + lane;
+    w.u0 = q.u0[i];
+    w.u1 = q.u1[i];
+    w.u2 = q.u2[i];
+    w.und = q.und[i];
+    w.lt = q.lt[i];
+    self = q.self[i];
+    site = q.site[i];
+    a = q.tag[i];
   }
-  const bool pend = has && w.und != 0ull && mm < 16u;
-  push(q4, n4, pend, w, self, site, (tag & 1u) | (mm << 1));
-  if (has && !pend) finish(c, self, tag & 1u, w);
+  __syncwarp();
+  n -= take;
+  const uint32_t c2 = sigma_c2(c, a);
+  pairs_range<kPhaseA, 8>(w, *c.p, c.tk, site, c2);
+  finish_tail(w, *c.p, c.tk, site, c2, c.lut);
+  if (has) finish(c, self, a, w);
 }
 
 }  // namespace jit
@@ -262,14 +228,11 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
   using namespace ianus;
   using namespace ianus::jit;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
-  Queue* queues = reinterpret_cast<Queue*>(dyn_smem);  // [kWarps][2]
   __shared__ uint8_t s_lut[32];
   if (threadIdx.x < 32) s_lut[threadIdx.x] = lut_t[threadIdx.x];
   __syncthreads();
-  const uint32_t warp = threadIdx.x >> 5;
-  Queue& q3 = queues[2 * warp];
-  Queue& q4 = queues[2 * warp + 1];
-  uint32_t n3 = 0, n4 = 0;
+  Queue* q = reinterpret_cast<Queue*>(dyn_smem) + (threadIdx.x >> 5);  // one queue per warp (mode 1)
+  uint32_t nq = 0;
   Ctx c;
   c.p = &p;
   const int gt = blockIdx.y;  // g * K + tslot
@@ -357,22 +320,10 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
       }
       if (kMode != 1) continue;
       const bool pend = valid && w.und != 0ull;
-      push(q3, n3, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, (uint32_t)a | ((uint32_t)kPhaseA << 1));
+      push(*q, nq, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, (uint32_t)a);
       if (valid && !pend) finish(c, n.self, (uint32_t)a, w);
-      while (n3 >= 32u) round3(q3, q4, n3, n4, 32u, c);
-      while (n4 >= 32u) round4(q4, n4, 32u, c);
+      if (nq >= 32u) round(*q, nq, 32u, c);
     }
   }
-  if (kMode != 1) return;
-  // Drain with partial warps.  round3 pushes at most 32 entries into q4, so
-  // it only runs while q4 holds fewer than 32 (q4 never exceeds 63 < kQ);
-  // every round4 advances its entries' pair index, which stops at 16.
-  while (n3 > 0u || n4 > 0u) {
-    if (n4 >= 32u)
-      round4(q4, n4, 32u, c);
-    else if (n3 > 0u)
-      round3(q3, q4, n3, n4, n3 < 32u ? n3 : 32u, c);
-    else
-      round4(q4, n4, n4, c);
-  }
+  if (kMode == 1 && nq > 0u) round(*q, nq, nq, c);
 }

@@ -468,7 +468,7 @@ cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t
 struct JitShape {
   int mode, phase_a, min_blocks;
 };
-constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 3, 3}, {1, 4, 3}, {1, 3, 4}, {1, 4, 4},
+constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 4, 3}, {1, 4, 4}, {1, 3, 3}, {1, 5, 3},
                                    {2, 8, 2}, {2, 8, 3}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 constexpr int kAutoJitVariant = 2;

@@ -102,10 +102,10 @@ size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
 void class_thresholds(int dim, int algo, double beta, uint64_t* thr /*[kMaxClasses]*/);
 
 // Run-time specialised bit-sliced sweep for lat.ulut (jit.cu); null when
-// runtime compilation is unavailable.  It takes kJitSmemBytes of dynamic
-// shared memory: two per-warp queues of 64 entries (5 x 8 + 3 x 4 bytes) for
+// runtime compilation is unavailable.  Its queued shape takes kJitSmemBytes
+// of dynamic shared memory: one queue of 64 entries (5 x 8 + 3 x 4 bytes) for
 // each of its 8 warps.
-constexpr size_t kJitSmemBytes = 8 * 2 * 64 * (5 * 8 + 3 * 4);
+constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
 cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks);
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
