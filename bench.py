@@ -79,20 +79,26 @@ def expected_plane_pairs(lanes: int = 64) -> float:
     return sum(1.0 - (1.0 - 4.0 ** (-m)) ** lanes for m in range(16))
 
 
-def algorithmic_ops_per_word_hb3d(R_: int = 2) -> float:
+def algorithmic_ops_per_word_hb3d(R_: int = 2) -> dict:
     """Minimal 32-bit integer operations one 3D heat-bath update of a 64-lane
-    site word needs (64-bit logic counts as two 32-bit operations):
-      fixed: 7 spin + 6/R coupling loads, 6 unsatisfied-bond words (12), the
-        6->3 adder tree (16), the always / needs-a-random masks (one lop3
-        each, 4), write-back (3);
-      per plane: the threshold bit-plane as one lop3 of (u2, u1, u0) (2), the
-        compare (r < T decided where r and T first differ: 4);
-      per plane pair: one Philox4x32-10 block (10 rounds x (2 mad.wide +
-        2 lop3) + 1 counter word) and merging the decided-less lanes (2);
-    times the expected number of plane pairs a word needs."""
-    fixed = (7 + 6.0 / R_) + 12 + 16 + 4 + 3
-    per_pair = 10 * 4 + 1 + 2 * (2 + 4) + 2
-    return fixed + expected_plane_pairs() * per_pair
+    site word needs, by pipe (64-bit logic counts as two 32-bit operations):
+      ALU pipe, fixed: 6 unsatisfied-bond words (12), the 6->3 adder tree
+        (16), the always / needs-a-random masks (one lop3 each, 4), the flip
+        (2);
+      ALU pipe, per plane: the threshold bit-plane as one lop3 of
+        (u2, u1, u0) (2) and the compare (4);
+      per plane pair: one Philox4x32-10 block = 10 rounds x (2 lop3 on the
+        ALU pipe + 2 mad.wide on the FMA pipe) + 1 counter word, and the
+        2-op merge of decided lanes;
+      load/store pipe: 7 spin + 6/R coupling loads, 1 store;
+    times the expected number of plane pairs a word needs.  The ALU pipe
+    binds (64 lop3 per clock per SM against 62.7 mad.wide per clock on the
+    FMA pipe, which carries less than half as many)."""
+    e_p = expected_plane_pairs()
+    alu = (12 + 16 + 4 + 2) + e_p * (2 * (2 + 4) + 21 + 2)
+    fma = e_p * 20
+    lsu = 7 + 6.0 / R_ + 1
+    return {"alu": alu, "fma": fma, "lsu": lsu, "total": alu + fma + lsu}
 
 
 # ---------------- distributed helpers ----------------
@@ -244,6 +250,12 @@ def run_gpu(args, ws, rank, local):
 
     lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=seed, layout="bits64",
                         series_capacity=4096, stream=stream)
+    tuned = None
+    if not args.no_tune:  # kernel variant and launch shape by the autotuner (restores the state)
+        from paper_0704_3573_gb300 import tune
+
+        t = tune.tune(lat, ianus.HEATBATH, beta, sweeps=40, use_cache=False)
+        tuned = {"variant": t["variant"], "block_words": t["block_words"], "us_per_sweep": t["us_per_sweep"]}
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             lat.sweep(ianus.HEATBATH, beta, SWEEPS_PER_STEP, MEASURE_EVERY)
@@ -285,15 +297,18 @@ def run_gpu(args, ws, rank, local):
     torch.cuda.synchronize()
     kern_s = a0.elapsed_time(a1) / 1e3 / (2 * nsw)
     words_per_launch = (S // 64) * R * L ** 3 // 2
-    ops_word = algorithmic_ops_per_word_hb3d(R)
-    achieved = ops_word * words_per_launch / kern_s / 1e12  # Tops/s
+    ops = algorithmic_ops_per_word_hb3d(R)
+    ops_word = ops["alu"]
+    achieved = ops_word * words_per_launch / kern_s / 1e12  # T ALU-pipe ops/s
     probe = probe_peak()
     peak = probe["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if probe else None
     traffic = TRAFFIC_BYTES_PER_LAUNCH if kernel_source_hash() == TRAFFIC_SOURCE_HASH else None
     roofline = {
-        "bound": "alu", "kernel": "ianus_jit_sweep (3D heat bath, R=2, thresholds as lop3 immediates)", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+        "bound": "alu", "kernel": "ianus_jit_sweep (3D heat bath, R=2, thresholds as lop3 immediates)",
+        "achieved": achieved, "peak": peak, "unit": "T ALU-pipe int32 ops/s",
         "frac": (achieved / peak) if peak else None, "traffic": traffic,
-        "ops_per_word": ops_word, "words_per_launch": words_per_launch, "launch_us": kern_s * 1e6,
+        "alu_ops_per_word": ops_word, "all_ops_per_word": ops, "words_per_launch": words_per_launch,
+        "launch_us": kern_s * 1e6, "variant": tuned,
         "peak_source": "probe lop3.b32 ops/clk/SM x 152 SMs x 2070 MHz" if probe else None,
         "probe": probe,
     }
@@ -490,6 +505,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=400)
     ap.add_argument("--no-others", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--serve-scale", type=float, default=0.05)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
