@@ -395,7 +395,18 @@ def run_other_configs(args):
     lat.sweep(ianus.METROPOLIS, 1 / 1.1, 10, 1)
     sec = timed(lambda: lat.sweep(ianus.METROPOLIS, 1 / 1.1, 1000, 1), 1)
     out["L16_single_sample_metropolis"] = {"updates_per_ns": 16 ** 3 * 1000 / (sec * 1e9), "ms_per_1000_sweeps": sec * 1e3,
-                                           "mode": "plain int8, shared-memory resident, E/M every sweep"}
+                                           "mode": "plain int8, shared-memory resident, E/M every sweep",
+                                           "bound": "latency (one lattice on one SM, 2000 colour barriers)"}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(dim=3, L=16, sample_ids=[0], seed=SEED - 1)
+        t0 = time.perf_counter()
+        o.sweep(oracle.METROPOLIS, 1 / 1.1, 100, measure_every=1)
+        dt = time.perf_counter() - t0
+        out["L16_single_sample_metropolis"]["cpu_baseline"] = {
+            "value": 16 ** 3 * 100 / (dt * 1e9), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the single sample, 100 sweeps with E/M every sweep"}
     del lat
     # parallel tempering
     K = 32
@@ -405,8 +416,29 @@ def run_other_configs(args):
     reps = 20
     sec = timed(lambda: pt.sweep_pt(ianus.METROPOLIS, beta, 100, swap_every=10), reps)
     upd = 64 * 2 * K * 32 ** 3 * 100 * reps
-    out["L32_pt_32temps"] = {"updates_per_ns": upd / (sec * 1e9), "ms_per_100_sweeps": sec * 1e3 / reps,
-                             "mode": "bit-sliced, per-lane threshold planes, device PT swap every 10 sweeps"}
+    rate = upd / (sec * 1e9)
+    # per-lane-plane kernel, 3D Metropolis: e-words 12, adder tree 16, class /
+    # always / need masks 10, per plane 3 class selections (6) + compare (4),
+    # per pair Philox 21 ALU + merge 2; ~3.9 plane pairs per word
+    alu_word = 38 + 3.9 * (2 * 10 + 23)
+    peak = _alu_peak()
+    out["L32_pt_32temps"] = {
+        "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
+        "mode": "bit-sliced, per-lane threshold planes, device PT swap every 10 sweeps",
+        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
+                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
+                     "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(dim=3, L=32, sample_ids=[0, 37], n_replicas=2, n_temps=K, seed=SEED + 1)
+        nthr = 2
+        t0 = time.perf_counter()
+        o.sweep(oracle.METROPOLIS, beta, 1, nthreads=nthr)
+        dt = time.perf_counter() - t0
+        out["L32_pt_32temps"]["cpu_baseline"] = {"value": 2 * 2 * K * 32 ** 3 / (dt * 1e9), "unit": UNIT, "cores": nthr,
+                                                 "kind": "oracle", "sample": "samples 0, 37 (64 configurations each), 1 sweep"}
     del pt
     # Potts q=4
     po = ianus.Lattice(model="potts", dim=3, L=32, n_samples=128, n_replicas=2, seed=SEED + 2, stream=stream)
@@ -414,9 +446,40 @@ def run_other_configs(args):
     reps = 10
     sec = timed(lambda: po.sweep(ianus.HEATBATH, 1 / 0.8, 100, 10), reps)
     upd = 128 * 2 * 32 ** 3 * 100 * reps
-    out["potts_L32_128x2"] = {"updates_per_ns": upd / (sec * 1e9), "ms_per_100_sweeps": sec * 1e3 / reps,
-                              "mode": "4 samples per uint32 word, heat bath, E/Q every 10 sweeps"}
+    rate = upd / (sec * 1e9)
+    # per 4-sample word: Philox 21 ALU; per sample 6 neighbours x (state,
+    # coupling, shift, add: 4) + 3 compares with "always" flags (6) + pack (3)
+    alu_word = 21 + 4 * (24 + 6 + 3)
+    out["potts_L32_128x2"] = {
+        "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
+        "mode": "4 samples per uint32 word, heat bath, E/Q every 10 sweeps",
+        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 4, "achieved": rate * alu_word / 4 / 1e3,
+                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
+                     "frac": (rate * alu_word / 4 / 1e3 / peak) if peak else None},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(model=oracle.MODEL_POTTS, dim=3, L=32, sample_ids=[0, 127], n_replicas=2, seed=SEED + 2)
+        t0 = time.perf_counter()
+        o.sweep(oracle.HEATBATH, 1 / 0.8, 2, nthreads=2)
+        dt = time.perf_counter() - t0
+        out["potts_L32_128x2"]["cpu_baseline"] = {"value": 2 * 2 * 32 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2,
+                                                  "kind": "oracle", "sample": "samples 0, 127 x 2 replicas, 2 sweeps"}
+    del po
+    # device-side set-up: couplings and initial spins of the bench workload from the seed
+    t0 = time.perf_counter()
+    lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 3, layout="bits64", stream=stream)
+    torch.cuda.synchronize()
+    out["init_L64_256x2"] = {"seconds": time.perf_counter() - t0,
+                             "what": "ianus_lattice_create: buffer clear + couplings and spins from the seed (wall)"}
+    del lat
     return out
+
+
+def _alu_peak():
+    p = probe_peak()
+    return p["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if p else None
 
 
 def run_serving(args):
