@@ -47,7 +47,7 @@ def lib():
         c = ctypes
         L.oracle_create.restype = c.c_void_p
         L.oracle_create.argtypes = [c.c_int, c.c_int, c.c_int, c.c_int, c.POINTER(c.c_int32), c.c_int,
-                                    c.c_int, c.c_int, c.c_uint64, c.c_int]
+                                    c.c_int, c.c_int, c.c_uint64, c.c_int, c.c_double, c.c_double]
         L.oracle_destroy.argtypes = [c.c_void_p]
         L.oracle_sweep.argtypes = [c.c_void_p, c.c_int, c.POINTER(c.c_double), c.c_uint64, c.c_uint32, c.c_int]
         L.oracle_pt_swap.argtypes = [c.c_void_p, c.POINTER(c.c_double)]
@@ -60,6 +60,8 @@ def lib():
         L.oracle_series_clear.argtypes = [c.c_void_p]
         for f in ("oracle_get_spins", "oracle_set_spins", "oracle_get_couplings", "oracle_set_couplings"):
             getattr(L, f).argtypes = [c.c_void_p, c.c_void_p]
+        L.oracle_get_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
+        L.oracle_set_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
         L.oracle_get_pt.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]
         L.oracle_bookkeeping_error.restype = c.c_int64
         L.oracle_bookkeeping_error.argtypes = [c.c_void_p]
@@ -77,6 +79,14 @@ def lib():
         L.oracle_table_potts.argtypes = [c.c_double, c.c_int, c.c_void_p, c.c_void_p]
         L.oracle_table_pt.restype = c.c_uint64
         L.oracle_table_pt.argtypes = [c.c_double, c.c_int64]
+        L.oracle_table_metropolis_x.restype = c.c_uint64
+        L.oracle_table_metropolis_x.argtypes = [c.c_double, c.c_double]
+        L.oracle_table_heatbath_x.restype = c.c_uint64
+        L.oracle_table_heatbath_x.argtypes = [c.c_double, c.c_double]
+        L.oracle_field_sign_bit.restype = c.c_int
+        L.oracle_field_sign_bit.argtypes = [c.c_uint64, c.c_int, c.c_uint32]
+        L.oracle_occupation_random.restype = c.c_uint32
+        L.oracle_occupation_random.argtypes = [c.c_uint64, c.c_int, c.c_uint32]
         _lib = L
     return _lib
 
@@ -125,8 +135,25 @@ def table_pt(dbeta_abs: float, dabs: int) -> int:
     return int(lib().oracle_table_pt(dbeta_abs, dabs))
 
 
+def table_metropolis_x(beta: float, x: float) -> int:
+    return int(lib().oracle_table_metropolis_x(beta, x))
+
+
+def table_heatbath_x(beta: float, x: float) -> int:
+    return int(lib().oracle_table_heatbath_x(beta, x))
+
+
+def field_sign_bit(seed, sample, site) -> int:
+    return int(lib().oracle_field_sign_bit(seed, sample, site))
+
+
+def occupation_random(seed, sample, site) -> int:
+    return int(lib().oracle_occupation_random(seed, sample, site))
+
+
 MODEL_ISING, MODEL_POTTS = 0, 1
 METROPOLIS, HEATBATH = 0, 1
+DIS_EA, DIS_FERRO, DIS_RFIM, DIS_DAFF = 0, 1, 2, 3
 
 
 class Oracle:
@@ -134,18 +161,25 @@ class Oracle:
 
     ``sample_ids`` selects which disorder samples are simulated; each keeps its
     true index, so sample s here follows the same streams as sample s of a
-    full batch.
+    full batch.  ``disorder`` is one of DIS_* (``ferro=True`` is DIS_FERRO);
+    ``field`` is |h| (random-field model) and ``occupation`` the site
+    occupation probability (diluted antiferromagnet).  Field models measure
+    M as [S, K, R, 2] = (sum x s, sum sign(h) x s).
     """
 
     def __init__(self, model=MODEL_ISING, dim=3, L=4, sample_ids=(0,), n_replicas=1, n_temps=1,
-                 seed=1, ferro=False, q=4):
+                 seed=1, ferro=False, q=4, disorder=None, field=0.0, occupation=1.0):
         ids = np.asarray(sample_ids, dtype=np.int32)
+        if disorder is None:
+            disorder = DIS_FERRO if ferro else DIS_EA
         self.model, self.q, self.dim, self.L = model, q, dim, L
+        self.disorder, self.field, self.occupation = disorder, float(field), float(occupation)
         self.N = L ** dim
         self.S, self.R, self.K = len(ids), n_replicas, n_temps
         self.sample_ids = ids
+        self.mq = q if model != MODEL_ISING else (2 if disorder in (DIS_RFIM, DIS_DAFF) else 1)
         h = lib().oracle_create(model, q, dim, L, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(ids),
-                                n_replicas, n_temps, seed, int(bool(ferro)))
+                                n_replicas, n_temps, seed, int(disorder), float(field), float(occupation))
         if not h:
             raise ValueError("invalid oracle configuration")
         self._h = ctypes.c_void_p(h)
@@ -173,7 +207,7 @@ class Oracle:
         """Returns (E [S,K,R], M [S,K,R] or [S,K,R,q], Q [S,K] or None)."""
         S, K, R = self.S, self.K, self.R
         E = np.zeros((S, K, R), dtype=np.int64)
-        M = np.zeros((S, K, R) if self.model == 0 else (S, K, R, self.q), dtype=np.int64)
+        M = np.zeros((S, K, R) if self.mq == 1 else (S, K, R, self.mq), dtype=np.int64)
         Q = np.zeros((S, K), dtype=np.int64)
         lib().oracle_measure(self._h, _ptr(E), _ptr(M), _ptr(Q) if R >= 2 else None)
         return E, M, (Q if R >= 2 else None)
@@ -183,7 +217,7 @@ class Oracle:
         S, K, R = self.S, self.K, self.R
         sw = np.zeros(n, dtype=np.uint64)
         E = np.zeros((n, S, K, R), dtype=np.int64)
-        M = np.zeros((n, S, K, R) if self.model == 0 else (n, S, K, R, self.q), dtype=np.int64)
+        M = np.zeros((n, S, K, R) if self.mq == 1 else (n, S, K, R, self.mq), dtype=np.int64)
         Q = np.zeros((n, S, K), dtype=np.int64)
         lib().oracle_series(self._h, _ptr(sw), _ptr(E), _ptr(M), _ptr(Q))
         return sw, E, M, (Q if R >= 2 else None)
@@ -208,6 +242,18 @@ class Oracle:
     def set_couplings(self, a):
         a = np.ascontiguousarray(a, dtype=np.int8).reshape(self.S, self.dim, self.N)
         lib().oracle_set_couplings(self._h, _ptr(a))
+
+    def sites(self):
+        """(sign(h_i) [S, N], x_i [S, N]) as int8."""
+        hs = np.zeros((self.S, self.N), dtype=np.int8)
+        x = np.zeros((self.S, self.N), dtype=np.int8)
+        lib().oracle_get_sites(self._h, _ptr(hs), _ptr(x))
+        return hs, x
+
+    def set_sites(self, hs=None, x=None):
+        hs = None if hs is None else np.ascontiguousarray(hs, dtype=np.int8).reshape(self.S, self.N)
+        x = None if x is None else np.ascontiguousarray(x, dtype=np.int8).reshape(self.S, self.N)
+        lib().oracle_set_sites(self._h, None if hs is None else _ptr(hs), None if x is None else _ptr(x))
 
     def pt_state(self):
         S, R, K = self.S, self.R, self.K

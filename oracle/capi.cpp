@@ -14,11 +14,12 @@ using namespace oracle;
 extern "C" {
 
 void* oracle_create(int model, int q, int dim, int L, const int32_t* sample_ids, int n_ids, int R,
-                    int K, uint64_t seed, int ferro) {
+                    int K, uint64_t seed, int disorder, double field, double occupation) {
   if (dim < 1 || dim > 3 || L < 2 || (L & 1) || n_ids < 1 || R < 1 || K < 1 || q < 2) return nullptr;
+  if (disorder < 0 || disorder > 3 || !(field >= 0.0) || !(occupation >= 0.0 && occupation <= 1.0)) return nullptr;
   State* st = new State();
   std::vector<int> ids(sample_ids, sample_ids + n_ids);
-  init_state(*st, model, q, dim, L, ids, R, K, seed, ferro);
+  init_state(*st, model, q, dim, L, ids, R, K, seed, disorder, field, occupation);
   return st;
 }
 
@@ -67,16 +68,45 @@ void oracle_get_spins(void* h, int8_t* out) {
     }
 }
 
+static void rebook(State* st) {
+  for (auto& smp : st->samples)
+    for (size_t sl = 0; sl < smp.spin.size(); ++sl) {
+      smp.E_run[sl] = energy(*st, smp, (int)sl);
+      smp.F_run[sl] = st->model == 0 ? field_sum(*st, smp, (int)sl) : 0;
+    }
+}
+
 void oracle_set_spins(void* h, const int8_t* in) {
   State* st = static_cast<State*>(h);
   size_t o = 0;
-  for (auto& smp : st->samples) {
+  for (auto& smp : st->samples)
     for (auto& v : smp.spin) {
       std::memcpy(v.data(), in + o, v.size());
       o += v.size();
     }
-    for (size_t sl = 0; sl < smp.spin.size(); ++sl) smp.E_run[sl] = energy(*st, smp, (int)sl);
+  rebook(st);
+}
+
+/* field signs / occupations int8 [n_ids][N] */
+void oracle_get_sites(void* h, int8_t* hs, int8_t* x) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples) {
+    if (hs) std::memcpy(hs + o, smp.hs.data(), smp.hs.size());
+    if (x) std::memcpy(x + o, smp.x.data(), smp.x.size());
+    o += smp.hs.size();
   }
+}
+
+void oracle_set_sites(void* h, const int8_t* hs, const int8_t* x) {
+  State* st = static_cast<State*>(h);
+  size_t o = 0;
+  for (auto& smp : st->samples) {
+    if (hs) std::memcpy(smp.hs.data(), hs + o, smp.hs.size());
+    if (x) std::memcpy(smp.x.data(), x + o, smp.x.size());
+    o += smp.hs.size();
+  }
+  rebook(st);
 }
 
 /* couplings int8 [n_ids][D][N] */
@@ -95,8 +125,8 @@ void oracle_set_couplings(void* h, const int8_t* in) {
   for (auto& smp : st->samples) {
     std::memcpy(smp.J.data(), in + o, smp.J.size());
     o += smp.J.size();
-    for (size_t sl = 0; sl < smp.spin.size(); ++sl) smp.E_run[sl] = energy(*st, smp, (int)sl);
   }
+  rebook(st);
 }
 
 /* slot_at int32 [n_ids][R][K], accepted uint64 [n_ids][R][K-1] */
@@ -113,7 +143,7 @@ void oracle_get_pt(void* h, int32_t* slot_at, uint64_t* accepted, uint64_t* step
   if (steps) *steps = st->steps;
 }
 
-/* max over configurations of |E_run - E recomputed from scratch| */
+/* max over configurations of |E_run - E recomputed| and |F_run - F recomputed| */
 int64_t oracle_bookkeeping_error(void* h) {
   State* st = static_cast<State*>(h);
   int64_t worst = 0;
@@ -122,6 +152,11 @@ int64_t oracle_bookkeeping_error(void* h) {
       int64_t diff = smp.E_run[sl] - energy(*st, smp, (int)sl);
       if (diff < 0) diff = -diff;
       if (diff > worst) worst = diff;
+      if (st->model == 0) {
+        int64_t df = smp.F_run[sl] - field_sum(*st, smp, (int)sl);
+        if (df < 0) df = -df;
+        if (df > worst) worst = df;
+      }
     }
   return worst;
 }
@@ -146,5 +181,11 @@ void oracle_table_potts(double beta, int q, const int32_t* n, uint64_t* T) {
   table_potts(beta, q, nn.data(), T);
 }
 uint64_t oracle_table_pt(double dbeta_abs, int64_t dabs) { return table_pt(dbeta_abs, dabs); }
+uint64_t oracle_table_metropolis_x(double beta, double x) { return table_metropolis_x(beta, x); }
+uint64_t oracle_table_heatbath_x(double beta, double x) { return table_heatbath_x(beta, x); }
+int oracle_field_sign_bit(uint64_t seed, int sample, uint32_t site) { return field_sign_bit(seed, sample, site); }
+uint32_t oracle_occupation_random(uint64_t seed, int sample, uint32_t site) {
+  return occupation_random(seed, sample, site);
+}
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include "oracle.h"
 
 #include <algorithm>
+#include <cmath>
 #include <thread>
 
 namespace oracle {
@@ -45,8 +46,10 @@ int colour(const State& st, uint32_t i) {
 /* ---- set-up: quenched couplings and initial configurations ---- */
 
 void init_state(State& st, int model, int q, int D, int L, const std::vector<int>& sample_ids,
-                int R, int K, uint64_t seed, int ferro) {
+                int R, int K, uint64_t seed, int disorder, double field, double occupation) {
   st.model = model;
+  st.disorder = model == 0 ? disorder : (disorder == DIS_FERRO ? DIS_FERRO : DIS_EA);
+  st.hmag = field;
   st.q = q;
   st.D = D;
   st.L = L;
@@ -59,13 +62,26 @@ void init_state(State& st, int model, int q, int D, int L, const std::vector<int
   st.steps = 0;
   st.samples.clear();
   const int slots = K * R;
+  /* site occupied iff its dilution random is below floor(2^32 occupation) */
+  const uint64_t T_occ = (uint64_t)std::floor(std::ldexp(occupation, 32));
   for (int s : sample_ids) {
     Sample smp;
     smp.s = s;
     smp.J.assign((size_t)D * st.N, 1);
     for (int d = 0; d < D; ++d)
-      for (uint32_t i = 0; i < (uint32_t)st.N; ++i)
-        smp.J[(size_t)d * st.N + i] = (ferro || !coupling_bit(seed, s, d, i)) ? 1 : -1;
+      for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+        int J;
+        if (st.disorder == DIS_EA) J = coupling_bit(seed, s, d, i) ? -1 : 1;
+        else if (st.disorder == DIS_DAFF) J = -1;  /* antiferromagnet */
+        else J = 1;                                /* ferromagnet, RFIM */
+        smp.J[(size_t)d * st.N + i] = (int8_t)J;
+      }
+    smp.x.assign(st.N, 1);
+    smp.hs.assign(st.N, 1);
+    for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+      if (st.disorder == DIS_RFIM) smp.hs[i] = field_sign_bit(seed, s, i) ? -1 : 1;
+      if (st.disorder == DIS_DAFF) smp.x[i] = ((uint64_t)occupation_random(seed, s, i) < T_occ) ? 1 : 0;
+    }
     smp.spin.assign(slots, std::vector<int8_t>(st.N));
     for (int sl = 0; sl < slots; ++sl)
       for (uint32_t i = 0; i < (uint32_t)st.N; ++i)
@@ -79,15 +95,19 @@ void init_state(State& st, int model, int q, int D, int L, const std::vector<int
   }
   for (auto& smp : st.samples) {
     smp.E_run.assign(slots, 0);
-    for (int sl = 0; sl < slots; ++sl) smp.E_run[sl] = energy(st, smp, sl);
+    smp.F_run.assign(slots, 0);
+    for (int sl = 0; sl < slots; ++sl) {
+      smp.E_run[sl] = energy(st, smp, sl);
+      if (model == 0) smp.F_run[sl] = field_sum(st, smp, sl);
+    }
   }
 }
 
 /* ---- observables (Sec. 4.1) ---- */
 
-/* Eq. (2) with x_i = 1, h_i = 0: E = -sum over bonds of J_ij s_i s_j.
- * Potts: E = -sum over bonds of J_ij delta(s_i, s_j).  Every bond is counted
- * once, as the forward bond of its lower end along d. */
+/* Bond part of Eq. (2): E_J = -sum over bonds of J_ij x_i x_j s_i s_j (EA:
+ * x = 1).  Potts: E = -sum over bonds of J_ij delta(s_i, s_j).  Every bond is
+ * counted once, as the forward bond of its lower end along d. */
 int64_t energy(const State& st, const Sample& smp, int slot) {
   const std::vector<int8_t>& s = smp.spin[slot];
   int64_t E = 0;
@@ -96,17 +116,26 @@ int64_t energy(const State& st, const Sample& smp, int slot) {
       uint32_t j = neighbour(st, i, d, +1);
       int J = smp.J[(size_t)d * st.N + i];
       if (st.model == 0)
-        E -= (int64_t)J * s[i] * s[j];
+        E -= (int64_t)J * smp.x[i] * smp.x[j] * s[i] * s[j];
       else
         E -= (s[i] == s[j]) ? J : 0;
     }
   return E;
 }
 
+/* M = sum_i x_i s_i */
 int64_t magnetisation(const State& st, const Sample& smp, int slot) {
   int64_t M = 0;
-  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) M += smp.spin[slot][i];
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) M += (int64_t)smp.x[i] * smp.spin[slot][i];
   return M;
+}
+
+/* Field part of Eq. (2) in units of |h|: F = sum_i sign(h_i) x_i s_i, so the
+ * energy is E_J - |h| F. */
+int64_t field_sum(const State& st, const Sample& smp, int slot) {
+  int64_t F = 0;
+  for (uint32_t i = 0; i < (uint32_t)st.N; ++i) F += (int64_t)smp.hs[i] * smp.x[i] * smp.spin[slot][i];
+  return F;
 }
 
 void potts_counts(const State& st, const Sample& smp, int slot, int64_t* counts) {
@@ -119,7 +148,7 @@ int64_t overlap(const State& st, const Sample& smp, int slot_a, int slot_b) {
   int64_t Q = 0;
   for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
     if (st.model == 0)
-      Q += (int64_t)smp.spin[slot_a][i] * smp.spin[slot_b][i];
+      Q += (int64_t)smp.x[i] * smp.spin[slot_a][i] * smp.spin[slot_b][i];
     else
       Q += (smp.spin[slot_a][i] == smp.spin[slot_b][i]) ? 1 : 0;
   }
@@ -134,31 +163,35 @@ void sweep_ising(const State& st, Sample& smp, int slot, int algo, double beta, 
   for (int c = 0; c < 2; ++c) {
     for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
       if (colour(st, i) != c) continue;
-      /* u = number of unsatisfied bonds (J s_i s_j = -1) at site i */
-      int u = 0;
+      if (!smp.x[i]) continue; /* an empty site carries no spin */
+      /* local field of the bonds: phi = sum_j J_ij x_j s_j; v = s_i phi */
+      int phi = 0;
       for (int d = 0; d < D; ++d) {
         uint32_t jf = neighbour(st, i, d, +1);
         uint32_t jb = neighbour(st, i, d, -1);
-        int Jf = smp.J[(size_t)d * st.N + i];
-        int Jb = smp.J[(size_t)d * st.N + jb];
-        if (Jf * s[i] * s[jf] == -1) ++u;
-        if (Jb * s[i] * s[jb] == -1) ++u;
+        phi += smp.J[(size_t)d * st.N + i] * smp.x[jf] * s[jf];
+        phi += smp.J[(size_t)d * st.N + jb] * smp.x[jb] * s[jb];
       }
-      const int dE = 4 * D - 4 * u; /* energy change if s_i flips */
+      const int v = s[i] * phi;
+      /* x = s_i (phi + h_i): the field adds +|h| if s_i h_i > 0, else -|h| */
+      double w = 0.0;
+      if (st.hmag != 0.0) w = (s[i] * smp.hs[i] > 0) ? st.hmag : -st.hmag;
+      const double x = (double)v + w;
+      const double dE = 2.0 * x; /* energy change if s_i flips */
       const uint32_t r = ising_random(st.seed, smp.s, slot, i, t);
       bool flip;
       if (algo == 0) {
         /* Metropolis: dE <= 0 is always taken; else with prob exp(-beta dE) */
-        flip = (dE <= 0) || ((uint64_t)r < table_metropolis(beta, dE));
+        flip = (dE <= 0.0) || ((uint64_t)r < table_metropolis_x(beta, x));
       } else {
         /* heat bath, Eq. (4) for the current value: keep with prob
-         * 1/(1+exp(-2 beta x)), x = s_i h_i = 2D - 2u */
-        const int x = 2 * D - 2 * u;
-        flip = !((uint64_t)r < table_heatbath(beta, x));
+         * 1/(1+exp(-2 beta x)) */
+        flip = !((uint64_t)r < table_heatbath_x(beta, x));
       }
       if (flip) {
+        smp.E_run[slot] += 2 * v;
+        smp.F_run[slot] -= 2 * smp.hs[i] * s[i];
         s[i] = (int8_t)-s[i];
-        smp.E_run[slot] += dE;
       }
     }
   }
@@ -196,8 +229,13 @@ void sweep_potts(const State& st, Sample& smp, int slot, double beta, uint64_t t
 
 /* ---- measurement rows, indexed by temperature k (not slot) ---- */
 
+static int mag_entries(const State& st) {
+  if (st.model != 0) return st.q;
+  return (st.disorder == DIS_RFIM || st.disorder == DIS_DAFF) ? 2 : 1;
+}
+
 void measure_all(const State& st, int64_t* E, int64_t* M, int64_t* Q) {
-  const int K = st.K, R = st.R, q = st.q;
+  const int K = st.K, R = st.R, q = st.q, mq = mag_entries(st);
   for (size_t si = 0; si < st.samples.size(); ++si) {
     const Sample& smp = st.samples[si];
     for (int k = 0; k < K; ++k) {
@@ -206,10 +244,14 @@ void measure_all(const State& st, int64_t* E, int64_t* M, int64_t* Q) {
         const size_t row = (si * K + k) * R + a;
         if (E) E[row] = energy(st, smp, slot);
         if (M) {
-          if (st.model == 0)
-            M[row] = magnetisation(st, smp, slot);
-          else
+          if (st.model != 0) {
             potts_counts(st, smp, slot, M + row * q);
+          } else if (mq == 2) {
+            M[row * 2] = magnetisation(st, smp, slot);
+            M[row * 2 + 1] = field_sum(st, smp, slot);
+          } else {
+            M[row] = magnetisation(st, smp, slot);
+          }
         }
       }
       if (Q && R >= 2) {
@@ -224,7 +266,7 @@ void measure_all(const State& st, int64_t* E, int64_t* M, int64_t* Q) {
 static void append_row(State& st) {
   const size_t S = st.samples.size();
   const size_t nEM = S * st.K * st.R;
-  const size_t nM = st.model == 0 ? nEM : nEM * st.q;
+  const size_t nM = nEM * (size_t)mag_entries(st);
   const size_t nQ = S * st.K;
   size_t e0 = st.ser_E.size(), m0 = st.ser_M.size(), q0 = st.ser_Q.size();
   st.ser_E.resize(e0 + nEM);

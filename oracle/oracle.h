@@ -28,7 +28,10 @@ namespace oracle {
 /* Philox4x32 with 10 rounds (Salmon et al., SC'11). */
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-enum { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6 };
+enum { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6, TAG_H = 7, TAG_X = 8 };
+
+/* Disorder kinds of the Ising-like Hamiltonian, Eq. (2) (Sec. 2.1). */
+enum { DIS_EA = 0, DIS_FERRO = 1, DIS_RFIM = 2, DIS_DAFF = 3 };
 
 uint32_t ising_random(uint64_t seed, int sample, int slot, uint32_t site, uint64_t sweep);
 uint32_t potts_random(uint64_t seed, int sample, int slot, uint32_t site, uint64_t sweep);
@@ -36,6 +39,8 @@ uint32_t pt_random(uint64_t seed, int sample, int replica, int pair, uint64_t st
 int coupling_bit(uint64_t seed, int sample, int d, uint32_t site);        /* 1 means J = -1 */
 int ising_init_bit(uint64_t seed, int sample, int slot, uint32_t site);   /* 1 means s = -1 */
 int potts_init_state(uint64_t seed, int sample, int slot, uint32_t site); /* 0..3           */
+int field_sign_bit(uint64_t seed, int sample, uint32_t site);             /* 1 means h_i < 0 */
+uint32_t occupation_random(uint64_t seed, int sample, uint32_t site);     /* plane-assembled  */
 
 /* Acceptance thresholds, values in [0, 2^32]; decision is r < T. */
 uint64_t table_metropolis(double beta, int dE);
@@ -43,18 +48,26 @@ uint64_t table_heatbath(double beta, int x);
 /* q-state Potts heat bath; n has q entries; T receives q-1 cumulative values. */
 void table_potts(double beta, int q, const int* n, uint64_t* T);
 uint64_t table_pt(double dbeta_abs, int64_t dabs);
+/* Ising-like model with a field: x = v + w (see sweep_ising). */
+uint64_t table_metropolis_x(double beta, double x); /* flip prob for dE = 2x > 0 */
+uint64_t table_heatbath_x(double beta, double x);   /* keep prob                */
 
 struct Sample {
   int s;                                    /* true sample index (drives the streams) */
   std::vector<int8_t> J;                    /* [D][N], +-1, forward bonds J_d(i)      */
+  std::vector<int8_t> x;                    /* [N] dilution, 1 = occupied              */
+  std::vector<int8_t> hs;                   /* [N] sign of the field h_i (+-1)         */
   std::vector<std::vector<int8_t>> spin;    /* [slots][N]; Ising +-1, Potts 0..q-1     */
-  std::vector<int64_t> E_run;               /* [slots] incremental energy bookkeeping */
+  std::vector<int64_t> E_run;               /* [slots] incremental (bond) energy      */
+  std::vector<int64_t> F_run;               /* [slots] incremental field sum          */
   std::vector<std::vector<int>> slot_at;    /* [R][K] temperature slot at temperature k */
   std::vector<std::vector<uint64_t>> accepted; /* [R][K-1] */
 };
 
 struct State {
-  int model;        /* 0 = EA +-J Ising, 1 = Potts */
+  int model;        /* 0 = Ising-like (Eq. 2), 1 = Potts */
+  int disorder;     /* DIS_* for the Ising-like model */
+  double hmag;      /* |h| */
   int q;            /* Potts states (4 in the library; any >= 2 here) */
   int D, L, N, R, K;
   uint64_t seed;
@@ -72,9 +85,10 @@ uint32_t neighbour(const State& st, uint32_t i, int d, int dir); /* dir +1 / -1 
 int colour(const State& st, uint32_t i);
 
 void init_state(State& st, int model, int q, int D, int L, const std::vector<int>& sample_ids,
-                int R, int K, uint64_t seed, int ferro);
+                int R, int K, uint64_t seed, int disorder, double field, double occupation);
 int64_t energy(const State& st, const Sample& smp, int slot);
 int64_t magnetisation(const State& st, const Sample& smp, int slot);
+int64_t field_sum(const State& st, const Sample& smp, int slot);
 void potts_counts(const State& st, const Sample& smp, int slot, int64_t* counts);
 int64_t overlap(const State& st, const Sample& smp, int slot_a, int slot_b);
 

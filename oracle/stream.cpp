@@ -106,6 +106,29 @@ int potts_init_state(uint64_t seed, int sample, int slot, uint32_t site) {
   return (int)(x[sample & 3] >> 30);
 }
 
+int field_sign_bit(uint64_t seed, int sample, uint32_t site) {
+  uint32_t x[4];
+  call(seed, site, 0u, ((uint32_t)TAG_H << 28) | ((uint32_t)sample >> 6), 0u, x);
+  uint64_t w = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+  return (int)((w >> (sample & 63)) & 1u);
+}
+
+/* 32-bit random of the dilution stream, assembled from its bit-planes. */
+uint32_t occupation_random(uint64_t seed, int sample, uint32_t site) {
+  const uint32_t g = (uint32_t)sample >> 6;
+  const int lane = sample & 63;
+  uint64_t W[32];
+  for (uint32_t m = 0; m < 16; ++m) {
+    uint32_t x[4];
+    call(seed, site, 0u, ((uint32_t)TAG_X << 28) | (m << 24) | g, 0u, x);
+    W[2 * m] = (uint64_t)x[0] | ((uint64_t)x[1] << 32);
+    W[2 * m + 1] = (uint64_t)x[2] | ((uint64_t)x[3] << 32);
+  }
+  uint32_t r = 0;
+  for (int p = 0; p < 32; ++p) r |= (uint32_t)((W[p] >> lane) & 1u) << (31 - p);
+  return r;
+}
+
 /* Sec. 2.2 Metropolis: a move that raises the energy by dE > 0 is taken with
  * probability exp(-beta dE); here as an integer threshold against 32-bit r. */
 uint64_t table_metropolis(double beta, int dE) {
@@ -130,6 +153,18 @@ void table_potts(double beta, int q, const int* n, uint64_t* T) {
   for (int k = 1; k < q; ++k) S[k] = S[k - 1] + w[k];
   double Z = S[q - 1];
   for (int k = 0; k < q - 1; ++k) T[k] = (uint64_t)std::floor(std::ldexp(S[k] / Z, 32));
+}
+
+/* Eq. (2) with a field: dE = 2x for x = v + w (v integer, w = +-|h|). */
+uint64_t table_metropolis_x(double beta, double x) {
+  const double dE = 2.0 * x;
+  double p = std::exp(-beta * dE);
+  return (uint64_t)std::floor(std::ldexp(p, 32));
+}
+
+uint64_t table_heatbath_x(double beta, double x) {
+  double p = 1.0 / (1.0 + std::exp(-2.0 * beta * x));
+  return (uint64_t)std::floor(std::ldexp(p, 32));
 }
 
 /* Parallel-tempering rejection branch: probability exp(-|dbeta| |d|). */
