@@ -57,7 +57,8 @@
  *   output (x0,x1,x2,x3).  Every random number is a function of the seed and
  *   of its coordinates only, so results do not depend on memory layout,
  *   kernel choice, launch shape or on how sweeps are split across calls.
- *   Tags: SPIN = 1, J = 2, INIT = 3, POTTS = 4, PINIT = 5, PT = 6.
+ *   Tags: SPIN = 1, J = 2, INIT = 3, POTTS = 4, PINIT = 5, PT = 6, H = 7,
+ *   X = 8.
  *   Sample s lives in group g = s >> 6 at lane l = s & 63.
  *
  *   Ising update random r(s, sigma, i, t), t = absolute sweep index:
@@ -72,7 +73,15 @@
  *
  *   Couplings: J_d(i) of sample s is -1 iff bit l of (x0 | x1 << 32) of
  *     Philox(key, c0 = i, c1 = d, c2 = (J << 28) | g, c3 = 0) is set.
- *     (IANUS_DISORDER_FERRO: every J = +1.)  Both models use this stream.
+ *     (IANUS_DISORDER_FERRO and RFIM: every J = +1; DAFF: every J = -1.)
+ *     Both models use this stream.
+ *   Random-field signs (RFIM): h_i of sample s is -|h| iff bit l of
+ *     (x0 | x1 << 32) of Philox(key, c0 = i, c1 = 0, c2 = (H << 28) | g,
+ *     c3 = 0) is set, else +|h|.  (DAFF: h_i = +|h| everywhere.)
+ *   Dilution (DAFF): site i of sample s is occupied (x_i = 1) iff
+ *     r_x < floor(ldexp(occupation, 32)), r_x assembled from bit-planes as the
+ *     update random, with c1 = 0 and c2 = (X << 28) | (m << 24) | g,
+ *     c3 = 0.  (Other disorder kinds: x_i = 1.)
  *   Initial Ising spin of (s, sigma, i): s = -1 iff bit l of (x0 | x1 << 32)
  *     of Philox(key, c0 = i, c1 = 0, c2 = (INIT << 28) | (sigma << 12) | g,
  *     c3 = 0) is set.
@@ -113,10 +122,23 @@
  *     usual acceptance min(1, exp(db * (E_A - E_B))).  Pairs are visited for
  *     k = 0 .. n_temps-2 in ascending order within one swap step.
  *
+ * Ising-like models with fields and dilution (Eq. (2): RFIM, DAFF).  An
+ * empty site (x_i = 0) carries no spin and is never updated.  For an occupied
+ * site, v = s_i sum_j J_ij x_j s_j (an integer in -2D..2D) and
+ * x = (double)v + w with w = +|h| when s_i h_i > 0 and w = -|h| otherwise
+ * (w = +0.0 when |h| = 0); dE = 2.0 * x.
+ *   Metropolis: flip iff dE <= 0 or r < floor(ldexp(exp(-beta * dE), 32));
+ *   heat bath: keep iff r < floor(ldexp(1.0 / (1.0 + exp(-2.0 * beta * x)), 32)).
+ * With |h| = 0 and x_i = 1 these are the EA tables above (v = 2D - 2u).
+ *
  * Measurements (Sec. 4.1): exact int64 values.
  *   Ising: E = -sum_bonds J s s, M = sum_i s_i, Q = sum_i s_i^0 s_i^1.
  *   Potts: E = -sum_bonds J delta(s_i, s_j); "magnetisation" = the four
  *     state counts n_k; Q = sum_i delta(s_i^0, s_i^1).
+ *   RFIM / DAFF: "energy" = the bond part E_J = -sum_bonds J x_i x_j s_i s_j;
+ *     "magnetisation" = two values, M = sum_i x_i s_i and the field sum
+ *     F = sum_i sign(h_i) x_i s_i, so that E = E_J - |h| F;
+ *     Q = sum_i x_i s_i^0 s_i^1.
  */
 #ifndef IANUS_H
 #define IANUS_H
@@ -128,7 +150,7 @@
 extern "C" {
 #endif
 
-#define IANUS_ABI_VERSION 1u
+#define IANUS_ABI_VERSION 2u
 
 typedef struct ianus_lattice ianus_lattice; /* opaque, library-owned */
 
@@ -150,7 +172,13 @@ typedef enum {
   IANUS_LAYOUT_BITS64 = 2, /* Ising: one uint64 per site holds 64 samples   */
   IANUS_LAYOUT_U8X4 = 3    /* Potts: one uint32 per site holds 4 samples    */
 } ianus_layout;
-typedef enum { IANUS_DISORDER_PM_J = 0, IANUS_DISORDER_FERRO = 1 } ianus_disorder;
+typedef enum {
+  IANUS_DISORDER_PM_J = 0,   /* EA: J = +-1 i.i.d., no field, no dilution        */
+  IANUS_DISORDER_FERRO = 1,  /* J = +1, no field, no dilution (tests)             */
+  IANUS_DISORDER_RFIM = 2,   /* random-field Ising model: J = +1, h_i = +-|h|     */
+  IANUS_DISORDER_DAFF = 3    /* diluted antiferromagnet in a field: J = -1,
+                                h_i = |h|, x_i = 1 with probability occupation */
+} ianus_disorder;
 
 typedef struct {
   uint32_t abi_version;     /* must equal IANUS_ABI_VERSION                 */
@@ -167,6 +195,8 @@ typedef struct {
   void* device_buffer;      /* optional caller-owned device memory, >= ianus_required_bytes */
   size_t device_buffer_bytes;
   void* cuda_stream;        /* cudaStream_t; NULL = the legacy default stream */
+  double field;             /* |h| >= 0 (RFIM, DAFF); must be 0 otherwise      */
+  double occupation;        /* DAFF site occupation probability in [0, 1]      */
 } ianus_config;
 
 /* Device bytes a lattice with this configuration uses (state, couplings,
@@ -178,8 +208,11 @@ size_t ianus_required_bytes(const ianus_config* cfg);
  * the couplings and the initial configuration from the seed on the device
  * (Sec. 2.1: quenched J_ij; initial state from the INIT/PINIT streams).
  * Sweep and swap counters start at 0, temperatures at the identity order.
- * Errors: EINVAL (bad cfg, out NULL, buffer too small), ENOMEM, ECUDA,
- * EUNSUPPORTED (e.g. Potts with layout I8/BITS64).  On error *out = NULL. */
+ * Errors: EINVAL (bad cfg, out NULL, buffer too small; field not finite or
+ * < 0, field != 0 for PM_J/FERRO, occupation outside [0, 1] for DAFF, Potts
+ * with RFIM/DAFF), ENOMEM, ECUDA, EUNSUPPORTED (e.g. Potts with layout
+ * I8/BITS64, DAFF with layout BITS64; AUTO picks I8 for DAFF).  On error
+ * *out = NULL. */
 ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out);
 
 /* Runs nsweeps full sweeps (Sec. 2.2: every site once; Sec. 3.1: colour 0
@@ -198,7 +231,9 @@ ianus_status ianus_sweep(ianus_lattice* lat, int32_t algo, const double* beta,
  * comment above): measures the exact energies on the device, then every
  * chain (sample, replica) visits its temperature pairs in ascending order.
  * Uses the beta array of the last ianus_sweep.  Asynchronous.  Errors:
- * EINVAL (n_temps == 1 or no prior sweep), EUNSUPPORTED (Potts), ECUDA. */
+ * EINVAL (n_temps == 1 or no prior sweep), EUNSUPPORTED (Potts, RFIM,
+ * DAFF: their energies E_J - |h| F are not on the integer grid of the swap
+ * table), ECUDA. */
 ianus_status ianus_pt_swap(ianus_lattice* lat);
 
 /* Fused loop: repeats { ianus_sweep(swap_every sweeps, measure_every);
@@ -214,6 +249,7 @@ ianus_status ianus_sweep_pt(ianus_lattice* lat, int32_t algo, const double* beta
  *   energy        int64 [n_samples][n_temps][n_replicas]
  *   magnetisation int64 [n_samples][n_temps][n_replicas]      (Ising)
  *                 int64 [n_samples][n_temps][n_replicas][4]   (Potts counts)
+ *                 int64 [n_samples][n_temps][n_replicas][2]   (RFIM, DAFF: M, F)
  *   overlap       int64 [n_samples][n_temps]  (replicas 0 and 1; needs
  *                 n_replicas >= 2, else EINVAL when non-NULL). */
 ianus_status ianus_measure(ianus_lattice* lat, int64_t* energy,
@@ -242,6 +278,17 @@ ianus_status ianus_set_spins_i8(ianus_lattice* lat, const int8_t* host);
 ianus_status ianus_get_couplings_i8(ianus_lattice* lat, int8_t* host);
 /* Overwrites the couplings (values must be +-1).  Used for gauge tests. */
 ianus_status ianus_set_couplings_i8(ianus_lattice* lat, const int8_t* host);
+/* Site disorder of the Ising-like models (Eq. (2)): hsign int8 [n_samples][N]
+ * = sign of h_i (+-1; +1 everywhere unless RFIM) and occupied int8
+ * [n_samples][N] = x_i (0 or 1; 1 everywhere unless DAFF).  Either pointer
+ * may be NULL.  Potts lattices: EUNSUPPORTED.  Synchronous. */
+ianus_status ianus_get_sites_i8(ianus_lattice* lat, int8_t* hsign, int8_t* occupied);
+/* Overwrites the site disorder of a field model (RFIM, DAFF; else
+ * EUNSUPPORTED).  hsign values must be +-1 and occupied values 0 or 1 (else
+ * EINVAL); the bit-sliced layout holds no dilution, so occupied must be all
+ * 1 there (else EUNSUPPORTED).  Either pointer may be NULL (kept).  Used for
+ * the global-flip and gauge tests. */
+ianus_status ianus_set_sites_i8(ianus_lattice* lat, const int8_t* hsign, const int8_t* occupied);
 
 /* Parallel-tempering state: slot_at int32 [n_samples][n_replicas][n_temps]
  * (the temperature slot tslot holding temperature k), accepted uint64
@@ -367,6 +414,12 @@ size_t ianus_table_potts(double beta, uint64_t* out, size_t n);
 /* PT: out[m-1] = T_PT(|d| = 4 m) = floor(ldexp(exp(-|db| * 4m), 32)) for
  * m = 1..n, db = beta_k - beta_k1.  Returns n, or 0 on bad arguments. */
 size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
+/* Field models (Eq. (2), RFIM / DAFF rules above): out[(v + 2 dim) * 2 + f]
+ * for v = -2 dim..2 dim and f = 1 when s_i h_i > 0, else 0; field = |h|.
+ * Metropolis (algo 0): the flip threshold, 2^32 where dE = 2x <= 0.  Heat
+ * bath (algo 1): the keep threshold.  n must be >= 2 (4 dim + 1).  Returns
+ * the count written, or 0 on bad arguments. */
+size_t ianus_table_field(int32_t dim, int32_t algo, double beta, double field, uint64_t* out, size_t n);
 
 #ifdef __cplusplus
 }

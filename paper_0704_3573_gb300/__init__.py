@@ -19,18 +19,19 @@ import numpy as np
 
 from . import build as _build
 
-ABI_VERSION = 1
+ABI_VERSION = 2
 
 EA_PM_J, POTTS4_J = 0, 1
 METROPOLIS, HEATBATH = 0, 1
 LAYOUT_AUTO, LAYOUT_I8, LAYOUT_BITS64, LAYOUT_U8X4 = 0, 1, 2, 3
-DISORDER_PM_J, DISORDER_FERRO = 0, 1
+DISORDER_PM_J, DISORDER_FERRO, DISORDER_RFIM, DISORDER_DAFF = 0, 1, 2, 3
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = range(7)
 
 _MODELS = {"ea": EA_PM_J, "potts": POTTS4_J}
 _ALGOS = {"metropolis": METROPOLIS, "heatbath": HEATBATH}
 _LAYOUTS = {"auto": LAYOUT_AUTO, "i8": LAYOUT_I8, "bits64": LAYOUT_BITS64, "u8x4": LAYOUT_U8X4}
+_DISORDERS = {"pm_j": DISORDER_PM_J, "ferro": DISORDER_FERRO, "rfim": DISORDER_RFIM, "daff": DISORDER_DAFF}
 
 EXPORTS = [
     "ianus_required_bytes", "ianus_lattice_create", "ianus_sweep", "ianus_pt_swap", "ianus_sweep_pt",
@@ -38,7 +39,7 @@ EXPORTS = [
     "ianus_set_couplings_i8", "ianus_get_pt_state", "ianus_get_sweeps", "ianus_get_state", "ianus_set_state",
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
-    "ianus_set_graphs", "ianus_set_resident",
+    "ianus_set_graphs", "ianus_set_resident", "ianus_get_sites_i8", "ianus_set_sites_i8", "ianus_table_field",
 ]
 
 
@@ -58,6 +59,8 @@ class IanusConfig(C.Structure):
         ("device_buffer", C.c_void_p),
         ("device_buffer_bytes", C.c_size_t),
         ("cuda_stream", C.c_void_p),
+        ("field", C.c_double),
+        ("occupation", C.c_double),
     ]
 
 
@@ -113,6 +116,9 @@ def lib(build_if_missing: bool = True):
         "ianus_set_block_words": (i32, [vp, u32]),
         "ianus_set_graphs": (i32, [vp, i32]),
         "ianus_set_resident": (i32, [vp, i32]),
+        "ianus_get_sites_i8": (i32, [vp, vp, vp]),
+        "ianus_set_sites_i8": (i32, [vp, vp, vp]),
+        "ianus_table_field": (sz, [i32, i32, C.c_double, C.c_double, vp, sz]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -155,6 +161,15 @@ def table_pt(beta_k: float, beta_k1: float, n: int) -> np.ndarray:
     return out
 
 
+def table_field(dim: int, algo: int, beta: float, field: float) -> np.ndarray:
+    """Thresholds of the field models, indexed [(v + 2 dim) * 2 + f]."""
+    out = np.zeros(32, dtype=np.uint64)
+    n = lib().ianus_table_field(dim, algo, beta, field, _ptr(out), out.size)
+    if n == 0:
+        raise ValueError("bad table arguments")
+    return out[:n]
+
+
 class Lattice:
     """A batch of lattices: n_samples disorder samples x n_temps x n_replicas.
 
@@ -163,7 +178,8 @@ class Lattice:
     """
 
     def __init__(self, model="ea", dim=3, L=16, n_samples=1, n_replicas=1, n_temps=1, seed=0,
-                 layout="auto", ferro=False, series_capacity=0, stream=None, device=None):
+                 layout="auto", ferro=False, series_capacity=0, stream=None, device=None, disorder=None,
+                 field=0.0, occupation=1.0):
         import torch
 
         if not torch.cuda.is_available():
@@ -173,7 +189,11 @@ class Lattice:
         self.dim, self.L = dim, L
         self.N = L ** dim
         self.S, self.R, self.K = n_samples, n_replicas, n_temps
-        self.mq = 4 if self.model == POTTS4_J else 1
+        if disorder is None:
+            disorder = DISORDER_FERRO if ferro else DISORDER_PM_J
+        self.disorder = _DISORDERS[disorder] if isinstance(disorder, str) else int(disorder)
+        self.field, self.occupation = float(field), float(occupation)
+        self.mq = 4 if self.model == POTTS4_J else (2 if self.disorder in (DISORDER_RFIM, DISORDER_DAFF) else 1)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(dev)
@@ -184,7 +204,9 @@ class Lattice:
         cfg.dim, cfg.L = dim, L
         cfg.n_samples, cfg.n_replicas, cfg.n_temps = n_samples, n_replicas, n_temps
         cfg.layout = _LAYOUTS[layout] if isinstance(layout, str) else int(layout)
-        cfg.disorder = DISORDER_FERRO if ferro else DISORDER_PM_J
+        cfg.disorder = self.disorder
+        cfg.field = self.field
+        cfg.occupation = self.occupation
         cfg.series_capacity = series_capacity
         cfg.seed = seed & 0xFFFFFFFFFFFFFFFF
         nbytes = self._lib.ianus_required_bytes(C.byref(cfg))
@@ -243,7 +265,7 @@ class Lattice:
         """(E [S,K,R], M [S,K,R] or [S,K,R,4], Q [S,K] or None), exact int64."""
         S, K, R = self.S, self.K, self.R
         E = np.zeros((S, K, R), dtype=np.int64)
-        M = np.zeros((S, K, R) if self.mq == 1 else (S, K, R, 4), dtype=np.int64)
+        M = np.zeros((S, K, R) if self.mq == 1 else (S, K, R, self.mq), dtype=np.int64)
         want_q = (R >= 2) if overlap is None else overlap
         Q = np.zeros((S, K), dtype=np.int64) if want_q else None
         _check(self._lib.ianus_measure(self._h, _ptr(E), _ptr(M), _ptr(Q)), "ianus_measure")
@@ -254,7 +276,7 @@ class Lattice:
         cap = min(max_rows, self.cfg.series_capacity or 1024)
         sw = np.zeros(cap, dtype=np.uint64)
         E = np.zeros((cap, S, K, R), dtype=np.int64)
-        M = np.zeros((cap, S, K, R) if self.mq == 1 else (cap, S, K, R, 4), dtype=np.int64)
+        M = np.zeros((cap, S, K, R) if self.mq == 1 else (cap, S, K, R, self.mq), dtype=np.int64)
         Q = np.zeros((cap, S, K), dtype=np.int64) if R >= 2 else None
         n = C.c_size_t()
         _check(self._lib.ianus_read_series(self._h, _ptr(sw), _ptr(E), _ptr(M), _ptr(Q), cap, C.byref(n),
@@ -279,6 +301,18 @@ class Lattice:
     def set_couplings(self, a):
         a = np.ascontiguousarray(a, dtype=np.int8).reshape(self.S, self.dim, self.N)
         _check(self._lib.ianus_set_couplings_i8(self._h, _ptr(a)), "ianus_set_couplings_i8")
+
+    def sites(self):
+        """(sign of h_i [S, N], x_i [S, N]) as int8 (Ising-like models)."""
+        hs = np.zeros((self.S, self.N), dtype=np.int8)
+        x = np.zeros((self.S, self.N), dtype=np.int8)
+        _check(self._lib.ianus_get_sites_i8(self._h, _ptr(hs), _ptr(x)), "ianus_get_sites_i8")
+        return hs, x
+
+    def set_sites(self, hs=None, x=None):
+        hs = None if hs is None else np.ascontiguousarray(hs, dtype=np.int8).reshape(self.S, self.N)
+        x = None if x is None else np.ascontiguousarray(x, dtype=np.int8).reshape(self.S, self.N)
+        _check(self._lib.ianus_set_sites_i8(self._h, _ptr(hs), _ptr(x)), "ianus_set_sites_i8")
 
     def pt_state(self):
         S, R, K = self.S, self.R, self.K

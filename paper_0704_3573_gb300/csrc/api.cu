@@ -22,10 +22,13 @@ constexpr uint64_t kStateMagic = 0x31534e4149ull;  // "IANS1"
 struct Sizes {
   int model, D, L, S, R, K, slots, layout, G, Q4, mq;
   uint32_t N, cap, pt_cap;
-  size_t off_spins, off_J, off_thr, off_tp, off_ptab, off_pttab, off_ptsign, off_slot, off_temp, off_acc_pt,
-      off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
-  size_t spins_bytes, J_bytes;
+  bool field;
+  size_t off_spins, off_J, off_thr, off_tp, off_fthr, off_ftp, off_sites, off_ptab, off_pttab, off_ptsign, off_slot,
+      off_temp, off_acc_pt, off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
+  size_t spins_bytes, J_bytes, sites_bytes;
 };
+
+constexpr size_t kMaxSmemPerBlock = 227 * 1024;
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
@@ -39,15 +42,26 @@ int plan(const ianus_config* c, Sizes& z) {
   if (c->n_samples < 1 || c->n_samples >= (1 << 18)) return IANUS_EINVAL;
   if (c->n_replicas < 1 || c->n_temps < 1) return IANUS_EINVAL;
   if ((long long)c->n_replicas * c->n_temps >= 4096) return IANUS_EINVAL;
-  if (c->disorder != IANUS_DISORDER_PM_J && c->disorder != IANUS_DISORDER_FERRO) return IANUS_EINVAL;
+  if (c->disorder < IANUS_DISORDER_PM_J || c->disorder > IANUS_DISORDER_DAFF) return IANUS_EINVAL;
+  const bool field = c->disorder == IANUS_DISORDER_RFIM || c->disorder == IANUS_DISORDER_DAFF;
+  if (!std::isfinite(c->field) || c->field < 0.0) return IANUS_EINVAL;
+  if (!field && c->field != 0.0) return IANUS_EINVAL;
+  if (c->disorder == IANUS_DISORDER_DAFF && !(c->occupation >= 0.0 && c->occupation <= 1.0)) return IANUS_EINVAL;
+  if (field && c->model != IANUS_EA_PM_J) return IANUS_EINVAL;
   uint64_t N = 1;
   for (int d = 0; d < c->dim; ++d) N *= (uint64_t)c->L;
   if (N >= (1ull << 31)) return IANUS_EINVAL;
   int layout = c->layout;
-  if (layout == IANUS_LAYOUT_AUTO) layout = c->model == IANUS_EA_PM_J ? IANUS_LAYOUT_BITS64 : IANUS_LAYOUT_U8X4;
+  if (layout == IANUS_LAYOUT_AUTO)
+    layout = c->model == IANUS_POTTS4_J ? IANUS_LAYOUT_U8X4
+             : c->disorder == IANUS_DISORDER_DAFF ? IANUS_LAYOUT_I8 : IANUS_LAYOUT_BITS64;
   if (layout < IANUS_LAYOUT_I8 || layout > IANUS_LAYOUT_U8X4) return IANUS_EINVAL;
   if (c->model == IANUS_EA_PM_J && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (c->model == IANUS_POTTS4_J && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
+  if (c->disorder == IANUS_DISORDER_DAFF && layout == IANUS_LAYOUT_BITS64) return IANUS_EUNSUPPORTED;
+  if (layout == IANUS_LAYOUT_BITS64 &&  // the sweep stages one block's threshold planes in shared memory
+      (size_t)c->n_replicas * kPlanes * (field ? kFieldPlaneClasses : kMaxClasses) * 8 > kMaxSmemPerBlock)
+    return IANUS_EUNSUPPORTED;
   z.model = c->model;
   z.D = c->dim;
   z.L = c->L;
@@ -59,7 +73,8 @@ int plan(const ianus_config* c, Sizes& z) {
   z.N = (uint32_t)N;
   z.G = (z.S + 63) / 64;
   z.Q4 = (z.S + 3) / 4;
-  z.mq = c->model == IANUS_POTTS4_J ? 4 : 1;
+  z.field = field;
+  z.mq = c->model == IANUS_POTTS4_J ? 4 : (field ? 2 : 1);
   z.cap = c->series_capacity ? c->series_capacity : kDefaultSeries;
   z.pt_cap = z.K > 1 ? (uint32_t)std::min<uint64_t>((uint64_t)z.D * N / 2 + 1, kPtCapMax) : 0;
   if (layout == IANUS_LAYOUT_I8) {
@@ -72,6 +87,7 @@ int plan(const ianus_config* c, Sizes& z) {
     z.spins_bytes = (size_t)z.slots * z.Q4 * N * 4;
     z.J_bytes = (size_t)z.Q4 * z.D * N * 4;
   }
+  z.sites_bytes = !field ? 0 : layout == IANUS_LAYOUT_I8 ? (size_t)2 * z.S * N : (size_t)z.G * N * 8;
   const size_t SKR = (size_t)z.S * z.K * z.R;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -82,7 +98,10 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_spins = take(z.spins_bytes);
   z.off_J = take(z.J_bytes);
   z.off_thr = take((size_t)z.K * kMaxClasses * 8 + sizeof(UniformLut));  // class thresholds, then the uniform tables
-  z.off_tp = take(layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
+  z.off_tp = take(layout == IANUS_LAYOUT_BITS64 && !field ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
+  z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 : 0);
+  z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
+  z.off_sites = take(z.sites_bytes);
   z.off_ptab = take(layout == IANUS_LAYOUT_U8X4 ? (size_t)z.K * 65536 * 16 : 0);
   z.off_pttab = take((size_t)std::max(z.K - 1, 0) * z.pt_cap * 8);
   z.off_ptsign = take((size_t)std::max(z.K - 1, 1));
@@ -133,7 +152,15 @@ bool beta_ok(const double* beta, int K) {
 // Rebuild and upload the acceptance tables for (algo, beta).
 int upload_tables(Lattice* lat, int algo, const double* beta) {
   const int K = lat->K;
-  if (lat->model == IANUS_EA_PM_J) {
+  if (lat->field) {
+    std::vector<uint64_t> fthr((size_t)K * kFieldClasses);
+    for (int k = 0; k < K; ++k) field_thresholds(lat->D, algo, beta[k], lat->hmag, &fthr[(size_t)k * kFieldClasses]);
+    CK(cudaMemcpyAsync(lat->fthr, fthr.data(), fthr.size() * 8, cudaMemcpyHostToDevice, lat->stream));
+    if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_field_planes(*lat));
+    lat->ulut_ok = false;
+    lat->jit = nullptr;
+    lat->jit_algo = -1;
+  } else if (lat->model == IANUS_EA_PM_J) {
     std::vector<uint64_t> thr((size_t)K * kMaxClasses);
     for (int k = 0; k < K; ++k) class_thresholds(lat->D, algo, beta[k], &thr[(size_t)k * kMaxClasses]);
     CK(cudaMemcpyAsync(lat->thr, thr.data(), thr.size() * 8, cudaMemcpyHostToDevice, lat->stream));
@@ -186,7 +213,7 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     }
     CK(cudaMemcpyAsync(lat->ptab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice, lat->stream));
   }
-  if (K > 1) {
+  if (K > 1 && !lat->field) {
     // PT tables: T(m) for |d| = 4m until the first zero (or the largest
     // possible |d|/4 = D N / 2).
     std::vector<uint64_t> pt((size_t)(K - 1) * lat->pt_cap, 0);
@@ -343,7 +370,8 @@ int sweeps_graphed(Lattice* lat, int inv, uint64_t n) {
 struct StateHeader {
   uint64_t magic;
   uint32_t version, model, dim, L, S, R, K, layout, disorder, pad;
-  uint64_t seed, sweeps, steps, spins_bytes, J_bytes;
+  uint64_t seed, sweeps, steps, spins_bytes, J_bytes, sites_bytes;
+  double field, occupation;
 };
 
 }  // namespace
@@ -377,6 +405,9 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->Q4 = z.Q4;
   lat->N = z.N;
   lat->mq = z.mq;
+  lat->disorder = cfg->disorder;
+  lat->field = z.field;
+  lat->hmag = cfg->field;
   lat->cap = z.cap;
   lat->pt_cap = z.pt_cap;
   lat->pt_len = z.pt_cap;
@@ -420,6 +451,11 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->J = b + z.off_J;
   lat->thr = (uint64_t*)(b + z.off_thr);
   lat->tp = (uint64_t*)(b + z.off_tp);
+  lat->fthr = (uint64_t*)(b + z.off_fthr);
+  lat->ftp = (uint64_t*)(b + z.off_ftp);
+  lat->hs = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) : nullptr;
+  lat->occ = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) + (size_t)z.S * z.N : nullptr;
+  lat->hbits = z.field && z.layout == IANUS_LAYOUT_BITS64 ? (uint64_t*)(b + z.off_sites) : nullptr;
   lat->ptab = (uint4*)(b + z.off_ptab);
   lat->pttab = (uint64_t*)(b + z.off_pttab);
   lat->pt_sign = (int8_t*)(b + z.off_ptsign);
@@ -456,14 +492,17 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
             cudaSuccess)
       return bail(IANUS_ECUDA);
   }
-  const int ferro = cfg->disorder == IANUS_DISORDER_FERRO;
+  // couplings: the J stream (EA), +1 (ferromagnet, RFIM) or -1 (DAFF)
+  const int jmode = cfg->disorder == IANUS_DISORDER_PM_J ? 0 : (cfg->disorder == IANUS_DISORDER_DAFF ? 2 : 1);
   cudaError_t e;
   if (lat->layout == IANUS_LAYOUT_I8)
-    e = launch_init_i8(*lat, ferro);
+    e = launch_init_i8(*lat, jmode);
   else if (lat->layout == IANUS_LAYOUT_BITS64)
-    e = launch_init_bits(*lat, ferro);
+    e = launch_init_bits(*lat, jmode);
   else
-    e = launch_init_potts(*lat, ferro);
+    e = launch_init_potts(*lat, jmode);
+  if (e == cudaSuccess && lat->field)
+    e = lat->layout == IANUS_LAYOUT_I8 ? launch_init_sites_i8(*lat, cfg->occupation) : launch_init_sites_bits(*lat);
   if (e != cudaSuccess || cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
   *out = reinterpret_cast<ianus_lattice*>(lat);
   return IANUS_OK;
@@ -517,7 +556,7 @@ ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uin
 ianus_status ianus_pt_swap(ianus_lattice* h) {
   GET_LAT(h);
   if (lat->K < 2 || !lat->tables_ok) return IANUS_EINVAL;
-  if (lat->model != IANUS_EA_PM_J) return IANUS_EUNSUPPORTED;
+  if (lat->model != IANUS_EA_PM_J || lat->field) return IANUS_EUNSUPPORTED;
   return (ianus_status)do_pt_swap(lat);
 }
 
@@ -526,7 +565,7 @@ ianus_status ianus_sweep_pt(ianus_lattice* h, int32_t algo, const double* beta, 
   GET_LAT(h);
   if (swap_every == 0 || nsweeps % swap_every != 0) return IANUS_EINVAL;
   if (lat->K < 2) return IANUS_EINVAL;
-  if (lat->model != IANUS_EA_PM_J) return IANUS_EUNSUPPORTED;
+  if (lat->model != IANUS_EA_PM_J || lat->field) return IANUS_EUNSUPPORTED;
   for (uint64_t n = 0; n < nsweeps; n += swap_every) {
     ianus_status st = ianus_sweep(h, algo, beta, swap_every, measure_every);
     if (st) return st;
@@ -644,6 +683,66 @@ ianus_status ianus_set_couplings_i8(ianus_lattice* h, const int8_t* host) {
   return staged_set(lat, host, bytes, fn);
 }
 
+ianus_status ianus_get_sites_i8(ianus_lattice* h, int8_t* hsign, int8_t* occupied) {
+  GET_LAT(h);
+  if (lat->model != IANUS_EA_PM_J) return IANUS_EUNSUPPORTED;
+  const size_t n = (size_t)lat->S * lat->N;
+  if (!lat->field) {
+    if (hsign) std::memset(hsign, 1, n);
+    if (occupied) std::memset(occupied, 1, n);
+    return IANUS_OK;
+  }
+  std::vector<int8_t> hs(n), occ(n, 1);
+  ianus_status st;
+  if (lat->layout == IANUS_LAYOUT_I8) {
+    int8_t* d = nullptr;
+    if (cudaMalloc(&d, 2 * n) != cudaSuccess) {
+      cudaGetLastError();
+      return IANUS_ENOMEM;
+    }
+    cudaError_t e = launch_get_sites_i8(*lat, d, d + n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d, n, cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(occ.data(), d + n, n, cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    cudaFree(d);
+    st = e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
+  } else {
+    st = staged_get(lat, hs.data(), n, launch_get_sites_bits);
+  }
+  if (st) return st;
+  if (hsign) std::memcpy(hsign, hs.data(), n);
+  if (occupied) std::memcpy(occupied, occ.data(), n);
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_sites_i8(ianus_lattice* h, const int8_t* hsign, const int8_t* occupied) {
+  GET_LAT(h);
+  if (!lat->field) return IANUS_EUNSUPPORTED;
+  const size_t n = (size_t)lat->S * lat->N;
+  for (size_t i = 0; hsign && i < n; ++i)
+    if (hsign[i] != 1 && hsign[i] != -1) return IANUS_EINVAL;
+  for (size_t i = 0; occupied && i < n; ++i)
+    if (occupied[i] != 0 && occupied[i] != 1) return IANUS_EINVAL;
+  if (lat->layout == IANUS_LAYOUT_BITS64) {
+    for (size_t i = 0; occupied && i < n; ++i)
+      if (occupied[i] != 1) return IANUS_EUNSUPPORTED;
+    if (!hsign) return IANUS_OK;
+    return staged_set(lat, hsign, n, launch_set_sites_bits);
+  }
+  int8_t* d = nullptr;
+  if (cudaMalloc(&d, 2 * n) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ENOMEM;
+  }
+  cudaError_t e = launch_get_sites_i8(*lat, d, d + n);  // keep what is not given
+  if (e == cudaSuccess && hsign) e = cudaMemcpyAsync(d, hsign, n, cudaMemcpyHostToDevice, lat->stream);
+  if (e == cudaSuccess && occupied) e = cudaMemcpyAsync(d + n, occupied, n, cudaMemcpyHostToDevice, lat->stream);
+  if (e == cudaSuccess) e = launch_set_sites_i8(*lat, d, d + n);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+  cudaFree(d);
+  return e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
+}
+
 ianus_status ianus_get_pt_state(ianus_lattice* h, int32_t* slot_at, uint64_t* accepted, uint64_t* swap_steps) {
   GET_LAT(h);
   const size_t n = (size_t)lat->S * lat->R * lat->K;
@@ -669,7 +768,7 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   plan(&lat->cfg, z);
   const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
   const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
-  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes;
+  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes;
   if (n) *n = need;
   if (!host_buf) return IANUS_OK;
   if (cap < need) return IANUS_EINVAL;
@@ -689,6 +788,9 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   hd.steps = lat->steps;
   hd.spins_bytes = z.spins_bytes;
   hd.J_bytes = z.J_bytes;
+  hd.sites_bytes = z.sites_bytes;
+  hd.field = lat->cfg.field;
+  hd.occupation = lat->cfg.occupation;
   uint8_t* o = (uint8_t*)host_buf;
   std::memcpy(o, &hd, sizeof hd);
   o += sizeof hd;
@@ -701,6 +803,8 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   CK(cudaMemcpyAsync(o, lat->J, z.J_bytes, cudaMemcpyDeviceToHost, lat->stream));
   o += z.J_bytes;
   CK(cudaMemcpyAsync(o, lat->spins, z.spins_bytes, cudaMemcpyDeviceToHost, lat->stream));
+  o += z.spins_bytes;
+  if (z.sites_bytes) CK(cudaMemcpyAsync(o, lat->base + z.off_sites, z.sites_bytes, cudaMemcpyDeviceToHost, lat->stream));
   CK(cudaStreamSynchronize(lat->stream));
   return IANUS_OK;
 }
@@ -712,14 +816,16 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   plan(&lat->cfg, z);
   const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
   const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
-  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes;
+  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes;
   if (n < need) return IANUS_ESTATE;
   StateHeader hd;
   std::memcpy(&hd, host_buf, sizeof hd);
   if (hd.magic != kStateMagic || hd.version != IANUS_ABI_VERSION || hd.model != (uint32_t)lat->model ||
       hd.dim != (uint32_t)lat->D || hd.L != (uint32_t)lat->L || hd.S != (uint32_t)lat->S ||
       hd.R != (uint32_t)lat->R || hd.K != (uint32_t)lat->K || hd.layout != (uint32_t)lat->layout ||
-      hd.seed != lat->cfg.seed || hd.spins_bytes != z.spins_bytes || hd.J_bytes != z.J_bytes)
+      hd.seed != lat->cfg.seed || hd.spins_bytes != z.spins_bytes || hd.J_bytes != z.J_bytes ||
+      hd.disorder != (uint32_t)lat->cfg.disorder || hd.sites_bytes != z.sites_bytes ||
+      std::memcmp(&hd.field, &lat->cfg.field, sizeof(double)) != 0)
     return IANUS_ESTATE;
   const uint8_t* in = (const uint8_t*)host_buf + sizeof hd;
   lat->sticky = 0;
@@ -732,6 +838,8 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   CK(cudaMemcpyAsync(lat->J, in, z.J_bytes, cudaMemcpyHostToDevice, lat->stream));
   in += z.J_bytes;
   CK(cudaMemcpyAsync(lat->spins, in, z.spins_bytes, cudaMemcpyHostToDevice, lat->stream));
+  in += z.spins_bytes;
+  if (z.sites_bytes) CK(cudaMemcpyAsync(lat->base + z.off_sites, in, z.sites_bytes, cudaMemcpyHostToDevice, lat->stream));
   CK(cudaMemsetAsync(lat->err, 0, 4, lat->stream));
   CK(cudaStreamSynchronize(lat->stream));
   lat->sweeps = hd.sweeps;

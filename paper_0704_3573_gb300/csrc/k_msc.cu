@@ -115,9 +115,145 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits(const BitsParams p) {
 }
 
 
+// Random-field model (Eq. 2 with h_i = +-|h|, x_i = 1): the class of a lane
+// is (u, f) with f = [s_i h_i > 0] = ~(b_i ^ hb_i), hb_i = lane bit set
+// where h_i < 0.  TP[p][8 f + u] are per-lane threshold planes as above; a
+// lane with T = 2^32 is decided without a random number, every other lane
+// compares (T = 0 lanes end at the first set bit of r).
+template <int D, int ALGO, bool P2>
+__global__ void __launch_bounds__(kBlock) k_sweep_bits_field(const BitsParams p, const uint64_t* __restrict__ hbits) {
+  constexpr int NF = kFieldPlaneClasses;
+  extern __shared__ uint64_t sm_tp[];  // [R][kPlanes][NF]
+  const int R = p.R;
+  const int gt = blockIdx.y;
+  const int g = gt / p.K, tslot = gt - g * p.K;
+  {
+    const uint64_t* src = p.tp + ((size_t)g * p.slots + (size_t)tslot * R) * kPlanes * NF;
+    for (int k = threadIdx.x; k < R * kPlanes * NF; k += kBlock) sm_tp[k] = src[k];
+  }
+  __syncthreads();
+  const Geom geom = p.geom;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = p.J + (size_t)g * D * N;
+  const uint64_t* Hg = hbits + (size_t)g * N;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
+    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
+    uint64_t jw[2 * D];
+    jw[0] = __ldg(Jg + n.self);
+    jw[1] = __ldg(Jg + n.xm);
+    jw[2] = __ldg(Jg + N + n.self);
+    jw[3] = __ldg(Jg + N + n.ym);
+    if (D == 3) {
+      jw[4] = __ldg(Jg + 2u * N + n.self);
+      jw[5] = __ldg(Jg + 2u * N + n.zm);
+    }
+    const uint64_t hb = __ldg(Hg + n.self);
+#pragma unroll 1
+    for (int a = 0; a < R; ++a) {
+      const int sigma = tslot * R + a;
+      uint64_t* sp = p.spins + ((size_t)g * p.slots + sigma) * N;
+      const uint64_t b = sp[n.self];
+      uint64_t e[2 * D];
+      e[0] = b ^ sp[n.xp] ^ jw[0];
+      e[1] = b ^ sp[n.xm] ^ jw[1];
+      e[2] = b ^ sp[n.yp] ^ jw[2];
+      e[3] = b ^ sp[n.ym] ^ jw[3];
+      if (D == 3) {
+        e[4] = b ^ sp[n.zp] ^ jw[4];
+        e[5] = b ^ sp[n.zm] ^ jw[5];
+      }
+      uint64_t u0, u1, u2;
+      count_unsat<D>(e, u0, u1, u2);
+      const uint64_t f = ~(b ^ hb);
+      uint64_t mc[2][2 * D + 1];
+#pragma unroll
+      for (int u = 0; u <= 2 * D; ++u) {
+        const uint64_t m = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
+        mc[0][u] = m & ~f;
+        mc[1][u] = m & f;
+      }
+      const uint64_t* tpa = sm_tp + (size_t)a * kPlanes * NF;
+      uint64_t always = 0;
+#pragma unroll
+      for (int u = 0; u <= 2 * D; ++u)
+        always |= (mc[0][u] & tpa[32 * NF + u]) | (mc[1][u] & tpa[32 * NF + 8 + u]);
+      uint64_t lt = always;
+      uint64_t und = ~always;
+      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
+#pragma unroll 1
+      for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
+        const uint4 x = philox10(n.site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
+                                    : ((uint64_t)x.z | ((uint64_t)x.w << 32));
+          const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * NF;
+          uint64_t tb = 0;
+#pragma unroll
+          for (int u = 0; u <= 2 * D; ++u) tb |= (mc[0][u] & row[u]) | (mc[1][u] & row[8 + u]);
+          lt |= und & ~r & tb;
+          und &= ~(r ^ tb);
+        }
+      }
+      const uint64_t flip = (ALGO == 0) ? lt : ~lt;
+      if (flip) sp[n.self] = b ^ flip;
+    }
+  }
+}
+
+// Field signs of the random-field model: lane bit l of word (g, i) is set
+// where h_i of sample 64 g + l is negative (the H stream).
+__global__ void k_init_sites_bits(uint64_t* hbits, Geom geom, int G, PhiloxKeys keys) {
+  const uint64_t total = (uint64_t)G * geom.N;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t g = (uint32_t)(idx / geom.N), i = (uint32_t)(idx - (uint64_t)g * geom.N);
+    const uint32_t L = (uint32_t)geom.L;
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint4 r = philox10(i, 0u, (TAG_H << 28) | g, 0u, keys);
+    hbits[(size_t)g * geom.N + split_index(geom, x, y, z)] = (uint64_t)r.x | ((uint64_t)r.y << 32);
+  }
+}
+
+__global__ void k_get_sites_bits(const uint64_t* hbits, int8_t* out, Geom geom, int S) {
+  const uint64_t total = (uint64_t)S * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const int s = (int)(idx / geom.N);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint64_t w = hbits[(size_t)(s >> 6) * geom.N + split_index(geom, x, y, z)];
+    out[idx] = ((w >> (s & 63)) & 1ull) ? -1 : 1;
+  }
+}
+
+__global__ void k_set_sites_bits(uint64_t* hbits, const int8_t* in, Geom geom, int S, int G) {
+  const uint64_t total = (uint64_t)G * geom.N;
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t i = (uint32_t)(idx % geom.N);
+    const int g = (int)(idx / geom.N);
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    uint64_t* wp = &hbits[(size_t)g * geom.N + split_index(geom, x, y, z)];
+    uint64_t w = *wp;
+    for (int l = 0; l < 64; ++l) {
+      const int s = 64 * g + l;
+      if (s >= S) break;
+      const uint64_t bit = in[(size_t)s * geom.N + i] < 0 ? 1ull : 0ull;
+      w = (w & ~(1ull << l)) | (bit << l);
+    }
+    *wp = w;
+  }
+}
+
 // ---- initialisation: one Philox block gives the word of 64 samples ----
 
-__global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int slots, int ferro,
+__global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int slots, int jmode,
                             PhiloxKeys keys) {
   const uint64_t total = (uint64_t)G * geom.N;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -128,7 +264,8 @@ __global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int 
     const uint32_t j = split_index(geom, x, y, z);
     for (int d = 0; d < geom.D; ++d) {
       const uint4 r = philox10(i, (uint32_t)d, (TAG_J << 28) | g, 0u, keys);
-      J[((size_t)g * geom.D + d) * geom.N + j] = ferro ? 0ull : ((uint64_t)r.x | ((uint64_t)r.y << 32));
+      J[((size_t)g * geom.D + d) * geom.N + j] =
+          jmode == 1 ? 0ull : (jmode == 2 ? ~0ull : ((uint64_t)r.x | ((uint64_t)r.y << 32)));
     }
     for (int sg = 0; sg < slots; ++sg) {
       const uint4 r = philox10(i, 0u, (TAG_INIT << 28) | ((uint32_t)sg << 12) | g, 0u, keys);
@@ -161,6 +298,37 @@ __global__ void k_build_planes(uint64_t* tp, const uint64_t* thr, const int32_t*
       }
     }
     for (int q = 0; q < kPlanes; ++q) tp[(((size_t)g * slots + sigma) * kPlanes + q) * kMaxClasses + u] = planes[q];
+  }
+}
+
+// Field planes: FTP[g][sigma][p][8 f + u] from the per-temperature field
+// thresholds fthr[k][(v + 2D) * 2 + f], v = 2D - 2u; classes u > 2D stay 0.
+__global__ void k_build_field_planes(uint64_t* ftp, const uint64_t* fthr, const int32_t* temp_of, int D, int G,
+                                     int S, int R, int K, int slots) {
+  constexpr int NF = kFieldPlaneClasses;
+  const int total = G * slots * NF;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int c = idx % NF, rest = idx / NF;
+    const int sigma = rest % slots, g = rest / slots;
+    const int tslot = sigma / R, a = sigma - tslot * R;
+    const int u = c & 7, f = c >> 3;
+    uint64_t planes[kPlanes];
+    for (int q = 0; q < kPlanes; ++q) planes[q] = 0;
+    if (u <= 2 * D) {
+      const int cls = (4 * D - 2 * u) * 2 + f;
+      for (int l = 0; l < 64; ++l) {
+        const int s = 64 * g + l;
+        const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
+        const uint64_t T = fthr[(size_t)k * kFieldClasses + cls];
+        if (T >= kTwo32) {
+          planes[32] |= 1ull << l;
+        } else {
+          for (int q = 0; q < 32; ++q)
+            if ((T >> (31 - q)) & 1ull) planes[q] |= 1ull << l;
+        }
+      }
+    }
+    for (int q = 0; q < kPlanes; ++q) ftp[(((size_t)g * slots + sigma) * kPlanes + q) * NF + c] = planes[q];
   }
 }
 
@@ -274,9 +442,12 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __re
   }
 }
 
-template <int D>
+// FIELD: also F = N - 2 popcount(b ^ hb) per lane into acc[2] (random-field
+// model, F = sum_i sign(h_i) s_i).
+template <int D, bool FIELD>
 __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restrict__ spins,
-                                                         const uint64_t* __restrict__ J, int64_t* acc,
+                                                         const uint64_t* __restrict__ J,
+                                                         const uint64_t* __restrict__ hbits, int64_t* acc,
                                                          Geom geom, int S, int R, int K, int slots) {
   const int gt = blockIdx.y;  // g * slots + sigma
   const int g = gt / slots, sigma = gt - g * slots;
@@ -285,9 +456,9 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
   const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
   const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
   const int lane = threadIdx.x & 31;
-  uint64_t cu[kCtr], cb[kCtr];
+  uint64_t cu[kCtr], cb[kCtr], cf[kCtr];
 #pragma unroll
-  for (int k = 0; k < kCtr; ++k) cu[k] = cb[k] = 0;
+  for (int k = 0; k < kCtr; ++k) cu[k] = cb[k] = cf[k] = 0;
   for (int it = 0; it < kMeasIters; ++it) {
     const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
     if (j < N) {
@@ -306,6 +477,7 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
         ctr_add(cu, bi ^ sp[split_index(geom, (int)x, (int)y, (int)zp)] ^ Jg[2u * N + j]);
       }
       ctr_add(cb, bi);
+      if (FIELD) ctr_add(cf, bi ^ hbits[(size_t)g * N + j]);
     }
   }
   long long lo, hi;
@@ -316,6 +488,11 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
   ctr_flush(cb, lo, hi);
   if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 1], (unsigned long long)lo);
   if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 1], (unsigned long long)hi);
+  if (FIELD) {
+    ctr_flush(cf, lo, hi);
+    if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 2], (unsigned long long)lo);
+    if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 2], (unsigned long long)hi);
+  }
 }
 
 // Overlap at temperature k between replicas 0 and 1 (Sec. 4.1).  After
@@ -451,8 +628,14 @@ cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t 
     k_sweep_bits<D, ALGO, 1, P2><<<grid, kBlock, smem, lat.stream>>>(p);
   else if (lat.R == 2)
     k_sweep_bits<D, ALGO, 2, P2><<<grid, kBlock, smem, lat.stream>>>(p);
-  else
+  else {
+    if (smem > 48 * 1024) {  // many replicas: opt in to more than 48 KiB of planes
+      cudaError_t e = cudaFuncSetAttribute(k_sweep_bits<D, ALGO, 0, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
     k_sweep_bits<D, ALGO, 0, P2><<<grid, kBlock, smem, lat.stream>>>(p);
+  }
   return cudaGetLastError();
 }
 
@@ -460,6 +643,27 @@ template <int D, int ALGO>
 cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
   return lat.geom.lL > 0 ? sweep_dispatch<D, ALGO, true>(lat, p, grid, smem)
                          : sweep_dispatch<D, ALGO, false>(lat, p, grid, smem);
+}
+
+template <int D, int ALGO, bool P2>
+cudaError_t field_launch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
+  auto kern = k_sweep_bits_field<D, ALGO, P2>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, kBlock, smem, lat.stream>>>(p, lat.hbits);
+  return cudaGetLastError();
+}
+
+cudaError_t field_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem, int algo) {
+  const bool p2 = lat.geom.lL > 0;
+  if (lat.D == 3) {
+    if (algo) return p2 ? field_launch<3, 1, true>(lat, p, grid, smem) : field_launch<3, 1, false>(lat, p, grid, smem);
+    return p2 ? field_launch<3, 0, true>(lat, p, grid, smem) : field_launch<3, 0, false>(lat, p, grid, smem);
+  }
+  if (algo) return p2 ? field_launch<2, 1, true>(lat, p, grid, smem) : field_launch<2, 1, false>(lat, p, grid, smem);
+  return p2 ? field_launch<2, 0, true>(lat, p, grid, smem) : field_launch<2, 0, false>(lat, p, grid, smem);
 }
 
 // Shapes of the run-time specialised sweep (variants 2..): lockstep plane
@@ -498,9 +702,31 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   }
 }
 
-cudaError_t launch_init_bits(Lattice& lat, int ferro) {
+cudaError_t launch_init_bits(Lattice& lat, int jmode) {
   k_init_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>((uint64_t*)lat.spins, (uint64_t*)lat.J,
-                                                                          lat.geom, lat.G, lat.slots, ferro, lat.keys);
+                                                                          lat.geom, lat.G, lat.slots, jmode, lat.keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_sites_bits(Lattice& lat) {
+  k_init_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, lat.geom, lat.G, lat.keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs) {
+  k_get_sites_bits<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(lat.hbits, dev_hs, lat.geom, lat.S);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs) {
+  k_set_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, dev_hs, lat.geom, lat.S,
+                                                                               lat.G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_build_field_planes(Lattice& lat) {
+  k_build_field_planes<<<grid_for((uint64_t)lat.G * lat.slots * kFieldPlaneClasses, 128), 128, 0, lat.stream>>>(
+      lat.ftp, lat.fthr, lat.temp_of, lat.D, lat.G, lat.S, lat.R, lat.K, lat.slots);
   return cudaGetLastError();
 }
 
@@ -536,6 +762,11 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   dim3 grid((half + wpb - 1) / wpb, gts);
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
+  if (lat.field) {
+    p.tp = lat.ftp;
+    const size_t fsmem = (size_t)lat.R * kPlanes * kFieldPlaneClasses * sizeof(uint64_t);
+    return field_dispatch(lat, p, grid, fsmem, algo);
+  }
   // Lane-uniform thresholds (one temperature): the kernel specialised for
   // them at run time.  Variants (ianus_set_variant): 0 = automatic (the
   // specialised kernel for lattices of >= 2^20 site words, else the per-lane
@@ -562,7 +793,7 @@ cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
   if (e != cudaSuccess) return e;
   const uint32_t per_block = kBlock * kMeasIters;
   const unsigned nx = (lat.N + per_block - 1) / per_block;
-  if (lat.K == 1 && (lat.R == 1 || lat.R == 2)) {
+  if (lat.K == 1 && (lat.R == 1 || lat.R == 2) && !lat.field) {
     // one pass for E, M and (R == 2) Q; the overlap is computed either way
     dim3 grid(nx, (unsigned)lat.G);
     const uint64_t* sp = (const uint64_t*)lat.spins;
@@ -576,12 +807,18 @@ cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
     return cudaGetLastError();
   }
   dim3 grid(nx, (unsigned)(lat.G * lat.slots));
-  if (lat.D == 3)
-    k_measure_bits<3><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
-                                                        lat.geom, lat.S, lat.R, lat.K, lat.slots);
+  const uint64_t* sp = (const uint64_t*)lat.spins;
+  const uint64_t* J = (const uint64_t*)lat.J;
+  if (lat.field)
+    lat.D == 3 ? k_measure_bits<3, true><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S,
+                                                                          lat.R, lat.K, lat.slots)
+               : k_measure_bits<2, true><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S,
+                                                                          lat.R, lat.K, lat.slots);
   else
-    k_measure_bits<2><<<grid, kBlock, 0, lat.stream>>>((const uint64_t*)lat.spins, (const uint64_t*)lat.J, lat.acc,
-                                                        lat.geom, lat.S, lat.R, lat.K, lat.slots);
+    lat.D == 3 ? k_measure_bits<3, false><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S,
+                                                                           lat.R, lat.K, lat.slots)
+               : k_measure_bits<2, false><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S,
+                                                                           lat.R, lat.K, lat.slots);
   if (want_q && lat.R >= 2) {
     dim3 gq(nx, (unsigned)(lat.G * lat.K));
     k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(

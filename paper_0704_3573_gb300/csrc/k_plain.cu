@@ -8,6 +8,7 @@
 // bit-planes per Philox call, from the most significant bit down, and the
 // comparison stops at the first plane where r and T differ.
 #include <algorithm>
+#include <cmath>
 
 #include "lattice.h"
 
@@ -91,6 +92,58 @@ __global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
   }
 }
 
+
+// Field models (Eq. 2 with fields h_i = +-|h| and occupations x_i): an empty
+// site is skipped; for an occupied one v = s_i sum_j J_ij x_j s_j and
+// f = [s_i h_i > 0] select the threshold of class (v + 2D) * 2 + f.
+struct FieldI8Params {
+  I8Params b;
+  const int8_t* hs;    // [S][N]
+  const int8_t* occ;   // [S][N]
+  const uint64_t* fthr;  // [K][kFieldClasses]
+};
+
+template <int D>
+__global__ void __launch_bounds__(256) k_sweep_field_i8(const FieldI8Params fp) {
+  const I8Params& p = fp.b;
+  const uint64_t total = (uint64_t)p.slots * p.S * p.half;
+  const uint32_t L = (uint32_t)p.L, h = L / 2u;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t lat = (uint32_t)(idx / p.half);
+    const uint32_t w = (uint32_t)(idx - (uint64_t)lat * p.half);
+    const int sigma = (int)(lat / (uint32_t)p.S);
+    const int s = (int)(lat - (uint32_t)sigma * (uint32_t)p.S);
+    const uint32_t row = w / h, k = w - row * h;
+    const uint32_t y = row % L, z = row / L;
+    const uint32_t x = 2u * k + ((uint32_t)(p.colour ^ (int)(y + z)) & 1u);
+    const uint32_t i = x + L * (y + L * z);
+    const int8_t* xo = fp.occ + (size_t)s * p.N;
+    if (!xo[i]) continue;
+    int8_t* sp = p.spins + (size_t)lat * p.N;
+    const int8_t* Jp = p.J + (size_t)s * D * p.N;
+    const int si = sp[i];
+    const uint32_t xp = (x + 1u == L ? 0u : x + 1u) + L * (y + L * z);
+    const uint32_t xm = (x == 0u ? L - 1u : x - 1u) + L * (y + L * z);
+    const uint32_t yp = x + L * ((y + 1u == L ? 0u : y + 1u) + L * z);
+    const uint32_t ym = x + L * ((y == 0u ? L - 1u : y - 1u) + L * z);
+    int phi = Jp[i] * xo[xp] * sp[xp] + Jp[xm] * xo[xm] * sp[xm] + Jp[p.N + i] * xo[yp] * sp[yp] +
+              Jp[p.N + ym] * xo[ym] * sp[ym];
+    if (D == 3) {
+      const uint32_t zp = x + L * (y + L * (z + 1u == L ? 0u : z + 1u));
+      const uint32_t zm = x + L * (y + L * (z == 0u ? L - 1u : z - 1u));
+      phi += Jp[2u * p.N + i] * xo[zp] * sp[zp] + Jp[2u * p.N + zm] * xo[zm] * sp[zm];
+    }
+    const int v = si * phi;
+    const int f = si * fp.hs[(size_t)s * p.N + i] > 0;
+    const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+    const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
+    const uint64_t T = fp.fthr[(size_t)kt * kFieldClasses + (v + 2 * D) * 2 + f];
+    const bool less = lazy_less(T, p, tk, s, sigma, i);
+    if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
+  }
+}
 
 // ---- resident mode: a whole configuration in shared memory ----
 //
@@ -207,7 +260,7 @@ struct InitParams {
   int8_t* J;
   int S, D, slots;
   uint32_t N;
-  int ferro;
+  int jmode;  // 0 = J stream, 1 = every J = +1, 2 = every J = -1
   PhiloxKeys keys;
 };
 
@@ -223,12 +276,100 @@ __global__ void k_init_i8(const InitParams p) {
     const uint32_t g = s >> 6, lane = s & 63u;
     for (int d = 0; d < p.D; ++d) {
       const uint4 x = philox10(i, (uint32_t)d, (TAG_J << 28) | g, 0u, p.keys);
-      p.J[((size_t)s * p.D + d) * p.N + i] = (p.ferro || !lane_bit(x, lane)) ? 1 : -1;
+      p.J[((size_t)s * p.D + d) * p.N + i] = p.jmode == 2 ? -1 : ((p.jmode == 1 || !lane_bit(x, lane)) ? 1 : -1);
     }
     for (int sg = 0; sg < p.slots; ++sg) {
       const uint4 x = philox10(i, 0u, (TAG_INIT << 28) | ((uint32_t)sg << 12) | g, 0u, p.keys);
       p.spins[((size_t)sg * p.S + s) * p.N + i] = lane_bit(x, lane) ? -1 : 1;
     }
+  }
+}
+
+// Site disorder: sign of h_i from the H stream (RFIM) and x_i = [r_x < T_occ]
+// with r_x assembled from the 32 bit-planes of the X stream (DAFF).
+__global__ void k_init_sites_i8(int8_t* hs, int8_t* occ, int S, uint32_t N, int rfim, int daff, uint64_t T_occ,
+                                PhiloxKeys keys) {
+  const uint64_t total = (uint64_t)S * N;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t s = (uint32_t)(idx / N), i = (uint32_t)(idx - (uint64_t)s * N);
+    const uint32_t g = s >> 6, lane = s & 63u;
+    int8_t h = 1, xo = 1;
+    if (rfim) {
+      const uint4 x = philox10(i, 0u, (TAG_H << 28) | g, 0u, keys);
+      h = lane_bit(x, lane) ? -1 : 1;
+    }
+    if (daff) {
+      uint32_t r = 0;
+      for (uint32_t m = 0; m < 16u; ++m) {
+        const uint4 x = philox10(i, 0u, (TAG_X << 28) | (m << 24) | g, 0u, keys);
+        const uint32_t b0 = lane_bit(x, lane);
+        const uint32_t b1 = (lane < 32u ? (x.z >> lane) : (x.w >> (lane - 32u))) & 1u;
+        r |= (b0 << (31u - 2u * m)) | (b1 << (30u - 2u * m));
+      }
+      xo = (uint64_t)r < T_occ ? 1 : 0;
+    }
+    hs[idx] = h;
+    occ[idx] = xo;
+  }
+}
+
+// Field models, block per configuration: E_J = -sum_bonds J x x s s,
+// M = sum x s, F = sum sign(h) x s (Sec. 4.1 observables of Eq. 2).
+template <int D>
+__global__ void __launch_bounds__(256) k_measure_field_i8(const int8_t* __restrict__ spins,
+                                                          const int8_t* __restrict__ J,
+                                                          const int8_t* __restrict__ hs,
+                                                          const int8_t* __restrict__ occ, int64_t* acc, int S,
+                                                          int slots, int L, uint32_t N) {
+  __shared__ long long red[3][8];
+  for (uint32_t lat = blockIdx.x; lat < (uint32_t)(slots * S); lat += gridDim.x) {
+    const int sigma = (int)(lat / (uint32_t)S), s = (int)(lat - (uint32_t)sigma * S);
+    const int8_t* sp = spins + (size_t)lat * N;
+    const int8_t* Jp = J + (size_t)s * D * N;
+    const int8_t* xo = occ + (size_t)s * N;
+    const int8_t* hp = hs + (size_t)s * N;
+    long long e = 0, m = 0, f = 0;
+    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
+      const uint32_t x = i % (uint32_t)L, y = (i / (uint32_t)L) % (uint32_t)L;
+      const uint32_t z = D == 3 ? i / ((uint32_t)L * (uint32_t)L) : 0u;
+      const int si = xo[i] * sp[i];
+      const uint32_t xp = (x + 1u == (uint32_t)L ? 0u : x + 1u) + (uint32_t)L * (y + (uint32_t)L * z);
+      const uint32_t yp = x + (uint32_t)L * ((y + 1u == (uint32_t)L ? 0u : y + 1u) + (uint32_t)L * z);
+      e -= Jp[i] * si * xo[xp] * sp[xp];
+      e -= Jp[N + i] * si * xo[yp] * sp[yp];
+      if (D == 3) {
+        const uint32_t zp = x + (uint32_t)L * (y + (uint32_t)L * (z + 1u == (uint32_t)L ? 0u : z + 1u));
+        e -= Jp[2u * N + i] * si * xo[zp] * sp[zp];
+      }
+      m += si;
+      f += hp[i] * si;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      e += __shfl_down_sync(0xffffffffu, e, off);
+      m += __shfl_down_sync(0xffffffffu, m, off);
+      f += __shfl_down_sync(0xffffffffu, f, off);
+    }
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+      red[0][wid] = e;
+      red[1][wid] = m;
+      red[2][wid] = f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long E = 0, M = 0, F = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        E += red[0][w];
+        M += red[1][w];
+        F += red[2][w];
+      }
+      int64_t* a = acc + ((size_t)s * slots + sigma) * kAccStride;
+      a[0] = E;
+      a[1] = M;
+      a[2] = F;
+    }
+    __syncthreads();
   }
 }
 
@@ -285,7 +426,8 @@ __global__ void __launch_bounds__(256) k_measure_i8(const int8_t* __restrict__ s
 // configurations of replicas 0 and 1 that currently hold temperature k
 // (Sec. 4.1 overlap).  Stored in acc[s][k*R][6].
 __global__ void __launch_bounds__(256) k_overlap_i8(const int8_t* __restrict__ spins, const int32_t* slot_at,
-                                                    int64_t* acc, int S, int R, int K, int slots, uint32_t N) {
+                                                    const int8_t* __restrict__ occ, int64_t* acc, int S, int R,
+                                                    int K, int slots, uint32_t N) {
   __shared__ long long red[8];
   for (uint32_t sk = blockIdx.x; sk < (uint32_t)(S * K); sk += gridDim.x) {
     const int s = (int)(sk / (uint32_t)K), k = (int)(sk - (uint32_t)s * K);
@@ -294,7 +436,12 @@ __global__ void __launch_bounds__(256) k_overlap_i8(const int8_t* __restrict__ s
     const int8_t* a0 = spins + ((size_t)s0 * S + s) * N;
     const int8_t* a1 = spins + ((size_t)s1 * S + s) * N;
     long long q = 0;
-    for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += a0[i] * a1[i];
+    if (occ) {  // Q = sum_i x_i s_i^0 s_i^1
+      const int8_t* xo = occ + (size_t)s * N;
+      for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += xo[i] * a0[i] * a1[i];
+    } else {
+      for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += a0[i] * a1[i];
+    }
     for (int off = 16; off > 0; off >>= 1) q += __shfl_down_sync(0xffffffffu, q, off);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = q;
     __syncthreads();
@@ -329,8 +476,8 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 
 }  // namespace
 
-cudaError_t launch_init_i8(Lattice& lat, int ferro) {
-  InitParams p{(int8_t*)lat.spins, (int8_t*)lat.J, lat.S, lat.D, lat.slots, lat.N, ferro, lat.keys};
+cudaError_t launch_init_i8(Lattice& lat, int jmode) {
+  InitParams p{(int8_t*)lat.spins, (int8_t*)lat.J, lat.S, lat.D, lat.slots, lat.N, jmode, lat.keys};
   k_init_i8<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(p);
   return cudaGetLastError();
 }
@@ -356,6 +503,14 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
   p.t_dev = lat.capturing ? lat.t_dev : nullptr;
   const uint64_t total = (uint64_t)lat.slots * lat.S * p.half;
   const unsigned grid = grid_for(total, 256, 152u * 8u);
+  if (lat.field) {
+    const FieldI8Params fp{p, lat.hs, lat.occ, lat.fthr};
+    if (lat.D == 3)
+      k_sweep_field_i8<3><<<grid, 256, 0, lat.stream>>>(fp);
+    else
+      k_sweep_field_i8<2><<<grid, 256, 0, lat.stream>>>(fp);
+    return cudaGetLastError();
+  }
   if (lat.D == 3)
     k_sweep_i8<3><<<grid, 256, 0, lat.stream>>>(p);
   else
@@ -365,7 +520,13 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
 
 cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)lat.slots * lat.S, 152u * 8u);
-  if (lat.D == 3)
+  if (lat.field && lat.D == 3)
+    k_measure_field_i8<3><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.hs,
+                                                         lat.occ, lat.acc, lat.S, lat.slots, lat.L, lat.N);
+  else if (lat.field)
+    k_measure_field_i8<2><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.hs,
+                                                         lat.occ, lat.acc, lat.S, lat.slots, lat.L, lat.N);
+  else if (lat.D == 3)
     k_measure_i8<3><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.acc,
                                                    lat.S, lat.R, lat.slots, lat.L, lat.N);
   else
@@ -373,14 +534,14 @@ cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
                                                    lat.S, lat.R, lat.slots, lat.L, lat.N);
   if (want_q && lat.R >= 2) {
     const unsigned gq = (unsigned)std::min<uint64_t>((uint64_t)lat.S * lat.K, 152u * 8u);
-    k_overlap_i8<<<gq, 256, 0, lat.stream>>>((const int8_t*)lat.spins, lat.slot_at, lat.acc, lat.S, lat.R, lat.K,
-                                            lat.slots, lat.N);
+    k_overlap_i8<<<gq, 256, 0, lat.stream>>>((const int8_t*)lat.spins, lat.slot_at, lat.field ? lat.occ : nullptr,
+                                            lat.acc, lat.S, lat.R, lat.K, lat.slots, lat.N);
   }
   return cudaGetLastError();
 }
 
 bool resident_i8_fits(const Lattice& lat) {
-  return lat.layout == IANUS_LAYOUT_I8 && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
+  return lat.layout == IANUS_LAYOUT_I8 && !lat.field && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
 }
 
 cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every) {
@@ -435,6 +596,28 @@ cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out) {
 
 cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in) {
   return cudaMemcpyAsync(lat.J, dev_in, (size_t)lat.S * lat.D * lat.N, cudaMemcpyDeviceToDevice, lat.stream);
+}
+
+cudaError_t launch_init_sites_i8(Lattice& lat, double occupation) {
+  const uint64_t T_occ = (uint64_t)std::floor(std::ldexp(occupation, 32));
+  k_init_sites_i8<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(
+      lat.hs, lat.occ, lat.S, lat.N, lat.disorder == IANUS_DISORDER_RFIM, lat.disorder == IANUS_DISORDER_DAFF, T_occ,
+      lat.keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_get_sites_i8(Lattice& lat, int8_t* dev_hs, int8_t* dev_occ) {
+  const size_t n = (size_t)lat.S * lat.N;
+  cudaError_t e = cudaMemcpyAsync(dev_hs, lat.hs, n, cudaMemcpyDeviceToDevice, lat.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dev_occ, lat.occ, n, cudaMemcpyDeviceToDevice, lat.stream);
+  return e;
+}
+
+cudaError_t launch_set_sites_i8(Lattice& lat, const int8_t* dev_hs, const int8_t* dev_occ) {
+  const size_t n = (size_t)lat.S * lat.N;
+  cudaError_t e = cudaMemcpyAsync(lat.hs, dev_hs, n, cudaMemcpyDeviceToDevice, lat.stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(lat.occ, dev_occ, n, cudaMemcpyDeviceToDevice, lat.stream);
+  return e;
 }
 
 }  // namespace ianus

@@ -304,7 +304,8 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 
 }  // namespace
 
-cudaError_t launch_init_potts(Lattice& lat, int ferro) {
+cudaError_t launch_init_potts(Lattice& lat, int jmode) {
+  const int ferro = jmode == 1;  // Potts lattices take the J stream or J = +1
   k_init_potts<<<grid_for((uint64_t)lat.Q4 * lat.N), 256, 0, lat.stream>>>(
       (uint32_t*)lat.spins, (uint32_t*)lat.J, lat.geom, lat.Q4, lat.slots, ferro, lat.keys);
   return cudaGetLastError();

@@ -17,7 +17,7 @@ __device__ __forceinline__ long long config_energy(const int64_t* row, int mode,
 
 __global__ void k_finalize(const int64_t* __restrict__ acc, const int32_t* __restrict__ slot_at, int64_t* E,
                            int64_t* M, int64_t* Q, uint64_t* sweep_out, uint64_t sweep, int S, int R, int K,
-                           int slots, int mode, int D, uint32_t N, int want_q) {
+                           int slots, int mode, int D, uint32_t N, int want_q, int field) {
   const int total = S * K * R;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int a = idx % R, sk = idx / R;
@@ -26,7 +26,15 @@ __global__ void k_finalize(const int64_t* __restrict__ acc, const int32_t* __res
     const int64_t* row = acc + ((size_t)s * slots + (size_t)tslot * R + a) * kAccStride;
     if (E) E[idx] = config_energy(row, mode, D, N);
     if (M) {
-      if (mode == IANUS_LAYOUT_U8X4) {
+      if (field) {  // M = sum x s, F = sum sign(h) x s
+        if (mode == IANUS_LAYOUT_BITS64) {
+          M[(size_t)idx * 2] = (int64_t)N - 2 * row[1];
+          M[(size_t)idx * 2 + 1] = (int64_t)N - 2 * row[2];
+        } else {
+          M[(size_t)idx * 2] = row[1];
+          M[(size_t)idx * 2 + 1] = row[2];
+        }
+      } else if (mode == IANUS_LAYOUT_U8X4) {
         for (int f = 0; f < 4; ++f) M[(size_t)idx * 4 + f] = row[2 + f];
       } else if (mode == IANUS_LAYOUT_BITS64) {
         M[idx] = (int64_t)N - 2 * row[1];
@@ -109,7 +117,7 @@ cudaError_t launch_finalize(Lattice& lat, int64_t* E, int64_t* M, int64_t* Q, ui
   const unsigned grid = (unsigned)std::min(152 * 4, (total + 255) / 256);
   k_finalize<<<grid > 0 ? grid : 1, 256, 0, lat.stream>>>(lat.acc, lat.slot_at, E, M, Q, sweep_out, lat.sweeps,
                                                          lat.S, lat.R, lat.K, lat.slots, lat.layout, lat.D, lat.N,
-                                                         want_q);
+                                                         want_q, lat.field ? 1 : 0);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,11 @@ constexpr int kMaxClasses = 8;   // u = 0..2D (7 in 3D), padded
 constexpr int kPlanes = 33;      // 32 threshold bit-planes + the "always" mask
 constexpr int kAccStride = 8;    // int64 accumulators per (sample, slot)
 constexpr uint64_t kTwo32 = 1ull << 32;
+// Field models (Eq. 2 with random fields or dilution): the I8 class of a site
+// is (v + 2D) * 2 + f, v = s_i sum_j J_ij x_j s_j in -2D..2D and f = 1 when
+// s_i h_i > 0; the bit-sliced class is 8 f + u with v = 2D - 2u.
+constexpr int kFieldClasses = 32;
+constexpr int kFieldPlaneClasses = 16;
 
 // Truth tables of the lane-uniform threshold path: t[p] bit u = bit (31-p)
 // of the class-u threshold; always bit u = (T(u) == 2^32); need bit u = the
@@ -60,7 +65,17 @@ struct Lattice {
   int64_t* ser_Q;       // [cap][S*K]
   uint32_t* err;        // device error word
 
-  int mq;               // magnetisation entries per configuration (1 Ising, 4 Potts)
+  // field models (RFIM, DAFF)
+  int disorder;         // IANUS_DISORDER_*
+  bool field;           // disorder is RFIM or DAFF
+  double hmag;          // |h|
+  uint64_t* fthr;       // u64 [K][kFieldClasses] threshold per field class
+  uint64_t* ftp;        // BITS64 field: u64 [G][slots][kPlanes][kFieldPlaneClasses]
+  int8_t* hs;           // I8 field: sign of h_i, int8 [S][N]
+  int8_t* occ;          // I8 field: x_i in {0, 1}, int8 [S][N]
+  uint64_t* hbits;      // BITS64 field: lane bit set where h_i < 0, u64 [G][N]
+
+  int mq;               // magnetisation entries per configuration (1 Ising, 4 Potts, 2 field models)
   uint32_t cap;         // series capacity
   uint64_t ser_count;   // rows recorded so far (ring position = ser_count % cap)
   uint64_t ser_first;   // first row still readable
@@ -100,6 +115,9 @@ size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
 // Metropolis: u < D -> T_M(4D - 4u), u >= D -> 2^32 (always); inv = 0.
 // Heat bath: T_H(2D - 2u), inv = 1 (keep iff r < T).
 void class_thresholds(int dim, int algo, double beta, uint64_t* thr /*[kMaxClasses]*/);
+// Field models: threshold per class (v + 2D) * 2 + f for the same unified
+// rule; Metropolis classes with dE <= 0 get 2^32.  Unused entries are 0.
+void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr /*[kFieldClasses]*/);
 
 // Run-time specialised bit-sliced sweep for lat.ulut (jit.cu); null when
 // runtime compilation is unavailable.  Its queued shape takes kJitSmemBytes
@@ -110,7 +128,12 @@ cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)
-cudaError_t launch_init_i8(Lattice& lat, int ferro);
+// Coupling modes of the initialisers: 0 = the J stream, 1 = every J = +1,
+// 2 = every J = -1.
+cudaError_t launch_init_i8(Lattice& lat, int jmode);
+cudaError_t launch_init_sites_i8(Lattice& lat, double occupation);  // hs, occ from the H and X streams
+cudaError_t launch_get_sites_i8(Lattice& lat, int8_t* dev_hs, int8_t* dev_occ);  // [S][N] each
+cudaError_t launch_set_sites_i8(Lattice& lat, const int8_t* dev_hs, const int8_t* dev_occ);
 cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv);
 cudaError_t launch_measure_i8(Lattice& lat, int want_q);
 // Resident mode (one block per configuration in shared memory, many sweeps
@@ -124,7 +147,11 @@ cudaError_t launch_set_spins_i8(Lattice& lat, const int8_t* dev_in);
 cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out);   // [S][D][N]
 cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in);
 // BITS64 (k_msc.cu)
-cudaError_t launch_init_bits(Lattice& lat, int ferro);
+cudaError_t launch_init_bits(Lattice& lat, int jmode);
+cudaError_t launch_init_sites_bits(Lattice& lat);                    // hbits from the H stream
+cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs);     // [S][N]
+cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs);
+cudaError_t launch_build_field_planes(Lattice& lat);                 // ftp from fthr and temp_of
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
 cudaError_t launch_measure_bits(Lattice& lat, int want_q);
 cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
@@ -133,7 +160,7 @@ cudaError_t launch_set_spins_bits(Lattice& lat, const int8_t* dev_in);
 cudaError_t launch_get_couplings_bits(Lattice& lat, int8_t* dev_out);
 cudaError_t launch_set_couplings_bits(Lattice& lat, const int8_t* dev_in);
 // U8X4 Potts (k_potts.cu)
-cudaError_t launch_init_potts(Lattice& lat, int ferro);
+cudaError_t launch_init_potts(Lattice& lat, int jmode);
 cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t);
 cudaError_t launch_measure_potts(Lattice& lat, int want_q);
 cudaError_t launch_get_spins_potts(Lattice& lat, int8_t* dev_out);

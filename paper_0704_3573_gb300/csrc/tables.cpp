@@ -46,6 +46,29 @@ void class_thresholds(int dim, int algo, double beta, uint64_t* thr) {
   }
 }
 
+// x = (double)v + w, w = +|h| (f = 1, s_i h_i > 0) or -|h| (f = 0), w = +0.0
+// when |h| = 0; dE = 2.0 * x.  The expressions follow include/ianus.h.
+static double field_x(int v, int f, double hmag) {
+  const double w = hmag == 0.0 ? 0.0 : (f ? hmag : -hmag);
+  return (double)v + w;
+}
+
+void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr) {
+  for (int c = 0; c < kFieldClasses; ++c) thr[c] = 0;
+  for (int v = -2 * dim; v <= 2 * dim; ++v)
+    for (int f = 0; f < 2; ++f) {
+      const double x = field_x(v, f, hmag);
+      uint64_t T;
+      if (algo == IANUS_METROPOLIS) {
+        const double dE = 2.0 * x;
+        T = dE <= 0.0 ? kTwo32 : to_threshold(std::exp(-beta * dE));
+      } else {
+        T = to_threshold(1.0 / (1.0 + std::exp(-2.0 * beta * x)));
+      }
+      thr[(v + 2 * dim) * 2 + f] = T;
+    }
+}
+
 size_t table_potts(double beta, uint64_t* out, size_t n) {
   const size_t need = 3u * 13u * 13u * 13u * 13u;
   if (!out || n < need || !(beta >= 0.0) || !std::isfinite(beta)) return 0;
@@ -81,5 +104,15 @@ size_t ianus_table_ising(int32_t dim, int32_t algo, double beta, uint64_t* out, 
 size_t ianus_table_potts(double beta, uint64_t* out, size_t n) { return ianus::table_potts(beta, out, n); }
 size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n) {
   return ianus::table_pt(beta_k, beta_k1, out, n);
+}
+size_t ianus_table_field(int32_t dim, int32_t algo, double beta, double field, uint64_t* out, size_t n) {
+  const size_t need = (size_t)(2 * (4 * dim + 1));
+  if ((dim != 2 && dim != 3) || !out || n < need || !(beta >= 0.0) || !std::isfinite(beta) || !(field >= 0.0) ||
+      !std::isfinite(field) || (algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH))
+    return 0;
+  uint64_t t[ianus::kFieldClasses];
+  ianus::field_thresholds(dim, algo, beta, field, t);
+  for (size_t c = 0; c < need; ++c) out[c] = t[c];
+  return need;
 }
 }

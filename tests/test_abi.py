@@ -41,7 +41,8 @@ def _cfg(**kw):
     c.abi_version = ianus.ABI_VERSION
     c.model, c.dim, c.L = kw.get("model", 0), kw.get("dim", 3), kw.get("L", 16)
     c.n_samples, c.n_replicas, c.n_temps = kw.get("S", 1), kw.get("R", 1), kw.get("K", 1)
-    c.layout, c.disorder, c.seed = kw.get("layout", 0), 0, 1
+    c.layout, c.disorder, c.seed = kw.get("layout", 0), kw.get("disorder", 0), 1
+    c.field, c.occupation = kw.get("field", 0.0), kw.get("occupation", 1.0)
     return c
 
 
@@ -63,6 +64,29 @@ def test_required_bytes_validation():
     bad = _cfg()
     bad.abi_version = 99
     assert lib.ianus_required_bytes(ctypes.byref(bad)) == 0
+
+
+def test_field_model_validation():
+    lib = ianus.lib()
+    rb = lambda **kw: lib.ianus_required_bytes(ctypes.byref(_cfg(**kw)))
+    RFIM, DAFF = ianus.DISORDER_RFIM, ianus.DISORDER_DAFF
+    assert rb(disorder=RFIM, field=1.5) > 0
+    assert rb(disorder=RFIM, field=1.5, layout=1) > 0
+    assert rb(disorder=DAFF, field=0.5, occupation=0.7) > 0            # AUTO -> I8
+    assert rb(disorder=DAFF, field=0.5, occupation=0.7, layout=2) == 0  # no dilution in BITS64
+    assert rb(disorder=DAFF, occupation=1.5) == 0
+    assert rb(disorder=DAFF, occupation=float("nan")) == 0
+    assert rb(disorder=RFIM, field=-1.0) == 0
+    assert rb(disorder=RFIM, field=float("inf")) == 0
+    assert rb(disorder=0, field=0.5) == 0                                # EA takes no field
+    assert rb(disorder=4) == 0
+    assert rb(model=1, disorder=RFIM, field=1.0) == 0                    # Potts has no field model
+    # the field model adds its sites (64-bit words) and field planes
+    assert rb(disorder=RFIM, field=1.0, L=16, S=64, layout=2) > rb(L=16, S=64, layout=2)
+    # bit-sliced sweeps stage one block's planes in shared memory: bounded replicas
+    assert rb(L=8, S=64, R=110, layout=2) > 0 and rb(L=8, S=64, R=111, layout=2) == 0
+    assert rb(disorder=RFIM, field=1.0, L=8, S=64, R=55, layout=2) > 0
+    assert rb(disorder=RFIM, field=1.0, L=8, S=64, R=56, layout=2) == 0
 
 
 @pytest.mark.parametrize("beta", [0.0, 0.25, 1 / 1.1, 1.0, 2.0, 7.5])
@@ -87,3 +111,27 @@ def test_pt_table_matches_oracle():
     t = ianus.table_pt(1 / 0.7, 1 / (0.7 + 0.9 / 31), 64)
     db = abs(1 / 0.7 - 1 / (0.7 + 0.9 / 31))
     assert [int(v) for v in t] == [oracle.table_pt(db, 4 * m) for m in range(1, 65)]
+
+
+@pytest.mark.parametrize("beta,h", [(0.0, 0.0), (0.3, 0.5), (1 / 1.1, 1.0), (1.0, 2.25), (4.0, 0.75), (0.5, 13.0)])
+def test_field_tables_match_oracle(beta, h):
+    for dim in (2, 3):
+        for algo, ref in ((ianus.METROPOLIS, oracle.table_metropolis_x), (ianus.HEATBATH, oracle.table_heatbath_x)):
+            t = ianus.table_field(dim, algo, beta, h)
+            assert len(t) == 2 * (4 * dim + 1)
+            for v in range(-2 * dim, 2 * dim + 1):
+                for f in (0, 1):
+                    w = 0.0 if h == 0 else (h if f else -h)
+                    x = float(v) + w
+                    if algo == ianus.METROPOLIS and 2 * x <= 0:
+                        want = 1 << 32  # dE <= 0 always flips
+                    else:
+                        want = ref(beta, x)
+                    assert int(t[(v + 2 * dim) * 2 + f]) == want, (dim, algo, v, f)
+    # at h = 0 the field tables are the EA tables
+    for dim in (2, 3):
+        t = ianus.table_field(dim, ianus.HEATBATH, beta, 0.0)
+        e = ianus.table_ising(dim, ianus.HEATBATH, beta)
+        for j in range(2 * dim + 1):
+            v = -2 * dim + 2 * j
+            assert t[(v + 2 * dim) * 2] == t[(v + 2 * dim) * 2 + 1] == e[j]
