@@ -60,6 +60,11 @@ def lib():
         L.oracle_series_clear.argtypes = [c.c_void_p]
         for f in ("oracle_get_spins", "oracle_set_spins", "oracle_get_couplings", "oracle_set_couplings"):
             getattr(L, f).argtypes = [c.c_void_p, c.c_void_p]
+        L.oracle_set_couplings.restype = c.c_int
+        L.oracle_perm_coupling_index.restype = c.c_int
+        L.oracle_perm_coupling_index.argtypes = [c.c_uint64, c.c_int, c.c_int, c.c_uint32]
+        L.oracle_perm_code.restype = c.c_int
+        L.oracle_perm_code.argtypes = [c.c_int]
         L.oracle_get_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
         L.oracle_set_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
         L.oracle_get_pt.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p, c.c_void_p]
@@ -151,7 +156,15 @@ def occupation_random(seed, sample, site) -> int:
     return int(lib().oracle_occupation_random(seed, sample, site))
 
 
-MODEL_ISING, MODEL_POTTS = 0, 1
+def perm_coupling_index(seed, sample, d, site) -> int:
+    return int(lib().oracle_perm_coupling_index(seed, sample, d, site))
+
+
+def perm_code(index) -> int:
+    return int(lib().oracle_perm_code(index))
+
+
+MODEL_ISING, MODEL_POTTS, MODEL_PERM = 0, 1, 2
 METROPOLIS, HEATBATH = 0, 1
 DIS_EA, DIS_FERRO, DIS_RFIM, DIS_DAFF = 0, 1, 2, 3
 
@@ -172,6 +185,8 @@ class Oracle:
         ids = np.asarray(sample_ids, dtype=np.int32)
         if disorder is None:
             disorder = DIS_FERRO if ferro else DIS_EA
+        if model == MODEL_PERM:
+            q = 4  # the glassy Potts model of Eq. (3) has four states
         self.model, self.q, self.dim, self.L = model, q, dim, L
         self.disorder, self.field, self.occupation = disorder, float(field), float(occupation)
         self.N = L ** dim
@@ -240,8 +255,10 @@ class Oracle:
         return out
 
     def set_couplings(self, a):
+        """J = +-1, or for the permutation model the 8-bit codes as int8."""
         a = np.ascontiguousarray(a, dtype=np.int8).reshape(self.S, self.dim, self.N)
-        lib().oracle_set_couplings(self._h, _ptr(a))
+        if lib().oracle_set_couplings(self._h, _ptr(a)) != 0:
+            raise ValueError("coupling code is not a permutation")
 
     def sites(self):
         """(sign(h_i) [S, N], x_i [S, N]) as int8."""

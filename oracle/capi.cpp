@@ -15,7 +15,8 @@ extern "C" {
 
 void* oracle_create(int model, int q, int dim, int L, const int32_t* sample_ids, int n_ids, int R,
                     int K, uint64_t seed, int disorder, double field, double occupation) {
-  if (dim < 1 || dim > 3 || L < 2 || (L & 1) || n_ids < 1 || R < 1 || K < 1 || q < 2) return nullptr;
+  if (dim < 1 || dim > 4 || L < 2 || (L & 1) || n_ids < 1 || R < 1 || K < 1 || q < 2) return nullptr;
+  if (model < 0 || model > 2 || (model == MODEL_PERM && q != 4)) return nullptr;
   if (disorder < 0 || disorder > 3 || !(field >= 0.0) || !(occupation >= 0.0 && occupation <= 1.0)) return nullptr;
   State* st = new State();
   std::vector<int> ids(sample_ids, sample_ids + n_ids);
@@ -72,7 +73,7 @@ static void rebook(State* st) {
   for (auto& smp : st->samples)
     for (size_t sl = 0; sl < smp.spin.size(); ++sl) {
       smp.E_run[sl] = energy(*st, smp, (int)sl);
-      smp.F_run[sl] = st->model == 0 ? field_sum(*st, smp, (int)sl) : 0;
+      smp.F_run[sl] = st->model == MODEL_ISING ? field_sum(*st, smp, (int)sl) : 0;
     }
 }
 
@@ -109,24 +110,30 @@ void oracle_set_sites(void* h, const int8_t* hs, const int8_t* x) {
   rebook(st);
 }
 
-/* couplings int8 [n_ids][D][N] */
+/* couplings int8 [n_ids][D][N]: J = +-1, or for model 2 the 8-bit code
+ * pi(0) | pi(1) << 2 | pi(2) << 4 | pi(3) << 6 stored as int8 */
 void oracle_get_couplings(void* h, int8_t* out) {
   State* st = static_cast<State*>(h);
   size_t o = 0;
-  for (auto& smp : st->samples) {
-    std::memcpy(out + o, smp.J.data(), smp.J.size());
-    o += smp.J.size();
-  }
+  for (auto& smp : st->samples)
+    for (size_t k = 0; k < smp.J.size(); ++k)
+      out[o++] = st->model == MODEL_PERM ? (int8_t)(uint8_t)perm_code(smp.J[k]) : smp.J[k];
 }
 
-void oracle_set_couplings(void* h, const int8_t* in) {
+/* Returns 0, or -1 (nothing changed) when a model-2 code is not a permutation. */
+int oracle_set_couplings(void* h, const int8_t* in) {
   State* st = static_cast<State*>(h);
+  size_t n = 0;
+  for (auto& smp : st->samples) n += smp.J.size();
+  if (st->model == MODEL_PERM)
+    for (size_t k = 0; k < n; ++k)
+      if (perm_index_of_code((uint8_t)in[k]) < 0) return -1;
   size_t o = 0;
-  for (auto& smp : st->samples) {
-    std::memcpy(smp.J.data(), in + o, smp.J.size());
-    o += smp.J.size();
-  }
+  for (auto& smp : st->samples)
+    for (size_t k = 0; k < smp.J.size(); ++k, ++o)
+      smp.J[k] = st->model == MODEL_PERM ? (int8_t)perm_index_of_code((uint8_t)in[o]) : in[o];
   rebook(st);
+  return 0;
 }
 
 /* slot_at int32 [n_ids][R][K], accepted uint64 [n_ids][R][K-1] */
@@ -187,5 +194,9 @@ int oracle_field_sign_bit(uint64_t seed, int sample, uint32_t site) { return fie
 uint32_t oracle_occupation_random(uint64_t seed, int sample, uint32_t site) {
   return occupation_random(seed, sample, site);
 }
+int oracle_perm_coupling_index(uint64_t seed, int sample, int d, uint32_t site) {
+  return perm_coupling_index(seed, sample, d, site);
+}
+int oracle_perm_code(int index) { return perm_code(index); }
 
 }  // extern "C"

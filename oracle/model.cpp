@@ -28,7 +28,7 @@ static uint32_t site_index(const State& st, const int* x) {
 }
 
 uint32_t neighbour(const State& st, uint32_t i, int d, int dir) {
-  int x[3];
+  int x[4];
   site_coords(st, i, x);
   x[d] = (x[d] + dir + st.L) % st.L;
   return site_index(st, x);
@@ -36,7 +36,7 @@ uint32_t neighbour(const State& st, uint32_t i, int d, int dir) {
 
 /* Sec. 3.1: the lattice is bipartite; colour = parity of the coordinate sum. */
 int colour(const State& st, uint32_t i) {
-  int x[3];
+  int x[4];
   site_coords(st, i, x);
   int sum = 0;
   for (int d = 0; d < st.D; ++d) sum += x[d];
@@ -71,7 +71,8 @@ void init_state(State& st, int model, int q, int D, int L, const std::vector<int
     for (int d = 0; d < D; ++d)
       for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
         int J;
-        if (st.disorder == DIS_EA) J = coupling_bit(seed, s, d, i) ? -1 : 1;
+        if (model == MODEL_PERM) J = perm_coupling_index(seed, s, d, i);
+        else if (st.disorder == DIS_EA) J = coupling_bit(seed, s, d, i) ? -1 : 1;
         else if (st.disorder == DIS_DAFF) J = -1;  /* antiferromagnet */
         else J = 1;                                /* ferromagnet, RFIM */
         smp.J[(size_t)d * st.N + i] = (int8_t)J;
@@ -115,10 +116,16 @@ int64_t energy(const State& st, const Sample& smp, int slot) {
     for (int d = 0; d < st.D; ++d) {
       uint32_t j = neighbour(st, i, d, +1);
       int J = smp.J[(size_t)d * st.N + i];
-      if (st.model == 0)
+      if (st.model == MODEL_ISING) {
         E -= (int64_t)J * smp.x[i] * smp.x[j] * s[i] * s[j];
-      else
+      } else if (st.model == MODEL_POTTS) {
         E -= (s[i] == s[j]) ? J : 0;
+      } else {
+        /* Eq. (3): the bond is satisfied iff s_i = pi_ij(s_j) */
+        int pi[4];
+        perm_unrank(J, pi);
+        E -= (s[i] == pi[s[j]]) ? 1 : 0;
+      }
     }
   return E;
 }
@@ -227,6 +234,44 @@ void sweep_potts(const State& st, Sample& smp, int slot, double beta, uint64_t t
   }
 }
 
+/* Eq. (3) heat bath: n_c counts the bonds of site i satisfied when s_i = c.
+ * A forward bond (i, i + e_d) carries pi = pi_d(i) and is satisfied iff
+ * c = pi(s_j); a backward bond (i - e_d, i) carries pi = pi_d(i - e_d) and is
+ * satisfied iff s_{i - e_d} = pi(c).  The new state follows the cumulative
+ * thresholds of exp(beta n_c), as for model 1. */
+void sweep_perm(const State& st, Sample& smp, int slot, double beta, uint64_t t) {
+  std::vector<int8_t>& s = smp.spin[slot];
+  int n[4];
+  uint64_t T[3];
+  for (int c = 0; c < 2; ++c) {
+    for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
+      if (colour(st, i) != c) continue;
+      for (int k = 0; k < 4; ++k) n[k] = 0;
+      for (int d = 0; d < st.D; ++d) {
+        const uint32_t jf = neighbour(st, i, d, +1);
+        const uint32_t jb = neighbour(st, i, d, -1);
+        int pf[4], pb[4];
+        perm_unrank(smp.J[(size_t)d * st.N + i], pf);
+        perm_unrank(smp.J[(size_t)d * st.N + jb], pb);
+        for (int cand = 0; cand < 4; ++cand) {
+          if (cand == pf[s[jf]]) n[cand] += 1;
+          if (s[jb] == pb[cand]) n[cand] += 1;
+        }
+      }
+      table_potts(beta, 4, n, T);
+      const uint32_t r = potts_random(st.seed, smp.s, slot, i, t);
+      int knew = 3;
+      for (int k = 0; k < 3; ++k)
+        if ((uint64_t)r < T[k]) {
+          knew = k;
+          break;
+        }
+      smp.E_run[slot] += n[s[i]] - n[knew];
+      s[i] = (int8_t)knew;
+    }
+  }
+}
+
 /* ---- measurement rows, indexed by temperature k (not slot) ---- */
 
 static int mag_entries(const State& st) {
@@ -300,10 +345,12 @@ void run_sweeps(State& st, int algo, const double* beta, uint64_t nsweeps, uint3
             const int tslot = smp.slot_at[a][k];
             const int slot = tslot * R + a;
             for (uint64_t t = t0; t < t0 + chunk; ++t) {
-              if (st.model == 0)
+              if (st.model == MODEL_ISING)
                 sweep_ising(st, smp, slot, algo, beta[k], t);
-              else
+              else if (st.model == MODEL_POTTS)
                 sweep_potts(st, smp, slot, beta[k], t);
+              else
+                sweep_perm(st, smp, slot, beta[k], t);
             }
           }
       }

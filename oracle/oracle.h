@@ -10,8 +10,10 @@
  * from the published definition of Philox4x32-10.
  *
  * Every function follows the paper's steps in plain loops:
- *   Hamiltonians          Sec. 2.1, Eq. (2) (EA: x_i = 1, h_i = 0, J = +-1)
- *                         and a J-weighted form of Eq. (3) for Potts
+ *   Hamiltonians          Sec. 2.1, Eq. (2) (EA: x_i = 1, h_i = 0, J = +-1;
+ *                         RFIM, DAFF), a J-weighted form of Eq. (3) for
+ *                         Potts (model 1) and the permutation form of
+ *                         Eq. (3) itself (model 2, 2 to 4 dimensions)
  *   Metropolis, heat bath Sec. 2.2 (acceptance exp(-beta dE); Eq. (4))
  *   sweep                 Sec. 2.2 (every site once per sweep)
  *   checkerboard          Sec. 3.1 (all of one colour, then the other)
@@ -28,7 +30,12 @@ namespace oracle {
 /* Philox4x32 with 10 rounds (Salmon et al., SC'11). */
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
-enum { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6, TAG_H = 7, TAG_X = 8 };
+enum { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6, TAG_H = 7, TAG_X = 8,
+       TAG_PERM = 9 };
+
+/* Models: 0 = Ising-like (Eq. 2), 1 = Potts with J = +-1 weights, 2 = the
+ * glassy Potts model of Eq. (3) with permutation couplings. */
+enum { MODEL_ISING = 0, MODEL_POTTS = 1, MODEL_PERM = 2 };
 
 /* Disorder kinds of the Ising-like Hamiltonian, Eq. (2) (Sec. 2.1). */
 enum { DIS_EA = 0, DIS_FERRO = 1, DIS_RFIM = 2, DIS_DAFF = 3 };
@@ -41,6 +48,12 @@ int ising_init_bit(uint64_t seed, int sample, int slot, uint32_t site);   /* 1 m
 int potts_init_state(uint64_t seed, int sample, int slot, uint32_t site); /* 0..3           */
 int field_sign_bit(uint64_t seed, int sample, uint32_t site);             /* 1 means h_i < 0 */
 uint32_t occupation_random(uint64_t seed, int sample, uint32_t site);     /* plane-assembled  */
+/* Permutation coupling of bond (d, site) of sample s: an index 0..23 into the
+ * permutations of (0,1,2,3) in lexicographic order. */
+int perm_coupling_index(uint64_t seed, int sample, int d, uint32_t site);
+void perm_unrank(int index, int out[4]);   /* the index-th permutation, lexicographic */
+int perm_code(int index);                  /* pi(0) | pi(1) << 2 | pi(2) << 4 | pi(3) << 6 */
+int perm_index_of_code(int code);          /* inverse of perm_code; -1 if not a permutation */
 
 /* Acceptance thresholds, values in [0, 2^32]; decision is r < T. */
 uint64_t table_metropolis(double beta, int dE);
@@ -54,7 +67,8 @@ uint64_t table_heatbath_x(double beta, double x);   /* keep prob                
 
 struct Sample {
   int s;                                    /* true sample index (drives the streams) */
-  std::vector<int8_t> J;                    /* [D][N], +-1, forward bonds J_d(i)      */
+  std::vector<int8_t> J;                    /* [D][N] forward bonds J_d(i): +-1, or the
+                                               permutation index (model 2)             */
   std::vector<int8_t> x;                    /* [N] dilution, 1 = occupied              */
   std::vector<int8_t> hs;                   /* [N] sign of the field h_i (+-1)         */
   std::vector<std::vector<int8_t>> spin;    /* [slots][N]; Ising +-1, Potts 0..q-1     */
@@ -65,7 +79,7 @@ struct Sample {
 };
 
 struct State {
-  int model;        /* 0 = Ising-like (Eq. 2), 1 = Potts */
+  int model;        /* MODEL_* */
   int disorder;     /* DIS_* for the Ising-like model */
   double hmag;      /* |h| */
   int q;            /* Potts states (4 in the library; any >= 2 here) */
@@ -95,6 +109,7 @@ int64_t overlap(const State& st, const Sample& smp, int slot_a, int slot_b);
 /* One sweep of one configuration at inverse temperature beta (sweep index t). */
 void sweep_ising(const State& st, Sample& smp, int slot, int algo, double beta, uint64_t t);
 void sweep_potts(const State& st, Sample& smp, int slot, double beta, uint64_t t);
+void sweep_perm(const State& st, Sample& smp, int slot, double beta, uint64_t t);
 
 /* nsweeps sweeps of every configuration; beta indexed by temperature. */
 void run_sweeps(State& st, int algo, const double* beta, uint64_t nsweeps, uint32_t measure_every,

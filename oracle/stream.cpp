@@ -113,6 +113,41 @@ int field_sign_bit(uint64_t seed, int sample, uint32_t site) {
   return (int)((w >> (sample & 63)) & 1u);
 }
 
+/* Eq. (3) couplings: one of the 4! permutations, chosen by the 32-bit random
+ * x of the bond as floor(24 x / 2^32). */
+int perm_coupling_index(uint64_t seed, int sample, int d, uint32_t site) {
+  uint32_t x[4];
+  call(seed, site, (uint32_t)d, ((uint32_t)TAG_PERM << 28) | ((uint32_t)sample >> 2), 0u, x);
+  return (int)(((uint64_t)x[sample & 3] * 24u) >> 32);
+}
+
+/* Lexicographic unranking: digit pos of the factorial number system picks
+ * among the values not used yet, in increasing order. */
+void perm_unrank(int index, int out[4]) {
+  int pool[4] = {0, 1, 2, 3};
+  int left = 4;
+  const int weight[4] = {6, 2, 1, 1};
+  for (int pos = 0; pos < 4; ++pos) {
+    const int pick = index / weight[pos];
+    index %= weight[pos];
+    out[pos] = pool[pick];
+    for (int m = pick; m + 1 < left; ++m) pool[m] = pool[m + 1];
+    --left;
+  }
+}
+
+int perm_code(int index) {
+  int p[4];
+  perm_unrank(index, p);
+  return p[0] | (p[1] << 2) | (p[2] << 4) | (p[3] << 6);
+}
+
+int perm_index_of_code(int code) {
+  for (int k = 0; k < 24; ++k)
+    if (perm_code(k) == (code & 0xff)) return k;
+  return -1;
+}
+
 /* 32-bit random of the dilution stream, assembled from its bit-planes. */
 uint32_t occupation_random(uint64_t seed, int sample, uint32_t site) {
   const uint32_t g = (uint32_t)sample >> 6;
