@@ -467,6 +467,98 @@ def run_other_configs(args):
         out["potts_L32_128x2"]["cpu_baseline"] = {"value": 2 * 2 * 32 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2,
                                                   "kind": "oracle", "sample": "samples 0, 127 x 2 replicas, 2 sweeps"}
     del po
+    # random-field Ising model (Eq. 2, h_i = +-|h|), bit-sliced layout, heat bath
+    hm, Tr = 1.5, 2.0
+    rf = ianus.Lattice(dim=3, L=64, n_samples=256, n_replicas=1, seed=SEED + 4, layout="bits64", disorder="rfim",
+                       field=hm, stream=stream)
+    rf.sweep(ianus.HEATBATH, 1 / Tr, 10, 10)
+    reps = 10
+    sec = timed(lambda: rf.sweep(ianus.HEATBATH, 1 / Tr, 100, 10), reps)
+    upd = 256 * 64 ** 3 * 100 * reps
+    rate = upd / (sec * 1e9)
+    # per word: e-words 12, adder tree 16, f and 14 (u, f) class masks 16,
+    # "always" 14; per plane 14 class selections + compare 4; per pair Philox
+    # 21 ALU + merge 2; ~3.9 plane pairs per word
+    alu_word = 58 + 3.9 * (2 * 18 + 23)
+    out["rfim_L64_256_h1.5"] = {
+        "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
+        "mode": "bit-sliced, per-lane planes of 16 (u, f) classes, heat bath T=2.0, |h|=1.5, E/M/F every 10 sweeps",
+        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
+                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
+                     "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(dim=3, L=64, sample_ids=[0, 255], seed=SEED + 4, disorder=oracle.DIS_RFIM, field=hm)
+        t0 = time.perf_counter()
+        o.sweep(oracle.HEATBATH, 1 / Tr, 2, nthreads=2)
+        dt = time.perf_counter() - t0
+        out["rfim_L64_256_h1.5"]["cpu_baseline"] = {"value": 2 * 64 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2,
+                                                    "kind": "oracle", "sample": "samples 0, 255, 2 sweeps"}
+    del rf
+    # diluted antiferromagnet in a field, plain layout, Metropolis
+    hd, occ, Td = 1.0, 0.7, 1.5
+    da = ianus.Lattice(dim=3, L=64, n_samples=256, n_replicas=1, seed=SEED + 5, layout="i8", disorder="daff",
+                       field=hd, occupation=occ, stream=stream)
+    da.sweep(ianus.METROPOLIS, 1 / Td, 10, 10)
+    reps = 3
+    sec = timed(lambda: da.sweep(ianus.METROPOLIS, 1 / Td, 50, 10), reps)
+    upd = 256 * 64 ** 3 * 50 * reps
+    rate = upd / (sec * 1e9)
+    # unique bytes per site and sweep: spin read + write (2), D forward
+    # couplings (3), occupation (1), field sign (1)
+    bytes_site = 7.0
+    hbm = MEASURED.get("hbm_gbs")
+    out["daff_L64_256_occ0.7_h1.0"] = {
+        "updates_per_ns": rate, "ms_per_50_sweeps": sec * 1e3 / reps,
+        "mode": "plain int8 per spin, Metropolis T=1.5, |h|=1.0, occupation 0.7, E/M/F every 10 sweeps",
+        "roofline": {"bound": "hbm", "bytes_per_update": bytes_site, "achieved": rate * bytes_site,
+                     "peak": hbm, "unit": "GB/s", "frac": (rate * bytes_site / hbm) if hbm else None},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(dim=3, L=64, sample_ids=[0, 255], seed=SEED + 5, disorder=oracle.DIS_DAFF, field=hd,
+                          occupation=occ)
+        t0 = time.perf_counter()
+        o.sweep(oracle.METROPOLIS, 1 / Td, 2, nthreads=2)
+        dt = time.perf_counter() - t0
+        out["daff_L64_256_occ0.7_h1.0"]["cpu_baseline"] = {
+            "value": 2 * 64 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2, "kind": "oracle",
+            "sample": "samples 0, 255, 2 sweeps"}
+    del da
+    # glassy Potts model with permutation couplings (Eq. 3), 3D and 4D, heat bath
+    for dim, Lp, bp, key in ((3, 32, 2.4, "potts_perm_3d_L32_256x2"), (4, 16, 1.405, "potts_perm_4d_L16_256x2")):
+        pp = ianus.Lattice(model="potts_perm", dim=dim, L=Lp, n_samples=256, n_replicas=2, seed=SEED + 6,
+                           stream=stream)
+        pp.sweep(ianus.HEATBATH, bp, 10, 10)
+        reps = 5
+        sec = timed(lambda: pp.sweep(ianus.HEATBATH, bp, 100, 10), reps)
+        upd = 256 * 2 * Lp ** dim * 100 * reps
+        rate = upd / (sec * 1e9)
+        # per 4-sample word: Philox 21; per sample and bond ~7 (state and code
+        # fields, target state, nibble increment), table index 4, selection 6,
+        # pack 2
+        alu_word = 21 + 4 * (2 * dim * 7 + 12)
+        out[key] = {
+            "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
+            "mode": f"4 samples per uint32 word, {dim}D, heat bath beta={bp}, E/Q every 10 sweeps",
+            "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 4, "achieved": rate * alu_word / 4 / 1e3,
+                         "peak": peak, "unit": "T ALU-pipe int32 ops/s",
+                         "frac": (rate * alu_word / 4 / 1e3 / peak) if peak else None},
+        }
+        if not args.no_cpu_baseline:
+            import oracle
+
+            o = oracle.Oracle(model=oracle.MODEL_PERM, dim=dim, L=Lp, sample_ids=[0, 255], n_replicas=2,
+                              seed=SEED + 6)
+            t0 = time.perf_counter()
+            o.sweep(oracle.HEATBATH, bp, 1, nthreads=2)
+            dt = time.perf_counter() - t0
+            out[key]["cpu_baseline"] = {"value": 2 * 2 * Lp ** dim / (dt * 1e9), "unit": UNIT, "cores": 2,
+                                        "kind": "oracle", "sample": "samples 0, 255 x 2 replicas, 1 sweep"}
+        del pp
     # device-side set-up: couplings and initial spins of the bench workload from the seed
     t0 = time.perf_counter()
     lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 3, layout="bits64", stream=stream)
@@ -475,6 +567,19 @@ def run_other_configs(args):
                              "what": "ianus_lattice_create: buffer clear + couplings and spins from the seed (wall)"}
     del lat
     return out
+
+
+def _measured_peaks() -> dict:
+    """Measured copy bandwidth and GEMM peaks of this GPU model, if recorded."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+MEASURED = _measured_peaks()
 
 
 def _alu_peak():

@@ -24,9 +24,10 @@
  * ------------------------------------------------------------------------
  * Lattice, colours, bonds (Sec. 2.1; Sec. 3.1)
  * ------------------------------------------------------------------------
- *   D in {2,3}, side L even and >= 2, N = L^D sites, periodic boundaries.
- *   Site index i = x + L*(y + L*z)  (z = 0 when D = 2).
- *   Colour c(i) = (x + y + z) mod 2.  A sweep updates every colour-0 site,
+ *   D in {2,3} (the permutation Potts model: D in {2,3,4}), side L even and
+ *   >= 2, N = L^D sites, periodic boundaries.
+ *   Site index i = x + L*(y + L*(z + L*w))  (missing coordinates are 0).
+ *   Colour c(i) = (x + y + z + w) mod 2.  A sweep updates every colour-0 site,
  *   then every colour-1 site; no bond joins two sites of the same colour.
  *   Bonds are stored as forward bonds J_d(i) joining i and i + e_d
  *   (d = 0..D-1, periodic); the backward bond of i along d is J_d(i - e_d).
@@ -58,7 +59,7 @@
  *   of its coordinates only, so results do not depend on memory layout,
  *   kernel choice, launch shape or on how sweeps are split across calls.
  *   Tags: SPIN = 1, J = 2, INIT = 3, POTTS = 4, PINIT = 5, PT = 6, H = 7,
- *   X = 8.
+ *   X = 8, PERM = 9.
  *   Sample s lives in group g = s >> 6 at lane l = s & 63.
  *
  *   Ising update random r(s, sigma, i, t), t = absolute sweep index:
@@ -90,6 +91,13 @@
  *     c3 = t >> 32).
  *   Potts initial state: x_{s & 3} >> 30 of Philox(key, c0 = i, c1 = 0,
  *     c2 = (PINIT << 28) | (sigma << 16) | (s >> 2), c3 = 0).
+ *   Permutation couplings (IANUS_POTTS4_PERM, Eq. (3)): bond (d, i) of
+ *     sample s carries permutation number p = floor(24 x / 2^32), x = x_{s & 3}
+ *     of Philox(key, c0 = i, c1 = d, c2 = (PERM << 28) | (s >> 2), c3 = 0),
+ *     where permutations of (0,1,2,3) are numbered in lexicographic order
+ *     (0 = (0,1,2,3), 23 = (3,2,1,0)).  It is stored and exchanged as the
+ *     8-bit code pi(0) | pi(1) << 2 | pi(2) << 4 | pi(3) << 6.
+ *     (IANUS_DISORDER_FERRO: every pi is the identity.)
  *   Parallel-tempering random for chain (s, a), temperature pair k, swap
  *     step tau: x_{s & 3} of Philox(key, c0 = k, c1 = tau & 0xffffffff,
  *     c2 = (PT << 28) | (a << 16) | (s >> 2), c3 = tau >> 32).
@@ -114,6 +122,12 @@
  *     w_k = exp(beta * n_k); S0 = w0; S1 = S0 + w1; S2 = S1 + w2;
  *     Z = S2 + w3; T_k = floor(ldexp(S_k / Z, 32)) for k = 0, 1, 2;
  *     new state = smallest k in 0..2 with r < T_k, else 3.
+ *   Permutation Potts heat bath (Eq. (3)): n_k = number of bonds of site i
+ *     satisfied when s_i = k, in 0..2D: a forward bond (i, i + e_d) with
+ *     permutation pi is satisfied iff k = pi(s_{i+e_d}), a backward bond
+ *     (i - e_d, i) with permutation pi iff s_{i-e_d} = pi(k).  Same
+ *     thresholds and selection as above.  Temperatures with 2 D beta > 700
+ *     are rejected (EINVAL).
  *   Parallel tempering (pair k of temperatures k and k+1):
  *     db = beta[k] - beta[k+1]; energies of the configurations at
  *     temperatures k and k+1 are E_A and E_B, d = E_B - E_A (a multiple of 4
@@ -135,6 +149,8 @@
  *   Ising: E = -sum_bonds J s s, M = sum_i s_i, Q = sum_i s_i^0 s_i^1.
  *   Potts: E = -sum_bonds J delta(s_i, s_j); "magnetisation" = the four
  *     state counts n_k; Q = sum_i delta(s_i^0, s_i^1).
+ *   Permutation Potts: E = -sum_bonds delta(s_i, pi_ij(s_j)) over forward
+ *     bonds (i, j = i + e_d); counts and Q as for Potts.
  *   RFIM / DAFF: "energy" = the bond part E_J = -sum_bonds J x_i x_j s_i s_j;
  *     "magnetisation" = two values, M = sum_i x_i s_i and the field sum
  *     F = sum_i sign(h_i) x_i s_i, so that E = E_J - |h| F;
@@ -164,7 +180,11 @@ typedef enum {
   IANUS_ESTATE = 6       /* lattice is in an error state / bad state blob */
 } ianus_status;
 
-typedef enum { IANUS_EA_PM_J = 0, IANUS_POTTS4_J = 1 } ianus_model;
+typedef enum {
+  IANUS_EA_PM_J = 0,     /* Ising-like models of Eq. (2): EA +-J, RFIM, DAFF      */
+  IANUS_POTTS4_J = 1,    /* q = 4 Potts glass H = -sum J_ij delta(s_i, s_j)      */
+  IANUS_POTTS4_PERM = 2  /* glassy Potts model of Eq. (3), permutation couplings */
+} ianus_model;
 typedef enum { IANUS_METROPOLIS = 0, IANUS_HEATBATH = 1 } ianus_algo;
 typedef enum {
   IANUS_LAYOUT_AUTO = 0,   /* BITS64 for Ising, U8X4 for Potts              */
@@ -183,7 +203,7 @@ typedef enum {
 typedef struct {
   uint32_t abi_version;     /* must equal IANUS_ABI_VERSION                 */
   int32_t model;            /* ianus_model                                  */
-  int32_t dim;              /* 2 or 3                                       */
+  int32_t dim;              /* 2 or 3 (IANUS_POTTS4_PERM: 2, 3 or 4)         */
   int32_t L;                /* even, >= 2                                   */
   int32_t n_samples;        /* disorder samples, >= 1                       */
   int32_t n_replicas;       /* real replicas per sample and temperature     */
@@ -274,9 +294,11 @@ ianus_status ianus_get_spins_i8(ianus_lattice* lat, int8_t* host);
 /* Overwrites every slot's spins from the same layout (Ising values must be
  * +-1, Potts 0..3; else EINVAL).  Asynchronous w.r.t. the device. */
 ianus_status ianus_set_spins_i8(ianus_lattice* lat, const int8_t* host);
-/* Couplings: int8 [n_samples][dim][N], J_d(i) in {+1,-1}.  Synchronous. */
+/* Couplings: int8 [n_samples][dim][N], J_d(i) in {+1,-1} (permutation
+ * Potts: the 8-bit permutation code as int8).  Synchronous. */
 ianus_status ianus_get_couplings_i8(ianus_lattice* lat, int8_t* host);
-/* Overwrites the couplings (values must be +-1).  Used for gauge tests. */
+/* Overwrites the couplings (values must be +-1, or permutation codes for the
+ * permutation Potts model; else EINVAL).  Used for gauge tests. */
 ianus_status ianus_set_couplings_i8(ianus_lattice* lat, const int8_t* host);
 /* Site disorder of the Ising-like models (Eq. (2)): hsign int8 [n_samples][N]
  * = sign of h_i (+-1; +1 everywhere unless RFIM) and occupied int8
@@ -411,6 +433,10 @@ size_t ianus_table_ising(int32_t dim, int32_t algo, double beta, uint64_t* out,
  * *13 + n2+6)*13 + n3+6, for all 13^4 tuples (also unreachable ones).
  * n must be >= 3 * 13^4.  Returns the count written or 0. */
 size_t ianus_table_potts(double beta, uint64_t* out, size_t n);
+/* Potts heat bath for one tuple of counts n[0..3] (any integers, the
+ * permutation model's n_k in 0..2D included): T[k] as above for k = 0..2.
+ * Returns 3, or 0 on bad arguments (NULL, beta not finite or < 0). */
+size_t ianus_table_potts_counts(double beta, const int32_t* n, uint64_t* T);
 /* PT: out[m-1] = T_PT(|d| = 4 m) = floor(ldexp(exp(-|db| * 4m), 32)) for
  * m = 1..n, db = beta_k - beta_k1.  Returns n, or 0 on bad arguments. */
 size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);

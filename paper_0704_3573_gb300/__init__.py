@@ -21,14 +21,14 @@ from . import build as _build
 
 ABI_VERSION = 2
 
-EA_PM_J, POTTS4_J = 0, 1
+EA_PM_J, POTTS4_J, POTTS4_PERM = 0, 1, 2
 METROPOLIS, HEATBATH = 0, 1
 LAYOUT_AUTO, LAYOUT_I8, LAYOUT_BITS64, LAYOUT_U8X4 = 0, 1, 2, 3
 DISORDER_PM_J, DISORDER_FERRO, DISORDER_RFIM, DISORDER_DAFF = 0, 1, 2, 3
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = range(7)
 
-_MODELS = {"ea": EA_PM_J, "potts": POTTS4_J}
+_MODELS = {"ea": EA_PM_J, "potts": POTTS4_J, "potts_perm": POTTS4_PERM}
 _ALGOS = {"metropolis": METROPOLIS, "heatbath": HEATBATH}
 _LAYOUTS = {"auto": LAYOUT_AUTO, "i8": LAYOUT_I8, "bits64": LAYOUT_BITS64, "u8x4": LAYOUT_U8X4}
 _DISORDERS = {"pm_j": DISORDER_PM_J, "ferro": DISORDER_FERRO, "rfim": DISORDER_RFIM, "daff": DISORDER_DAFF}
@@ -40,6 +40,7 @@ EXPORTS = [
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
     "ianus_set_graphs", "ianus_set_resident", "ianus_get_sites_i8", "ianus_set_sites_i8", "ianus_table_field",
+    "ianus_table_potts_counts",
 ]
 
 
@@ -119,6 +120,7 @@ def lib(build_if_missing: bool = True):
         "ianus_get_sites_i8": (i32, [vp, vp, vp]),
         "ianus_set_sites_i8": (i32, [vp, vp, vp]),
         "ianus_table_field": (sz, [i32, i32, C.c_double, C.c_double, vp, sz]),
+        "ianus_table_potts_counts": (sz, [C.c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -161,6 +163,15 @@ def table_pt(beta_k: float, beta_k1: float, n: int) -> np.ndarray:
     return out
 
 
+def table_potts_counts(beta: float, n) -> list[int]:
+    """Potts heat-bath thresholds T_0..T_2 for one tuple of counts n_0..n_3."""
+    nn = np.ascontiguousarray(n, dtype=np.int32)
+    out = np.zeros(3, dtype=np.uint64)
+    if lib().ianus_table_potts_counts(beta, _ptr(nn), _ptr(out)) != 3:
+        raise ValueError("bad table arguments")
+    return [int(v) for v in out]
+
+
 def table_field(dim: int, algo: int, beta: float, field: float) -> np.ndarray:
     """Thresholds of the field models, indexed [(v + 2 dim) * 2 + f]."""
     out = np.zeros(32, dtype=np.uint64)
@@ -193,7 +204,7 @@ class Lattice:
             disorder = DISORDER_FERRO if ferro else DISORDER_PM_J
         self.disorder = _DISORDERS[disorder] if isinstance(disorder, str) else int(disorder)
         self.field, self.occupation = float(field), float(occupation)
-        self.mq = 4 if self.model == POTTS4_J else (2 if self.disorder in (DISORDER_RFIM, DISORDER_DAFF) else 1)
+        self.mq = 4 if self.model != EA_PM_J else (2 if self.disorder in (DISORDER_RFIM, DISORDER_DAFF) else 1)
         dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         if stream is None:
             stream = torch.cuda.current_stream(dev)

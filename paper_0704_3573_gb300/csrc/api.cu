@@ -36,8 +36,8 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 int plan(const ianus_config* c, Sizes& z) {
   if (!c) return IANUS_EINVAL;
   if (c->abi_version != IANUS_ABI_VERSION) return IANUS_EINVAL;
-  if (c->model != IANUS_EA_PM_J && c->model != IANUS_POTTS4_J) return IANUS_EINVAL;
-  if (c->dim != 2 && c->dim != 3) return IANUS_EINVAL;
+  if (c->model != IANUS_EA_PM_J && c->model != IANUS_POTTS4_J && c->model != IANUS_POTTS4_PERM) return IANUS_EINVAL;
+  if (c->dim != 2 && c->dim != 3 && !(c->dim == 4 && c->model == IANUS_POTTS4_PERM)) return IANUS_EINVAL;
   if (c->L < 2 || (c->L & 1) || c->L > 4096) return IANUS_EINVAL;
   if (c->n_samples < 1 || c->n_samples >= (1 << 18)) return IANUS_EINVAL;
   if (c->n_replicas < 1 || c->n_temps < 1) return IANUS_EINVAL;
@@ -52,12 +52,12 @@ int plan(const ianus_config* c, Sizes& z) {
   for (int d = 0; d < c->dim; ++d) N *= (uint64_t)c->L;
   if (N >= (1ull << 31)) return IANUS_EINVAL;
   int layout = c->layout;
+  const bool potts = c->model != IANUS_EA_PM_J;
   if (layout == IANUS_LAYOUT_AUTO)
-    layout = c->model == IANUS_POTTS4_J ? IANUS_LAYOUT_U8X4
-             : c->disorder == IANUS_DISORDER_DAFF ? IANUS_LAYOUT_I8 : IANUS_LAYOUT_BITS64;
+    layout = potts ? IANUS_LAYOUT_U8X4 : c->disorder == IANUS_DISORDER_DAFF ? IANUS_LAYOUT_I8 : IANUS_LAYOUT_BITS64;
   if (layout < IANUS_LAYOUT_I8 || layout > IANUS_LAYOUT_U8X4) return IANUS_EINVAL;
-  if (c->model == IANUS_EA_PM_J && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
-  if (c->model == IANUS_POTTS4_J && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
+  if (!potts && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
+  if (potts && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (c->disorder == IANUS_DISORDER_DAFF && layout == IANUS_LAYOUT_BITS64) return IANUS_EUNSUPPORTED;
   if (layout == IANUS_LAYOUT_BITS64 &&  // the sweep stages one block's threshold planes in shared memory
       (size_t)c->n_replicas * kPlanes * (field ? kFieldPlaneClasses : kMaxClasses) * 8 > kMaxSmemPerBlock)
@@ -74,7 +74,7 @@ int plan(const ianus_config* c, Sizes& z) {
   z.G = (z.S + 63) / 64;
   z.Q4 = (z.S + 3) / 4;
   z.field = field;
-  z.mq = c->model == IANUS_POTTS4_J ? 4 : (field ? 2 : 1);
+  z.mq = potts ? 4 : (field ? 2 : 1);
   z.cap = c->series_capacity ? c->series_capacity : kDefaultSeries;
   z.pt_cap = z.K > 1 ? (uint32_t)std::min<uint64_t>((uint64_t)z.D * N / 2 + 1, kPtCapMax) : 0;
   if (layout == IANUS_LAYOUT_I8) {
@@ -102,7 +102,9 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 : 0);
   z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
   z.off_sites = take(z.sites_bytes);
-  z.off_ptab = take(layout == IANUS_LAYOUT_U8X4 ? (size_t)z.K * 65536 * 16 : 0);
+  z.off_ptab = take(layout != IANUS_LAYOUT_U8X4 ? 0
+                    : c->model == IANUS_POTTS4_PERM ? (size_t)z.K * perm_table_entries(z.D) * 16
+                                                    : (size_t)z.K * 65536 * 16);
   z.off_pttab = take((size_t)std::max(z.K - 1, 0) * z.pt_cap * 8);
   z.off_ptsign = take((size_t)std::max(z.K - 1, 1));
   z.off_slot = take((size_t)z.S * z.R * z.K * 4 * 2);  // slot_at then temp_of
@@ -186,6 +188,30 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     }
     lat->jit = nullptr;  // specialised lazily by the first launch that wants it
     lat->jit_algo = -1;
+  } else if (lat->model == IANUS_POTTS4_PERM) {
+    // compact table of the permutation model: counts n_k in 0..2D with
+    // n0 + n1 + n2 + n3 = 2D, entry n0 + B (n1 + B n2), B = 2D + 1
+    const int D = lat->D, B = 2 * D + 1;
+    for (int k = 0; k < K; ++k)
+      if (2.0 * D * beta[k] > 700.0) return IANUS_EINVAL;  // exp(2D beta) must stay finite
+    const uint32_t NT = perm_table_entries(D);
+    std::vector<uint4> tab((size_t)K * NT);
+    std::memset(tab.data(), 0, tab.size() * sizeof(uint4));
+    for (int k = 0; k < K; ++k)
+      for (int n0 = 0; n0 <= 2 * D; ++n0)
+        for (int n1 = 0; n0 + n1 <= 2 * D; ++n1)
+          for (int n2 = 0; n0 + n1 + n2 <= 2 * D; ++n2) {
+            const int n[4] = {n0, n1, n2, 2 * D - n0 - n1 - n2};
+            uint64_t T[3];
+            potts_thresholds(beta[k], n, T);
+            uint4 e;
+            e.x = (uint32_t)T[0];
+            e.y = (uint32_t)T[1];
+            e.z = (uint32_t)T[2];
+            e.w = (T[0] >= kTwo32 ? 1u : 0u) | (T[1] >= kTwo32 ? 2u : 0u) | (T[2] >= kTwo32 ? 4u : 0u);
+            tab[(size_t)k * NT + n0 + B * (n1 + B * n2)] = e;
+          }
+    CK(cudaMemcpyAsync(lat->ptab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice, lat->stream));
   } else {
     if (beta_ok(beta, K)) {
       for (int k = 0; k < K; ++k)
@@ -213,7 +239,7 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     }
     CK(cudaMemcpyAsync(lat->ptab, tab.data(), tab.size() * sizeof(uint4), cudaMemcpyHostToDevice, lat->stream));
   }
-  if (K > 1 && !lat->field) {
+  if (K > 1 && lat->model == IANUS_EA_PM_J && !lat->field) {
     // PT tables: T(m) for |d| = 4m until the first zero (or the largest
     // possible |d|/4 = D N / 2).
     std::vector<uint64_t> pt((size_t)(K - 1) * lat->pt_cap, 0);
@@ -518,7 +544,7 @@ ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uin
   GET_LAT(h);
   if (!beta || (algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH)) return IANUS_EINVAL;
   if (!beta_ok(beta, lat->K)) return IANUS_EINVAL;
-  if (lat->model == IANUS_POTTS4_J && algo == IANUS_METROPOLIS) return IANUS_EUNSUPPORTED;
+  if (lat->model != IANUS_EA_PM_J && algo == IANUS_METROPOLIS) return IANUS_EUNSUPPORTED;
   if (!lat->tables_ok || lat->algo != algo || !same_beta(lat, beta)) {
     int st = upload_tables(lat, algo, beta);
     if (st) return (ianus_status)st;
@@ -676,8 +702,15 @@ ianus_status ianus_set_couplings_i8(ianus_lattice* h, const int8_t* host) {
   GET_LAT(h);
   if (!host) return IANUS_EINVAL;
   const size_t bytes = (size_t)lat->S * lat->D * lat->N;
-  for (size_t i = 0; i < bytes; ++i)
-    if (host[i] != 1 && host[i] != -1) return IANUS_EINVAL;
+  for (size_t i = 0; i < bytes; ++i) {
+    if (lat->model == IANUS_POTTS4_PERM) {  // the four 2-bit fields must be 0, 1, 2, 3 in some order
+      const uint32_t c = (uint8_t)host[i];
+      const uint32_t seen = (1u << (c & 3u)) | (1u << ((c >> 2) & 3u)) | (1u << ((c >> 4) & 3u)) | (1u << (c >> 6));
+      if (seen != 0xFu) return IANUS_EINVAL;
+    } else if (host[i] != 1 && host[i] != -1) {
+      return IANUS_EINVAL;
+    }
+  }
   auto fn = lat->layout == IANUS_LAYOUT_I8 ? launch_set_couplings_i8
             : lat->layout == IANUS_LAYOUT_BITS64 ? launch_set_couplings_bits : launch_set_couplings_potts;
   return staged_set(lat, host, bytes, fn);

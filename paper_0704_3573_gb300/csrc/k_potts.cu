@@ -305,6 +305,7 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 }  // namespace
 
 cudaError_t launch_init_potts(Lattice& lat, int jmode) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_init_perm(lat, jmode);
   const int ferro = jmode == 1;  // Potts lattices take the J stream or J = +1
   k_init_potts<<<grid_for((uint64_t)lat.Q4 * lat.N), 256, 0, lat.stream>>>(
       (uint32_t*)lat.spins, (uint32_t*)lat.J, lat.geom, lat.Q4, lat.slots, ferro, lat.keys);
@@ -312,6 +313,7 @@ cudaError_t launch_init_potts(Lattice& lat, int jmode) {
 }
 
 cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_sweep_perm(lat, colour, t);
   PottsParams p;
   p.spins = (uint32_t*)lat.spins;
   p.J = (const uint32_t*)lat.J;
@@ -344,6 +346,7 @@ cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t) {
 }
 
 cudaError_t launch_measure_potts(Lattice& lat, int want_q) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_measure_perm(lat, want_q);
   cudaError_t e = cudaMemsetAsync(lat.acc, 0, (size_t)lat.S * lat.slots * kAccStride * sizeof(int64_t), lat.stream);
   if (e != cudaSuccess) return e;
   const uint32_t per_block = kBlock * kPottsMeasIters;
@@ -354,33 +357,41 @@ cudaError_t launch_measure_potts(Lattice& lat, int want_q) {
   else
     k_measure_potts<2><<<grid, kBlock, 0, lat.stream>>>((const uint32_t*)lat.spins, (const uint32_t*)lat.J,
                                                          lat.acc, lat.geom, lat.S, lat.Q4, lat.slots);
-  if (want_q && lat.R >= 2) {
-    dim3 gq((lat.N + per_block - 1) / per_block, (unsigned)(lat.Q4 * lat.K));
-    k_overlap_potts<<<gq, kBlock, 0, lat.stream>>>((const uint32_t*)lat.spins, lat.slot_at, lat.acc, lat.N, lat.S,
-                                                   lat.R, lat.K, lat.Q4, lat.slots);
-  }
+  if (want_q && lat.R >= 2) return launch_overlap_potts(lat);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_overlap_potts(Lattice& lat) {
+  const uint32_t per_block = kBlock * kPottsMeasIters;
+  dim3 gq((lat.N + per_block - 1) / per_block, (unsigned)(lat.Q4 * lat.K));
+  k_overlap_potts<<<gq, kBlock, 0, lat.stream>>>((const uint32_t*)lat.spins, lat.slot_at, lat.acc, lat.N, lat.S,
+                                                 lat.R, lat.K, lat.Q4, lat.slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_spins_potts(Lattice& lat, int8_t* dev_out) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_get_spins_perm(lat, dev_out);
   k_get_spins_potts<<<grid_for((uint64_t)lat.S * lat.slots * lat.N), 256, 0, lat.stream>>>(
       (const uint32_t*)lat.spins, dev_out, lat.geom, lat.S, lat.Q4, lat.slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_spins_potts(Lattice& lat, const int8_t* dev_in) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_set_spins_perm(lat, dev_in);
   k_set_spins_potts<<<grid_for((uint64_t)lat.slots * lat.Q4 * lat.N), 256, 0, lat.stream>>>(
       (uint32_t*)lat.spins, dev_in, lat.geom, lat.S, lat.Q4, lat.slots);
   return cudaGetLastError();
 }
 
 cudaError_t launch_get_couplings_potts(Lattice& lat, int8_t* dev_out) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_get_couplings_perm(lat, dev_out);
   k_get_couplings_potts<<<grid_for((uint64_t)lat.S * lat.D * lat.N), 256, 0, lat.stream>>>(
       (const uint32_t*)lat.J, dev_out, lat.geom, lat.S);
   return cudaGetLastError();
 }
 
 cudaError_t launch_set_couplings_potts(Lattice& lat, const int8_t* dev_in) {
+  if (lat.model == IANUS_POTTS4_PERM) return launch_set_couplings_perm(lat, dev_in);
   k_set_couplings_potts<<<grid_for((uint64_t)lat.Q4 * lat.D * lat.N), 256, 0, lat.stream>>>(
       (uint32_t*)lat.J, dev_in, lat.geom, lat.S, lat.Q4);
   return cudaGetLastError();

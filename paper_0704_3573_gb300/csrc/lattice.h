@@ -49,7 +49,7 @@ struct Lattice {
   void* J;              // I8: int8 [S][D][N];     BITS64: u64 [G][D][N];     U8X4: u32 [Q4][D][N]
   uint64_t* thr;        // Ising: u64 [K][kMaxClasses] threshold per class u
   uint64_t* tp;         // BITS64: u64 [G][slots][kMaxClasses][kPlanes]
-  uint4* ptab;          // Potts: uint4 [K][65536]
+  uint4* ptab;          // Potts: uint4 [K][65536]; permutation Potts: [K][(2D+1)^3]
   uint64_t* pttab;      // PT: u64 [K-1][pt_len], T_PT(|d| = 4m) at m-1
   int8_t* pt_sign;      // PT: sign of beta[k] - beta[k+1], [K-1]
   int32_t* slot_at;     // [S][R][K]
@@ -110,6 +110,8 @@ struct Lattice {
 // ---- host table builders (tables.cpp) ----
 size_t table_ising(int dim, int algo, double beta, uint64_t* out, size_t n);
 size_t table_potts(double beta, uint64_t* out, size_t n);
+// Potts heat-bath thresholds T[0..2] for one tuple of counts n[0..3].
+void potts_thresholds(double beta, const int* n, uint64_t* T);
 size_t table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n);
 // Threshold per class u = 0..2D for the unified rule "flip iff (r < T) != inv":
 // Metropolis: u < D -> T_M(4D - 4u), u >= D -> 2^32 (always); inv = 0.
@@ -167,6 +169,18 @@ cudaError_t launch_get_spins_potts(Lattice& lat, int8_t* dev_out);
 cudaError_t launch_set_spins_potts(Lattice& lat, const int8_t* dev_in);
 cudaError_t launch_get_couplings_potts(Lattice& lat, int8_t* dev_out);
 cudaError_t launch_set_couplings_potts(Lattice& lat, const int8_t* dev_in);
+cudaError_t launch_overlap_potts(Lattice& lat);  // Q into acc (both Potts models)
+// Permutation Potts model of Eq. (3), U8X4 storage, D = 2..4 (k_perm.cu).
+// The Potts launchers above forward to these for IANUS_POTTS4_PERM.
+cudaError_t launch_init_perm(Lattice& lat, int jmode);
+cudaError_t launch_sweep_perm(Lattice& lat, int colour, uint64_t t);
+cudaError_t launch_measure_perm(Lattice& lat, int want_q);
+cudaError_t launch_get_spins_perm(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_spins_perm(Lattice& lat, const int8_t* dev_in);
+cudaError_t launch_get_couplings_perm(Lattice& lat, int8_t* dev_out);
+cudaError_t launch_set_couplings_perm(Lattice& lat, const int8_t* dev_in);
+// compact permutation-model table: entry n0 + B (n1 + B n2), B = 2D + 1
+inline uint32_t perm_table_entries(int D) { return (uint32_t)(2 * D + 1) * (2 * D + 1) * (2 * D + 1); }
 // shared (k_pt.cu)
 cudaError_t launch_finalize(Lattice& lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q);
 cudaError_t launch_pt_swap(Lattice& lat);

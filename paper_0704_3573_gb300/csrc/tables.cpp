@@ -69,21 +69,26 @@ void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr
     }
 }
 
+// w_k = exp(beta n_k); S0 = w0, S1 = S0 + w1, S2 = S1 + w2, Z = S2 + w3;
+// T_k = floor(2^32 S_k / Z): the cumulative heat-bath thresholds.
+void potts_thresholds(double beta, const int* n, uint64_t* T) {
+  const double w0 = std::exp(beta * (double)n[0]), w1 = std::exp(beta * (double)n[1]);
+  const double w2 = std::exp(beta * (double)n[2]), w3 = std::exp(beta * (double)n[3]);
+  const double S0 = w0, S1 = S0 + w1, S2 = S1 + w2, Z = S2 + w3;
+  T[0] = to_threshold(S0 / Z);
+  T[1] = to_threshold(S1 / Z);
+  T[2] = to_threshold(S2 / Z);
+}
+
 size_t table_potts(double beta, uint64_t* out, size_t n) {
   const size_t need = 3u * 13u * 13u * 13u * 13u;
   if (!out || n < need || !(beta >= 0.0) || !std::isfinite(beta)) return 0;
   size_t idx = 0;
-  for (int n0 = -6; n0 <= 6; ++n0)
-    for (int n1 = -6; n1 <= 6; ++n1)
-      for (int n2 = -6; n2 <= 6; ++n2)
-        for (int n3 = -6; n3 <= 6; ++n3) {
-          const double w0 = std::exp(beta * (double)n0), w1 = std::exp(beta * (double)n1);
-          const double w2 = std::exp(beta * (double)n2), w3 = std::exp(beta * (double)n3);
-          const double S0 = w0, S1 = S0 + w1, S2 = S1 + w2, Z = S2 + w3;
-          out[idx++] = to_threshold(S0 / Z);
-          out[idx++] = to_threshold(S1 / Z);
-          out[idx++] = to_threshold(S2 / Z);
-        }
+  int c[4];
+  for (c[0] = -6; c[0] <= 6; ++c[0])
+    for (c[1] = -6; c[1] <= 6; ++c[1])
+      for (c[2] = -6; c[2] <= 6; ++c[2])
+        for (c[3] = -6; c[3] <= 6; ++c[3], idx += 3) potts_thresholds(beta, c, out + idx);
   return need;
 }
 
@@ -104,6 +109,12 @@ size_t ianus_table_ising(int32_t dim, int32_t algo, double beta, uint64_t* out, 
 size_t ianus_table_potts(double beta, uint64_t* out, size_t n) { return ianus::table_potts(beta, out, n); }
 size_t ianus_table_pt(double beta_k, double beta_k1, uint64_t* out, size_t n) {
   return ianus::table_pt(beta_k, beta_k1, out, n);
+}
+size_t ianus_table_potts_counts(double beta, const int32_t* n, uint64_t* T) {
+  if (!n || !T || !(beta >= 0.0) || !std::isfinite(beta)) return 0;
+  const int c[4] = {n[0], n[1], n[2], n[3]};
+  ianus::potts_thresholds(beta, c, T);
+  return 3;
 }
 size_t ianus_table_field(int32_t dim, int32_t algo, double beta, double field, uint64_t* out, size_t n) {
   const size_t need = (size_t)(2 * (4 * dim + 1));

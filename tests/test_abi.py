@@ -52,7 +52,11 @@ def test_required_bytes_validation():
     assert rb() > 0
     assert rb(L=5) == 0                      # odd side
     assert rb(L=0) == 0
-    assert rb(dim=4) == 0
+    assert rb(dim=4) == 0                    # 4D: the permutation Potts model only
+    assert rb(model=1, dim=4) == 0
+    assert rb(model=2, dim=4, L=4) > 0
+    assert rb(model=2, dim=4, L=4, layout=2) == 0
+    assert rb(model=3) == 0
     assert rb(S=0) == 0
     assert rb(R=64, K=64) == 0               # slot field limit 4096
     assert rb(model=1, layout=1) == 0        # Potts has no I8 layout
@@ -135,3 +139,14 @@ def test_field_tables_match_oracle(beta, h):
         for j in range(2 * dim + 1):
             v = -2 * dim + 2 * j
             assert t[(v + 2 * dim) * 2] == t[(v + 2 * dim) * 2 + 1] == e[j]
+
+
+@pytest.mark.parametrize("beta", [0.0, 0.7, 1.405, 2.4, 40.0])
+def test_potts_count_tables_match_oracle(beta):
+    """Permutation model counts n_k in 0..2D (D up to 4) with sum 2D."""
+    for D in (2, 3, 4):
+        for n0 in range(2 * D + 1):
+            for n1 in range(2 * D + 1 - n0):
+                for n2 in range(2 * D + 1 - n0 - n1):
+                    n = [n0, n1, n2, 2 * D - n0 - n1 - n2]
+                    assert ianus.table_potts_counts(beta, n) == oracle.table_potts(beta, n), (D, n)
