@@ -47,7 +47,7 @@ def lib():
         c = ctypes
         L.oracle_create.restype = c.c_void_p
         L.oracle_create.argtypes = [c.c_int, c.c_int, c.c_int, c.c_int, c.POINTER(c.c_int32), c.c_int,
-                                    c.c_int, c.c_int, c.c_uint64, c.c_int, c.c_double, c.c_double]
+                                    c.c_int, c.c_int, c.c_uint64, c.c_int, c.c_double, c.c_double, c.c_int]
         L.oracle_destroy.argtypes = [c.c_void_p]
         L.oracle_sweep.argtypes = [c.c_void_p, c.c_int, c.POINTER(c.c_double), c.c_uint64, c.c_uint32, c.c_int]
         L.oracle_pt_swap.argtypes = [c.c_void_p, c.POINTER(c.c_double)]
@@ -64,6 +64,9 @@ def lib():
         L.oracle_perm_coupling_index.restype = c.c_int
         L.oracle_perm_coupling_index.argtypes = [c.c_uint64, c.c_int, c.c_int, c.c_uint32]
         L.oracle_perm_code.restype = c.c_int
+        L.oracle_wheel.argtypes = [c.c_uint64, c.c_int, c.c_int, c.c_uint32, c.c_int, c.c_void_p, c.c_uint32,
+                                   c.c_void_p]
+        L.oracle_wheel_from.argtypes = [c.c_void_p, c.c_uint32, c.c_void_p]
         L.oracle_perm_code.argtypes = [c.c_int]
         L.oracle_get_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
         L.oracle_set_sites.argtypes = [c.c_void_p, c.c_void_p, c.c_void_p]
@@ -164,9 +167,25 @@ def perm_code(index) -> int:
     return int(lib().oracle_perm_code(index))
 
 
+def wheel(seed, sample, slot, row, colour, n):
+    """(I(-61..-1), R(0..n-1)) of a freshly seeded Parisi-Rapuano wheel."""
+    start = np.zeros(61, dtype=np.uint32)
+    out = np.zeros(n, dtype=np.uint32)
+    lib().oracle_wheel(seed, sample, slot, row, colour, _ptr(start), n, _ptr(out))
+    return start, out
+
+
+def wheel_from(start61, n):
+    s = np.ascontiguousarray(start61, dtype=np.uint32)
+    out = np.zeros(n, dtype=np.uint32)
+    lib().oracle_wheel_from(_ptr(s), n, _ptr(out))
+    return out
+
+
 MODEL_ISING, MODEL_POTTS, MODEL_PERM = 0, 1, 2
 METROPOLIS, HEATBATH = 0, 1
 DIS_EA, DIS_FERRO, DIS_RFIM, DIS_DAFF = 0, 1, 2, 3
+RNG_PHILOX, RNG_WHEEL = 0, 1
 
 
 class Oracle:
@@ -177,11 +196,13 @@ class Oracle:
     full batch.  ``disorder`` is one of DIS_* (``ferro=True`` is DIS_FERRO);
     ``field`` is |h| (random-field model) and ``occupation`` the site
     occupation probability (diluted antiferromagnet).  Field models measure
-    M as [S, K, R, 2] = (sum x s, sum sign(h) x s).
+    M as [S, K, R, 2] = (sum x s, sum sign(h) x s).  ``rng`` selects the
+    Ising update stream: RNG_PHILOX (the plane stream) or RNG_WHEEL (one
+    Parisi-Rapuano wheel per sample, slot, row and colour).
     """
 
     def __init__(self, model=MODEL_ISING, dim=3, L=4, sample_ids=(0,), n_replicas=1, n_temps=1,
-                 seed=1, ferro=False, q=4, disorder=None, field=0.0, occupation=1.0):
+                 seed=1, ferro=False, q=4, disorder=None, field=0.0, occupation=1.0, rng=RNG_PHILOX):
         ids = np.asarray(sample_ids, dtype=np.int32)
         if disorder is None:
             disorder = DIS_FERRO if ferro else DIS_EA
@@ -194,7 +215,7 @@ class Oracle:
         self.sample_ids = ids
         self.mq = q if model != MODEL_ISING else (2 if disorder in (DIS_RFIM, DIS_DAFF) else 1)
         h = lib().oracle_create(model, q, dim, L, ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), len(ids),
-                                n_replicas, n_temps, seed, int(disorder), float(field), float(occupation))
+                                n_replicas, n_temps, seed, int(disorder), float(field), float(occupation), int(rng))
         if not h:
             raise ValueError("invalid oracle configuration")
         self._h = ctypes.c_void_p(h)

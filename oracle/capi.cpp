@@ -14,13 +14,17 @@ using namespace oracle;
 extern "C" {
 
 void* oracle_create(int model, int q, int dim, int L, const int32_t* sample_ids, int n_ids, int R,
-                    int K, uint64_t seed, int disorder, double field, double occupation) {
+                    int K, uint64_t seed, int disorder, double field, double occupation, int rng) {
   if (dim < 1 || dim > 4 || L < 2 || (L & 1) || n_ids < 1 || R < 1 || K < 1 || q < 2) return nullptr;
   if (model < 0 || model > 2 || (model == MODEL_PERM && q != 4)) return nullptr;
   if (disorder < 0 || disorder > 3 || !(field >= 0.0) || !(occupation >= 0.0 && occupation <= 1.0)) return nullptr;
   State* st = new State();
   std::vector<int> ids(sample_ids, sample_ids + n_ids);
-  init_state(*st, model, q, dim, L, ids, R, K, seed, disorder, field, occupation);
+  if (rng < 0 || rng > 1 || (rng == RNG_WHEEL && model != MODEL_ISING)) {
+    delete st;
+    return nullptr;
+  }
+  init_state(*st, model, q, dim, L, ids, R, K, seed, disorder, field, occupation, rng);
   return st;
 }
 
@@ -198,5 +202,21 @@ int oracle_perm_coupling_index(uint64_t seed, int sample, int d, uint32_t site) 
   return perm_coupling_index(seed, sample, d, site);
 }
 int oracle_perm_code(int index) { return perm_code(index); }
+
+/* A freshly seeded wheel: its 61 starting values and its first n outputs. */
+void oracle_wheel(uint64_t seed, int sample, int slot, uint32_t row, int colour, uint32_t* start61, uint32_t n,
+                  uint32_t* out) {
+  Wheel w = wheel_seeded(seed, sample, slot, row, colour);
+  if (start61)
+    for (int k = 0; k < 61; ++k) start61[k] = w.hist[k];
+  for (uint32_t k = 0; k < n; ++k) out[k] = w.next();
+}
+
+/* n outputs of Eq. (5) from caller-given starting values I(-61) .. I(-1). */
+void oracle_wheel_from(const uint32_t* start61, uint32_t n, uint32_t* out) {
+  Wheel w;
+  w.hist.assign(start61, start61 + 61);
+  for (uint32_t k = 0; k < n; ++k) out[k] = w.next();
+}
 
 }  // extern "C"

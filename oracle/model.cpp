@@ -46,8 +46,9 @@ int colour(const State& st, uint32_t i) {
 /* ---- set-up: quenched couplings and initial configurations ---- */
 
 void init_state(State& st, int model, int q, int D, int L, const std::vector<int>& sample_ids,
-                int R, int K, uint64_t seed, int disorder, double field, double occupation) {
+                int R, int K, uint64_t seed, int disorder, double field, double occupation, int rng) {
   st.model = model;
+  st.rng = model == MODEL_ISING ? rng : RNG_PHILOX;
   st.disorder = model == 0 ? disorder : (disorder == DIS_FERRO ? DIS_FERRO : DIS_EA);
   st.hmag = field;
   st.q = q;
@@ -92,6 +93,13 @@ void init_state(State& st, int model, int q, int D, int L, const std::vector<int
     for (int a = 0; a < R; ++a)
       for (int k = 0; k < K; ++k) smp.slot_at[a][k] = k;
     smp.accepted.assign(R, std::vector<uint64_t>(K > 1 ? K - 1 : 0, 0));
+    if (st.rng == RNG_WHEEL) {
+      const uint32_t rows = (uint32_t)st.N / (uint32_t)L;
+      smp.wheels.assign(slots, std::vector<Wheel>());
+      for (int sl = 0; sl < slots; ++sl)
+        for (uint32_t row = 0; row < rows; ++row)
+          for (int c = 0; c < 2; ++c) smp.wheels[sl].push_back(wheel_seeded(seed, s, sl, row, c));
+    }
     st.samples.push_back(smp);
   }
   for (auto& smp : st.samples) {
@@ -170,6 +178,10 @@ void sweep_ising(const State& st, Sample& smp, int slot, int algo, double beta, 
   for (int c = 0; c < 2; ++c) {
     for (uint32_t i = 0; i < (uint32_t)st.N; ++i) {
       if (colour(st, i) != c) continue;
+      /* the wheel of the site's row and colour gives one number per site and
+       * sweep, empty sites included, in increasing x */
+      uint32_t r_wheel = 0;
+      if (st.rng == RNG_WHEEL) r_wheel = smp.wheels[slot][(i / (uint32_t)st.L) * 2 + c].next();
       if (!smp.x[i]) continue; /* an empty site carries no spin */
       /* local field of the bonds: phi = sum_j J_ij x_j s_j; v = s_i phi */
       int phi = 0;
@@ -185,7 +197,7 @@ void sweep_ising(const State& st, Sample& smp, int slot, int algo, double beta, 
       if (st.hmag != 0.0) w = (s[i] * smp.hs[i] > 0) ? st.hmag : -st.hmag;
       const double x = (double)v + w;
       const double dE = 2.0 * x; /* energy change if s_i flips */
-      const uint32_t r = ising_random(st.seed, smp.s, slot, i, t);
+      const uint32_t r = st.rng == RNG_WHEEL ? r_wheel : ising_random(st.seed, smp.s, slot, i, t);
       bool flip;
       if (algo == 0) {
         /* Metropolis: dE <= 0 is always taken; else with prob exp(-beta dE) */

@@ -20,6 +20,7 @@
  *   32-bit LUT compare    Sec. 3.2, Sec. 3.3
  *   parallel tempering    Sec. 2.2 names it; the rule is the standard one
  *   E, M, Q measurements  Sec. 4.1
+ *   Parisi-Rapuano wheel  Sec. 3.3, Eq. (5) (the alternative random stream)
  */
 #pragma once
 #include <cstdint>
@@ -31,7 +32,21 @@ namespace oracle {
 void philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 
 enum { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6, TAG_H = 7, TAG_X = 8,
-       TAG_PERM = 9 };
+       TAG_PERM = 9, TAG_WHEEL = 10 };
+
+/* Random streams of the Ising-like sweep: the counter-based plane stream, or
+ * one Parisi-Rapuano wheel per (sample, slot, row, colour). */
+enum { RNG_PHILOX = 0, RNG_WHEEL = 1 };
+
+/* Parisi-Rapuano shift register, Eq. (5): I(k) = I(k-24) + I(k-55) mod 2^32,
+ * R(k) = I(k) xor I(k-61).  hist holds I(k-61) .. I(k-1), oldest first. */
+struct Wheel {
+  std::vector<uint32_t> hist;
+  uint32_t next();
+};
+/* The 61 starting values I(-61) .. I(-1) of the wheel of (sample, slot, row,
+ * colour): words of the WHEEL stream; I(-61) is made odd. */
+Wheel wheel_seeded(uint64_t seed, int sample, int slot, uint32_t row, int colour);
 
 /* Models: 0 = Ising-like (Eq. 2), 1 = Potts with J = +-1 weights, 2 = the
  * glassy Potts model of Eq. (3) with permutation couplings. */
@@ -76,12 +91,14 @@ struct Sample {
   std::vector<int64_t> F_run;               /* [slots] incremental field sum          */
   std::vector<std::vector<int>> slot_at;    /* [R][K] temperature slot at temperature k */
   std::vector<std::vector<uint64_t>> accepted; /* [R][K-1] */
+  std::vector<std::vector<Wheel>> wheels;   /* [slots][row * 2 + colour], RNG_WHEEL only */
 };
 
 struct State {
   int model;        /* MODEL_* */
   int disorder;     /* DIS_* for the Ising-like model */
   double hmag;      /* |h| */
+  int rng;          /* RNG_* (Ising-like model) */
   int q;            /* Potts states (4 in the library; any >= 2 here) */
   int D, L, N, R, K;
   uint64_t seed;
@@ -99,7 +116,7 @@ uint32_t neighbour(const State& st, uint32_t i, int d, int dir); /* dir +1 / -1 
 int colour(const State& st, uint32_t i);
 
 void init_state(State& st, int model, int q, int D, int L, const std::vector<int>& sample_ids,
-                int R, int K, uint64_t seed, int disorder, double field, double occupation);
+                int R, int K, uint64_t seed, int disorder, double field, double occupation, int rng = RNG_PHILOX);
 int64_t energy(const State& st, const Sample& smp, int slot);
 int64_t magnetisation(const State& st, const Sample& smp, int slot);
 int64_t field_sum(const State& st, const Sample& smp, int slot);

@@ -148,6 +148,27 @@ int perm_index_of_code(int code) {
   return -1;
 }
 
+uint32_t Wheel::next() {
+  const size_t n = hist.size(); /* 61 */
+  const uint32_t Ik = hist[n - 24] + hist[n - 55];
+  const uint32_t R = Ik ^ hist[n - 61];
+  hist.erase(hist.begin());
+  hist.push_back(Ik);
+  return R;
+}
+
+Wheel wheel_seeded(uint64_t seed, int sample, int slot, uint32_t row, int colour) {
+  Wheel w;
+  for (uint32_t n = 0; n < 61; ++n) {
+    uint32_t x[4];
+    const uint32_t c2 = ((uint32_t)TAG_WHEEL << 28) | ((n >> 2) << 24) | ((uint32_t)slot << 12) | (uint32_t)colour;
+    call(seed, row, (uint32_t)sample, c2, 0u, x);
+    w.hist.push_back(x[n & 3]);
+  }
+  w.hist[0] |= 1u; /* an odd value gives the additive generator its full period */
+  return w;
+}
+
 /* 32-bit random of the dilution stream, assembled from its bit-planes. */
 uint32_t occupation_random(uint64_t seed, int sample, uint32_t site) {
   const uint32_t g = (uint32_t)sample >> 6;
