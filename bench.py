@@ -528,6 +528,33 @@ def run_other_configs(args):
             "value": 2 * 64 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2, "kind": "oracle",
             "sample": "samples 0, 255, 2 sweeps"}
     del da
+    # the bench workload on the plain layout driven by Parisi-Rapuano wheels (Eq. 5)
+    wh = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 7, layout="i8", rng="wheel", stream=stream)
+    wh.sweep(ianus.HEATBATH, 1.0 / T, 2, 0)
+    reps = 3
+    sec = timed(lambda: wh.sweep(ianus.HEATBATH, 1.0 / T, 10, 10), reps)
+    upd = S * R * L ** 3 * 10 * reps
+    rate = upd / (sec * 1e9)
+    # unique bytes per update: spin read + write (2), 3 couplings, and per
+    # row-colour wheel the 64-word ring read + L/2 words written for L/2 updates
+    bytes_upd = 2.0 + 3.0 + (64 + L / 2) * 4 / (L / 2)
+    hbm = MEASURED.get("hbm_gbs")
+    out["wheel_L64_256x2_hb"] = {
+        "updates_per_ns": rate, "ms_per_10_sweeps": sec * 1e3 / reps,
+        "mode": "plain int8, one Parisi-Rapuano wheel per (configuration, row, colour), heat bath T=1.0",
+        "roofline": {"bound": "hbm", "bytes_per_update": bytes_upd, "achieved": rate * bytes_upd, "peak": hbm,
+                     "unit": "GB/s", "frac": (rate * bytes_upd / hbm) if hbm else None},
+    }
+    if not args.no_cpu_baseline:
+        import oracle
+
+        o = oracle.Oracle(dim=3, L=L, sample_ids=[0, 255], n_replicas=R, seed=SEED + 7, rng=oracle.RNG_WHEEL)
+        t0 = time.perf_counter()
+        o.sweep(oracle.HEATBATH, 1.0 / T, 1, nthreads=2)
+        dt = time.perf_counter() - t0
+        out["wheel_L64_256x2_hb"]["cpu_baseline"] = {"value": 2 * R * L ** 3 / (dt * 1e9), "unit": UNIT, "cores": 2,
+                                                     "kind": "oracle", "sample": "samples 0, 255 x 2 replicas, 1 sweep"}
+    del wh
     # glassy Potts model with permutation couplings (Eq. 3), 3D and 4D, heat bath
     for dim, Lp, bp, key in ((3, 32, 2.4, "potts_perm_3d_L32_256x2"), (4, 16, 1.405, "potts_perm_4d_L16_256x2")):
         pp = ianus.Lattice(model="potts_perm", dim=dim, L=Lp, n_samples=256, n_replicas=2, seed=SEED + 6,

@@ -59,7 +59,7 @@
  *   of its coordinates only, so results do not depend on memory layout,
  *   kernel choice, launch shape or on how sweeps are split across calls.
  *   Tags: SPIN = 1, J = 2, INIT = 3, POTTS = 4, PINIT = 5, PT = 6, H = 7,
- *   X = 8, PERM = 9.
+ *   X = 8, PERM = 9, WHEEL = 10.
  *   Sample s lives in group g = s >> 6 at lane l = s & 63.
  *
  *   Ising update random r(s, sigma, i, t), t = absolute sweep index:
@@ -83,6 +83,16 @@
  *     r_x < floor(ldexp(occupation, 32)), r_x assembled from bit-planes as the
  *     update random, with c1 = 0 and c2 = (X << 28) | (m << 24) | g,
  *     c3 = 0.  (Other disorder kinds: x_i = 1.)
+ *   Parisi-Rapuano wheels (IANUS_RNG_WHEEL, Sec. 3.3, Eq. (5)): the Ising
+ *     update random of a site is drawn instead from the wheel of its
+ *     (sample s, slot sigma, row, colour c), row = i / L:
+ *       I(k) = I(k-24) + I(k-55) mod 2^32,  R(k) = I(k) xor I(k-61),
+ *     with starting values I(-61 + n), n = 0..60, = x_{n & 3} of
+ *     Philox(key, c0 = row, c1 = s, c2 = (WHEEL << 28) | ((n >> 2) << 24) |
+ *     (sigma << 12) | c, c3 = 0), and I(-61) made odd (full period).  In sweep
+ *     t the colour-c site of the row with x = 2 j + ((c + row parity) mod 2)
+ *     takes r = R(t L/2 + j), empty sites included; the decision and tables
+ *     are those of the plane stream.
  *   Initial Ising spin of (s, sigma, i): s = -1 iff bit l of (x0 | x1 << 32)
  *     of Philox(key, c0 = i, c1 = 0, c2 = (INIT << 28) | (sigma << 12) | g,
  *     c3 = 0) is set.
@@ -166,7 +176,7 @@
 extern "C" {
 #endif
 
-#define IANUS_ABI_VERSION 2u
+#define IANUS_ABI_VERSION 3u
 
 typedef struct ianus_lattice ianus_lattice; /* opaque, library-owned */
 
@@ -200,6 +210,12 @@ typedef enum {
                                 h_i = |h|, x_i = 1 with probability occupation */
 } ianus_disorder;
 
+/* Random stream of the Ising-like update (see the stream definitions). */
+typedef enum {
+  IANUS_RNG_PHILOX = 0,  /* the counter-based plane stream (every layout)       */
+  IANUS_RNG_WHEEL = 1    /* Parisi-Rapuano wheels, Eq. (5) (layout I8 only)     */
+} ianus_rng;
+
 typedef struct {
   uint32_t abi_version;     /* must equal IANUS_ABI_VERSION                 */
   int32_t model;            /* ianus_model                                  */
@@ -217,6 +233,8 @@ typedef struct {
   void* cuda_stream;        /* cudaStream_t; NULL = the legacy default stream */
   double field;             /* |h| >= 0 (RFIM, DAFF); must be 0 otherwise      */
   double occupation;        /* DAFF site occupation probability in [0, 1]      */
+  int32_t rng;              /* ianus_rng; WHEEL needs the Ising-like model and
+                               layout I8 (AUTO picks I8), else EUNSUPPORTED    */
 } ianus_config;
 
 /* Device bytes a lattice with this configuration uses (state, couplings,

@@ -19,18 +19,20 @@ import numpy as np
 
 from . import build as _build
 
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 EA_PM_J, POTTS4_J, POTTS4_PERM = 0, 1, 2
 METROPOLIS, HEATBATH = 0, 1
 LAYOUT_AUTO, LAYOUT_I8, LAYOUT_BITS64, LAYOUT_U8X4 = 0, 1, 2, 3
 DISORDER_PM_J, DISORDER_FERRO, DISORDER_RFIM, DISORDER_DAFF = 0, 1, 2, 3
+RNG_PHILOX, RNG_WHEEL = 0, 1
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED, ESTATE = range(7)
 
 _MODELS = {"ea": EA_PM_J, "potts": POTTS4_J, "potts_perm": POTTS4_PERM}
 _ALGOS = {"metropolis": METROPOLIS, "heatbath": HEATBATH}
 _LAYOUTS = {"auto": LAYOUT_AUTO, "i8": LAYOUT_I8, "bits64": LAYOUT_BITS64, "u8x4": LAYOUT_U8X4}
+_RNGS = {"philox": RNG_PHILOX, "wheel": RNG_WHEEL}
 _DISORDERS = {"pm_j": DISORDER_PM_J, "ferro": DISORDER_FERRO, "rfim": DISORDER_RFIM, "daff": DISORDER_DAFF}
 
 EXPORTS = [
@@ -62,6 +64,7 @@ class IanusConfig(C.Structure):
         ("cuda_stream", C.c_void_p),
         ("field", C.c_double),
         ("occupation", C.c_double),
+        ("rng", C.c_int32),
     ]
 
 
@@ -190,7 +193,7 @@ class Lattice:
 
     def __init__(self, model="ea", dim=3, L=16, n_samples=1, n_replicas=1, n_temps=1, seed=0,
                  layout="auto", ferro=False, series_capacity=0, stream=None, device=None, disorder=None,
-                 field=0.0, occupation=1.0):
+                 field=0.0, occupation=1.0, rng="philox"):
         import torch
 
         if not torch.cuda.is_available():
@@ -218,11 +221,16 @@ class Lattice:
         cfg.disorder = self.disorder
         cfg.field = self.field
         cfg.occupation = self.occupation
+        cfg.rng = _RNGS[rng] if isinstance(rng, str) else int(rng)
         cfg.series_capacity = series_capacity
         cfg.seed = seed & 0xFFFFFFFFFFFFFFFF
         nbytes = self._lib.ianus_required_bytes(C.byref(cfg))
         if nbytes == 0:
-            raise IanusError(EINVAL, "ianus_required_bytes")
+            # invalid configuration: ianus_lattice_create validates it the
+            # same way (before any allocation) and names the reason
+            h = C.c_void_p()
+            st = self._lib.ianus_lattice_create(C.byref(cfg), C.byref(h))
+            raise IanusError(st if st != OK else EINVAL, "ianus_lattice_create")
         with torch.cuda.device(dev):
             self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=dev)
         cfg.device_buffer = self.buffer.data_ptr()

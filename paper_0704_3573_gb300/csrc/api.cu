@@ -23,6 +23,8 @@ struct Sizes {
   int model, D, L, S, R, K, slots, layout, G, Q4, mq;
   uint32_t N, cap, pt_cap;
   bool field;
+  uint32_t rows;
+  size_t off_wheels, wheel_bytes;
   size_t off_spins, off_J, off_thr, off_tp, off_fthr, off_ftp, off_sites, off_ptab, off_pttab, off_ptsign, off_slot,
       off_temp, off_acc_pt, off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
   size_t spins_bytes, J_bytes, sites_bytes;
@@ -48,17 +50,21 @@ int plan(const ianus_config* c, Sizes& z) {
   if (!field && c->field != 0.0) return IANUS_EINVAL;
   if (c->disorder == IANUS_DISORDER_DAFF && !(c->occupation >= 0.0 && c->occupation <= 1.0)) return IANUS_EINVAL;
   if (field && c->model != IANUS_EA_PM_J) return IANUS_EINVAL;
+  if (c->rng != IANUS_RNG_PHILOX && c->rng != IANUS_RNG_WHEEL) return IANUS_EINVAL;
   uint64_t N = 1;
   for (int d = 0; d < c->dim; ++d) N *= (uint64_t)c->L;
   if (N >= (1ull << 31)) return IANUS_EINVAL;
   int layout = c->layout;
   const bool potts = c->model != IANUS_EA_PM_J;
   if (layout == IANUS_LAYOUT_AUTO)
-    layout = potts ? IANUS_LAYOUT_U8X4 : c->disorder == IANUS_DISORDER_DAFF ? IANUS_LAYOUT_I8 : IANUS_LAYOUT_BITS64;
+    layout = potts ? IANUS_LAYOUT_U8X4
+             : (c->disorder == IANUS_DISORDER_DAFF || c->rng == IANUS_RNG_WHEEL) ? IANUS_LAYOUT_I8
+                                                                             : IANUS_LAYOUT_BITS64;
   if (layout < IANUS_LAYOUT_I8 || layout > IANUS_LAYOUT_U8X4) return IANUS_EINVAL;
   if (!potts && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (potts && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (c->disorder == IANUS_DISORDER_DAFF && layout == IANUS_LAYOUT_BITS64) return IANUS_EUNSUPPORTED;
+  if (c->rng == IANUS_RNG_WHEEL && (potts || layout != IANUS_LAYOUT_I8)) return IANUS_EUNSUPPORTED;
   if (layout == IANUS_LAYOUT_BITS64 &&  // the sweep stages one block's threshold planes in shared memory
       (size_t)c->n_replicas * kPlanes * (field ? kFieldPlaneClasses : kMaxClasses) * 8 > kMaxSmemPerBlock)
     return IANUS_EUNSUPPORTED;
@@ -88,6 +94,8 @@ int plan(const ianus_config* c, Sizes& z) {
     z.J_bytes = (size_t)z.Q4 * z.D * N * 4;
   }
   z.sites_bytes = !field ? 0 : layout == IANUS_LAYOUT_I8 ? (size_t)2 * z.S * N : (size_t)z.G * N * 8;
+  z.rows = (uint32_t)(N / (uint64_t)c->L);
+  z.wheel_bytes = c->rng == IANUS_RNG_WHEEL ? (size_t)z.slots * z.S * 2 * 64 * z.rows * 4 : 0;
   const size_t SKR = (size_t)z.S * z.K * z.R;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -102,6 +110,7 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 : 0);
   z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
   z.off_sites = take(z.sites_bytes);
+  z.off_wheels = take(z.wheel_bytes);
   z.off_ptab = take(layout != IANUS_LAYOUT_U8X4 ? 0
                     : c->model == IANUS_POTTS4_PERM ? (size_t)z.K * perm_table_entries(z.D) * 16
                                                     : (size_t)z.K * 65536 * 16);
@@ -396,7 +405,7 @@ int sweeps_graphed(Lattice* lat, int inv, uint64_t n) {
 struct StateHeader {
   uint64_t magic;
   uint32_t version, model, dim, L, S, R, K, layout, disorder, pad;
-  uint64_t seed, sweeps, steps, spins_bytes, J_bytes, sites_bytes;
+  uint64_t seed, sweeps, steps, spins_bytes, J_bytes, sites_bytes, wheel_bytes;
   double field, occupation;
 };
 
@@ -434,6 +443,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->disorder = cfg->disorder;
   lat->field = z.field;
   lat->hmag = cfg->field;
+  lat->rng = cfg->rng;
+  lat->rows = z.rows;
   lat->cap = z.cap;
   lat->pt_cap = z.pt_cap;
   lat->pt_len = z.pt_cap;
@@ -482,6 +493,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->hs = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) : nullptr;
   lat->occ = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) + (size_t)z.S * z.N : nullptr;
   lat->hbits = z.field && z.layout == IANUS_LAYOUT_BITS64 ? (uint64_t*)(b + z.off_sites) : nullptr;
+  lat->wheels = z.wheel_bytes ? (uint32_t*)(b + z.off_wheels) : nullptr;
   lat->ptab = (uint4*)(b + z.off_ptab);
   lat->pttab = (uint64_t*)(b + z.off_pttab);
   lat->pt_sign = (int8_t*)(b + z.off_ptsign);
@@ -529,6 +541,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
     e = launch_init_potts(*lat, jmode);
   if (e == cudaSuccess && lat->field)
     e = lat->layout == IANUS_LAYOUT_I8 ? launch_init_sites_i8(*lat, cfg->occupation) : launch_init_sites_bits(*lat);
+  if (e == cudaSuccess && lat->wheels) e = launch_init_wheels(*lat);
   if (e != cudaSuccess || cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
   *out = reinterpret_cast<ianus_lattice*>(lat);
   return IANUS_OK;
@@ -801,7 +814,8 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   plan(&lat->cfg, z);
   const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
   const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
-  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes;
+  const size_t need =
+      sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes + z.wheel_bytes;
   if (n) *n = need;
   if (!host_buf) return IANUS_OK;
   if (cap < need) return IANUS_EINVAL;
@@ -822,6 +836,7 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   hd.spins_bytes = z.spins_bytes;
   hd.J_bytes = z.J_bytes;
   hd.sites_bytes = z.sites_bytes;
+  hd.wheel_bytes = z.wheel_bytes;
   hd.field = lat->cfg.field;
   hd.occupation = lat->cfg.occupation;
   uint8_t* o = (uint8_t*)host_buf;
@@ -838,6 +853,9 @@ ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_
   CK(cudaMemcpyAsync(o, lat->spins, z.spins_bytes, cudaMemcpyDeviceToHost, lat->stream));
   o += z.spins_bytes;
   if (z.sites_bytes) CK(cudaMemcpyAsync(o, lat->base + z.off_sites, z.sites_bytes, cudaMemcpyDeviceToHost, lat->stream));
+  o += z.sites_bytes;
+  if (z.wheel_bytes)
+    CK(cudaMemcpyAsync(o, lat->base + z.off_wheels, z.wheel_bytes, cudaMemcpyDeviceToHost, lat->stream));
   CK(cudaStreamSynchronize(lat->stream));
   return IANUS_OK;
 }
@@ -849,7 +867,8 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   plan(&lat->cfg, z);
   const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
   const size_t accb = (size_t)lat->S * lat->R * std::max(lat->K - 1, 1) * 8;
-  const size_t need = sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes;
+  const size_t need =
+      sizeof(StateHeader) + 2 * perm + accb + z.J_bytes + z.spins_bytes + z.sites_bytes + z.wheel_bytes;
   if (n < need) return IANUS_ESTATE;
   StateHeader hd;
   std::memcpy(&hd, host_buf, sizeof hd);
@@ -858,6 +877,7 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
       hd.R != (uint32_t)lat->R || hd.K != (uint32_t)lat->K || hd.layout != (uint32_t)lat->layout ||
       hd.seed != lat->cfg.seed || hd.spins_bytes != z.spins_bytes || hd.J_bytes != z.J_bytes ||
       hd.disorder != (uint32_t)lat->cfg.disorder || hd.sites_bytes != z.sites_bytes ||
+      hd.wheel_bytes != z.wheel_bytes ||
       std::memcmp(&hd.field, &lat->cfg.field, sizeof(double)) != 0)
     return IANUS_ESTATE;
   const uint8_t* in = (const uint8_t*)host_buf + sizeof hd;
@@ -873,6 +893,9 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   CK(cudaMemcpyAsync(lat->spins, in, z.spins_bytes, cudaMemcpyHostToDevice, lat->stream));
   in += z.spins_bytes;
   if (z.sites_bytes) CK(cudaMemcpyAsync(lat->base + z.off_sites, in, z.sites_bytes, cudaMemcpyHostToDevice, lat->stream));
+  in += z.sites_bytes;
+  if (z.wheel_bytes)
+    CK(cudaMemcpyAsync(lat->base + z.off_wheels, in, z.wheel_bytes, cudaMemcpyHostToDevice, lat->stream));
   CK(cudaMemsetAsync(lat->err, 0, 4, lat->stream));
   CK(cudaStreamSynchronize(lat->stream));
   lat->sweeps = hd.sweeps;

@@ -145,6 +145,117 @@ __global__ void __launch_bounds__(256) k_sweep_field_i8(const FieldI8Params fp) 
   }
 }
 
+// ---- Parisi-Rapuano wheels (Sec. 3.3, Eq. 5) ----
+//
+// One thread per (configuration, row) walks the colour-c sites of its row in
+// increasing x, drawing R(k) = I(k) ^ I(k-61), I(k) = I(k-24) + I(k-55), from
+// the row's wheel; k = t L/2 + j for the j-th site.  The ring of 64 words
+// (I(k) at index k mod 64) sits in shared memory for the launch, ring index
+// major so that the threads of a warp, which share k, hit 32 banks.
+constexpr int kWheelBlock = 128;
+
+struct WheelParams {
+  I8Params b;
+  uint32_t* wheels;      // [slots * S][2][64][rows]
+  uint32_t rows;
+  const int8_t* hs;      // field models: [S][N], else null
+  const int8_t* occ;
+  const uint64_t* fthr;  // field models: [K][kFieldClasses]
+};
+
+template <int D, bool FIELD>
+__global__ void __launch_bounds__(kWheelBlock) k_sweep_wheel_i8(const WheelParams wp) {
+  __shared__ uint32_t ring[64 * kWheelBlock];
+  const I8Params& p = wp.b;
+  const uint32_t L = (uint32_t)p.L, h = L / 2u, rows = wp.rows;
+  const uint64_t total = (uint64_t)p.slots * p.S * rows;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  const uint32_t k0 = tk.lo * h;  // t L/2 mod 2^32; only k mod 64 is used
+  const uint32_t tid = threadIdx.x;
+  for (uint64_t base = (uint64_t)blockIdx.x * kWheelBlock; base < total; base += (uint64_t)gridDim.x * kWheelBlock) {
+    const uint64_t idx = base + tid;
+    const bool active = idx < total;
+    const uint32_t lat = active ? (uint32_t)(idx / rows) : 0u;
+    const uint32_t row = active ? (uint32_t)(idx - (uint64_t)lat * rows) : 0u;
+    uint32_t* wg = wp.wheels + ((size_t)lat * 2 + (size_t)p.colour) * 64 * rows + row;
+    if (active)
+      for (int m = 0; m < 64; ++m) ring[m * kWheelBlock + tid] = wg[(size_t)m * rows];
+    if (active) {
+      const int sigma = (int)(lat / (uint32_t)p.S);
+      const int s = (int)(lat - (uint32_t)sigma * (uint32_t)p.S);
+      const uint32_t y = row % L, z = row / L;  // D = 2: z = 0
+      const uint32_t x0 = (uint32_t)(p.colour ^ (int)(y + z)) & 1u;
+      int8_t* sp = p.spins + (size_t)lat * p.N;
+      const int8_t* Jp = p.J + (size_t)s * D * p.N;
+      const int8_t* xo = FIELD ? wp.occ + (size_t)s * p.N : nullptr;
+      const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+      const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
+      // rows of the neighbours along y and z
+      const uint32_t yp = (y + 1u == L ? 0u : y + 1u) + L * z, ym = (y == 0u ? L - 1u : y - 1u) + L * z;
+      const uint32_t zp = y + L * (z + 1u == L ? 0u : z + 1u), zm = y + L * (z == 0u ? L - 1u : z - 1u);
+      for (uint32_t j = 0; j < h; ++j) {
+        const uint32_t k = k0 + j;
+        const uint32_t Ik = ring[((k - 24u) & 63u) * kWheelBlock + tid] + ring[((k - 55u) & 63u) * kWheelBlock + tid];
+        const uint32_t r = Ik ^ ring[((k - 61u) & 63u) * kWheelBlock + tid];
+        ring[(k & 63u) * kWheelBlock + tid] = Ik;
+        const uint32_t x = 2u * j + x0;
+        const uint32_t i = x + L * row;
+        if (FIELD && !xo[i]) continue;
+        const uint32_t xp = (x + 1u == L ? 0u : x + 1u) + L * row;
+        const uint32_t xm = (x == 0u ? L - 1u : x - 1u) + L * row;
+        const uint32_t iyp = x + L * yp, iym = x + L * ym;
+        const int si = sp[i];
+        uint64_t T;
+        if (FIELD) {
+          int phi = Jp[i] * xo[xp] * sp[xp] + Jp[xm] * xo[xm] * sp[xm] + Jp[p.N + i] * xo[iyp] * sp[iyp] +
+                    Jp[p.N + iym] * xo[iym] * sp[iym];
+          if (D == 3) {
+            const uint32_t izp = x + L * zp, izm = x + L * zm;
+            phi += Jp[2u * p.N + i] * xo[izp] * sp[izp] + Jp[2u * p.N + izm] * xo[izm] * sp[izm];
+          }
+          const int v = si * phi;
+          const int f = si * wp.hs[(size_t)s * p.N + i] > 0;
+          T = wp.fthr[(size_t)kt * kFieldClasses + (v + 2 * D) * 2 + f];
+        } else {
+          int u = (Jp[i] * si * sp[xp] < 0) + (Jp[xm] * si * sp[xm] < 0) + (Jp[p.N + i] * si * sp[iyp] < 0) +
+                  (Jp[p.N + iym] * si * sp[iym] < 0);
+          if (D == 3) {
+            const uint32_t izp = x + L * zp, izm = x + L * zm;
+            u += (Jp[2u * p.N + i] * si * sp[izp] < 0) + (Jp[2u * p.N + izm] * si * sp[izm] < 0);
+          }
+          T = p.thr[(size_t)kt * kMaxClasses + u];
+        }
+        const bool less = (uint64_t)r < T;
+        if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
+      }
+      for (int m = 0; m < 64; ++m) wg[(size_t)m * rows] = ring[m * kWheelBlock + tid];
+    }
+  }
+}
+
+// Starting values: I(-61 + n) = word n of the WHEEL stream of the wheel, at
+// ring index (n + 3) mod 64; I(-61) made odd.
+__global__ void k_init_wheels(uint32_t* wheels, int S, int slots, uint32_t rows, PhiloxKeys keys) {
+  const uint64_t total = (uint64_t)slots * S * 2u * rows;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t row = (uint32_t)(idx % rows);
+    const uint64_t rest = idx / rows;
+    const uint32_t c = (uint32_t)(rest & 1u), lat = (uint32_t)(rest >> 1);
+    const uint32_t sigma = lat / (uint32_t)S, s = lat - sigma * (uint32_t)S;
+    uint32_t* w = wheels + ((size_t)lat * 2 + c) * 64 * rows + row;
+    for (uint32_t blk = 0; blk < 16u; ++blk) {
+      const uint4 x = philox10(row, s, (TAG_WHEEL << 28) | (blk << 24) | (sigma << 12) | c, 0u, keys);
+      const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+      for (uint32_t e = 0; e < 4u; ++e) {
+        const uint32_t n = 4u * blk + e;
+        if (n < 61u) w[(size_t)((n + 3u) & 63u) * rows] = n == 0u ? (xs[e] | 1u) : xs[e];
+      }
+    }
+    for (uint32_t m = 0; m < 3u; ++m) w[(size_t)m * rows] = 0u;
+  }
+}
+
 // ---- resident mode: a whole configuration in shared memory ----
 //
 // One block per configuration (n_temps == 1) keeps the spins and the
@@ -501,6 +612,17 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
   p.t_hi = (uint32_t)(t >> 32);
   p.keys = lat.keys;
   p.t_dev = lat.capturing ? lat.t_dev : nullptr;
+  if (lat.rng == IANUS_RNG_WHEEL) {
+    const WheelParams wp{p, lat.wheels, lat.rows, lat.hs, lat.occ, lat.fthr};
+    const unsigned wgrid = grid_for((uint64_t)lat.slots * lat.S * lat.rows, kWheelBlock, 152u * 12u);
+    if (lat.field)
+      lat.D == 3 ? k_sweep_wheel_i8<3, true><<<wgrid, kWheelBlock, 0, lat.stream>>>(wp)
+                 : k_sweep_wheel_i8<2, true><<<wgrid, kWheelBlock, 0, lat.stream>>>(wp);
+    else
+      lat.D == 3 ? k_sweep_wheel_i8<3, false><<<wgrid, kWheelBlock, 0, lat.stream>>>(wp)
+                 : k_sweep_wheel_i8<2, false><<<wgrid, kWheelBlock, 0, lat.stream>>>(wp);
+    return cudaGetLastError();
+  }
   const uint64_t total = (uint64_t)lat.slots * lat.S * p.half;
   const unsigned grid = grid_for(total, 256, 152u * 8u);
   if (lat.field) {
@@ -541,7 +663,7 @@ cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
 }
 
 bool resident_i8_fits(const Lattice& lat) {
-  return lat.layout == IANUS_LAYOUT_I8 && !lat.field && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
+  return lat.layout == IANUS_LAYOUT_I8 && !lat.field && lat.rng == IANUS_RNG_PHILOX && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
 }
 
 cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every) {
@@ -596,6 +718,12 @@ cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out) {
 
 cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in) {
   return cudaMemcpyAsync(lat.J, dev_in, (size_t)lat.S * lat.D * lat.N, cudaMemcpyDeviceToDevice, lat.stream);
+}
+
+cudaError_t launch_init_wheels(Lattice& lat) {
+  k_init_wheels<<<grid_for((uint64_t)lat.slots * lat.S * 2u * lat.rows), 256, 0, lat.stream>>>(
+      lat.wheels, lat.S, lat.slots, lat.rows, lat.keys);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_init_sites_i8(Lattice& lat, double occupation) {

@@ -74,6 +74,12 @@ struct Lattice {
   int8_t* hs;           // I8 field: sign of h_i, int8 [S][N]
   int8_t* occ;          // I8 field: x_i in {0, 1}, int8 [S][N]
   uint64_t* hbits;      // BITS64 field: lane bit set where h_i < 0, u64 [G][N]
+  // Parisi-Rapuano wheels (IANUS_RNG_WHEEL, I8 only): ring of 64 words per
+  // (slot, sample, colour, row), I(k) at ring index k mod 64;
+  // u32 [slots * S][2][64][rows], rows = N / L
+  int rng;
+  uint32_t* wheels;
+  uint32_t rows;
 
   int mq;               // magnetisation entries per configuration (1 Ising, 4 Potts, 2 field models)
   uint32_t cap;         // series capacity
@@ -136,6 +142,7 @@ cudaError_t launch_init_i8(Lattice& lat, int jmode);
 cudaError_t launch_init_sites_i8(Lattice& lat, double occupation);  // hs, occ from the H and X streams
 cudaError_t launch_get_sites_i8(Lattice& lat, int8_t* dev_hs, int8_t* dev_occ);  // [S][N] each
 cudaError_t launch_set_sites_i8(Lattice& lat, const int8_t* dev_hs, const int8_t* dev_occ);
+cudaError_t launch_init_wheels(Lattice& lat);  // starting values of every wheel
 cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv);
 cudaError_t launch_measure_i8(Lattice& lat, int want_q);
 // Resident mode (one block per configuration in shared memory, many sweeps

@@ -43,6 +43,7 @@ def _cfg(**kw):
     c.n_samples, c.n_replicas, c.n_temps = kw.get("S", 1), kw.get("R", 1), kw.get("K", 1)
     c.layout, c.disorder, c.seed = kw.get("layout", 0), kw.get("disorder", 0), 1
     c.field, c.occupation = kw.get("field", 0.0), kw.get("occupation", 1.0)
+    c.rng = kw.get("rng", 0)
     return c
 
 
@@ -57,6 +58,15 @@ def test_required_bytes_validation():
     assert rb(model=2, dim=4, L=4) > 0
     assert rb(model=2, dim=4, L=4, layout=2) == 0
     assert rb(model=3) == 0
+    # Parisi-Rapuano wheels: Ising-like model, plain layout (AUTO picks it)
+    W = ianus.RNG_WHEEL
+    assert rb(rng=W, layout=1) > rb(layout=1)
+    assert rb(rng=W) == rb(rng=W, layout=1)
+    assert rb(rng=W, layout=2) == 0
+    assert rb(model=1, rng=W) == 0
+    assert rb(rng=2) == 0
+    # one ring of 64 words per (slot, sample, colour, row)
+    assert rb(rng=W, layout=1, L=16, S=3, R=2) - rb(layout=1, L=16, S=3, R=2) >= 6 * 2 * 64 * 256 * 4
     assert rb(S=0) == 0
     assert rb(R=64, K=64) == 0               # slot field limit 4096
     assert rb(model=1, layout=1) == 0        # Potts has no I8 layout
