@@ -626,10 +626,24 @@ def run_serving(args):
     server = serve.Server(mem_budget=16 << 30, max_active=64, n_streams=16, chunk_sweeps=50)
     calib = jobs[: max(10, len(jobs) // 5)]
     rate = serve.calibrated_rate(server, calib, load=0.8)
-    _, st = server.run(serve.poisson_arrivals(jobs, rate))
+    arrivals = serve.poisson_arrivals(jobs, rate)
+    _, st = server.run(arrivals)
     st["arrival_rate_per_s"] = rate
     st["sweep_scale"] = args.serve_scale
     st["mix"] = "3D L in {8..80} / 2D L in {64..1024}, 1-64 samples, T~U[0.5,2], sweeps log-U[1e3,1e5] x scale"
+    # lane fusion: jobs of equal (D, L) share the 64-bit lanes of pool lattices;
+    # the same arrivals, then both servers saturated on the calibration jobs
+    fused = serve.FusedServer(mem_budget=16 << 30, groups_per_pool=4, n_streams=16, chunk_sweeps=50)
+    _, fst = fused.run(arrivals)
+    _, sat_plain = server.run(calib, realtime=False)
+    _, sat_fused = fused.run(calib, realtime=False)
+    st["fused"] = {
+        "p50_latency_s": fst["p50_latency_s"], "p99_latency_s": fst["p99_latency_s"],
+        "makespan_s": fst["makespan_s"], "updates_per_ns": fst["updates_per_ns"], "pools": fst["pools"],
+        "saturated_updates_per_ns": sat_fused["updates_per_ns"],
+        "saturated_updates_per_ns_unfused": sat_plain["updates_per_ns"],
+        "what": "same Poisson arrivals; saturated = the calibration jobs all at t=0",
+    }
     return st
 
 

@@ -330,6 +330,40 @@ ianus_status ianus_get_sites_i8(ianus_lattice* lat, int8_t* hsign, int8_t* occup
  * the global-flip and gauge tests. */
 ianus_status ianus_set_sites_i8(ianus_lattice* lat, const int8_t* hsign, const int8_t* occupied);
 
+/* ---- Fused serving (several jobs in the lanes of one lattice) ----
+ * A pool is a bit-sliced EA lattice with n_replicas = n_temps = 1; each of
+ * its n_samples / 64 groups holds up to 64 lanes.  A segment is up to 64
+ * samples of a job, 64 job_group + b for b = 0..n-1, in lanes lane0 + b of one
+ * group; it runs at the job's algorithm and beta.  (A job of more than 64
+ * samples takes one segment per 64.)  Its lanes get the couplings and initial
+ * spins that the job's own lattice (its seed, one replica, one temperature)
+ * gives those samples, and each sweep draws their random planes from that
+ * lattice's stream (key = the job's seed, group job_group, slot 0, sweep =
+ * the segment's own sweep count).  So a job's trajectory is that
+ * of its own lattice, bit for bit, whatever else the pool holds.  Once a
+ * pool has a segment, ianus_sweep and ianus_pt_swap return EINVAL and
+ * ianus_get_state EUNSUPPORTED on it; ianus_measure reports every lane
+ * (sample index 64 group + lane). */
+
+/* Loads samples 64 job_group .. 64 job_group + n - 1 of a job into lanes
+ * [lane0, lane0 + n) of group `group`: couplings and spins from `seed`,
+ * per-lane thresholds of (algo, beta), nsweeps sweeps to run (the lanes
+ * freeze after them).  Errors: EINVAL (bad group, lanes, job_group (< 4096)
+ * or arguments, lanes already taken, 64 segments in the group),
+ * EUNSUPPORTED (not a pool-capable lattice), ECUDA.  Synchronous. */
+ianus_status ianus_segment_load(ianus_lattice* lat, int32_t group, int32_t lane0, int32_t n, uint64_t seed,
+                                int32_t job_group, int32_t algo, double beta, uint64_t nsweeps);
+/* Frees the job whose lanes start at lane0 of `group` (its lanes freeze
+ * until reused).  EINVAL if there is none.  Synchronous. */
+ianus_status ianus_segment_release(ianus_lattice* lat, int32_t group, int32_t lane0);
+/* Sweeps done and requested of the job at (group, lane0).  Host only. */
+ianus_status ianus_segment_state(ianus_lattice* lat, int32_t group, int32_t lane0, uint64_t* sweeps_done,
+                                 uint64_t* sweeps_requested);
+/* Runs nsweeps sweeps of every live job of the pool (a job whose count has
+ * reached its request stays frozen), as one launch per colour plus a counter
+ * advance per sweep, replayed from CUDA graphs.  Asynchronous. */
+ianus_status ianus_sweep_segments(ianus_lattice* lat, uint64_t nsweeps);
+
 /* Parallel-tempering state: slot_at int32 [n_samples][n_replicas][n_temps]
  * (the temperature slot tslot holding temperature k), accepted uint64
  * [n_samples][n_replicas][n_temps-1] (swaps accepted per pair so far),

@@ -42,7 +42,8 @@ EXPORTS = [
     "ianus_synchronize", "ianus_destroy", "ianus_status_string", "ianus_table_ising", "ianus_table_potts",
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
     "ianus_set_graphs", "ianus_set_resident", "ianus_get_sites_i8", "ianus_set_sites_i8", "ianus_table_field",
-    "ianus_table_potts_counts",
+    "ianus_table_potts_counts", "ianus_segment_load", "ianus_segment_release", "ianus_segment_state",
+    "ianus_sweep_segments",
 ]
 
 
@@ -124,6 +125,10 @@ def lib(build_if_missing: bool = True):
         "ianus_set_sites_i8": (i32, [vp, vp, vp]),
         "ianus_table_field": (sz, [i32, i32, C.c_double, C.c_double, vp, sz]),
         "ianus_table_potts_counts": (sz, [C.c_double, vp, vp]),
+        "ianus_segment_load": (i32, [vp, i32, i32, i32, u64, i32, i32, C.c_double, u64]),
+        "ianus_segment_release": (i32, [vp, i32, i32]),
+        "ianus_segment_state": (i32, [vp, i32, i32, C.POINTER(u64), C.POINTER(u64)]),
+        "ianus_sweep_segments": (i32, [vp, u64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -272,6 +277,27 @@ class Lattice:
 
     def pt_swap(self):
         _check(self._lib.ianus_pt_swap(self._h), "ianus_pt_swap")
+
+    # ---- fused serving (pool lattices) ----
+    def segment_load(self, group: int, lane0: int, n: int, seed: int, algo, beta: float, nsweeps: int,
+                     job_group: int = 0):
+        """Samples 64 job_group .. + n - 1 of the job with this seed into
+        lanes lane0 .. lane0 + n - 1 of `group`."""
+        a = _ALGOS[algo] if isinstance(algo, str) else int(algo)
+        _check(self._lib.ianus_segment_load(self._h, group, lane0, n, seed & 0xFFFFFFFFFFFFFFFF, job_group, a,
+                                            float(beta), nsweeps), "ianus_segment_load")
+
+    def segment_release(self, group: int, lane0: int):
+        _check(self._lib.ianus_segment_release(self._h, group, lane0), "ianus_segment_release")
+
+    def segment_state(self, group: int, lane0: int) -> tuple[int, int]:
+        done, req = C.c_uint64(), C.c_uint64()
+        _check(self._lib.ianus_segment_state(self._h, group, lane0, C.byref(done), C.byref(req)),
+               "ianus_segment_state")
+        return int(done.value), int(req.value)
+
+    def sweep_segments(self, nsweeps: int):
+        _check(self._lib.ianus_sweep_segments(self._h, nsweeps), "ianus_sweep_segments")
 
     def sweep_pt(self, algo, beta, nsweeps: int, swap_every: int, measure_every: int = 0):
         a = _ALGOS[algo] if isinstance(algo, str) else int(algo)

@@ -25,6 +25,8 @@ struct Sizes {
   bool field;
   uint32_t rows;
   size_t off_wheels, wheel_bytes;
+  bool poolable;
+  size_t off_segs, off_nseg;
   size_t off_spins, off_J, off_thr, off_tp, off_fthr, off_ftp, off_sites, off_ptab, off_pttab, off_ptsign, off_slot,
       off_temp, off_acc_pt, off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
   size_t spins_bytes, J_bytes, sites_bytes;
@@ -111,6 +113,11 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
   z.off_sites = take(z.sites_bytes);
   z.off_wheels = take(z.wheel_bytes);
+  // segment tables for fused serving: bit-sliced EA lattices with one replica
+  // and one temperature
+  z.poolable = !potts && !field && layout == IANUS_LAYOUT_BITS64 && z.R == 1 && z.K == 1;
+  z.off_segs = take(z.poolable ? (size_t)z.G * kMaxSegs * sizeof(Segment) : 0);
+  z.off_nseg = take(z.poolable ? (size_t)z.G * 4 : 0);
   z.off_ptab = take(layout != IANUS_LAYOUT_U8X4 ? 0
                     : c->model == IANUS_POTTS4_PERM ? (size_t)z.K * perm_table_entries(z.D) * 16
                                                     : (size_t)z.K * 65536 * 16);
@@ -494,6 +501,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->occ = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) + (size_t)z.S * z.N : nullptr;
   lat->hbits = z.field && z.layout == IANUS_LAYOUT_BITS64 ? (uint64_t*)(b + z.off_sites) : nullptr;
   lat->wheels = z.wheel_bytes ? (uint32_t*)(b + z.off_wheels) : nullptr;
+  lat->segs = z.poolable ? (Segment*)(b + z.off_segs) : nullptr;
+  lat->nseg = z.poolable ? (uint32_t*)(b + z.off_nseg) : nullptr;
   lat->ptab = (uint4*)(b + z.off_ptab);
   lat->pttab = (uint64_t*)(b + z.off_pttab);
   lat->pt_sign = (int8_t*)(b + z.off_ptsign);
@@ -520,6 +529,17 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
     delete lat;
     return (ianus_status)code;
   };
+  if (z.poolable) {
+    lat->segs_host = new (std::nothrow) std::vector<Segment>((size_t)z.G * kMaxSegs);
+    lat->nseg_host = new (std::nothrow) std::vector<uint32_t>((size_t)z.G, 0u);
+    lat->tp_host = new (std::nothrow) std::vector<uint64_t>((size_t)z.G * kPlanes * kMaxClasses, 0ull);
+    if (!lat->segs_host || !lat->nseg_host || !lat->tp_host) {
+      delete lat->segs_host;
+      delete lat->nseg_host;
+      delete lat->tp_host;
+      return bail(IANUS_ENOMEM);
+    }
+  }
   if (cudaMemsetAsync(lat->base, 0, z.total, lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
   {
     std::vector<int32_t> perm((size_t)z.S * z.R * z.K);
@@ -555,6 +575,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
 ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uint64_t nsweeps,
                          uint32_t measure_every) {
   GET_LAT(h);
+  if (lat->pool) return IANUS_EINVAL;  // a pool is driven by ianus_sweep_segments
   if (!beta || (algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH)) return IANUS_EINVAL;
   if (!beta_ok(beta, lat->K)) return IANUS_EINVAL;
   if (lat->model != IANUS_EA_PM_J && algo == IANUS_METROPOLIS) return IANUS_EUNSUPPORTED;
@@ -594,6 +615,7 @@ ianus_status ianus_sweep(ianus_lattice* h, int32_t algo, const double* beta, uin
 
 ianus_status ianus_pt_swap(ianus_lattice* h) {
   GET_LAT(h);
+  if (lat->pool) return IANUS_EINVAL;
   if (lat->K < 2 || !lat->tables_ok) return IANUS_EINVAL;
   if (lat->model != IANUS_EA_PM_J || lat->field) return IANUS_EUNSUPPORTED;
   return (ianus_status)do_pt_swap(lat);
@@ -789,6 +811,152 @@ ianus_status ianus_set_sites_i8(ianus_lattice* h, const int8_t* hsign, const int
   return e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
 }
 
+// ---- fused serving: jobs in lanes of a pool lattice ----
+
+static int segment_find(const Lattice* lat, int group, int lane0) {
+  const uint32_t ns = (*lat->nseg_host)[group];
+  for (uint32_t j = 0; j < ns; ++j)
+    if ((int)(*lat->segs_host)[(size_t)group * kMaxSegs + j].lane0 == lane0) return (int)j;
+  return -1;
+}
+
+static ianus_status upload_group(Lattice* lat, int group) {
+  CK(cudaMemcpyAsync(lat->segs + (size_t)group * kMaxSegs, lat->segs_host->data() + (size_t)group * kMaxSegs,
+                     kMaxSegs * sizeof(Segment), cudaMemcpyHostToDevice, lat->stream));
+  CK(cudaMemcpyAsync(lat->nseg + group, lat->nseg_host->data() + group, 4, cudaMemcpyHostToDevice, lat->stream));
+  CK(cudaMemcpyAsync(lat->tp + (size_t)group * kPlanes * kMaxClasses,
+                     lat->tp_host->data() + (size_t)group * kPlanes * kMaxClasses,
+                     kPlanes * kMaxClasses * sizeof(uint64_t), cudaMemcpyHostToDevice, lat->stream));
+  // the host copies may change again before the copy runs: wait for it
+  CK(cudaStreamSynchronize(lat->stream));
+  return IANUS_OK;
+}
+
+ianus_status ianus_segment_load(ianus_lattice* h, int32_t group, int32_t lane0, int32_t n, uint64_t seed,
+                                int32_t job_group, int32_t algo, double beta, uint64_t nsweeps) {
+  GET_LAT(h);
+  if (!lat->segs) return IANUS_EUNSUPPORTED;
+  if (group < 0 || group >= lat->G || lane0 < 0 || n < 1 || lane0 + n > 64) return IANUS_EINVAL;
+  if (job_group < 0 || job_group >= 4096) return IANUS_EINVAL;
+  if ((algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH) || !std::isfinite(beta) || beta < 0.0) return IANUS_EINVAL;
+  const uint64_t mask = (n >= 64 ? ~0ull : ((1ull << n) - 1ull)) << lane0;
+  uint32_t& ns = (*lat->nseg_host)[group];
+  for (uint32_t j = 0; j < ns; ++j)
+    if ((*lat->segs_host)[(size_t)group * kMaxSegs + j].mask & mask) return IANUS_EINVAL;  // lanes taken
+  if (ns >= (uint32_t)kMaxSegs) return IANUS_EINVAL;
+  if (!lat->pool) {
+    lat->pool = true;
+    drop_graphs(lat);
+  }
+  const PhiloxKeys keys = make_keys(seed);
+  CK(launch_load_segment(*lat, group, (uint32_t)lane0, (uint32_t)n, (uint32_t)job_group, keys));
+  // per-lane thresholds of the job's (algo, beta), as its own lattice would use
+  uint64_t thr[kMaxClasses];
+  class_thresholds(lat->D, algo, beta, thr);
+  uint64_t* tp = lat->tp_host->data() + (size_t)group * kPlanes * kMaxClasses;
+  for (int u = 0; u < kMaxClasses; ++u) {
+    for (int q = 0; q < kPlanes; ++q) tp[q * kMaxClasses + u] &= ~mask;
+    if (u > 2 * lat->D) continue;
+    if (thr[u] >= kTwo32) {
+      tp[32 * kMaxClasses + u] |= mask;
+    } else {
+      for (int q = 0; q < 32; ++q)
+        if ((thr[u] >> (31 - q)) & 1ull) tp[q * kMaxClasses + u] |= mask;
+    }
+  }
+  Segment sg{};
+  sg.mask = mask;
+  sg.t = 0;
+  sg.t_end = nsweeps;
+  sg.key_lo = (uint32_t)(seed & 0xffffffffu);
+  sg.key_hi = (uint32_t)(seed >> 32);
+  sg.lane0 = (uint32_t)lane0;
+  sg.inv = algo == IANUS_HEATBATH ? 1u : 0u;
+  sg.jgroup = (uint32_t)job_group;
+  (*lat->segs_host)[(size_t)group * kMaxSegs + ns] = sg;
+  ns += 1;
+  return upload_group(lat, group);
+}
+
+ianus_status ianus_segment_release(ianus_lattice* h, int32_t group, int32_t lane0) {
+  GET_LAT(h);
+  if (!lat->segs || group < 0 || group >= lat->G) return IANUS_EINVAL;
+  const int j = segment_find(lat, group, lane0);
+  if (j < 0) return IANUS_EINVAL;
+  uint32_t& ns = (*lat->nseg_host)[group];
+  Segment* base = lat->segs_host->data() + (size_t)group * kMaxSegs;
+  base[j] = base[ns - 1];  // keep the table compact; order is immaterial
+  base[ns - 1] = Segment{};
+  ns -= 1;
+  return upload_group(lat, group);
+}
+
+ianus_status ianus_segment_state(ianus_lattice* h, int32_t group, int32_t lane0, uint64_t* sweeps_done,
+                                 uint64_t* sweeps_requested) {
+  GET_LAT(h);
+  if (!lat->segs || group < 0 || group >= lat->G) return IANUS_EINVAL;
+  const int j = segment_find(lat, group, lane0);
+  if (j < 0) return IANUS_EINVAL;
+  const Segment& sg = (*lat->segs_host)[(size_t)group * kMaxSegs + j];
+  if (sweeps_done) *sweeps_done = sg.t;
+  if (sweeps_requested) *sweeps_requested = sg.t_end;
+  return IANUS_OK;
+}
+
+static int fused_sweep_once(Lattice* lat) {
+  CK(launch_sweep_fused(*lat, 0));
+  CK(launch_sweep_fused(*lat, 1));
+  CK(launch_advance_segments(*lat));
+  return IANUS_OK;
+}
+
+ianus_status ianus_sweep_segments(ianus_lattice* h, uint64_t nsweeps) {
+  GET_LAT(h);
+  if (!lat->segs) return IANUS_EUNSUPPORTED;
+  uint64_t left = nsweeps;
+  while (left > 0) {
+    const uint32_t B = (uint32_t)std::min<uint64_t>(left, 64);
+    if (B < 4 || !lat->use_graphs || !lat->graphs) {
+      for (uint32_t k = 0; k < B; ++k) {
+        int st = fused_sweep_once(lat);
+        if (st) return (ianus_status)st;
+      }
+    } else {
+      const uint32_t key = (1u << 31) | B;
+      auto it = lat->graphs->find(key);
+      if (it == lat->graphs->end()) {
+        if (!lat->cap_stream) CK(cudaStreamCreateWithFlags(&lat->cap_stream, cudaStreamNonBlocking));
+        cudaStream_t user = lat->stream;
+        lat->stream = lat->cap_stream;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(lat->cap_stream, cudaStreamCaptureModeThreadLocal);
+        int st = IANUS_OK;
+        for (uint32_t k = 0; e == cudaSuccess && st == IANUS_OK && k < B; ++k) st = fused_sweep_once(lat);
+        cudaError_t e2 = cudaStreamEndCapture(lat->cap_stream, &g);
+        lat->stream = user;
+        cudaGraphExec_t ex = nullptr;
+        if (e != cudaSuccess || e2 != cudaSuccess || st != IANUS_OK || !g ||
+            cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          return IANUS_ECUDA;
+        }
+        cudaGraphDestroy(g);
+        it = lat->graphs->emplace(key, ex).first;
+      }
+      CK(cudaGraphLaunch(it->second, lat->stream));
+    }
+    // the host copy follows the device counters: every live segment advances
+    for (int g = 0; g < lat->G; ++g)
+      for (uint32_t j = 0; j < (*lat->nseg_host)[g]; ++j) {
+        Segment& sg = (*lat->segs_host)[(size_t)g * kMaxSegs + j];
+        sg.t = std::min<uint64_t>(sg.t_end, sg.t + B);
+      }
+    left -= B;
+  }
+  return IANUS_OK;
+}
+
 ianus_status ianus_get_pt_state(ianus_lattice* h, int32_t* slot_at, uint64_t* accepted, uint64_t* swap_steps) {
   GET_LAT(h);
   const size_t n = (size_t)lat->S * lat->R * lat->K;
@@ -810,6 +978,7 @@ ianus_status ianus_get_sweeps(ianus_lattice* h, uint64_t* sweeps) {
 
 ianus_status ianus_get_state(ianus_lattice* h, void* host_buf, size_t cap, size_t* n) {
   GET_LAT(h);
+  if (lat->pool) return IANUS_EUNSUPPORTED;  // segment tables are not part of the blob
   Sizes z;
   plan(&lat->cfg, z);
   const size_t perm = (size_t)lat->S * lat->R * lat->K * 4;
@@ -955,6 +1124,9 @@ ianus_status ianus_destroy(ianus_lattice* h) {
   cudaStreamSynchronize(lat->stream);
   drop_graphs(lat);
   delete lat->graphs;
+  delete lat->segs_host;
+  delete lat->nseg_host;
+  delete lat->tp_host;
   if (lat->cap_stream) cudaStreamDestroy(lat->cap_stream);
   if (lat->owns_buffer) cudaFree(lat->base);
   delete lat;

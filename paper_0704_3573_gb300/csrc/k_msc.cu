@@ -251,6 +251,140 @@ __global__ void k_set_sites_bits(uint64_t* hbits, const int8_t* in, Geom geom, i
   }
 }
 
+// ---- fused serving: several jobs in the lanes of one group ----
+//
+// One block per (word range, group).  The block stages the group's per-lane
+// threshold planes and its segment table.  Per plane pair, every segment
+// that still has undecided lanes draws one Philox block from its own stream
+// (key of the job's seed, counter of the job's sweep t, group 0, slot 0) and
+// contributes its bits 0..n-1 shifted to its lanes.  Heat-bath lanes flip on
+// "not less" (inv lanes), Metropolis lanes on "less"; lanes of no live
+// segment never flip.
+template <int D, bool P2>
+__global__ void __launch_bounds__(kBlock) k_sweep_fused(const BitsParams p, const Segment* __restrict__ segs,
+                                                        const uint32_t* __restrict__ nseg) {
+  __shared__ uint64_t tpa[kPlanes * kMaxClasses];
+  __shared__ uint64_t s_mask[kMaxSegs];
+  __shared__ uint32_t s_klo[kMaxSegs], s_khi[kMaxSegs];
+  __shared__ Tick s_t[kMaxSegs];
+  __shared__ uint32_t s_lane0[kMaxSegs], s_c2[kMaxSegs];
+  __shared__ int s_n;
+  __shared__ uint64_t s_live, s_inv;
+  const int g = blockIdx.y;
+  for (int k = threadIdx.x; k < kPlanes * kMaxClasses; k += kBlock)
+    tpa[k] = p.tp[(size_t)g * kPlanes * kMaxClasses + k];
+  if (threadIdx.x == 0) {
+    const uint32_t ns = min(nseg[g], (uint32_t)kMaxSegs);
+    uint64_t live = 0, inv = 0;
+    int n = 0;
+    for (uint32_t j = 0; j < ns; ++j) {
+      const Segment sg = segs[(size_t)g * kMaxSegs + j];
+      if (sg.t >= sg.t_end || sg.mask == 0ull) continue;
+      s_mask[n] = sg.mask;
+      s_klo[n] = sg.key_lo;
+      s_khi[n] = sg.key_hi;
+      s_t[n] = Tick{(uint32_t)sg.t, (uint32_t)(sg.t >> 32)};
+      s_lane0[n] = sg.lane0;
+      s_c2[n] = (TAG_SPIN << 28) | sg.jgroup;  // slot 0, the job's own group
+      live |= sg.mask;
+      if (sg.inv) inv |= sg.mask;
+      ++n;
+    }
+    s_n = n;
+    s_live = live;
+    s_inv = inv;
+  }
+  __syncthreads();
+  const uint64_t live = s_live, inv = s_inv;
+  const int nsg = s_n;
+  if (live == 0ull) return;
+  const Geom geom = p.geom;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = p.J + (size_t)g * D * N;
+  uint64_t* sp = p.spins + (size_t)g * N;  // one slot per group
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
+    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
+    const uint64_t b = sp[n.self];
+    uint64_t e[2 * D];
+    e[0] = b ^ sp[n.xp] ^ __ldg(Jg + n.self);
+    e[1] = b ^ sp[n.xm] ^ __ldg(Jg + n.xm);
+    e[2] = b ^ sp[n.yp] ^ __ldg(Jg + N + n.self);
+    e[3] = b ^ sp[n.ym] ^ __ldg(Jg + N + n.ym);
+    if (D == 3) {
+      e[4] = b ^ sp[n.zp] ^ __ldg(Jg + 2u * N + n.self);
+      e[5] = b ^ sp[n.zm] ^ __ldg(Jg + 2u * N + n.zm);
+    }
+    uint64_t u0, u1, u2;
+    count_unsat<D>(e, u0, u1, u2);
+    uint64_t m[2 * D + 1];
+#pragma unroll
+    for (int u = 0; u <= 2 * D; ++u)
+      m[u] = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
+    uint64_t always = 0;
+#pragma unroll
+    for (int u = 0; u <= 2 * D; ++u) always |= m[u] & tpa[32 * kMaxClasses + u];
+    uint64_t lt = always;
+    uint64_t und = ~always & live;
+#pragma unroll 1
+    for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
+      uint64_t r0 = 0, r1 = 0;
+#pragma unroll 1
+      for (int j = 0; j < nsg; ++j) {
+        const uint64_t mk = s_mask[j];
+        if (!(und & mk)) continue;
+        const uint4 x = philox10_key(n.site, s_t[j].lo, s_c2[j] | (mm << 24), s_t[j].hi, s_klo[j], s_khi[j]);
+        const uint32_t sh = s_lane0[j];
+        r0 |= (((uint64_t)x.x | ((uint64_t)x.y << 32)) << sh) & mk;
+        r1 |= (((uint64_t)x.z | ((uint64_t)x.w << 32)) << sh) & mk;
+      }
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const uint64_t r = q == 0 ? r0 : r1;
+        const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * kMaxClasses;
+        uint64_t tb = 0;
+#pragma unroll
+        for (int u = 0; u <= 2 * D; ++u) tb |= m[u] & row[u];
+        lt |= und & ~r & tb;
+        und &= ~(r ^ tb);
+      }
+    }
+    const uint64_t flip = (lt ^ inv) & live;
+    if (flip) sp[n.self] = b ^ flip;
+  }
+}
+
+// A job's couplings and initial spins, as samples 64 jgroup + b of its own
+// lattice (group jgroup, slot 0 of the J and INIT streams under the job's
+// key), written into lanes lane0 + b of group g.
+__global__ void k_load_segment(uint64_t* spins, uint64_t* J, Geom geom, int g, uint32_t lane0, uint64_t mask,
+                               uint32_t jgroup, PhiloxKeys keys) {
+  const uint32_t L = (uint32_t)geom.L;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < geom.N; i += gridDim.x * blockDim.x) {
+    const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
+    const uint32_t j = split_index(geom, x, y, z);
+    for (int d = 0; d < geom.D; ++d) {
+      const uint4 r = philox10(i, (uint32_t)d, (TAG_J << 28) | jgroup, 0u, keys);
+      uint64_t* wp = J + ((size_t)g * geom.D + d) * geom.N + j;
+      *wp = (*wp & ~mask) | ((((uint64_t)r.x | ((uint64_t)r.y << 32)) << lane0) & mask);
+    }
+    const uint4 r = philox10(i, 0u, (TAG_INIT << 28) | jgroup, 0u, keys);
+    uint64_t* wp = spins + (size_t)g * geom.N + j;
+    *wp = (*wp & ~mask) | ((((uint64_t)r.x | ((uint64_t)r.y << 32)) << lane0) & mask);
+  }
+}
+
+__global__ void k_advance_segments(Segment* segs, const uint32_t* nseg, int G) {
+  const int total = G * kMaxSegs;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int g = idx / kMaxSegs, j = idx - g * kMaxSegs;
+    if ((uint32_t)j >= nseg[g]) continue;
+    Segment& sg = segs[idx];
+    if (sg.mask != 0ull && sg.t < sg.t_end) sg.t += 1;
+  }
+}
+
 // ---- initialisation: one Philox block gives the word of 64 samples ----
 
 __global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int slots, int jmode,
@@ -721,6 +855,55 @@ cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs) {
 cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs) {
   k_set_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, dev_hs, lat.geom, lat.S,
                                                                                lat.G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_t n, uint32_t jgroup,
+                                PhiloxKeys job_keys) {
+  const uint64_t mask = (n >= 64u ? ~0ull : ((1ull << n) - 1ull)) << lane0;
+  k_load_segment<<<grid_for(lat.N), 256, 0, lat.stream>>>((uint64_t*)lat.spins, (uint64_t*)lat.J, lat.geom, group,
+                                                          lane0, mask, jgroup, job_keys);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance_segments(Lattice& lat) {
+  k_advance_segments<<<grid_for((uint64_t)lat.G * kMaxSegs, 128), 128, 0, lat.stream>>>(lat.segs, lat.nseg, lat.G);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_sweep_fused(Lattice& lat, int colour) {
+  BitsParams p;
+  p.spins = (uint64_t*)lat.spins;
+  p.J = (const uint64_t*)lat.J;
+  p.tp = lat.tp;
+  p.geom = lat.geom;
+  p.G = lat.G;
+  p.R = 1;
+  p.K = 1;
+  p.slots = 1;
+  p.colour = colour;
+  p.t_lo = p.t_hi = 0;
+  p.keys = lat.keys;
+  p.t_dev = nullptr;
+  const uint32_t half = lat.geom.half;
+  uint32_t target_blocks = (152u * 8u + (uint32_t)lat.G - 1) / (uint32_t)lat.G;
+  uint32_t wpb = (half + target_blocks - 1) / target_blocks;
+  wpb = ((wpb + kBlock - 1) / kBlock) * kBlock;
+  if (wpb < (uint32_t)kBlock) wpb = kBlock;
+  p.words_per_block = wpb;
+  dim3 grid((half + wpb - 1) / wpb, (unsigned)lat.G);
+  const bool p2 = lat.geom.lL > 0;
+  if (lat.D == 3) {
+    if (p2)
+      k_sweep_fused<3, true><<<grid, kBlock, 0, lat.stream>>>(p, lat.segs, lat.nseg);
+    else
+      k_sweep_fused<3, false><<<grid, kBlock, 0, lat.stream>>>(p, lat.segs, lat.nseg);
+  } else {
+    if (p2)
+      k_sweep_fused<2, true><<<grid, kBlock, 0, lat.stream>>>(p, lat.segs, lat.nseg);
+    else
+      k_sweep_fused<2, false><<<grid, kBlock, 0, lat.stream>>>(p, lat.segs, lat.nseg);
+  }
   return cudaGetLastError();
 }
 

@@ -32,6 +32,23 @@ struct UniformLut {
   uint8_t always, need, pad0, pad1;
 };
 
+// Fused serving: a job occupies the lanes [lane0, lane0 + n) of one 64-lane
+// group of a pool lattice (bit-sliced, one replica, one temperature).  Its
+// lanes draw the random planes of the job's own stream (key from its seed,
+// its own sweep counter t), so its trajectory equals that of the job run on
+// its own lattice.
+struct Segment {
+  uint64_t mask;      // lanes of the segment
+  uint64_t t;         // sweeps done
+  uint64_t t_end;     // sweeps requested
+  uint32_t key_lo, key_hi;
+  uint32_t lane0;
+  uint32_t inv;       // heat bath: 1
+  uint32_t jgroup;    // the lanes are samples 64 jgroup + (lane - lane0) of the job
+  uint32_t pad;
+};
+constexpr int kMaxSegs = 64;  // per group
+
 struct Lattice {
   ianus_config cfg;
   int model, D, L, S, R, K, slots, layout;
@@ -80,6 +97,13 @@ struct Lattice {
   int rng;
   uint32_t* wheels;
   uint32_t rows;
+  // fused serving (pool lattices): segment tables [G][kMaxSegs], counts [G]
+  bool pool;
+  Segment* segs;
+  uint32_t* nseg;
+  std::vector<Segment>* segs_host;
+  std::vector<uint32_t>* nseg_host;
+  std::vector<uint64_t>* tp_host;  // per-lane planes [G][kPlanes][kMaxClasses]
 
   int mq;               // magnetisation entries per configuration (1 Ising, 4 Potts, 2 field models)
   uint32_t cap;         // series capacity
@@ -161,6 +185,11 @@ cudaError_t launch_init_sites_bits(Lattice& lat);                    // hbits fr
 cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs);     // [S][N]
 cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs);
 cudaError_t launch_build_field_planes(Lattice& lat);                 // ftp from fthr and temp_of
+// fused serving (k_msc.cu)
+cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_t n, uint32_t jgroup,
+                                PhiloxKeys job_keys);
+cudaError_t launch_sweep_fused(Lattice& lat, int colour);
+cudaError_t launch_advance_segments(Lattice& lat);
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
 cudaError_t launch_measure_bits(Lattice& lat, int want_q);
 cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
