@@ -30,6 +30,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -146,7 +147,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"ianus_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -251,7 +252,11 @@ def run_gpu(args, ws, rank, local):
     lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=seed, layout="bits64",
                         series_capacity=4096, stream=stream)
     tuned = None
-    if not args.no_tune:  # kernel variant and launch shape by the autotuner (restores the state)
+    if args.variant is not None:  # a fixed kernel variant and launch shape (profiling runs)
+        lat.set_variant(args.variant)
+        lat.set_block_words(args.block_words)
+        tuned = {"variant": args.variant, "block_words": args.block_words, "us_per_sweep": None}
+    elif not args.no_tune:  # kernel variant and launch shape by the autotuner (restores the state)
         from paper_0704_3573_gb300 import tune
 
         t = tune.tune(lat, ianus.HEATBATH, beta, sweeps=40, use_cache=False)
@@ -715,6 +720,8 @@ def main():
     ap.add_argument("--serve-jobs", type=int, default=400)
     ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--variant", type=int, default=None, help="fixed kernel variant instead of the autotuner")
+    ap.add_argument("--block-words", type=int, default=0, help="launch shape with --variant (0 = heuristic)")
     ap.add_argument("--serve-scale", type=float, default=0.05)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)

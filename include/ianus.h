@@ -403,7 +403,10 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       after 4, 4, 3 or 5 lockstep plane pairs, finished 32 at a time, with
  *       3, 4, 3 or 3 blocks per SM; 8, 9 =
  *       lockstep with the two replicas interleaved in one thread, 2 or 3
- *       blocks per SM (needs two replicas; otherwise shape 2 is used).
+ *       blocks per SM (needs two replicas; otherwise shape 2 is used);
+ *   10..12 = shapes 2, 4 and a queue after 6 pairs, with the Philox blocks
+ *       of two consecutive plane pairs computed together (two independent
+ *       round chains in flight), 3 blocks per SM.
  * If run-time compilation is unavailable, the precompiled kernel runs.
  * EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);

@@ -1092,7 +1092,7 @@ ianus_status ianus_synchronize(ianus_lattice* h) {
 
 ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   GET_LAT(h);
-  if (variant < 0 || variant > 9) return IANUS_EINVAL;
+  if (variant < 0 || variant > kMaxVariant) return IANUS_EINVAL;
   if (lat->variant != variant) drop_graphs(lat);
   lat->variant = variant;
   return IANUS_OK;

@@ -36,6 +36,14 @@ constexpr int kBlock = 256;
 constexpr int kMode = IANUS_JIT_MODE;
 constexpr int kPhaseA = IANUS_JIT_PHASEA;
 constexpr int kUnrolled = kMode == 1 ? kPhaseA : 8;
+// IANUS_JIT_GROUP 2: the Philox blocks of two consecutive plane pairs are
+// computed back to back before either is compared, so that two independent
+// round chains are in flight.  A warp runs a pair whenever any of its words
+// needs it, so the second block is almost never extra issue work.
+#ifndef IANUS_JIT_GROUP
+#define IANUS_JIT_GROUP 1
+#endif
+constexpr int kGroup = IANUS_JIT_GROUP;
 
 template <uint32_t LUT>
 __device__ __forceinline__ uint64_t lop3c(uint64_t a, uint64_t b, uint64_t c) {
@@ -53,10 +61,9 @@ struct Word {
   uint64_t u0, u1, u2, und, lt;
 };
 
-// One plane pair with compile-time tables: planes 2M and 2M+1.
+// Planes 2M and 2M+1 from their Philox block x, compile-time tables.
 template <int M>
-__device__ __forceinline__ void pair(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
-  const uint4 x = philox10(site, tk.lo, c2 | ((uint32_t)M << 24), tk.hi, p.keys);
+__device__ __forceinline__ void planes(Word& w, const uint4& x) {
   const uint64_t r0 = (uint64_t)x.x | ((uint64_t)x.y << 32);
   const uint64_t r1 = (uint64_t)x.z | ((uint64_t)x.w << 32);
   const uint64_t t0 = lop3c<kLut[2 * M]>(w.u2, w.u1, w.u0);
@@ -66,6 +73,13 @@ __device__ __forceinline__ void pair(Word& w, const BitsParams& p, const Tick& t
   const uint64_t c1 = w.und & t1 & ~r1;
   w.und &= ~(r1 ^ t1);
   w.lt |= c0 | c1;
+}
+
+// One plane pair: planes 2M and 2M+1.
+template <int M>
+__device__ __forceinline__ void pair(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
+  const uint4 x = philox10(site, tk.lo, c2 | ((uint32_t)M << 24), tk.hi, p.keys);
+  planes<M>(w, x);
 }
 
 template <int M>
@@ -79,13 +93,28 @@ __device__ __forceinline__ void pairs2(Word& w0, Word& w1, const BitsParams& p, 
   }
 }
 
+// Pairs M..END-1 in lockstep with immediate tables (two at a time with
+// IANUS_JIT_GROUP 2).
+template <int M, int END>
+__device__ __forceinline__ void pairs_range(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
+  if constexpr (M < END) {
+    if (w.und == 0ull) return;
+    if constexpr (kGroup == 2 && M + 1 < END) {
+      const uint4 xa = philox10(site, tk.lo, c2 | ((uint32_t)M << 24), tk.hi, p.keys);
+      const uint4 xb = philox10(site, tk.lo, c2 | ((uint32_t)(M + 1) << 24), tk.hi, p.keys);
+      planes<M>(w, xa);
+      planes<M + 1>(w, xb);
+      pairs_range<M + 2, END>(w, p, tk, site, c2);
+    } else {
+      pair<M>(w, p, tk, site, c2);
+      pairs_range<M + 1, END>(w, p, tk, site, c2);
+    }
+  }
+}
+
 template <int M>
 __device__ __forceinline__ void pairs(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
-  if constexpr (M < kUnrolled) {
-    if (w.und == 0ull) return;
-    pair<M>(w, p, tk, site, c2);
-    pairs<M + 1>(w, p, tk, site, c2);
-  }
+  pairs_range<M, kUnrolled>(w, p, tk, site, c2);
 }
 
 // Modes 0 and 2 (and the queued words of mode 1): pairs 8..15 of one word,
@@ -164,15 +193,6 @@ __device__ __forceinline__ void finish(const Ctx& c, uint32_t self, uint32_t a, 
   if (flip) sp[self] ^= flip;
 }
 
-// Pairs M..END-1 in lockstep with immediate tables.
-template <int M, int END>
-__device__ __forceinline__ void pairs_range(Word& w, const BitsParams& p, const Tick& tk, uint32_t site, uint32_t c2) {
-  if constexpr (M < END) {
-    if (w.und == 0ull) return;
-    pair<M>(w, p, tk, site, c2);
-    pairs_range<M + 1, END>(w, p, tk, site, c2);
-  }
-}
 
 // Warp-wide append of the lanes with pred set; n is warp-uniform.
 __device__ __forceinline__ void push(Queue& q, uint32_t& n, bool pred, const Word& w, uint32_t self, uint32_t site,

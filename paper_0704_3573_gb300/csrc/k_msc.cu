@@ -466,25 +466,22 @@ __global__ void k_build_field_planes(uint64_t* ftp, const uint64_t* fthr, const 
   }
 }
 
-// ---- measurements: per-lane counts with vertical (bit-sliced) counters ----
+// ---- measurements: per-lane column sums by warp bit-transposes ----
 //
-// Per site and configuration: unsatisfied forward bonds U (E = 2U - D N) and
-// spin-down count B (M = N - 2B).  Each thread adds its masks into 6-plane
-// vertical counters over kMeasIters sites (at most 3 increments a site:
-// 48 < 64), then the warp transposes each plane with shuffles so that thread
-// j holds bit j of every thread's plane; a popcount gives lane j's total.
+// A warp holds 32 site words, one per thread.  For a 64-bit quantity per
+// word (bits of the unsatisfied forward bonds, the spin-down bits, the
+// disagreement bits of two replicas), transposing the low and the high 32x32
+// halves across the warp leaves in thread t the bits of sample lanes t and
+// 32 + t of all 32 words, so a popcount gives each lane's count over those
+// sites.  The D forward bonds of a site are first added into a 2-bit number
+// (sum and carry words, weights 1 and 2).  Each thread keeps the running
+// totals of its two lanes; at the end the block sums its warps in shared
+// memory and adds one value per lane and quantity to the accumulators.
+// Per site and configuration this gives U (E = 2U - D N), B (M = N - 2B) and
+// X (Q = N - 2X).
 
-constexpr int kCtr = 6;
-constexpr int kMeasIters = 16;
-
-__device__ __forceinline__ void ctr_add(uint64_t* c, uint64_t x) {
-#pragma unroll
-  for (int k = 0; k < kCtr; ++k) {
-    const uint64_t t = c[k] & x;
-    c[k] ^= x;
-    x = t;
-  }
-}
+constexpr int kMeasWarps = kBlock / 32;
+constexpr int kMeasMaxQ = 7;  // quantities per block: U and B of two replicas, X, field F
 
 // 32x32 bit transpose across the warp: afterwards thread j holds, in bit t,
 // bit j of the word thread t passed in (five butterfly exchanges).
@@ -500,145 +497,182 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
   return x;
 }
 
-// Warp-wide per-lane totals of a vertical counter; thread t receives the
-// totals of sample lanes t and t+32.
-__device__ __forceinline__ void ctr_flush(const uint64_t* c, long long& lo, long long& hi) {
-  lo = hi = 0;
-#pragma unroll
-  for (int k = 0; k < kCtr; ++k) {
-    lo += (long long)__popc(warp_transpose32((uint32_t)c[k])) << k;
-    hi += (long long)__popc(warp_transpose32((uint32_t)(c[k] >> 32))) << k;
+// Adds the per-lane column counts of w (weight 2^shift) over the warp's 32
+// words to the totals of lanes (t, 32 + t).
+__device__ __forceinline__ void col_add(uint64_t w, int shift, long long& lo, long long& hi) {
+  lo += (long long)__popc(warp_transpose32((uint32_t)w)) << shift;
+  hi += (long long)__popc(warp_transpose32((uint32_t)(w >> 32))) << shift;
+}
+
+// Split index j -> split indices of the forward neighbours x+1, y+1, z+1.
+struct Fwd {
+  uint32_t x, y, z;
+};
+
+template <bool P2>
+__device__ __forceinline__ Fwd split_forward(const Geom& g, uint32_t j) {
+  const uint32_t h = (uint32_t)g.h, L = (uint32_t)g.L;
+  uint32_t rc, k, y, z;
+  if (P2) {
+    rc = j >> g.lh;
+    k = j & (h - 1u);
+    y = (rc >> 1) & (L - 1u);
+    z = (rc >> 1) >> g.lL;
+  } else {
+    rc = j / h;
+    k = j - rc * h;
+    y = (rc >> 1) % L;
+    z = (rc >> 1) / L;
+  }
+  const uint32_t row = rc >> 1, c = rc & 1u, oc = c ^ 1u;
+  const uint32_t x = 2u * k + ((c ^ (y + z)) & 1u);
+  Fwd f;
+  f.x = (2u * row + oc) * h + (x + 1u == L ? 0u : (x + 1u) >> 1);
+  f.y = (2u * ((y + 1u == L ? 0u : y + 1u) + L * z) + oc) * h + k;
+  f.z = g.D == 3 ? (2u * (y + L * (z + 1u == L ? 0u : z + 1u)) + oc) * h + k : 0u;
+  return f;
+}
+
+// Unsatisfied forward bonds of a site as a 2-bit number (sum, carry).
+template <int D>
+__device__ __forceinline__ void bond_count(uint64_t b, uint64_t nx, uint64_t ny, uint64_t nz, uint64_t Jx,
+                                           uint64_t Jy, uint64_t Jz, uint64_t& s1, uint64_t& c1) {
+  const uint64_t ex = b ^ nx ^ Jx, ey = b ^ ny ^ Jy;
+  if (D == 3) {
+    const uint64_t ez = b ^ nz ^ Jz;
+    s1 = ex ^ ey ^ ez;
+    c1 = (ex & ey) | (ex & ez) | (ey & ez);
+  } else {
+    s1 = ex ^ ey;
+    c1 = ex & ey;
   }
 }
 
-__device__ __forceinline__ void acc_add(int64_t* acc, int s, int S, size_t row, int field, long long v) {
-  if (s < S) atomicAdd((unsigned long long*)&acc[row * kAccStride + field], (unsigned long long)v);
+// Block reduction of the per-thread lane totals tot[q][2] and one atomic add
+// per (lane, quantity) into acc[sample][row_of(q)][field_of(q)].
+__device__ __forceinline__ void block_flush(long long (*red)[64], const long long (*tot)[2], int nq, int g, int S,
+                                            int64_t* acc, const int* row_off, const int* field, int row_stride) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int q = 0; q < nq; ++q) {
+    red[warp * kMeasMaxQ + q][lane] = tot[q][0];
+    red[warp * kMeasMaxQ + q][32 + lane] = tot[q][1];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nq * 64; idx += kBlock) {
+    const int q = idx >> 6, l = idx & 63;
+    long long v = 0;
+    for (int w = 0; w < kMeasWarps; ++w) v += red[w * kMeasMaxQ + q][l];
+    const int s = 64 * g + l;
+    if (s < S && v != 0)
+      atomicAdd((unsigned long long*)&acc[((size_t)s * row_stride + row_off[q]) * kAccStride + field[q]],
+                (unsigned long long)v);
+  }
 }
 
-// One temperature (slot = replica): E and M of every replica and, with two
-// replicas, Q = N - 2X with X the disagreement count, in one pass.
-template <int D, int R>
+// One temperature (slot = replica): U and B of every replica and, with two
+// replicas, X, in one pass.  Grid (chunks, groups).
+template <int D, int R, bool P2>
 __global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __restrict__ spins,
                                                             const uint64_t* __restrict__ J, int64_t* acc, Geom geom,
                                                             int S) {
+  __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
   const int g = blockIdx.y;
-  const uint32_t N = geom.N, L = (uint32_t)geom.L, h = (uint32_t)geom.h;
+  const uint32_t N = geom.N;
   const uint64_t* Jg = J + (size_t)g * D * N;
   const uint64_t* sg = spins + (size_t)g * R * N;
-  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
-  uint64_t cu[R][kCtr], cb[R][kCtr], cx[kCtr];
+  constexpr int NQ = 2 * R + (R == 2 ? 1 : 0);
+  long long tot[NQ][2];
 #pragma unroll
-  for (int k = 0; k < kCtr; ++k) {
-    cx[k] = 0;
+  for (int q = 0; q < NQ; ++q) tot[q][0] = tot[q][1] = 0;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * kBlock;
+  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
+    const uint32_t j = base + lane;
+    uint64_t bw[R], s1[R], c1[R];
 #pragma unroll
-    for (int a = 0; a < R; ++a) cu[a][k] = cb[a][k] = 0;
-  }
-  for (int it = 0; it < kMeasIters; ++it) {
-    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+    for (int a = 0; a < R; ++a) bw[a] = s1[a] = c1[a] = 0;
     if (j < N) {
-      const uint32_t rc = j / h, k = j - rc * h;
-      const uint32_t row = rc >> 1, c = rc & 1u;
-      const uint32_t y = row % L, z = row / L;
-      const uint32_t x = 2u * k + ((c ^ (y + z)) & 1u);
-      const uint32_t jx = split_index(geom, (int)((x + 1u == L) ? 0u : x + 1u), (int)y, (int)z);
-      const uint32_t jy = split_index(geom, (int)x, (int)((y + 1u == L) ? 0u : y + 1u), (int)z);
-      const uint32_t jz = D == 3 ? split_index(geom, (int)x, (int)y, (int)((z + 1u == L) ? 0u : z + 1u)) : 0u;
+      const Fwd f = split_forward<P2>(geom, j);
       const uint64_t Jx = Jg[j], Jy = Jg[N + j], Jz = D == 3 ? Jg[2u * N + j] : 0ull;
-      uint64_t b[R];
 #pragma unroll
       for (int a = 0; a < R; ++a) {
         const uint64_t* sp = sg + (size_t)a * N;
-        b[a] = sp[j];
-        ctr_add(cu[a], b[a] ^ sp[jx] ^ Jx);
-        ctr_add(cu[a], b[a] ^ sp[jy] ^ Jy);
-        if (D == 3) ctr_add(cu[a], b[a] ^ sp[jz] ^ Jz);
-        ctr_add(cb[a], b[a]);
+        bw[a] = sp[j];
+        bond_count<D>(bw[a], sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jx, Jy, Jz, s1[a], c1[a]);
       }
-      if (R == 2) ctr_add(cx, b[0] ^ b[R - 1]);
     }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      col_add(s1[a], 0, tot[2 * a][0], tot[2 * a][1]);
+      col_add(c1[a], 1, tot[2 * a][0], tot[2 * a][1]);
+      col_add(bw[a], 0, tot[2 * a + 1][0], tot[2 * a + 1][1]);
+    }
+    if (R == 2) col_add(bw[0] ^ bw[R - 1], 0, tot[NQ - 1][0], tot[NQ - 1][1]);
   }
-  const int lane = threadIdx.x & 31;
-  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
-  long long lo, hi;
+  int row_off[NQ], field[NQ];
 #pragma unroll
   for (int a = 0; a < R; ++a) {
-    ctr_flush(cu[a], lo, hi);
-    acc_add(acc, s_lo, S, (size_t)s_lo * R + a, 0, lo);
-    acc_add(acc, s_hi, S, (size_t)s_hi * R + a, 0, hi);
-    ctr_flush(cb[a], lo, hi);
-    acc_add(acc, s_lo, S, (size_t)s_lo * R + a, 1, lo);
-    acc_add(acc, s_hi, S, (size_t)s_hi * R + a, 1, hi);
+    row_off[2 * a] = row_off[2 * a + 1] = a;
+    field[2 * a] = 0;
+    field[2 * a + 1] = 1;
   }
   if (R == 2) {
-    ctr_flush(cx, lo, hi);
-    acc_add(acc, s_lo, S, (size_t)s_lo * R, 6, lo);
-    acc_add(acc, s_hi, S, (size_t)s_hi * R, 6, hi);
+    row_off[NQ - 1] = 0;
+    field[NQ - 1] = 6;
   }
+  block_flush(red, tot, NQ, g, S, acc, row_off, field, R);
 }
 
-// FIELD: also F = N - 2 popcount(b ^ hb) per lane into acc[2] (random-field
-// model, F = sum_i sign(h_i) s_i).
-template <int D, bool FIELD>
+// Any number of temperatures: U, B (and for the random-field model F, the
+// count of lanes with b != h-bit, F = N - 2 that) of one slot.  Grid
+// (chunks, groups x slots).
+template <int D, bool FIELD, bool P2>
 __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restrict__ spins,
                                                          const uint64_t* __restrict__ J,
                                                          const uint64_t* __restrict__ hbits, int64_t* acc,
                                                          Geom geom, int S, int R, int K, int slots) {
+  __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
   const int gt = blockIdx.y;  // g * slots + sigma
   const int g = gt / slots, sigma = gt - g * slots;
-  const uint32_t N = geom.N, L = (uint32_t)geom.L, h = (uint32_t)geom.h;
+  const uint32_t N = geom.N;
   const uint64_t* Jg = J + (size_t)g * D * N;
   const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
-  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
-  const int lane = threadIdx.x & 31;
-  uint64_t cu[kCtr], cb[kCtr], cf[kCtr];
+  constexpr int NQ = FIELD ? 3 : 2;
+  long long tot[NQ][2];
 #pragma unroll
-  for (int k = 0; k < kCtr; ++k) cu[k] = cb[k] = cf[k] = 0;
-  for (int it = 0; it < kMeasIters; ++it) {
-    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+  for (int q = 0; q < NQ; ++q) tot[q][0] = tot[q][1] = 0;
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * kBlock;
+  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
+    const uint32_t j = base + lane;
+    uint64_t bw = 0, s1 = 0, c1 = 0, fw = 0;
     if (j < N) {
-      // split index j -> row, colour, k -> coordinates
-      const uint32_t rc = j / h, k = j - rc * h;
-      const uint32_t row = rc >> 1, c = rc & 1u;
-      const uint32_t y = row % L, z = row / L;
-      const uint32_t x = 2u * k + ((c ^ (y + z)) & 1u);
-      const uint64_t bi = sp[j];
-      const uint32_t xp = (x + 1u == L) ? 0u : x + 1u;
-      const uint32_t yp = (y + 1u == L) ? 0u : y + 1u;
-      ctr_add(cu, bi ^ sp[split_index(geom, (int)xp, (int)y, (int)z)] ^ Jg[j]);
-      ctr_add(cu, bi ^ sp[split_index(geom, (int)x, (int)yp, (int)z)] ^ Jg[N + j]);
-      if (D == 3) {
-        const uint32_t zp = (z + 1u == L) ? 0u : z + 1u;
-        ctr_add(cu, bi ^ sp[split_index(geom, (int)x, (int)y, (int)zp)] ^ Jg[2u * N + j]);
-      }
-      ctr_add(cb, bi);
-      if (FIELD) ctr_add(cf, bi ^ hbits[(size_t)g * N + j]);
+      const Fwd f = split_forward<P2>(geom, j);
+      bw = sp[j];
+      bond_count<D>(bw, sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jg[j], Jg[N + j], D == 3 ? Jg[2u * N + j] : 0ull,
+                    s1, c1);
+      if (FIELD) fw = bw ^ hbits[(size_t)g * N + j];
     }
+    col_add(s1, 0, tot[0][0], tot[0][1]);
+    col_add(c1, 1, tot[0][0], tot[0][1]);
+    col_add(bw, 0, tot[1][0], tot[1][1]);
+    if (FIELD) col_add(fw, 0, tot[2][0], tot[2][1]);
   }
-  long long lo, hi;
-  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
-  ctr_flush(cu, lo, hi);
-  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 0], (unsigned long long)lo);
-  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 0], (unsigned long long)hi);
-  ctr_flush(cb, lo, hi);
-  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 1], (unsigned long long)lo);
-  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 1], (unsigned long long)hi);
-  if (FIELD) {
-    ctr_flush(cf, lo, hi);
-    if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + sigma) * kAccStride + 2], (unsigned long long)lo);
-    if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + sigma) * kAccStride + 2], (unsigned long long)hi);
-  }
+  const int row_off[3] = {sigma, sigma, sigma}, field[3] = {0, 1, 2};
+  block_flush(red, tot, NQ, g, S, acc, row_off, field, slots);
 }
 
 // Overlap at temperature k between replicas 0 and 1 (Sec. 4.1).  After
 // parallel-tempering swaps the configuration holding temperature k differs
 // per sample, so the word of replica a at temperature k is assembled lane by
 // lane: W_a = OR_t (sel[a][t] & spins[t*R + a]), sel[a][t] = lanes whose
-// temperature k sits in slot t.  X = popcount per lane of W_0 ^ W_1,
-// Q = N - 2X, stored in acc[s][k*R][6].
+// temperature k sits in slot t.  X = count per lane of W_0 ^ W_1, Q = N - 2X,
+// stored in acc[s][k*R][6].  Grid (chunks, groups x temperatures).
 __global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restrict__ spins,
                                                          const int32_t* __restrict__ slot_at, int64_t* acc,
                                                          uint32_t N, int S, int R, int K, int slots) {
   extern __shared__ uint64_t sel[];  // [2][K]
+  __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
   const int gk = blockIdx.y;
   const int g = gk / K, k = gk - g * K;
   for (int t = threadIdx.x; t < 2 * K; t += kBlock) {
@@ -653,28 +687,23 @@ __global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restr
   }
   __syncthreads();
   const uint64_t* sg = spins + (size_t)g * slots * N;
-  const uint32_t base = blockIdx.x * (uint32_t)(kBlock * kMeasIters);
-  const int lane = threadIdx.x & 31;
-  uint64_t cx[kCtr];
-#pragma unroll
-  for (int q = 0; q < kCtr; ++q) cx[q] = 0;
-  for (int it = 0; it < kMeasIters; ++it) {
-    const uint32_t j = base + (uint32_t)it * kBlock + threadIdx.x;
+  long long tot[1][2] = {{0, 0}};
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * kBlock;
+  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
+    const uint32_t j = base + lane;
+    uint64_t w0 = 0, w1 = 0;
     if (j < N) {
-      uint64_t w0 = 0, w1 = 0;
       for (int t = 0; t < K; ++t) {
         const uint64_t m0 = sel[t], m1 = sel[K + t];
         if (m0) w0 |= m0 & sg[((size_t)t * R + 0) * N + j];
         if (m1) w1 |= m1 & sg[((size_t)t * R + 1) * N + j];
       }
-      ctr_add(cx, w0 ^ w1);
     }
+    col_add(w0 ^ w1, 0, tot[0][0], tot[0][1]);
   }
-  long long lo, hi;
-  const int s_lo = 64 * g + lane, s_hi = 64 * g + 32 + lane;
-  ctr_flush(cx, lo, hi);
-  if (s_lo < S) atomicAdd((unsigned long long*)&acc[((size_t)s_lo * slots + (size_t)k * R) * kAccStride + 6], (unsigned long long)lo);
-  if (s_hi < S) atomicAdd((unsigned long long*)&acc[((size_t)s_hi * slots + (size_t)k * R) * kAccStride + 6], (unsigned long long)hi);
+  const int row_off[1] = {k * R}, field[1] = {6};
+  block_flush(red, tot, 1, g, S, acc, row_off, field, slots);
 }
 
 // ---- layout conversions (natural int8 <-> bit-sliced split words) ----
@@ -804,11 +833,13 @@ cudaError_t field_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t 
 // loop or per-warp queues entered after phase_a pairs; registers capped so
 // that min_blocks blocks of 256 threads fit on an SM.
 struct JitShape {
-  int mode, phase_a, min_blocks;
+  int mode, phase_a, min_blocks, group;
 };
-constexpr JitShape kJitShapes[] = {{0, 8, 3}, {0, 8, 4}, {1, 4, 3}, {1, 4, 4}, {1, 3, 3}, {1, 5, 3},
-                                   {2, 8, 2}, {2, 8, 3}};
+constexpr JitShape kJitShapes[] = {{0, 8, 3, 1}, {0, 8, 4, 1}, {1, 4, 3, 1}, {1, 4, 4, 1}, {1, 3, 3, 1},
+                                   {1, 5, 3, 1}, {2, 8, 2, 1}, {2, 8, 3, 1}, {0, 8, 3, 2}, {1, 4, 3, 2},
+                                   {1, 6, 3, 2}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
+static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 2;
 
 // The specialised kernel shape the next sweep uses (>= 2), or 1 for the
@@ -830,7 +861,7 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   if (v < 2) return;
   if (lat.jit_algo != algo || lat.jit_variant != v) {
     const JitShape& js = kJitShapes[v - 2];
-    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks);
+    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group);
     lat.jit_algo = algo;
     lat.jit_variant = v;
   }
@@ -971,43 +1002,48 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   return algo ? sweep_dispatch2<2, 1>(lat, p, grid, smem) : sweep_dispatch2<2, 0>(lat, p, grid, smem);
 }
 
+// Blocks along the lattice for a measurement kernel with `ys` blocks across:
+// about two blocks per SM in all, each warp taking 32 words at a time.
+inline unsigned meas_blocks(uint32_t N, unsigned ys) {
+  const unsigned want = (152u * 2u + ys - 1u) / ys;
+  const unsigned most = (N + kBlock - 1) / kBlock;
+  return want < 1u ? 1u : (want > most ? most : want);
+}
+
+template <int D, bool P2>
+cudaError_t measure_dispatch(Lattice& lat, int want_q) {
+  const uint64_t* sp = (const uint64_t*)lat.spins;
+  const uint64_t* J = (const uint64_t*)lat.J;
+  if (lat.K == 1 && (lat.R == 1 || lat.R == 2) && !lat.field) {
+    // one pass for E, M and (R == 2) Q
+    dim3 grid(meas_blocks(lat.N, (unsigned)lat.G), (unsigned)lat.G);
+    if (lat.R == 2)
+      k_measure_bits_k1<D, 2, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
+    else
+      k_measure_bits_k1<D, 1, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
+    return cudaGetLastError();
+  }
+  dim3 grid(meas_blocks(lat.N, (unsigned)(lat.G * lat.slots)), (unsigned)(lat.G * lat.slots));
+  if (lat.field)
+    k_measure_bits<D, true, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S, lat.R,
+                                                                 lat.K, lat.slots);
+  else
+    k_measure_bits<D, false, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S, lat.R,
+                                                                  lat.K, lat.slots);
+  if (want_q && lat.R >= 2) {
+    dim3 gq(meas_blocks(lat.N, (unsigned)(lat.G * lat.K)), (unsigned)(lat.G * lat.K));
+    k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(sp, lat.slot_at, lat.acc, lat.N, lat.S,
+                                                                           lat.R, lat.K, lat.slots);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
   cudaError_t e = cudaMemsetAsync(lat.acc, 0, (size_t)lat.S * lat.slots * kAccStride * sizeof(int64_t), lat.stream);
   if (e != cudaSuccess) return e;
-  const uint32_t per_block = kBlock * kMeasIters;
-  const unsigned nx = (lat.N + per_block - 1) / per_block;
-  if (lat.K == 1 && (lat.R == 1 || lat.R == 2) && !lat.field) {
-    // one pass for E, M and (R == 2) Q; the overlap is computed either way
-    dim3 grid(nx, (unsigned)lat.G);
-    const uint64_t* sp = (const uint64_t*)lat.spins;
-    const uint64_t* J = (const uint64_t*)lat.J;
-    if (lat.D == 3)
-      lat.R == 2 ? k_measure_bits_k1<3, 2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S)
-                 : k_measure_bits_k1<3, 1><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
-    else
-      lat.R == 2 ? k_measure_bits_k1<2, 2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S)
-                 : k_measure_bits_k1<2, 1><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S);
-    return cudaGetLastError();
-  }
-  dim3 grid(nx, (unsigned)(lat.G * lat.slots));
-  const uint64_t* sp = (const uint64_t*)lat.spins;
-  const uint64_t* J = (const uint64_t*)lat.J;
-  if (lat.field)
-    lat.D == 3 ? k_measure_bits<3, true><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S,
-                                                                          lat.R, lat.K, lat.slots)
-               : k_measure_bits<2, true><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S,
-                                                                          lat.R, lat.K, lat.slots);
-  else
-    lat.D == 3 ? k_measure_bits<3, false><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S,
-                                                                           lat.R, lat.K, lat.slots)
-               : k_measure_bits<2, false><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S,
-                                                                           lat.R, lat.K, lat.slots);
-  if (want_q && lat.R >= 2) {
-    dim3 gq(nx, (unsigned)(lat.G * lat.K));
-    k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(
-        (const uint64_t*)lat.spins, lat.slot_at, lat.acc, lat.N, lat.S, lat.R, lat.K, lat.slots);
-  }
-  return cudaGetLastError();
+  const bool p2 = lat.geom.lL > 0;
+  if (lat.D == 3) return p2 ? measure_dispatch<3, true>(lat, want_q) : measure_dispatch<3, false>(lat, want_q);
+  return p2 ? measure_dispatch<2, true>(lat, want_q) : measure_dispatch<2, false>(lat, want_q);
 }
 
 cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out) {

@@ -211,9 +211,9 @@ def test_errors_are_reported_not_raised_in_kernels(ianus):
     lat.synchronize()
 
 
-# ---------------- BASELINE-sized workloads ----------------
+# ---------------- full-size workloads ----------------
 
-def test_cfg0_full_run(ianus):
+def test_L16_single_sample_metropolis_full_run(ianus):
     """3D EA L=16, one sample, Metropolis T=1.1, 1000 sweeps, E and M after
     every sweep: the whole series bit-exact against the oracle."""
     seed = SEED + 0
@@ -230,7 +230,7 @@ def test_cfg0_full_run(ianus):
         assert np.array_equal(lat.spins(), orc.spins())
 
 
-def test_cfg1_full_size_sampled(ianus):
+def test_L64_256x2_heatbath_full_size_sampled(ianus):
     """L=64, 256 samples x 2 replicas, heat bath T=1.0 on the GPU in the bench
     launch configuration; samples 0, 63, 64, 255 checked against the oracle."""
     seed = SEED + 1
@@ -249,7 +249,7 @@ def test_cfg1_full_size_sampled(ianus):
     assert np.array_equal(E_now, E[-1])
 
 
-def test_cfg2_full_size_sampled(ianus):
+def test_L32_pt_32_temperatures_full_size_sampled(ianus):
     """L=32, 32 temperatures in [0.7, 1.6], 64 samples x 2 replicas,
     Metropolis with a device PT swap every 10 sweeps; samples 0 and 37."""
     seed = SEED + 2
@@ -272,7 +272,7 @@ def test_cfg2_full_size_sampled(ianus):
     assert np.array_equal(E[ids], Eo)
 
 
-def test_cfg3_full_size_sampled(ianus):
+def test_potts_L32_128x2_full_size_sampled(ianus):
     """Potts q=4, L=32, 128 samples x 2 replicas, heat bath T=0.8."""
     seed = SEED + 3
     lat = ianus.Lattice(model="potts", dim=3, L=32, n_samples=128, n_replicas=2, seed=seed)
@@ -286,7 +286,7 @@ def test_cfg3_full_size_sampled(ianus):
     assert np.array_equal(E[:, ids], Eo) and np.array_equal(M[:, ids], Mo) and np.array_equal(Q[:, ids], Qo)
 
 
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_every_variant_and_launch_shape_is_bit_exact(ianus, variant):
     """All kernel variants and several launch shapes give the same
     trajectory (L=16: several blocks per (group, slot), ragged last block)."""
