@@ -406,7 +406,15 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       blocks per SM (needs two replicas; otherwise shape 2 is used);
  *   10..12 = shapes 2, 4 and a queue after 6 pairs, with the Philox blocks
  *       of two consecutive plane pairs computed together (two independent
- *       round chains in flight), 3 blocks per SM.
+ *       round chains in flight), 3 blocks per SM;
+ *   13..16 = with 4 blocks per SM, each replica reading its coupling words
+ *       again instead of holding them: the queue after 4 pairs and lockstep,
+ *       each with two and with one Philox chain (13, 14 two; 15 lockstep
+ *       one; 16 queue one);
+ *   17..19 = two Philox chains, the class planes of both replicas computed
+ *       before the first plane loop (all loads of a site in flight at once):
+ *       the queue after 4 pairs with 3 blocks per SM, lockstep with 4 and
+ *       with 3 blocks per SM.
  * If run-time compilation is unavailable, the precompiled kernel runs.
  * EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);

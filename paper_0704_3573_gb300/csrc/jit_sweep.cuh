@@ -44,6 +44,19 @@ constexpr int kUnrolled = kMode == 1 ? kPhaseA : 8;
 #define IANUS_JIT_GROUP 1
 #endif
 constexpr int kGroup = IANUS_JIT_GROUP;
+// IANUS_JIT_JRELOAD 1: each replica reads its coupling words again (L1 hits)
+// instead of keeping the six words of the site live across the plane loop.
+#ifndef IANUS_JIT_JRELOAD
+#define IANUS_JIT_JRELOAD 0
+#endif
+constexpr bool kJReload = IANUS_JIT_JRELOAD != 0;
+// IANUS_JIT_UFIRST 1: the class planes (u2 u1 u0) of every replica of the
+// site are computed before the first plane loop, so that all of the site's
+// loads are in flight together (one L2 round trip per site, not per replica).
+#ifndef IANUS_JIT_UFIRST
+#define IANUS_JIT_UFIRST 0
+#endif
+constexpr bool kUFirst = IANUS_JIT_UFIRST != 0 && kMode != 2;
 
 template <uint32_t LUT>
 __device__ __forceinline__ uint64_t lop3c(uint64_t a, uint64_t b, uint64_t c) {
@@ -272,6 +285,8 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
     uint64_t jw[2 * D];
     if (valid) {
       n = split_neighbours_t<P2>(geom, p.colour, wi);
+    }
+    if (valid && !(kJReload && !kUFirst && !(kMode == 2 && R == 2))) {
       jw[0] = __ldg(Jg + n.self);
       jw[1] = __ldg(Jg + n.xm);
       jw[2] = __ldg(Jg + N + n.self);
@@ -309,14 +324,10 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
       finish(c, n.self, 1u, wa[1]);
       continue;
     }
+    uint64_t uu[R][3];
+    if (kUFirst && valid) {
 #pragma unroll
-    for (int a = 0; a < R; ++a) {
-      Word w;
-      w.und = 0;
-      w.lt = 0;
-      w.u0 = w.u1 = w.u2 = 0;
-      uint32_t c2 = 0;
-      if (valid) {
+      for (int a = 0; a < R; ++a) {
         const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
         const uint64_t b = sp[n.self];
         uint64_t e[2 * D];
@@ -328,7 +339,46 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
           e[4] = b ^ sp[n.zp] ^ jw[4];
           e[5] = b ^ sp[n.zm] ^ jw[5];
         }
+        count_unsat<D>(e, uu[a][0], uu[a][1], uu[a][2]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < R; ++a) {
+      Word w;
+      w.und = 0;
+      w.lt = 0;
+      w.u0 = w.u1 = w.u2 = 0;
+      uint32_t c2 = 0;
+      if (valid && kUFirst) {
+        w.u0 = uu[a][0];
+        w.u1 = uu[a][1];
+        w.u2 = uu[a][2];
+      } else if (valid) {
+        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t b = sp[n.self];
+        uint64_t e[2 * D];
+        if (kJReload) {  // coupling words from L1 again for each replica: none held across the plane loop
+          e[0] = b ^ sp[n.xp] ^ __ldg(Jg + n.self);
+          e[1] = b ^ sp[n.xm] ^ __ldg(Jg + n.xm);
+          e[2] = b ^ sp[n.yp] ^ __ldg(Jg + N + n.self);
+          e[3] = b ^ sp[n.ym] ^ __ldg(Jg + N + n.ym);
+          if (D == 3) {
+            e[4] = b ^ sp[n.zp] ^ __ldg(Jg + 2u * N + n.self);
+            e[5] = b ^ sp[n.zm] ^ __ldg(Jg + 2u * N + n.zm);
+          }
+        } else {
+          e[0] = b ^ sp[n.xp] ^ jw[0];
+          e[1] = b ^ sp[n.xm] ^ jw[1];
+          e[2] = b ^ sp[n.yp] ^ jw[2];
+          e[3] = b ^ sp[n.ym] ^ jw[3];
+          if (D == 3) {
+            e[4] = b ^ sp[n.zp] ^ jw[4];
+            e[5] = b ^ sp[n.zm] ^ jw[5];
+          }
+        }
         count_unsat<D>(e, w.u0, w.u1, w.u2);
+      }
+      if (valid) {
         w.lt = kAlways ? lop3c<kAlways>(w.u2, w.u1, w.u0) : 0ull;
         w.und = lop3c<kNeed>(w.u2, w.u1, w.u0);
         c2 = sigma_c2(c, (uint32_t)a);

@@ -833,11 +833,13 @@ cudaError_t field_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t 
 // loop or per-warp queues entered after phase_a pairs; registers capped so
 // that min_blocks blocks of 256 threads fit on an SM.
 struct JitShape {
-  int mode, phase_a, min_blocks, group;
+  int mode, phase_a, min_blocks, group, jreload, ufirst;
 };
-constexpr JitShape kJitShapes[] = {{0, 8, 3, 1}, {0, 8, 4, 1}, {1, 4, 3, 1}, {1, 4, 4, 1}, {1, 3, 3, 1},
-                                   {1, 5, 3, 1}, {2, 8, 2, 1}, {2, 8, 3, 1}, {0, 8, 3, 2}, {1, 4, 3, 2},
-                                   {1, 6, 3, 2}};
+constexpr JitShape kJitShapes[] = {{0, 8, 3, 1, 0, 0}, {0, 8, 4, 1, 0, 0}, {1, 4, 3, 1, 0, 0}, {1, 4, 4, 1, 0, 0},
+                                   {1, 3, 3, 1, 0, 0}, {1, 5, 3, 1, 0, 0}, {2, 8, 2, 1, 0, 0}, {2, 8, 3, 1, 0, 0},
+                                   {0, 8, 3, 2, 0, 0}, {1, 4, 3, 2, 0, 0}, {1, 6, 3, 2, 0, 0}, {1, 4, 4, 2, 1, 0},
+                                   {0, 8, 4, 2, 1, 0}, {0, 8, 4, 1, 1, 0}, {1, 4, 4, 1, 1, 0}, {1, 4, 3, 2, 0, 1},
+                                   {0, 8, 4, 2, 0, 1}, {0, 8, 3, 2, 0, 1}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 2;
@@ -861,7 +863,7 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   if (v < 2) return;
   if (lat.jit_algo != algo || lat.jit_variant != v) {
     const JitShape& js = kJitShapes[v - 2];
-    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group);
+    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst);
     lat.jit_algo = algo;
     lat.jit_variant = v;
   }

@@ -156,8 +156,9 @@ void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr
 // of dynamic shared memory: one queue of 64 entries (5 x 8 + 3 x 4 bytes) for
 // each of its 8 warps.
 constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
-cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group);
-constexpr int kMaxVariant = 12;  // ianus_set_variant accepts 0..kMaxVariant
+cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group,
+                        int jreload, int ufirst);
+constexpr int kMaxVariant = 19;  // ianus_set_variant accepts 0..kMaxVariant
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)

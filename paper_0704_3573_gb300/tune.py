@@ -16,7 +16,7 @@ import json
 import os
 import tempfile
 
-VARIANTS = (1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12)
+VARIANTS = tuple(range(1, 20))
 BLOCK_WORDS = (0, 256, 512, 1024, 2048)
 
 

@@ -20,18 +20,20 @@ def _nvrtc():
     pytest.skip("NVRTC not available")
 
 
-@pytest.mark.parametrize("D,algo,R,P2,mode,phase,minb,group", [(3, 1, 2, 1, 0, 8, 3, 1), (3, 0, 1, 0, 1, 3, 4, 1),
-                                                              (2, 1, 1, 1, 1, 4, 3, 1), (2, 0, 2, 0, 0, 8, 4, 1),
-                                                              (3, 1, 2, 1, 0, 8, 3, 2), (3, 1, 2, 0, 1, 4, 3, 2),
-                                                              (2, 0, 1, 1, 1, 6, 3, 2)])
-def test_jit_kernel_compiles_for_sm103a(D, algo, R, P2, mode, phase, minb, group):
+@pytest.mark.parametrize("D,algo,R,P2,mode,phase,minb,group,jr,uf", [
+    (3, 1, 2, 1, 0, 8, 3, 1, 0, 0), (3, 0, 1, 0, 1, 3, 4, 1, 0, 0), (2, 1, 1, 1, 1, 4, 3, 1, 0, 0),
+    (2, 0, 2, 0, 0, 8, 4, 1, 0, 0), (3, 1, 2, 1, 0, 8, 3, 2, 0, 0), (3, 1, 2, 0, 1, 4, 3, 2, 0, 0),
+    (2, 0, 1, 1, 1, 6, 3, 2, 0, 0), (3, 1, 2, 1, 1, 4, 4, 2, 1, 0), (3, 0, 2, 0, 0, 8, 4, 1, 1, 0),
+    (2, 1, 1, 1, 1, 4, 4, 1, 1, 0), (3, 1, 2, 1, 1, 4, 3, 2, 0, 1), (3, 0, 2, 0, 0, 8, 4, 2, 0, 1),
+    (2, 1, 1, 0, 0, 8, 3, 2, 0, 1)])
+def test_jit_kernel_compiles_for_sm103a(D, algo, R, P2, mode, phase, minb, group, jr, uf):
     lib = _nvrtc()
     hdrs = [open(os.path.join(CSRC, n), "rb").read() for n in ("common.cuh", "jit_sweep.cuh")]
     luts = ",".join(str((13 * q + 5) & 0x7F) for q in range(32))
     pre = (f"#define IANUS_JIT_D {D}\n#define IANUS_JIT_ALGO {algo}\n#define IANUS_JIT_R {R}\n"
            f"#define IANUS_JIT_P2 {P2}\n#define IANUS_JIT_LUTS {luts}\n#define IANUS_JIT_ALWAYS 0\n"
            f"#define IANUS_JIT_NEED 127\n#define IANUS_JIT_MODE {mode}\n#define IANUS_JIT_PHASEA {phase}\n"
-           f"#define IANUS_JIT_MINB {minb}\n#define IANUS_JIT_GROUP {group}\n#include \"jit_sweep.cuh\"\n").encode()
+           f"#define IANUS_JIT_MINB {minb}\n#define IANUS_JIT_GROUP {group}\n#define IANUS_JIT_JRELOAD {jr}\n#define IANUS_JIT_UFIRST {uf}\n#include \"jit_sweep.cuh\"\n").encode()
     prog = C.c_void_p()
     H = (C.c_char_p * 2)(*hdrs)
     N = (C.c_char_p * 2)(b"common.cuh", b"jit_sweep.cuh")
