@@ -53,8 +53,8 @@ SM_MAX_MHZ = 2070.0
 # kernel from one ncu capture (profiles/ianus_jit_sweep_hb3d_L64_S256x2.md),
 # per (kernel variant, words per block), valid while the kernel source is
 # unchanged (hash of the sources it is compiled from).
-TRAFFIC_BYTES_PER_LAUNCH = {(11, 512): 41978112 + 512}
-TRAFFIC_SOURCE_HASH = "102454f7de00b776"
+TRAFFIC_BYTES_PER_LAUNCH = {(17, 512): 41978112 + 768}
+TRAFFIC_SOURCE_HASH = "47d13ebd670d8587"
 # The kernel variant and launch shape the bench runs by default: the
 # autotuner's pick on this workload (within noise of the other queued and
 # lockstep shapes), fixed so that the profile above describes the timed kernel.
