@@ -487,13 +487,15 @@ def run_other_configs(args):
     sec = timed(lambda: rf.sweep(ianus.HEATBATH, 1 / Tr, 100, 10), reps)
     upd = 256 * 64 ** 3 * 100 * reps
     rate = upd / (sec * 1e9)
-    # per word: e-words 12, adder tree 16, f and 14 (u, f) class masks 16,
-    # "always" 14; per plane 14 class selections + compare 4; per pair Philox
-    # 21 ALU + merge 2; ~3.9 plane pairs per word
-    alu_word = 58 + 3.9 * (2 * 18 + 23)
+    # kernel specialised at run time for the field tables; per word: e-words
+    # 12, adder tree 16, f 2, "always"/"need" tables (u, f) 12, write-back 3;
+    # per plane: threshold bit 3 lop3 x 2 halves + compare 4; per pair Philox
+    # 21 ALU + merge 2; 3.92 plane pairs per word on average
+    alu_word = 45 + 3.92 * (2 * (6 + 4) + 23)
     out["rfim_L64_256_h1.5"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
-        "mode": "bit-sliced, per-lane planes of 16 (u, f) classes, heat bath T=2.0, |h|=1.5, E/M/F every 10 sweeps",
+        "mode": "bit-sliced, field kernel specialised at run time ((u, f) tables as lop3 immediates), heat bath "
+                "T=2.0, |h|=1.5, E/M/F every 10 sweeps",
         "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
                      "peak": peak, "unit": "T ALU-pipe int32 ops/s",
                      "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},

@@ -109,7 +109,7 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_J = take(z.J_bytes);
   z.off_thr = take((size_t)z.K * kMaxClasses * 8 + sizeof(UniformLut));  // class thresholds, then the uniform tables
   z.off_tp = take(layout == IANUS_LAYOUT_BITS64 && !field ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
-  z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 : 0);
+  z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 + sizeof(FieldLut) : 0);  // then the uniform tables
   z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
   z.off_sites = take(z.sites_bytes);
   z.off_wheels = take(z.wheel_bytes);
@@ -178,6 +178,29 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     lat->ulut_ok = false;
     lat->jit = nullptr;
     lat->jit_algo = -1;
+    lat->flut_ok = false;
+    lat->jitf = nullptr;
+    lat->jitf_algo = -1;
+    if (K == 1 && lat->layout == IANUS_LAYOUT_BITS64) {
+      // one temperature: the truth tables of the specialised field kernel,
+      // class (u, f) <- field class (v + 2D) * 2 + f with v = 2D - 2u
+      FieldLut fl{};
+      for (int f = 0; f < 2; ++f)
+        for (int u = 0; u <= 2 * lat->D; ++u) {
+          const uint64_t T = fthr[(size_t)(4 * lat->D - 2 * u) * 2 + f];
+          if (T >= kTwo32) {
+            fl.always[f] |= (uint8_t)(1u << u);
+          } else {
+            fl.need[f] |= (uint8_t)(1u << u);
+            for (int q = 0; q < 32; ++q)
+              if ((T >> (31 - q)) & 1ull) fl.t[f][q] |= (uint8_t)(1u << u);
+          }
+        }
+      lat->flut = fl;
+      CK(cudaMemcpyAsync(lat->fthr + (size_t)K * kFieldClasses, &lat->flut, sizeof(FieldLut), cudaMemcpyHostToDevice,
+                         lat->stream));
+      lat->flut_ok = true;
+    }
   } else if (lat->model == IANUS_EA_PM_J) {
     std::vector<uint64_t> thr((size_t)K * kMaxClasses);
     for (int k = 0; k < K; ++k) class_thresholds(lat->D, algo, beta[k], &thr[(size_t)k * kMaxClasses]);
@@ -470,7 +493,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->algo = -1;
   lat->jit_algo = -1;
   lat->jit_variant = -1;
-  lat->jit_variant = -1;
+  lat->jitf_algo = -1;
   lat->bytes = z.total;
   if (cfg->device_buffer) {
     if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {

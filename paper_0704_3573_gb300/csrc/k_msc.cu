@@ -859,6 +859,13 @@ int jit_variant_for(const Lattice& lat) {
 
 void prepare_sweep_bits(Lattice& lat, int inv) {
   const int algo = inv ? 1 : 0;
+  if (lat.field) {
+    if (lat.flut_ok && lat.variant != 1 && lat.jitf_algo != algo) {
+      lat.jitf = jit_field_kernel(lat, algo, 3);
+      lat.jitf_algo = algo;
+    }
+    return;
+  }
   const int v = jit_variant_for(lat);
   if (v < 2) return;
   if (lat.jit_algo != algo || lat.jit_variant != v) {
@@ -979,6 +986,19 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);
   const int algo = inv ? 1 : 0;
   if (lat.field) {
+    // one temperature: the field kernel specialised at run time for the
+    // lattice's tables (variants 0 (large lattices) and 2..); else per-lane planes
+    const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
+    const bool want_jit = lat.flut_ok && lat.variant != 1 && (lat.variant != 0 || words >= (1ull << 20));
+    if (want_jit) {
+      prepare_sweep_bits(lat, inv);
+      if (lat.jitf) {
+        const uint64_t* hb = lat.hbits;
+        const uint8_t* lut = (const uint8_t*)(lat.fthr + (size_t)lat.K * kFieldClasses);
+        void* args[] = {(void*)&p, (void*)&hb, (void*)&lut};
+        return cudaLaunchKernel((const void*)lat.jitf, grid, dim3(kBlock), args, 0, lat.stream);
+      }
+    }
     p.tp = lat.ftp;
     const size_t fsmem = (size_t)lat.R * kPlanes * kFieldPlaneClasses * sizeof(uint64_t);
     return field_dispatch(lat, p, grid, fsmem, algo);

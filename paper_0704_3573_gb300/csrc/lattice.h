@@ -32,6 +32,14 @@ struct UniformLut {
   uint8_t always, need, pad0, pad1;
 };
 
+// The same for the random-field model, one table set per f = [s_i h_i > 0]
+// (bit u = the class (u, f)); t[f] is laid out as the 64 bytes the field
+// kernel's tail reads.
+struct FieldLut {
+  uint8_t t[2][32];
+  uint8_t always[2], need[2];
+};
+
 // Fused serving: a job occupies the lanes [lane0, lane0 + n) of one 64-lane
 // group of a pool lattice (bit-sliced, one replica, one temperature).  Its
 // lanes draw the random planes of the job's own stream (key from its seed,
@@ -91,6 +99,10 @@ struct Lattice {
   int8_t* hs;           // I8 field: sign of h_i, int8 [S][N]
   int8_t* occ;          // I8 field: x_i in {0, 1}, int8 [S][N]
   uint64_t* hbits;      // BITS64 field: lane bit set where h_i < 0, u64 [G][N]
+  FieldLut flut;        // valid when flut_ok (BITS64 field model, one temperature)
+  bool flut_ok;
+  cudaKernel_t jitf;    // field sweep specialised for flut (null: per-lane planes)
+  int jitf_algo;        // algorithm it was requested for; -1 = not yet
   // Parisi-Rapuano wheels (IANUS_RNG_WHEEL, I8 only): ring of 64 words per
   // (slot, sample, colour, row), I(k) at ring index k mod 64;
   // u32 [slots * S][2][64][rows], rows = N / L
@@ -159,6 +171,9 @@ constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
 cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group,
                         int jreload, int ufirst);
 constexpr int kMaxVariant = 19;  // ianus_set_variant accepts 0..kMaxVariant
+// Run-time specialised random-field sweep for lat.flut (jit.cu; null when
+// unavailable).
+cudaKernel_t jit_field_kernel(const Lattice& lat, int algo, int min_blocks);
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)

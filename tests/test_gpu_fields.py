@@ -23,14 +23,21 @@ SEED = 0x0704357300000F00
 
 def _pair(ianus, disorder, dim=3, L=4, S=1, R=1, K=1, h=0.75, occ=0.7, layout="auto", seed=SEED):
     name = "rfim" if disorder == DIS_RFIM else "daff"
+    variant = 0
+    if layout == "bits64-jit":  # the field kernel specialised at run time for the tables
+        layout, variant = "bits64", 2
+    elif layout == "bits64":  # per-lane threshold planes
+        variant = 1
     lat = ianus.Lattice(dim=dim, L=L, n_samples=S, n_replicas=R, n_temps=K, seed=seed, layout=layout,
                         disorder=name, field=h, occupation=occ, series_capacity=4096)
+    if variant:
+        lat.set_variant(variant)
     orc = Oracle(dim=dim, L=L, sample_ids=list(range(S)), n_replicas=R, n_temps=K, seed=seed, disorder=disorder,
                  field=h, occupation=occ)
     return lat, orc
 
 
-LAYOUTS = [(DIS_RFIM, "i8"), (DIS_RFIM, "bits64"), (DIS_DAFF, "i8")]
+LAYOUTS = [(DIS_RFIM, "i8"), (DIS_RFIM, "bits64"), (DIS_RFIM, "bits64-jit"), (DIS_DAFF, "i8")]
 
 
 @pytest.mark.parametrize("disorder,layout", LAYOUTS)
@@ -216,7 +223,7 @@ def test_rfim_full_size_sampled(ianus):
     L, S, R, h, beta = 64, 256, 2, 2.0, 1 / 2.5
     lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 77, layout="bits64", disorder="rfim",
                         field=h)
-    lat.sweep(HEATBATH, beta, 20)
+    lat.sweep(HEATBATH, beta, 20)  # 2^21 site words: the specialised field kernel
     ids = [0, 1, 63, 64, 127, 128, 200, 255, 17, 99, 150, 230]
     orc = Oracle(dim=3, L=L, sample_ids=ids, n_replicas=R, seed=SEED + 77, disorder=DIS_RFIM, field=h)
     orc.sweep(HEATBATH, beta, 20, nthreads=8)

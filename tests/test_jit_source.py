@@ -49,3 +49,27 @@ def test_jit_kernel_compiles_for_sm103a(D, algo, R, P2, mode, phase, minb, group
     lib.nvrtcDestroyProgram(C.byref(prog))
     assert rc == 0, log.value.decode()
     assert size.value > 1000
+
+
+@pytest.mark.parametrize("D,algo,R,P2", [(3, 1, 1, 1), (3, 0, 2, 0), (2, 1, 2, 1)])
+def test_jit_field_kernel_compiles_for_sm103a(D, algo, R, P2):
+    lib = _nvrtc()
+    hdrs = [open(os.path.join(CSRC, n), "rb").read() for n in ("common.cuh", "jit_field.cuh")]
+    l0 = ",".join(str((13 * q + 5) & 0x7F) for q in range(32))
+    l1 = ",".join(str((7 * q + 3) & 0x7F) for q in range(32))
+    pre = (f"#define IANUS_JIT_D {D}\n#define IANUS_JIT_ALGO {algo}\n#define IANUS_JIT_R {R}\n"
+           f"#define IANUS_JIT_P2 {P2}\n#define IANUS_JIT_MINB 3\n#define IANUS_JIT_LUT0 {l0}\n"
+           f"#define IANUS_JIT_LUT1 {l1}\n#define IANUS_JIT_ALWAYS0 0\n#define IANUS_JIT_ALWAYS1 64\n"
+           f"#define IANUS_JIT_NEED0 127\n#define IANUS_JIT_NEED1 63\n#include \"jit_field.cuh\"\n").encode()
+    prog = C.c_void_p()
+    H = (C.c_char_p * 2)(*hdrs)
+    N = (C.c_char_p * 2)(b"common.cuh", b"jit_field.cuh")
+    assert lib.nvrtcCreateProgram(C.byref(prog), pre, b"ianus_jit.cu", 2, H, N) == 0
+    opts = (C.c_char_p * 2)(b"--gpu-architecture=sm_103a", b"-std=c++17")
+    rc = lib.nvrtcCompileProgram(prog, 2, opts)
+    n = C.c_size_t()
+    lib.nvrtcGetProgramLogSize(prog, C.byref(n))
+    log = C.create_string_buffer(n.value)
+    lib.nvrtcGetProgramLog(prog, log)
+    lib.nvrtcDestroyProgram(C.byref(prog))
+    assert rc == 0, log.value.decode()
