@@ -23,6 +23,7 @@ struct Sizes {
   int model, D, L, S, R, K, slots, layout, G, Q4, mq;
   uint32_t N, cap, pt_cap;
   bool field;
+  int fpc;
   uint32_t rows;
   size_t off_wheels, wheel_bytes;
   bool poolable;
@@ -60,15 +61,16 @@ int plan(const ianus_config* c, Sizes& z) {
   const bool potts = c->model != IANUS_EA_PM_J;
   if (layout == IANUS_LAYOUT_AUTO)
     layout = potts ? IANUS_LAYOUT_U8X4
-             : (c->disorder == IANUS_DISORDER_DAFF || c->rng == IANUS_RNG_WHEEL) ? IANUS_LAYOUT_I8
-                                                                             : IANUS_LAYOUT_BITS64;
+             : c->rng == IANUS_RNG_WHEEL ? IANUS_LAYOUT_I8
+                                         : IANUS_LAYOUT_BITS64;
   if (layout < IANUS_LAYOUT_I8 || layout > IANUS_LAYOUT_U8X4) return IANUS_EINVAL;
   if (!potts && layout == IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (potts && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
-  if (c->disorder == IANUS_DISORDER_DAFF && layout == IANUS_LAYOUT_BITS64) return IANUS_EUNSUPPORTED;
   if (c->rng == IANUS_RNG_WHEEL && (potts || layout != IANUS_LAYOUT_I8)) return IANUS_EUNSUPPORTED;
   if (layout == IANUS_LAYOUT_BITS64 &&  // the sweep stages one block's threshold planes in shared memory
-      (size_t)c->n_replicas * kPlanes * (field ? kFieldPlaneClasses : kMaxClasses) * 8 > kMaxSmemPerBlock)
+      (size_t)c->n_replicas * kPlanes *
+              (!field ? kMaxClasses : c->disorder == IANUS_DISORDER_DAFF ? kDiluteClasses : kFieldPlaneClasses) * 8 >
+          kMaxSmemPerBlock)
     return IANUS_EUNSUPPORTED;
   z.model = c->model;
   z.D = c->dim;
@@ -95,7 +97,9 @@ int plan(const ianus_config* c, Sizes& z) {
     z.spins_bytes = (size_t)z.slots * z.Q4 * N * 4;
     z.J_bytes = (size_t)z.Q4 * z.D * N * 4;
   }
-  z.sites_bytes = !field ? 0 : layout == IANUS_LAYOUT_I8 ? (size_t)2 * z.S * N : (size_t)z.G * N * 8;
+  // I8: hs, occ int8 [S][N]; BITS64: hbits, xbits u64 [G][N]
+  z.sites_bytes = !field ? 0 : layout == IANUS_LAYOUT_I8 ? (size_t)2 * z.S * N : (size_t)2 * z.G * N * 8;
+  z.fpc = c->disorder == IANUS_DISORDER_DAFF ? kDiluteClasses : kFieldPlaneClasses;
   z.rows = (uint32_t)(N / (uint64_t)c->L);
   z.wheel_bytes = c->rng == IANUS_RNG_WHEEL ? (size_t)z.slots * z.S * 2 * 64 * z.rows * 4 : 0;
   const size_t SKR = (size_t)z.S * z.K * z.R;
@@ -110,7 +114,7 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_thr = take((size_t)z.K * kMaxClasses * 8 + sizeof(UniformLut));  // class thresholds, then the uniform tables
   z.off_tp = take(layout == IANUS_LAYOUT_BITS64 && !field ? (size_t)z.G * z.slots * kPlanes * kMaxClasses * 8 : 0);
   z.off_fthr = take(field ? (size_t)z.K * kFieldClasses * 8 + sizeof(FieldLut) : 0);  // then the uniform tables
-  z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * kFieldPlaneClasses * 8 : 0);
+  z.off_ftp = take(field && layout == IANUS_LAYOUT_BITS64 ? (size_t)z.G * z.slots * kPlanes * z.fpc * 8 : 0);
   z.off_sites = take(z.sites_bytes);
   z.off_wheels = take(z.wheel_bytes);
   // segment tables for fused serving: bit-sliced EA lattices with one replica
@@ -182,18 +186,22 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     lat->jitf = nullptr;
     lat->jitf_algo = -1;
     if (K == 1 && lat->layout == IANUS_LAYOUT_BITS64) {
-      // one temperature: the truth tables of the specialised field kernel,
-      // class (u, f) <- field class (v + 2D) * 2 + f with v = 2D - 2u
+      // one temperature: the truth tables of the specialised field kernel.
+      // Without dilution the class is (u, f), field class (v + 2D) * 2 + f
+      // with v = 2D - 2u, tables [f][0] bit u.  With dilution it is (t, f),
+      // t = v + 2D = 8 t3 + k, tables [f][t3] bit k.
       FieldLut fl{};
       for (int f = 0; f < 2; ++f)
-        for (int u = 0; u <= 2 * lat->D; ++u) {
-          const uint64_t T = fthr[(size_t)(4 * lat->D - 2 * u) * 2 + f];
+        for (int cls = 0; cls <= (lat->dilute ? 4 * lat->D : 2 * lat->D); ++cls) {
+          const int t = lat->dilute ? cls : 4 * lat->D - 2 * cls;
+          const int hi = lat->dilute ? (cls >> 3) : 0, bit = lat->dilute ? (cls & 7) : cls;
+          const uint64_t T = fthr[(size_t)t * 2 + f];
           if (T >= kTwo32) {
-            fl.always[f] |= (uint8_t)(1u << u);
+            fl.always[f][hi] |= (uint8_t)(1u << bit);
           } else {
-            fl.need[f] |= (uint8_t)(1u << u);
+            fl.need[f][hi] |= (uint8_t)(1u << bit);
             for (int q = 0; q < 32; ++q)
-              if ((T >> (31 - q)) & 1ull) fl.t[f][q] |= (uint8_t)(1u << u);
+              if ((T >> (31 - q)) & 1ull) fl.t[f][hi][q] |= (uint8_t)(1u << bit);
           }
         }
       lat->flut = fl;
@@ -523,6 +531,9 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->hs = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) : nullptr;
   lat->occ = z.field && z.layout == IANUS_LAYOUT_I8 ? (int8_t*)(b + z.off_sites) + (size_t)z.S * z.N : nullptr;
   lat->hbits = z.field && z.layout == IANUS_LAYOUT_BITS64 ? (uint64_t*)(b + z.off_sites) : nullptr;
+  lat->xbits = lat->hbits ? lat->hbits + (size_t)z.G * z.N : nullptr;
+  lat->dilute = z.field && z.layout == IANUS_LAYOUT_BITS64 && cfg->disorder == IANUS_DISORDER_DAFF;
+  lat->fpc = z.fpc;
   lat->wheels = z.wheel_bytes ? (uint32_t*)(b + z.off_wheels) : nullptr;
   lat->segs = z.poolable ? (Segment*)(b + z.off_segs) : nullptr;
   lat->nseg = z.poolable ? (uint32_t*)(b + z.off_nseg) : nullptr;
@@ -583,7 +594,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   else
     e = launch_init_potts(*lat, jmode);
   if (e == cudaSuccess && lat->field)
-    e = lat->layout == IANUS_LAYOUT_I8 ? launch_init_sites_i8(*lat, cfg->occupation) : launch_init_sites_bits(*lat);
+    e = lat->layout == IANUS_LAYOUT_I8 ? launch_init_sites_i8(*lat, cfg->occupation)
+                                       : launch_init_sites_bits(*lat, cfg->occupation);
   if (e == cudaSuccess && lat->wheels) e = launch_init_wheels(*lat);
   if (e != cudaSuccess || cudaStreamSynchronize(lat->stream) != cudaSuccess) return bail(IANUS_ECUDA);
   *out = reinterpret_cast<ianus_lattice*>(lat);
@@ -798,7 +810,17 @@ ianus_status ianus_get_sites_i8(ianus_lattice* h, int8_t* hsign, int8_t* occupie
     cudaFree(d);
     st = e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
   } else {
-    st = staged_get(lat, hs.data(), n, launch_get_sites_bits);
+    int8_t* d = nullptr;
+    if (cudaMalloc(&d, 2 * n) != cudaSuccess) {
+      cudaGetLastError();
+      return IANUS_ENOMEM;
+    }
+    cudaError_t e = launch_get_sites_bits(*lat, d, d + n);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs.data(), d, n, cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(occ.data(), d + n, n, cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
+    cudaFree(d);
+    st = e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);
   }
   if (st) return st;
   if (hsign) std::memcpy(hsign, hs.data(), n);
@@ -814,21 +836,20 @@ ianus_status ianus_set_sites_i8(ianus_lattice* h, const int8_t* hsign, const int
     if (hsign[i] != 1 && hsign[i] != -1) return IANUS_EINVAL;
   for (size_t i = 0; occupied && i < n; ++i)
     if (occupied[i] != 0 && occupied[i] != 1) return IANUS_EINVAL;
-  if (lat->layout == IANUS_LAYOUT_BITS64) {
+  if (lat->layout == IANUS_LAYOUT_BITS64 && !lat->dilute) {  // the random-field model has no empty sites
     for (size_t i = 0; occupied && i < n; ++i)
       if (occupied[i] != 1) return IANUS_EUNSUPPORTED;
-    if (!hsign) return IANUS_OK;
-    return staged_set(lat, hsign, n, launch_set_sites_bits);
   }
+  const bool bits = lat->layout == IANUS_LAYOUT_BITS64;
   int8_t* d = nullptr;
   if (cudaMalloc(&d, 2 * n) != cudaSuccess) {
     cudaGetLastError();
     return IANUS_ENOMEM;
   }
-  cudaError_t e = launch_get_sites_i8(*lat, d, d + n);  // keep what is not given
+  cudaError_t e = bits ? launch_get_sites_bits(*lat, d, d + n) : launch_get_sites_i8(*lat, d, d + n);  // keep the rest
   if (e == cudaSuccess && hsign) e = cudaMemcpyAsync(d, hsign, n, cudaMemcpyHostToDevice, lat->stream);
   if (e == cudaSuccess && occupied) e = cudaMemcpyAsync(d + n, occupied, n, cudaMemcpyHostToDevice, lat->stream);
-  if (e == cudaSuccess) e = launch_set_sites_i8(*lat, d, d + n);
+  if (e == cudaSuccess) e = bits ? launch_set_sites_bits(*lat, d, d + n) : launch_set_sites_i8(*lat, d, d + n);
   if (e == cudaSuccess) e = cudaStreamSynchronize(lat->stream);
   cudaFree(d);
   return e == cudaSuccess ? IANUS_OK : (ianus_status)fail(lat, IANUS_ECUDA);

@@ -18,6 +18,7 @@
 // TP[u][p] are 64-bit lane masks, so every lane can carry its own threshold
 // (parallel tempering moves temperatures per sample).
 #include <algorithm>
+#include <cmath>
 
 #include "lattice.h"
 
@@ -204,21 +205,155 @@ __global__ void __launch_bounds__(kBlock) k_sweep_bits_field(const BitsParams p,
   }
 }
 
-// Field signs of the random-field model: lane bit l of word (g, i) is set
-// where h_i of sample 64 g + l is negative (the H stream).
-__global__ void k_init_sites_bits(uint64_t* hbits, Geom geom, int G, PhiloxKeys keys) {
+// Diluted model (DAFF; Eq. 2 with x_i in {0,1}), generic per-lane planes.
+// Per neighbour j the bond contributes c_j = x_j (1 - 2 e_j) to v (e_j the
+// unsatisfied bit); c_j + 1 in {0, 1, 2} is 2 hi_j + lo_j with hi_j = x_j &
+// ~e_j and lo_j = ~x_j, so t = v + 2D = 2 sum(hi) + sum(lo), 4 bit-planes.
+// The plane class is 16 f + t.  Empty sites are never updated.
+template <int D, int ALGO, bool P2>
+__global__ void __launch_bounds__(kBlock) k_sweep_bits_dilute(const BitsParams p, const uint64_t* __restrict__ hbits,
+                                                              const uint64_t* __restrict__ xbits) {
+  constexpr int NF = kDiluteClasses;
+  constexpr int NT = 4 * D + 1;  // t = 0..4D
+  extern __shared__ uint64_t sm_tp[];  // [R][kPlanes][NF]
+  const int R = p.R;
+  const int gt = blockIdx.y;
+  const int g = gt / p.K, tslot = gt - g * p.K;
+  {
+    const uint64_t* src = p.tp + ((size_t)g * p.slots + (size_t)tslot * R) * kPlanes * NF;
+    for (int k = threadIdx.x; k < R * kPlanes * NF; k += kBlock) sm_tp[k] = src[k];
+  }
+  __syncthreads();
+  const Geom geom = p.geom;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = p.J + (size_t)g * D * N;
+  const uint64_t* Hg = hbits + (size_t)g * N;
+  const uint64_t* Xg = xbits + (size_t)g * N;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  for (uint32_t w = w_begin + threadIdx.x; w < w_end; w += kBlock) {
+    const Nbr n = split_neighbours_t<P2>(geom, p.colour, w);
+    uint64_t jw[2 * D], xw[2 * D];
+    jw[0] = __ldg(Jg + n.self);
+    jw[1] = __ldg(Jg + n.xm);
+    jw[2] = __ldg(Jg + N + n.self);
+    jw[3] = __ldg(Jg + N + n.ym);
+    xw[0] = __ldg(Xg + n.xp);
+    xw[1] = __ldg(Xg + n.xm);
+    xw[2] = __ldg(Xg + n.yp);
+    xw[3] = __ldg(Xg + n.ym);
+    if (D == 3) {
+      jw[4] = __ldg(Jg + 2u * N + n.self);
+      jw[5] = __ldg(Jg + 2u * N + n.zm);
+      xw[4] = __ldg(Xg + n.zp);
+      xw[5] = __ldg(Xg + n.zm);
+    }
+    const uint64_t hb = __ldg(Hg + n.self), xs = __ldg(Xg + n.self);
+    uint64_t lo[2 * D];
+#pragma unroll
+    for (int j = 0; j < 2 * D; ++j) lo[j] = ~xw[j];
+    uint64_t l0, l1, l2;
+    count_unsat<D>(lo, l0, l1, l2);  // sum of lo_j
+#pragma unroll 1
+    for (int a = 0; a < R; ++a) {
+      const int sigma = tslot * R + a;
+      uint64_t* sp = p.spins + ((size_t)g * p.slots + sigma) * N;
+      const uint64_t b = sp[n.self];
+      uint64_t hi[2 * D];
+      hi[0] = xw[0] & ~(b ^ sp[n.xp] ^ jw[0]);
+      hi[1] = xw[1] & ~(b ^ sp[n.xm] ^ jw[1]);
+      hi[2] = xw[2] & ~(b ^ sp[n.yp] ^ jw[2]);
+      hi[3] = xw[3] & ~(b ^ sp[n.ym] ^ jw[3]);
+      if (D == 3) {
+        hi[4] = xw[4] & ~(b ^ sp[n.zp] ^ jw[4]);
+        hi[5] = xw[5] & ~(b ^ sp[n.zm] ^ jw[5]);
+      }
+      uint64_t h0, h1, h2;
+      count_unsat<D>(hi, h0, h1, h2);
+      // t = 2 (h2 h1 h0) + (l2 l1 l0) <= 4D < 16
+      const uint64_t t0 = l0, t1 = h0 ^ l1, k1 = h0 & l1;
+      const uint64_t t2 = h1 ^ l2 ^ k1, k2 = (h1 & l2) | (h1 & k1) | (l2 & k1);
+      const uint64_t t3 = h2 ^ k2;
+      const uint64_t f = ~(b ^ hb);
+      uint64_t mc[2][NT];
+#pragma unroll
+      for (int t = 0; t < NT; ++t) {
+        const uint64_t m = ((t & 8) ? t3 : ~t3) & ((t & 4) ? t2 : ~t2) & ((t & 2) ? t1 : ~t1) & ((t & 1) ? t0 : ~t0);
+        mc[0][t] = m & ~f;
+        mc[1][t] = m & f;
+      }
+      const uint64_t* tpa = sm_tp + (size_t)a * kPlanes * NF;
+      uint64_t always = 0;
+#pragma unroll
+      for (int t = 0; t < NT; ++t) always |= (mc[0][t] & tpa[32 * NF + t]) | (mc[1][t] & tpa[32 * NF + 16 + t]);
+      always &= xs;
+      uint64_t lt = always;
+      uint64_t und = ~always & xs;
+      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | (uint32_t)g;
+#pragma unroll 1
+      for (uint32_t mm = 0; mm < 16u && und != 0ull; ++mm) {
+        const uint4 x = philox10(n.site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const uint64_t r = q == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
+                                    : ((uint64_t)x.z | ((uint64_t)x.w << 32));
+          const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * NF;
+          uint64_t tb = 0;
+#pragma unroll
+          for (int t = 0; t < NT; ++t) tb |= (mc[0][t] & row[t]) | (mc[1][t] & row[16 + t]);
+          lt |= und & ~r & tb;
+          und &= ~(r ^ tb);
+        }
+      }
+      const uint64_t flip = ((ALGO == 0) ? lt : ~lt) & xs;
+      if (flip) sp[n.self] = b ^ flip;
+    }
+  }
+}
+
+// Site disorder of the bit-sliced field models, lane bit l of word (g, i)
+// for sample 64 g + l: hbits = [h_i < 0] (RFIM: the H stream; DAFF: 0),
+// xbits = [x_i = 1] (RFIM: all; DAFF: r_x < T_occ, r_x from the 32 planes of
+// the X stream compared from the most significant plane down).
+__global__ void k_init_sites_bits(uint64_t* hbits, uint64_t* xbits, Geom geom, int G, int rfim, int daff,
+                                  uint64_t T_occ, PhiloxKeys keys) {
   const uint64_t total = (uint64_t)G * geom.N;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const uint32_t g = (uint32_t)(idx / geom.N), i = (uint32_t)(idx - (uint64_t)g * geom.N);
     const uint32_t L = (uint32_t)geom.L;
     const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
-    const uint4 r = philox10(i, 0u, (TAG_H << 28) | g, 0u, keys);
-    hbits[(size_t)g * geom.N + split_index(geom, x, y, z)] = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    const size_t j = (size_t)g * geom.N + split_index(geom, x, y, z);
+    uint64_t hw = 0, xw = ~0ull;
+    if (rfim) {
+      const uint4 r = philox10(i, 0u, (TAG_H << 28) | g, 0u, keys);
+      hw = (uint64_t)r.x | ((uint64_t)r.y << 32);
+    }
+    if (daff) {
+      if (T_occ >= kTwo32) {
+        xw = ~0ull;
+      } else {
+        uint64_t lt = 0, und = ~0ull;
+        for (uint32_t m = 0; m < 16u && und != 0ull; ++m) {
+          const uint4 r = philox10(i, 0u, (TAG_X << 28) | (m << 24) | g, 0u, keys);
+          for (int q = 0; q < 2; ++q) {
+            const uint64_t w = q == 0 ? ((uint64_t)r.x | ((uint64_t)r.y << 32)) : ((uint64_t)r.z | ((uint64_t)r.w << 32));
+            const uint64_t tb = ((T_occ >> (31u - (2u * m + (uint32_t)q))) & 1ull) ? ~0ull : 0ull;
+            lt |= und & ~w & tb;
+            und &= ~(w ^ tb);
+          }
+        }
+        xw = lt;
+      }
+    }
+    hbits[j] = hw;
+    xbits[j] = xw;
   }
 }
 
-__global__ void k_get_sites_bits(const uint64_t* hbits, int8_t* out, Geom geom, int S) {
+__global__ void k_get_sites_bits(const uint64_t* hbits, const uint64_t* xbits, int8_t* out_hs, int8_t* out_occ,
+                                 Geom geom, int S) {
   const uint64_t total = (uint64_t)S * geom.N;
   const uint32_t L = (uint32_t)geom.L;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -226,12 +361,14 @@ __global__ void k_get_sites_bits(const uint64_t* hbits, int8_t* out, Geom geom, 
     const uint32_t i = (uint32_t)(idx % geom.N);
     const int s = (int)(idx / geom.N);
     const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
-    const uint64_t w = hbits[(size_t)(s >> 6) * geom.N + split_index(geom, x, y, z)];
-    out[idx] = ((w >> (s & 63)) & 1ull) ? -1 : 1;
+    const size_t j = (size_t)(s >> 6) * geom.N + split_index(geom, x, y, z);
+    out_hs[idx] = ((hbits[j] >> (s & 63)) & 1ull) ? -1 : 1;
+    out_occ[idx] = (int8_t)((xbits[j] >> (s & 63)) & 1ull);
   }
 }
 
-__global__ void k_set_sites_bits(uint64_t* hbits, const int8_t* in, Geom geom, int S, int G) {
+__global__ void k_set_sites_bits(uint64_t* hbits, uint64_t* xbits, const int8_t* in_hs, const int8_t* in_occ,
+                                 Geom geom, int S, int G) {
   const uint64_t total = (uint64_t)G * geom.N;
   const uint32_t L = (uint32_t)geom.L;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -239,15 +376,18 @@ __global__ void k_set_sites_bits(uint64_t* hbits, const int8_t* in, Geom geom, i
     const uint32_t i = (uint32_t)(idx % geom.N);
     const int g = (int)(idx / geom.N);
     const int x = (int)(i % L), y = (int)((i / L) % L), z = geom.D == 3 ? (int)(i / (L * L)) : 0;
-    uint64_t* wp = &hbits[(size_t)g * geom.N + split_index(geom, x, y, z)];
-    uint64_t w = *wp;
+    const size_t j = (size_t)g * geom.N + split_index(geom, x, y, z);
+    uint64_t hw = hbits[j], xw = xbits[j];
     for (int l = 0; l < 64; ++l) {
       const int s = 64 * g + l;
       if (s >= S) break;
-      const uint64_t bit = in[(size_t)s * geom.N + i] < 0 ? 1ull : 0ull;
-      w = (w & ~(1ull << l)) | (bit << l);
+      const uint64_t hbit = in_hs[(size_t)s * geom.N + i] < 0 ? 1ull : 0ull;
+      const uint64_t xbit = in_occ[(size_t)s * geom.N + i] ? 1ull : 0ull;
+      hw = (hw & ~(1ull << l)) | (hbit << l);
+      xw = (xw & ~(1ull << l)) | (xbit << l);
     }
-    *wp = w;
+    hbits[j] = hw;
+    xbits[j] = xw;
   }
 }
 
@@ -437,19 +577,21 @@ __global__ void k_build_planes(uint64_t* tp, const uint64_t* thr, const int32_t*
 
 // Field planes: FTP[g][sigma][p][8 f + u] from the per-temperature field
 // thresholds fthr[k][(v + 2D) * 2 + f], v = 2D - 2u; classes u > 2D stay 0.
+// With dilution (NF = kDiluteClasses) the class is 16 f + t, field class
+// t * 2 + f; classes t > 4D stay 0.
 __global__ void k_build_field_planes(uint64_t* ftp, const uint64_t* fthr, const int32_t* temp_of, int D, int G,
-                                     int S, int R, int K, int slots) {
-  constexpr int NF = kFieldPlaneClasses;
+                                     int S, int R, int K, int slots, int NF) {
   const int total = G * slots * NF;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
     const int c = idx % NF, rest = idx / NF;
     const int sigma = rest % slots, g = rest / slots;
     const int tslot = sigma / R, a = sigma - tslot * R;
-    const int u = c & 7, f = c >> 3;
+    const bool dil = NF == kDiluteClasses;
+    const int u = dil ? (c & 15) : (c & 7), f = dil ? (c >> 4) : (c >> 3);
     uint64_t planes[kPlanes];
     for (int q = 0; q < kPlanes; ++q) planes[q] = 0;
-    if (u <= 2 * D) {
-      const int cls = (4 * D - 2 * u) * 2 + f;
+    if (dil ? u <= 4 * D : u <= 2 * D) {
+      const int cls = (dil ? u : 4 * D - 2 * u) * 2 + f;
       for (int l = 0; l < 64; ++l) {
         const int s = 64 * g + l;
         const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
@@ -623,43 +765,97 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __re
   block_flush(red, tot, NQ, g, S, acc, row_off, field, R);
 }
 
-// Any number of temperatures: U, B (and for the random-field model F, the
-// count of lanes with b != h-bit, F = N - 2 that) of one slot.  Grid
-// (chunks, groups x slots).
-template <int D, bool FIELD, bool P2>
+// Any number of temperatures: U and B of one slot.  Grid (chunks, groups x
+// slots).
+template <int D, bool P2>
 __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restrict__ spins,
-                                                         const uint64_t* __restrict__ J,
-                                                         const uint64_t* __restrict__ hbits, int64_t* acc,
-                                                         Geom geom, int S, int R, int K, int slots) {
+                                                         const uint64_t* __restrict__ J, int64_t* acc, Geom geom,
+                                                         int S, int R, int K, int slots) {
   __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
   const int gt = blockIdx.y;  // g * slots + sigma
   const int g = gt / slots, sigma = gt - g * slots;
   const uint32_t N = geom.N;
   const uint64_t* Jg = J + (size_t)g * D * N;
   const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
-  constexpr int NQ = FIELD ? 3 : 2;
-  long long tot[NQ][2];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) tot[q][0] = tot[q][1] = 0;
+  long long tot[2][2] = {{0, 0}, {0, 0}};
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * kBlock;
   for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
     const uint32_t j = base + lane;
-    uint64_t bw = 0, s1 = 0, c1 = 0, fw = 0;
+    uint64_t bw = 0, s1 = 0, c1 = 0;
     if (j < N) {
       const Fwd f = split_forward<P2>(geom, j);
       bw = sp[j];
       bond_count<D>(bw, sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jg[j], Jg[N + j], D == 3 ? Jg[2u * N + j] : 0ull,
                     s1, c1);
-      if (FIELD) fw = bw ^ hbits[(size_t)g * N + j];
     }
     col_add(s1, 0, tot[0][0], tot[0][1]);
     col_add(c1, 1, tot[0][0], tot[0][1]);
     col_add(bw, 0, tot[1][0], tot[1][1]);
-    if (FIELD) col_add(fw, 0, tot[2][0], tot[2][1]);
+  }
+  const int row_off[2] = {sigma, sigma}, field[2] = {0, 1};
+  block_flush(red, tot, 2, g, S, acc, row_off, field, slots);
+}
+
+// Field models (RFIM, DAFF) of one slot, values rather than counts:
+// E_J = sum over forward bonds with both ends occupied of (2 e - 1), as
+// 2 U - O with U, O the per-site counts of occupied unsatisfied and occupied
+// bonds (each a 2-bit sum); M = sum x s = X - 2 sum x b and F = sum sign(h)
+// x s = X - 2 sum x (b ^ hb), X = sum x.  acc[0..2] = E_J, M, F.
+__device__ __forceinline__ void col_signed(uint64_t w, int shift, long long sign, long long& lo, long long& hi) {
+  lo += sign * ((long long)__popc(warp_transpose32((uint32_t)w)) << shift);
+  hi += sign * ((long long)__popc(warp_transpose32((uint32_t)(w >> 32))) << shift);
+}
+
+template <int D, bool P2>
+__global__ void __launch_bounds__(kBlock) k_measure_field_bits(const uint64_t* __restrict__ spins,
+                                                               const uint64_t* __restrict__ J,
+                                                               const uint64_t* __restrict__ hbits,
+                                                               const uint64_t* __restrict__ xbits, int64_t* acc,
+                                                               Geom geom, int S, int slots) {
+  __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
+  const int gt = blockIdx.y;  // g * slots + sigma
+  const int g = gt / slots, sigma = gt - g * slots;
+  const uint32_t N = geom.N;
+  const uint64_t* Jg = J + (size_t)g * D * N;
+  const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
+  const uint64_t* Hg = hbits + (size_t)g * N;
+  const uint64_t* Xg = xbits + (size_t)g * N;
+  long long tot[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t stride = gridDim.x * kBlock;
+  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
+    const uint32_t j = base + lane;
+    uint64_t s1 = 0, c1 = 0, s2 = 0, c2 = 0, xs = 0, xb = 0, xf = 0;
+    if (j < N) {
+      const Fwd f = split_forward<P2>(geom, j);
+      const uint64_t b = sp[j];
+      xs = Xg[j];
+      const uint64_t ox = xs & Xg[f.x], oy = xs & Xg[f.y], oz = D == 3 ? xs & Xg[f.z] : 0ull;
+      const uint64_t ux = ox & (b ^ sp[f.x] ^ Jg[j]), uy = oy & (b ^ sp[f.y] ^ Jg[N + j]);
+      const uint64_t uz = D == 3 ? oz & (b ^ sp[f.z] ^ Jg[2u * N + j]) : 0ull;
+      s1 = ux ^ uy ^ uz;
+      c1 = (ux & uy) | (ux & uz) | (uy & uz);
+      s2 = ox ^ oy ^ oz;
+      c2 = (ox & oy) | (ox & oz) | (oy & oz);
+      xb = xs & b;
+      xf = xs & (b ^ Hg[j]);
+    }
+    col_signed(s1, 1, 1, tot[0][0], tot[0][1]);
+    col_signed(c1, 2, 1, tot[0][0], tot[0][1]);
+    col_signed(s2, 0, -1, tot[0][0], tot[0][1]);
+    col_signed(c2, 1, -1, tot[0][0], tot[0][1]);
+    long long xl = 0, xh = 0;
+    col_signed(xs, 0, 1, xl, xh);
+    tot[1][0] += xl;
+    tot[1][1] += xh;
+    tot[2][0] += xl;
+    tot[2][1] += xh;
+    col_signed(xb, 1, -1, tot[1][0], tot[1][1]);
+    col_signed(xf, 1, -1, tot[2][0], tot[2][1]);
   }
   const int row_off[3] = {sigma, sigma, sigma}, field[3] = {0, 1, 2};
-  block_flush(red, tot, NQ, g, S, acc, row_off, field, slots);
+  block_flush(red, tot, 3, g, S, acc, row_off, field, slots);
 }
 
 // Overlap at temperature k between replicas 0 and 1 (Sec. 4.1).  After
@@ -668,8 +864,11 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
 // lane: W_a = OR_t (sel[a][t] & spins[t*R + a]), sel[a][t] = lanes whose
 // temperature k sits in slot t.  X = count per lane of W_0 ^ W_1, Q = N - 2X,
 // stored in acc[s][k*R][6].  Grid (chunks, groups x temperatures).
+// With occupations (field models) the value Q = sum x (1 - 2 (w0 ^ w1)) is
+// stored instead of the count.
 __global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restrict__ spins,
-                                                         const int32_t* __restrict__ slot_at, int64_t* acc,
+                                                         const int32_t* __restrict__ slot_at,
+                                                         const uint64_t* __restrict__ xbits, int64_t* acc,
                                                          uint32_t N, int S, int R, int K, int slots) {
   extern __shared__ uint64_t sel[];  // [2][K]
   __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
@@ -692,15 +891,21 @@ __global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restr
   const uint32_t stride = gridDim.x * kBlock;
   for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
     const uint32_t j = base + lane;
-    uint64_t w0 = 0, w1 = 0;
+    uint64_t w0 = 0, w1 = 0, xw = 0;
     if (j < N) {
       for (int t = 0; t < K; ++t) {
         const uint64_t m0 = sel[t], m1 = sel[K + t];
         if (m0) w0 |= m0 & sg[((size_t)t * R + 0) * N + j];
         if (m1) w1 |= m1 & sg[((size_t)t * R + 1) * N + j];
       }
+      if (xbits) xw = xbits[(size_t)g * N + j];
     }
-    col_add(w0 ^ w1, 0, tot[0][0], tot[0][1]);
+    if (xbits) {
+      col_signed(xw, 0, 1, tot[0][0], tot[0][1]);
+      col_signed(xw & (w0 ^ w1), 1, -1, tot[0][0], tot[0][1]);
+    } else {
+      col_add(w0 ^ w1, 0, tot[0][0], tot[0][1]);
+    }
   }
   const int row_off[1] = {k * R}, field[1] = {6};
   block_flush(red, tot, 1, g, S, acc, row_off, field, slots);
@@ -810,6 +1015,15 @@ cudaError_t sweep_dispatch2(Lattice& lat, const BitsParams& p, dim3 grid, size_t
 
 template <int D, int ALGO, bool P2>
 cudaError_t field_launch(Lattice& lat, const BitsParams& p, dim3 grid, size_t smem) {
+  if (lat.dilute) {
+    auto kern = k_sweep_bits_dilute<D, ALGO, P2>;
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, kBlock, smem, lat.stream>>>(p, lat.hbits, lat.xbits);
+    return cudaGetLastError();
+  }
   auto kern = k_sweep_bits_field<D, ALGO, P2>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -861,7 +1075,7 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   const int algo = inv ? 1 : 0;
   if (lat.field) {
     if (lat.flut_ok && lat.variant != 1 && lat.jitf_algo != algo) {
-      lat.jitf = jit_field_kernel(lat, algo, 3);
+      lat.jitf = jit_field_kernel(lat, algo, lat.dilute && lat.R == 2 ? 2 : 3);  // the diluted pair of replicas needs room
       lat.jitf_algo = algo;
     }
     return;
@@ -882,19 +1096,23 @@ cudaError_t launch_init_bits(Lattice& lat, int jmode) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_init_sites_bits(Lattice& lat) {
-  k_init_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, lat.geom, lat.G, lat.keys);
+cudaError_t launch_init_sites_bits(Lattice& lat, double occupation) {
+  const uint64_t T_occ = (uint64_t)std::floor(std::ldexp(occupation, 32));
+  k_init_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(
+      lat.hbits, lat.xbits, lat.geom, lat.G, lat.disorder == IANUS_DISORDER_RFIM, lat.disorder == IANUS_DISORDER_DAFF,
+      T_occ, lat.keys);
   return cudaGetLastError();
 }
 
-cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs) {
-  k_get_sites_bits<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(lat.hbits, dev_hs, lat.geom, lat.S);
+cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs, int8_t* dev_occ) {
+  k_get_sites_bits<<<grid_for((uint64_t)lat.S * lat.N), 256, 0, lat.stream>>>(lat.hbits, lat.xbits, dev_hs, dev_occ,
+                                                                             lat.geom, lat.S);
   return cudaGetLastError();
 }
 
-cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs) {
-  k_set_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, dev_hs, lat.geom, lat.S,
-                                                                               lat.G);
+cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs, const int8_t* dev_occ) {
+  k_set_sites_bits<<<grid_for((uint64_t)lat.G * lat.N), 256, 0, lat.stream>>>(lat.hbits, lat.xbits, dev_hs, dev_occ,
+                                                                               lat.geom, lat.S, lat.G);
   return cudaGetLastError();
 }
 
@@ -948,8 +1166,8 @@ cudaError_t launch_sweep_fused(Lattice& lat, int colour) {
 }
 
 cudaError_t launch_build_field_planes(Lattice& lat) {
-  k_build_field_planes<<<grid_for((uint64_t)lat.G * lat.slots * kFieldPlaneClasses, 128), 128, 0, lat.stream>>>(
-      lat.ftp, lat.fthr, lat.temp_of, lat.D, lat.G, lat.S, lat.R, lat.K, lat.slots);
+  k_build_field_planes<<<grid_for((uint64_t)lat.G * lat.slots * lat.fpc, 128), 128, 0, lat.stream>>>(
+      lat.ftp, lat.fthr, lat.temp_of, lat.D, lat.G, lat.S, lat.R, lat.K, lat.slots, lat.fpc);
   return cudaGetLastError();
 }
 
@@ -994,13 +1212,14 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
       prepare_sweep_bits(lat, inv);
       if (lat.jitf) {
         const uint64_t* hb = lat.hbits;
+        const uint64_t* xb = lat.xbits;
         const uint8_t* lut = (const uint8_t*)(lat.fthr + (size_t)lat.K * kFieldClasses);
-        void* args[] = {(void*)&p, (void*)&hb, (void*)&lut};
+        void* args[] = {(void*)&p, (void*)&hb, (void*)&xb, (void*)&lut};
         return cudaLaunchKernel((const void*)lat.jitf, grid, dim3(kBlock), args, 0, lat.stream);
       }
     }
     p.tp = lat.ftp;
-    const size_t fsmem = (size_t)lat.R * kPlanes * kFieldPlaneClasses * sizeof(uint64_t);
+    const size_t fsmem = (size_t)lat.R * kPlanes * lat.fpc * sizeof(uint64_t);
     return field_dispatch(lat, p, grid, fsmem, algo);
   }
   // Lane-uniform thresholds (one temperature): the kernel specialised for
@@ -1047,15 +1266,14 @@ cudaError_t measure_dispatch(Lattice& lat, int want_q) {
   }
   dim3 grid(meas_blocks(lat.N, (unsigned)(lat.G * lat.slots)), (unsigned)(lat.G * lat.slots));
   if (lat.field)
-    k_measure_bits<D, true, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.acc, lat.geom, lat.S, lat.R,
-                                                                 lat.K, lat.slots);
+    k_measure_field_bits<D, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.hbits, lat.xbits, lat.acc, lat.geom,
+                                                                 lat.S, lat.slots);
   else
-    k_measure_bits<D, false, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, nullptr, lat.acc, lat.geom, lat.S, lat.R,
-                                                                  lat.K, lat.slots);
+    k_measure_bits<D, P2><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S, lat.R, lat.K, lat.slots);
   if (want_q && lat.R >= 2) {
     dim3 gq(meas_blocks(lat.N, (unsigned)(lat.G * lat.K)), (unsigned)(lat.G * lat.K));
-    k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(sp, lat.slot_at, lat.acc, lat.N, lat.S,
-                                                                           lat.R, lat.K, lat.slots);
+    k_overlap_bits<<<gq, kBlock, 2 * lat.K * sizeof(uint64_t), lat.stream>>>(
+        sp, lat.slot_at, lat.field ? lat.xbits : nullptr, lat.acc, lat.N, lat.S, lat.R, lat.K, lat.slots);
   }
   return cudaGetLastError();
 }

@@ -24,16 +24,11 @@ __global__ void k_finalize(const int64_t* __restrict__ acc, const int32_t* __res
     const int k = sk % K, s = sk / K;
     const int tslot = slot_at[((size_t)s * R + a) * K + k];
     const int64_t* row = acc + ((size_t)s * slots + (size_t)tslot * R + a) * kAccStride;
-    if (E) E[idx] = config_energy(row, mode, D, N);
+    if (E) E[idx] = field ? row[0] : config_energy(row, mode, D, N);
     if (M) {
-      if (field) {  // M = sum x s, F = sum sign(h) x s
-        if (mode == IANUS_LAYOUT_BITS64) {
-          M[(size_t)idx * 2] = (int64_t)N - 2 * row[1];
-          M[(size_t)idx * 2 + 1] = (int64_t)N - 2 * row[2];
-        } else {
-          M[(size_t)idx * 2] = row[1];
-          M[(size_t)idx * 2 + 1] = row[2];
-        }
+      if (field) {  // M = sum x s, F = sum sign(h) x s (values in both layouts)
+        M[(size_t)idx * 2] = row[1];
+        M[(size_t)idx * 2 + 1] = row[2];
       } else if (mode == IANUS_LAYOUT_U8X4) {
         for (int f = 0; f < 4; ++f) M[(size_t)idx * 4 + f] = row[2 + f];
       } else if (mode == IANUS_LAYOUT_BITS64) {
@@ -44,7 +39,7 @@ __global__ void k_finalize(const int64_t* __restrict__ acc, const int32_t* __res
     }
     if (Q && want_q && a == 0) {
       const int64_t x = acc[((size_t)s * slots + (size_t)k * R) * kAccStride + 6];
-      Q[sk] = mode == IANUS_LAYOUT_BITS64 ? (int64_t)N - 2 * x : x;
+      Q[sk] = mode == IANUS_LAYOUT_BITS64 && !field ? (int64_t)N - 2 * x : x;
     }
   }
   if (sweep_out && blockIdx.x == 0 && threadIdx.x == 0) *sweep_out = sweep;

@@ -23,6 +23,10 @@ constexpr uint64_t kTwo32 = 1ull << 32;
 // s_i h_i > 0; the bit-sliced class is 8 f + u with v = 2D - 2u.
 constexpr int kFieldClasses = 32;
 constexpr int kFieldPlaneClasses = 16;
+// With dilution (DAFF) the bit-sliced local field is t = v + 2D in 0..4D,
+// summed as 4 bit-planes from per-neighbour contributions c_j + 1 in {0,1,2};
+// plane class 16 f + t.
+constexpr int kDiluteClasses = 32;
 
 // Truth tables of the lane-uniform threshold path: t[p] bit u = bit (31-p)
 // of the class-u threshold; always bit u = (T(u) == 2^32); need bit u = the
@@ -36,8 +40,8 @@ struct UniformLut {
 // (bit u = the class (u, f)); t[f] is laid out as the 64 bytes the field
 // kernel's tail reads.
 struct FieldLut {
-  uint8_t t[2][32];
-  uint8_t always[2], need[2];
+  uint8_t t[2][2][32];            // [f][t3 (dilute models; 0 otherwise)][plane]
+  uint8_t always[2][2], need[2][2];
 };
 
 // Fused serving: a job occupies the lanes [lane0, lane0 + n) of one 64-lane
@@ -99,6 +103,9 @@ struct Lattice {
   int8_t* hs;           // I8 field: sign of h_i, int8 [S][N]
   int8_t* occ;          // I8 field: x_i in {0, 1}, int8 [S][N]
   uint64_t* hbits;      // BITS64 field: lane bit set where h_i < 0, u64 [G][N]
+  uint64_t* xbits;      // BITS64 field: lane bit set where x_i = 1 (occupied), u64 [G][N]
+  bool dilute;          // BITS64 DAFF: local field from the 4-bit sum t (plane classes kDiluteClasses)
+  int fpc;              // plane classes of the field planes (kFieldPlaneClasses or kDiluteClasses)
   FieldLut flut;        // valid when flut_ok (BITS64 field model, one temperature)
   bool flut_ok;
   cudaKernel_t jitf;    // field sweep specialised for flut (null: per-lane planes)
@@ -198,9 +205,9 @@ cudaError_t launch_get_couplings_i8(Lattice& lat, int8_t* dev_out);   // [S][D][
 cudaError_t launch_set_couplings_i8(Lattice& lat, const int8_t* dev_in);
 // BITS64 (k_msc.cu)
 cudaError_t launch_init_bits(Lattice& lat, int jmode);
-cudaError_t launch_init_sites_bits(Lattice& lat);                    // hbits from the H stream
-cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs);     // [S][N]
-cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs);
+cudaError_t launch_init_sites_bits(Lattice& lat, double occupation);  // hbits (H stream), xbits (X stream)
+cudaError_t launch_get_sites_bits(Lattice& lat, int8_t* dev_hs, int8_t* dev_occ);  // [S][N] each
+cudaError_t launch_set_sites_bits(Lattice& lat, const int8_t* dev_hs, const int8_t* dev_occ);
 cudaError_t launch_build_field_planes(Lattice& lat);                 // ftp from fthr and temp_of
 // fused serving (k_msc.cu)
 cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_t n, uint32_t jgroup,

@@ -86,8 +86,9 @@ def test_field_model_validation():
     RFIM, DAFF = ianus.DISORDER_RFIM, ianus.DISORDER_DAFF
     assert rb(disorder=RFIM, field=1.5) > 0
     assert rb(disorder=RFIM, field=1.5, layout=1) > 0
-    assert rb(disorder=DAFF, field=0.5, occupation=0.7) > 0            # AUTO -> I8
-    assert rb(disorder=DAFF, field=0.5, occupation=0.7, layout=2) == 0  # no dilution in BITS64
+    assert rb(disorder=DAFF, field=0.5, occupation=0.7) > 0
+    assert rb(disorder=DAFF, field=0.5, occupation=0.7, layout=1) > 0
+    assert rb(disorder=DAFF, field=0.5, occupation=0.7, layout=2) > 0   # bit-sliced with dilution
     assert rb(disorder=DAFF, occupation=1.5) == 0
     assert rb(disorder=DAFF, occupation=float("nan")) == 0
     assert rb(disorder=RFIM, field=-1.0) == 0
@@ -101,6 +102,8 @@ def test_field_model_validation():
     assert rb(L=8, S=64, R=110, layout=2) > 0 and rb(L=8, S=64, R=111, layout=2) == 0
     assert rb(disorder=RFIM, field=1.0, L=8, S=64, R=55, layout=2) > 0
     assert rb(disorder=RFIM, field=1.0, L=8, S=64, R=56, layout=2) == 0
+    assert rb(disorder=DAFF, field=1.0, L=8, S=64, R=27, layout=2) > 0   # 32 plane classes
+    assert rb(disorder=DAFF, field=1.0, L=8, S=64, R=28, layout=2) == 0
 
 
 @pytest.mark.parametrize("beta", [0.0, 0.25, 1 / 1.1, 1.0, 2.0, 7.5])

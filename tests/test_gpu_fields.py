@@ -37,7 +37,8 @@ def _pair(ianus, disorder, dim=3, L=4, S=1, R=1, K=1, h=0.75, occ=0.7, layout="a
     return lat, orc
 
 
-LAYOUTS = [(DIS_RFIM, "i8"), (DIS_RFIM, "bits64"), (DIS_RFIM, "bits64-jit"), (DIS_DAFF, "i8")]
+LAYOUTS = [(DIS_RFIM, "i8"), (DIS_RFIM, "bits64"), (DIS_RFIM, "bits64-jit"), (DIS_DAFF, "i8"), (DIS_DAFF, "bits64"),
+           (DIS_DAFF, "bits64-jit")]
 
 
 @pytest.mark.parametrize("disorder,layout", LAYOUTS)
@@ -109,9 +110,10 @@ def test_field_extreme_temperatures_and_fields(ianus, beta, h):
             assert np.array_equal(lat.spins(), orc.spins()), (disorder, layout, algo)
 
 
+@pytest.mark.parametrize("layout", ["i8", "bits64", "bits64-jit"])
 @pytest.mark.parametrize("occ", [0.0, 1.0])
-def test_daff_occupation_edges(ianus, occ):
-    lat, orc = _pair(ianus, DIS_DAFF, dim=3, L=6, S=9, R=2, h=0.5, occ=occ)
+def test_daff_occupation_edges(ianus, occ, layout):
+    lat, orc = _pair(ianus, DIS_DAFF, dim=3, L=6, S=9, R=2, h=0.5, occ=occ, layout=layout)
     before = lat.spins()
     for algo in (METROPOLIS, HEATBATH):
         lat.sweep(algo, 0.6, 4)
@@ -125,9 +127,8 @@ def test_daff_occupation_edges(ianus, occ):
 
 @pytest.mark.parametrize("disorder,layout", LAYOUTS)
 def test_field_set_sites_gauge(ianus, disorder, layout):
-    """Gauge-transformed couplings, field signs and spins (the bit-sliced
-    layout holds no dilution, so only the RFIM there): GPU against the oracle
-    given the same sites, and e s(t) against the untransformed run."""
+    """Gauge-transformed couplings, field signs and spins: GPU against the
+    oracle given the same sites, and e s(t) against the untransformed run."""
     L, D, S = 4, 3, 5
     N = L ** D
     eps = np.random.default_rng(3).choice([-1, 1], size=(S, N)).astype(np.int8)
@@ -205,8 +206,6 @@ def test_field_errors(ianus):
     with pytest.raises(ianus.IanusError) as e:
         bits.set_sites(x=np.zeros((3, 64), dtype=np.int8))
     assert e.value.status == ianus.EUNSUPPORTED
-    with pytest.raises(ianus.IanusError):
-        ianus.Lattice(dim=3, L=4, layout="bits64", disorder="daff", occupation=0.5)
     ea = ianus.Lattice(dim=3, L=4, n_samples=2)
     hs, x = ea.sites()
     assert np.all(hs == 1) and np.all(x == 1)
@@ -238,3 +237,49 @@ def test_rfim_full_size_sampled(ianus):
     Fs = (s * hs[:, None, :]).sum(axis=2)
     assert np.array_equal(M[:, 0, :, 0], Ms) and np.array_equal(M[:, 0, :, 1], Fs)
     assert np.array_equal(Q[:, 0], (s[:, 0] * s[:, 1]).sum(axis=1))
+
+
+def test_daff_plain_and_bitsliced_agree(ianus):
+    kw = dict(dim=3, L=8, n_samples=70, n_replicas=2, seed=6, disorder="daff", field=1.25, occupation=0.65)
+    a = ianus.Lattice(layout="i8", **kw)
+    b = ianus.Lattice(layout="bits64", **kw)
+    assert np.array_equal(a.sites()[1], b.sites()[1])
+    for algo in (METROPOLIS, HEATBATH):
+        a.sweep(algo, 0.6, 5)
+        b.sweep(algo, 0.6, 5)
+        assert np.array_equal(a.spins(), b.spins())
+        for u, v in zip(a.measure(), b.measure()):
+            assert np.array_equal(u, v)
+
+
+def test_daff_full_size_sampled(ianus):
+    """DAFF 3D L=64, 256 samples, occupation 0.7, |h|=1.0, Metropolis T=1.5 on
+    the bit-sliced layout (the specialised kernel: 2^20 site words): a sample
+    of configurations equals the oracle run of exactly those samples, and
+    E_J, M, F of every configuration equal the values recomputed from the
+    downloaded spins, sites and couplings."""
+    L, S, h, occ, beta = 64, 256, 1.0, 0.7, 1 / 1.5
+    lat = ianus.Lattice(dim=3, L=L, n_samples=S, seed=SEED + 78, layout="bits64", disorder="daff", field=h,
+                        occupation=occ)
+    lat.sweep(METROPOLIS, beta, 12)
+    ids = [0, 1, 63, 64, 200, 255, 31]
+    orc = Oracle(dim=3, L=L, sample_ids=ids, seed=SEED + 78, disorder=DIS_DAFF, field=h, occupation=occ)
+    orc.sweep(METROPOLIS, beta, 12, nthreads=8)
+    sp = lat.spins()
+    assert np.array_equal(sp[ids], orc.spins())
+    E, M, _ = lat.measure(overlap=False)
+    Eo, Mo, _ = orc.measure()
+    assert np.array_equal(E[ids], Eo) and np.array_equal(M[ids], Mo)
+    hs, x = lat.sites()
+    s = sp[:, 0].astype(np.int64) * x
+    assert np.array_equal(M[:, 0, 0, 0], s.sum(axis=1))
+    assert np.array_equal(M[:, 0, 0, 1], (s * hs).sum(axis=1))
+    idx = np.arange(L ** 3)
+    coords = [(idx // L ** d) % L for d in range(3)]
+    EJ = np.zeros(S, dtype=np.int64)
+    for d in range(3):
+        c = [q.copy() for q in coords]
+        c[d] = (c[d] + 1) % L
+        j = c[0] + L * (c[1] + L * c[2])
+        EJ += (s * s[:, j]).sum(axis=1)  # J = -1: E_J = + sum x x s s
+    assert np.array_equal(E[:, 0, 0], EJ)

@@ -51,16 +51,18 @@ def test_jit_kernel_compiles_for_sm103a(D, algo, R, P2, mode, phase, minb, group
     assert size.value > 1000
 
 
-@pytest.mark.parametrize("D,algo,R,P2", [(3, 1, 1, 1), (3, 0, 2, 0), (2, 1, 2, 1)])
-def test_jit_field_kernel_compiles_for_sm103a(D, algo, R, P2):
+@pytest.mark.parametrize("D,algo,R,P2,dil", [(3, 1, 1, 1, 0), (3, 0, 2, 0, 0), (2, 1, 2, 1, 0), (3, 0, 1, 1, 1),
+                                             (3, 1, 2, 0, 1), (2, 0, 2, 1, 1)])
+def test_jit_field_kernel_compiles_for_sm103a(D, algo, R, P2, dil):
     lib = _nvrtc()
     hdrs = [open(os.path.join(CSRC, n), "rb").read() for n in ("common.cuh", "jit_field.cuh")]
-    l0 = ",".join(str((13 * q + 5) & 0x7F) for q in range(32))
-    l1 = ",".join(str((7 * q + 3) & 0x7F) for q in range(32))
     pre = (f"#define IANUS_JIT_D {D}\n#define IANUS_JIT_ALGO {algo}\n#define IANUS_JIT_R {R}\n"
-           f"#define IANUS_JIT_P2 {P2}\n#define IANUS_JIT_MINB 3\n#define IANUS_JIT_LUT0 {l0}\n"
-           f"#define IANUS_JIT_LUT1 {l1}\n#define IANUS_JIT_ALWAYS0 0\n#define IANUS_JIT_ALWAYS1 64\n"
-           f"#define IANUS_JIT_NEED0 127\n#define IANUS_JIT_NEED1 63\n#include \"jit_field.cuh\"\n").encode()
+           f"#define IANUS_JIT_P2 {P2}\n#define IANUS_JIT_MINB 3\n#define IANUS_JIT_DILUTE {dil}\n")
+    for f in range(2):
+        for h in range(2):
+            pre += f"#define IANUS_JIT_LUT{f}{h} " + ",".join(str((13 * q + 5 * f + 3 * h) & 0x7F) for q in range(32))
+            pre += f"\n#define IANUS_JIT_ALWAYS{f}{h} {64 * f}\n#define IANUS_JIT_NEED{f}{h} {127 - 64 * f}\n"
+    pre = (pre + "#include \"jit_field.cuh\"\n").encode()
     prog = C.c_void_p()
     H = (C.c_char_p * 2)(*hdrs)
     N = (C.c_char_p * 2)(b"common.cuh", b"jit_field.cuh")
