@@ -68,9 +68,9 @@ int plan(const ianus_config* c, Sizes& z) {
   if (potts && layout != IANUS_LAYOUT_U8X4) return IANUS_EUNSUPPORTED;
   if (c->rng == IANUS_RNG_WHEEL && (potts || layout != IANUS_LAYOUT_I8)) return IANUS_EUNSUPPORTED;
   if (layout == IANUS_LAYOUT_BITS64 &&  // the sweep stages one block's threshold planes in shared memory
-      (size_t)c->n_replicas * kPlanes *
-              (!field ? kMaxClasses : c->disorder == IANUS_DISORDER_DAFF ? kDiluteClasses : kFieldPlaneClasses) * 8 >
-          kMaxSmemPerBlock)
+      (!field ? sweep_bits_smem(c->n_replicas)
+              : (size_t)c->n_replicas * kPlanes *
+                    (c->disorder == IANUS_DISORDER_DAFF ? kDiluteClasses : kFieldPlaneClasses) * 8) > kMaxSmemPerBlock)
     return IANUS_EUNSUPPORTED;
   z.model = c->model;
   z.D = c->dim;

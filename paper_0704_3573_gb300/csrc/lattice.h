@@ -215,6 +215,7 @@ cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_
 cudaError_t launch_sweep_fused(Lattice& lat, int colour);
 cudaError_t launch_advance_segments(Lattice& lat);
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
+size_t sweep_bits_smem(int R);  // shared memory of the per-lane-plane sweep for R replicas
 cudaError_t launch_measure_bits(Lattice& lat, int want_q);
 cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
 cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out);
