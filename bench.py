@@ -406,8 +406,10 @@ def run_other_configs(args):
     lat.sweep(ianus.METROPOLIS, 1 / 1.1, 10, 1)
     sec = timed(lambda: lat.sweep(ianus.METROPOLIS, 1 / 1.1, 1000, 1), 1)
     out["L16_single_sample_metropolis"] = {"updates_per_ns": 16 ** 3 * 1000 / (sec * 1e9), "ms_per_1000_sweeps": sec * 1e3,
-                                           "mode": "plain int8, shared-memory resident, E/M every sweep",
-                                           "bound": "latency (one lattice on one SM, 2000 colour barriers)"}
+                                           "sweep_us": sec * 1e3,
+                                           "mode": "plain int8, one lattice split over a 16-block cluster "
+                                                   "(one z-plane per block, halos in shared memory), E/M every sweep",
+                                           "bound": "latency (2 cluster barriers and 2 dependent passes per sweep)"}
     if not args.no_cpu_baseline:
         import oracle
 

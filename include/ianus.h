@@ -434,10 +434,23 @@ ianus_status ianus_set_graphs(ianus_lattice* lat, int32_t enable);
 
 /* Resident mode for small plain lattices (default on): with layout I8, one
  * temperature, (1 + dim) L^dim bytes <= 200 KiB, and either one replica or no
- * measurements, each configuration is held in the shared memory of one
- * thread block that runs all requested sweeps (the two colours separated by
- * a block barrier, Sec. 3.1) and records E and M itself.  Same results as the
- * launch-per-colour path.  enable = 0 turns it off. */
+ * measurements, each configuration is held in shared memory by one launch
+ * that runs all requested sweeps (the two colours separated by barriers,
+ * Sec. 3.1) and records E and M itself.  Same results as the
+ * launch-per-colour path.
+ *   enable = 1 (default): with few configurations (at most two blocks per SM
+ *            when each is split) a thread-block cluster of C blocks holds
+ *            one configuration, C the largest divisor of L in 2..16 that
+ *            can be scheduled; block r owns the slab of L/C planes along the
+ *            last axis, neighbours across a face come from the neighbouring
+ *            block's shared memory, cluster barriers separate the colours.
+ *            Otherwise one thread block per configuration.
+ *   enable = 2: one thread block per configuration always.
+ *   enable = 3: a cluster per configuration whenever L has a divisor in
+ *            2..16 for which a cluster can be scheduled, however many
+ *            configurations there are.
+ *   enable = 0: off.
+ * Other values: IANUS_EINVAL. */
 ianus_status ianus_set_resident(ianus_lattice* lat, int32_t enable);
 
 /* Frees what the lattice allocated.  NULL is accepted.  The caller-owned

@@ -398,9 +398,12 @@ class Lattice:
         """Replay sweep blocks from captured CUDA graphs (default) or launch directly."""
         _check(self._lib.ianus_set_graphs(self._h, int(bool(enable))), "ianus_set_graphs")
 
-    def set_resident(self, enable: bool):
-        """Shared-memory-resident sweeps for small plain lattices (default on)."""
-        _check(self._lib.ianus_set_resident(self._h, int(bool(enable))), "ianus_set_resident")
+    def set_resident(self, enable):
+        """Shared-memory-resident sweeps for small plain lattices: True / 1
+        (default: a block cluster per configuration when there are few), 2
+        (one block per configuration always), 3 (a cluster per configuration
+        whenever one can be formed), False / 0 (off)."""
+        _check(self._lib.ianus_set_resident(self._h, int(enable)), "ianus_set_resident")
 
     def synchronize(self):
         _check(self._lib.ianus_synchronize(self._h), "ianus_synchronize")

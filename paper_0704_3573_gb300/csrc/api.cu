@@ -555,6 +555,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->t_dev = (uint64_t*)(b + z.off_tdev);
   lat->use_graphs = true;
   lat->use_resident = true;
+  lat->resident_mode = 1;
   lat->graphs = new (std::nothrow) std::map<uint32_t, cudaGraphExec_t>();
 
   auto bail = [&](int code) {
@@ -1158,7 +1159,9 @@ ianus_status ianus_set_graphs(ianus_lattice* h, int32_t enable) {
 
 ianus_status ianus_set_resident(ianus_lattice* h, int32_t enable) {
   GET_LAT(h);
+  if (enable < 0 || enable > 3) return IANUS_EINVAL;
   lat->use_resident = enable != 0;
+  if (enable) lat->resident_mode = enable;
   return IANUS_OK;
 }
 

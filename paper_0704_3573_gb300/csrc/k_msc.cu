@@ -1174,23 +1174,26 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
   return (unsigned)g;
 }
 
-template <int D, int ALGO, int RT, bool P2>
+template <int D, int ALGO, int RT, bool P2, bool Q>
 cudaError_t sweep_launch(Lattice& lat, const BitsParams& p, dim3 grid) {
-  const size_t smem = bits_sweep_smem(lat.R, ALGO == 1);
+  const size_t smem = bits_sweep_smem(lat.R, Q);
   if (smem > 48 * 1024) {  // many replicas: opt in to more than 48 KiB of planes and queues
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_bits<D, ALGO, RT, P2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_bits<D, ALGO, RT, P2, Q>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_sweep_bits<D, ALGO, RT, P2><<<grid, kBlock, smem, lat.stream>>>(p);
+  k_sweep_bits<D, ALGO, RT, P2, Q><<<grid, kBlock, smem, lat.stream>>>(p);
   return cudaGetLastError();
 }
 
 template <int D, int ALGO, bool P2>
 cudaError_t sweep_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t) {
-  if (lat.R == 1) return sweep_launch<D, ALGO, 1, P2>(lat, p, grid);
-  if (lat.R == 2) return sweep_launch<D, ALGO, 2, P2>(lat, p, grid);
-  return sweep_launch<D, ALGO, 0, P2>(lat, p, grid);
+  if (lat.R == 1) return sweep_launch<D, ALGO, 1, P2, ALGO == 1>(lat, p, grid);
+  if (lat.R == 2) return sweep_launch<D, ALGO, 2, P2, ALGO == 1>(lat, p, grid);
+  // the heat bath's queues when they fit beside the planes (up to 97 replicas)
+  if (ALGO == 1 && bits_sweep_smem(lat.R, true) <= 227u * 1024u)
+    return sweep_launch<D, ALGO, 0, P2, true>(lat, p, grid);
+  return sweep_launch<D, ALGO, 0, P2, false>(lat, p, grid);
 }
 
 template <int D, int ALGO>
@@ -1363,7 +1366,7 @@ cudaError_t launch_build_planes(Lattice& lat) {
   return cudaGetLastError();
 }
 
-size_t sweep_bits_smem(int R) { return bits_sweep_smem(R); }
+size_t sweep_bits_smem(int R) { return bits_sweep_smem(R, false); }
 
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   BitsParams p;

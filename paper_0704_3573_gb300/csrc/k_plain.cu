@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "lattice.h"
 
 namespace ianus {
@@ -366,6 +368,356 @@ __global__ void __launch_bounds__(1024) k_resident_i8(const ResidentParams p) {
   for (uint32_t i = threadIdx.x; i < p.N; i += blockDim.x) gsp[i] = sp[i];
 }
 
+// ---- cluster-resident mode: one configuration across a thread-block cluster ----
+//
+// When there are few configurations, one block each leaves most SMs idle and
+// every colour pass is as long as the slowest of a block's many sites.  Here
+// a cluster of C blocks (C divides L) holds one configuration: block r owns
+// the slab of P = L/C planes along the last axis (z in 3D, y in 2D), its
+// spins and forward couplings in shared memory plus the plane of last-axis
+// couplings just below the slab.  Neighbours across a slab face are read from
+// the neighbouring block's shared memory (distributed shared memory), and the
+// two colours are separated by cluster barriers (Sec. 3.1).  The random
+// stream and the update rule are those of k_sweep_i8, so the results are the
+// same bit for bit; E and M are summed per block, then across the cluster in
+// block 0's shared memory.
+
+// Sum of (e, m) over the block, valid in thread 0; red holds one pair per warp.
+__device__ __forceinline__ void block_sum2(long long (*red)[32], long long e, long long m, long long& E,
+                                           long long& M) {
+  for (int off = 16; off > 0; off >>= 1) {
+    e += __shfl_down_sync(0xffffffffu, e, off);
+    m += __shfl_down_sync(0xffffffffu, m, off);
+  }
+  __syncthreads();  // red may still be read from the previous sum
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = e;
+    red[1][threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  E = M = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
+      E += red[0][w];
+      M += red[1][w];
+    }
+}
+
+// The first eight planes of a site's random number (plane 0 in bit 7), from
+// four Philox blocks computed together: they do not depend on the spins, so
+// a block computes them while it waits at the barrier before the pass.
+__device__ __forceinline__ uint32_t first_planes(const PhiloxKeys& keys, const Tick& tk, int s, int sigma,
+                                                 uint32_t site) {
+  const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
+  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+  uint4 x[4];
+#pragma unroll
+  for (uint32_t m = 0; m < 4u; ++m) x[m] = philox10(site, tk.lo, c2base | (m << 24), tk.hi, keys);
+  uint32_t r8 = 0;
+#pragma unroll
+  for (uint32_t m = 0; m < 4u; ++m) {
+    const uint32_t w0 = lane < 32u ? (x[m].x >> lane) : (x[m].y >> (lane - 32u));
+    const uint32_t w1 = lane < 32u ? (x[m].z >> lane) : (x[m].w >> (lane - 32u));
+    r8 |= ((w0 & 1u) << (7u - 2u * m)) | ((w1 & 1u) << (6u - 2u * m));
+  }
+  return r8;
+}
+
+// r < T (as lazy_less) given the first eight planes r8; planes 8.. drawn
+// one Philox block at a time when those agree with T.
+__device__ __forceinline__ bool less_from(uint64_t T, uint32_t r8, const PhiloxKeys& keys, const Tick& tk, int s,
+                                          int sigma, uint32_t site) {
+  if (T >= kTwo32) return true;
+  const uint32_t T32 = (uint32_t)T;
+  const uint32_t t8 = T32 >> 24;
+  if (r8 != t8) return r8 < t8;
+  const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
+  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+#pragma unroll 1
+  for (uint32_t m = 4; m < 16u; ++m) {
+    const uint4 y = philox10(site, tk.lo, c2base | (m << 24), tk.hi, keys);
+    const uint32_t w0 = lane < 32u ? (y.x >> lane) : (y.y >> (lane - 32u));
+    const uint32_t w1 = lane < 32u ? (y.z >> lane) : (y.w >> (lane - 32u));
+    const uint32_t r0 = w0 & 1u, t0 = (T32 >> (31u - 2u * m)) & 1u;
+    if (r0 != t0) return r0 < t0;
+    const uint32_t r1 = w1 & 1u, t1 = (T32 >> (30u - 2u * m)) & 1u;
+    if (r1 != t1) return r1 < t1;
+  }
+  return false;  // r == T
+}
+
+// Split cluster barrier: arrive (release: this block's shared-memory writes
+// become visible) and wait (acquire).  Not the .aligned forms, so that they
+// need no warp convergence.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release;\n" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire;\n" ::: "memory"); }
+
+constexpr unsigned kClusterBlockMax = 512;  // threads per block of the cluster-resident kernel
+
+// Sum of (e, m) over the block into thread 0 (64-bit), from 32-bit thread
+// values: one warp reduction each, one word per warp in red.  The caller
+// makes sure red is not still being read from an earlier sum.
+__device__ __forceinline__ void block_sum2_i32(int (*red)[32], int e, int m, long long& E, long long& M) {
+  e = __reduce_add_sync(0xffffffffu, e);
+  m = __reduce_add_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = e;
+    red[1][threadIdx.x >> 5] = m;
+  }
+  __syncthreads();
+  E = M = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)((blockDim.x + 31) >> 5); ++w) {
+      E += red[0][w];
+      M += red[1][w];
+    }
+}
+
+// E and M of a block's slab (forward bonds of its own sites; the plane above
+// the slab from the halo), summed over the block by thread 0.
+template <int D>
+__device__ __forceinline__ void slab_energy(const int8_t* sp, const int8_t* Js, const int8_t* halo_up, uint32_t L,
+                                            uint32_t A, uint32_t P, long long (*red)[32], long long& E,
+                                            long long& M) {
+  const uint32_t PA = P * A;
+  long long e = 0, m = 0;
+  for (uint32_t j = threadIdx.x; j < PA; j += blockDim.x) {
+    const uint32_t zl = j / A, ip = j - zl * A;
+    const uint32_t x = ip % L;
+    const int si = sp[j];
+    e -= Js[j] * si * sp[j - x + (x + 1u == L ? 0u : x + 1u)];
+    if (D == 3) {
+      const uint32_t y = ip / L;
+      e -= Js[PA + j] * si * sp[j - L * y + L * (y + 1u == L ? 0u : y + 1u)];
+    }
+    const int8_t s_up = zl + 1u < P ? sp[j + A] : halo_up[ip];
+    e -= Js[(D - 1) * PA + j] * si * s_up;
+    m += si;
+  }
+  block_sum2(red, e, m, E, M);
+}
+
+// One colour-c site of a slab: where it is, where its 2D neighbours are (in
+// this block's slab or halo planes), its 2D coupling values, and the halo
+// cells of the neighbouring blocks that mirror it (null when it is inside
+// the slab).
+template <int D>
+struct SlabSite {
+  uint32_t j, i;            // slab index, natural site index
+  uint32_t n[2 * D - 2];    // in-slab neighbours (x+, x-, y+, y-)
+  const int8_t* up;         // last axis +1
+  const int8_t* dn;         // last axis -1
+  int8_t* mirror_prev;      // the previous block's upper halo cell (bottom plane)
+  int8_t* mirror_next;      // the next block's lower halo cell (top plane)
+  int8_t J[2 * D];          // couplings in the order x+, x-, (y+, y-,) up, dn
+};
+
+// Shared memory of one block: spins[P*A], J[D][P*A], the plane of last-axis
+// couplings below the slab, and the halos: copies of the next block's bottom
+// plane (up) and of the previous block's top plane (dn), kept current by
+// their owners' stores.
+struct SlabMem {
+  int8_t *sp, *Js, *Jh, *halo_up, *halo_dn;
+  int8_t *prev_halo_up, *next_halo_dn;  // in the neighbouring blocks
+};
+
+template <int D>
+__device__ __forceinline__ SlabSite<D> slab_site(uint32_t w, int colour, uint32_t L, uint32_t A, uint32_t P,
+                                                 uint32_t z0, const SlabMem& sm) {
+  const uint32_t h = L / 2u, PA = P * A;
+  const uint32_t row = w / h, k = w - row * h;  // local row of the slab
+  uint32_t y, z, zl;
+  if (D == 3) {
+    y = row % L;
+    zl = row / L;
+    z = z0 + zl;
+  } else {
+    zl = row;
+    y = z0 + zl;
+    z = 0;
+  }
+  const uint32_t x = 2u * k + ((uint32_t)(colour ^ (int)(y + z)) & 1u);
+  const uint32_t ip = D == 3 ? x + L * y : x;  // index within the plane
+  SlabSite<D> q;
+  q.j = ip + A * zl;
+  q.i = ip + A * (z0 + zl);
+  const uint32_t xm = q.j - x + (x == 0u ? L - 1u : x - 1u);
+  q.n[0] = q.j - x + (x + 1u == L ? 0u : x + 1u);
+  q.n[1] = xm;
+  q.J[0] = sm.Js[q.j];
+  q.J[1] = sm.Js[xm];
+  if constexpr (D == 3) {
+    const uint32_t ym = (y == 0u ? L - 1u : y - 1u) * L + x + A * zl;
+    q.n[2] = (y + 1u == L ? 0u : y + 1u) * L + x + A * zl;
+    q.n[3] = ym;
+    q.J[2] = sm.Js[PA + q.j];
+    q.J[3] = sm.Js[PA + ym];
+  }
+  q.up = zl + 1u < P ? sm.sp + q.j + A : sm.halo_up + ip;
+  q.dn = zl > 0u ? sm.sp + q.j - A : sm.halo_dn + ip;
+  q.mirror_prev = zl == 0u ? sm.prev_halo_up + ip : nullptr;
+  q.mirror_next = zl + 1u == P ? sm.next_halo_dn + ip : nullptr;
+  q.J[2 * D - 2] = sm.Js[(D - 1) * PA + q.j];
+  q.J[2 * D - 1] = zl > 0u ? sm.Js[(D - 1) * PA + q.j - A] : sm.Jh[ip];
+  return q;
+}
+
+// One site's update: unsatisfied bonds (J s_i s_j < 0), the decision, and on
+// a flip the new spin in the slab and in the neighbours' halos, with the
+// changes of E and M.
+template <int D>
+__device__ __forceinline__ void slab_update(const SlabSite<D>& q, int8_t* sp, const uint64_t* thr, uint32_t r8,
+                                            const PhiloxKeys& keys, const Tick& tk, int s, int sigma, int inv,
+                                            int& dE, int& dM) {
+  const int si = sp[q.j];
+  int u = 0;
+#pragma unroll
+  for (int b = 0; b < 2 * D - 2; ++b) u += (q.J[b] * si * sp[q.n[b]]) < 0;
+  u += (q.J[2 * D - 2] * si * *q.up) < 0;
+  u += (q.J[2 * D - 1] * si * *q.dn) < 0;
+  const uint64_t T = thr[u];
+  if (T < kTwo32 && r8 == 0xFFFFFFFFu) r8 = first_planes(keys, tk, s, sigma, q.i);
+  if (less_from(T, r8, keys, tk, s, sigma, q.i) != (inv != 0)) {
+    const int8_t ns = (int8_t)(-si);
+    sp[q.j] = ns;
+    if (q.mirror_prev) *q.mirror_prev = ns;
+    if (q.mirror_next) *q.mirror_next = ns;
+    dE += 4 * D - 4 * u;
+    dM -= 2 * si;
+  }
+}
+
+// ONE: every block has at most one site of each colour per thread; the
+// sites' neighbourhoods are then worked out once per launch and the first
+// eight random planes of the next pass are drawn during each barrier wait.
+// E and M are measured once at the start of a launch and then carried by the
+// flips: a flip of a site with u unsatisfied bonds changes E by 4D - 4u and
+// M by -2 s_i.  A launch runs at most 65536 sweeps, so a thread's changes
+// between two measurements fit 32 bits.
+template <int D, bool ONE>
+__global__ void __launch_bounds__(kClusterBlockMax) k_resident_cluster_i8(const ResidentParams p, int C) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ int8_t smem[];
+  __shared__ long long red[2][32];
+  __shared__ int red32[2][32];
+  __shared__ long long part[2][16];  // per-block sums, read in block 0
+  __shared__ uint64_t thr_s[kMaxClasses];
+  const uint32_t L = (uint32_t)p.L;
+  const uint32_t A = D == 3 ? L * L : L;  // sites per plane of the last axis
+  const uint32_t P = L / (uint32_t)C;     // planes per block
+  const uint32_t PA = P * A;
+  const uint32_t rank = cl.block_rank();
+  const uint32_t prev = (rank + (uint32_t)C - 1u) % (uint32_t)C, next = (rank + 1u) % (uint32_t)C;
+  const uint32_t z0 = rank * P;  // first plane of this block's slab
+  SlabMem sm;
+  sm.sp = smem;
+  sm.Js = smem + PA;
+  sm.Jh = sm.Js + (size_t)D * PA;
+  sm.halo_up = sm.Jh + A;
+  sm.halo_dn = sm.halo_up + A;
+  sm.prev_halo_up = cl.map_shared_rank(sm.halo_up, prev);
+  sm.next_halo_dn = cl.map_shared_rank(sm.halo_dn, next);
+  int8_t* sp = sm.sp;
+  const uint32_t lat = blockIdx.x / (uint32_t)C;  // sigma * S + s
+  const int sigma = (int)(lat / (uint32_t)p.S), s = (int)(lat - (uint32_t)sigma * (uint32_t)p.S);
+  int8_t* gsp = p.spins + (size_t)lat * p.N + (size_t)z0 * A;
+  const int8_t* gJ = p.J + (size_t)s * D * p.N;
+  cl.sync();  // every block of the cluster running before any store into another's shared memory
+  for (uint32_t j = threadIdx.x; j < PA; j += blockDim.x) {
+    const int8_t v = gsp[j];
+    sp[j] = v;
+    if (j < A) sm.prev_halo_up[j] = v;                  // bottom plane
+    if (j >= PA - A) sm.next_halo_dn[j - (PA - A)] = v;  // top plane
+  }
+  for (uint32_t d = 0; d < (uint32_t)D; ++d)
+    for (uint32_t j = threadIdx.x; j < PA; j += blockDim.x) sm.Js[d * PA + j] = gJ[(size_t)d * p.N + z0 * A + j];
+  const uint32_t zb = (z0 + L - 1u) % L;  // plane below the slab
+  for (uint32_t j = threadIdx.x; j < A; j += blockDim.x) sm.Jh[j] = gJ[(size_t)(D - 1) * p.N + zb * A + j];
+  if (threadIdx.x < (unsigned)kMaxClasses) thr_s[threadIdx.x] = p.thr[threadIdx.x];
+  long long* part0 = cl.map_shared_rank(&part[0][0], 0u);
+  const uint32_t nw = PA / 2u;  // sites of one colour in the slab
+  const bool mine = threadIdx.x < nw;
+  __syncthreads();  // couplings staged before the sites read them
+  SlabSite<D> site[2];
+  uint32_t r8 = 0;  // first planes of this thread's site in the next pass
+  if (ONE && mine) {
+    site[0] = slab_site<D>(threadIdx.x, 0, L, A, P, z0, sm);
+    site[1] = slab_site<D>(threadIdx.x, 1, L, A, P, z0, sm);
+  }
+  cluster_arrive();
+  if (ONE && mine && p.nsweeps > 0)
+    r8 = first_planes(p.keys, Tick{(uint32_t)p.t0, (uint32_t)(p.t0 >> 32)}, s, sigma, site[0].i);
+  cluster_wait();  // slabs and halos loaded
+  long long E_run = 0, M_run = 0;  // block 0, thread 0
+  if (p.measure_every) {
+    long long E, M;
+    slab_energy<D>(sp, sm.Js, sm.halo_up, L, A, P, red, E, M);
+    if (threadIdx.x == 0) {
+      part0[rank] = E;
+      part0[16 + rank] = M;
+    }
+    cl.sync();
+    if (rank == 0 && threadIdx.x == 0)
+      for (int r = 0; r < C; ++r) {
+        E_run += part[0][r];
+        M_run += part[1][r];
+      }
+  }
+  int dE = 0, dM = 0;  // this thread's flips since the last measurement
+  uint64_t row = p.cap ? p.row0 % p.cap : 0;  // series row of the next measurement
+  // sweeps until the next measured one: sweep t is measured when (t + 1) % every == 0
+  uint32_t left = p.measure_every ? (uint32_t)(p.measure_every - p.t0 % p.measure_every) : 0u;
+  for (uint32_t it = 0; it < p.nsweeps; ++it) {
+    const uint64_t t = p.t0 + it;
+    const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
+    const bool measured = left == 1u;
+    if (p.measure_every) left = measured ? p.measure_every : left - 1u;
+#pragma unroll
+    for (int colour = 0; colour < 2; ++colour) {
+      if (ONE) {
+        if (mine) slab_update<D>(site[colour], sp, thr_s, r8, p.keys, tk, s, sigma, p.inv, dE, dM);
+      } else {
+        for (uint32_t w = threadIdx.x; w < nw; w += blockDim.x)
+          slab_update<D>(slab_site<D>(w, colour, L, A, P, z0, sm), sp, thr_s, 0xFFFFFFFFu, p.keys, tk, s, sigma,
+                         p.inv, dE, dM);
+      }
+      if (colour == 1 && measured) {  // this sweep's changes, into block 0 before the barrier
+        long long bE, bM;
+        block_sum2_i32(red32, dE, dM, bE, bM);
+        dE = dM = 0;
+        if (threadIdx.x == 0) {
+          part0[rank] = bE;
+          part0[16 + rank] = bM;
+        }
+      }
+      cluster_arrive();
+      if (ONE && mine) {  // the next pass: the other colour, or colour 0 of the next sweep
+        if (colour == 0)
+          r8 = first_planes(p.keys, tk, s, sigma, site[1].i);
+        else if (it + 1 < p.nsweeps)
+          r8 = first_planes(p.keys, Tick{(uint32_t)(t + 1), (uint32_t)((t + 1) >> 32)}, s, sigma, site[0].i);
+      }
+      cluster_wait();
+    }
+    if (measured) {
+      if (rank == 0 && threadIdx.x == 0) {
+        for (int r = 0; r < C; ++r) {
+          E_run += part[0][r];
+          M_run += part[1][r];
+        }
+        const size_t at = (size_t)row * p.S * p.R + (size_t)s * p.R + (size_t)sigma;  // one temperature
+        p.ser_E[at] = E_run;
+        p.ser_M[at] = M_run;
+        if (lat == 0) p.ser_sweep[row] = t + 1;
+      }
+      row = row + 1u == p.cap ? 0u : row + 1u;
+    }
+  }
+  for (uint32_t j = threadIdx.x; j < PA; j += blockDim.x) gsp[j] = sp[j];
+  cl.sync();  // no block leaves while another may still write into its shared memory
+}
+
 struct InitParams {
   int8_t* spins;
   int8_t* J;
@@ -666,6 +1018,82 @@ bool resident_i8_fits(const Lattice& lat) {
   return lat.layout == IANUS_LAYOUT_I8 && !lat.field && lat.rng == IANUS_RNG_PHILOX && lat.K == 1 && (size_t)lat.N * (1 + lat.D) <= kResidentSmemMax;
 }
 
+// Launch geometry of the cluster-resident kernel for cluster size C.
+struct ClusterShape {
+  uint32_t PA, A;    // sites of a slab, of a plane
+  unsigned threads;  // per block
+  size_t smem;
+  bool one;          // at most one site of each colour per thread
+};
+
+inline ClusterShape cluster_shape(const Lattice& lat, int C) {
+  ClusterShape c;
+  const uint32_t L = (uint32_t)lat.L;
+  c.A = lat.D == 3 ? L * L : L;
+  c.PA = (L / (uint32_t)C) * c.A;
+  c.threads = std::min(kClusterBlockMax, ((c.PA / 2u + 31u) / 32u) * 32u);
+  c.smem = (size_t)c.PA * (1 + lat.D) + 3u * c.A;
+  c.one = c.PA / 2u <= c.threads;
+  return c;
+}
+
+template <int D, bool ONE>
+cudaError_t cluster_launch(const Lattice& lat, const ResidentParams* p, unsigned configs, int C, bool query, int* n) {
+  const ClusterShape sh = cluster_shape(lat, C);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(configs * (unsigned)C);
+  cfg.blockDim = dim3(sh.threads);
+  cfg.dynamicSmemBytes = sh.smem;
+  cfg.stream = query ? 0 : lat.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (query) {
+    if (C > 8) {
+      const cudaError_t e =
+          cudaFuncSetAttribute(k_resident_cluster_i8<D, ONE>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveClusters(n, k_resident_cluster_i8<D, ONE>, &cfg);
+  }
+  return cudaLaunchKernelEx(&cfg, k_resident_cluster_i8<D, ONE>, *p, C);
+}
+
+template <int D>
+cudaError_t cluster_dispatch(const Lattice& lat, const ResidentParams* p, unsigned configs, int C, bool query,
+                             int* n) {
+  return cluster_shape(lat, C).one ? cluster_launch<D, true>(lat, p, configs, C, query, n)
+                                   : cluster_launch<D, false>(lat, p, configs, C, query, n);
+}
+
+// Cluster-resident launch shape of one configuration: the largest divisor C
+// of L with 2 <= C <= 16 that keeps the grid within two blocks per SM (unless
+// forced) and for which a cluster can be scheduled; 0 = one block per
+// configuration.
+int resident_cluster_size(const Lattice& lat, unsigned configs, bool force) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  const uint32_t L = (uint32_t)lat.L;
+  for (int C = 16; C >= 2; --C) {
+    if (L % (uint32_t)C != 0u || (!force && (uint64_t)configs * (uint64_t)C > 2ull * (uint64_t)sms)) continue;
+    int n = 0;
+    const cudaError_t e = lat.D == 3 ? cluster_dispatch<3>(lat, nullptr, configs, C, true, &n)
+                                     : cluster_dispatch<2>(lat, nullptr, configs, C, true, &n);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (n >= 1) return C;
+  }
+  return 0;
+}
+
 cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every) {
   ResidentParams p;
   p.spins = (int8_t*)lat.spins;
@@ -689,6 +1117,12 @@ cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t
   p.keys = lat.keys;
   const size_t smem = (size_t)lat.N * (1 + lat.D);
   const unsigned blocks = (unsigned)(lat.slots * lat.S);
+  if (lat.resident_mode == 1 || lat.resident_mode == 3) {
+    const int C = resident_cluster_size(lat, blocks, lat.resident_mode == 3);
+    if (C > 0)
+      return lat.D == 3 ? cluster_dispatch<3>(lat, &p, blocks, C, false, nullptr)
+                        : cluster_dispatch<2>(lat, &p, blocks, C, false, nullptr);
+  }
   cudaError_t e;
   if (lat.D == 3) {
     e = cudaFuncSetAttribute(k_resident_i8<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kResidentSmemMax);

@@ -151,6 +151,7 @@ struct Lattice {
   bool capturing;            // launchers pass t_dev (and an offset) while true
   bool use_graphs;
   bool use_resident;         // resident mode for small I8 lattices (default on)
+  int resident_mode;         // 1 = clusters when few configurations, 2 = one block each, 3 = clusters
   bool t_dev_valid;          // *t_dev == sweeps
   cudaStream_t cap_stream;
   std::map<uint32_t, cudaGraphExec_t>* graphs;  // by block length
@@ -215,7 +216,7 @@ cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_
 cudaError_t launch_sweep_fused(Lattice& lat, int colour);
 cudaError_t launch_advance_segments(Lattice& lat);
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
-size_t sweep_bits_smem(int R);  // shared memory of the per-lane-plane sweep for R replicas
+size_t sweep_bits_smem(int R);  // least shared memory of the per-lane-plane sweep for R replicas
 cudaError_t launch_measure_bits(Lattice& lat, int want_q);
 cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
 cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out);

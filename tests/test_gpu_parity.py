@@ -163,6 +163,29 @@ def test_potts_sweep_bit_exact(ianus, dim, L, S, R):
         assert np.array_equal(Q, Qo)
 
 
+@pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
+@pytest.mark.parametrize("R,K", [(3, 3), (5, 2), (100, 2)])
+def test_many_replicas_with_tempering(ianus, algo, R, K):
+    """Per-lane-plane kernel with a run-time replica count: heat-bath words
+    queued per warp (up to 97 replicas), beyond that, and for Metropolis,
+    each word run to the end in place; swaps give every lane its own
+    temperature."""
+    beta = [1.0 / (0.8 + 0.6 * k / (K - 1)) for k in range(K)]
+    lat, orc, _ = _pair(ianus, dim=3, L=4, S=67, R=R, K=K, layout="bits64", seed=SEED + 50 + R)
+    for _ in range(3):
+        lat.sweep(algo, beta, 2)
+        orc.sweep(algo, beta, 2)
+        lat.pt_swap()
+        orc.pt_swap(beta)
+        assert np.array_equal(lat.spins(), orc.spins())
+    sa, acc, _ = lat.pt_state()
+    sao, acco, _ = orc.pt_state()
+    assert np.array_equal(sa, sao) and np.array_equal(acc, acco)
+    E, M, Q = lat.measure()
+    Eo, Mo, Qo = orc.measure()
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo) and np.array_equal(Q, Qo)
+
+
 @pytest.mark.parametrize("layout", ["i8", "bits64"])
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
 def test_parallel_tempering_matches_oracle(ianus, layout, algo):
@@ -355,22 +378,37 @@ def test_graphs_with_parallel_tempering(ianus):
     assert np.array_equal(lat.pt_state()[0], orc.pt_state()[0])
 
 
-@pytest.mark.parametrize("dim,L,S,every", [(3, 16, 1, 1), (3, 8, 5, 3), (2, 32, 3, 0), (3, 2, 1, 1), (3, 32, 2, 7)])
-def test_resident_mode_equals_oracle_and_eager(ianus, dim, L, S, every):
-    """Resident mode (configurations in shared memory, many sweeps per
-    launch, series written in the kernel) against the oracle and the
-    launch-per-colour path."""
+@pytest.mark.parametrize("dim,L,S,R,every", [(3, 16, 1, 1, 1), (3, 8, 5, 1, 3), (2, 32, 3, 1, 0), (3, 2, 1, 1, 1),
+                                             (3, 32, 2, 1, 7), (3, 6, 2, 1, 1), (2, 12, 1, 1, 2), (3, 8, 3, 2, 0),
+                                             (3, 4, 1, 1, 1), (2, 6, 1, 1, 1), (3, 10, 1, 1, 1), (2, 2, 1, 1, 1),
+                                             (3, 8, 70, 1, 5)])
+def test_resident_mode_equals_oracle_and_eager(ianus, dim, L, S, R, every):
+    """Resident modes against the oracle and the launch-per-colour path:
+    automatic, every configuration split over a block cluster (slabs along
+    the last axis, faces read from the neighbouring block's shared memory;
+    L = 2 and one-plane slabs make both faces remote; E and M carried by the
+    flips), one block per configuration, and off.  Many sweeps per launch,
+    series written in the kernel."""
     runs = []
-    for resident in (True, False):
-        lat = ianus.Lattice(dim=dim, L=L, n_samples=S, seed=SEED + 95, layout="i8", series_capacity=100)
+    for resident in (1, 3, 2, 0):
+        lat = ianus.Lattice(dim=dim, L=L, n_samples=S, n_replicas=R, seed=SEED + 95, layout="i8",
+                            series_capacity=100)
         lat.set_resident(resident)
         lat.sweep(METROPOLIS, 1.0 / 1.1, 40, measure_every=every)
         lat.sweep(HEATBATH, 0.8, 13, measure_every=every)
         runs.append((lat.spins(), lat.series()))
-    orc = Oracle(dim=dim, L=L, sample_ids=list(range(S)), seed=SEED + 95)
+    orc = Oracle(dim=dim, L=L, sample_ids=list(range(S)), n_replicas=R, seed=SEED + 95)
     orc.sweep(METROPOLIS, 1.0 / 1.1, 40, measure_every=every)
     orc.sweep(HEATBATH, 0.8, 13, measure_every=every)
     for sp, (sw, E, M, _) in runs:
         assert np.array_equal(sp, orc.spins())
         swo, Eo, Mo, _ = orc.series()
         assert np.array_equal(sw, swo) and np.array_equal(E, Eo) and np.array_equal(M, Mo)
+
+
+def test_resident_mode_values(ianus):
+    lat = ianus.Lattice(dim=3, L=4, seed=1, layout="i8")
+    for bad in (-1, 4):
+        with pytest.raises(ianus.IanusError) as e:
+            lat.set_resident(bad)
+        assert e.value.status == ianus.EINVAL
