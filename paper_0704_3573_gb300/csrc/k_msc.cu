@@ -792,19 +792,18 @@ __global__ void k_build_field_planes(uint64_t* ftp, const uint64_t* fthr, const 
   }
 }
 
-// ---- measurements: per-lane column sums by warp bit-transposes ----
+// ---- measurements: per-lane counts by vertical counters and warp bit-transposes ----
 //
-// A warp holds 32 site words, one per thread.  For a 64-bit quantity per
-// word (bits of the unsatisfied forward bonds, the spin-down bits, the
-// disagreement bits of two replicas), transposing the low and the high 32x32
-// halves across the warp leaves in thread t the bits of sample lanes t and
-// 32 + t of all 32 words, so a popcount gives each lane's count over those
-// sites.  The D forward bonds of a site are first added into a 2-bit number
-// (sum and carry words, weights 1 and 2).  Each thread keeps the running
-// totals of its two lanes; at the end the block sums its warps in shared
-// memory and adds one value per lane and quantity to the accumulators.
-// Per site and configuration this gives U (E = 2U - D N), B (M = N - 2B) and
-// X (Q = N - 2X).
+// Each thread adds the 64-bit words of its sites (bits of the unsatisfied
+// forward bonds as a 2-bit number, the spin-down bits, the disagreement bits
+// of two replicas) into per-lane counters held as bit-planes (LaneCounter),
+// up to kMeasChunk words at a time.  A flush transposes each plane's low and
+// high 32x32 halves across the warp, which leaves in thread t the plane bits
+// of sample lanes t and 32 + t of all 32 threads, so a popcount weighted by
+// the plane gives each lane's count over the warp's sites.  At the end the
+// block sums its warps in shared memory and adds one value per lane and
+// quantity to the accumulators.  Per site and configuration this gives U
+// (E = 2U - D N), B (M = N - 2B) and X (Q = N - 2X).
 
 constexpr int kMeasWarps = kBlock / 32;
 constexpr int kMeasMaxQ = 7;  // quantities per block: U and B of two replicas, X, field F
@@ -823,12 +822,54 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t x) {
   return x;
 }
 
-// Adds the per-lane column counts of w (weight 2^shift) over the warp's 32
-// words to the totals of lanes (t, 32 + t).
-__device__ __forceinline__ void col_add(uint64_t w, int shift, long long& lo, long long& hi) {
-  lo += (long long)__popc(warp_transpose32((uint32_t)w)) << shift;
-  hi += (long long)__popc(warp_transpose32((uint32_t)(w >> 32))) << shift;
-}
+// Per-lane counts held vertically across a thread's words: plane b has bit
+// l set when bit b of lane l's count is set.  add1 adds 0/1 per lane, add2 a
+// 2-bit number (s + 2 cy) per lane, both as ripple-carry adders over the
+// planes; flush adds the warp's per-lane totals (lanes t and 32 + t in
+// thread t) by one transpose per plane and half, and clears the counter.
+// A counter of K planes holds up to 2^K - 1, which bounds the words a
+// thread may add between flushes (kMeasChunk).
+template <int K>
+struct LaneCounter {
+  uint64_t c[K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int b = 0; b < K; ++b) c[b] = 0;
+  }
+  __device__ __forceinline__ void add1(uint64_t x) {
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      const uint64_t t = c[b] & x;
+      c[b] ^= x;
+      x = t;
+    }
+  }
+  __device__ __forceinline__ void add2(uint64_t s, uint64_t cy) {
+    const uint64_t t0 = c[0] & s;
+    c[0] ^= s;
+    uint64_t x = (c[1] & t0) | (c[1] & cy) | (t0 & cy);
+    c[1] ^= t0 ^ cy;
+#pragma unroll
+    for (int b = 2; b < K; ++b) {
+      const uint64_t t = c[b] & x;
+      c[b] ^= x;
+      x = t;
+    }
+  }
+  __device__ __forceinline__ void flush(int shift, long long sign, long long& lo, long long& hi) {
+#pragma unroll
+    for (int b = 0; b < K; ++b) {
+      lo += sign * ((long long)__popc(warp_transpose32((uint32_t)c[b])) << (shift + b));
+      hi += sign * ((long long)__popc(warp_transpose32((uint32_t)(c[b] >> 32))) << (shift + b));
+      c[b] = 0;
+    }
+  }
+};
+
+// Words a thread adds between flushes: 21 words of up to 3 (a site's
+// forward bonds) fit 6 planes, of up to 1 fit 5.
+constexpr int kMeasChunk = 21;
+constexpr int kPlanesBond = 6, kPlanesBit = 5;
 
 // Split index j -> split indices of the forward neighbours x+1, y+1, z+1.
 struct Fwd {
@@ -898,7 +939,7 @@ __device__ __forceinline__ void block_flush(long long (*red)[64], const long lon
 // One temperature (slot = replica): U and B of every replica and, with two
 // replicas, X, in one pass.  Grid (chunks, groups).
 template <int D, int R, bool P2>
-__global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __restrict__ spins,
+__global__ void __launch_bounds__(kBlock, 2) k_measure_bits_k1(const uint64_t* __restrict__ spins,
                                                             const uint64_t* __restrict__ J, int64_t* acc, Geom geom,
                                                             int S) {
   __shared__ long long red[kMeasWarps * kMeasMaxQ][64];
@@ -910,30 +951,41 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits_k1(const uint64_t* __re
   long long tot[NQ][2];
 #pragma unroll
   for (int q = 0; q < NQ; ++q) tot[q][0] = tot[q][1] = 0;
+  LaneCounter<kPlanesBond> cu[R];
+  LaneCounter<kPlanesBit> cb[R], cx;
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    cu[a].zero();
+    cb[a].zero();
+  }
+  cx.zero();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * kBlock;
-  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
-    const uint32_t j = base + lane;
-    uint64_t bw[R], s1[R], c1[R];
-#pragma unroll
-    for (int a = 0; a < R; ++a) bw[a] = s1[a] = c1[a] = 0;
-    if (j < N) {
+  uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u);  // uniform across the warp
+  while (base < N) {
+    for (int n = 0; n < kMeasChunk && base < N; ++n, base += stride) {
+      const uint32_t j = base + lane;
+      if (j >= N) continue;
       const Fwd f = split_forward<P2>(geom, j);
       const uint64_t Jx = Jg[j], Jy = Jg[N + j], Jz = D == 3 ? Jg[2u * N + j] : 0ull;
+      uint64_t bw[R];
 #pragma unroll
       for (int a = 0; a < R; ++a) {
         const uint64_t* sp = sg + (size_t)a * N;
+        uint64_t s1, c1;
         bw[a] = sp[j];
-        bond_count<D>(bw[a], sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jx, Jy, Jz, s1[a], c1[a]);
+        bond_count<D>(bw[a], sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jx, Jy, Jz, s1, c1);
+        cu[a].add2(s1, c1);
+        cb[a].add1(bw[a]);
       }
+      if (R == 2) cx.add1(bw[0] ^ bw[R - 1]);
     }
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-      col_add(s1[a], 0, tot[2 * a][0], tot[2 * a][1]);
-      col_add(c1[a], 1, tot[2 * a][0], tot[2 * a][1]);
-      col_add(bw[a], 0, tot[2 * a + 1][0], tot[2 * a + 1][1]);
+      cu[a].flush(0, 1, tot[2 * a][0], tot[2 * a][1]);
+      cb[a].flush(0, 1, tot[2 * a + 1][0], tot[2 * a + 1][1]);
     }
-    if (R == 2) col_add(bw[0] ^ bw[R - 1], 0, tot[NQ - 1][0], tot[NQ - 1][1]);
+    if (R == 2) cx.flush(0, 1, tot[NQ - 1][0], tot[NQ - 1][1]);
   }
   int row_off[NQ], field[NQ];
 #pragma unroll
@@ -962,20 +1014,27 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
   const uint64_t* Jg = J + (size_t)g * D * N;
   const uint64_t* sp = spins + ((size_t)g * slots + sigma) * N;
   long long tot[2][2] = {{0, 0}, {0, 0}};
+  LaneCounter<kPlanesBond> cu;
+  LaneCounter<kPlanesBit> cb;
+  cu.zero();
+  cb.zero();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * kBlock;
-  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
-    const uint32_t j = base + lane;
-    uint64_t bw = 0, s1 = 0, c1 = 0;
-    if (j < N) {
+  uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u);  // uniform across the warp
+  while (base < N) {
+    for (int n = 0; n < kMeasChunk && base < N; ++n, base += stride) {
+      const uint32_t j = base + lane;
+      if (j >= N) continue;
       const Fwd f = split_forward<P2>(geom, j);
-      bw = sp[j];
+      const uint64_t bw = sp[j];
+      uint64_t s1, c1;
       bond_count<D>(bw, sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jg[j], Jg[N + j], D == 3 ? Jg[2u * N + j] : 0ull,
                     s1, c1);
+      cu.add2(s1, c1);
+      cb.add1(bw);
     }
-    col_add(s1, 0, tot[0][0], tot[0][1]);
-    col_add(c1, 1, tot[0][0], tot[0][1]);
-    col_add(bw, 0, tot[1][0], tot[1][1]);
+    cu.flush(0, 1, tot[0][0], tot[0][1]);
+    cb.flush(0, 1, tot[1][0], tot[1][1]);
   }
   const int row_off[2] = {sigma, sigma}, field[2] = {0, 1};
   block_flush(red, tot, 2, g, S, acc, row_off, field, slots);
@@ -986,11 +1045,6 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
 // 2 U - O with U, O the per-site counts of occupied unsatisfied and occupied
 // bonds (each a 2-bit sum); M = sum x s = X - 2 sum x b and F = sum sign(h)
 // x s = X - 2 sum x (b ^ hb), X = sum x.  acc[0..2] = E_J, M, F.
-__device__ __forceinline__ void col_signed(uint64_t w, int shift, long long sign, long long& lo, long long& hi) {
-  lo += sign * ((long long)__popc(warp_transpose32((uint32_t)w)) << shift);
-  hi += sign * ((long long)__popc(warp_transpose32((uint32_t)(w >> 32))) << shift);
-}
-
 template <int D, bool P2>
 __global__ void __launch_bounds__(kBlock) k_measure_field_bits(const uint64_t* __restrict__ spins,
                                                                const uint64_t* __restrict__ J,
@@ -1006,37 +1060,45 @@ __global__ void __launch_bounds__(kBlock) k_measure_field_bits(const uint64_t* _
   const uint64_t* Hg = hbits + (size_t)g * N;
   const uint64_t* Xg = xbits + (size_t)g * N;
   long long tot[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+  // U: occupied unsatisfied forward bonds, O: occupied forward bonds,
+  // X: occupied sites, XB: occupied down spins, XF: occupied against the field
+  LaneCounter<kPlanesBond> cuu, coo;
+  LaneCounter<kPlanesBit> cxs, cxb, cxf;
+  cuu.zero();
+  coo.zero();
+  cxs.zero();
+  cxb.zero();
+  cxf.zero();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * kBlock;
-  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
-    const uint32_t j = base + lane;
-    uint64_t s1 = 0, c1 = 0, s2 = 0, c2 = 0, xs = 0, xb = 0, xf = 0;
-    if (j < N) {
+  uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u);  // uniform across the warp
+  while (base < N) {
+    for (int n = 0; n < kMeasChunk && base < N; ++n, base += stride) {
+      const uint32_t j = base + lane;
+      if (j >= N) continue;
       const Fwd f = split_forward<P2>(geom, j);
       const uint64_t b = sp[j];
-      xs = Xg[j];
+      const uint64_t xs = Xg[j];
       const uint64_t ox = xs & Xg[f.x], oy = xs & Xg[f.y], oz = D == 3 ? xs & Xg[f.z] : 0ull;
       const uint64_t ux = ox & (b ^ sp[f.x] ^ Jg[j]), uy = oy & (b ^ sp[f.y] ^ Jg[N + j]);
       const uint64_t uz = D == 3 ? oz & (b ^ sp[f.z] ^ Jg[2u * N + j]) : 0ull;
-      s1 = ux ^ uy ^ uz;
-      c1 = (ux & uy) | (ux & uz) | (uy & uz);
-      s2 = ox ^ oy ^ oz;
-      c2 = (ox & oy) | (ox & oz) | (oy & oz);
-      xb = xs & b;
-      xf = xs & (b ^ Hg[j]);
+      cuu.add2(ux ^ uy ^ uz, (ux & uy) | (ux & uz) | (uy & uz));
+      coo.add2(ox ^ oy ^ oz, (ox & oy) | (ox & oz) | (oy & oz));
+      cxs.add1(xs);
+      cxb.add1(xs & b);
+      cxf.add1(xs & (b ^ Hg[j]));
     }
-    col_signed(s1, 1, 1, tot[0][0], tot[0][1]);
-    col_signed(c1, 2, 1, tot[0][0], tot[0][1]);
-    col_signed(s2, 0, -1, tot[0][0], tot[0][1]);
-    col_signed(c2, 1, -1, tot[0][0], tot[0][1]);
+    // E_J = 2U - O, M = X - 2 XB, F = X - 2 XF
+    cuu.flush(1, 1, tot[0][0], tot[0][1]);
+    coo.flush(0, -1, tot[0][0], tot[0][1]);
     long long xl = 0, xh = 0;
-    col_signed(xs, 0, 1, xl, xh);
+    cxs.flush(0, 1, xl, xh);
     tot[1][0] += xl;
     tot[1][1] += xh;
     tot[2][0] += xl;
     tot[2][1] += xh;
-    col_signed(xb, 1, -1, tot[1][0], tot[1][1]);
-    col_signed(xf, 1, -1, tot[2][0], tot[2][1]);
+    cxb.flush(1, -1, tot[1][0], tot[1][1]);
+    cxf.flush(1, -1, tot[2][0], tot[2][1]);
   }
   const int row_off[3] = {sigma, sigma, sigma}, field[3] = {0, 1, 2};
   block_flush(red, tot, 3, g, S, acc, row_off, field, slots);
@@ -1071,24 +1133,35 @@ __global__ void __launch_bounds__(kBlock) k_overlap_bits(const uint64_t* __restr
   __syncthreads();
   const uint64_t* sg = spins + (size_t)g * slots * N;
   long long tot[1][2] = {{0, 0}};
+  LaneCounter<kPlanesBit> cd, cw;  // disagreements (occupied), occupied sites
+  cd.zero();
+  cw.zero();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t stride = gridDim.x * kBlock;
-  for (uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u); base < N; base += stride) {
-    const uint32_t j = base + lane;
-    uint64_t w0 = 0, w1 = 0, xw = 0;
-    if (j < N) {
+  uint32_t base = blockIdx.x * kBlock + (threadIdx.x & ~31u);  // uniform across the warp
+  while (base < N) {
+    for (int n = 0; n < kMeasChunk && base < N; ++n, base += stride) {
+      const uint32_t j = base + lane;
+      if (j >= N) continue;
+      uint64_t w0 = 0, w1 = 0;
       for (int t = 0; t < K; ++t) {
         const uint64_t m0 = sel[t], m1 = sel[K + t];
         if (m0) w0 |= m0 & sg[((size_t)t * R + 0) * N + j];
         if (m1) w1 |= m1 & sg[((size_t)t * R + 1) * N + j];
       }
-      if (xbits) xw = xbits[(size_t)g * N + j];
+      if (xbits) {
+        const uint64_t xw = xbits[(size_t)g * N + j];
+        cw.add1(xw);
+        cd.add1(xw & (w0 ^ w1));
+      } else {
+        cd.add1(w0 ^ w1);
+      }
     }
-    if (xbits) {
-      col_signed(xw, 0, 1, tot[0][0], tot[0][1]);
-      col_signed(xw & (w0 ^ w1), 1, -1, tot[0][0], tot[0][1]);
+    if (xbits) {  // Q = sum x (1 - 2 (w0 ^ w1))
+      cw.flush(0, 1, tot[0][0], tot[0][1]);
+      cd.flush(1, -1, tot[0][0], tot[0][1]);
     } else {
-      col_add(w0 ^ w1, 0, tot[0][0], tot[0][1]);
+      cd.flush(0, 1, tot[0][0], tot[0][1]);
     }
   }
   const int row_off[1] = {k * R}, field[1] = {6};
