@@ -420,8 +420,9 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
 
 /* Launch shape of the bit-sliced sweep: colour words handled by one block of
- * 256 threads (rounded up to a multiple of 256); 0 restores the default,
- * which sizes the grid to about 8 blocks per SM.  EINVAL above 2^24. */
+ * 256 threads (rounded up to a multiple of 32, whole warps); 0 restores the
+ * default, a multiple of 256 that sizes the grid to about 8 blocks per SM.
+ * EINVAL above 2^24. */
 ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
 
 /* Sweep blocks through CUDA graphs (default on): runs of at least 4 sweeps

@@ -164,7 +164,7 @@ struct BitsParams {
   int G, R, K, slots;
   int colour;
   uint32_t t_lo, t_hi;
-  uint32_t words_per_block;  // colour-c words handled by one block (multiple of the block size)
+  uint32_t words_per_block;  // colour-c words handled by one block (a multiple of 32)
   PhiloxKeys keys;
   const uint64_t* t_dev;     // non-null in captured graphs: sweep = *t_dev + t_lo
 };

@@ -1460,9 +1460,14 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   const uint32_t half = lat.geom.half;
   const uint32_t gts = (uint32_t)(lat.G * lat.K);
   uint32_t target_blocks = (152u * 8u + gts - 1) / gts;
-  uint32_t wpb = lat.block_words ? lat.block_words : (half + target_blocks - 1) / target_blocks;
-  wpb = ((wpb + kBlock - 1) / kBlock) * kBlock;
-  if (wpb < (uint32_t)kBlock) wpb = kBlock;
+  uint32_t wpb;
+  if (lat.block_words) {  // explicit shape: whole warps
+    wpb = (lat.block_words + 31u) / 32u * 32u;
+  } else {
+    wpb = (half + target_blocks - 1) / target_blocks;
+    wpb = ((wpb + kBlock - 1) / kBlock) * kBlock;
+    if (wpb < (uint32_t)kBlock) wpb = kBlock;
+  }
   p.words_per_block = wpb;
   dim3 grid((half + wpb - 1) / wpb, gts);
   const size_t smem = (size_t)lat.R * kPlanes * kMaxClasses * sizeof(uint64_t);

@@ -312,9 +312,10 @@ def test_potts_L32_128x2_full_size_sampled(ianus):
 @pytest.mark.parametrize("variant", list(range(1, 20)))
 def test_every_variant_and_launch_shape_is_bit_exact(ianus, variant):
     """All kernel variants and several launch shapes give the same
-    trajectory (L=16: several blocks per (group, slot), ragged last block)."""
+    trajectory (L=16: several blocks per (group, slot), ragged last block;
+    shapes of whole warps that leave part of a block idle)."""
     ref = None
-    for bw in (0, 256, 768):
+    for bw in (0, 256, 768, 96, 480):
         lat = ianus.Lattice(dim=3, L=16, n_samples=100, n_replicas=2, seed=SEED + 77, layout="bits64")
         lat.set_variant(variant)
         lat.set_block_words(bw)
