@@ -66,6 +66,25 @@ struct LazyWord {
   uint64_t u0, u1, u2, und, lt;
 };
 
+// Threshold bit-plane of the lanes' classes: row[u] selected by the class
+// bits (u2 u1 u0) with a tree of bitwise multiplexers (x ? a : b is one
+// lop3).  Only undecided lanes use the result, and their classes take a
+// random: u < D for Metropolis (so u2 = 0, and u1 = 0 in 2D), u <= 2D for the
+// heat bath (u = 7 never occurs, so class 6 needs no partner).
+template <int D, int ALGO>
+__device__ __forceinline__ uint64_t class_select(const uint64_t* row, uint64_t u0, uint64_t u1, uint64_t u2) {
+  auto mux = [](uint64_t x, uint64_t a, uint64_t b) { return (x & a) | (~x & b); };
+  if (ALGO == 0) {
+    const uint64_t t01 = mux(u0, row[1], row[0]);
+    return D == 3 ? mux(u1, row[2], t01) : t01;
+  }
+  const uint64_t a = mux(u0, row[1], row[0]), b = mux(u0, row[3], row[2]);
+  const uint64_t lo = mux(u1, b, a);
+  if (D == 2) return mux(u2, row[4], lo);
+  const uint64_t c = mux(u0, row[5], row[4]);
+  return mux(u2, mux(u1, row[6], c), lo);
+}
+
 // Plane pairs mm0, mm0 + 1, ... (below mm_end) of one word against the
 // per-lane planes tpa, two Philox blocks at a time (two independent round
 // chains in flight); stops when every lane is decided.
@@ -73,11 +92,6 @@ template <int D, int ALGO>
 __device__ __forceinline__ void bits_plane_pairs(LazyWord& w, const uint64_t* tpa, const BitsParams& p,
                                                  const Tick& tk, uint32_t site, uint32_t c2, uint32_t mm0,
                                                  uint32_t mm_end) {
-  constexpr int NC = (ALGO == 0) ? D : 2 * D + 1;  // classes that take a random
-  uint64_t m[NC];
-#pragma unroll
-  for (int u = 0; u < NC; ++u)
-    m[u] = ((u & 4) ? w.u2 : ~w.u2) & ((u & 2) ? w.u1 : ~w.u1) & ((u & 1) ? w.u0 : ~w.u0);
   uint64_t und = w.und, lt = w.lt;
 #pragma unroll 1
   for (uint32_t mm = mm0; mm < mm_end && und != 0ull; mm += 2u) {
@@ -88,10 +102,7 @@ __device__ __forceinline__ void bits_plane_pairs(LazyWord& w, const uint64_t* tp
       const uint4& x = q < 2 ? xa : xb;
       const uint64_t r = (q & 1) == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
                                       : ((uint64_t)x.z | ((uint64_t)x.w << 32));
-      const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * kMaxClasses;
-      uint64_t tb = 0;
-#pragma unroll
-      for (int u = 0; u < NC; ++u) tb |= m[u] & row[u];
+      const uint64_t tb = class_select<D, ALGO>(tpa + (2u * mm + (uint32_t)q) * kMaxClasses, w.u0, w.u1, w.u2);
       lt |= und & ~r & tb;
       und &= ~(r ^ tb);
     }
