@@ -430,10 +430,12 @@ def run_other_configs(args):
     sec = timed(lambda: pt.sweep_pt(ianus.METROPOLIS, beta, 100, swap_every=10), reps)
     upd = 64 * 2 * K * 32 ** 3 * 100 * reps
     rate = upd / (sec * 1e9)
-    # per-lane-plane kernel, 3D Metropolis: e-words 12, adder tree 16, class /
-    # always / need masks 10, per plane 3 class selections (6) + compare (4),
-    # per pair Philox 21 ALU + merge 2; ~3.9 plane pairs per word
-    alu_word = 38 + 3.9 * (2 * 10 + 23)
+    # per-lane-plane kernel, 3D Metropolis: e-words 12, adder tree 16, the
+    # "always" plane by a 6-multiplexer tree over the class bits (12) and the
+    # need / undecided masks (4); per plane the threshold bit by 2
+    # multiplexers (4) + compare (4), per pair Philox 21 ALU + merge 2;
+    # ~3.9 plane pairs per word
+    alu_word = 44 + 3.9 * (2 * 8 + 23)
     peak = _alu_peak()
     out["L32_pt_32temps"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,

@@ -120,14 +120,10 @@ __device__ __forceinline__ LazyWord bits_word_start(const uint64_t* tpa, uint64_
   w.u0 = u0;
   w.u1 = u1;
   w.u2 = u2;
-  uint64_t always = 0, need = 0;
-#pragma unroll
-  for (int u = 0; u <= 2 * D; ++u) {
-    const uint64_t m = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
-    always |= m & tpa[32 * kMaxClasses + u];
-    if (u < D) need |= m;
-  }
+  const uint64_t always = class_select<D, 1>(tpa + 32 * kMaxClasses, u0, u1, u2);
   w.lt = always;
+  // Metropolis: u < D draws (3D: u2 = 0 and not u = 3; 2D: u2 = u1 = 0)
+  const uint64_t need = D == 3 ? ~u2 & ~(u1 & u0) : ~u2 & ~u1;
   w.und = (ALGO == 0) ? (~always & need) : ~always;
   return w;
 }
@@ -653,13 +649,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep_fused(const BitsParams p, cons
     }
     uint64_t u0, u1, u2;
     count_unsat<D>(e, u0, u1, u2);
-    uint64_t m[2 * D + 1];
-#pragma unroll
-    for (int u = 0; u <= 2 * D; ++u)
-      m[u] = ((u & 4) ? u2 : ~u2) & ((u & 2) ? u1 : ~u1) & ((u & 1) ? u0 : ~u0);
-    uint64_t always = 0;
-#pragma unroll
-    for (int u = 0; u <= 2 * D; ++u) always |= m[u] & tpa[32 * kMaxClasses + u];
+    // a segment's lanes may hold either algorithm's planes: select over all classes
+    const uint64_t always = class_select<D, 1>(tpa + 32 * kMaxClasses, u0, u1, u2);
     uint64_t lt = always;
     uint64_t und = ~always & live;
 #pragma unroll 1
@@ -677,10 +668,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_fused(const BitsParams p, cons
 #pragma unroll
       for (int q = 0; q < 2; ++q) {
         const uint64_t r = q == 0 ? r0 : r1;
-        const uint64_t* row = tpa + (2u * mm + (uint32_t)q) * kMaxClasses;
-        uint64_t tb = 0;
-#pragma unroll
-        for (int u = 0; u <= 2 * D; ++u) tb |= m[u] & row[u];
+        const uint64_t tb = class_select<D, 1>(tpa + (2u * mm + (uint32_t)q) * kMaxClasses, u0, u1, u2);
         lt |= und & ~r & tb;
         und &= ~(r ^ tb);
       }
