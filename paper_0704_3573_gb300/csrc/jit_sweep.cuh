@@ -26,6 +26,16 @@ constexpr uint32_t kLut[32] = {IANUS_JIT_LUTS};
 constexpr uint32_t kAlways = IANUS_JIT_ALWAYS;
 constexpr uint32_t kNeed = IANUS_JIT_NEED;
 constexpr int kBlock = 256;
+// IANUS_JIT_L, IANUS_JIT_LH, IANUS_JIT_LL: the lattice side and the base-2
+// logarithms of L/2 and L (0 when L is not a power of two).  The kernel runs
+// at one temperature (n_temps = 1, so slots = R); with the geometry fixed at
+// compile time the index arithmetic folds, and the replicas' words of a
+// site, N words apart, are reached by constant offsets from one address.
+#ifdef IANUS_JIT_L
+constexpr uint32_t kNsites = D == 3 ? (uint32_t)IANUS_JIT_L * IANUS_JIT_L * IANUS_JIT_L
+                                    : (uint32_t)IANUS_JIT_L * IANUS_JIT_L;
+constexpr Geom kGeom = {D, IANUS_JIT_L, IANUS_JIT_L / 2, kNsites, kNsites / 2, IANUS_JIT_LH, IANUS_JIT_LL};
+#endif
 // IANUS_JIT_MODE 0: all plane pairs in lockstep across the warp (pairs
 // 0..7 with immediate tables, then run-time tables); 1: pairs 0..PHASEA-1 in
 // lockstep, then a per-warp queue (below); 2 (two replicas): as 0, with the
@@ -192,6 +202,7 @@ struct Ctx {
   int g, tslot;
   const uint8_t* lut;  // shared-memory copy of the 32 tables
   Tick tk;
+  uint64_t* sp0;       // spins of the block's first replica; replica a is a * N further
 };
 
 __device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
@@ -199,9 +210,16 @@ __device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
   return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
 }
 
+__device__ __forceinline__ uint32_t sites_of(const BitsParams& p) {
+#ifdef IANUS_JIT_L
+  return kNsites;
+#else
+  return p.geom.N;
+#endif
+}
+
 __device__ __forceinline__ void finish(const Ctx& c, uint32_t self, uint32_t a, const Word& w) {
-  const BitsParams& p = *c.p;
-  uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R) + a) * p.geom.N;
+  uint64_t* sp = c.sp0 + (uint64_t)a * sites_of(*c.p);
   const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
   if (flip) sp[self] ^= flip;
 }
@@ -268,13 +286,22 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
   uint32_t nq = 0;
   Ctx c;
   c.p = &p;
+#ifdef IANUS_JIT_L
+  constexpr Geom geom = kGeom;
+  c.g = blockIdx.y;  // one temperature: blockIdx.y = g
+  c.tslot = 0;
+  constexpr uint64_t slots = R;
+#else
   const int gt = blockIdx.y;  // g * K + tslot
   c.g = gt / p.K;
   c.tslot = gt - c.g * p.K;
+  const Geom geom = p.geom;
+  const uint64_t slots = (uint64_t)p.slots;
+#endif
   c.lut = s_lut;
   c.tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
-  const Geom geom = p.geom;
   const uint32_t N = geom.N;
+  c.sp0 = p.spins + ((uint64_t)c.g * slots + (uint64_t)(c.tslot * R)) * N;
   const uint64_t* Jg = p.J + (uint64_t)c.g * D * N;
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
@@ -301,7 +328,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
       Word wa[2];
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
-        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t* sp = c.sp0 + (uint64_t)a * N;
         const uint64_t b = sp[n.self];
         uint64_t e[2 * D];
         e[0] = b ^ sp[n.xp] ^ jw[0];
@@ -328,7 +355,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
     if (kUFirst && valid) {
 #pragma unroll
       for (int a = 0; a < R; ++a) {
-        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t* sp = c.sp0 + (uint64_t)a * N;
         const uint64_t b = sp[n.self];
         uint64_t e[2 * D];
         e[0] = b ^ sp[n.xp] ^ jw[0];
@@ -354,7 +381,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
         w.u1 = uu[a][1];
         w.u2 = uu[a][2];
       } else if (valid) {
-        const uint64_t* sp = p.spins + ((uint64_t)c.g * p.slots + (uint64_t)(c.tslot * R + a)) * N;
+        const uint64_t* sp = c.sp0 + (uint64_t)a * N;
         const uint64_t b = sp[n.self];
         uint64_t e[2 * D];
         if (kJReload) {  // coupling words from L1 again for each replica: none held across the plane loop
