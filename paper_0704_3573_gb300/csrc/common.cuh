@@ -95,6 +95,16 @@ struct Geom {
   int lh, lL;     // log2(h), log2(L) when L is a power of two (else 0)
 };
 
+#ifdef IANUS_JIT_L
+// Kernels compiled at run time for one lattice get its geometry as constants
+// (IANUS_JIT_D, IANUS_JIT_L, and IANUS_JIT_LH, IANUS_JIT_LL as above), so
+// that the index arithmetic folds and words N apart are constant offsets.
+constexpr uint32_t kJitSites = IANUS_JIT_D == 3 ? (uint32_t)IANUS_JIT_L * IANUS_JIT_L * IANUS_JIT_L
+                                                : (uint32_t)IANUS_JIT_L * IANUS_JIT_L;
+constexpr Geom kJitGeom = {IANUS_JIT_D, IANUS_JIT_L, IANUS_JIT_L / 2, kJitSites, kJitSites / 2, IANUS_JIT_LH,
+                           IANUS_JIT_LL};
+#endif
+
 __host__ __device__ __forceinline__ uint32_t split_index(const Geom& g, int x, int y, int z) {
   const int c = (x + y + z) & 1;
   const uint32_t row = (uint32_t)y + (uint32_t)g.L * (uint32_t)z;

@@ -139,15 +139,22 @@ extern "C" __global__ void __launch_bounds__(ianus::jitf::kBlock, IANUS_JIT_MINB
   __shared__ uint8_t s_lut[128];
   if (threadIdx.x < 128) s_lut[threadIdx.x] = lut_t[threadIdx.x];
   __syncthreads();
+#ifdef IANUS_JIT_L
+  constexpr Geom geom = kJitGeom;
+  const int g = blockIdx.y, tslot = 0;  // one temperature
+  constexpr uint64_t slots = R;
+#else
   const int gt = blockIdx.y;  // g * K + tslot (K = 1)
   const int g = gt / p.K, tslot = gt - g * p.K;
-  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const Geom geom = p.geom;
+  const uint64_t slots = (uint64_t)p.slots;
+#endif
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const uint32_t N = geom.N;
   const uint64_t* Jg = p.J + (uint64_t)g * D * N;
   const uint64_t* Hg = hbits + (uint64_t)g * N;
   const uint64_t* Xg = xbits + (uint64_t)g * N;
-  uint64_t* s0 = p.spins + ((uint64_t)g * p.slots + (uint64_t)(tslot * R)) * N;
+  uint64_t* s0 = p.spins + ((uint64_t)g * slots + (uint64_t)(tslot * R)) * N;
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
   for (uint32_t wi = w_begin + threadIdx.x; wi < w_end; wi += kBlock) {

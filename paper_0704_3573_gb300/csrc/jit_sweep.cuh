@@ -31,11 +31,6 @@ constexpr int kBlock = 256;
 // at one temperature (n_temps = 1, so slots = R); with the geometry fixed at
 // compile time the index arithmetic folds, and the replicas' words of a
 // site, N words apart, are reached by constant offsets from one address.
-#ifdef IANUS_JIT_L
-constexpr uint32_t kNsites = D == 3 ? (uint32_t)IANUS_JIT_L * IANUS_JIT_L * IANUS_JIT_L
-                                    : (uint32_t)IANUS_JIT_L * IANUS_JIT_L;
-constexpr Geom kGeom = {D, IANUS_JIT_L, IANUS_JIT_L / 2, kNsites, kNsites / 2, IANUS_JIT_LH, IANUS_JIT_LL};
-#endif
 // IANUS_JIT_MODE 0: all plane pairs in lockstep across the warp (pairs
 // 0..7 with immediate tables, then run-time tables); 1: pairs 0..PHASEA-1 in
 // lockstep, then a per-warp queue (below); 2 (two replicas): as 0, with the
@@ -212,7 +207,7 @@ __device__ __forceinline__ uint32_t sigma_c2(const Ctx& c, uint32_t a) {
 
 __device__ __forceinline__ uint32_t sites_of(const BitsParams& p) {
 #ifdef IANUS_JIT_L
-  return kNsites;
+  return kJitSites;
 #else
   return p.geom.N;
 #endif
@@ -287,7 +282,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
   Ctx c;
   c.p = &p;
 #ifdef IANUS_JIT_L
-  constexpr Geom geom = kGeom;
+  constexpr Geom geom = kJitGeom;
   c.g = blockIdx.y;  // one temperature: blockIdx.y = g
   c.tslot = 0;
   constexpr uint64_t slots = R;
