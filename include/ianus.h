@@ -395,9 +395,11 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * and the sweep kernel can be specialised for them at run time (NVRTC, a
  * fraction of a second per new table set, cached per device).
  *   0 = automatic: the specialised lockstep kernel for lattices of >= 2^20
- *       site words, else the precompiled kernel with per-lane threshold
- *       bit-planes;
- *   1 = always the precompiled per-lane kernel;
+ *       site words, else the kernel with per-lane threshold bit-planes,
+ *       compiled at run time for the lattice's geometry (also with several
+ *       temperatures and for parallel tempering);
+ *   1 = always the precompiled per-lane kernel (geometry from the launch
+ *       parameters);
  *   2..9 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
  *       blocks per SM; 4..7 = a per-warp queue of the words still undecided
  *       after 4, 4, 3 or 5 lockstep plane pairs, finished 32 at a time, with
@@ -415,8 +417,9 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       before the first plane loop (all loads of a site in flight at once):
  *       the queue after 4 pairs with 3 blocks per SM, lockstep with 4 and
  *       with 3 blocks per SM.
- * If run-time compilation is unavailable, the precompiled kernel runs.
- * EINVAL for other values. */
+ * With several temperatures every variant but 1 uses the per-lane kernel
+ * compiled for the geometry.  If run-time compilation is unavailable, the
+ * precompiled kernel runs.  EINVAL for other values. */
 ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
 
 /* Launch shape of the bit-sliced sweep: colour words handled by one block of

@@ -502,6 +502,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->jit_algo = -1;
   lat->jit_variant = -1;
   lat->jitf_algo = -1;
+  lat->jitp[0] = lat->jitp[1] = nullptr;
+  lat->jitp_tried[0] = lat->jitp_tried[1] = false;
   lat->bytes = z.total;
   if (cfg->device_buffer) {
     if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {

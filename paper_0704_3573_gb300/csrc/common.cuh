@@ -24,6 +24,12 @@ namespace ianus {
 enum : uint32_t { TAG_SPIN = 1, TAG_J = 2, TAG_INIT = 3, TAG_POTTS = 4, TAG_PINIT = 5, TAG_PT = 6, TAG_H = 7, TAG_X = 8,
                    TAG_PERM = 9, TAG_WHEEL = 10 };
 
+// Per-lane threshold planes of the bit-sliced layout: per class u = 0..2D
+// (padded to 8), 32 bit-planes of the threshold, most significant first, and
+// the "always" mask (threshold 2^32).
+constexpr int kMaxClasses = 8;
+constexpr int kPlanes = 33;
+
 // Round keys of Philox4x32-10 for one seed: k[r] = key + r * (W0, W1) mod 2^32.
 // Passed by value inside kernel parameters so that the XOR with the round key
 // reads the constant bank.

@@ -21,6 +21,7 @@
 #include <cmath>
 
 #include "lattice.h"
+#include "sweep_planes.cuh"
 
 namespace ianus {
 
@@ -28,284 +29,14 @@ namespace {
 
 constexpr int kBlock = 256;
 
-// ALGO 0 = Metropolis (only classes u < D need a random number),
-// ALGO 1 = heat bath (all 2D+1 classes).
-//
-// The generic kernel below draws against per-lane threshold planes staged in
-// shared memory (every lane may be at its own temperature).  A warp's 32
-// words need different numbers of plane pairs; for the heat bath (~4 pairs a
-// word on average, ~6.5 for the slowest of 32) the lazy compare runs in two
-// phases: the first kPhaseA pairs in lockstep, then the words still
-// undecided go to a per-warp queue in shared memory, and whenever 32 are
-// queued the warp finishes them together.  Every word is written once, by
-// the lane that finishes it; a colour-c pass writes colour-c words only, so
-// the order of the writes does not matter.  Metropolis words need fewer
-// pairs (only the classes with dE > 0 draw), and there the queue's registers
-// cost more occupancy than it saves: each word runs to the end in place.
+using planes::bits_sweep_smem;
+using planes::class_select;
 
-constexpr int kWarpsPerBlock = kBlock / 32;
-constexpr uint32_t kQueue = 64;  // < 32 left + <= 32 pushed
-
-// Undecided words of one warp: class planes, lazy-compare state, where the
-// word goes and which replica (a) of the block it belongs to.
-struct WordQueue {
-  uint64_t u0[kQueue], u1[kQueue], u2[kQueue], und[kQueue], lt[kQueue];
-  uint32_t self[kQueue], site[kQueue], a[kQueue];
-};
-
-// Shared memory of the generic kernel: R replicas' threshold planes, then
-// the warps' queues (Q).
-inline size_t bits_sweep_smem(int R, bool Q = true) {
-  return (size_t)R * kPlanes * kMaxClasses * sizeof(uint64_t) + (Q ? kWarpsPerBlock * sizeof(WordQueue) : 0);
-}
-
-// Plane pairs before a heat-bath word can be queued.
-constexpr uint32_t kPhaseA = 4u;
-
-struct LazyWord {
-  uint64_t u0, u1, u2, und, lt;
-};
-
-// Threshold bit-plane of the lanes' classes: row[u] selected by the class
-// bits (u2 u1 u0) with a tree of bitwise multiplexers (x ? a : b is one
-// lop3).  Only undecided lanes use the result, and their classes take a
-// random: u < D for Metropolis (so u2 = 0, and u1 = 0 in 2D), u <= 2D for the
-// heat bath (u = 7 never occurs, so class 6 needs no partner).
-template <int D, int ALGO>
-__device__ __forceinline__ uint64_t class_select(const uint64_t* row, uint64_t u0, uint64_t u1, uint64_t u2) {
-  auto mux = [](uint64_t x, uint64_t a, uint64_t b) { return (x & a) | (~x & b); };
-  if (ALGO == 0) {
-    const uint64_t t01 = mux(u0, row[1], row[0]);
-    return D == 3 ? mux(u1, row[2], t01) : t01;
-  }
-  const uint64_t a = mux(u0, row[1], row[0]), b = mux(u0, row[3], row[2]);
-  const uint64_t lo = mux(u1, b, a);
-  if (D == 2) return mux(u2, row[4], lo);
-  const uint64_t c = mux(u0, row[5], row[4]);
-  return mux(u2, mux(u1, row[6], c), lo);
-}
-
-// Plane pairs mm0, mm0 + 1, ... (below mm_end) of one word against the
-// per-lane planes tpa, two Philox blocks at a time (two independent round
-// chains in flight); stops when every lane is decided.
-template <int D, int ALGO>
-__device__ __forceinline__ void bits_plane_pairs(LazyWord& w, const uint64_t* tpa, const BitsParams& p,
-                                                 const Tick& tk, uint32_t site, uint32_t c2, uint32_t mm0,
-                                                 uint32_t mm_end) {
-  uint64_t und = w.und, lt = w.lt;
-#pragma unroll 1
-  for (uint32_t mm = mm0; mm < mm_end && und != 0ull; mm += 2u) {
-    const uint4 xa = philox10(site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
-    const uint4 xb = philox10(site, tk.lo, c2 | ((mm + 1u) << 24), tk.hi, p.keys);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const uint4& x = q < 2 ? xa : xb;
-      const uint64_t r = (q & 1) == 0 ? ((uint64_t)x.x | ((uint64_t)x.y << 32))
-                                      : ((uint64_t)x.z | ((uint64_t)x.w << 32));
-      const uint64_t tb = class_select<D, ALGO>(tpa + (2u * mm + (uint32_t)q) * kMaxClasses, w.u0, w.u1, w.u2);
-      lt |= und & ~r & tb;
-      und &= ~(r ^ tb);
-    }
-  }
-  w.und = und;
-  w.lt = lt;
-}
-
-// Start of a word's lazy compare: lanes that always flip (threshold 2^32)
-// are decided, and for Metropolis so are the lanes with dE <= 0 (u >= D,
-// which are among them).
-template <int D, int ALGO>
-__device__ __forceinline__ LazyWord bits_word_start(const uint64_t* tpa, uint64_t u0, uint64_t u1, uint64_t u2) {
-  LazyWord w;
-  w.u0 = u0;
-  w.u1 = u1;
-  w.u2 = u2;
-  const uint64_t always = class_select<D, 1>(tpa + 32 * kMaxClasses, u0, u1, u2);
-  w.lt = always;
-  // Metropolis: u < D draws (3D: u2 = 0 and not u = 3; 2D: u2 = u1 = 0)
-  const uint64_t need = D == 3 ? ~u2 & ~(u1 & u0) : ~u2 & ~u1;
-  w.und = (ALGO == 0) ? (~always & need) : ~always;
-  return w;
-}
-
-// Class planes of one replica's word: the spin word b and the count of
-// unsatisfied bonds as bit-planes.
-template <int D>
-__device__ __forceinline__ void bits_class_planes(const uint64_t* sp, const Nbr& n, const uint64_t* jw, uint64_t& b,
-                                                  uint64_t& u0, uint64_t& u1, uint64_t& u2) {
-  b = sp[n.self];
-  uint64_t e[2 * D];
-  e[0] = b ^ sp[n.xp] ^ jw[0];
-  e[1] = b ^ sp[n.xm] ^ jw[1];
-  e[2] = b ^ sp[n.yp] ^ jw[2];
-  e[3] = b ^ sp[n.ym] ^ jw[3];
-  if (D == 3) {
-    e[4] = b ^ sp[n.zp] ^ jw[4];
-    e[5] = b ^ sp[n.zm] ^ jw[5];
-  }
-  count_unsat<D>(e, u0, u1, u2);
-}
-
-// Everything a word's update needs besides its own state.
-struct SweepCtx {
-  const BitsParams* p;
-  const uint64_t* tp;  // shared-memory planes of the block's replicas
-  uint64_t* sp0;       // spins of the block's first replica
-  Tick tk;
-  int g, tslot, R;
-};
-
-__device__ __forceinline__ uint32_t bits_c2(const SweepCtx& c, uint32_t a) {
-  const uint32_t sigma = (uint32_t)(c.tslot * c.R) + a;
-  return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
-}
-
-// Warp-wide append of the lanes with pred set; n is warp-uniform.
-__device__ __forceinline__ void queue_push(WordQueue& q, uint32_t& n, bool pred, const LazyWord& w, uint32_t self,
-                                           uint32_t site, uint32_t a) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t mk = __ballot_sync(0xffffffffu, pred);
-  if (pred) {
-    const uint32_t i = n + __popc(mk & ((1u << lane) - 1u));
-    q.u0[i] = w.u0;
-    q.u1[i] = w.u1;
-    q.u2[i] = w.u2;
-    q.und[i] = w.und;
-    q.lt[i] = w.lt;
-    q.self[i] = self;
-    q.site[i] = site;
-    q.a[i] = a;
-  }
-  n += __popc(mk);
-  __syncwarp();
-}
-
-// Finish the top `take` (<= 32) queued words: pairs kPhaseA.. to the end.
-template <int D, int ALGO>
-__device__ __forceinline__ void queue_round(WordQueue& q, uint32_t& n, uint32_t take, const SweepCtx& c) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const bool has = lane < take;
-  LazyWord w;
-  w.u0 = w.u1 = w.u2 = w.und = w.lt = 0;
-  uint32_t self = 0, site = 0, a = 0;
-  if (has) {
-    const uint32_t i = n - take + lane;
-    w.u0 = q.u0[i];
-    w.u1 = q.u1[i];
-    w.u2 = q.u2[i];
-    w.und = q.und[i];
-    w.lt = q.lt[i];
-    self = q.self[i];
-    site = q.site[i];
-    a = q.a[i];
-  }
-  __syncwarp();
-  n -= take;
-  if (has) {
-    bits_plane_pairs<D, ALGO>(w, c.tp + (size_t)a * kPlanes * kMaxClasses, *c.p, c.tk, site, bits_c2(c, a),
-                              kPhaseA, 16u);
-    uint64_t* sp = c.sp0 + (size_t)a * c.p->geom.N;
-    const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
-    if (flip) sp[self] ^= flip;
-  }
-}
-
-// Phase A of one replica's word, then either its write or its place in the
-// queue (Q); without the queue, all its plane pairs and its write.
-template <int D, int ALGO, bool Q>
-__device__ __forceinline__ void bits_update(WordQueue& q, uint32_t& nq, const SweepCtx& c, bool valid, const Nbr& n,
-                                            uint32_t a, uint64_t b, uint64_t u0, uint64_t u1, uint64_t u2) {
-  const uint64_t* tpa = c.tp + (size_t)a * kPlanes * kMaxClasses;
-  LazyWord w;
-  w.und = 0;
-  if (valid) {
-    w = bits_word_start<D, ALGO>(tpa, u0, u1, u2);
-    bits_plane_pairs<D, ALGO>(w, tpa, *c.p, c.tk, n.site, bits_c2(c, a), 0u, Q ? kPhaseA : 16u);
-  }
-  if (!Q) {
-    const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
-    if (valid && flip) c.sp0[(size_t)a * c.p->geom.N + n.self] = b ^ flip;
-    return;
-  }
-  const bool pend = valid && w.und != 0ull;
-  queue_push(q, nq, pend, w, valid ? n.self : 0u, valid ? n.site : 0u, a);
-  if (valid && !pend) {
-    const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
-    if (flip) c.sp0[(size_t)a * c.p->geom.N + n.self] = b ^ flip;
-  }
-  if (nq >= 32u) queue_round<D, ALGO>(q, nq, 32u, c);
-}
-
-// With a compile-time replica count RT, the class planes of every replica of
-// a word are computed before the first replica's update, so that all the
-// word's loads are in flight together; with RT = 0 the replicas go in turn.
+// The per-lane-plane sweep, precompiled (sweep_planes.cuh).
 template <int D, int ALGO, int RT, bool P2, bool Q = (ALGO == 1)>
 __global__ void __launch_bounds__(kBlock, Q ? 3 : 4) k_sweep_bits(const BitsParams p) {
-  extern __shared__ uint64_t sm_tp[];  // [R][kPlanes][kMaxClasses], then the queues
-  const int R = RT > 0 ? RT : p.R;
-  const int gt = blockIdx.y;  // g * K + tslot
-  const int g = gt / p.K, tslot = gt - g * p.K;
-  // stage this block's threshold planes
-  {
-    const uint64_t* src = p.tp + ((size_t)g * p.slots + (size_t)tslot * R) * kPlanes * kMaxClasses;
-    for (int k = threadIdx.x; k < R * kPlanes * kMaxClasses; k += kBlock) sm_tp[k] = src[k];
-  }
-  __syncthreads();
-  WordQueue& q = reinterpret_cast<WordQueue*>(sm_tp + (size_t)R * kPlanes * kMaxClasses)[threadIdx.x >> 5];
-  uint32_t nq = 0;
-  const Geom geom = p.geom;
-  const uint32_t N = geom.N;
-  const uint64_t* Jg = p.J + (size_t)g * D * N;
-  SweepCtx c;
-  c.p = &p;
-  c.tp = sm_tp;
-  c.sp0 = p.spins + ((size_t)g * p.slots + (size_t)tslot * R) * N;
-  c.tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
-  c.g = g;
-  c.tslot = tslot;
-  c.R = R;
-  const uint32_t w_begin = blockIdx.x * p.words_per_block;
-  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
-  for (uint32_t base = w_begin; base < w_end; base += kBlock) {  // uniform across the block
-    const uint32_t wi = base + threadIdx.x;
-    const bool valid = wi < w_end;
-    if (!Q && !valid) break;  // without the queue, threads need not stay together
-    Nbr n;
-    n.self = n.site = 0;
-    uint64_t jw[2 * D];
-    if (valid) {
-      n = split_neighbours_t<P2>(geom, p.colour, wi);
-      jw[0] = __ldg(Jg + n.self);
-      jw[1] = __ldg(Jg + n.xm);
-      jw[2] = __ldg(Jg + N + n.self);
-      jw[3] = __ldg(Jg + N + n.ym);
-      if (D == 3) {
-        jw[4] = __ldg(Jg + 2u * N + n.self);
-        jw[5] = __ldg(Jg + 2u * N + n.zm);
-      }
-    }
-    if (RT > 0) {
-      uint64_t b[RT > 0 ? RT : 1], u0[RT > 0 ? RT : 1], u1[RT > 0 ? RT : 1], u2[RT > 0 ? RT : 1];
-#pragma unroll
-      for (int a = 0; a < RT; ++a) {
-        b[a] = u0[a] = u1[a] = u2[a] = 0;
-        if (valid) bits_class_planes<D>(c.sp0 + (size_t)a * N, n, jw, b[a], u0[a], u1[a], u2[a]);
-      }
-#pragma unroll
-      for (int a = 0; a < RT; ++a)
-        bits_update<D, ALGO, Q>(q, nq, c, valid, n, (uint32_t)a, b[a], u0[a], u1[a], u2[a]);
-    } else {
-#pragma unroll 1
-      for (int a = 0; a < R; ++a) {
-        uint64_t b = 0, u0 = 0, u1 = 0, u2 = 0;
-        if (valid) bits_class_planes<D>(c.sp0 + (size_t)a * N, n, jw, b, u0, u1, u2);
-        bits_update<D, ALGO, Q>(q, nq, c, valid, n, (uint32_t)a, b, u0, u1, u2);
-      }
-    }
-  }
-  if (Q && nq > 0u) queue_round<D, ALGO>(q, nq, nq, c);
+  planes::sweep_planes_body<D, ALGO, RT, P2, Q>(p, p.geom);
 }
-
 
 // Random-field model (Eq. 2 with h_i = +-|h|, x_i = 1): the class of a lane
 // is (u, f) with f = [s_i h_i > 0] = ~(b_i ^ hb_i), hb_i = lane bit set
@@ -1342,12 +1073,19 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
     return;
   }
   const int v = jit_variant_for(lat);
-  if (v < 2) return;
-  if (lat.jit_algo != algo || lat.jit_variant != v) {
+  if (v >= 2 && (lat.jit_algo != algo || lat.jit_variant != v)) {
     const JitShape& js = kJitShapes[v - 2];
     lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst);
     lat.jit_algo = algo;
     lat.jit_variant = v;
+  }
+  // the per-lane planes (also the fallback of a failed specialisation),
+  // compiled for the geometry unless variant 1 asks for the precompiled kernel
+  if ((v < 2 || !lat.jit) && lat.variant != 1 && !lat.jitp_tried[algo]) {
+    const int rt = lat.R == 1 || lat.R == 2 ? lat.R : 0;
+    const bool q = algo == 1 && bits_sweep_smem(lat.R, true) <= 227u * 1024u;
+    lat.jitp[algo] = jit_planes_kernel(lat, algo, rt, q, q ? 3 : 4, (size_t)bits_sweep_smem(lat.R, q));
+    lat.jitp_tried[algo] = true;
   }
 }
 
@@ -1504,6 +1242,19 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
       void* args[] = {(void*)&p, (void*)&lut_t};
       return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, js.mode == 1 ? kJitSmemBytes : 0,
                               lat.stream);
+    }
+  }
+  // Per-lane planes: the kernel compiled for the lattice's geometry, else
+  // (variant 1, or no run-time compiler) the precompiled one.
+  if (lat.variant != 1) {
+    prepare_sweep_bits(lat, inv);
+    if (lat.jitp[algo]) {
+      const bool q = algo == 1 && bits_sweep_smem(lat.R, true) <= 227u * 1024u;
+      void* args[] = {(void*)&p};
+      const cudaError_t e = cudaLaunchKernel((const void*)lat.jitp[algo], grid, dim3(kBlock), args,
+                                             (size_t)bits_sweep_smem(lat.R, q), lat.stream);
+      if (e != cudaSuccess) cudaGetLastError();  // a refused launch leaves no pending error behind
+      return e;
     }
   }
   if (lat.D == 3)

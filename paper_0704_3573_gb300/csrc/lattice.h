@@ -14,8 +14,6 @@
 
 namespace ianus {
 
-constexpr int kMaxClasses = 8;   // u = 0..2D (7 in 3D), padded
-constexpr int kPlanes = 33;      // 32 threshold bit-planes + the "always" mask
 constexpr int kAccStride = 8;    // int64 accumulators per (sample, slot)
 constexpr uint64_t kTwo32 = 1ull << 32;
 // Field models (Eq. 2 with random fields or dilution): the I8 class of a site
@@ -142,6 +140,8 @@ struct Lattice {
   UniformLut ulut;           // valid when ulut_ok (n_temps == 1)
   bool ulut_ok;
   cudaKernel_t jit;          // sweep kernel specialised for ulut (null: use the per-lane planes)
+  cudaKernel_t jitp[2];      // per-lane-plane sweep compiled for the geometry, per algorithm (null: precompiled)
+  bool jitp_tried[2];
   int jit_algo;              // algorithm the specialisation was requested for; -1 = not yet
   int jit_variant;           // variant it was built for
   uint32_t block_words;      // words per block of the bit-sliced sweep; 0 = heuristic
@@ -182,6 +182,9 @@ constexpr int kMaxVariant = 19;  // ianus_set_variant accepts 0..kMaxVariant
 // Run-time specialised random-field sweep for lat.flut (jit.cu; null when
 // unavailable).
 cudaKernel_t jit_field_kernel(const Lattice& lat, int algo, int min_blocks);
+// The per-lane-plane sweep (sweep_planes.cuh) compiled for the lattice's
+// geometry: rt replicas at compile time (0: run time), per-warp queues.
+cudaKernel_t jit_planes_kernel(const Lattice& lat, int algo, int rt, bool queue, int min_blocks, size_t smem);
 
 // ---- launchers; each returns cudaGetLastError() of its launches ----
 // I8 (k_plain.cu)

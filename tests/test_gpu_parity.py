@@ -164,12 +164,35 @@ def test_potts_sweep_bit_exact(ianus, dim, L, S, R):
 
 
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
-@pytest.mark.parametrize("R,K", [(3, 3), (5, 2), (100, 2)])
+@pytest.mark.parametrize("dim,L,S,R,K", [(3, 6, 67, 2, 3), (2, 10, 5, 1, 4), (3, 8, 130, 3, 2), (2, 16, 64, 2, 2)])
+def test_per_lane_kernel_compiled_for_the_geometry(ianus, algo, dim, L, S, R, K):
+    """The per-lane-plane sweep compiled at run time for the lattice's
+    geometry (default) and the precompiled one (variant 1) against the
+    oracle, with swaps so that lanes sit at different temperatures; L not a
+    power of two, one and three replicas, ragged sample counts."""
+    beta = [1.0 / (0.8 + 0.7 * k / (K - 1)) for k in range(K)]
+    runs = []
+    for variant in (0, 1):
+        lat, orc, _ = _pair(ianus, dim=dim, L=L, S=S, R=R, K=K, layout="bits64", seed=SEED + 60 + L)
+        lat.set_variant(variant)
+        for _ in range(3):
+            lat.sweep(algo, beta, 2)
+            lat.pt_swap()
+        runs.append(lat.spins())
+    for _ in range(3):
+        orc.sweep(algo, beta, 2)
+        orc.pt_swap(beta)
+    assert np.array_equal(runs[0], orc.spins()) and np.array_equal(runs[1], orc.spins())
+
+
+@pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
+@pytest.mark.parametrize("R,K", [(3, 3), (5, 2), (30, 2), (100, 2)])
 def test_many_replicas_with_tempering(ianus, algo, R, K):
     """Per-lane-plane kernel with a run-time replica count: heat-bath words
     queued per warp (up to 97 replicas), beyond that, and for Metropolis,
     each word run to the end in place; swaps give every lane its own
-    temperature."""
+    temperature.  One compiled kernel serves all replica counts, so the
+    cases in turn need more and more of its shared memory."""
     beta = [1.0 / (0.8 + 0.6 * k / (K - 1)) for k in range(K)]
     lat, orc, _ = _pair(ianus, dim=3, L=4, S=67, R=R, K=K, layout="bits64", seed=SEED + 50 + R)
     for _ in range(3):
