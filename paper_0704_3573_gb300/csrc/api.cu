@@ -696,15 +696,20 @@ ianus_status ianus_read_series(ianus_lattice* h, uint64_t* sweep, int64_t* energ
   uint64_t n = lat->ser_count - first;
   if (n > cap_rows) n = cap_rows;
   const size_t SKR = (size_t)lat->S * lat->K * lat->R, SK = (size_t)lat->S * lat->K;
-  for (uint64_t r = 0; r < n; ++r) {
+  // the rows are contiguous in the ring except where it wraps: at most two
+  // copies per array
+  for (uint64_t r = 0; r < n;) {
     const size_t pos = (size_t)((first + r) % lat->cap);
-    if (sweep) CK(cudaMemcpyAsync(sweep + r, lat->ser_sweep + pos, 8, cudaMemcpyDeviceToHost, lat->stream));
-    if (energy) CK(cudaMemcpyAsync(energy + r * SKR, lat->ser_E + pos * SKR, SKR * 8, cudaMemcpyDeviceToHost, lat->stream));
+    const size_t m = (size_t)std::min<uint64_t>(n - r, lat->cap - pos);
+    if (sweep) CK(cudaMemcpyAsync(sweep + r, lat->ser_sweep + pos, m * 8, cudaMemcpyDeviceToHost, lat->stream));
+    if (energy)
+      CK(cudaMemcpyAsync(energy + r * SKR, lat->ser_E + pos * SKR, m * SKR * 8, cudaMemcpyDeviceToHost, lat->stream));
     if (magnetisation)
-      CK(cudaMemcpyAsync(magnetisation + r * SKR * lat->mq, lat->ser_M + pos * SKR * lat->mq, SKR * lat->mq * 8,
-                         cudaMemcpyDeviceToHost, lat->stream));
+      CK(cudaMemcpyAsync(magnetisation + r * SKR * lat->mq, lat->ser_M + pos * SKR * lat->mq,
+                         m * SKR * lat->mq * 8, cudaMemcpyDeviceToHost, lat->stream));
     if (overlap && lat->R >= 2)
-      CK(cudaMemcpyAsync(overlap + r * SK, lat->ser_Q + pos * SK, SK * 8, cudaMemcpyDeviceToHost, lat->stream));
+      CK(cudaMemcpyAsync(overlap + r * SK, lat->ser_Q + pos * SK, m * SK * 8, cudaMemcpyDeviceToHost, lat->stream));
+    r += m;
   }
   CK(cudaStreamSynchronize(lat->stream));
   if (n_rows) *n_rows = (size_t)n;
@@ -1113,11 +1118,16 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
   if (z.wheel_bytes)
     CK(cudaMemcpyAsync(lat->base + z.off_wheels, in, z.wheel_bytes, cudaMemcpyHostToDevice, lat->stream));
   CK(cudaMemsetAsync(lat->err, 0, 4, lat->stream));
+  // The tables depend on beta and the algorithm only, the per-lane planes
+  // also on the restored temperature permutation: those are rebuilt in
+  // place, so that the tables, the specialised kernels and the captured
+  // sweep graphs stay valid.
+  if (lat->tables_ok && lat->layout == IANUS_LAYOUT_BITS64)
+    CK(lat->field ? launch_build_field_planes(*lat) : launch_build_planes(*lat));
   CK(cudaStreamSynchronize(lat->stream));
   lat->sweeps = hd.sweeps;
   lat->steps = hd.steps;
   lat->t_dev_valid = false;
-  lat->tables_ok = false;  // per-lane planes depend on the restored permutation
   return IANUS_OK;
 }
 

@@ -193,6 +193,21 @@ def test_field_checkpoint(ianus, disorder, layout):
         other.set_state(blob)
 
 
+@pytest.mark.parametrize("disorder", [DIS_RFIM, DIS_DAFF])
+def test_field_restore_into_a_running_lattice(ianus, disorder):
+    """Two temperatures (per-lane field planes): a checkpoint restored into
+    the lattice that wrote it replays the same continuation."""
+    lat, _ = _pair(ianus, disorder, dim=3, L=6, S=70, R=2, K=2, layout="bits64", seed=12)
+    beta = [0.7, 1.2]
+    lat.sweep(HEATBATH, beta, 9)
+    blob = lat.get_state()
+    lat.sweep(HEATBATH, beta, 13)
+    first = lat.spins()
+    lat.set_state(blob)
+    lat.sweep(HEATBATH, beta, 13)
+    assert np.array_equal(lat.spins(), first)
+
+
 def test_field_errors(ianus):
     lat, _ = _pair(ianus, DIS_RFIM, dim=3, L=4, S=3, K=2)
     lat.sweep(HEATBATH, [0.5, 0.6], 1)
