@@ -1263,9 +1263,12 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
 }
 
 // Blocks along the lattice for a measurement kernel with `ys` blocks across:
-// about two blocks per SM in all, each warp taking 32 words at a time.
+// about two blocks per SM in all, each warp taking 32 words at a time, and
+// enough that a thread adds at most kMeasChunk words (one counter flush).
 inline unsigned meas_blocks(uint32_t N, unsigned ys) {
-  const unsigned want = (152u * 2u + ys - 1u) / ys;
+  unsigned want = (152u * 2u + ys - 1u) / ys;
+  const unsigned one_flush = (N + kBlock * kMeasChunk - 1) / (kBlock * kMeasChunk);
+  if (want < one_flush) want = one_flush;
   const unsigned most = (N + kBlock - 1) / kBlock;
   return want < 1u ? 1u : (want > most ? most : want);
 }
