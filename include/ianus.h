@@ -416,7 +416,8 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *   17..19 = two Philox chains, the class planes of both replicas computed
  *       before the first plane loop (all loads of a site in flight at once):
  *       the queue after 4 pairs with 3 blocks per SM, lockstep with 4 and
- *       with 3 blocks per SM.
+ *       with 3 blocks per SM;
+ *   20, 21 = shape 17 in blocks of 128 threads, 7 or 6 blocks per SM.
  * With several temperatures every variant but 1 uses the per-lane kernel
  * compiled for the geometry.  If run-time compilation is unavailable, the
  * precompiled kernel runs.  EINVAL for other values. */

@@ -25,7 +25,11 @@ constexpr bool P2 = IANUS_JIT_P2 != 0;
 constexpr uint32_t kLut[32] = {IANUS_JIT_LUTS};
 constexpr uint32_t kAlways = IANUS_JIT_ALWAYS;
 constexpr uint32_t kNeed = IANUS_JIT_NEED;
-constexpr int kBlock = 256;
+// IANUS_JIT_BLOCK: threads per block (default 256).
+#ifndef IANUS_JIT_BLOCK
+#define IANUS_JIT_BLOCK 256
+#endif
+constexpr int kBlock = IANUS_JIT_BLOCK;
 // IANUS_JIT_L, IANUS_JIT_LH, IANUS_JIT_LL: the lattice side and the base-2
 // logarithms of L/2 and L (0 when L is not a power of two).  The kernel runs
 // at one temperature (n_temps = 1, so slots = R); with the geometry fixed at

@@ -1039,13 +1039,14 @@ cudaError_t field_dispatch(Lattice& lat, const BitsParams& p, dim3 grid, size_t 
 // loop or per-warp queues entered after phase_a pairs; registers capped so
 // that min_blocks blocks of 256 threads fit on an SM.
 struct JitShape {
-  int mode, phase_a, min_blocks, group, jreload, ufirst;
+  int mode, phase_a, min_blocks, group, jreload, ufirst, block;
 };
-constexpr JitShape kJitShapes[] = {{0, 8, 3, 1, 0, 0}, {0, 8, 4, 1, 0, 0}, {1, 4, 3, 1, 0, 0}, {1, 4, 4, 1, 0, 0},
-                                   {1, 3, 3, 1, 0, 0}, {1, 5, 3, 1, 0, 0}, {2, 8, 2, 1, 0, 0}, {2, 8, 3, 1, 0, 0},
-                                   {0, 8, 3, 2, 0, 0}, {1, 4, 3, 2, 0, 0}, {1, 6, 3, 2, 0, 0}, {1, 4, 4, 2, 1, 0},
-                                   {0, 8, 4, 2, 1, 0}, {0, 8, 4, 1, 1, 0}, {1, 4, 4, 1, 1, 0}, {1, 4, 3, 2, 0, 1},
-                                   {0, 8, 4, 2, 0, 1}, {0, 8, 3, 2, 0, 1}};
+constexpr JitShape kJitShapes[] = {
+    {0, 8, 3, 1, 0, 0, 256}, {0, 8, 4, 1, 0, 0, 256}, {1, 4, 3, 1, 0, 0, 256}, {1, 4, 4, 1, 0, 0, 256},
+    {1, 3, 3, 1, 0, 0, 256}, {1, 5, 3, 1, 0, 0, 256}, {2, 8, 2, 1, 0, 0, 256}, {2, 8, 3, 1, 0, 0, 256},
+    {0, 8, 3, 2, 0, 0, 256}, {1, 4, 3, 2, 0, 0, 256}, {1, 6, 3, 2, 0, 0, 256}, {1, 4, 4, 2, 1, 0, 256},
+    {0, 8, 4, 2, 1, 0, 256}, {0, 8, 4, 1, 1, 0, 256}, {1, 4, 4, 1, 1, 0, 256}, {1, 4, 3, 2, 0, 1, 256},
+    {0, 8, 4, 2, 0, 1, 256}, {0, 8, 3, 2, 0, 1, 256}, {1, 4, 7, 2, 0, 1, 128}, {1, 4, 6, 2, 0, 1, 128}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 2;
@@ -1075,7 +1076,7 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   const int v = jit_variant_for(lat);
   if (v >= 2 && (lat.jit_algo != algo || lat.jit_variant != v)) {
     const JitShape& js = kJitShapes[v - 2];
-    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst);
+    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst, js.block);
     lat.jit_algo = algo;
     lat.jit_variant = v;
   }
@@ -1240,7 +1241,8 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
     if (lat.jit) {
       const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
       void* args[] = {(void*)&p, (void*)&lut_t};
-      return cudaLaunchKernel((const void*)lat.jit, grid, dim3(kBlock), args, js.mode == 1 ? kJitSmemBytes : 0,
+      return cudaLaunchKernel((const void*)lat.jit, grid, dim3(js.block), args,
+                              js.mode == 1 ? kJitSmemBytes / 256 * js.block : 0,
                               lat.stream);
     }
   }

@@ -177,8 +177,8 @@ void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr
 // each of its 8 warps.
 constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
 cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group,
-                        int jreload, int ufirst);
-constexpr int kMaxVariant = 19;  // ianus_set_variant accepts 0..kMaxVariant
+                        int jreload, int ufirst, int block);
+constexpr int kMaxVariant = 21;  // ianus_set_variant accepts 0..kMaxVariant
 // Run-time specialised random-field sweep for lat.flut (jit.cu; null when
 // unavailable).
 cudaKernel_t jit_field_kernel(const Lattice& lat, int algo, int min_blocks);
