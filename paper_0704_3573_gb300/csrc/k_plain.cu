@@ -405,8 +405,8 @@ __device__ __forceinline__ void block_sum2(long long (*red)[32], long long e, lo
 
 // Four planes 2 m0 .. 2 m0 + 3 of a site's random number (plane 2 m0 in bit
 // 3), from two Philox blocks computed together.  The first eight planes do
-// not depend on the spins, so a block draws them for its next pass while
-// its stores drain and while it waits at the cluster barrier.
+// not depend on the spins, so a block draws them for its next pass while it
+// waits at the cluster barrier.
 __device__ __forceinline__ uint32_t planes4(const PhiloxKeys& keys, const Tick& tk, int s, int sigma, uint32_t site,
                                             uint32_t m0) {
   const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
@@ -699,15 +699,12 @@ __global__ void __launch_bounds__(kClusterBlockMax) k_resident_cluster_i8(const 
         }
       }
       // the next pass (the other colour, or colour 0 of the next sweep): its
-      // first four planes while this pass's stores drain, the next four
-      // while the barrier completes
-      const bool next = ONE && mine && (colour == 0 || it + 1 < p.nsweeps);
-      const Tick tn = colour == 0 ? tk : Tick{(uint32_t)(t + 1), (uint32_t)((t + 1) >> 32)};
-      const uint32_t in = site[colour ^ 1].i;
-      uint32_t r4 = 0;
-      if (next) r4 = planes4(p.keys, tn, s, sigma, in, 0u);
+      // first eight planes while the barrier completes
       cluster_arrive();
-      if (next) r8 = (r4 << 4) | planes4(p.keys, tn, s, sigma, in, 2u);
+      if (ONE && mine && (colour == 0 || it + 1 < p.nsweeps)) {
+        const Tick tn = colour == 0 ? tk : Tick{(uint32_t)(t + 1), (uint32_t)((t + 1) >> 32)};
+        r8 = first_planes(p.keys, tn, s, sigma, site[colour ^ 1].i);
+      }
       cluster_wait();
     }
     if (measured) {
