@@ -465,60 +465,78 @@ __global__ void k_init_bits(uint64_t* spins, uint64_t* J, Geom geom, int G, int 
 // ---- threshold planes: TP[g][sigma][p][u], bit l = bit (31-p) of T of the
 // temperature sample 64g+l holds in slot sigma; plane 32 = (T == 2^32). ----
 
+// Threshold planes of one 64-lane word, one warp each: thread t holds the
+// thresholds of lanes t and 32 + t, and plane q is the ballot of bit 31 - q
+// (plane 32: threshold 2^32, "always").  Thread q < 32 keeps plane q, and
+// thread 0 also the always plane; the caller stores them.
+__device__ __forceinline__ void warp_planes(uint64_t T_lo, uint64_t T_hi, uint64_t& mine, uint64_t& always) {
+  const uint32_t lane = threadIdx.x & 31u;
+  always = (uint64_t)__ballot_sync(0xffffffffu, T_lo >= kTwo32) |
+           ((uint64_t)__ballot_sync(0xffffffffu, T_hi >= kTwo32) << 32);
+  mine = 0;
+#pragma unroll 4
+  for (uint32_t q = 0; q < 32u; ++q) {
+    const uint32_t lo = __ballot_sync(0xffffffffu, T_lo < kTwo32 && ((T_lo >> (31u - q)) & 1ull));
+    const uint32_t hi = __ballot_sync(0xffffffffu, T_hi < kTwo32 && ((T_hi >> (31u - q)) & 1ull));
+    if (lane == q) mine = (uint64_t)lo | ((uint64_t)hi << 32);
+  }
+}
+
+// TP[g][sigma][p][u] from the per-temperature thresholds thr[k][u] of each
+// lane's temperature, one warp per (group, slot, class).
 __global__ void k_build_planes(uint64_t* tp, const uint64_t* thr, const int32_t* temp_of, int G, int S, int R,
                                int K, int slots) {
   const int total = G * slots * kMaxClasses;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); idx < total;
+       idx += (int)((gridDim.x * blockDim.x) >> 5)) {  // uniform across the warp
     const int u = idx % kMaxClasses, rest = idx / kMaxClasses;
     const int sigma = rest % slots, g = rest / slots;
     const int tslot = sigma / R, a = sigma - tslot * R;
-    uint64_t planes[kPlanes];
-    for (int q = 0; q < kPlanes; ++q) planes[q] = 0;
-    for (int l = 0; l < 64; ++l) {
-      const int s = 64 * g + l;
+    uint64_t T[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = 64 * g + 32 * h + (int)lane;
       const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
-      const uint64_t T = thr[(size_t)k * kMaxClasses + u];
-      if (T >= kTwo32) {
-        planes[32] |= 1ull << l;
-      } else {
-        for (int q = 0; q < 32; ++q)
-          if ((T >> (31 - q)) & 1ull) planes[q] |= 1ull << l;
-      }
+      T[h] = thr[(size_t)k * kMaxClasses + u];
     }
-    for (int q = 0; q < kPlanes; ++q) tp[(((size_t)g * slots + sigma) * kPlanes + q) * kMaxClasses + u] = planes[q];
+    uint64_t mine, always;
+    warp_planes(T[0], T[1], mine, always);
+    uint64_t* out = tp + ((size_t)g * slots + sigma) * kPlanes * kMaxClasses + u;
+    out[(size_t)lane * kMaxClasses] = mine;
+    if (lane == 0) out[(size_t)32 * kMaxClasses] = always;
   }
 }
 
 // Field planes: FTP[g][sigma][p][8 f + u] from the per-temperature field
 // thresholds fthr[k][(v + 2D) * 2 + f], v = 2D - 2u; classes u > 2D stay 0.
 // With dilution (NF = kDiluteClasses) the class is 16 f + t, field class
-// t * 2 + f; classes t > 4D stay 0.
+// t * 2 + f; classes t > 4D stay 0.  One warp per (group, slot, class).
 __global__ void k_build_field_planes(uint64_t* ftp, const uint64_t* fthr, const int32_t* temp_of, int D, int G,
                                      int S, int R, int K, int slots, int NF) {
   const int total = G * slots * NF;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (int idx = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); idx < total;
+       idx += (int)((gridDim.x * blockDim.x) >> 5)) {  // uniform across the warp
     const int c = idx % NF, rest = idx / NF;
     const int sigma = rest % slots, g = rest / slots;
     const int tslot = sigma / R, a = sigma - tslot * R;
     const bool dil = NF == kDiluteClasses;
     const int u = dil ? (c & 15) : (c & 7), f = dil ? (c >> 4) : (c >> 3);
-    uint64_t planes[kPlanes];
-    for (int q = 0; q < kPlanes; ++q) planes[q] = 0;
-    if (dil ? u <= 4 * D : u <= 2 * D) {
-      const int cls = (dil ? u : 4 * D - 2 * u) * 2 + f;
-      for (int l = 0; l < 64; ++l) {
-        const int s = 64 * g + l;
-        const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
-        const uint64_t T = fthr[(size_t)k * kFieldClasses + cls];
-        if (T >= kTwo32) {
-          planes[32] |= 1ull << l;
-        } else {
-          for (int q = 0; q < 32; ++q)
-            if ((T >> (31 - q)) & 1ull) planes[q] |= 1ull << l;
-        }
-      }
+    const bool live = dil ? u <= 4 * D : u <= 2 * D;
+    const int cls = (dil ? u : 4 * D - 2 * u) * 2 + f;
+    uint64_t T[2] = {0, 0};
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int s = 64 * g + 32 * h + (int)lane;
+      const int k = s < S ? temp_of[((size_t)s * R + a) * K + tslot] : tslot;
+      if (live) T[h] = fthr[(size_t)k * kFieldClasses + cls];
     }
-    for (int q = 0; q < kPlanes; ++q) ftp[(((size_t)g * slots + sigma) * kPlanes + q) * NF + c] = planes[q];
+    uint64_t mine, always;
+    warp_planes(T[0], T[1], mine, always);
+    uint64_t* out = ftp + ((size_t)g * slots + sigma) * kPlanes * NF + c;
+    out[(size_t)lane * NF] = mine;
+    if (lane == 0) out[(size_t)32 * NF] = always;
   }
 }
 
@@ -1166,13 +1184,13 @@ cudaError_t launch_sweep_fused(Lattice& lat, int colour) {
 }
 
 cudaError_t launch_build_field_planes(Lattice& lat) {
-  k_build_field_planes<<<grid_for((uint64_t)lat.G * lat.slots * lat.fpc, 128), 128, 0, lat.stream>>>(
+  k_build_field_planes<<<grid_for((uint64_t)lat.G * lat.slots * lat.fpc * 32, 256), 256, 0, lat.stream>>>(
       lat.ftp, lat.fthr, lat.temp_of, lat.D, lat.G, lat.S, lat.R, lat.K, lat.slots, lat.fpc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_build_planes(Lattice& lat) {
-  k_build_planes<<<grid_for((uint64_t)lat.G * lat.slots * kMaxClasses, 128), 128, 0, lat.stream>>>(
+  k_build_planes<<<grid_for((uint64_t)lat.G * lat.slots * kMaxClasses * 32, 256), 256, 0, lat.stream>>>(
       lat.tp, lat.thr, lat.temp_of, lat.G, lat.S, lat.R, lat.K, lat.slots);
   return cudaGetLastError();
 }
