@@ -317,6 +317,12 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
   return IANUS_OK;
 }
 
+void acc_fresh(Lattice* lat) {
+  lat->acc_ok = true;
+  lat->acc_sweeps = lat->sweeps;
+  lat->acc_mut = lat->mut;
+}
+
 int measure_into(Lattice* lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* sweep_out, int want_q) {
   want_q = want_q && lat->R >= 2;
   if (lat->layout == IANUS_LAYOUT_I8)
@@ -325,6 +331,7 @@ int measure_into(Lattice* lat, int64_t* E, int64_t* M, int64_t* Q, uint64_t* swe
     CK(launch_measure_bits(*lat, want_q));
   else
     CK(launch_measure_potts(*lat, want_q));
+  acc_fresh(lat);
   CK(launch_finalize(*lat, E, M, Q, sweep_out, want_q));
   return IANUS_OK;
 }
@@ -361,8 +368,16 @@ bool same_beta(const Lattice* lat, const double* beta) {
 }
 
 int do_pt_swap(Lattice* lat) {
-  int st = measure_into(lat, nullptr, nullptr, nullptr, nullptr, 0);
-  if (st) return st;
+  // energies of every configuration: those of the last measurement when no
+  // sweep or other change came after it, else measured (U only when
+  // bit-sliced)
+  if (!(lat->acc_ok && lat->acc_sweeps == lat->sweeps && lat->acc_mut == lat->mut)) {
+    if (lat->layout == IANUS_LAYOUT_BITS64)
+      CK(launch_measure_bits(*lat, 0, true));
+    else
+      CK(launch_measure_i8(*lat, 0));
+    acc_fresh(lat);
+  }
   CK(launch_pt_swap(*lat));
   lat->steps += 1;
   if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
@@ -504,6 +519,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->jitf_algo = -1;
   lat->jitp[0] = lat->jitp[1] = nullptr;
   lat->jitp_tried[0] = lat->jitp_tried[1] = false;
+  lat->mut = 0;
+  lat->acc_ok = false;
   lat->bytes = z.total;
   if (cfg->device_buffer) {
     if (cfg->device_buffer_bytes < z.total || ((uintptr_t)cfg->device_buffer & 255u)) {
@@ -756,6 +773,7 @@ ianus_status ianus_get_spins_i8(ianus_lattice* h, int8_t* host) {
 
 ianus_status ianus_set_spins_i8(ianus_lattice* h, const int8_t* host) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!host) return IANUS_EINVAL;
   const size_t bytes = (size_t)lat->S * lat->slots * lat->N;
   for (size_t i = 0; i < bytes; ++i) {
@@ -778,6 +796,7 @@ ianus_status ianus_get_couplings_i8(ianus_lattice* h, int8_t* host) {
 
 ianus_status ianus_set_couplings_i8(ianus_lattice* h, const int8_t* host) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!host) return IANUS_EINVAL;
   const size_t bytes = (size_t)lat->S * lat->D * lat->N;
   for (size_t i = 0; i < bytes; ++i) {
@@ -838,6 +857,7 @@ ianus_status ianus_get_sites_i8(ianus_lattice* h, int8_t* hsign, int8_t* occupie
 
 ianus_status ianus_set_sites_i8(ianus_lattice* h, const int8_t* hsign, const int8_t* occupied) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!lat->field) return IANUS_EUNSUPPORTED;
   const size_t n = (size_t)lat->S * lat->N;
   for (size_t i = 0; hsign && i < n; ++i)
@@ -887,6 +907,7 @@ static ianus_status upload_group(Lattice* lat, int group) {
 ianus_status ianus_segment_load(ianus_lattice* h, int32_t group, int32_t lane0, int32_t n, uint64_t seed,
                                 int32_t job_group, int32_t algo, double beta, uint64_t nsweeps) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!lat->segs) return IANUS_EUNSUPPORTED;
   if (group < 0 || group >= lat->G || lane0 < 0 || n < 1 || lane0 + n > 64) return IANUS_EINVAL;
   if (job_group < 0 || job_group >= 4096) return IANUS_EINVAL;
@@ -932,6 +953,7 @@ ianus_status ianus_segment_load(ianus_lattice* h, int32_t group, int32_t lane0, 
 
 ianus_status ianus_segment_release(ianus_lattice* h, int32_t group, int32_t lane0) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!lat->segs || group < 0 || group >= lat->G) return IANUS_EINVAL;
   const int j = segment_find(lat, group, lane0);
   if (j < 0) return IANUS_EINVAL;
@@ -964,6 +986,7 @@ static int fused_sweep_once(Lattice* lat) {
 
 ianus_status ianus_sweep_segments(ianus_lattice* h, uint64_t nsweeps) {
   GET_LAT(h);
+  lat->mut += 1;  // the state changes other than by sweeps
   if (!lat->segs) return IANUS_EUNSUPPORTED;
   uint64_t left = nsweeps;
   while (left > 0) {
@@ -1103,6 +1126,7 @@ ianus_status ianus_set_state(ianus_lattice* h, const void* host_buf, size_t n) {
     return IANUS_ESTATE;
   const uint8_t* in = (const uint8_t*)host_buf + sizeof hd;
   lat->sticky = 0;
+  lat->mut += 1;  // the state changes other than by sweeps
   CK(cudaMemcpyAsync(lat->slot_at, in, perm, cudaMemcpyHostToDevice, lat->stream));
   in += perm;
   CK(cudaMemcpyAsync(lat->temp_of, in, perm, cudaMemcpyHostToDevice, lat->stream));

@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_measure_bits_k1(const uint64_t* _
 
 // Any number of temperatures: U and B of one slot.  Grid (chunks, groups x
 // slots).
-template <int D, bool P2>
+template <int D, bool P2, bool EONLY = false>
 __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restrict__ spins,
                                                          const uint64_t* __restrict__ J, int64_t* acc, Geom geom,
                                                          int S, int R, int K, int slots) {
@@ -779,13 +779,13 @@ __global__ void __launch_bounds__(kBlock) k_measure_bits(const uint64_t* __restr
       bond_count<D>(bw, sp[f.x], sp[f.y], D == 3 ? sp[f.z] : 0ull, Jg[j], Jg[N + j], D == 3 ? Jg[2u * N + j] : 0ull,
                     s1, c1);
       cu.add2(s1, c1);
-      cb.add1(bw);
+      if (!EONLY) cb.add1(bw);
     }
     cu.flush(0, 1, tot[0][0], tot[0][1]);
-    cb.flush(0, 1, tot[1][0], tot[1][1]);
+    if (!EONLY) cb.flush(0, 1, tot[1][0], tot[1][1]);
   }
   const int row_off[2] = {sigma, sigma}, field[2] = {0, 1};
-  block_flush(red, tot, 2, g, S, acc, row_off, field, slots);
+  block_flush(red, tot, EONLY ? 1 : 2, g, S, acc, row_off, field, slots);
 }
 
 // Field models (RFIM, DAFF) of one slot, values rather than counts:
@@ -1294,9 +1294,15 @@ inline unsigned meas_blocks(uint32_t N, unsigned ys) {
 }
 
 template <int D, bool P2>
-cudaError_t measure_dispatch(Lattice& lat, int want_q) {
+cudaError_t measure_dispatch(Lattice& lat, int want_q, bool energy_only) {
   const uint64_t* sp = (const uint64_t*)lat.spins;
   const uint64_t* J = (const uint64_t*)lat.J;
+  if (energy_only && !lat.field) {  // U of every configuration, for the PT swap
+    dim3 grid(meas_blocks(lat.N, (unsigned)(lat.G * lat.slots)), (unsigned)(lat.G * lat.slots));
+    k_measure_bits<D, P2, true><<<grid, kBlock, 0, lat.stream>>>(sp, J, lat.acc, lat.geom, lat.S, lat.R, lat.K,
+                                                                 lat.slots);
+    return cudaGetLastError();
+  }
   if (lat.K == 1 && (lat.R == 1 || lat.R == 2) && !lat.field) {
     // one pass for E, M and (R == 2) Q
     dim3 grid(meas_blocks(lat.N, (unsigned)lat.G), (unsigned)lat.G);
@@ -1320,12 +1326,15 @@ cudaError_t measure_dispatch(Lattice& lat, int want_q) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_measure_bits(Lattice& lat, int want_q) {
+cudaError_t launch_measure_bits(Lattice& lat, int want_q, bool energy_only) {
   cudaError_t e = cudaMemsetAsync(lat.acc, 0, (size_t)lat.S * lat.slots * kAccStride * sizeof(int64_t), lat.stream);
   if (e != cudaSuccess) return e;
   const bool p2 = lat.geom.lL > 0;
-  if (lat.D == 3) return p2 ? measure_dispatch<3, true>(lat, want_q) : measure_dispatch<3, false>(lat, want_q);
-  return p2 ? measure_dispatch<2, true>(lat, want_q) : measure_dispatch<2, false>(lat, want_q);
+  if (lat.D == 3)
+    return p2 ? measure_dispatch<3, true>(lat, want_q, energy_only)
+              : measure_dispatch<3, false>(lat, want_q, energy_only);
+  return p2 ? measure_dispatch<2, true>(lat, want_q, energy_only)
+            : measure_dispatch<2, false>(lat, want_q, energy_only);
 }
 
 cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out) {

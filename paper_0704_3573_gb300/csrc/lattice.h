@@ -152,6 +152,10 @@ struct Lattice {
   bool use_graphs;
   bool use_resident;         // resident mode for small I8 lattices (default on)
   int resident_mode;         // 1 = clusters when few configurations, 2 = one block each, 3 = clusters
+  // The accumulators hold the measurement of the state at (acc_sweeps,
+  // acc_mut) when acc_ok; mut counts changes of the state other than sweeps.
+  uint64_t mut, acc_sweeps, acc_mut;
+  bool acc_ok;
   bool t_dev_valid;          // *t_dev == sweeps
   cudaStream_t cap_stream;
   std::map<uint32_t, cudaGraphExec_t>* graphs;  // by block length
@@ -220,7 +224,8 @@ cudaError_t launch_sweep_fused(Lattice& lat, int colour);
 cudaError_t launch_advance_segments(Lattice& lat);
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
 size_t sweep_bits_smem(int R);  // least shared memory of the per-lane-plane sweep for R replicas
-cudaError_t launch_measure_bits(Lattice& lat, int want_q);
+// energy_only: U of every configuration only (the PT swap needs no more)
+cudaError_t launch_measure_bits(Lattice& lat, int want_q, bool energy_only = false);
 cudaError_t launch_build_planes(Lattice& lat);  // tp from thr and temp_of
 cudaError_t launch_get_spins_bits(Lattice& lat, int8_t* dev_out);
 cudaError_t launch_set_spins_bits(Lattice& lat, const int8_t* dev_in);

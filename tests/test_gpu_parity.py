@@ -184,6 +184,33 @@ def test_potts_sweep_bit_exact(ianus, dim, L, S, R):
         assert np.array_equal(Q, Qo)
 
 
+@pytest.mark.parametrize("layout", ["i8", "bits64"])
+def test_tempering_with_measurements_at_the_swaps(ianus, layout):
+    """Series measured at every swap: the swap takes its energies from that
+    measurement instead of measuring again; a set_spins between a
+    measurement and a swap forces a new one."""
+    K = 4
+    beta = [1.0 / (0.7 + 0.3 * k) for k in range(K)]
+    lat, orc, _ = _pair(ianus, dim=3, L=4, S=67, R=2, K=K, layout=layout, seed=SEED + 98)
+    lat.sweep_pt(HEATBATH, beta, 20, swap_every=5, measure_every=5)
+    for _ in range(4):
+        orc.sweep(HEATBATH, beta, 5, measure_every=5)
+        orc.pt_swap(beta)
+    assert np.array_equal(lat.spins(), orc.spins())
+    assert np.array_equal(lat.pt_state()[0], orc.pt_state()[0])
+    _, E, M, Q = lat.series()
+    _, Eo, Mo, Qo = orc.series()
+    assert np.array_equal(E, Eo) and np.array_equal(M, Mo) and np.array_equal(Q, Qo)
+    lat.measure()
+    orc.measure()
+    fresh = np.random.default_rng(7).choice(np.array([-1, 1], dtype=np.int8), size=lat.spins().shape)
+    lat.set_spins(fresh)
+    orc.set_spins(fresh)
+    lat.pt_swap()
+    orc.pt_swap(beta)
+    assert np.array_equal(lat.pt_state()[0], orc.pt_state()[0])
+
+
 @pytest.mark.parametrize("algo", [METROPOLIS, HEATBATH])
 @pytest.mark.parametrize("dim,L,S,R,K", [(3, 6, 67, 2, 3), (2, 10, 5, 1, 4), (3, 8, 130, 3, 2), (2, 16, 64, 2, 2)])
 def test_per_lane_kernel_compiled_for_the_geometry(ianus, algo, dim, L, S, R, K):
