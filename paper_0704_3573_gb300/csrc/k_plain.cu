@@ -374,13 +374,15 @@ __global__ void __launch_bounds__(1024) k_resident_i8(const ResidentParams p) {
 // every colour pass is as long as the slowest of a block's many sites.  Here
 // a cluster of C blocks (C divides L) holds one configuration: block r owns
 // the slab of P = L/C planes along the last axis (z in 3D, y in 2D), its
-// spins and forward couplings in shared memory plus the plane of last-axis
-// couplings just below the slab.  Neighbours across a slab face are read from
-// the neighbouring block's shared memory (distributed shared memory), and the
-// two colours are separated by cluster barriers (Sec. 3.1).  The random
-// stream and the update rule are those of k_sweep_i8, so the results are the
-// same bit for bit; E and M are summed per block, then across the cluster in
-// block 0's shared memory.
+// spins and forward couplings in shared memory, the plane of last-axis
+// couplings just below the slab, and halo copies of the neighbouring blocks'
+// face planes.  A flip on a face is also stored into the neighbour's halo
+// (distributed shared memory), so every read is local, and the two colours
+// are separated by cluster barriers (Sec. 3.1) whose release/acquire makes
+// those stores visible.  The random stream and the update rule are those of
+// k_sweep_i8, so the results are the same bit for bit.  E and M are measured
+// once per launch and then carried by the flips; per-block changes are
+// summed in block 0's shared memory at each measured sweep.
 
 // Sum of (e, m) over the block, valid in thread 0; red holds one pair per warp.
 __device__ __forceinline__ void block_sum2(long long (*red)[32], long long e, long long m, long long& E,
