@@ -405,11 +405,19 @@ def run_other_configs(args):
     lat = ianus.Lattice(dim=3, L=16, n_samples=1, seed=SEED - 1, layout="i8", series_capacity=1000, stream=stream)
     lat.sweep(ianus.METROPOLIS, 1 / 1.1, 10, 1)
     sec = timed(lambda: lat.sweep(ianus.METROPOLIS, 1 / 1.1, 1000, 1), 1)
+    # latency floor of a sweep: two passes, each a cluster barrier round trip
+    # (0.19 us, measured with a barrier probe on GB300) and one dependent
+    # update of a site (about 410 cycles at 2070 MHz, read with clock64)
+    floor_us = 2 * (0.19 + 410 / 2070.0)
+    sweep_us = sec * 1e3
     out["L16_single_sample_metropolis"] = {"updates_per_ns": 16 ** 3 * 1000 / (sec * 1e9), "ms_per_1000_sweeps": sec * 1e3,
-                                           "sweep_us": sec * 1e3,
+                                           "sweep_us": sweep_us,
                                            "mode": "plain int8, one lattice split over a 16-block cluster "
                                                    "(one z-plane per block, halos in shared memory), E/M every sweep",
-                                           "bound": "latency (2 cluster barriers and 2 dependent passes per sweep)"}
+                                           "bound": "latency (2 cluster barriers and 2 dependent passes per sweep)",
+                                           "roofline": {"bound": "latency", "achieved": sweep_us, "peak": floor_us,
+                                                        "unit": "us per sweep (lower is better)",
+                                                        "frac": floor_us / sweep_us}}
     if not args.no_cpu_baseline:
         import oracle
 
