@@ -405,31 +405,24 @@ __device__ __forceinline__ void block_sum2(long long (*red)[32], long long e, lo
     }
 }
 
-// Four planes 2 m0 .. 2 m0 + 3 of a site's random number (plane 2 m0 in bit
-// 3), from two Philox blocks computed together.  The first eight planes do
-// not depend on the spins, so a block draws them for its next pass while it
-// waits at the cluster barrier.
-__device__ __forceinline__ uint32_t planes4(const PhiloxKeys& keys, const Tick& tk, int s, int sigma, uint32_t site,
-                                            uint32_t m0) {
-  const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
-  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
-  uint4 x[2];
-#pragma unroll
-  for (uint32_t m = 0; m < 2u; ++m) x[m] = philox10(site, tk.lo, c2base | ((m0 + m) << 24), tk.hi, keys);
-  uint32_t r4 = 0;
-#pragma unroll
-  for (uint32_t m = 0; m < 2u; ++m) {
-    const uint32_t w0 = lane < 32u ? (x[m].x >> lane) : (x[m].y >> (lane - 32u));
-    const uint32_t w1 = lane < 32u ? (x[m].z >> lane) : (x[m].w >> (lane - 32u));
-    r4 |= ((w0 & 1u) << (3u - 2u * m)) | ((w1 & 1u) << (2u - 2u * m));
-  }
-  return r4;
-}
-
-// The first eight planes (plane 0 in bit 7).
+// The first eight planes of a site's random number (plane 0 in bit 7), from
+// four Philox blocks computed together: they do not depend on the spins, so
+// a block draws them for its next pass while it waits at the cluster barrier.
 __device__ __forceinline__ uint32_t first_planes(const PhiloxKeys& keys, const Tick& tk, int s, int sigma,
                                                  uint32_t site) {
-  return (planes4(keys, tk, s, sigma, site, 0u) << 4) | planes4(keys, tk, s, sigma, site, 2u);
+  const uint32_t lane = (uint32_t)s & 63u, g = (uint32_t)s >> 6;
+  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+  uint4 x[4];
+#pragma unroll
+  for (uint32_t m = 0; m < 4u; ++m) x[m] = philox10(site, tk.lo, c2base | (m << 24), tk.hi, keys);
+  uint32_t r8 = 0;
+#pragma unroll
+  for (uint32_t m = 0; m < 4u; ++m) {
+    const uint32_t w0 = lane < 32u ? (x[m].x >> lane) : (x[m].y >> (lane - 32u));
+    const uint32_t w1 = lane < 32u ? (x[m].z >> lane) : (x[m].w >> (lane - 32u));
+    r8 |= ((w0 & 1u) << (7u - 2u * m)) | ((w1 & 1u) << (6u - 2u * m));
+  }
+  return r8;
 }
 
 // r < T (as lazy_less) given the first eight planes r8; planes 8.. drawn
@@ -700,12 +693,12 @@ __global__ void __launch_bounds__(kClusterBlockMax) k_resident_cluster_i8(const 
           part0[16 + rank] = bM;
         }
       }
-      // the next pass (the other colour, or colour 0 of the next sweep): its
-      // first eight planes while the barrier completes
       cluster_arrive();
-      if (ONE && mine && (colour == 0 || it + 1 < p.nsweeps)) {
-        const Tick tn = colour == 0 ? tk : Tick{(uint32_t)(t + 1), (uint32_t)((t + 1) >> 32)};
-        r8 = first_planes(p.keys, tn, s, sigma, site[colour ^ 1].i);
+      if (ONE && mine) {  // the next pass: the other colour, or colour 0 of the next sweep
+        if (colour == 0)
+          r8 = first_planes(p.keys, tk, s, sigma, site[1].i);
+        else if (it + 1 < p.nsweeps)
+          r8 = first_planes(p.keys, Tick{(uint32_t)(t + 1), (uint32_t)((t + 1) >> 32)}, s, sigma, site[0].i);
       }
       cluster_wait();
     }
