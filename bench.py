@@ -557,6 +557,33 @@ def run_other_configs(args):
             "value": 2 * 64 ** 3 * 2 / (dt * 1e9), "unit": UNIT, "cores": 2, "kind": "oracle",
             "sample": "samples 0, 255, 2 sweeps"}
     del da
+    # the headline update on a lattice 8x larger than the bench workload, L=128:
+    # 320 MiB of spins and couplings, beyond the 129 MB L2, so every sweep
+    # streams the state from HBM; unique bytes per site word per sweep: both
+    # replicas' words read and written (32) and the three couplings (24), for
+    # 128 updates
+    big = ianus.Lattice(dim=3, L=128, n_samples=S, n_replicas=R, seed=SEED + 8, layout="bits64", stream=stream)
+    big.set_variant(DEFAULT_VARIANT[0])
+    big.set_block_words(DEFAULT_VARIANT[1])
+    big.sweep(ianus.HEATBATH, 1.0 / T, 4, 0)
+    reps = 3
+    sec = timed(lambda: big.sweep(ianus.HEATBATH, 1.0 / T, 20, 0), reps)
+    upd = S * R * 128 ** 3 * 20 * reps
+    rate = upd / (sec * 1e9)
+    bytes_upd = (32 + 24) / 128.0
+    hbm = MEASURED.get("hbm_gbs")
+    ops_word = algorithmic_ops_per_word_hb3d(R)["alu"]
+    peak_alu = _alu_peak()
+    out["L128_256x2_hb_out_of_l2"] = {
+        "updates_per_ns": rate, "ms_per_sweep": sec * 1e3 / (20 * reps),
+        "mode": "bit-sliced, specialised kernel (the bench variant), state 320 MiB > L2",
+        "roofline": {"bound": "alu", "achieved": rate * ops_word / 64 / 1e3, "peak": peak_alu,
+                     "unit": "T ALU-pipe int32 ops/s",
+                     "frac": (rate * ops_word / 64 / 1e3 / peak_alu) if peak_alu else None},
+        "hbm": {"bytes_per_update": bytes_upd, "achieved": rate * bytes_upd, "peak": hbm, "unit": "GB/s",
+                "frac": (rate * bytes_upd / hbm) if hbm else None},
+    }
+    del big
     # the bench workload on the plain layout driven by Parisi-Rapuano wheels (Eq. 5)
     wh = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 7, layout="i8", rng="wheel", stream=stream)
     wh.sweep(ianus.HEATBATH, 1.0 / T, 2, 0)
