@@ -380,7 +380,10 @@ ianus_status ianus_get_sweeps(ianus_lattice* lat, uint64_t* sweeps);
  * temperature permutation, the couplings and the spins.  With host_buf NULL,
  * *n receives the size needed.  Synchronous.  ianus_set_state restores a
  * blob taken from a lattice of the same configuration (else ESTATE) and
- * clears a previous error state. */
+ * clears a previous error state.  The acceptance tables of the last beta and
+ * algorithm, the kernels specialised for them and captured sweep graphs are
+ * kept (per-lane threshold planes are rebuilt for the restored temperature
+ * permutation), so a restore into a running lattice costs only the copies. */
 ianus_status ianus_get_state(ianus_lattice* lat, void* host_buf, size_t cap,
                              size_t* n);
 ianus_status ianus_set_state(ianus_lattice* lat, const void* host_buf,
