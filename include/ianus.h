@@ -266,8 +266,10 @@ ianus_status ianus_sweep(ianus_lattice* lat, int32_t algo, const double* beta,
                          uint64_t nsweeps, uint32_t measure_every);
 
 /* One parallel-tempering swap step (Sec. 2.2 names PT; rules in the header
- * comment above): measures the exact energies on the device, then every
- * chain (sample, replica) visits its temperature pairs in ascending order.
+ * comment above): measures the exact energies on the device (or takes them
+ * from a measurement of the same state, when no sweep or state change came
+ * after it), then every chain (sample, replica) visits its temperature pairs
+ * in ascending order.
  * Uses the beta array of the last ianus_sweep.  Asynchronous.  Errors:
  * EINVAL (n_temps == 1 or no prior sweep), EUNSUPPORTED (Potts, RFIM,
  * DAFF: their energies E_J - |h| F are not on the integer grid of the swap
