@@ -199,6 +199,16 @@ __device__ __forceinline__ Tick sweep_tick(uint32_t t_lo, uint32_t t_hi, const u
   return Tick{t_lo, t_hi};
 }
 
+// Entry of a kernel launched with programmatic stream serialisation: wait
+// until the previous kernel on the stream has completed and its writes are
+// visible (nothing of the previous grid is read or written before this),
+// then allow the next such kernel's blocks onto the SMs this grid's tail
+// leaves free.  Both are no-ops for a plain launch.
+__device__ __forceinline__ void dependent_launch_entry() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Number of unsatisfied bonds per lane as bit-planes (u2, u1, u0), from the
 // 2D unsatisfied-bond words e[]: a carry-save adder tree.
 template <int D>

@@ -279,6 +279,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jit::kBlock, IANUS_JIT_MINB)
   using namespace ianus::jit;
   extern __shared__ __align__(16) unsigned char dyn_smem[];
   __shared__ uint8_t s_lut[32];
+  dependent_launch_entry();
   if (threadIdx.x < 32) s_lut[threadIdx.x] = lut_t[threadIdx.x];
   __syncthreads();
   Queue* q = reinterpret_cast<Queue*>(dyn_smem) + (threadIdx.x >> 5);  // one queue per warp (mode 1)

@@ -1197,6 +1197,25 @@ cudaError_t launch_build_planes(Lattice& lat) {
 
 size_t sweep_bits_smem(int R) { return bits_sweep_smem(R, false); }
 
+// Launches a run-time compiled sweep kernel with programmatic stream
+// serialisation: its blocks may become resident while the previous kernel on
+// the stream drains, and its entry (dependent_launch_entry) holds them until
+// that kernel has completed.  Inside a stream capture this becomes a
+// programmatic edge of the graph.
+static cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, k, args);
+}
+
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   BitsParams p;
   p.spins = (uint64_t*)lat.spins;
@@ -1259,9 +1278,8 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
     if (lat.jit) {
       const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
       void* args[] = {(void*)&p, (void*)&lut_t};
-      return cudaLaunchKernel((const void*)lat.jit, grid, dim3(js.block), args,
-                              js.mode == 1 ? kJitSmemBytes / 256 * js.block : 0,
-                              lat.stream);
+      return launch_dependent((const void*)lat.jit, grid, dim3(js.block), args,
+                              js.mode == 1 ? kJitSmemBytes / 256 * js.block : 0, lat.stream);
     }
   }
   // Per-lane planes: the kernel compiled for the lattice's geometry, else
@@ -1271,7 +1289,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
     if (lat.jitp[algo]) {
       const bool q = algo == 1 && bits_sweep_smem(lat.R, true) <= 227u * 1024u;
       void* args[] = {(void*)&p};
-      const cudaError_t e = cudaLaunchKernel((const void*)lat.jitp[algo], grid, dim3(kBlock), args,
+      const cudaError_t e = launch_dependent((const void*)lat.jitp[algo], grid, dim3(kBlock), args,
                                              (size_t)bits_sweep_smem(lat.R, q), lat.stream);
       if (e != cudaSuccess) cudaGetLastError();  // a refused launch leaves no pending error behind
       return e;

@@ -306,6 +306,7 @@ __device__ __forceinline__ void sweep_planes_body(const BitsParams& p, const Geo
 extern "C" __global__ void __launch_bounds__(ianus::planes::kPlanesBlock, IANUS_JIT_MINB)
     ianus_jit_planes_sweep(const ianus::BitsParams p) {
   constexpr ianus::Geom geom = ianus::kJitGeom;
+  ianus::dependent_launch_entry();
   ianus::planes::sweep_planes_body<IANUS_JIT_D, IANUS_JIT_ALGO, IANUS_JIT_RT, IANUS_JIT_P2 != 0, IANUS_JIT_Q != 0>(
       p, geom);
 }
