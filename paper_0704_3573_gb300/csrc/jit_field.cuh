@@ -137,6 +137,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jitf::kBlock, IANUS_JIT_MINB
   using namespace ianus;
   using namespace ianus::jitf;
   __shared__ uint8_t s_lut[128];
+  dependent_launch_entry();
   if (threadIdx.x < 128) s_lut[threadIdx.x] = lut_t[threadIdx.x];
   __syncthreads();
 #ifdef IANUS_JIT_L

@@ -1197,12 +1197,11 @@ cudaError_t launch_build_planes(Lattice& lat) {
 
 size_t sweep_bits_smem(int R) { return bits_sweep_smem(R, false); }
 
-// Launches a run-time compiled sweep kernel with programmatic stream
-// serialisation: its blocks may become resident while the previous kernel on
-// the stream drains, and its entry (dependent_launch_entry) holds them until
-// that kernel has completed.  Inside a stream capture this becomes a
-// programmatic edge of the graph.
-static cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
+// Launches a sweep kernel with programmatic stream serialisation: its blocks
+// may become resident while the previous kernel on the stream drains, and its
+// entry (dependent_launch_entry) holds them until that kernel has completed.
+// Inside a stream capture this becomes a programmatic edge of the graph.
+cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
   cfg.blockDim = block;
@@ -1259,7 +1258,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
         const uint64_t* xb = lat.xbits;
         const uint8_t* lut = (const uint8_t*)(lat.fthr + (size_t)lat.K * kFieldClasses);
         void* args[] = {(void*)&p, (void*)&hb, (void*)&xb, (void*)&lut};
-        return cudaLaunchKernel((const void*)lat.jitf, grid, dim3(kBlock), args, 0, lat.stream);
+        return launch_dependent((const void*)lat.jitf, grid, dim3(kBlock), args, 0, lat.stream);
       }
     }
     p.tp = lat.ftp;

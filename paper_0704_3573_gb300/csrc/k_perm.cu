@@ -124,6 +124,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep_perm(const PermParams p) {
   constexpr uint32_t NT = B * B * B;
   __shared__ uint8_t inv_s[256];
   for (uint32_t c = threadIdx.x; c < 256u; c += kBlock) inv_s[c] = (uint8_t)inverse_code(c);
+  dependent_launch_entry();  // the table above reads no memory
   const int sq = blockIdx.y;  // sigma * Q4 + q
   const int sigma = sq / p.Q4, q = sq - sigma * p.Q4;
   const int tslot = sigma / p.R, a = sigma - tslot * p.R;
@@ -339,13 +340,11 @@ cudaError_t launch_sweep_perm(Lattice& lat, int colour, uint64_t t) {
   if (wpb < (uint32_t)kBlock) wpb = kBlock;
   p.words_per_block = wpb;
   dim3 grid((half + wpb - 1) / wpb, ys);
-  if (lat.D == 4)
-    k_sweep_perm<4><<<grid, kBlock, 0, lat.stream>>>(p);
-  else if (lat.D == 3)
-    k_sweep_perm<3><<<grid, kBlock, 0, lat.stream>>>(p);
-  else
-    k_sweep_perm<2><<<grid, kBlock, 0, lat.stream>>>(p);
-  return cudaGetLastError();
+  void* args[] = {(void*)&p};
+  const void* k = lat.D == 4   ? (const void*)k_sweep_perm<4>
+                  : lat.D == 3 ? (const void*)k_sweep_perm<3>
+                               : (const void*)k_sweep_perm<2>;
+  return launch_dependent(k, grid, dim3(kBlock), args, 0, lat.stream);
 }
 
 cudaError_t launch_measure_perm(Lattice& lat, int want_q) {

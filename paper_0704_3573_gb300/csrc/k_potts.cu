@@ -35,6 +35,7 @@ struct PottsParams {
 
 template <int D>
 __global__ void __launch_bounds__(kBlock) k_sweep_potts(const PottsParams p) {
+  dependent_launch_entry();
   const int sq = blockIdx.y;  // sigma * Q4 + q
   const int sigma = sq / p.Q4, q = sq - sigma * p.Q4;
   const int tslot = sigma / p.R, a = sigma - tslot * p.R;
@@ -338,11 +339,9 @@ cudaError_t launch_sweep_potts(Lattice& lat, int colour, uint64_t t) {
   if (wpb < (uint32_t)kBlock) wpb = kBlock;
   p.words_per_block = wpb;
   dim3 grid((half + wpb - 1) / wpb, ys);
-  if (lat.D == 3)
-    k_sweep_potts<3><<<grid, kBlock, 0, lat.stream>>>(p);
-  else
-    k_sweep_potts<2><<<grid, kBlock, 0, lat.stream>>>(p);
-  return cudaGetLastError();
+  void* args[] = {(void*)&p};
+  const void* k = lat.D == 3 ? (const void*)k_sweep_potts<3> : (const void*)k_sweep_potts<2>;
+  return launch_dependent(k, grid, dim3(kBlock), args, 0, lat.stream);
 }
 
 cudaError_t launch_measure_potts(Lattice& lat, int want_q) {

@@ -223,6 +223,9 @@ cudaError_t launch_load_segment(Lattice& lat, int group, uint32_t lane0, uint32_
 cudaError_t launch_sweep_fused(Lattice& lat, int colour);
 cudaError_t launch_advance_segments(Lattice& lat);
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv);
+// Launch with programmatic stream serialisation, for sweep kernels that
+// begin with dependent_launch_entry() (k_msc.cu)
+cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s);
 size_t sweep_bits_smem(int R);  // least shared memory of the per-lane-plane sweep for R replicas
 // energy_only: U of every configuration only (the PT swap needs no more)
 cudaError_t launch_measure_bits(Lattice& lat, int want_q, bool energy_only = false);
