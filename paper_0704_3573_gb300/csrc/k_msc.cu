@@ -1200,7 +1200,8 @@ size_t sweep_bits_smem(int R) { return bits_sweep_smem(R, false); }
 // Launches a sweep kernel with programmatic stream serialisation: its blocks
 // may become resident while the previous kernel on the stream drains, and its
 // entry (dependent_launch_entry) holds them until that kernel has completed.
-// Inside a stream capture this becomes a programmatic edge of the graph.
+// Inside a stream capture this becomes a programmatic edge of the graph.  A
+// refused launch returns its error and leaves no pending error behind.
 cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = grid;
@@ -1212,7 +1213,9 @@ cudaError_t launch_dependent(const void* k, dim3 grid, dim3 block, void** args, 
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelExC(&cfg, k, args);
+  const cudaError_t e = cudaLaunchKernelExC(&cfg, k, args);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
 }
 
 cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
@@ -1288,10 +1291,8 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
     if (lat.jitp[algo]) {
       const bool q = algo == 1 && bits_sweep_smem(lat.R, true) <= 227u * 1024u;
       void* args[] = {(void*)&p};
-      const cudaError_t e = launch_dependent((const void*)lat.jitp[algo], grid, dim3(kBlock), args,
-                                             (size_t)bits_sweep_smem(lat.R, q), lat.stream);
-      if (e != cudaSuccess) cudaGetLastError();  // a refused launch leaves no pending error behind
-      return e;
+      return launch_dependent((const void*)lat.jitp[algo], grid, dim3(kBlock), args,
+                              (size_t)bits_sweep_smem(lat.R, q), lat.stream);
     }
   }
   if (lat.D == 3)
