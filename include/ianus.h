@@ -20,6 +20,12 @@
  * the caller.  Every entry point returns an ianus_status and never aborts,
  * exits or prints.  Every device operation is enqueued on the lattice's CUDA
  * stream; the calls documented as synchronous synchronise that stream only.
+ * Sweep kernels are launched as programmatic dependents: they wait for the
+ * previous kernel on the stream to complete before touching memory, and let
+ * the next kernel's blocks start early.  A caller kernel enqueued after a
+ * sweep with the programmatic-serialisation attribute must itself wait
+ * (griddepcontrol.wait / cudaGridDependencySynchronize) before reading the
+ * lattice; plain launches are ordered as usual.
  *
  * ------------------------------------------------------------------------
  * Lattice, colours, bonds (Sec. 2.1; Sec. 3.1)
