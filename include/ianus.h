@@ -20,9 +20,10 @@
  * the caller.  Every entry point returns an ianus_status and never aborts,
  * exits or prints.  Every device operation is enqueued on the lattice's CUDA
  * stream; the calls documented as synchronous synchronise that stream only.
- * Sweep kernels are launched as programmatic dependents: they wait for the
- * previous kernel on the stream to complete before touching memory, and let
- * the next kernel's blocks start early.  A caller kernel enqueued after a
+ * The run-time specialised bit-sliced sweeps and the Potts sweeps are
+ * launched as programmatic dependents: they wait for the previous kernel on
+ * the stream to complete before touching memory, and let the next kernel's
+ * blocks start early.  A caller kernel enqueued after a
  * sweep with the programmatic-serialisation attribute must itself wait
  * (griddepcontrol.wait / cudaGridDependencySynchronize) before reading the
  * lattice; plain launches are ordered as usual.
@@ -429,6 +430,11 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       the queue after 4 pairs with 3 blocks per SM, lockstep with 4 and
  *       with 3 blocks per SM;
  *   20, 21 = shape 17 in blocks of 128 threads, 7 or 6 blocks per SM.
+ * The fastest shape depends on the lattice and the algorithm: on the L=64,
+ * 256-sample x 2-replica heat-bath lattice it is 21 with 256 words per block
+ * (ianus_set_block_words), faster than the automatic lockstep shape by
+ * about a sixth.  The Python autotuner (tune.py) times the shapes on the
+ * caller's lattice.
  * With several temperatures every variant but 1 uses the per-lane kernel
  * compiled for the geometry.  If run-time compilation is unavailable, the
  * precompiled kernel runs.  EINVAL for other values. */
