@@ -324,11 +324,22 @@ def test_L16_single_sample_metropolis_full_run(ianus):
         assert np.array_equal(lat.spins(), orc.spins())
 
 
-def test_L64_256x2_heatbath_full_size_sampled(ianus):
-    """L=64, 256 samples x 2 replicas, heat bath T=1.0 on the GPU in the bench
-    launch configuration; samples 0, 63, 64, 255 checked against the oracle."""
+# The kernel variant and words per block bench.py times on this workload
+# (checked against bench.DEFAULT_VARIANT by a CPU test).
+BENCH_SHAPE = (21, 256)
+
+
+@pytest.mark.parametrize("shape", [None, BENCH_SHAPE])
+def test_L64_256x2_heatbath_full_size_sampled(ianus, shape):
+    """L=64, 256 samples x 2 replicas, heat bath T=1.0 on the GPU, with the
+    automatic kernel choice and with the kernel and launch shape bench.py
+    times (variant 21, 256 words per block); samples 0, 63, 64, 255 checked
+    against the oracle."""
     seed = SEED + 1
     lat = ianus.Lattice(dim=3, L=64, n_samples=256, n_replicas=2, seed=seed, layout="bits64")
+    if shape is not None:
+        lat.set_variant(shape[0])
+        lat.set_block_words(shape[1])
     lat.sweep(HEATBATH, 1.0, 10, measure_every=5)
     ids = [0, 63, 64, 255]
     orc = Oracle(dim=3, L=64, sample_ids=ids, n_replicas=2, seed=seed)

@@ -1,6 +1,7 @@
 """Multi-process host logic of bench.py on CPU (gloo, world size 2): rank
 discovery, barrier, max-over-ranks timing, per-rank sample batches, and the
-reference arm printing only on rank 0."""
+reference arm printing only on rank 0; and that the full-size parity test
+runs the launch shape bench.py times."""
 
 import json
 import os
@@ -56,3 +57,13 @@ def test_reference_arm_prints_on_rank0_only():
     assert len(printed) == 1
     line = json.loads(printed[0].strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+
+
+def test_full_size_parity_runs_the_benchmarked_shape():
+    """The full-size GPU parity test checks the kernel and launch shape that
+    bench.py times by default."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from tests.test_gpu_parity import BENCH_SHAPE
+
+    assert tuple(bench.DEFAULT_VARIANT) == BENCH_SHAPE
