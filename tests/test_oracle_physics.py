@@ -40,16 +40,23 @@ def test_energy_bookkeeping(model, dim, L, algo):
     for _ in range(6):
         o.sweep(algo, 0.9, 1)
         assert o.bookkeeping_error() == 0
-    # the oracle's energy agrees with an independent energy function
+    # the oracle's energy agrees with an independent energy function, and
+    # M and Q with their definitions written out on the read-back spins
     sp, J = o.spins(), o.couplings()
-    E, _, _ = o.measure()
+    E, M, Q = o.measure()
     for s in range(o.S):
         for a in range(2):
             if model == MODEL_ISING:
                 ref = pins.ising_energy(sp[s, a], J[s], L, dim)
+                assert M[s, 0, a] == int(sp[s, a].astype(np.int64).sum())
             else:
                 ref = pins.potts_energy(sp[s, a], J[s], L, dim)
+                assert np.array_equal(M[s, 0, a], np.bincount(sp[s, a], minlength=4))
             assert E[s, 0, a] == ref
+        if model == MODEL_ISING:
+            assert Q[s, 0] == int((sp[s, 0].astype(np.int64) * sp[s, 1]).sum())
+        else:
+            assert Q[s, 0] == int((sp[s, 0] == sp[s, 1]).sum())
 
 
 # ---------------- exact enumeration ----------------
