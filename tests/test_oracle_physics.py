@@ -445,3 +445,22 @@ def test_split_runs_threads_and_subsets_agree():
     c = Oracle(sample_ids=[5], **kw)
     c.sweep(HEATBATH, 0.9, 7)
     assert np.array_equal(c.spins()[0], a.spins()[5])
+
+
+def test_series_rows_are_measurements_after_the_sweep():
+    """Measurement timing: with measure_every = k the series holds a row
+    after every sweep whose absolute count t is a multiple of k (none for the
+    initial state), each equal to a measurement of the state after that sweep,
+    here taken by stopping a second run there."""
+    kw = dict(dim=3, L=4, sample_ids=[0, 3], n_replicas=2, seed=SEED + 16)
+    a = Oracle(**kw)
+    a.sweep(METROPOLIS, 0.8, 7, measure_every=3)
+    sw, E, M, Q = a.series()
+    assert [int(t) for t in sw] == [3, 6]
+    b = Oracle(**kw)
+    done = 0
+    for row, t in enumerate(sw):
+        b.sweep(METROPOLIS, 0.8, int(t) - done)
+        done = int(t)
+        Eb, Mb, Qb = b.measure()
+        assert np.array_equal(E[row], Eb) and np.array_equal(M[row], Mb) and np.array_equal(Q[row], Qb)
