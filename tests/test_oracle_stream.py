@@ -4,7 +4,8 @@ Pins used (none is the oracle checking itself):
 * Philox4x32-10 known-answer vectors published with the generator
   (tests/golden/philox4x32_10_kat.txt);
 * a third, pure-Python implementation of the stream definition for the
-  bit-plane assembly (tests/pins.py), itself pinned by the same vectors;
+  bit-plane assembly, the couplings and the initial states (tests/pins.py),
+  itself pinned by the same vectors;
 * uniformity of the assembled 32-bit values (chi-square);
 * acceptance tables against 60-digit evaluations with sympy, and the
   identities p(x) + p(-x) = 1 and monotonicity in the energy argument.
@@ -73,6 +74,38 @@ def test_potts_and_pt_random_words():
         a = rng.randrange(0, 3)
         x = pins.philox4x32_10([k, t & pins.MASK32, (6 << 28) | (a << 16) | (s >> 2), t >> 32], pins.key_of(seed))
         assert oracle.pt_random(seed, s, a, k, t) == x[s & 3]
+
+
+def _lane_bit(seed, c0, c1, c2, lane):
+    x = pins.philox4x32_10([c0, c1, c2, 0], pins.key_of(seed))
+    return ((x[0] | (x[1] << 32)) >> lane) & 1
+
+
+@pytest.mark.parametrize("model", [oracle.MODEL_ISING, oracle.MODEL_POTTS])
+def test_disorder_and_initial_state_streams(model):
+    """Couplings (J stream: bit l of x0 | x1 << 32 at c0 = i, c1 = d,
+    c2 = (2 << 28) | g; set bit = J = -1) and initial states (Ising: INIT
+    stream, c2 = (3 << 28) | (sigma << 12) | g; Potts: x_{s & 3} >> 30 of the
+    PINIT stream, c2 = (5 << 28) | (sigma << 16) | (s >> 2)), recomputed
+    with the independent Philox for samples in three 64-lane groups."""
+    seed, ids, dim, L, R = 0x0123456789ABCDEF, [0, 5, 70, 130], 3, 4, 2
+    o = oracle.Oracle(model=model, dim=dim, L=L, sample_ids=ids, n_replicas=R, seed=seed)
+    J, sp = o.couplings(), o.spins()
+    N = L ** dim
+    key = pins.key_of(seed)
+    for k, s in enumerate(ids):
+        g, lane = s >> 6, s & 63
+        for d in range(dim):
+            for i in range(N):
+                assert J[k, d, i] == 1 - 2 * _lane_bit(seed, i, d, (2 << 28) | g, lane)
+        for sigma in range(R):
+            for i in range(N):
+                if model == oracle.MODEL_ISING:
+                    want = 1 - 2 * _lane_bit(seed, i, 0, (3 << 28) | (sigma << 12) | g, lane)
+                else:
+                    x = pins.philox4x32_10([i, 0, (5 << 28) | (sigma << 16) | (s >> 2), 0], key)
+                    want = x[s & 3] >> 30
+                assert sp[k, sigma, i] == want
 
 
 def test_ising_random_uniform():
