@@ -401,9 +401,10 @@ def test_pt_permutation_and_energy_multiset():
 
 
 def test_pt_acceptance_frequency():
-    """Two temperatures, configurations frozen: whenever the colder one holds
-    the higher energy (d > 0) the swap is taken with probability
-    T_PT(|d|)/2^32 = floor(2^32 exp(-db d))/2^32."""
+    """Two temperatures, configurations frozen: whenever the hotter one holds
+    the higher energy (d = E_hot - E_cold > 0) the swap is taken with
+    probability T_PT(d)/2^32 = floor(2^32 exp(-db d))/2^32, and otherwise
+    always (the standard rule min(1, exp(-db d)), db = beta_cold - beta_hot)."""
     beta = [0.75, 0.7]
     o = Oracle(dim=2, L=4, sample_ids=[0], n_replicas=1, n_temps=2, seed=SEED + 14)
     rng = np.random.default_rng(2)
