@@ -278,6 +278,23 @@ def test_potts_chain_matches_boltzmann():
     assert chi2 / dof < 1.6, (chi2, dof)
 
 
+@pytest.mark.parametrize("dim,L", [(2, 6), (3, 4)])
+def test_potts_beta_zero_takes_the_top_bits_of_the_stream(dim, L):
+    """At beta = 0 the cumulative thresholds are (k + 1) 2^30, so the new
+    state is the top two bits of the site's POTTS word: this fixes the state
+    order of the cumulative selection, which the Boltzmann pins cannot see."""
+    ids = [0, 5, 70]
+    o = Oracle(model=MODEL_POTTS, dim=dim, L=L, sample_ids=ids, n_replicas=2, seed=SEED + 17)
+    o.sweep(HEATBATH, 0.0, 1)
+    sp = o.spins()
+    key = pins.key_of(SEED + 17)
+    for k, s in enumerate(ids):
+        for slot in range(2):
+            for i in range(L ** dim):
+                x = pins.philox4x32_10([i, 0, (4 << 28) | (slot << 16) | (s >> 2), 0], key)
+                assert sp[k, slot, i] == x[s & 3] >> 30
+
+
 def test_potts_q2_energy_reduction():
     """delta(s, s') = (1 + sigma sigma')/2 with sigma = 1 - 2s, so
     E_Potts(q=2) = (E_Ising(sigma) - sum J) / 2 exactly."""
