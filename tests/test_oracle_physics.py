@@ -377,6 +377,17 @@ def test_heatbath_beta_zero_flips_on_plane0():
                     assert after[si, slot, i] == before[si, slot, i] * (-1 if bit else 1)
 
 
+def test_metropolis_beta_zero_flips_every_spin():
+    """At beta = 0 every Metropolis proposal is accepted (p = exp(0) = 1, the
+    threshold 2^32 above every 32-bit random), so one sweep negates every
+    spin, whatever the stream."""
+    o = Oracle(dim=3, L=4, sample_ids=[0, 70], n_replicas=2, seed=SEED + 18)
+    for _ in range(3):
+        before = o.spins()
+        o.sweep(METROPOLIS, 0.0, 1)
+        assert np.array_equal(o.spins(), -before)
+
+
 def test_metropolis_zero_temperature_never_raises_energy():
     o = Oracle(dim=3, L=6, sample_ids=[0, 1], seed=SEED + 11)
     E0, _, _ = o.measure()
