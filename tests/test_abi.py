@@ -1,6 +1,7 @@
 """C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
 every entry point include/ianus.h declares, validates configurations, and its
-host table builders agree bytewise with the oracle's independent builders."""
+host table builders agree bytewise with the oracle's independent builders;
+without a GPU the product path refuses to run."""
 
 import ctypes
 import os
@@ -163,3 +164,14 @@ def test_potts_count_tables_match_oracle(beta):
                 for n2 in range(2 * D + 1 - n0 - n1):
                     n = [n0, n1, n2, 2 * D - n0 - n1 - n2]
                     assert ianus.table_potts_counts(beta, n) == oracle.table_potts(beta, n), (D, n)
+
+
+def test_no_cpu_fallback_without_a_gpu():
+    """Without a CUDA device the product path refuses to run: constructing a
+    lattice raises instead of computing anywhere else."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        ianus.Lattice(dim=3, L=4, n_samples=1)
