@@ -5,9 +5,9 @@
  * The paper has no counterpart: its update engines are FPGA logic whose
  * throughput is fixed by the clock and the number of update cells
  * (Sec. 3.1, Sec. 4.1.1).  On the GPU the sweep is bound by 32-bit integer
- * issue (Philox multiplies and three-input logic), and the driver-measured
- * peaks cover only memory copies and bf16 GEMMs, so this probe measures
- * per-SM integer rates directly.
+ * issue (Philox multiplies and three-input logic), while the usual measured
+ * peaks (a memory copy, a bf16 GEMM) say nothing about integer issue, so
+ * this probe measures per-SM integer rates directly.
  *
  * ianus_probe_int(kind, blocks_per_sm, out):
  *   kind 0: lop3.b32 (three-input logic)           -> ops / clock / SM
