@@ -57,6 +57,18 @@ def test_reference_arm_prints_on_rank0_only():
     assert len(printed) == 1
     line = json.loads(printed[0].strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
+    sys.path.insert(0, ROOT)
+    import bench
+
+    # the reference arm's line: the same metric and config as the GPU arm,
+    # a cpu_baseline describing this run, and an e2e block with no copies
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT and line["higher_is_better"] is True
+    assert line["config"]["workload"] == bench.WORKLOAD
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == line["value"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["unit"] == line["unit"]
+    assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
 
 
 def test_full_size_parity_runs_the_benchmarked_shape():
