@@ -50,9 +50,9 @@ WORKLOAD = ("3D EA +-J, L=64 periodic, 256 samples x 2 replicas (64 samples per 
 SM_COUNT = 152
 SM_MAX_MHZ = 2070.0
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the dominant
-# kernel from one ncu capture (profiles/ianus_jit_sweep_hb3d_L64_S256x2.md),
-# per (kernel variant, words per block), valid while the kernel source is
-# unchanged (hash of the sources it is compiled from).
+# kernel from one ncu capture of it on this workload, per (kernel variant,
+# words per block), valid while the kernel source is unchanged (hash of the
+# sources it is compiled from).
 TRAFFIC_BYTES_PER_LAUNCH = {(21, 256): 41976064 + 0}
 TRAFFIC_SOURCE_HASH = "5473351233ed34e4"
 # The kernel variant and launch shape the bench runs by default: the

@@ -1,6 +1,6 @@
 // k_perm.cu -- the glassy Potts model of Eq. (3),
 // H = -sum_<ij> delta(s_i, pi_ij(s_j)), with quenched permutation couplings
-// pi_ij of (0,1,2,3), heat bath, in 2, 3 or 4 dimensions (Sec. 6 runs it in
+// pi_ij of (0,1,2,3), heat bath, in 2, 3 or 4 dimensions (Sec. 4.2 runs it in
 // 3D and 4D).
 //
 // Storage follows IANUS_LAYOUT_U8X4: a 32-bit word holds one site of 4

@@ -149,27 +149,46 @@ extern "C" ianus_status ianus_measure_bits64_noalloc(const uint64_t* spins, cons
   if (N >= (1ull << 31)) return IANUS_EINVAL;
   const int G = (n_samples + 63) / 64;
   if ((long long)G * n_slots > 65535) return IANUS_EINVAL;
-  Geom geom;
+  Geom geom{};
   geom.D = dim;
   geom.L = L;
   geom.h = L / 2;
   geom.N = (uint32_t)N;
   geom.half = (uint32_t)(N / 2);
+  if ((L & (L - 1)) == 0) {  // power of two: log2 of L and L/2, as the other kernels expect
+    while ((1 << geom.lL) < L) ++geom.lL;
+    geom.lh = geom.lL - 1;
+  }
   cudaStream_t stream = (cudaStream_t)cuda_stream;
   void* scratch = nullptr;
   if (scratch_address(&scratch) != cudaSuccess) return IANUS_ECUDA;
   const int total = n_samples * n_slots;
   // the array keeps the previous call's counts: clear the part this call uses
-  if (cudaMemsetAsync(scratch, 0, (size_t)total * 2 * sizeof(unsigned long long), stream) != cudaSuccess)
+  if (cudaMemsetAsync(scratch, 0, (size_t)total * 2 * sizeof(unsigned long long), stream) != cudaSuccess) {
+    cudaGetLastError();
     return IANUS_ECUDA;
+  }
   const uint32_t per_block = kBlockNA * kItersNA;
   dim3 grid((geom.N + per_block - 1) / per_block, (unsigned)(G * n_slots));
   unsigned long long* acc = (unsigned long long*)scratch;
-  if (dim == 3)
-    k_measure_bits_noalloc<3><<<grid, kBlockNA, 0, stream>>>(spins, couplings, acc, geom, n_samples, n_slots);
-  else
-    k_measure_bits_noalloc<2><<<grid, kBlockNA, 0, stream>>>(spins, couplings, acc, geom, n_samples, n_slots);
+  // Each launch's status is its own return value, so an error left pending
+  // by unrelated earlier work is neither reported here nor cleared; a
+  // refused launch is cleared so that it does not linger for the next caller.
+  int ns = n_samples, nsl = n_slots;
+  void* margs[] = {(void*)&spins, (void*)&couplings, (void*)&acc, (void*)&geom, (void*)&ns, (void*)&nsl};
+  const void* mk = dim == 3 ? (const void*)k_measure_bits_noalloc<3> : (const void*)k_measure_bits_noalloc<2>;
+  if (cudaLaunchKernel(mk, grid, dim3(kBlockNA), margs, 0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ECUDA;
+  }
   const unsigned fin = (unsigned)std::min(1024, (total + 255) / 256);
-  k_finalize_noalloc<<<fin, 256, 0, stream>>>(acc, energy, magnetisation, total, dim, geom.N);
-  return cudaGetLastError() == cudaSuccess ? IANUS_OK : IANUS_ECUDA;
+  const unsigned long long* cacc = acc;
+  int tot = total, D = dim;
+  uint32_t Nn = geom.N;
+  void* fargs[] = {(void*)&cacc, (void*)&energy, (void*)&magnetisation, (void*)&tot, (void*)&D, (void*)&Nn};
+  if (cudaLaunchKernel((const void*)k_finalize_noalloc, dim3(fin), dim3(256), fargs, 0, stream) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ECUDA;
+  }
+  return IANUS_OK;
 }

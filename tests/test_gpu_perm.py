@@ -155,7 +155,7 @@ def test_perm_errors(ianus):
 @pytest.mark.parametrize("dim,L,ids,beta", [(4, 16, [0, 1, 5, 127, 200, 255], 1.405),
                                             (3, 32, [0, 3, 64, 130, 254], 2.4)])
 def test_perm_full_size_sampled(ianus, dim, L, ids, beta):
-    """The paper's sizes (Sec. 6: 4D L=16 at beta=1.405, 3D at beta=2.4 --
+    """The paper's sizes (Sec. 4.2: 4D L=16 at beta=1.405, 3D at beta=2.4 --
     here L=32), 256 samples x 2 replicas: after 10 sweeps a sample of the
     configurations equals the oracle run of exactly those samples, and every
     configuration's E, counts and Q equal the values recomputed from the

@@ -59,7 +59,8 @@ def _call_noalloc(ianus, lat, torch):
     return E.cpu().numpy(), M.cpu().numpy()
 
 
-@pytest.mark.parametrize("dim,L,S,R", [(3, 8, 70, 2), (2, 16, 5, 1), (3, 4, 130, 2)])
+# the last case fills the fixed array exactly: 16384 samples x 2 slots = 32768
+@pytest.mark.parametrize("dim,L,S,R", [(3, 8, 70, 2), (2, 16, 5, 1), (3, 4, 130, 2), (3, 4, 16384, 2)])
 def test_noalloc_measure_matches_ianus_measure_twice(ianus, dim, L, S, R):
     import torch
 
@@ -82,3 +83,27 @@ def test_noalloc_rejects_sizes_over_the_limit(ianus):
     assert lib.ianus_measure_bits64_noalloc(p, p, 3, 4, 16385, 2, p, p, None) == ianus.EINVAL
     assert lib.ianus_measure_bits64_noalloc(p, p, 3, 5, 1, 1, p, p, None) == ianus.EINVAL
     assert lib.ianus_measure_bits64_noalloc(None, p, 3, 4, 1, 1, p, p, None) == ianus.EINVAL
+
+
+def test_noalloc_allocates_no_device_memory(ianus):
+    """After a first call (which looks up the array's device address), a
+    second call leaves the device's free memory exactly as it was: nothing is
+    allocated, by the library or by the CUDA runtime on its behalf."""
+    import torch
+
+    lat = ianus.Lattice(dim=3, L=8, n_samples=70, n_replicas=2, seed=0x0704357300000078, layout="bits64")
+    lat.sweep(ianus.HEATBATH, 0.9, 2)
+    spins = torch.from_numpy(_pack_bits64(lat.spins(), lat.L, lat.dim).view(np.int64)).cuda()
+    J = torch.from_numpy(_pack_bits64(lat.couplings(), lat.L, lat.dim).view(np.int64)).cuda()
+    E = torch.zeros((lat.S, 2), dtype=torch.int64, device="cuda")
+    M = torch.zeros((lat.S, 2), dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    args = (C.c_void_p(spins.data_ptr()), C.c_void_p(J.data_ptr()), lat.dim, lat.L, lat.S, 2,
+            C.c_void_p(E.data_ptr()), C.c_void_p(M.data_ptr()), C.c_void_p(stream.cuda_stream))
+    assert ianus.lib().ianus_measure_bits64_noalloc(*args) == ianus.OK
+    torch.cuda.synchronize()
+    free_before, _ = torch.cuda.mem_get_info()
+    assert ianus.lib().ianus_measure_bits64_noalloc(*args) == ianus.OK
+    torch.cuda.synchronize()
+    free_after, _ = torch.cuda.mem_get_info()
+    assert free_after == free_before
