@@ -429,7 +429,13 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       before the first plane loop (all loads of a site in flight at once):
  *       the queue after 4 pairs with 3 blocks per SM, lockstep with 4 and
  *       with 3 blocks per SM;
- *   20, 21 = shape 17 in blocks of 128 threads, 7 or 6 blocks per SM.
+ *   20, 21 = shape 17 in blocks of 128 threads, 7 or 6 blocks per SM;
+ *   22..24 = the lane-queue kernel: Philox rounds 0 and 1 split into a site
+ *       part and a block-uniform part, plane pairs 0..3 for every word, the
+ *       lanes still undecided queued per warp and finished 32 at a time one
+ *       plane pair per round; 8 or 6 blocks of 128 threads per SM (22, 23),
+ *       4 blocks of 256 (24).  With no explicit launch shape its grid is one
+ *       wave of about that many blocks per SM.
  * The fastest shape depends on the lattice and the algorithm: on the L=64,
  * 256-sample x 2-replica heat-bath lattice it is 21 with 256 words per block
  * (ianus_set_block_words), faster than the automatic lockstep shape by

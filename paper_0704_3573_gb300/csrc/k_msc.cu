@@ -1064,7 +1064,9 @@ constexpr JitShape kJitShapes[] = {
     {1, 3, 3, 1, 0, 0, 256}, {1, 5, 3, 1, 0, 0, 256}, {2, 8, 2, 1, 0, 0, 256}, {2, 8, 3, 1, 0, 0, 256},
     {0, 8, 3, 2, 0, 0, 256}, {1, 4, 3, 2, 0, 0, 256}, {1, 6, 3, 2, 0, 0, 256}, {1, 4, 4, 2, 1, 0, 256},
     {0, 8, 4, 2, 1, 0, 256}, {0, 8, 4, 1, 1, 0, 256}, {1, 4, 4, 1, 1, 0, 256}, {1, 4, 3, 2, 0, 1, 256},
-    {0, 8, 4, 2, 0, 1, 256}, {0, 8, 3, 2, 0, 1, 256}, {1, 4, 7, 2, 0, 1, 128}, {1, 4, 6, 2, 0, 1, 128}};
+    {0, 8, 4, 2, 0, 1, 256}, {0, 8, 3, 2, 0, 1, 256}, {1, 4, 7, 2, 0, 1, 128}, {1, 4, 6, 2, 0, 1, 128},
+    // mode 3: the lane-queue kernel (jit_sweep_lt.cuh), blocks/SM and block size
+    {3, 4, 8, 1, 0, 0, 128}, {3, 4, 6, 1, 0, 0, 128}, {3, 4, 4, 1, 0, 0, 256}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 2;
@@ -1277,6 +1279,21 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   if (v >= 2) {
     const JitShape& js = kJitShapes[v - 2];
     prepare_sweep_bits(lat, inv);
+    if (lat.jit && js.mode == 3) {
+      // one wave: about min_blocks blocks per SM in all, whole warps of words
+      uint32_t w3;
+      if (lat.block_words) {
+        w3 = (lat.block_words + 31u) / 32u * 32u;
+      } else {
+        const uint32_t per_group = std::max<uint32_t>(1u, 152u * (uint32_t)js.min_blocks / (uint32_t)lat.G);
+        w3 = (half + per_group - 1u) / per_group;
+        w3 = std::max<uint32_t>(32u, (w3 + 31u) / 32u * 32u);
+      }
+      p.words_per_block = w3;
+      void* args[] = {(void*)&p};
+      return launch_dependent((const void*)lat.jit, dim3((half + w3 - 1u) / w3, (unsigned)lat.G), dim3(js.block), args,
+                              0, lat.stream);
+    }
     if (lat.jit) {
       const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);
       void* args[] = {(void*)&p, (void*)&lut_t};

@@ -182,7 +182,10 @@ void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr
 constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
 cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group,
                         int jreload, int ufirst, int block);
-constexpr int kMaxVariant = 21;  // ianus_set_variant accepts 0..kMaxVariant
+// The lane-queue shape of the same sweep (jit_sweep_lt.cuh): shared Philox
+// rounds 0..1, four plane pairs for every word, undecided lanes queued.
+cudaKernel_t jit_lt_kernel(const Lattice& lat, int algo, int min_blocks, int block);
+constexpr int kMaxVariant = 24;  // ianus_set_variant accepts 0..kMaxVariant
 // Run-time specialised random-field sweep for lat.flut (jit.cu; null when
 // unavailable).
 cudaKernel_t jit_field_kernel(const Lattice& lat, int algo, int min_blocks);

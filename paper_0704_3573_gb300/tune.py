@@ -16,7 +16,7 @@ import json
 import os
 import tempfile
 
-VARIANTS = tuple(range(1, 22))
+VARIANTS = tuple(range(1, 25))
 BLOCK_WORDS = (0, 256, 512, 1024, 2048)
 
 
