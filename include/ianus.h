@@ -406,10 +406,12 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * differs).  With one temperature the thresholds are the same in every lane
  * and the sweep kernel can be specialised for them at run time (NVRTC, a
  * fraction of a second per new table set, cached per device).
- *   0 = automatic: the specialised lockstep kernel for lattices of >= 2^20
- *       site words, else the kernel with per-lane threshold bit-planes,
- *       compiled at run time for the lattice's geometry (also with several
- *       temperatures and for parallel tempering);
+ *   0 = automatic: with one temperature and one or two replicas the
+ *       lane-queue kernel (variant 24, below), the fastest shape measured on
+ *       every lattice from L = 8 to L = 128; otherwise the kernel with
+ *       per-lane threshold bit-planes, compiled at run time for the
+ *       lattice's geometry (also with several temperatures and for parallel
+ *       tempering);
  *   1 = always the precompiled per-lane kernel (geometry from the launch
  *       parameters);
  *   2..9 = a specialised kernel shape: 2, 3 = lockstep plane loop with 3 or 4
@@ -435,7 +437,15 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       lanes still undecided queued per warp and finished 32 at a time one
  *       plane pair per round; 8 or 6 blocks of 128 threads per SM (22, 23),
  *       4 blocks of 256 (24).  With no explicit launch shape its grid is one
- *       wave of about that many blocks per SM.
+ *       wave of about that many blocks per SM;
+ *   25, 26 = the persistent form of the lane-queue kernel: one cooperative
+ *       launch runs every sweep between two measurements.  Each block owns
+ *       a fixed range of rows and starts a colour pass once the blocks that
+ *       own its sites' neighbours have finished the previous pass (bounded
+ *       waits, ianus_set_persistent_wait), so there is no kernel boundary
+ *       between colours; at least 512 (25) or 128 (26) colour words per
+ *       block, at most as many blocks as are resident at once.  Where that
+ *       launch cannot run it falls back to variant 22's per-pass kernel.
  * The fastest shape depends on the lattice and the algorithm: on the L=64,
  * 256-sample x 2-replica heat-bath lattice it is 21 with 256 words per block
  * (ianus_set_block_words), faster than the automatic lockstep shape by
@@ -451,6 +461,16 @@ ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
  * default, a multiple of 256 that sizes the grid to about 8 blocks per SM.
  * EINVAL above 2^24. */
 ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
+
+/* Waits of the persistent sweep (variants 25, 26): each wait of a block for
+ * its neighbours' progress is bounded by timeout_ns (default 2 s).  A wait
+ * that runs out sets the device error word and the block returns; the next
+ * ianus_synchronize reports IANUS_ETIMEOUT and the lattice is ESTATE
+ * (restore it with ianus_set_state).  absent_block >= 0 makes that block of
+ * the next launches return at once without doing its work: a wait that
+ * nothing ends, for testing the timeout path (-1: none).  EINVAL for
+ * timeout_ns = 0 or absent_block < -1. */
+ianus_status ianus_set_persistent_wait(ianus_lattice* lat, uint64_t timeout_ns, int32_t absent_block);
 
 /* Sweep blocks through CUDA graphs (default on): runs of at least 4 sweeps
  * between measurements are replayed from graphs of up to 64 sweeps, captured

@@ -43,7 +43,7 @@ EXPORTS = [
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
     "ianus_set_graphs", "ianus_set_resident", "ianus_get_sites_i8", "ianus_set_sites_i8", "ianus_table_field",
     "ianus_table_potts_counts", "ianus_segment_load", "ianus_segment_release", "ianus_segment_state",
-    "ianus_sweep_segments",
+    "ianus_sweep_segments", "ianus_set_persistent_wait",
 ]
 
 
@@ -119,6 +119,7 @@ def lib(build_if_missing: bool = True):
         "ianus_measure_bits64_noalloc": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp]),
         "ianus_set_variant": (i32, [vp, i32]),
         "ianus_set_block_words": (i32, [vp, u32]),
+        "ianus_set_persistent_wait": (i32, [vp, u64, i32]),
         "ianus_set_graphs": (i32, [vp, i32]),
         "ianus_set_resident": (i32, [vp, i32]),
         "ianus_get_sites_i8": (i32, [vp, vp, vp]),
@@ -387,12 +388,18 @@ class Lattice:
 
     def set_variant(self, variant: int):
         """Bit-sliced sweep kernel: 0 automatic, 1 per-lane threshold planes,
-        2..7 shapes of the kernel specialised at run time (include/ianus.h)."""
+        2..26 shapes of the kernel specialised at run time (include/ianus.h)."""
         _check(self._lib.ianus_set_variant(self._h, variant), "ianus_set_variant")
 
     def set_block_words(self, words: int):
         """Colour words per 256-thread block of the bit-sliced sweep (0 = default)."""
         _check(self._lib.ianus_set_block_words(self._h, words), "ianus_set_block_words")
+
+    def set_persistent_wait(self, timeout_ns: int, absent_block: int = -1):
+        """Bound of each wait of the persistent sweep (variants 25, 26), and a
+        block told to return at once (tests of the timeout path; -1 none)."""
+        _check(self._lib.ianus_set_persistent_wait(self._h, int(timeout_ns), int(absent_block)),
+               "ianus_set_persistent_wait")
 
     def set_graphs(self, enable: bool):
         """Replay sweep blocks from captured CUDA graphs (default) or launch directly."""

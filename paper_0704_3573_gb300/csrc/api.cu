@@ -29,7 +29,7 @@ struct Sizes {
   bool poolable;
   size_t off_segs, off_nseg;
   size_t off_spins, off_J, off_thr, off_tp, off_fthr, off_ftp, off_sites, off_ptab, off_pttab, off_ptsign, off_slot,
-      off_temp, off_acc_pt, off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, total;
+      off_temp, off_acc_pt, off_acc, off_oE, off_oM, off_oQ, off_sw, off_sE, off_sM, off_sQ, off_err, off_tdev, off_flags, total;
   size_t spins_bytes, J_bytes, sites_bytes;
 };
 
@@ -140,6 +140,8 @@ int plan(const ianus_config* c, Sizes& z) {
   z.off_sQ = take((size_t)z.cap * z.S * z.K * 8);
   z.off_err = take(8);
   z.off_tdev = take(8);
+  // progress flags of the persistent one-temperature bit-sliced sweep
+  z.off_flags = take(layout == IANUS_LAYOUT_BITS64 && !field && z.K == 1 ? (size_t)kMaxPersistBlocks * 4 : 0);
   z.total = o;
   return IANUS_OK;
 }
@@ -428,6 +430,21 @@ int build_graph(Lattice* lat, int inv, uint32_t B, cudaGraphExec_t* out) {
 // Runs n sweeps (no measurement inside) through cached graphs of blocks of
 // up to 64 sweeps; short runs (< 4 sweeps) launch eagerly.
 int sweeps_graphed(Lattice* lat, int inv, uint64_t n) {
+  // the persistent one-temperature sweep: all n sweeps in launches of up to
+  // 2^20 sweeps, no graphs needed (falls through when it cannot run)
+  if (lat->layout == IANUS_LAYOUT_BITS64 && persistent_variant(*lat)) {
+    bool ran = true;
+    while (n > 0 && ran) {
+      const uint32_t B = (uint32_t)std::min<uint64_t>(n, 1u << 20);
+      cudaError_t e = launch_sweep_persistent(*lat, inv, lat->sweeps, B, &ran);
+      if (e != cudaSuccess) return fail(lat, IANUS_ECUDA);
+      if (!ran) break;
+      lat->sweeps += B;
+      lat->t_dev_valid = false;
+      n -= B;
+    }
+    if (n == 0) return IANUS_OK;
+  }
   while (n > 0) {
     const uint32_t B = (uint32_t)std::min<uint64_t>(n, 64);
     if (B < 4 || !lat->use_graphs || !lat->graphs) {
@@ -516,6 +533,8 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->algo = -1;
   lat->jit_algo = -1;
   lat->jit_variant = -1;
+  lat->persist_timeout_ns = 2000000000ull;  // 2 s
+  lat->persist_absent = -1;
   lat->jitf_algo = -1;
   lat->jitp[0] = lat->jitp[1] = nullptr;
   lat->jitp_tried[0] = lat->jitp_tried[1] = false;
@@ -571,6 +590,7 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->ser_M = (int64_t*)(b + z.off_sM);
   lat->ser_Q = (int64_t*)(b + z.off_sQ);
   lat->err = (uint32_t*)(b + z.off_err);
+  lat->flags = (z.layout == IANUS_LAYOUT_BITS64 && !z.field && z.K == 1) ? (uint32_t*)(b + z.off_flags) : nullptr;
   lat->t_dev = (uint64_t*)(b + z.off_tdev);
   lat->use_graphs = true;
   lat->use_resident = true;
@@ -1176,6 +1196,14 @@ ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   if (variant < 0 || variant > kMaxVariant) return IANUS_EINVAL;
   if (lat->variant != variant) drop_graphs(lat);
   lat->variant = variant;
+  return IANUS_OK;
+}
+
+ianus_status ianus_set_persistent_wait(ianus_lattice* h, uint64_t timeout_ns, int32_t absent_block) {
+  GET_LAT(h);
+  if (timeout_ns == 0 || absent_block < -1) return IANUS_EINVAL;
+  lat->persist_timeout_ns = timeout_ns;
+  lat->persist_absent = absent_block;
   return IANUS_OK;
 }
 

@@ -185,6 +185,26 @@ struct BitsParams {
   const uint64_t* t_dev;     // non-null in captured graphs: sweep = *t_dev + t_lo
 };
 
+// Launch parameters of the persistent form of the lane-queue sweep
+// (jit_sweep_lt.cuh with IANUS_JIT_PERSIST): one launch runs npass colour
+// passes (colour 0 first) of sweeps t0, t0 + 1, ...  Block b owns rows
+// [j R_g / cpg, (j + 1) R_g / cpg) of group g = b / cpg, j = b % cpg
+// (R_g = N / L rows of L/2 words per colour).  flags[b] counts the passes b
+// has completed in this launch (zeroed before the launch); a block starts a
+// pass once the blocks owning the rows its sites' neighbours live in have
+// completed the previous one, waiting at most timeout_ns.  On a wait that
+// runs out the block sets ERR_TIMEOUT in *err and returns.  skip_block >= 0
+// makes that block return at once (a wait that nothing ends, for tests).
+struct PersistParams {
+  uint32_t* flags;
+  uint32_t* err;
+  uint32_t npass;
+  uint32_t cpg;
+  uint32_t t0_lo, t0_hi;
+  uint64_t timeout_ns;
+  int32_t skip_block;
+};
+
 // The absolute sweep index of a launch: the (t_hi, t_lo) parameters, or in a
 // captured graph the device-resident counter plus the offset in t_lo.
 struct Tick {

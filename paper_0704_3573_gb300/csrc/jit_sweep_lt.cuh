@@ -29,15 +29,11 @@
 //   probability 1 - (1 - 4^-m)^64: 1, 1, 0.98, 0.64).  The decided lanes of
 //   a word are then written by the thread that owns it.  A word with lanes
 //   still undecided (a fifth of them) goes to a per-warp queue in shared
-//   memory; a round takes 32 queued words, so all lanes of the warp work,
-//   and runs pair 4 for them with its tables as immediates.  The lanes still
-//   undecided after that (about 0.07 per word) go one by one, as 8-byte
-//   items (site, lane, class, next pair, slot), to a second queue, whose
-//   rounds compare an item's two random bits of one pair with the two
-//   threshold bits of its class and either finish it or put it back with
-//   the next pair.  Lanes finished from a queue are flipped by an atomic XOR
-//   of their bits, since the word's owner has already written it and
-//   several of its lanes may finish in one round.
+//   memory; a round takes 32 queued words, so every lane of the warp has
+//   one, and runs pairs 4, 5, ... in lockstep while any of them is
+//   undecided (tables as immediates up to pair 7, read at run time after
+//   that).  Its lanes are then flipped by an atomic XOR of their bits, since
+//   the word's owner has already written the word.
 #include "common.cuh"
 
 namespace ianus {
@@ -59,25 +55,17 @@ constexpr int kWarps = kBlock / 32;
 constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
 constexpr uint32_t kFull = 0xffffffffu;
 constexpr int kHeadPairs = 4;  // plane pairs every word runs
-constexpr uint32_t kQ = 64;            // lane queue: < 32 left + <= 32 pushed
+#ifndef IANUS_JIT_PERSIST
+#define IANUS_JIT_PERSIST 0
+#endif
 constexpr uint32_t kQW = 32 * (R + 1);  // word queue: < 32 left + <= 32 per slot pushed
 
-// Class threshold as a 32-bit number: bit (31 - p) of T_u is bit u of the
-// truth table of plane p.  Evaluated at compile time; used by the queued
-// lanes.
-__host__ __device__ constexpr uint32_t thr_of(int u) {
-  uint32_t t = 0;
-  for (int p = 0; p < 32; ++p) t |= ((kLut[p] >> u) & 1u) << (31 - p);
-  return t;
-}
-
-__device__ __forceinline__ uint32_t class_threshold(uint32_t u) {
-  constexpr uint32_t t0 = thr_of(0), t1 = thr_of(1), t2 = thr_of(2), t3 = thr_of(3), t4 = thr_of(4),
-                     t5 = thr_of(5), t6 = thr_of(6), t7 = thr_of(7);
-  const uint32_t v[8] = {t0, t1, t2, t3, t4, t5, t6, t7};
-  uint32_t r = t0;
+// Truth table of plane p (0..31) at run time.
+__device__ __forceinline__ uint32_t lut_of(uint32_t p) {
+  constexpr uint32_t v[32] = {IANUS_JIT_LUTS};
+  uint32_t r = v[0];
 #pragma unroll
-  for (int k = 1; k < 8; ++k) r = u == (uint32_t)k ? v[k] : r;
+  for (int k = 1; k < 32; ++k) r = p == (uint32_t)k ? v[k] : r;
   return r;
 }
 
@@ -145,11 +133,6 @@ __device__ __forceinline__ void pair_planes(Half& lo, Half& hi, const uint4& x) 
   plane<2 * M + 1>(hi, x.w);
 }
 
-// A queued lane: site, lane, class, next plane pair, slot.
-struct Item {
-  uint32_t site, meta;  // meta: lane | class << 6 | pair << 9 | slot << 13
-};
-
 // A queued word (undecided after pairs 0..3): site and slot, the undecided
 // lanes and the class planes, in three parts so that each store and load is
 // one 16- or 8-byte access.
@@ -161,9 +144,8 @@ struct WordQ {
 
 struct Shared {
   uint4 u[R * 16];         // uniform parts of rounds 0..1 per (slot, pair)
-  uint32_t thr[8];         // class thresholds
+  uint8_t lut[32];         // truth tables of the planes (pairs 8..15 read them at run time)
   WordQ wq[kWarps];        // per-warp queues of words that need pair kHeadPairs
-  Item lq[kWarps][kQ];     // per-warp queues of single lanes (pairs kHeadPairs + 1 ..)
 };
 
 struct Ctx {
@@ -181,48 +163,48 @@ __device__ __forceinline__ uint32_t self_of(uint32_t site, int colour) {
 
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << (threadIdx.x & 31u)) - 1u; }
 
-// One round over the top `take` (<= 32) queued lanes: one plane pair each.
-// A lane whose random bits equal its threshold bits goes back with the next
-// pair; after pair 15 (all 32 bits equal) r == T, which is not below.
-__device__ __forceinline__ void lane_round(const Shared& sh, Item* q, uint32_t& nq, uint32_t take, const Ctx& c) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const bool has = lane < take;
-  Item it{0u, 0u};
-  if (has) it = q[nq - take + lane];
-  __syncwarp();
-  nq -= take;
-  bool again = false;
-  if (has) {
-    const uint32_t l = it.meta & 63u, cls = (it.meta >> 6) & 7u, m = (it.meta >> 9) & 15u, a = it.meta >> 13;
-    const uint4 x = rounds_rest(site_key(it.site, c.thi_k), sh.u[a * 16u + m], *c.keys);
-    const uint32_t w0 = l < 32u ? x.x : x.y, w1 = l < 32u ? x.z : x.w;
-    const uint32_t rb = (((w0 >> (l & 31u)) & 1u) << 1) | ((w1 >> (l & 31u)) & 1u);
-    const uint32_t tb = (sh.thr[cls] >> (30u - 2u * m)) & 3u;
-    if (rb == tb && m < 15u) {
-      again = true;
-      it.meta += 1u << 9;
-    } else {
-      const bool lt = rb < tb;
-      const bool flip = ALGO == 0 ? lt : !lt;
-      if (flip) {
-        uint64_t* w = c.sp0 + (uint64_t)a * kJitSites + self_of(it.site, c.colour);
-        atomicXor((unsigned long long*)w, 1ull << l);
-      }
-    }
-  }
-  const uint32_t bal = __ballot_sync(kFull, again);
-  if (again) q[nq + __popc(bal & lanemask_lt())] = it;
-  nq += __popc(bal);
-  __syncwarp();
+// Spin words.  In the persistent form other blocks write them during the
+// launch, so they are read from L2 (ld.global.cg), never from a stale L1 line.
+__device__ __forceinline__ uint64_t ld_spin(const uint64_t* p) {
+#if IANUS_JIT_PERSIST
+  return __ldcg((const unsigned long long*)p);
+#else
+  return *p;
+#endif
 }
 
-// One round over the top `take` (<= 32) queued words: plane pair kHeadPairs
-// with its tables as immediates; lanes decided there are flipped in place,
-// lanes still undecided go to the lane queue one at a time.
-__device__ __forceinline__ void word_round(Shared& sh, uint32_t& nw, uint32_t take, uint32_t& nl, const Ctx& c) {
+// Plane p with its truth table given at run time (pairs 8..15, rarely
+// reached): bit u of tab for a lane of class u, by a multiplexer tree.
+__device__ __forceinline__ void plane_rt(Half& h, uint32_t r, uint32_t tab) {
+  uint32_t m[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) m[k] = 0u - ((tab >> k) & 1u);
+  const uint32_t a0 = lop3<0xCA>(h.u0, m[1], m[0]), a1 = lop3<0xCA>(h.u0, m[3], m[2]);
+  const uint32_t a2 = lop3<0xCA>(h.u0, m[5], m[4]), a3 = lop3<0xCA>(h.u0, m[7], m[6]);
+  const uint32_t b0 = lop3<0xCA>(h.u1, a1, a0), b1 = lop3<0xCA>(h.u1, a3, a2);
+  const uint32_t t = lop3<0xCA>(h.u2, b1, b0);
+  h.res = lop3<0xCA>(h.und, t, h.res);
+  h.und = lop3<0x90>(h.und, r, t);
+}
+
+// Pairs M..7 of a queued word in lockstep across the warp, while any word
+// of the warp is undecided, with the tables as immediates.
+template <int M>
+__device__ __forceinline__ void tail_pairs(Half& lo, Half& hi, const SiteKey& sk, const uint4* U,
+                                           const PhiloxKeys& K) {
+  if constexpr (M < 8) {
+    if (!__any_sync(kFull, (lo.und | hi.und) != 0u)) return;
+    pair_planes<M>(lo, hi, rounds_rest(sk, U[M], K));
+    tail_pairs<M + 1>(lo, hi, sk, U, K);
+  }
+}
+
+// One round over the top `take` (<= 32) queued words: pair kHeadPairs and
+// the following ones until every word of the warp is decided; the queued
+// lanes are then flipped in place.
+__device__ __forceinline__ void word_round(Shared& sh, uint32_t& nw, uint32_t take, const Ctx& c) {
   const uint32_t wp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   WordQ& wq = sh.wq[wp];
-  Item* lq = sh.lq[wp];
   const bool has = lane < take;
   uint4 qa = make_uint4(0u, 0u, 0u, 0u), qb = qa;
   uint2 qc = make_uint2(0u, 0u);
@@ -235,38 +217,25 @@ __device__ __forceinline__ void word_round(Shared& sh, uint32_t& nw, uint32_t ta
   __syncwarp();
   nw -= take;
   Half lo{qb.x, qb.z, qc.x, qa.z, 0u}, hi{qb.y, qb.w, qc.y, qa.w, 0u};
+  const SiteKey sk = site_key(qa.x, c.thi_k);
+  const uint4* U = sh.u + qa.y * 16u;
+  tail_pairs<kHeadPairs>(lo, hi, sk, U, *c.keys);
+  for (uint32_t m = 8; m < 16u && __any_sync(kFull, (lo.und | hi.und) != 0u); ++m) {
+    const uint4 x = rounds_rest(sk, U[m], *c.keys);
+    const uint32_t t0 = sh.lut[2u * m], t1 = sh.lut[2u * m + 1u];
+    plane_rt(lo, x.x, t0);
+    plane_rt(hi, x.y, t0);
+    plane_rt(lo, x.z, t1);
+    plane_rt(hi, x.w, t1);
+  }
   if (has) {
-    const uint4 x = rounds_rest(site_key(qa.x, c.thi_k), sh.u[qa.y * 16u + kHeadPairs], *c.keys);
-    pair_planes<kHeadPairs>(lo, hi, x);
-    const uint32_t dlo = qa.z & ~lo.und, dhi = qa.w & ~hi.und;  // decided at this pair
-    const uint64_t flip = ((uint64_t)((ALGO == 0 ? lo.res : ~lo.res) & dlo)) |
-                          ((uint64_t)((ALGO == 0 ? hi.res : ~hi.res) & dhi) << 32);
+    // lanes still undecided after 32 planes have r == T: not below
+    const uint32_t rlo = lo.res & ~lo.und, rhi = hi.res & ~hi.und;
+    const uint64_t flip = ((uint64_t)((ALGO == 0 ? rlo : ~rlo) & qa.z)) | ((uint64_t)((ALGO == 0 ? rhi : ~rhi) & qa.w) << 32);
     if (flip) {
       uint64_t* w = c.sp0 + (uint64_t)qa.y * kJitSites + self_of(qa.x, c.colour);
       atomicXor((unsigned long long*)w, flip);
     }
-  }
-  uint32_t plo = has ? lo.und : 0u, phi = has ? hi.und : 0u;
-  for (;;) {
-    const bool more = (plo | phi) != 0u;
-    const uint32_t bal = __ballot_sync(kFull, more);
-    if (bal == 0u) break;
-    if (more) {
-      const bool up = plo == 0u;
-      const uint32_t w = up ? phi : plo;
-      const uint32_t bit = w & (0u - w);
-      const uint32_t s = 31u - __clz(bit);
-      if (up) phi ^= bit;
-      else plo ^= bit;
-      const uint32_t v0 = up ? hi.u0 : lo.u0, v1 = up ? hi.u1 : lo.u1, v2 = up ? hi.u2 : lo.u2;
-      const uint32_t cls = (((v2 >> s) & 1u) << 2) | (((v1 >> s) & 1u) << 1) | ((v0 >> s) & 1u);
-      const uint32_t l = s + (up ? 32u : 0u);
-      lq[nl + __popc(bal & lanemask_lt())] =
-          Item{qa.x, l | (cls << 6) | ((uint32_t)(kHeadPairs + 1) << 9) | (qa.y << 13)};
-    }
-    nl += __popc(bal);
-    __syncwarp();
-    if (nl >= 32u) lane_round(sh, lq, nl, 32u, c);
   }
 }
 
@@ -292,40 +261,15 @@ __device__ __forceinline__ void head_pairs(Half (&lo)[R], Half (&hi)[R], const S
   }
 }
 
-}  // namespace jlt
-}  // namespace ianus
-
-extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
-    ianus_jit_sweep_lt(const ianus::BitsParams p) {
-  using namespace ianus;
-  using namespace ianus::jlt;
-  __shared__ Shared sh;
-  dependent_launch_entry();
-  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
-  const int g = blockIdx.y;  // one temperature: blockIdx.y = group
-  // uniform parts of Philox rounds 0 and 1 for every (slot, pair)
-  if (threadIdx.x < (unsigned)(R * 16)) {
-    const uint32_t a = threadIdx.x >> 4, m = threadIdx.x & 15u;
-    const uint32_t c2 = (TAG_SPIN << 28) | (m << 24) | (a << 12) | (uint32_t)g;
-    const uint64_t p1 = (uint64_t)kM1 * c2;
-    const uint32_t c0r = (uint32_t)(p1 >> 32) ^ tk.lo ^ p.keys.k0[0];
-    const uint64_t p0 = (uint64_t)kM0 * c0r;
-    sh.u[threadIdx.x] = make_uint4((uint32_t)p1 ^ p.keys.k0[1], (uint32_t)(p0 >> 32) ^ p.keys.k1[1], (uint32_t)p0, 0u);
-  }
-  if (threadIdx.x < 8) sh.thr[threadIdx.x] = class_threshold(threadIdx.x);
-  __syncthreads();
+// The colour-c words [w_begin, w_end) of one group (word w = row * L/2 + k
+// of the colour's half rows): pairs 0..3 for every word, then the queues,
+// drained before returning.
+__device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint64_t* __restrict__ Jg,
+                                            uint32_t w_begin, uint32_t w_end) {
   constexpr Geom geom = kJitGeom;
   constexpr uint32_t N = kJitSites;
-  Ctx c;
-  c.keys = &p.keys;
-  c.thi_k = tk.hi ^ p.keys.k1[0];
-  c.sp0 = p.spins + (uint64_t)g * R * N;
-  c.colour = p.colour;
-  const uint64_t* Jg = p.J + (uint64_t)g * D * N;
   WordQ& wq = sh.wq[threadIdx.x >> 5];
-  uint32_t nw = 0, nl = 0;
-  const uint32_t w_begin = blockIdx.x * p.words_per_block;
-  const uint32_t w_end = min(w_begin + p.words_per_block, geom.half);
+  uint32_t nw = 0;
   for (uint32_t base = w_begin; base < w_end; base += kBlock) {
     const uint32_t wi = base + threadIdx.x;
     if (__ballot_sync(kFull, wi < w_end) == 0u) break;  // warp past the end of the block's words
@@ -335,7 +279,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
     uint64_t b[R];
     Nbr n{};
     if (valid) {
-      n = split_neighbours_t<P2>(geom, p.colour, wi);
+      n = split_neighbours_t<P2>(geom, c.colour, wi);
       site = n.site;
       uint64_t jw[2 * D];
       jw[0] = __ldg(Jg + n.self);
@@ -349,15 +293,15 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
 #pragma unroll
       for (int a = 0; a < R; ++a) {
         const uint64_t* sp = c.sp0 + (uint64_t)a * N;
-        b[a] = sp[n.self];
+        b[a] = ld_spin(sp + n.self);
         uint64_t e[2 * D];
-        e[0] = b[a] ^ sp[n.xp] ^ jw[0];
-        e[1] = b[a] ^ sp[n.xm] ^ jw[1];
-        e[2] = b[a] ^ sp[n.yp] ^ jw[2];
-        e[3] = b[a] ^ sp[n.ym] ^ jw[3];
+        e[0] = b[a] ^ ld_spin(sp + n.xp) ^ jw[0];
+        e[1] = b[a] ^ ld_spin(sp + n.xm) ^ jw[1];
+        e[2] = b[a] ^ ld_spin(sp + n.yp) ^ jw[2];
+        e[3] = b[a] ^ ld_spin(sp + n.ym) ^ jw[3];
         if (D == 3) {
-          e[4] = b[a] ^ sp[n.zp] ^ jw[4];
-          e[5] = b[a] ^ sp[n.zm] ^ jw[5];
+          e[4] = b[a] ^ ld_spin(sp + n.zp) ^ jw[4];
+          e[5] = b[a] ^ ld_spin(sp + n.zm) ^ jw[5];
         }
         uint64_t u0, u1, u2;
         count_unsat<D>(e, u0, u1, u2);
@@ -388,7 +332,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
       }
     }
     const SiteKey sk = site_key(site, c.thi_k);
-    head_pairs<0>(lo, hi, sk, sh, p.keys);
+    head_pairs<0>(lo, hi, sk, sh, *c.keys);
     // decided lanes: flip where (r < T) != heat bath
 #pragma unroll
     for (int a = 0; a < R; ++a) {
@@ -411,8 +355,146 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
       nw += __popc(bal);
     }
     __syncwarp();
-    while (nw >= 32u) word_round(sh, nw, 32u, nl, c);
+    while (nw >= 32u) word_round(sh, nw, 32u, c);
   }
-  while (nw > 0u) word_round(sh, nw, nw < 32u ? nw : 32u, nl, c);
-  while (nl > 0u) lane_round(sh, sh.lq[threadIdx.x >> 5], nl, nl < 32u ? nl : 32u, c);
+  while (nw > 0u) word_round(sh, nw, nw < 32u ? nw : 32u, c);
 }
+
+// Uniform parts of Philox rounds 0 and 1 for every (slot, pair) of group g
+// at sweep tk (threads 0 .. 16R - 1).
+__device__ __forceinline__ void fill_uniform(Shared& sh, uint32_t g, const Tick& tk, const PhiloxKeys& K) {
+  if (threadIdx.x < (unsigned)(R * 16)) {
+    const uint32_t a = threadIdx.x >> 4, m = threadIdx.x & 15u;
+    const uint32_t c2 = (TAG_SPIN << 28) | (m << 24) | (a << 12) | g;
+    const uint64_t p1 = (uint64_t)kM1 * c2;
+    const uint32_t c0r = (uint32_t)(p1 >> 32) ^ tk.lo ^ K.k0[0];
+    const uint64_t p0 = (uint64_t)kM0 * c0r;
+    sh.u[threadIdx.x] = make_uint4((uint32_t)p1 ^ K.k0[1], (uint32_t)(p0 >> 32) ^ K.k1[1], (uint32_t)p0, 0u);
+  }
+}
+
+}  // namespace jlt
+}  // namespace ianus
+
+#if !IANUS_JIT_PERSIST
+
+// One colour pass: block (x, g) updates colour words [x wpb, (x + 1) wpb) of
+// group g.
+extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
+    ianus_jit_sweep_lt(const ianus::BitsParams p) {
+  using namespace ianus;
+  using namespace ianus::jlt;
+  __shared__ Shared sh;
+  dependent_launch_entry();
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  const uint32_t g = blockIdx.y;  // one temperature: blockIdx.y = group
+  fill_uniform(sh, g, tk, p.keys);
+  if (threadIdx.x < 32) sh.lut[threadIdx.x] = (uint8_t)lut_of(threadIdx.x);
+  __syncthreads();
+  Ctx c;
+  c.keys = &p.keys;
+  c.thi_k = tk.hi ^ p.keys.k1[0];
+  c.sp0 = p.spins + (uint64_t)g * R * kJitSites;
+  c.colour = p.colour;
+  const uint32_t w_begin = blockIdx.x * p.words_per_block;
+  const uint32_t w_end = min(w_begin + p.words_per_block, kJitGeom.half);
+  sweep_words(sh, c, p.J + (uint64_t)g * D * kJitSites, w_begin, w_end);
+}
+
+#else
+
+namespace ianus {
+namespace jlt {
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Waits until *f >= target (acquire at GPU scope), at most timeout_ns.
+__device__ __forceinline__ bool wait_flag(const uint32_t* f, uint32_t target, uint64_t timeout_ns) {
+  const uint64_t t0 = global_ns();
+  uint32_t nap = 32;
+  for (;;) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(f) : "memory");
+    if (v >= target) return true;
+    if (global_ns() - t0 > timeout_ns) return false;
+    __nanosleep(nap);
+    if (nap < 256u) nap <<= 1;
+  }
+}
+
+// Block of group-row r when rows [j Rg / cpg, (j + 1) Rg / cpg) belong to block j.
+__device__ __forceinline__ uint32_t owner(uint32_t r, uint32_t cpg, uint32_t Rg) {
+  return (uint32_t)((((uint64_t)r + 1u) * cpg - 1u) / Rg);
+}
+
+}  // namespace jlt
+}  // namespace ianus
+
+// npass colour passes in one launch, the blocks of a pass separated by
+// bounded waits on their neighbours' progress flags (see PersistParams).
+// Launched cooperatively, so that every block is resident.
+extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
+    ianus_jit_sweep_ltp(const ianus::BitsParams p, const ianus::PersistParams pp) {
+  using namespace ianus;
+  using namespace ianus::jlt;
+  __shared__ Shared sh;
+  __shared__ int s_abort;
+  const uint32_t b = blockIdx.x;
+  if ((int32_t)b == pp.skip_block) return;
+  constexpr uint32_t L = (uint32_t)IANUS_JIT_L, h = L / 2u, Rg = kJitSites / L;
+  constexpr uint32_t W = D == 3 ? L : 1u;  // rows between a site and its farthest neighbour
+  const uint32_t cpg = pp.cpg, g = b / cpg, j = b - g * cpg;
+  const uint32_t ra = (uint32_t)(((uint64_t)j * Rg) / cpg), rb = (uint32_t)(((uint64_t)(j + 1u) * Rg) / cpg);
+  // blocks owning the rows of the cyclic interval [ra - W, rb + W)
+  uint32_t dlo = 0, ndep = cpg;
+  if (rb - ra + 2u * W < Rg) {
+    dlo = owner((ra + Rg - W) % Rg, cpg, Rg);
+    const uint32_t dhi = owner((rb - 1u + W) % Rg, cpg, Rg);
+    ndep = (dhi + cpg - dlo) % cpg + 1u;
+  }
+  if (threadIdx.x < 32) sh.lut[threadIdx.x] = (uint8_t)lut_of(threadIdx.x);
+  if (threadIdx.x == 0) s_abort = 0;
+  Ctx c;
+  c.keys = &p.keys;
+  c.sp0 = p.spins + (uint64_t)g * R * kJitSites;
+  const uint64_t* Jg = p.J + (uint64_t)g * D * kJitSites;
+  const uint64_t t0 = (uint64_t)pp.t0_lo | ((uint64_t)pp.t0_hi << 32);
+  for (uint32_t pass = 0; pass < pp.npass; ++pass) {
+    if (pass > 0u) {
+      if (threadIdx.x < 32u) {
+        bool ok = true;
+        for (uint32_t d = threadIdx.x; d < ndep; d += 32u) {
+          const uint32_t blk = g * cpg + (dlo + d) % cpg;
+          if (blk != b && ok) ok = wait_flag(pp.flags + blk, pass, pp.timeout_ns);
+        }
+        if (!__all_sync(kFull, ok) && threadIdx.x == 0) {
+          atomicOr(pp.err, ERR_TIMEOUT);
+          s_abort = 1;
+        }
+        __threadfence();
+      }
+      __syncthreads();
+      if (s_abort) return;
+    }
+    const uint64_t t = t0 + (pass >> 1);
+    const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
+    if ((pass & 1u) == 0u) {  // a new sweep: its uniform Philox parts
+      fill_uniform(sh, g, tk, p.keys);
+      __syncthreads();
+    }
+    c.thi_k = tk.hi ^ p.keys.k1[0];
+    c.colour = (int)(pass & 1u);
+    sweep_words(sh, c, Jg, ra * h, rb * h);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(pp.flags + b), "r"(pass + 1u) : "memory");
+    }
+  }
+}
+
+#endif

@@ -1066,23 +1066,103 @@ constexpr JitShape kJitShapes[] = {
     {0, 8, 4, 2, 1, 0, 256}, {0, 8, 4, 1, 1, 0, 256}, {1, 4, 4, 1, 1, 0, 256}, {1, 4, 3, 2, 0, 1, 256},
     {0, 8, 4, 2, 0, 1, 256}, {0, 8, 3, 2, 0, 1, 256}, {1, 4, 7, 2, 0, 1, 128}, {1, 4, 6, 2, 0, 1, 128},
     // mode 3: the lane-queue kernel (jit_sweep_lt.cuh), blocks/SM and block size
-    {3, 4, 8, 1, 0, 0, 128}, {3, 4, 6, 1, 0, 0, 128}, {3, 4, 4, 1, 0, 0, 256}};
+    {3, 4, 8, 1, 0, 0, 128}, {3, 4, 6, 1, 0, 0, 128}, {3, 4, 4, 1, 0, 0, 256},
+    // mode 4: its persistent form; phase_a = least colour words per block / 128
+    {4, 4, 8, 1, 0, 0, 128}, {4, 1, 8, 1, 0, 0, 128}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
-constexpr int kAutoJitVariant = 2;
+constexpr int kAutoJitVariant = 24;  // the lane-queue kernel, 4 blocks of 256 per SM
 
 // The specialised kernel shape the next sweep uses (>= 2), or 1 for the
 // precompiled per-lane kernel.
 int jit_variant_for(const Lattice& lat) {
-  const uint64_t words = (uint64_t)lat.G * lat.slots * lat.N;
   int v = lat.variant;
-  if (v == 0) v = words >= (1ull << 20) ? kAutoJitVariant : 1;
+  if (v == 0) v = kAutoJitVariant;
   bool ok = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
   if (ok && kJitShapes[v - 2].mode == 2 && lat.R != 2) v = 2;  // the interleaved shape needs two replicas
   return ok ? v : 1;
 }
 
 }  // namespace
+
+bool persistent_variant(const Lattice& lat) {
+  const int v = jit_variant_for(lat);
+  return v >= 2 && kJitShapes[v - 2].mode == 4 && !lat.field && lat.flags;
+}
+
+cudaError_t launch_sweep_persistent(Lattice& lat, int inv, uint64_t t0, uint32_t nsweeps, bool* ran) {
+  *ran = false;
+  const int v = jit_variant_for(lat);
+  if (v < 2 || kJitShapes[v - 2].mode != 4 || nsweeps == 0) return cudaSuccess;
+  const JitShape& js = kJitShapes[v - 2];
+  prepare_sweep_bits(lat, inv);
+  if (!lat.jit) return cudaSuccess;
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)lat.jit, js.block, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  // blocks per group: as many as are resident at once, each with at least
+  // phase_a * 128 colour words and at least one row
+  const uint32_t Rg = lat.N / (uint32_t)lat.L, h = (uint32_t)lat.L / 2u;
+  const uint32_t resident = (uint32_t)sms * (uint32_t)per_sm;
+  uint32_t cpg = resident / (uint32_t)lat.G;
+  const uint32_t min_words = 128u * (uint32_t)js.phase_a;
+  cpg = std::min(cpg, std::max<uint32_t>(1u, Rg * h / min_words));
+  cpg = std::min(cpg, Rg);
+  const uint64_t blocks = (uint64_t)cpg * (uint64_t)lat.G;
+  if (cpg == 0 || blocks > (uint64_t)resident || blocks > (uint64_t)kMaxPersistBlocks) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(lat.flags, 0, (size_t)blocks * 4, lat.stream);
+  if (e != cudaSuccess) return e;
+  BitsParams p;
+  p.spins = (uint64_t*)lat.spins;
+  p.J = (const uint64_t*)lat.J;
+  p.tp = lat.tp;
+  p.geom = lat.geom;
+  p.G = lat.G;
+  p.R = lat.R;
+  p.K = lat.K;
+  p.slots = lat.slots;
+  p.colour = 0;
+  p.t_lo = (uint32_t)t0;
+  p.t_hi = (uint32_t)(t0 >> 32);
+  p.words_per_block = 0;
+  p.keys = lat.keys;
+  p.t_dev = nullptr;
+  PersistParams pp;
+  pp.flags = lat.flags;
+  pp.err = lat.err;
+  pp.npass = 2u * nsweeps;
+  pp.cpg = cpg;
+  pp.t0_lo = (uint32_t)t0;
+  pp.t0_hi = (uint32_t)(t0 >> 32);
+  pp.timeout_ns = lat.persist_timeout_ns;
+  pp.skip_block = lat.persist_absent;
+  void* args[] = {(void*)&p, (void*)&pp};
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3((unsigned)js.block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = lat.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelExC(&cfg, (const void*)lat.jit, args);
+  if (e == cudaErrorCooperativeLaunchTooLarge) {  // not resident at once here: per-pass kernels instead
+    cudaGetLastError();
+    return cudaSuccess;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return e;
+  }
+  *ran = true;
+  return cudaSuccess;
+}
 
 void prepare_sweep_bits(Lattice& lat, int inv) {
   const int algo = inv ? 1 : 0;
@@ -1279,7 +1359,9 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   if (v >= 2) {
     const JitShape& js = kJitShapes[v - 2];
     prepare_sweep_bits(lat, inv);
-    if (lat.jit && js.mode == 3) {
+    // mode 4 (persistent) passes that run one at a time use its per-pass form
+    const cudaKernel_t k3 = js.mode == 4 ? jit_lt_kernel(lat, algo, js.min_blocks, js.block) : lat.jit;
+    if (k3 && (js.mode == 3 || js.mode == 4)) {
       // one wave: about min_blocks blocks per SM in all, whole warps of words
       uint32_t w3;
       if (lat.block_words) {
@@ -1291,8 +1373,8 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
       }
       p.words_per_block = w3;
       void* args[] = {(void*)&p};
-      return launch_dependent((const void*)lat.jit, dim3((half + w3 - 1u) / w3, (unsigned)lat.G), dim3(js.block), args,
-                              0, lat.stream);
+      return launch_dependent((const void*)k3, dim3((half + w3 - 1u) / w3, (unsigned)lat.G), dim3(js.block), args, 0,
+                              lat.stream);
     }
     if (lat.jit) {
       const uint8_t* lut_t = (const uint8_t*)(lat.thr + (size_t)lat.K * kMaxClasses);

@@ -91,6 +91,9 @@ struct Lattice {
   int64_t* ser_M;       // [cap][S*K*R*mq]
   int64_t* ser_Q;       // [cap][S*K]
   uint32_t* err;        // device error word
+  uint32_t* flags;      // progress flags of the persistent sweep [kMaxPersistBlocks]
+  uint64_t persist_timeout_ns;  // bound of each wait of the persistent sweep
+  int32_t persist_absent;       // block told to return at once (tests), -1 = none
 
   // field models (RFIM, DAFF)
   int disorder;         // IANUS_DISORDER_*
@@ -185,7 +188,18 @@ cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int
 // The lane-queue shape of the same sweep (jit_sweep_lt.cuh): shared Philox
 // rounds 0..1, four plane pairs for every word, undecided lanes queued.
 cudaKernel_t jit_lt_kernel(const Lattice& lat, int algo, int min_blocks, int block);
-constexpr int kMaxVariant = 24;  // ianus_set_variant accepts 0..kMaxVariant
+// Its persistent form (IANUS_JIT_PERSIST): many sweeps per launch.
+cudaKernel_t jit_ltp_kernel(const Lattice& lat, int algo, int min_blocks, int block);
+constexpr int kMaxVariant = 26;  // ianus_set_variant accepts 0..kMaxVariant
+constexpr int kMaxPersistBlocks = 4096;
+// True when the selected variant is the persistent sweep and the lattice
+// qualifies (one temperature, one or two replicas, lane-uniform tables).
+bool persistent_variant(const Lattice& lat);
+// Runs nsweeps sweeps from sweep t0 in one cooperative launch of the
+// persistent sweep.  *ran = false (and cudaSuccess) when it cannot run here
+// (no run-time compiler, or too many blocks to be resident at once): the
+// caller then sweeps with the per-pass kernels.
+cudaError_t launch_sweep_persistent(Lattice& lat, int inv, uint64_t t0, uint32_t nsweeps, bool* ran);
 // Run-time specialised random-field sweep for lat.flut (jit.cu; null when
 // unavailable).
 cudaKernel_t jit_field_kernel(const Lattice& lat, int algo, int min_blocks);

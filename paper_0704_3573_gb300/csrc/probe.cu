@@ -28,6 +28,30 @@ __device__ __forceinline__ uint64_t mad_wide(uint32_t a, uint32_t b, uint64_t c)
   return d;
 }
 
+__device__ __forceinline__ uint32_t mad_lo(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("mad.lo.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t mul_hi(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm volatile("mul.hi.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t mul_lo(uint32_t a, uint32_t b) {
+  uint32_t d;
+  asm volatile("mul.lo.u32 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+  return d;
+}
+
+__device__ __forceinline__ uint32_t add3(uint32_t a, uint32_t b, uint32_t c) {
+  uint32_t d;
+  asm volatile("{ .reg .u32 t; add.u32 t, %1, %2; add.u32 %0, t, %3; }" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+
 __device__ __forceinline__ uint32_t smid() {
   uint32_t r;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
@@ -65,6 +89,116 @@ __global__ void __launch_bounds__(kThreads) k_probe(int kind, uint32_t seed, uin
         x[j] = lop3_xor(x[j], (uint32_t)(w[j] >> 32), 0x6789u);
       }
     }
+  } else if (kind == 4) {  // independent lop3 and mad.wide chains side by side
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = lop3_xor(x[j], x[(j + 1) & 3], 0x5A5A5A5Au);
+        w[4 + j] = mad_wide(x[4 + j], 0xD2511F53u, w[4 + j]);
+      }
+    }
+  } else if (kind == 5) {  // 32-bit multiply-add
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = mad_lo(x[j], 0x9E3779B1u, x[(j + 1) & 7]);
+    }
+  } else if (kind == 6) {  // three-input add
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = add3(x[j], x[(j + 1) & 7], x[(j + 3) & 7]);
+    }
+  } else if (kind == 7) {  // independent lop3 and 32-bit multiply-add chains side by side
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = lop3_xor(x[j], x[(j + 1) & 3], 0x5A5A5A5Au);
+        x[4 + j] = mad_lo(x[4 + j], 0x9E3779B1u, x[4 + ((j + 1) & 3)]);
+      }
+    }
+  } else if (kind == 8) {  // 32-bit high product chains
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = mul_hi(x[j], 0xD2511F53u);
+    }
+  } else if (kind == 9) {  // independent lop3 and 32-bit high-product chains side by side
+    for (int i = 0; i < kIters; ++i) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        x[j] = lop3_xor(x[j], x[(j + 1) & 3], 0x5A5A5A5Au);
+        x[4 + j] = mul_hi(x[4 + j], 0xD2511F53u);
+      }
+    }
+  } else if (kind == 10) {  // Philox blocks with the products as separate high and low halves
+    for (int i = 0; i < kIters / 16; ++i) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        uint32_t c0 = x[4 * j], c1 = x[4 * j + 1], c2 = x[4 * j + 2], c3 = x[4 * j + 3];
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+          const uint32_t h0 = mul_hi(c0, 0xD2511F53u), l0 = mul_lo(c0, 0xD2511F53u);
+          const uint32_t h1 = mul_hi(c2, 0xCD9E8D57u), l1 = mul_lo(c2, 0xCD9E8D57u);
+          c0 = lop3_xor(h1, c1, keys.k0[r]);
+          c2 = lop3_xor(h0, c3, keys.k1[r]);
+          c1 = l1;
+          c3 = l0;
+        }
+        x[4 * j] = c0;
+        x[4 * j + 1] = c1;
+        x[4 * j + 2] = c2;
+        x[4 * j + 3] = c3;
+      }
+    }
+  } else if (kind >= 11) {
+    // Philox blocks with each product (11, 13) or the first product of a
+    // round (14) as a separate high multiply and a low multiply-add that
+    // cannot be merged with it (lo(a M) = a (M - 1) + a), or both as
+    // 64-bit products (12); 12..14 also run 24 lop3.b32 of an independent
+    // chain per block, as a sweep does besides its random numbers.
+    uint32_t y0 = x[0] ^ 0x1234u, y1 = x[1] ^ 0x5678u;
+    for (int i = 0; i < kIters / 16; ++i) {
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        uint32_t c0 = x[4 * j], c1 = x[4 * j + 1], c2 = x[4 * j + 2], c3 = x[4 * j + 3];
+#pragma unroll
+        for (int r = 0; r < 10; ++r) {
+          uint32_t h0, l0, h1, l1;
+          if (kind == 12) {
+            const uint64_t p0 = mad_wide(c0, 0xD2511F53u, 0ull), p1 = mad_wide(c2, 0xCD9E8D57u, 0ull);
+            h0 = (uint32_t)(p0 >> 32);
+            l0 = (uint32_t)p0;
+            h1 = (uint32_t)(p1 >> 32);
+            l1 = (uint32_t)p1;
+          } else if (kind == 14) {
+            const uint64_t p1 = mad_wide(c2, 0xCD9E8D57u, 0ull);
+            h0 = mul_hi(c0, 0xD2511F53u);
+            l0 = mad_lo(c0, 0xD2511F52u, c0);
+            h1 = (uint32_t)(p1 >> 32);
+            l1 = (uint32_t)p1;
+          } else {
+            h0 = mul_hi(c0, 0xD2511F53u);
+            l0 = mad_lo(c0, 0xD2511F52u, c0);
+            h1 = mul_hi(c2, 0xCD9E8D57u);
+            l1 = mad_lo(c2, 0xCD9E8D56u, c2);
+          }
+          c0 = lop3_xor(h1, c1, keys.k0[r]);
+          c2 = lop3_xor(h0, c3, keys.k1[r]);
+          c1 = l1;
+          c3 = l0;
+          if (kind != 11 && (r & 3) != 3) {  // 24 lop3 per block beside the block's own
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+              y0 = lop3_xor(y0, y1, 0x0F0F0F0Fu);
+              y1 = lop3_xor(y1, y0, 0x33333333u);
+            }
+          }
+        }
+        x[4 * j] = c0;
+        x[4 * j + 1] = c1;
+        x[4 * j + 2] = c2;
+        x[4 * j + 3] = c3;
+      }
+    }
+    x[5] ^= y0 ^ y1;
   } else {
     for (int i = 0; i < kIters / 16; ++i) {
 #pragma unroll
@@ -93,7 +227,7 @@ __global__ void __launch_bounds__(kThreads) k_probe(int kind, uint32_t seed, uin
 }  // namespace
 
 extern "C" int ianus_probe_int(int kind, int blocks_per_sm, double* out) {
-  if (kind < 0 || kind > 3 || blocks_per_sm < 1 || blocks_per_sm > 8 || !out) return 1;
+  if (kind < 0 || kind > 14 || blocks_per_sm < 1 || blocks_per_sm > 8 || !out) return 1;
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 3;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 3;
@@ -114,7 +248,7 @@ extern "C" int ianus_probe_int(int kind, int blocks_per_sm, double* out) {
   cudaFree(sink);
   if (e != cudaSuccess) return 3;
   double ops_per_block;
-  if (kind == 0 || kind == 1)
+  if (kind == 0 || kind == 1 || (kind >= 4 && kind <= 9))
     ops_per_block = (double)kThreads * kIters * 8;
   else if (kind == 2)
     ops_per_block = (double)kThreads * kIters * 8 * 3;
