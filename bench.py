@@ -53,19 +53,19 @@ SM_MAX_MHZ = 2070.0
 # kernel from one ncu capture of it on this workload, per (kernel variant,
 # words per block), valid while the kernel source is unchanged (hash of the
 # sources it is compiled from).
-TRAFFIC_BYTES_PER_LAUNCH = {(21, 256): 41976064 + 0}
-TRAFFIC_SOURCE_HASH = "5473351233ed34e4"
+TRAFFIC_BYTES_PER_LAUNCH = {}
+TRAFFIC_SOURCE_HASH = ""
 # The kernel variant and launch shape the bench runs by default: the
-# autotuner's pick on this workload (within noise of the other queued and
-# lockstep shapes), fixed so that the profile above describes the timed kernel.
-DEFAULT_VARIANT = (21, 256)
+# lane-queue kernel in its one-wave launch (the automatic choice for one
+# temperature), fixed so that the profile above describes the timed kernel.
+DEFAULT_VARIANT = (24, 0)
 
 
 def kernel_source_hash() -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("common.cuh", "jit_sweep.cuh", "jit.cu"):
+    for name in ("common.cuh", "jit_sweep_lt.cuh", "jit.cu"):
         with open(os.path.join(ROOT, "paper_0704_3573_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -85,25 +85,31 @@ def expected_plane_pairs(lanes: int = 64) -> float:
 
 
 def algorithmic_ops_per_word_hb3d(R_: int = 2) -> dict:
-    """Minimal 32-bit integer operations one 3D heat-bath update of a 64-lane
-    site word needs, by pipe (64-bit logic counts as two 32-bit operations):
-      ALU pipe, fixed: 6 unsatisfied-bond words (12), the 6->3 adder tree
-        (16), the always / needs-a-random masks (one lop3 each, 4), the flip
-        (2);
-      ALU pipe, per plane: the threshold bit-plane as one lop3 of
-        (u2, u1, u0) (2) and the compare (4);
-      per plane pair: one Philox4x32-10 block = 10 rounds x (2 lop3 on the
-        ALU pipe + 2 mad.wide on the FMA pipe) + 1 counter word, and the
-        2-op merge of decided lanes;
-      load/store pipe: 7 spin + 6/R coupling loads, 1 store;
-    times the expected number of plane pairs a word needs.  The ALU pipe
-    binds (64 lop3 per clock per SM against 62.7 mad.wide per clock on the
-    FMA pipe, which carries less than half as many)."""
+    """Least 32-bit integer operations one 3D heat-bath update of a 64-lane
+    site word needs (64-bit logic counts as two 32-bit operations), counted
+    on the resource they share: three-input logic (lop3) and 64-bit products
+    (mad.wide) issue from one slot on GB300 -- the probe's independent
+    lop3 / mad.wide chains run no faster together than either alone.
+      per word: 6 unsatisfied-bond words (12) and the 6 -> 3 adder tree (16)
+        of lop3; the flip as one lop3 per half (2);
+      per plane pair (times the expected pairs a word needs): Philox4x32-10
+        rounds 2..9, 8 x (2 mad.wide + 2 lop3) = 32; rounds 0 and 1 leave
+        each counter word a site part XOR a part shared by every site of the
+        block, 2 lop3 to combine them; the two planes, 3 lop3 per half each
+        (12);
+      once per word: plane 0 with every lane undecided takes 2 lop3 per half
+        instead of 3 (-2);
+      per site, shared by its R words: the site part of rounds 0 and 1
+        (2 mad.wide + 1 lop3).
+    Loads and stores (7 spin + 6/R coupling words, 1 store) issue elsewhere
+    and are listed apart.  ALU-only count of the earlier definition (Philox
+    rounds 0 and 1 not shared, 2-lop3 merges): the "alu_previous" entry."""
     e_p = expected_plane_pairs()
-    alu = (12 + 16 + 4 + 2) + e_p * (2 * (2 + 4) + 21 + 2)
-    fma = e_p * 20
+    lop3 = 12 + 16 + 2 + e_p * (16 + 2 + 12) - 2 + 1.0 / R_
+    mad_wide = e_p * 16 + 2.0 / R_
+    alu_previous = (12 + 16 + 4 + 2) + e_p * (2 * (2 + 4) + 21 + 2)
     lsu = 7 + 6.0 / R_ + 1
-    return {"alu": alu, "fma": fma, "lsu": lsu, "total": alu + fma + lsu}
+    return {"issue": lop3 + mad_wide, "lop3": lop3, "mad_wide": mad_wide, "lsu": lsu, "alu_previous": alu_previous}
 
 
 # ---------------- distributed helpers ----------------
@@ -218,21 +224,24 @@ def run_reference(args, ws, rank):
     o = oracle.Oracle(dim=3, L=L, sample_ids=ids, n_replicas=R, seed=SEED)
     for _ in range(args.warmup):
         o.sweep(oracle.HEATBATH, 1.0 / T, 1, nthreads=nthr)
+    # one step: MEASURE_EVERY sweeps ending in one E/Q measurement, as the workload measures
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        o.sweep(oracle.HEATBATH, 1.0 / T, 1, measure_every=1, nthreads=nthr)
+        o.sweep(oracle.HEATBATH, 1.0 / T, MEASURE_EVERY, measure_every=MEASURE_EVERY, nthreads=nthr)
         times.append(time.perf_counter() - t0)
-    upd_step = nthr * R * L ** 3
+    upd_step = nthr * R * L ** 3 * MEASURE_EVERY
     total = sum(times)
     value = upd_step * args.steps / (total * 1e9)
-    sample = f"{nthr} samples x {R} replicas of the L=64 workload, 1 sweep + E/Q per step"
+    sample = (f"{nthr} samples x {R} replicas of the L=64 workload, {MEASURE_EVERY} sweeps + one E/Q "
+              f"measurement per step (the workload's cadence); {cores} host cores")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i8", "data": "synthetic",
         "config": config_dict(ws),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": nthr, "nproc": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -308,19 +317,24 @@ def run_gpu(args, ws, rank, local):
     kern_s = a0.elapsed_time(a1) / 1e3 / (2 * nsw)
     words_per_launch = (S // 64) * R * L ** 3 // 2
     ops = algorithmic_ops_per_word_hb3d(R)
-    ops_word = ops["alu"]
-    achieved = ops_word * words_per_launch / kern_s / 1e12  # T ALU-pipe ops/s
+    achieved = ops["issue"] * words_per_launch / kern_s / 1e12  # T lop3 + mad.wide ops/s
     probe = probe_peak()
-    peak = probe["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if probe else None
+    peak = _issue_peak()
+    peak_alu = _alu_peak()
     vkey = (tuned["variant"], tuned["block_words"]) if tuned else None
     traffic = TRAFFIC_BYTES_PER_LAUNCH.get(vkey) if kernel_source_hash() == TRAFFIC_SOURCE_HASH else None
+    ach_prev = ops["alu_previous"] * words_per_launch / kern_s / 1e12
     roofline = {
-        "bound": "alu", "kernel": "ianus_jit_sweep (3D heat bath, R=2, thresholds as lop3 immediates)",
-        "achieved": achieved, "peak": peak, "unit": "T ALU-pipe int32 ops/s",
+        "bound": "alu", "kernel": "ianus_jit_sweep_lt (3D heat bath, R=2, lane-queue kernel, tables as lop3 "
+                                  "immediates)",
+        "achieved": achieved, "peak": peak, "unit": "T int32 ops/s (lop3 + mad.wide, one shared issue slot)",
         "frac": (achieved / peak) if peak else None, "traffic": traffic,
-        "alu_ops_per_word": ops_word, "all_ops_per_word": ops, "words_per_launch": words_per_launch,
-        "launch_us": kern_s * 1e6, "variant": tuned,
-        "peak_source": "probe lop3.b32 ops/clk/SM x 152 SMs x 2070 MHz" if probe else None,
+        "ops_per_word": ops, "words_per_launch": words_per_launch, "launch_us": kern_s * 1e6, "variant": tuned,
+        "peak_source": ("probe: independent lop3.b32 and mad.wide.u32 chains side by side, ops/clk/SM x 152 SMs "
+                        "x 2070 MHz (of measured)") if peak else None,
+        "previous_definition": {"alu_ops_per_word": ops["alu_previous"], "achieved": ach_prev, "peak": peak_alu,
+                                "frac": (ach_prev / peak_alu) if peak_alu else None,
+                                "what": "ALU-pipe share only, against lop3 alone"},
         "probe": probe,
     }
 
@@ -355,11 +369,12 @@ def run_gpu(args, ws, rank, local):
         import oracle
 
         oracle.build()
-        nthr = max(1, min(os.cpu_count() or 1, 16))
+        nproc = os.cpu_count() or 1
+        nthr = max(1, min(nproc, 16))
         rate, dt, upd = oracle_rate(nthr, args.cpu_sweeps)
-        cpu = {"value": rate, "unit": UNIT, "cores": nthr, "kind": "oracle",
-               "sample": f"samples 0..{nthr - 1} x {R} replicas, {args.cpu_sweeps} sweeps of the L=64 workload "
-                         f"({upd} updates, {dt:.1f} s wall)"}
+        cpu = {"value": rate, "unit": UNIT, "cores": nthr, "nproc": nproc, "kind": "oracle",
+               "sample": f"samples 0..{nthr - 1} x {R} replicas, {args.cpu_sweeps} sweeps of the L=64 workload with "
+                         f"E/Q every {MEASURE_EVERY} ({upd} updates, {dt:.1f} s wall)"}
 
     serving = run_serving(args) if (rank == 0 and args.serve_jobs > 0) else None
     others = run_other_configs(args) if (rank == 0 and not args.no_others) else None
@@ -410,14 +425,31 @@ def run_other_configs(args):
     # update of a site (about 410 cycles at 2070 MHz, read with clock64)
     floor_us = 2 * (0.19 + 410 / 2070.0)
     sweep_us = sec * 1e3
-    out["L16_single_sample_metropolis"] = {"updates_per_ns": 16 ** 3 * 1000 / (sec * 1e9), "ms_per_1000_sweeps": sec * 1e3,
+    # integer work per update (one lane of the plane stream, plain layout):
+    # the local field 2 per bond (12), E[pairs] = 1 + 1/4 + 1/16 + ... = 4/3
+    # Philox blocks of 16 lop3-class + 16 mad.wide (rounds 2..9) + 2 + 3 for
+    # rounds 0..1, the compare 3 per plane (8/3 planes), flip and write-back 2
+    rate16 = 16 ** 3 * 1000 / (sec * 1e9)
+    alu_u, madw_u = 12 + (4 / 3) * (16 + 2 + 1) + 3 * 8 / 3 + 2, (4 / 3) * (16 + 2)
+    ach = rate16 * (alu_u + madw_u) / 1e3
+    pk = _issue_peak()
+    sms_used = 16
+    out["L16_single_sample_metropolis"] = {"updates_per_ns": rate16, "ms_per_1000_sweeps": sec * 1e3,
                                            "sweep_us": sweep_us,
                                            "mode": "plain int8, one lattice split over a 16-block cluster "
                                                    "(one z-plane per block, halos in shared memory), E/M every sweep",
                                            "bound": "latency (2 cluster barriers and 2 dependent passes per sweep)",
-                                           "roofline": {"bound": "latency", "achieved": sweep_us, "peak": floor_us,
-                                                        "unit": "us per sweep (lower is better)",
-                                                        "frac": floor_us / sweep_us}}
+                                           "roofline": {"bound": "alu", "ops_per_update": alu_u + madw_u,
+                                                        "achieved": ach,
+                                                        "peak": pk * sms_used / SM_COUNT if pk else None,
+                                                        "unit": "T int32 ops/s on the 16 SMs used",
+                                                        "frac": ach / (pk * sms_used / SM_COUNT) if pk else None,
+                                                        "one_sm_peak": pk / SM_COUNT if pk else None,
+                                                        "frac_of_one_sm": ach / (pk / SM_COUNT) if pk else None},
+                                           "latency_floor": {"achieved_us": sweep_us, "floor_us": floor_us,
+                                                             "frac": floor_us / sweep_us,
+                                                             "what": "2 cluster barrier round trips + 2 dependent "
+                                                                     "site updates per sweep"}}
     if not args.no_cpu_baseline:
         import oracle
 
@@ -443,14 +475,12 @@ def run_other_configs(args):
     # need / undecided masks (4); per plane the threshold bit by 2
     # multiplexers (4) + compare (4), per pair Philox 21 ALU + merge 2;
     # ~3.9 plane pairs per word
+    # (and 20 mad.wide per Philox block)
     alu_word = 44 + 3.9 * (2 * 8 + 23)
-    peak = _alu_peak()
     out["L32_pt_32temps"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "bit-sliced, per-lane threshold planes, device PT swap every 10 sweeps",
-        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
-                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
-                     "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},
+        "roofline": issue_roof(alu_word, 3.9 * 20, 64, rate),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -476,9 +506,7 @@ def run_other_configs(args):
     out["potts_L32_128x2"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "4 samples per uint32 word, heat bath, E/Q every 10 sweeps",
-        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 4, "achieved": rate * alu_word / 4 / 1e3,
-                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
-                     "frac": (rate * alu_word / 4 / 1e3 / peak) if peak else None},
+        "roofline": issue_roof(alu_word, 20, 4, rate),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -508,9 +536,7 @@ def run_other_configs(args):
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "bit-sliced, field kernel specialised at run time ((u, f) tables as lop3 immediates), heat bath "
                 "T=2.0, |h|=1.5, E/M/F every 10 sweeps",
-        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
-                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
-                     "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},
+        "roofline": issue_roof(alu_word, 3.92 * 20, 64, rate),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -541,9 +567,7 @@ def run_other_configs(args):
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "bit-sliced with occupation words, kernel specialised at run time ((t, f) tables, t = v + 2D as "
                 "4 bit-planes), Metropolis T=1.5, |h|=1.0, occupation 0.7, E/M/F every 10 sweeps",
-        "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 64, "achieved": rate * alu_word / 64 / 1e3,
-                     "peak": peak, "unit": "T ALU-pipe int32 ops/s",
-                     "frac": (rate * alu_word / 64 / 1e3 / peak) if peak else None},
+        "roofline": issue_roof(alu_word, 3.92 * 20, 64, rate),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -572,14 +596,11 @@ def run_other_configs(args):
     rate = upd / (sec * 1e9)
     bytes_upd = (32 + 24) / 128.0
     hbm = MEASURED.get("hbm_gbs")
-    ops_word = algorithmic_ops_per_word_hb3d(R)["alu"]
-    peak_alu = _alu_peak()
+    ops = algorithmic_ops_per_word_hb3d(R)
     out["L128_256x2_hb_out_of_l2"] = {
         "updates_per_ns": rate, "ms_per_sweep": sec * 1e3 / (20 * reps),
-        "mode": "bit-sliced, specialised kernel (the bench variant), state 320 MiB > L2",
-        "roofline": {"bound": "alu", "achieved": rate * ops_word / 64 / 1e3, "peak": peak_alu,
-                     "unit": "T ALU-pipe int32 ops/s",
-                     "frac": (rate * ops_word / 64 / 1e3 / peak_alu) if peak_alu else None},
+        "mode": "bit-sliced, lane-queue kernel (the bench variant), state 320 MiB > L2",
+        "roofline": issue_roof(ops["lop3"], ops["mad_wide"], 64, rate),
         "hbm": {"bytes_per_update": bytes_upd, "achieved": rate * bytes_upd, "peak": hbm, "unit": "GB/s",
                 "frac": (rate * bytes_upd / hbm) if hbm else None},
     }
@@ -627,9 +648,7 @@ def run_other_configs(args):
         out[key] = {
             "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
             "mode": f"4 samples per uint32 word, {dim}D, heat bath beta={bp}, E/Q every 10 sweeps",
-            "roofline": {"bound": "alu", "alu_ops_per_update": alu_word / 4, "achieved": rate * alu_word / 4 / 1e3,
-                         "peak": peak, "unit": "T ALU-pipe int32 ops/s",
-                         "frac": (rate * alu_word / 4 / 1e3 / peak) if peak else None},
+            "roofline": issue_roof(alu_word, 20, 4, rate),
         }
         if not args.no_cpu_baseline:
             import oracle
@@ -670,6 +689,25 @@ def _alu_peak():
     return p["lop3_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if p else None
 
 
+def issue_roof(alu_word: float, madw_word: float, lanes: int, rate: float) -> dict:
+    """Roofline entry of an integer-bound sweep: algorithmic lop3-class ops
+    (ALU pipe) and 64-bit products (mad.wide) per word of `lanes` updates,
+    against the shared issue peak of the two."""
+    peak = _issue_peak()
+    per_upd = (alu_word + madw_word) / lanes
+    ach = rate * per_upd / 1e3
+    return {"bound": "alu", "ops_per_update": per_upd, "alu_ops_per_word": alu_word, "mad_wide_per_word": madw_word,
+            "achieved": ach, "peak": peak, "unit": "T int32 ops/s (lop3 + mad.wide, one shared issue slot)",
+            "frac": (ach / peak) if peak else None}
+
+
+def _issue_peak():
+    """lop3 and mad.wide share one issue slot: the rate of the two side by
+    side is the peak for any mix of them."""
+    p = probe_peak()
+    return p["lop3_madwide_per_clk_sm"] * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12 if p else None
+
+
 def run_serving(args):
     """The serving mix (3D/2D EA jobs of 1..64 samples, L from the listed
     sides, T in [0.5, 2], sweeps log-uniform in [10^3, 10^5] scaled by
@@ -703,22 +741,33 @@ def run_serving(args):
     return st
 
 
+_PROBE = []
+
+
 def probe_peak():
+    """Integer rates per clock per SM from libianus_probe.so (measured once
+    per process)."""
+    if _PROBE:
+        return _PROBE[0]
     import paper_0704_3573_gb300.build as b
 
+    out = None
     try:
         P = C.CDLL(b.PROBE_LIB)
         P.ianus_probe_int.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double)]
         out = {}
         for kind, name in ((0, "lop3_per_clk_sm"), (1, "imad_wide_per_clk_sm"), (2, "philox_mix_per_clk_sm"),
-                           (3, "philox_blocks_per_clk_sm")):
+                           (3, "philox_blocks_per_clk_sm"), (4, "lop3_madwide_per_clk_sm"),
+                           (7, "lop3_imad_per_clk_sm"), (8, "imad_hi_per_clk_sm")):
             v = C.c_double()
             if P.ianus_probe_int(kind, 4, C.byref(v)) != 0:
-                return None
+                out = None
+                break
             out[name] = v.value
-        return out
     except OSError:
-        return None
+        out = None
+    _PROBE.append(out)
+    return out
 
 
 def run_e2e(ianus, lat, stream, args, ws):
@@ -766,7 +815,7 @@ def main():
     ap.add_argument("--impl", default="ianus", choices=["ianus", "reference"])
     ap.add_argument("--plain-steps", type=int, default=3)
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=MEASURE_EVERY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--serve-jobs", type=int, default=400)
     ap.add_argument("--no-others", action="store_true")

@@ -451,6 +451,11 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * (ianus_set_block_words), faster than the automatic lockstep shape by
  * about a sixth.  The Python autotuner (tune.py) times the shapes on the
  * caller's lattice.
+ * The plain one-byte-per-spin layout (IANUS_LAYOUT_I8) has two sweep
+ * kernels: variant 1 runs one thread per update, each drawing its own
+ * random planes; every other value runs the tiled kernel, in which a block
+ * draws the planes of a site once for the site's 64-sample group and each
+ * update reads an 8-bit prefix of its random number from shared memory.
  * With several temperatures every variant but 1 uses the per-lane kernel
  * compiled for the geometry.  If run-time compilation is unavailable, the
  * precompiled kernel runs.  EINVAL for other values. */

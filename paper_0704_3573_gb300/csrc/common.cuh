@@ -250,7 +250,9 @@ __device__ __forceinline__ void count_unsat(const uint64_t* e, uint64_t& u0, uin
   }
 }
 
-// Device error word bits (read by ianus_synchronize).
-enum : uint32_t { ERR_BOUNDS = 1u, ERR_PT_PARITY = 2u, ERR_TIMEOUT = 4u };
+// Device error word bits (read by ianus_synchronize): a PT energy difference
+// off the multiple-of-4 grid (k_pt.cu), a bounded wait of the persistent
+// sweep that ran out (jit_sweep_lt.cuh).
+enum : uint32_t { ERR_PT_PARITY = 2u, ERR_TIMEOUT = 4u };
 
 }  // namespace ianus

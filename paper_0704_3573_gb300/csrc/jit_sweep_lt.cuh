@@ -84,11 +84,20 @@ struct Half {
 // Plane p of one half: threshold bits t = table p of (u2, u1, u0); res takes
 // t where undecided (0xCA: a ? b : c); und keeps the lanes with r == t (0x90:
 // a & ~(b ^ c)).
+// With every lane undecided at plane 0 (every class compares, none always
+// flips: the heat bath), plane 0 reduces to res = t, und = ~(r ^ t) (0xC3).
+constexpr bool kAllUndecided = (kNeed & kReach) == kReach && (kAlways & kReach) == 0u;
+
 template <int P>
 __device__ __forceinline__ void plane(Half& h, uint32_t r) {
   const uint32_t t = lop3<kLut[P]>(h.u2, h.u1, h.u0);
-  h.res = lop3<0xCA>(h.und, t, h.res);
-  h.und = lop3<0x90>(h.und, r, t);
+  if constexpr (P == 0 && kAllUndecided) {
+    h.res = t;
+    h.und = lop3<0xC3>(r, t, r);
+  } else {
+    h.res = lop3<0xCA>(h.und, t, h.res);
+    h.und = lop3<0x90>(h.und, r, t);
+  }
 }
 
 // Site part of Philox rounds 0 and 1: with P0 = M0 * site, round 0 gives
@@ -333,13 +342,14 @@ __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint
     }
     const SiteKey sk = site_key(site, c.thi_k);
     head_pairs<0>(lo, hi, sk, sh, *c.keys);
-    // decided lanes: flip where (r < T) != heat bath
+    // decided lanes: flip where (r < T) != heat bath, one lop3 per half:
+    // b ^ (res & ~und) (0xB4, Metropolis) or b ^ (~res & ~und) (0xE1)
 #pragma unroll
     for (int a = 0; a < R; ++a) {
-      const uint64_t und = (uint64_t)lo[a].und | ((uint64_t)hi[a].und << 32);
-      const uint64_t res = (uint64_t)lo[a].res | ((uint64_t)hi[a].res << 32);
-      const uint64_t flip = (ALGO == 0 ? res : ~res) & ~und;
-      if (valid && flip) c.sp0[(uint64_t)a * N + n.self] = b[a] ^ flip;
+      constexpr uint32_t kFlip = ALGO == 0 ? 0xB4u : 0xE1u;
+      const uint32_t nlo = lop3<kFlip>((uint32_t)b[a], lo[a].res, lo[a].und);
+      const uint32_t nhi = lop3<kFlip>((uint32_t)(b[a] >> 32), hi[a].res, hi[a].und);
+      if (valid) c.sp0[(uint64_t)a * N + n.self] = (uint64_t)nlo | ((uint64_t)nhi << 32);
     }
     // queue the words with undecided lanes (slot 0's, then slot 1's)
 #pragma unroll

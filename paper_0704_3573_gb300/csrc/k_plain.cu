@@ -95,6 +95,149 @@ __global__ void __launch_bounds__(256) k_sweep_i8(const I8Params p) {
 }
 
 
+// ---- plain layout, tiled: the random planes of a site shared by its group ----
+//
+// The random number of sample s at (site, sweep) is bit (s mod 64) of the
+// 32 bit-planes drawn for the site and its group of 64 samples, so one
+// Philox block serves 64 updates.  A block of kTileThreads threads takes a
+// tile of up to kTileSites colour-c sites (consecutive colour words
+// w = row * L/2 + k of one configuration slot) and one group:
+//   phase A: one thread per site draws plane pairs 0..3 (planes 0..7) and
+//     transposes them, 8 lanes at a time (an 8 x 8 bit transpose), into one
+//     8-bit prefix of the random number per (site, lane) in shared memory;
+//     the block also stages the class thresholds of its 64 samples;
+//   phase B: thread t keeps site t and runs through the group's samples, so
+//     the 32 threads of a warp read 32 neighbouring sites of one sample;
+//     each update compares the 8-bit prefix with the top 8 bits of its
+//     threshold and is decided there unless the two are equal (probability
+//     1/256), in which case it continues with pairs 4.. on its own.
+constexpr int kTileThreads = 256;
+constexpr int kTileSites = 256;
+constexpr int kTileRow = 68;  // bytes per site of prefixes: 64 lanes + 4 of padding (no bank conflicts)
+
+// 8 x 8 bit transpose: element (i, j) = bit 8 i + j goes to bit 8 j + i.
+__device__ __forceinline__ uint64_t transpose8(uint64_t x) {
+  uint64_t t = (x ^ (x >> 7)) & 0x00AA00AA00AA00AAull;
+  x = x ^ t ^ (t << 7);
+  t = (x ^ (x >> 14)) & 0x0000CCCC0000CCCCull;
+  x = x ^ t ^ (t << 14);
+  t = (x ^ (x >> 28)) & 0x00000000F0F0F0F0ull;
+  return x ^ t ^ (t << 28);
+}
+
+// r < T decided from plane pairs m0.. of the lane's random number (the
+// planes before m0 equal those of T).
+__device__ __noinline__ bool lazy_less_from(uint32_t T32, uint32_t m0, const I8Params& p, const Tick& tk, int sigma,
+                                            uint32_t g, uint32_t lane, uint32_t site) {
+  const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+  for (uint32_t m = m0; m < 16u; ++m) {
+    const uint4 x = philox10(site, tk.lo, c2base | (m << 24), tk.hi, p.keys);
+    const uint32_t w0 = lane < 32u ? (x.x >> lane) : (x.y >> (lane - 32u));
+    const uint32_t w1 = lane < 32u ? (x.z >> lane) : (x.w >> (lane - 32u));
+    const uint32_t r0 = w0 & 1u, t0 = (T32 >> (31u - 2u * m)) & 1u;
+    if (r0 != t0) return r0 < t0;
+    const uint32_t r1 = w1 & 1u, t1 = (T32 >> (30u - 2u * m)) & 1u;
+    if (r1 != t1) return r1 < t1;
+  }
+  return false;  // r == T
+}
+
+// grid: (tiles of kTileSites colour words, groups, slots)
+template <int D>
+__global__ void __launch_bounds__(kTileThreads) k_sweep_i8_tiled(const I8Params p) {
+  __shared__ __align__(16) uint8_t s_r8[kTileSites * kTileRow];
+  __shared__ uint64_t s_thr[64][kMaxClasses];
+  const uint32_t g = blockIdx.y;
+  const int sigma = (int)blockIdx.z;
+  const uint32_t L = (uint32_t)p.L, h = L / 2u;
+  const uint32_t w0 = blockIdx.x * (uint32_t)kTileSites;
+  const uint32_t nsites = min((uint32_t)kTileSites, p.half - w0);
+  const uint32_t t = threadIdx.x;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  // the site of this thread: colour word w -> row, k -> natural index
+  const bool has_site = t < nsites;
+  uint32_t i = 0, xp = 0, xm = 0, yp = 0, ym = 0, zp = 0, zm = 0;
+  if (has_site) {
+    const uint32_t w = w0 + t;
+    const uint32_t row = w / h, k = w - row * h;
+    const uint32_t y = row % L, z = row / L;
+    const uint32_t x = 2u * k + ((uint32_t)(p.colour ^ (int)(y + z)) & 1u);
+    i = x + L * row;
+    xp = (x + 1u == L ? 0u : x + 1u) + L * row;
+    xm = (x == 0u ? L - 1u : x - 1u) + L * row;
+    yp = x + L * ((y + 1u == L ? 0u : y + 1u) + L * z);
+    ym = x + L * ((y == 0u ? L - 1u : y - 1u) + L * z);
+    if (D == 3) {
+      zp = x + L * (y + L * (z + 1u == L ? 0u : z + 1u));
+      zm = x + L * (y + L * (z == 0u ? L - 1u : z - 1u));
+    }
+  }
+  // phase A: planes 0..7 of the site for the group's 64 lanes, as 8-bit prefixes
+  if (has_site) {
+    const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+    uint32_t pw[8][2];  // plane p: lanes 0..31, 32..63
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint4 x = philox10(i, tk.lo, c2base | ((uint32_t)m << 24), tk.hi, p.keys);
+      pw[2 * m][0] = x.x;
+      pw[2 * m][1] = x.y;
+      pw[2 * m + 1][0] = x.z;
+      pw[2 * m + 1][1] = x.w;
+    }
+    uint8_t* dst = s_r8 + t * kTileRow;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      // byte 7 - p of M = byte c of plane p's 64-bit word (lanes 8c .. 8c+7)
+      const int hw = c >> 2, sh = 8 * (c & 3);
+      uint64_t M = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) M |= (uint64_t)((pw[q][hw] >> sh) & 0xFFu) << (8 * (7 - q));
+      const uint64_t r = transpose8(M);  // byte j: lane 8c + j, bit 7 - p = plane p
+      *reinterpret_cast<uint32_t*>(dst + 8 * c) = (uint32_t)r;
+      *reinterpret_cast<uint32_t*>(dst + 8 * c + 4) = (uint32_t)(r >> 32);
+    }
+  }
+  // thresholds of the group's samples (their temperatures may differ)
+  for (uint32_t e = t; e < 64u * kMaxClasses; e += kTileThreads) {
+    const uint32_t lane = e / kMaxClasses, u = e - lane * kMaxClasses;
+    const uint32_t s = 64u * g + lane;
+    uint64_t T = 0;
+    if (s < (uint32_t)p.S) {
+      const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+      const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
+      T = p.thr[(size_t)kt * kMaxClasses + u];
+    }
+    s_thr[lane][u] = T;
+  }
+  __syncthreads();
+  if (!has_site) return;
+  // phase B: site t, every sample of the group
+  const uint32_t lanes = min(64u, (uint32_t)p.S - 64u * g);
+  const uint32_t N = p.N;
+  const int8_t* r8row = reinterpret_cast<const int8_t*>(s_r8 + t * kTileRow);
+  for (uint32_t lane = 0; lane < lanes; ++lane) {
+    const uint32_t s = 64u * g + lane;
+    int8_t* sp = p.spins + ((size_t)sigma * p.S + s) * N;
+    const int8_t* Jp = p.J + (size_t)s * D * N;
+    const int si = sp[i];
+    int u = (Jp[i] * si * sp[xp] < 0) + (Jp[xm] * si * sp[xm] < 0) + (Jp[N + i] * si * sp[yp] < 0) +
+            (Jp[N + ym] * si * sp[ym] < 0);
+    if (D == 3) u += (Jp[2u * N + i] * si * sp[zp] < 0) + (Jp[2u * N + zm] * si * sp[zm] < 0);
+    const uint64_t T = s_thr[lane][u];
+    bool less;
+    if (T >= kTwo32) {
+      less = true;
+    } else {
+      const uint32_t r8 = (uint8_t)r8row[lane], T8 = (uint32_t)(T >> 24);
+      if (r8 != T8)
+        less = r8 < T8;
+      else
+        less = lazy_less_from((uint32_t)T, 4u, p, tk, sigma, g, lane, i);
+    }
+    if (less != (p.inv != 0)) sp[i] = (int8_t)(-si);
+  }
+}
+
 // Field models (Eq. 2 with fields h_i = +-|h| and occupations x_i): an empty
 // site is skipped; for an occupied one v = s_i sum_j J_ij x_j s_j and
 // f = [s_i h_i > 0] select the threshold of class (v + 2D) * 2 + f.
@@ -985,6 +1128,14 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
       k_sweep_field_i8<3><<<grid, 256, 0, lat.stream>>>(fp);
     else
       k_sweep_field_i8<2><<<grid, 256, 0, lat.stream>>>(fp);
+    return cudaGetLastError();
+  }
+  if (lat.variant != 1) {  // the tiled kernel (planes shared by the group); variant 1: one thread per update
+    const dim3 tgrid((p.half + kTileSites - 1) / kTileSites, (unsigned)lat.G, (unsigned)lat.slots);
+    if (lat.D == 3)
+      k_sweep_i8_tiled<3><<<tgrid, kTileThreads, 0, lat.stream>>>(p);
+    else
+      k_sweep_i8_tiled<2><<<tgrid, kTileThreads, 0, lat.stream>>>(p);
     return cudaGetLastError();
   }
   if (lat.D == 3)

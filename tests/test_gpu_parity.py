@@ -377,6 +377,32 @@ def test_L32_pt_32_temperatures_full_size_sampled(ianus):
     assert np.array_equal(E[ids], Eo)
 
 
+def test_L32_pt_32_temperatures_sweep_pt_as_benched(ianus):
+    """The parallel-tempering workload through ianus_sweep_pt exactly as the
+    bench times it (captured sweep graphs, swaps on the device every 10
+    sweeps, energies for the swap reused from the measurement pass): L=32,
+    32 temperatures, 64 samples x 2 replicas, 30 sweeps; samples 0 and 37
+    against the oracle's sweep-then-swap sequence."""
+    seed = SEED + 2
+    K = 32
+    beta = [1.0 / (0.7 + 0.9 * k / 31) for k in range(K)]
+    lat = ianus.Lattice(dim=3, L=32, n_samples=64, n_replicas=2, n_temps=K, seed=seed, layout="bits64")
+    lat.sweep_pt(METROPOLIS, beta, 30, swap_every=10)
+    ids = [0, 37]
+    orc = Oracle(dim=3, L=32, sample_ids=ids, n_replicas=2, n_temps=K, seed=seed)
+    for _ in range(3):
+        orc.sweep(METROPOLIS, beta, 10, nthreads=2)
+        orc.pt_swap(beta)
+    sa, acc, steps = lat.pt_state()
+    sao, acco, stepso = orc.pt_state()
+    assert steps == stepso == 3
+    assert np.array_equal(sa[ids], sao) and np.array_equal(acc[ids], acco)
+    assert np.array_equal(lat.spins()[ids], orc.spins())
+    E, _, Q = lat.measure()
+    Eo, _, Qo = orc.measure()
+    assert np.array_equal(E[ids], Eo) and np.array_equal(Q[ids], Qo)
+
+
 def test_potts_L32_128x2_full_size_sampled(ianus):
     """Potts q=4, L=32, 128 samples x 2 replicas, heat bath T=0.8."""
     seed = SEED + 3
