@@ -326,14 +326,14 @@ def test_L16_single_sample_metropolis_full_run(ianus):
 
 # The kernel variant and words per block bench.py times on this workload
 # (checked against bench.DEFAULT_VARIANT by a CPU test).
-BENCH_SHAPE = (21, 256)
+BENCH_SHAPE = (24, 0)
 
 
 @pytest.mark.parametrize("shape", [None, BENCH_SHAPE])
 def test_L64_256x2_heatbath_full_size_sampled(ianus, shape):
     """L=64, 256 samples x 2 replicas, heat bath T=1.0 on the GPU, with the
     automatic kernel choice and with the kernel and launch shape bench.py
-    times (variant 21, 256 words per block); samples 0, 63, 64, 255 checked
+    times (the lane-queue kernel, variant 24, in its one-wave launch); samples 0, 63, 64, 255 checked
     against the oracle."""
     seed = SEED + 1
     lat = ianus.Lattice(dim=3, L=64, n_samples=256, n_replicas=2, seed=seed, layout="bits64")
