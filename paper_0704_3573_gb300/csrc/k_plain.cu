@@ -238,6 +238,160 @@ __global__ void __launch_bounds__(kTileThreads) k_sweep_i8_tiled(const I8Params 
   }
 }
 
+// The same with each thread on one aligned 4-byte word of a row (sites
+// x0 .. x0+3, two of them of the active colour), for L a multiple of 4.  The
+// local fields of the word's four sites come out together: per direction
+// the sign bits of s_i ^ s_j ^ J_ij (bytes of +-1) mark the unsatisfied
+// bonds, x-neighbours by funnel shifts with the adjacent words, and the
+// per-byte counts are summed in the word.  Thread t takes word q0 + t of
+// every sample of the group, loading the next sample's words while it
+// updates the current one (the sweep waits on memory, not on arithmetic).
+// Its two active sites are rows j kWordThreads + t of the prefix table.
+constexpr int kWordThreads = 128;
+
+// the words one update of a 4-byte word reads
+template <int D>
+struct WordLoads {
+  uint32_t self, prev, next, yp, ym, zp, zm;
+  uint32_t j0s, j0p, j1s, j1m, j2s, j2m;
+};
+
+struct WordOffsets {
+  uint32_t self, prev, next, yp, ym, zp, zm;
+};
+
+template <int D>
+__device__ __forceinline__ void load_word(WordLoads<D>& w, const int8_t* sp, const int8_t* Jp, uint32_t N,
+                                          const WordOffsets& o) {
+  w.self = *reinterpret_cast<const uint32_t*>(sp + o.self);
+  w.prev = *reinterpret_cast<const uint32_t*>(sp + o.prev);
+  w.next = *reinterpret_cast<const uint32_t*>(sp + o.next);
+  w.yp = *reinterpret_cast<const uint32_t*>(sp + o.yp);
+  w.ym = *reinterpret_cast<const uint32_t*>(sp + o.ym);
+  w.j0s = __ldg(reinterpret_cast<const uint32_t*>(Jp + o.self));
+  w.j0p = __ldg(reinterpret_cast<const uint32_t*>(Jp + o.prev));
+  w.j1s = __ldg(reinterpret_cast<const uint32_t*>(Jp + N + o.self));
+  w.j1m = __ldg(reinterpret_cast<const uint32_t*>(Jp + N + o.ym));
+  if (D == 3) {
+    w.zp = *reinterpret_cast<const uint32_t*>(sp + o.zp);
+    w.zm = *reinterpret_cast<const uint32_t*>(sp + o.zm);
+    w.j2s = __ldg(reinterpret_cast<const uint32_t*>(Jp + 2u * N + o.self));
+    w.j2m = __ldg(reinterpret_cast<const uint32_t*>(Jp + 2u * N + o.zm));
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(kWordThreads, 6) k_sweep_i8_words(const I8Params p) {
+  __shared__ __align__(16) uint8_t s_r8[2 * kWordThreads * kTileRow];
+  __shared__ uint32_t s_thr[64][kMaxClasses];  // low 32 bits of T (the lazy path)
+  __shared__ uint16_t s_t8[64][kMaxClasses];   // top 8 bits of T, 256 for T = 2^32 (always below)
+  const uint32_t g = blockIdx.y;
+  const int sigma = (int)blockIdx.z;
+  const uint32_t L = (uint32_t)p.L, N = p.N, nq = N / 4u, qrow = L / 4u;
+  const uint32_t q0 = blockIdx.x * (uint32_t)kWordThreads;
+  const uint32_t t = threadIdx.x;
+  const bool has = q0 + t < nq;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  uint32_t row = 0, x0 = 0, y = 0, z = 0, b0 = 0;
+  if (has) {
+    const uint32_t q = q0 + t;
+    row = q / qrow;
+    x0 = 4u * (q - row * qrow);
+    y = row % L;
+    z = row / L;
+    b0 = (uint32_t)(p.colour ^ (int)(y + z)) & 1u;  // byte of the first active site
+  }
+  // phase A: planes 0..7 of the two active sites for the group's 64 lanes
+  if (has) {
+    const uint32_t c2base = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+#pragma unroll 1
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t i = x0 + b0 + 2u * (uint32_t)j + L * row;
+      uint32_t pw[8][2];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const uint4 x = philox10(i, tk.lo, c2base | ((uint32_t)m << 24), tk.hi, p.keys);
+        pw[2 * m][0] = x.x;
+        pw[2 * m][1] = x.y;
+        pw[2 * m + 1][0] = x.z;
+        pw[2 * m + 1][1] = x.w;
+      }
+      uint8_t* dst = s_r8 + ((uint32_t)j * kWordThreads + t) * kTileRow;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int hw = c >> 2, sh = 8 * (c & 3);
+        uint64_t M = 0;
+#pragma unroll
+        for (int qq = 0; qq < 8; ++qq) M |= (uint64_t)((pw[qq][hw] >> sh) & 0xFFu) << (8 * (7 - qq));
+        const uint64_t r = transpose8(M);
+        *reinterpret_cast<uint32_t*>(dst + 8 * c) = (uint32_t)r;
+        *reinterpret_cast<uint32_t*>(dst + 8 * c + 4) = (uint32_t)(r >> 32);
+      }
+    }
+  }
+  for (uint32_t e = t; e < 64u * kMaxClasses; e += kWordThreads) {
+    const uint32_t lane = e / kMaxClasses, u = e - lane * kMaxClasses;
+    const uint32_t s = 64u * g + lane;
+    uint64_t T = 0;
+    if (s < (uint32_t)p.S) {
+      const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+      const int kt = p.temp_of[((size_t)s * p.R + a) * p.K + tslot];
+      T = p.thr[(size_t)kt * kMaxClasses + u];
+    }
+    s_thr[lane][u] = (uint32_t)T;
+    s_t8[lane][u] = T >= kTwo32 ? (uint16_t)256u : (uint16_t)(T >> 24);
+  }
+  __syncthreads();
+  if (!has) return;
+  // word offsets within a configuration (bytes), all multiples of 4
+  WordOffsets o;
+  o.self = L * row + x0;
+  o.prev = L * row + (x0 == 0u ? L - 4u : x0 - 4u);
+  o.next = L * row + (x0 + 4u == L ? 0u : x0 + 4u);
+  o.yp = L * ((y + 1u == L ? 0u : y + 1u) + L * z) + x0;
+  o.ym = L * ((y == 0u ? L - 1u : y - 1u) + L * z) + x0;
+  o.zp = o.zm = 0u;
+  if (D == 3) {
+    o.zp = L * (y + L * (z + 1u == L ? 0u : z + 1u)) + x0;
+    o.zm = L * (y + L * (z == 0u ? L - 1u : z - 1u)) + x0;
+  }
+  const uint32_t lanes = min(64u, (uint32_t)p.S - 64u * g);
+  const uint32_t sh1 = 8u * b0, sh2 = 8u * (b0 + 2u);
+  int8_t* spl = p.spins + ((size_t)sigma * p.S + 64u * g) * N;
+  const int8_t* Jl = p.J + (size_t)64u * g * D * N;
+  WordLoads<D> cur, nxt;
+  load_word<D>(cur, spl, Jl, N, o);
+#pragma unroll 1
+  for (uint32_t lane = 0; lane < lanes; ++lane) {
+    if (lane + 1u < lanes) load_word<D>(nxt, spl + (size_t)(lane + 1u) * N, Jl + (size_t)(lane + 1u) * D * N, N, o);
+    // sign bit 7 of each byte: bond unsatisfied
+    const uint32_t self = cur.self;
+    uint32_t cnt = ((self ^ __funnelshift_r(self, cur.next, 8) ^ cur.j0s) >> 7) & 0x01010101u;  // x + 1
+    cnt += ((self ^ __funnelshift_l(cur.prev, self, 8) ^ __funnelshift_l(cur.j0p, cur.j0s, 8)) >> 7) &
+           0x01010101u;  // x - 1
+    cnt += ((self ^ cur.yp ^ cur.j1s) >> 7) & 0x01010101u;
+    cnt += ((self ^ cur.ym ^ cur.j1m) >> 7) & 0x01010101u;
+    if (D == 3) {
+      cnt += ((self ^ cur.zp ^ cur.j2s) >> 7) & 0x01010101u;
+      cnt += ((self ^ cur.zm ^ cur.j2m) >> 7) & 0x01010101u;
+    }
+    uint32_t flip = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const uint32_t shj = j == 0 ? sh1 : sh2;
+      const uint32_t u = (cnt >> shj) & 0xFFu;
+      const uint32_t t8 = s_t8[lane][u];
+      const uint32_t r8 = s_r8[((uint32_t)j * kWordThreads + t) * kTileRow + lane];
+      bool less = r8 < t8;  // decided by the first 8 planes unless equal (then T < 2^32)
+      if (r8 == t8)
+        less = lazy_less_from(s_thr[lane][u], 4u, p, tk, sigma, g, lane, x0 + b0 + 2u * (uint32_t)j + L * row);
+      if (less != (p.inv != 0)) flip |= 0xFEu << shj;  // +1 (0x01) <-> -1 (0xFF)
+    }
+    if (flip) *reinterpret_cast<uint32_t*>(spl + (size_t)lane * N + o.self) = self ^ flip;
+    cur = nxt;
+  }
+}
+
 // Field models (Eq. 2 with fields h_i = +-|h| and occupations x_i): an empty
 // site is skipped; for an occupied one v = s_i sum_j J_ij x_j s_j and
 // f = [s_i h_i > 0] select the threshold of class (v + 2D) * 2 + f.
@@ -1128,6 +1282,14 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
       k_sweep_field_i8<3><<<grid, 256, 0, lat.stream>>>(fp);
     else
       k_sweep_field_i8<2><<<grid, 256, 0, lat.stream>>>(fp);
+    return cudaGetLastError();
+  }
+  if (lat.variant != 1 && lat.L % 4 == 0) {  // the word kernel: 4-byte words, planes shared by the group
+    const dim3 wgrid((lat.N / 4u + kWordThreads - 1) / kWordThreads, (unsigned)lat.G, (unsigned)lat.slots);
+    if (lat.D == 3)
+      k_sweep_i8_words<3><<<wgrid, kWordThreads, 0, lat.stream>>>(p);
+    else
+      k_sweep_i8_words<2><<<wgrid, kWordThreads, 0, lat.stream>>>(p);
     return cudaGetLastError();
   }
   if (lat.variant != 1) {  // the tiled kernel (planes shared by the group); variant 1: one thread per update
