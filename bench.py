@@ -12,9 +12,13 @@ stream).
 Printed JSON line (rank 0): value = spin updates/ns of the device-resident
 run; e2e = the same through the C ABI with the state uploaded from pinned
 host memory and the measurement series read back every step; plain = the
-one-byte-per-spin kernel on the same workload; roofline = the dominant
-sweep kernel against the integer-issue peak; cpu_baseline = the CPU oracle on
-a bounded sample of the same workload.
+one-byte-per-spin kernel on the same workload, with its roofline; roofline =
+the dominant sweep kernel against the integer-issue peak (lop3-class logic
+and 64-bit products share one issue slot, measured by the integer probe);
+cpu_baseline = the CPU oracle on a bounded sample of the same workload;
+serving = the 2000-job serving mix at 0.8 x its calibrated capacity (p50 /
+p99 job latency, aggregate updates/ns); other_workloads = the other
+configurations and the paper's other models, each with its roofline.
 
 ``--impl reference`` times the CPU oracle instead (the only reference this
 method has: the paper ships no code).
@@ -53,19 +57,26 @@ SM_MAX_MHZ = 2070.0
 # kernel from one ncu capture of it on this workload, per (kernel variant,
 # words per block), valid while the kernel source is unchanged (hash of the
 # sources it is compiled from).
-TRAFFIC_BYTES_PER_LAUNCH = {}
-TRAFFIC_SOURCE_HASH = ""
+TRAFFIC_BYTES_PER_LAUNCH = {(24, 0): 41969920 + 0}
+TRAFFIC_SOURCE_HASH = "2c04fa2358a310c8"
+# Memory traffic of one colour launch of the q=4 Potts sweep (k_sweep_potts)
+# on its L=32, 128 x 2 workload, from one ncu capture, valid while its
+# sources are unchanged: global loads through L1 (spin words, couplings and
+# the 16-byte table row of every update), L2 and DRAM bytes, L1 hit rate.
+POTTS_TRAFFIC = {"l1_global_load_bytes": 179127744, "l2_bytes": 73770400, "dram_bytes": 21049344,
+                 "l1_hit_rate_pct": 78.5}
+POTTS_SOURCE_HASH = "ab9e8badae2a5729"
 # The kernel variant and launch shape the bench runs by default: the
 # lane-queue kernel in its one-wave launch (the automatic choice for one
 # temperature), fixed so that the profile above describes the timed kernel.
 DEFAULT_VARIANT = (24, 0)
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(names=("common.cuh", "jit_sweep_lt.cuh", "jit.cu")) -> str:
     import hashlib
 
     h = hashlib.sha256()
-    for name in ("common.cuh", "jit_sweep_lt.cuh", "jit.cu"):
+    for name in names:
         with open(os.path.join(ROOT, "paper_0704_3573_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -360,8 +371,26 @@ def run_gpu(args, ws, rank, local):
         torch.cuda.synchronize()
         ps = p0.elapsed_time(p1) / 1e3
         pv = S * R * L ** 3 * nps / (ps * 1e9)
+        # roofline of the plain form: the smaller of two bounds.  HBM: per
+        # update the site's byte read and written and its share of the other
+        # colour's bytes (3 B) and the 6 coupling bytes each configuration
+        # streams (9 B, the couplings larger than L2).  Issue: per update 6
+        # bond tests (2 ops each), the Philox blocks of the site shared by the
+        # 64 samples of its group (3.92 pairs x 37 ops / 64), about 8/3 plane
+        # compares and the flip (lop3 + mad.wide ops, one shared issue slot)
+        hbm = MEASURED.get("hbm_gbs")
+        b_upd = 9.0
+        ops_upd = 12 + expected_plane_pairs() * 37 / 64 + 8 / 3 + 1
+        pk = _issue_peak()
+        bounds = {"hbm": hbm / b_upd if hbm else None, "alu": pk * 1e3 / ops_upd if pk else None}
+        binding = min((v, k) for k, v in bounds.items() if v)[1] if any(bounds.values()) else None
         plain = {"value": pv, "unit": UNIT, "layout": "i8 (one byte per spin)", "sweeps": nps,
-                 "speedup_bitsliced_over_plain": value / ws / pv}
+                 "kernel": "k_sweep_i8_words (4-byte words, planes shared by the 64-sample group)",
+                 "speedup_bitsliced_over_plain": value / ws / pv,
+                 "roofline": {"bound": binding, "bytes_per_update": b_upd, "ops_per_update": ops_upd,
+                              "bound_updates_per_ns": bounds,
+                              "frac": pv / bounds[binding] if binding else None,
+                              "peaks": {"hbm_gbs": hbm, "issue_tops": pk}}}
         del pl
 
     cpu = None
@@ -503,10 +532,18 @@ def run_other_configs(args):
     # per 4-sample word: Philox 21 ALU; per sample 6 neighbours x (state,
     # coupling, shift, add: 4) + 3 compares with "always" flags (6) + pack (3)
     alu_word = 21 + 4 * (24 + 6 + 3)
+    upd_launch = 128 * 2 * 32 ** 3 // 2
+    potts_traffic = None
+    if kernel_source_hash(("common.cuh", "k_potts.cu")) == POTTS_SOURCE_HASH:
+        potts_traffic = dict(POTTS_TRAFFIC)
+        potts_traffic["table_lookup_bytes_algorithmic"] = 16 * upd_launch  # one 16-byte row per update
+        potts_traffic["updates_per_launch"] = upd_launch
+        potts_traffic["source"] = "ncu, one colour launch of k_sweep_potts on this workload"
     out["potts_L32_128x2"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "4 samples per uint32 word, heat bath, E/Q every 10 sweeps",
         "roofline": issue_roof(alu_word, 20, 4, rate),
+        "table_traffic_per_launch": potts_traffic,
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -709,35 +746,38 @@ def _issue_peak():
 
 
 def run_serving(args):
-    """The serving mix (3D/2D EA jobs of 1..64 samples, L from the listed
-    sides, T in [0.5, 2], sweeps log-uniform in [10^3, 10^5] scaled by
-    --serve-scale), Poisson arrivals at 0.8 x the capacity measured on a
-    saturated run of the first fifth of the jobs; p50/p99 latency and
-    aggregate spin updates/ns."""
+    """The serving mix as configured (2000 jobs: 3D/2D EA jobs of 1..64
+    samples, L from the listed sides, T in [0.5, 2], sweeps log-uniform in
+    [10^3, 10^5] times --serve-scale, Metropolis or heat bath), Poisson
+    arrivals at 0.8 x the capacity the lane-fusing server (FusedServer: jobs
+    of equal (D, L) share the 64-bit lanes of pool lattices, large jobs on
+    their own lattices) reaches on a saturated run of the whole mix; p50/p99
+    latency and aggregate spin updates/ns.  Beside it, the server that gives
+    every job its own lattice (Server), saturated on the first 100 jobs."""
     from paper_0704_3573_gb300 import serve
 
     jobs = serve.job_mix(args.serve_jobs, sweep_scale=args.serve_scale)
-    server = serve.Server(mem_budget=16 << 30, max_active=64, n_streams=16, chunk_sweeps=50)
-    calib = jobs[: max(10, len(jobs) // 5)]
-    rate = serve.calibrated_rate(server, calib, load=0.8)
-    arrivals = serve.poisson_arrivals(jobs, rate)
-    _, st = server.run(arrivals)
-    st["arrival_rate_per_s"] = rate
-    st["sweep_scale"] = args.serve_scale
-    st["mix"] = "3D L in {8..80} / 2D L in {64..1024}, 1-64 samples, T~U[0.5,2], sweeps log-U[1e3,1e5] x scale"
-    # lane fusion: jobs of equal (D, L) share the 64-bit lanes of pool lattices;
-    # the same arrivals, then both servers saturated on the calibration jobs
     fused = serve.FusedServer(mem_budget=16 << 30, groups_per_pool=4, n_streams=16, chunk_sweeps=50)
-    _, fst = fused.run(arrivals)
-    _, sat_plain = server.run(calib, realtime=False)
-    _, sat_fused = fused.run(calib, realtime=False)
-    st["fused"] = {
-        "p50_latency_s": fst["p50_latency_s"], "p99_latency_s": fst["p99_latency_s"],
-        "makespan_s": fst["makespan_s"], "updates_per_ns": fst["updates_per_ns"], "pools": fst["pools"],
-        "saturated_updates_per_ns": sat_fused["updates_per_ns"],
-        "saturated_updates_per_ns_unfused": sat_plain["updates_per_ns"],
-        "what": "same Poisson arrivals; saturated = the calibration jobs all at t=0",
-    }
+    calib = jobs  # capacity: the whole mix at t = 0
+    _, sat = fused.run(calib, realtime=False)
+    rate = 0.8 * len(calib) / sat["makespan_s"] if sat["makespan_s"] > 0 else math.inf
+    arrivals = serve.poisson_arrivals(jobs, rate)
+    _, st = fused.run(arrivals)
+    st["server"] = "FusedServer (lane fusion of jobs of equal (D, L); jobs over 2^16 sites on their own lattices)"
+    st["arrival_rate_per_s"] = rate
+    st["offered_load"] = 0.8
+    st["sweep_scale"] = args.serve_scale
+    st["mix"] = ("3D L in {8..80} / 2D L in {64..1024}, 1-64 samples, T~U[0.5,2], sweeps log-U[1e3,1e5] x scale, "
+                 "Metropolis / heat bath")
+    st["saturated"] = {"jobs": len(calib), "makespan_s": sat["makespan_s"], "updates_per_ns": sat["updates_per_ns"],
+                       "p50_latency_s": sat["p50_latency_s"], "p99_latency_s": sat["p99_latency_s"],
+                       "what": "the whole mix at t = 0: the capacity the arrival rate is calibrated on"}
+    plain = serve.Server(mem_budget=16 << 30, max_active=64, n_streams=16, chunk_sweeps=50)
+    sub = jobs[: min(100, len(jobs))]
+    _, sat_plain = plain.run(sub, realtime=False)
+    st["unfused_saturated"] = {"jobs": len(sub), "makespan_s": sat_plain["makespan_s"],
+                               "updates_per_ns": sat_plain["updates_per_ns"],
+                               "what": "Server: every job on its own lattice, all jobs at t=0"}
     return st
 
 
@@ -817,12 +857,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-sweeps", type=int, default=MEASURE_EVERY)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--serve-jobs", type=int, default=400)
+    ap.add_argument("--serve-jobs", type=int, default=2000)
     ap.add_argument("--no-others", action="store_true")
     ap.add_argument("--tune", action="store_true", help="pick the kernel variant with the autotuner")
     ap.add_argument("--variant", type=int, default=None, help="kernel variant (default: the profiled one)")
     ap.add_argument("--block-words", type=int, default=0, help="launch shape with --variant (0 = heuristic)")
-    ap.add_argument("--serve-scale", type=float, default=0.05)
+    ap.add_argument("--serve-scale", type=float, default=1.0)
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws, rank, local = dist_setup()
