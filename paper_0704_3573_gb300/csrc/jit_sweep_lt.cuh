@@ -155,6 +155,7 @@ struct Shared {
   uint4 u[R * 16];         // uniform parts of rounds 0..1 per (slot, pair)
   uint8_t lut[32];         // truth tables of the planes (pairs 8..15 read them at run time)
   WordQ wq[kWarps];        // per-warp queues of words that need pair kHeadPairs
+  uint32_t left[kWarps];   // words each warp leaves queued at the end of its words
 };
 
 struct Ctx {
@@ -208,23 +209,19 @@ __device__ __forceinline__ void tail_pairs(Half& lo, Half& hi, const SiteKey& sk
   }
 }
 
-// One round over the top `take` (<= 32) queued words: pair kHeadPairs and
-// the following ones until every word of the warp is decided; the queued
-// lanes are then flipped in place.
-__device__ __forceinline__ void word_round(Shared& sh, uint32_t& nw, uint32_t take, const Ctx& c) {
-  const uint32_t wp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-  WordQ& wq = sh.wq[wp];
-  const bool has = lane < take;
+// One round over queued words, one per lane: item `idx` of warp `src`'s
+// queue where `has`.  Pair kHeadPairs and the following ones run until every
+// word of the warp is decided; the queued lanes are then flipped in place.
+__device__ __forceinline__ void word_round_at(const Shared& sh, uint32_t src, uint32_t idx, bool has,
+                                              const Ctx& c) {
   uint4 qa = make_uint4(0u, 0u, 0u, 0u), qb = qa;
   uint2 qc = make_uint2(0u, 0u);
   if (has) {
-    const uint32_t i = nw - take + lane;
-    qa = wq.a[i];
-    qb = wq.b[i];
-    qc = wq.c[i];
+    const WordQ& wq = sh.wq[src];
+    qa = wq.a[idx];
+    qb = wq.b[idx];
+    qc = wq.c[idx];
   }
-  __syncwarp();
-  nw -= take;
   Half lo{qb.x, qb.z, qc.x, qa.z, 0u}, hi{qb.y, qb.w, qc.y, qa.w, 0u};
   const SiteKey sk = site_key(qa.x, c.thi_k);
   const uint4* U = sh.u + qa.y * 16u;
@@ -246,6 +243,41 @@ __device__ __forceinline__ void word_round(Shared& sh, uint32_t& nw, uint32_t ta
       atomicXor((unsigned long long*)w, flip);
     }
   }
+}
+
+// The top `take` (<= 32) words of this warp's queue.
+__device__ __forceinline__ void word_round(const Shared& sh, uint32_t& nw, uint32_t take, const Ctx& c) {
+  const uint32_t wp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  word_round_at(sh, wp, nw - take + lane, lane < take, c);
+  __syncwarp();  // every lane has read its item before the queue is pushed to again
+  nw -= take;
+}
+
+// The words the warps left queued (fewer than 32 each), as full rounds
+// spread over the warps: warp w takes rounds w, w + kWarps, ... of the
+// concatenated queues.  Called by every thread of the block.
+__device__ __forceinline__ void drain_block(Shared& sh, uint32_t nw, const Ctx& c) {
+  const uint32_t wp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  if (lane == 0) sh.left[wp] = nw;
+  __syncthreads();
+  uint32_t off[kWarps], total = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    off[w] = total;
+    total += sh.left[w];
+  }
+  for (uint32_t r = wp; 32u * r < total; r += kWarps) {
+    const uint32_t k = 32u * r + lane;
+    uint32_t src = 0, base = 0;
+#pragma unroll
+    for (int w = 1; w < kWarps; ++w)
+      if (off[w] <= k) {
+        src = (uint32_t)w;
+        base = off[w];
+      }
+    word_round_at(sh, src, k - base, k < total, c);
+  }
+  __syncthreads();  // the queues are free again
 }
 
 // Pairs 0..kHeadPairs-1 for the words of one site (R words, two Philox
@@ -367,7 +399,7 @@ __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint
     __syncwarp();
     while (nw >= 32u) word_round(sh, nw, 32u, c);
   }
-  while (nw > 0u) word_round(sh, nw, nw < 32u ? nw : 32u, c);
+  drain_block(sh, nw, c);
 }
 
 // Uniform parts of Philox rounds 0 and 1 for every (slot, pair) of group g
