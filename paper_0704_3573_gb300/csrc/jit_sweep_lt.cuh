@@ -151,10 +151,18 @@ struct WordQ {
   uint2 c[kQW];  // u2 lo, u2 hi
 };
 
+// A warp's shared memory: its word queue, which before the first push holds
+// the Philox blocks of pairs 0..kHeadPairs-1 of the warp's first sites,
+// drawn before the kernel waits for the previous colour pass.
+union WarpArea {
+  WordQ wq;
+  uint4 pre[kHeadPairs][R][32];
+};
+
 struct Shared {
   uint4 u[R * 16];         // uniform parts of rounds 0..1 per (slot, pair)
   uint8_t lut[32];         // truth tables of the planes (pairs 8..15 read them at run time)
-  WordQ wq[kWarps];        // per-warp queues of words that need pair kHeadPairs
+  WarpArea wa[kWarps];     // per-warp queues of words that need pair kHeadPairs
   uint32_t left[kWarps];   // words each warp leaves queued at the end of its words
 };
 
@@ -217,7 +225,7 @@ __device__ __forceinline__ void word_round_at(const Shared& sh, uint32_t src, ui
   uint4 qa = make_uint4(0u, 0u, 0u, 0u), qb = qa;
   uint2 qc = make_uint2(0u, 0u);
   if (has) {
-    const WordQ& wq = sh.wq[src];
+    const WordQ& wq = sh.wa[src].wq;
     qa = wq.a[idx];
     qb = wq.b[idx];
     qc = wq.c[idx];
@@ -302,14 +310,44 @@ __device__ __forceinline__ void head_pairs(Half (&lo)[R], Half (&hi)[R], const S
   }
 }
 
+// Pairs 0..kHeadPairs-1 from Philox blocks drawn earlier (WarpArea::pre).
+template <int M>
+__device__ __forceinline__ void head_pairs_pre(Half (&lo)[R], Half (&hi)[R], const WarpArea& wa, uint32_t lane) {
+  if constexpr (M < kHeadPairs) {
+#pragma unroll
+    for (int a = 0; a < R; ++a) pair_planes<M>(lo[a], hi[a], wa.pre[M][a][lane]);
+    head_pairs_pre<M + 1>(lo, hi, wa, lane);
+  }
+}
+
+// Natural site index of colour word w (w = row * L/2 + k).
+__device__ __forceinline__ uint32_t site_of_word(uint32_t w, int colour) {
+  constexpr uint32_t L = (uint32_t)IANUS_JIT_L, h = L / 2u;
+  const uint32_t row = w / h, k = w - row * h;
+  const uint32_t y = row % L, z = row / L;
+  return 2u * k + ((uint32_t)(colour ^ (int)(y + z)) & 1u) + L * row;
+}
+
+// Draws the Philox blocks of pairs 0..kHeadPairs-1 of every slot for the
+// thread's first site (colour word w) into its warp's area.
+__device__ __forceinline__ void draw_first(Shared& sh, uint32_t w, const Ctx& c) {
+  const uint32_t lane = threadIdx.x & 31u;
+  WarpArea& wa = sh.wa[threadIdx.x >> 5];
+  const SiteKey sk = site_key(site_of_word(w, c.colour), c.thi_k);
+#pragma unroll
+  for (int m = 0; m < kHeadPairs; ++m)
+#pragma unroll
+    for (int a = 0; a < R; ++a) wa.pre[m][a][lane] = rounds_rest(sk, sh.u[a * 16 + m], *c.keys);
+}
+
 // The colour-c words [w_begin, w_end) of one group (word w = row * L/2 + k
 // of the colour's half rows): pairs 0..3 for every word, then the queues,
 // drained before returning.
 __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint64_t* __restrict__ Jg,
-                                            uint32_t w_begin, uint32_t w_end) {
+                                            uint32_t w_begin, uint32_t w_end, bool first_drawn) {
   constexpr Geom geom = kJitGeom;
   constexpr uint32_t N = kJitSites;
-  WordQ& wq = sh.wq[threadIdx.x >> 5];
+  WordQ& wq = sh.wa[threadIdx.x >> 5].wq;
   uint32_t nw = 0;
   for (uint32_t base = w_begin; base < w_end; base += kBlock) {
     const uint32_t wi = base + threadIdx.x;
@@ -372,8 +410,13 @@ __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint
         }
       }
     }
-    const SiteKey sk = site_key(site, c.thi_k);
-    head_pairs<0>(lo, hi, sk, sh, *c.keys);
+    if (first_drawn && base == w_begin) {  // the blocks of the first sites were drawn before the wait
+      head_pairs_pre<0>(lo, hi, sh.wa[threadIdx.x >> 5], threadIdx.x & 31u);
+      __syncwarp();  // every lane has read them before the warp's queue reuses the area
+    } else {
+      const SiteKey sk = site_key(site, c.thi_k);
+      head_pairs<0>(lo, hi, sk, sh, *c.keys);
+    }
     // decided lanes: flip where (r < T) != heat bath, one lop3 per half:
     // b ^ (res & ~und) (0xB4, Metropolis) or b ^ (~res & ~und) (0xE1)
 #pragma unroll
@@ -427,7 +470,11 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
   using namespace ianus;
   using namespace ianus::jlt;
   __shared__ Shared sh;
-  dependent_launch_entry();
+  // Before the wait for the previous colour pass nothing it writes is read:
+  // the sweep index (a launch parameter, or the captured graph's counter,
+  // written before the graph starts) and the Philox blocks of this thread's
+  // first site, which depend on the site and the sweep only.  Drawing them
+  // here uses the SMs the previous launch's last blocks leave idle.
   const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
   const uint32_t g = blockIdx.y;  // one temperature: blockIdx.y = group
   fill_uniform(sh, g, tk, p.keys);
@@ -440,7 +487,9 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
   c.colour = p.colour;
   const uint32_t w_begin = blockIdx.x * p.words_per_block;
   const uint32_t w_end = min(w_begin + p.words_per_block, kJitGeom.half);
-  sweep_words(sh, c, p.J + (uint64_t)g * D * kJitSites, w_begin, w_end);
+  draw_first(sh, min(w_begin + threadIdx.x, kJitGeom.half - 1u), c);
+  dependent_launch_entry();
+  sweep_words(sh, c, p.J + (uint64_t)g * D * kJitSites, w_begin, w_end, true);
 }
 
 #else
@@ -530,7 +579,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
     }
     c.thi_k = tk.hi ^ p.keys.k1[0];
     c.colour = (int)(pass & 1u);
-    sweep_words(sh, c, Jg, ra * h, rb * h);
+    sweep_words(sh, c, Jg, ra * h, rb * h, false);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();
