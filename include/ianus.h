@@ -438,13 +438,14 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       plane pair per round; 8 or 6 blocks of 128 threads per SM (22, 23),
  *       4 blocks of 256 (24).  With no explicit launch shape its grid is one
  *       wave of about that many blocks per SM;
- *   25, 26 = the persistent form of the lane-queue kernel: one cooperative
+ *   25..27 = the persistent form of the lane-queue kernel: one cooperative
  *       launch runs every sweep between two measurements.  Each block owns
  *       a fixed range of rows and starts a colour pass once the blocks that
  *       own its sites' neighbours have finished the previous pass (bounded
  *       waits, ianus_set_persistent_wait), so there is no kernel boundary
- *       between colours; at least 512 (25) or 128 (26) colour words per
- *       block, at most as many blocks as are resident at once.  Where that
+ *       between colours; blocks of 128 threads with at least 512 (25) or
+ *       128 (26) colour words, or of 256 threads with at least 512 (27), at
+ *       most as many blocks as are resident at once.  Where that
  *       launch cannot run it falls back to variant 22's per-pass kernel.
  * The fastest shape depends on the lattice and the algorithm: on the L=64,
  * 256-sample x 2-replica heat-bath lattice it is 21 with 256 words per block
@@ -467,7 +468,7 @@ ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
  * EINVAL above 2^24. */
 ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
 
-/* Waits of the persistent sweep (variants 25, 26): each wait of a block for
+/* Waits of the persistent sweep (variants 25..27): each wait of a block for
  * its neighbours' progress is bounded by timeout_ns (default 2 s).  A wait
  * that runs out sets the device error word and the block returns; the next
  * ianus_synchronize reports IANUS_ETIMEOUT and the lattice is ESTATE

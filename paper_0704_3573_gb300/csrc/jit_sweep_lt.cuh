@@ -555,6 +555,17 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
   const uint64_t* Jg = p.J + (uint64_t)g * D * kJitSites;
   const uint64_t t0 = (uint64_t)pp.t0_lo | ((uint64_t)pp.t0_hi << 32);
   for (uint32_t pass = 0; pass < pp.npass; ++pass) {
+    const uint64_t t = t0 + (pass >> 1);
+    const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
+    if ((pass & 1u) == 0u) {  // a new sweep: its uniform Philox parts
+      fill_uniform(sh, g, tk, p.keys);
+      __syncthreads();
+    }
+    c.thi_k = tk.hi ^ p.keys.k1[0];
+    c.colour = (int)(pass & 1u);
+    // the Philox blocks of the first sites depend on the sweep only: drawn
+    // while the neighbours may still be finishing the previous pass
+    draw_first(sh, min(ra * h + threadIdx.x, kJitGeom.half - 1u), c);
     if (pass > 0u) {
       if (threadIdx.x < 32u) {
         bool ok = true;
@@ -571,15 +582,7 @@ extern "C" __global__ void __launch_bounds__(ianus::jlt::kBlock, IANUS_JIT_MINB)
       __syncthreads();
       if (s_abort) return;
     }
-    const uint64_t t = t0 + (pass >> 1);
-    const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
-    if ((pass & 1u) == 0u) {  // a new sweep: its uniform Philox parts
-      fill_uniform(sh, g, tk, p.keys);
-      __syncthreads();
-    }
-    c.thi_k = tk.hi ^ p.keys.k1[0];
-    c.colour = (int)(pass & 1u);
-    sweep_words(sh, c, Jg, ra * h, rb * h, false);
+    sweep_words(sh, c, Jg, ra * h, rb * h, true);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();

@@ -1068,7 +1068,7 @@ constexpr JitShape kJitShapes[] = {
     // mode 3: the lane-queue kernel (jit_sweep_lt.cuh), blocks/SM and block size
     {3, 4, 8, 1, 0, 0, 128}, {3, 4, 6, 1, 0, 0, 128}, {3, 4, 4, 1, 0, 0, 256},
     // mode 4: its persistent form; phase_a = least colour words per block / 128
-    {4, 4, 8, 1, 0, 0, 128}, {4, 1, 8, 1, 0, 0, 128}};
+    {4, 4, 8, 1, 0, 0, 128}, {4, 1, 8, 1, 0, 0, 128}, {4, 4, 4, 1, 0, 0, 256}};
 constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 24;  // the lane-queue kernel, 4 blocks of 256 per SM

@@ -190,7 +190,7 @@ cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int
 cudaKernel_t jit_lt_kernel(const Lattice& lat, int algo, int min_blocks, int block);
 // Its persistent form (IANUS_JIT_PERSIST): many sweeps per launch.
 cudaKernel_t jit_ltp_kernel(const Lattice& lat, int algo, int min_blocks, int block);
-constexpr int kMaxVariant = 26;  // ianus_set_variant accepts 0..kMaxVariant
+constexpr int kMaxVariant = 27;  // ianus_set_variant accepts 0..kMaxVariant
 constexpr int kMaxPersistBlocks = 4096;
 // True when the selected variant is the persistent sweep and the lattice
 // qualifies (one temperature, one or two replicas, lane-uniform tables).

@@ -16,7 +16,7 @@ import json
 import os
 import tempfile
 
-VARIANTS = tuple(range(1, 27))
+VARIANTS = tuple(range(1, 28))
 BLOCK_WORDS = (0, 256, 512, 1024, 2048)
 
 

@@ -45,7 +45,7 @@ def _run(ianus, variant, dim, L, S, R, steps, block_words=0, seed=SEED, graphs=N
 STEPS = [(HEATBATH, 0.9, 4, 2), (METROPOLIS, 1.1, 3, 3)]
 
 
-@pytest.mark.parametrize("variant", [22, 23, 24, 25, 26])
+@pytest.mark.parametrize("variant", [22, 23, 24, 25, 26, 27])
 @pytest.mark.parametrize("dim,L,S,R", [(3, 8, 70, 2), (3, 16, 130, 1), (2, 32, 65, 2), (3, 6, 64, 2),
                                        (2, 10, 3, 1), (3, 2, 67, 2), (2, 2, 1, 1), (3, 12, 100, 2)])
 def test_lane_queue_bit_exact(ianus, variant, dim, L, S, R):
