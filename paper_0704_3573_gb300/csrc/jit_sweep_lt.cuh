@@ -320,12 +320,45 @@ __device__ __forceinline__ void head_pairs_pre(Half (&lo)[R], Half (&hi)[R], con
   }
 }
 
-// Natural site index of colour word w (w = row * L/2 + k).
+// Colour-c word w = row * L/2 + k of the split layout: the site x + L row
+// with x = 2k + xpar, xpar the parity that gives the site colour c.  Since
+// L = 2h the natural index is 2w + xpar, the word is w + (row + c) h, and
+// the other colour's word of the same row and k is 2(w - k) + (1 - c) h + k;
+// the y and z neighbours are that word plus or minus 2h and 2hL rows' worth
+// of words, wrapped at the faces.
+__device__ __forceinline__ Nbr neighbours_lt(uint32_t w, int colour) {
+  constexpr uint32_t L = (uint32_t)IANUS_JIT_L, h = L / 2u;
+  const uint32_t c = (uint32_t)colour;
+  const uint32_t row = w / h, k = w - row * h;
+  const uint32_t y = row % L, z = D == 3 ? row / L : 0u;
+  const uint32_t xpar = (c ^ y ^ z) & 1u;
+  Nbr n;
+  n.self = w + (row + c) * h;
+  n.site = 2u * w + xpar;
+  const uint32_t base_o = 2u * (w - k) + (1u - c) * h;
+  uint32_t kp = k + xpar, km = k + xpar - 1u;  // (x + 1) / 2 and (x - 1) / 2, mod h
+  if (kp == h) kp = 0u;
+  if (km == 0xffffffffu) km = h - 1u;
+  n.xp = base_o + kp;
+  n.xm = base_o + km;
+  const uint32_t ko = base_o + k;
+  n.yp = ko + (y == L - 1u ? 0u - 2u * h * (L - 1u) : 2u * h);
+  n.ym = ko + (y == 0u ? 2u * h * (L - 1u) : 0u - 2u * h);
+  if (D == 3) {
+    n.zp = ko + (z == L - 1u ? 0u - 2u * h * L * (L - 1u) : 2u * h * L);
+    n.zm = ko + (z == 0u ? 2u * h * L * (L - 1u) : 0u - 2u * h * L);
+  } else {
+    n.zp = n.zm = 0u;
+  }
+  return n;
+}
+
+// Natural site index of colour word w.
 __device__ __forceinline__ uint32_t site_of_word(uint32_t w, int colour) {
   constexpr uint32_t L = (uint32_t)IANUS_JIT_L, h = L / 2u;
-  const uint32_t row = w / h, k = w - row * h;
-  const uint32_t y = row % L, z = row / L;
-  return 2u * k + ((uint32_t)(colour ^ (int)(y + z)) & 1u) + L * row;
+  const uint32_t row = w / h;
+  const uint32_t y = row % L, z = D == 3 ? row / L : 0u;
+  return 2u * w + (((uint32_t)colour ^ y ^ z) & 1u);
 }
 
 // Draws the Philox blocks of pairs 0..kHeadPairs-1 of every slot for the
@@ -345,7 +378,6 @@ __device__ __forceinline__ void draw_first(Shared& sh, uint32_t w, const Ctx& c)
 // drained before returning.
 __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint64_t* __restrict__ Jg,
                                             uint32_t w_begin, uint32_t w_end, bool first_drawn) {
-  constexpr Geom geom = kJitGeom;
   constexpr uint32_t N = kJitSites;
   WordQ& wq = sh.wa[threadIdx.x >> 5].wq;
   uint32_t nw = 0;
@@ -358,7 +390,7 @@ __device__ __forceinline__ void sweep_words(Shared& sh, const Ctx& c, const uint
     uint64_t b[R];
     Nbr n{};
     if (valid) {
-      n = split_neighbours_t<P2>(geom, c.colour, wi);
+      n = neighbours_lt(wi, c.colour);
       site = n.site;
       uint64_t jw[2 * D];
       jw[0] = __ldg(Jg + n.self);
