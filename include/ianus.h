@@ -448,15 +448,18 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  *       most as many blocks as are resident at once.  Where that
  *       launch cannot run it falls back to variant 22's per-pass kernel.
  * The fastest shape depends on the lattice and the algorithm: on the L=64,
- * 256-sample x 2-replica heat-bath lattice it is 21 with 256 words per block
- * (ianus_set_block_words), faster than the automatic lockstep shape by
- * about a sixth.  The Python autotuner (tune.py) times the shapes on the
- * caller's lattice.
- * The plain one-byte-per-spin layout (IANUS_LAYOUT_I8) has two sweep
+ * 256-sample x 2-replica heat-bath lattice it is the automatic one (24 in
+ * its one-wave grid), which takes a fifth less time per sweep than 21 with
+ * 256 words per block (ianus_set_block_words), the fastest shape before the
+ * lane-queue kernel.  The
+ * Python autotuner (tune.py) times the shapes on the caller's lattice.
+ * The plain one-byte-per-spin layout (IANUS_LAYOUT_I8) has three sweep
  * kernels: variant 1 runs one thread per update, each drawing its own
- * random planes; every other value runs the tiled kernel, in which a block
- * draws the planes of a site once for the site's 64-sample group and each
- * update reads an 8-bit prefix of its random number from shared memory.
+ * random planes; every other value runs a kernel in which a block draws the
+ * planes of a site once for the site's 64-sample group and each update
+ * compares an 8-bit prefix of its random number from shared memory: the
+ * word kernel (four spins of one sample per 32-bit load) when L is a
+ * multiple of 4, else the tiled kernel (one byte per thread).
  * With several temperatures every variant but 1 uses the per-lane kernel
  * compiled for the geometry.  If run-time compilation is unavailable, the
  * precompiled kernel runs.  EINVAL for other values. */
@@ -464,9 +467,34 @@ ianus_status ianus_set_variant(ianus_lattice* lat, int32_t variant);
 
 /* Launch shape of the bit-sliced sweep: colour words handled by one block of
  * 256 threads (rounded up to a multiple of 32, whole warps); 0 restores the
- * default, a multiple of 256 that sizes the grid to about 8 blocks per SM.
+ * default, a multiple of 256 that sizes the grid to about 8 blocks per SM
+ * (for the lane-queue kernels 22..24: a multiple of 32 that makes the grid
+ * one wave of resident blocks).
  * EINVAL above 2^24. */
 ianus_status ianus_set_block_words(ianus_lattice* lat, uint32_t words_per_block);
+
+/* Compiles (or finds in the per-process cache) the kernel that a sweep of
+ * this lattice at (algo, beta[0]) under kernel variant `variant` would
+ * specialise for its acceptance thresholds (the Metropolis and heat-bath
+ * rules of Sec. 2.2 and Eq. (4), as the look-up table of Sec. 3.2), without
+ * launching anything and without changing the lattice.  A sweep that finds no kernel compiles it on the
+ * calling thread first, a fraction of a second; a server calls this on a
+ * worker thread instead and runs the job meanwhile under variant 1 (the
+ * precompiled kernel, same results), switching to `variant` once *ready.
+ * Reads only the lattice's shape, fixed at creation, so it may run while
+ * other threads sweep this or other lattices (the lattice must not be
+ * destroyed before the call returns); concurrent calls compile different
+ * kernels in parallel and wait for one another on the same one.
+ * beta: one inverse temperature per temperature of the lattice (n_temps),
+ * finite and >= 0.  *ready = 1 when the specialised kernel is now cached,
+ * 0 when the variant selects none on this lattice (several temperatures,
+ * a field or Potts model, the plain layout, variant 1) or run-time
+ * compilation is unavailable or failed (the sweep then uses a per-lane
+ * kernel, as it would anyway).  EINVAL for a null pointer, an unknown algo,
+ * a variant outside 0..27 or a bad beta; ECUDA when the lattice's device
+ * cannot be made current. */
+ianus_status ianus_prepare_sweep(ianus_lattice* lat, int32_t algo, const double* beta, int32_t variant,
+                                 int32_t* ready);
 
 /* Waits of the persistent sweep (variants 25..27): each wait of a block for
  * its neighbours' progress is bounded by timeout_ns (default 2 s).  A wait

@@ -43,7 +43,7 @@ EXPORTS = [
     "ianus_table_pt", "ianus_measure_bits64_noalloc", "ianus_set_variant", "ianus_set_block_words",
     "ianus_set_graphs", "ianus_set_resident", "ianus_get_sites_i8", "ianus_set_sites_i8", "ianus_table_field",
     "ianus_table_potts_counts", "ianus_segment_load", "ianus_segment_release", "ianus_segment_state",
-    "ianus_sweep_segments", "ianus_set_persistent_wait",
+    "ianus_sweep_segments", "ianus_set_persistent_wait", "ianus_prepare_sweep",
 ]
 
 
@@ -120,6 +120,7 @@ def lib(build_if_missing: bool = True):
         "ianus_set_variant": (i32, [vp, i32]),
         "ianus_set_block_words": (i32, [vp, u32]),
         "ianus_set_persistent_wait": (i32, [vp, u64, i32]),
+        "ianus_prepare_sweep": (i32, [vp, i32, vp, i32, vp]),
         "ianus_set_graphs": (i32, [vp, i32]),
         "ianus_set_resident": (i32, [vp, i32]),
         "ianus_get_sites_i8": (i32, [vp, vp, vp]),
@@ -276,6 +277,18 @@ class Lattice:
         _check(self._lib.ianus_sweep(self._h, a, b.ctypes.data_as(C.POINTER(C.c_double)), nsweeps, measure_every),
                "ianus_sweep")
 
+    def prepare_sweep(self, algo, beta, variant: int = 0) -> bool:
+        """Compile (or find cached) the kernel a sweep at (algo, beta) under
+        `variant` would specialise, without launching or changing anything;
+        True when that kernel is ready.  Safe on a worker thread while other
+        threads sweep (the call releases the GIL)."""
+        a = _ALGOS[algo] if isinstance(algo, str) else int(algo)
+        b = self._beta(beta)
+        ready = C.c_int32(0)
+        _check(self._lib.ianus_prepare_sweep(self._h, a, b.ctypes.data_as(C.POINTER(C.c_double)), int(variant),
+                                             C.byref(ready)), "ianus_prepare_sweep")
+        return bool(ready.value)
+
     def pt_swap(self):
         _check(self._lib.ianus_pt_swap(self._h), "ianus_pt_swap")
 
@@ -388,7 +401,7 @@ class Lattice:
 
     def set_variant(self, variant: int):
         """Bit-sliced sweep kernel: 0 automatic, 1 per-lane threshold planes,
-        2..26 shapes of the kernel specialised at run time (include/ianus.h)."""
+        2..27 shapes of the kernel specialised at run time (include/ianus.h)."""
         _check(self._lib.ianus_set_variant(self._h, variant), "ianus_set_variant")
 
     def set_block_words(self, words: int):
@@ -396,7 +409,7 @@ class Lattice:
         _check(self._lib.ianus_set_block_words(self._h, words), "ianus_set_block_words")
 
     def set_persistent_wait(self, timeout_ns: int, absent_block: int = -1):
-        """Bound of each wait of the persistent sweep (variants 25, 26), and a
+        """Bound of each wait of the persistent sweep (variants 25..27), and a
         block told to return at once (tests of the timeout path; -1 none)."""
         _check(self._lib.ianus_set_persistent_wait(self._h, int(timeout_ns), int(absent_block)),
                "ianus_set_persistent_wait")

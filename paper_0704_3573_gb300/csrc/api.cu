@@ -167,6 +167,28 @@ Fail fail(Lattice* lat, int st) {
 
 void drop_graphs(Lattice* lat);
 
+}  // namespace
+
+// Bit c of t[q] is bit 31 - q of class c's threshold; `always` marks the
+// classes that flip whatever the random number (threshold 2^32), `need` the
+// classes whose comparison decides the flip.
+UniformLut ianus::uniform_lut(int dim, int algo, const uint64_t* thr) {
+  UniformLut u{};
+  uint32_t always = 0, cmp = 0;
+  for (int c = 0; c <= 2 * dim; ++c) {
+    const uint64_t T = thr[c];
+    if (T >= kTwo32) always |= 1u << c;
+    else if (algo == IANUS_HEATBATH || c < dim) cmp |= 1u << c;
+    for (int q = 0; q < 32; ++q)
+      if (T < kTwo32 && ((T >> (31 - q)) & 1ull)) u.t[q] |= (uint8_t)(1u << c);
+  }
+  u.always = (uint8_t)always;
+  u.need = (uint8_t)cmp;
+  return u;
+}
+
+namespace {
+
 bool beta_ok(const double* beta, int K) {
   for (int k = 0; k < K; ++k)
     if (!std::isfinite(beta[k]) || beta[k] < 0.0) return false;
@@ -218,19 +240,7 @@ int upload_tables(Lattice* lat, int algo, const double* beta) {
     if (lat->layout == IANUS_LAYOUT_BITS64) CK(launch_build_planes(*lat));
     lat->ulut_ok = false;
     if (K == 1) {
-      UniformLut u{};
-      const int nclass = 2 * lat->D + 1;
-      uint32_t always = 0, cmp = 0;
-      for (int c = 0; c < nclass; ++c) {
-        const uint64_t T = thr[c];
-        if (T >= kTwo32) always |= 1u << c;
-        else if (algo == IANUS_HEATBATH || c < lat->D) cmp |= 1u << c;
-        for (int q = 0; q < 32; ++q)
-          if (T < kTwo32 && ((T >> (31 - q)) & 1ull)) u.t[q] |= (uint8_t)(1u << c);
-      }
-      u.always = (uint8_t)always;
-      u.need = (uint8_t)cmp;
-      lat->ulut = u;
+      lat->ulut = uniform_lut(lat->D, algo, thr.data());
       CK(cudaMemcpyAsync(lat->thr + (size_t)K * kMaxClasses, &lat->ulut, sizeof(UniformLut), cudaMemcpyHostToDevice,
                          lat->stream));
       lat->ulut_ok = true;
@@ -530,6 +540,10 @@ ianus_status ianus_lattice_create(const ianus_config* cfg, ianus_lattice** out) 
   lat->geom.half = z.N / 2;
   lat->stream = (cudaStream_t)cfg->cuda_stream;
   lat->keys = make_keys(cfg->seed);
+  if (cudaGetDevice(&lat->dev) != cudaSuccess) {
+    cudaGetLastError();
+    lat->dev = 0;
+  }
   lat->algo = -1;
   lat->jit_algo = -1;
   lat->jit_variant = -1;
@@ -1196,6 +1210,36 @@ ianus_status ianus_set_variant(ianus_lattice* h, int32_t variant) {
   if (variant < 0 || variant > kMaxVariant) return IANUS_EINVAL;
   if (lat->variant != variant) drop_graphs(lat);
   lat->variant = variant;
+  return IANUS_OK;
+}
+
+ianus_status ianus_prepare_sweep(ianus_lattice* h, int32_t algo, const double* beta, int32_t variant,
+                                 int32_t* ready) {
+  Lattice* lat = reinterpret_cast<Lattice*>(h);
+  if (!lat || !beta || !ready) return IANUS_EINVAL;
+  *ready = 0;
+  if ((algo != IANUS_METROPOLIS && algo != IANUS_HEATBATH) || variant < 0 || variant > kMaxVariant) return IANUS_EINVAL;
+  if (!beta_ok(beta, lat->K)) return IANUS_EINVAL;
+  // only the bit-sliced +-J sweep at one temperature has specialised kernels
+  if (lat->model != IANUS_EA_PM_J || lat->layout != IANUS_LAYOUT_BITS64 || lat->field || lat->pool || lat->K != 1)
+    return IANUS_OK;
+  const int v = specialised_variant(*lat, variant);
+  if (v < 2) return IANUS_OK;
+  uint64_t thr[kMaxClasses];
+  class_thresholds(lat->D, algo, beta[0], thr);
+  const UniformLut u = uniform_lut(lat->D, algo, thr);
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    prev = -1;
+  }
+  if (prev != lat->dev && cudaSetDevice(lat->dev) != cudaSuccess) {
+    cudaGetLastError();
+    return IANUS_ECUDA;
+  }
+  *ready = specialised_sweep_kernel(*lat, u, algo, v) ? 1 : 0;
+  if (prev >= 0 && prev != lat->dev) cudaSetDevice(prev);
+  cudaGetLastError();
   return IANUS_OK;
 }
 

@@ -1073,17 +1073,22 @@ constexpr int kNumJitShapes = sizeof(kJitShapes) / sizeof(kJitShapes[0]);
 static_assert(kNumJitShapes + 1 == kMaxVariant, "variants 2..kMaxVariant are the shapes");
 constexpr int kAutoJitVariant = 24;  // the lane-queue kernel, 4 blocks of 256 per SM
 
-// The specialised kernel shape the next sweep uses (>= 2), or 1 for the
-// precompiled per-lane kernel.
-int jit_variant_for(const Lattice& lat) {
-  int v = lat.variant;
-  if (v == 0) v = kAutoJitVariant;
-  bool ok = lat.K == 1 && lat.ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
+// The specialised kernel shape (>= 2) that variant `variant` selects on this
+// lattice with lane-uniform tables (ulut_ok), or 1 for the per-lane kernel.
+int jit_variant_of(const Lattice& lat, int variant, bool ulut_ok) {
+  int v = variant == 0 ? kAutoJitVariant : variant;
+  bool ok = lat.K == 1 && ulut_ok && v >= 2 && v < 2 + kNumJitShapes && (lat.R == 1 || lat.R == 2);
   if (ok && kJitShapes[v - 2].mode == 2 && lat.R != 2) v = 2;  // the interleaved shape needs two replicas
   return ok ? v : 1;
 }
 
+// The specialised kernel shape the next sweep uses (>= 2), or 1 for the
+// precompiled per-lane kernel.
+int jit_variant_for(const Lattice& lat) { return jit_variant_of(lat, lat.variant, lat.ulut_ok); }
+
 }  // namespace
+
+int specialised_variant(const Lattice& lat, int variant) { return jit_variant_of(lat, variant, true); }
 
 bool persistent_variant(const Lattice& lat) {
   const int v = jit_variant_for(lat);
@@ -1164,6 +1169,12 @@ cudaError_t launch_sweep_persistent(Lattice& lat, int inv, uint64_t t0, uint32_t
   return cudaSuccess;
 }
 
+cudaKernel_t specialised_sweep_kernel(const Lattice& lat, const UniformLut& u, int algo, int v) {
+  if (v < 2 || v >= 2 + kNumJitShapes) return nullptr;
+  const JitShape& js = kJitShapes[v - 2];
+  return jit_kernel(lat, u, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst, js.block);
+}
+
 void prepare_sweep_bits(Lattice& lat, int inv) {
   const int algo = inv ? 1 : 0;
   if (lat.field) {
@@ -1175,8 +1186,7 @@ void prepare_sweep_bits(Lattice& lat, int inv) {
   }
   const int v = jit_variant_for(lat);
   if (v >= 2 && (lat.jit_algo != algo || lat.jit_variant != v)) {
-    const JitShape& js = kJitShapes[v - 2];
-    lat.jit = jit_kernel(lat, algo, js.mode, js.phase_a, js.min_blocks, js.group, js.jreload, js.ufirst, js.block);
+    lat.jit = specialised_sweep_kernel(lat, lat.ulut, algo, v);
     lat.jit_algo = algo;
     lat.jit_variant = v;
   }
@@ -1360,7 +1370,7 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
     const JitShape& js = kJitShapes[v - 2];
     prepare_sweep_bits(lat, inv);
     // mode 4 (persistent) passes that run one at a time use its per-pass form
-    const cudaKernel_t k3 = js.mode == 4 ? jit_lt_kernel(lat, algo, js.min_blocks, js.block) : lat.jit;
+    const cudaKernel_t k3 = js.mode == 4 ? jit_lt_kernel(lat, lat.ulut, algo, js.min_blocks, js.block) : lat.jit;
     if (k3 && (js.mode == 3 || js.mode == 4)) {
       // one wave: about min_blocks blocks per SM in all, whole warps of words
       uint32_t w3;

@@ -140,6 +140,7 @@ struct Lattice {
   bool pt_tables_ok;
   int sticky;                // sticky error status (ESTATE after a failure)
   int variant;               // kernel variant knob (tuner), 0 = default
+  int dev;                   // CUDA device current when the lattice was created
   UniformLut ulut;           // valid when ulut_ok (n_temps == 1)
   bool ulut_ok;
   cudaKernel_t jit;          // sweep kernel specialised for ulut (null: use the per-lane planes)
@@ -183,13 +184,24 @@ void field_thresholds(int dim, int algo, double beta, double hmag, uint64_t* thr
 // of dynamic shared memory: one queue of 64 entries (5 x 8 + 3 x 4 bytes) for
 // each of its 8 warps.
 constexpr size_t kJitSmemBytes = 8 * 64 * (5 * 8 + 3 * 4);
-cudaKernel_t jit_kernel(const Lattice& lat, int algo, int mode, int phase_a, int min_blocks, int group,
-                        int jreload, int ufirst, int block);
+cudaKernel_t jit_kernel(const Lattice& lat, const UniformLut& u, int algo, int mode, int phase_a, int min_blocks,
+                        int group, int jreload, int ufirst, int block);
 // The lane-queue shape of the same sweep (jit_sweep_lt.cuh): shared Philox
 // rounds 0..1, four plane pairs for every word, undecided lanes queued.
-cudaKernel_t jit_lt_kernel(const Lattice& lat, int algo, int min_blocks, int block);
+cudaKernel_t jit_lt_kernel(const Lattice& lat, const UniformLut& u, int algo, int min_blocks, int block);
 // Its persistent form (IANUS_JIT_PERSIST): many sweeps per launch.
-cudaKernel_t jit_ltp_kernel(const Lattice& lat, int algo, int min_blocks, int block);
+cudaKernel_t jit_ltp_kernel(const Lattice& lat, const UniformLut& u, int algo, int min_blocks, int block);
+// The specialised shape (>= 2) that `variant` selects on this lattice when
+// its tables are lane-uniform, or 1 when it selects none (k_msc.cu).
+int specialised_variant(const Lattice& lat, int variant);
+// The kernel of shape v (>= 2) specialised for tables u and algorithm algo
+// (0 Metropolis, 1 heat bath); null when run-time compilation is
+// unavailable or fails.  Reads only the lattice's shape (D, L, R, K,
+// geometry), which is fixed at creation, so any thread may call it.
+cudaKernel_t specialised_sweep_kernel(const Lattice& lat, const UniformLut& u, int algo, int v);
+// Lane-uniform tables of one temperature from the class thresholds
+// thr[0..2D] (api.cu).
+UniformLut uniform_lut(int dim, int algo, const uint64_t* thr);
 constexpr int kMaxVariant = 27;  // ianus_set_variant accepts 0..kMaxVariant
 constexpr int kMaxPersistBlocks = 4096;
 // True when the selected variant is the persistent sweep and the lattice

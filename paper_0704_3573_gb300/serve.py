@@ -29,6 +29,7 @@ import dataclasses
 import math
 import time
 from collections import deque
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -115,14 +116,22 @@ def footprint(job: Job) -> int:
 
 
 class _Active:
-    __slots__ = ("job", "lat", "stream", "event", "done", "admitted", "footprint")
+    __slots__ = ("job", "lat", "stream", "event", "done", "admitted", "footprint", "ready")
 
 
 class Server:
-    """Admission by memory and slots; chunked, stream-interleaved sweeps."""
+    """Admission by memory and slots; chunked, stream-interleaved sweeps.
+
+    A job's lattice sweeps with a kernel specialised for its temperature,
+    compiled at run time.  With compile_workers > 0 that compilation runs on
+    worker threads (ianus_prepare_sweep): the job starts at once on the
+    precompiled kernel (variant 1, the same trajectory bit for bit) and
+    switches at its next chunk after its kernel is ready, so no compilation
+    stalls the scheduling loop.  With compile_workers = 0 the first sweep of
+    a job compiles on the scheduling thread."""
 
     def __init__(self, mem_budget: int = 8 << 30, max_active: int = 64, n_streams: int = 8,
-                 chunk_sweeps: int = 100):
+                 chunk_sweeps: int = 100, compile_workers: int = 8):
         import torch
 
         self.torch = torch
@@ -131,6 +140,8 @@ class Server:
         self.chunk = chunk_sweeps
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
         self._rr = 0
+        self._pool = ThreadPoolExecutor(max_workers=compile_workers) if compile_workers > 0 else None
+        self._closing: list = []  # (lattice, compile future) of finished jobs
 
     def _admit(self, job: Job, now: float) -> _Active:
         a = _Active()
@@ -139,13 +150,46 @@ class Server:
         self._rr += 1
         a.lat = Lattice(dim=job.dim, L=job.L, n_samples=job.samples, n_replicas=1, seed=job.seed,
                         layout="bits64", series_capacity=1, stream=a.stream)
+        a.ready = None
+        if self._pool is not None:
+            a.lat.set_variant(1)
+            a.ready = self._pool.submit(a.lat.prepare_sweep, job.algo, 1.0 / job.T, 0)
         a.event = None
         a.done = 0
         a.admitted = now
         a.footprint = footprint(job)
         return a
 
+    def _retire(self, a: _Active):
+        """Close a finished job's lattice, or keep it until the compilation
+        that reads its shape on a worker thread returns."""
+        if a.ready is not None and not a.ready.done() and not a.ready.cancel():
+            self._closing.append((a.lat, a.ready))
+        else:
+            a.lat.close()
+        a.lat = None
+        self._reap()
+
+    def _reap(self):
+        keep = []
+        for lat, fut in self._closing:
+            if fut.done():
+                lat.close()
+            else:
+                keep.append((lat, fut))
+        self._closing = keep
+
+    def _drain(self):
+        for lat, fut in self._closing:
+            fut.result()
+            lat.close()
+        self._closing = []
+
     def _issue(self, a: _Active):
+        if a.ready is not None and a.ready.done():
+            if a.ready.result():
+                a.lat.set_variant(0)
+            a.ready = None
         n = min(self.chunk, a.job.sweeps - a.done)
         with self.torch.cuda.stream(a.stream):
             a.lat.sweep(a.job.algo, 1.0 / a.job.T, n)
@@ -190,9 +234,9 @@ class Server:
                 fin = time.perf_counter() - t0
                 results.append(Result(a.job, E[:, 0, 0].copy(), M[:, 0, 0].copy(), a.admitted, fin))
                 used -= a.footprint
-                a.lat.close()
-                del a.lat
+                self._retire(a)
             active = still
+            self._reap()
             if not progressed:
                 if realtime and not active and pending:
                     time.sleep(max(0.0, min(0.002, pending[0].arrival - (time.perf_counter() - t0))))
@@ -200,6 +244,7 @@ class Server:
                     time.sleep(0.0002)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        self._drain()
         lat = np.array([r.latency for r in results])
         upd = sum(r.job.updates for r in results)
         stats = {
@@ -303,7 +348,8 @@ class FusedServer:
     different temperatures cannot use."""
 
     def __init__(self, mem_budget: int = 8 << 30, groups_per_pool: int = 4, n_streams: int = 8,
-                 chunk_sweeps: int = 100, fuse_max_sites: int = 1 << 16, max_solo: int = 32):
+                 chunk_sweeps: int = 100, fuse_max_sites: int = 1 << 16, max_solo: int = 32,
+                 compile_workers: int = 8):
         import torch
 
         self.torch = torch
@@ -313,7 +359,8 @@ class FusedServer:
         self.fuse_max_sites = fuse_max_sites
         self.max_solo = max_solo
         self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
-        self._solo = Server(mem_budget, max_active=max_solo, n_streams=1, chunk_sweeps=chunk_sweeps)
+        self._solo = Server(mem_budget, max_active=max_solo, n_streams=1, chunk_sweeps=chunk_sweeps,
+                            compile_workers=compile_workers)
         self._solo.streams = self.streams
 
     def run(self, jobs: list[Job], realtime: bool = True) -> tuple[list[Result], dict]:
@@ -361,9 +408,9 @@ class FusedServer:
                 results.append(Result(a.job, E[:, 0, 0].copy(), M[:, 0, 0].copy(), a.admitted,
                                       time.perf_counter() - t0))
                 used -= a.footprint
-                a.lat.close()
-                del a.lat
+                self._solo._retire(a)
             solo = still
+            self._solo._reap()
             for key, q in waiting.items():
                 ps = pools.setdefault(key, [])
                 # admit in arrival order into idle pools (a busy pool is fed after its chunk)
@@ -425,6 +472,7 @@ class FusedServer:
                     time.sleep(0.0002)
         torch.cuda.synchronize()
         wall = time.perf_counter() - t0
+        self._solo._drain()
         for ps in pools.values():
             for p in ps:
                 p.lat.close()
