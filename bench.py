@@ -58,7 +58,7 @@ SM_MAX_MHZ = 2070.0
 # words per block), valid while the kernel source is unchanged (hash of the
 # sources it is compiled from).
 TRAFFIC_BYTES_PER_LAUNCH = {(24, 0): 41977600}
-TRAFFIC_SOURCE_HASH = "1276329b91b232ea"
+TRAFFIC_SOURCE_HASH = "0b06d535be286e49"
 # Memory traffic of one colour launch of the q=4 Potts sweep (k_sweep_potts)
 # on its L=32, 128 x 2 workload, from one ncu capture, valid while its
 # sources are unchanged: global loads through L1 (spin words, couplings and
