@@ -698,6 +698,36 @@ def run_other_configs(args):
             out[key]["cpu_baseline"] = {"value": 2 * 2 * Lp ** dim / (dt * 1e9), "unit": UNIT, "cores": 2,
                                         "kind": "oracle", "sample": "samples 0, 255 x 2 replicas, 1 sweep"}
         del pp
+    # resident sweeps of small bit-sliced lattices: 3D L=8 (the serving mix's
+    # smallest side), one replica, heat bath T=1.0, no measurements; 152
+    # groups of 64 samples (one resident block per SM) and a single group,
+    # against the same lattices swept launch by launch (resident mode off)
+    res_out = {}
+    for groups, n in ((152, 1000), (1, 1000)):
+        rl = ianus.Lattice(dim=3, L=8, n_samples=64 * groups, n_replicas=1, seed=SEED + 9, layout="bits64",
+                           stream=stream)
+        rates = {}
+        for mode in (1, 0):
+            rl.set_resident(mode)
+            rl.sweep(ianus.HEATBATH, 1.0, 20)
+            reps = 3
+            sec = timed(lambda: rl.sweep(ianus.HEATBATH, 1.0, n), reps)
+            rates["resident" if mode else "launch_per_colour"] = {
+                "updates_per_ns": 64 * groups * 8 ** 3 * n * reps / (sec * 1e9), "us_per_sweep": sec * 1e6 / (n * reps)}
+        res_out[f"{groups}x64"] = rates
+        del rl
+    # per-lane-plane update, 3D heat bath: e-words 12, adder tree 16, the
+    # "always" plane (12) and the undecided mask (4); per plane the
+    # threshold bit by a 7-way multiplexer tree (6) + compare (4); per pair
+    # Philox 21 ALU + merge 2; 3.92 plane pairs per word (and 20 mad.wide
+    # per Philox block)
+    alu_word = 44 + 3.92 * (2 * 10 + 23)
+    out["resident_L8_64xG_hb"] = {
+        **res_out,
+        "mode": "bit-sliced, k_resident_bits: one block per 64-sample group holds spins, couplings and threshold "
+                "planes in shared memory for up to 4096 sweeps per launch; heat bath T=1.0, one replica",
+        "roofline": issue_roof(alu_word, 3.92 * 20, 64, res_out["152x64"]["resident"]["updates_per_ns"]),
+    }
     # device-side set-up: couplings and initial spins of the bench workload from the seed
     t0 = time.perf_counter()
     lat = ianus.Lattice(dim=3, L=L, n_samples=S, n_replicas=R, seed=SEED + 3, layout="bits64", stream=stream)

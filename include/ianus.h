@@ -406,9 +406,11 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * differs).  With one temperature the thresholds are the same in every lane
  * and the sweep kernel can be specialised for them at run time (NVRTC, a
  * fraction of a second per new table set, cached per device).
- *   0 = automatic: with one temperature and one or two replicas the
- *       lane-queue kernel (variant 24, below), the fastest shape measured on
- *       every lattice from L = 8 to L = 128; otherwise the kernel with
+ *   0 = automatic: a lattice small enough for shared memory sweeps
+ *       resident (ianus_set_resident); otherwise, with one temperature and
+ *       one or two replicas, the lane-queue kernel (variant 24, below), the
+ *       fastest shape measured on every lattice from L = 8 to L = 128; else
+ *       the kernel with
  *       per-lane threshold bit-planes, compiled at run time for the
  *       lattice's geometry (also with several temperatures and for parallel
  *       tempering);
@@ -514,7 +516,26 @@ ianus_status ianus_set_persistent_wait(ianus_lattice* lat, uint64_t timeout_ns, 
  * and without graphs.  enable = 0 launches every kernel directly. */
 ianus_status ianus_set_graphs(ianus_lattice* lat, int32_t enable);
 
-/* Resident mode for small plain lattices (default on): with layout I8, one
+/* Resident mode for small lattices (default on).
+ *
+ * Bit-sliced layout (IANUS_LAYOUT_BITS64, models of Eq. (2) without fields):
+ * under the automatic kernel variant (0), a lattice whose state per (group,
+ * temperature slot) fits in 220 KiB of shared memory -- R spin words and dim
+ * coupling words per site and R x 33 x 8 threshold-plane words, 8 (R + dim)
+ * L^dim + 2112 R bytes: 3D L <= 17 with two replicas and L <= 19 with one,
+ * 2D L <= 83 and L <= 96 -- can run every block of two or more sweeps
+ * between measurements in launches of up to 4096 sweeps, one thread block
+ * per (group, temperature slot) holding that state, the colours separated
+ * by block barriers (Sec. 3.1); measurements run between the launches as
+ * usual.  A pool lattice (ianus_segment_load) sweeps the same way, one
+ * block per group, when N + dim N + 264 words fit; each block advances its
+ * jobs' sweep counters itself.  Same results, bit for bit, as the
+ * launch-per-colour path.  enable = 1 (default) takes it where it is the
+ * faster sweep: at most 512 word updates per block and sweep (R N), or
+ * 1024 with at least 32 blocks (3D L = 8; 2D L <= 22 with one replica);
+ * enable = 2 or 3 takes it wherever it fits; enable = 0: off.
+ *
+ * Plain layout: with layout I8, one
  * temperature, (1 + dim) L^dim bytes <= 200 KiB, and either one replica or no
  * measurements, each configuration is held in shared memory by one launch
  * that runs all requested sweeps (the two colours separated by barriers,

@@ -419,10 +419,12 @@ class Lattice:
         _check(self._lib.ianus_set_graphs(self._h, int(bool(enable))), "ianus_set_graphs")
 
     def set_resident(self, enable):
-        """Shared-memory-resident sweeps for small plain lattices: True / 1
-        (default: a block cluster per configuration when there are few), 2
-        (one block per configuration always), 3 (a cluster per configuration
-        whenever one can be formed), False / 0 (off)."""
+        """Shared-memory-resident sweeps for small lattices.  Plain layout:
+        True / 1 (default: a block cluster per configuration when there are
+        few), 2 (one block per configuration always), 3 (a cluster per
+        configuration whenever one can be formed), False / 0 (off).
+        Bit-sliced layout (automatic variant) and pools: any nonzero value
+        on, 0 off."""
         _check(self._lib.ianus_set_resident(self._h, int(enable)), "ianus_set_resident")
 
     def synchronize(self):

@@ -439,7 +439,23 @@ int build_graph(Lattice* lat, int inv, uint32_t B, cudaGraphExec_t* out) {
 
 // Runs n sweeps (no measurement inside) through cached graphs of blocks of
 // up to 64 sweeps; short runs (< 4 sweeps) launch eagerly.
+// Sweeps per launch of the resident bit-sliced sweep: long enough that the
+// launch costs nothing, short enough that no launch runs for long.
+constexpr uint32_t kResidentBlock = 4096;
+
 int sweeps_graphed(Lattice* lat, int inv, uint64_t n) {
+  // small bit-sliced lattices under the automatic variant: resident sweeps,
+  // many per launch, the lattice in shared memory
+  if (n >= 2 && lat->use_resident && lat->variant == 0 && resident_bits_fits(*lat)) {
+    while (n > 0) {
+      const uint32_t B = (uint32_t)std::min<uint64_t>(n, kResidentBlock);
+      CK(launch_resident_bits(*lat, inv, lat->sweeps, B));
+      lat->sweeps += B;
+      lat->t_dev_valid = false;
+      n -= B;
+    }
+    return IANUS_OK;
+  }
   // the persistent one-temperature sweep: all n sweeps in launches of up to
   // 2^20 sweeps, no graphs needed (falls through when it cannot run)
   if (lat->layout == IANUS_LAYOUT_BITS64 && persistent_variant(*lat)) {
@@ -1023,9 +1039,12 @@ ianus_status ianus_sweep_segments(ianus_lattice* h, uint64_t nsweeps) {
   lat->mut += 1;  // the state changes other than by sweeps
   if (!lat->segs) return IANUS_EUNSUPPORTED;
   uint64_t left = nsweeps;
+  const bool resident = nsweeps >= 2 && lat->use_resident && resident_fused_fits(*lat);
   while (left > 0) {
-    const uint32_t B = (uint32_t)std::min<uint64_t>(left, 64);
-    if (B < 4 || !lat->use_graphs || !lat->graphs) {
+    const uint32_t B = (uint32_t)std::min<uint64_t>(left, resident ? kResidentBlock : 64);
+    if (resident) {
+      CK(launch_resident_fused(*lat, B));
+    } else if (B < 4 || !lat->use_graphs || !lat->graphs) {
       for (uint32_t k = 0; k < B; ++k) {
         int st = fused_sweep_once(lat);
         if (st) return (ianus_status)st;

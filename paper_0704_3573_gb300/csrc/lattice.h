@@ -235,6 +235,17 @@ cudaError_t launch_measure_i8(Lattice& lat, int want_q);
 // (1 + D) N bytes <= kResidentSmemMax.
 constexpr size_t kResidentSmemMax = 200 * 1024;
 bool resident_i8_fits(const Lattice& lat);
+// Resident bit-sliced sweeps (k_resident_bits.cu): one block per (group,
+// temperature slot) -- or per group of a fused pool -- holding its spins,
+// couplings and threshold planes in shared memory for many sweeps.  The
+// *_fits tests also ask that the resident sweep be the faster one, unless
+// resident_mode >= 2 forces it wherever it fits.
+bool resident_bits_fits(const Lattice& lat);
+bool resident_fused_fits(const Lattice& lat);
+// nsweeps sweeps t0, t0 + 1, ... of every configuration (no measurements).
+cudaError_t launch_resident_bits(Lattice& lat, int inv, uint64_t t0, uint32_t nsweeps);
+// nsweeps sweeps of a pool, each advancing its running segments by one.
+cudaError_t launch_resident_fused(Lattice& lat, uint32_t nsweeps);
 cudaError_t launch_resident_i8(Lattice& lat, int inv, uint32_t nsweeps, uint32_t measure_every);
 cudaError_t launch_get_spins_i8(Lattice& lat, int8_t* dev_out);       // [S][slots][N]
 cudaError_t launch_set_spins_i8(Lattice& lat, const int8_t* dev_in);
