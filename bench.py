@@ -66,6 +66,11 @@ TRAFFIC_SOURCE_HASH = "0b06d535be286e49"
 POTTS_TRAFFIC = {"l1_global_load_bytes": 179127744, "l2_bytes": 73770400, "dram_bytes": 21049344,
                  "l1_hit_rate_pct": 78.5}
 POTTS_SOURCE_HASH = "ab9e8badae2a5729"
+# DRAM traffic of one colour launch of the plain-layout sweep
+# (k_sweep_i8_sliced) on the bench workload, from one ncu capture, valid
+# while its sources are unchanged.
+PLAIN_TRAFFIC = {"dram_read_bytes": 338100736, "dram_write_bytes": 96539392}
+PLAIN_SOURCE_HASH = "18811308de067f11"
 # The kernel variant and launch shape the bench runs by default: the
 # lane-queue kernel in its one-wave launch (the automatic choice for one
 # temperature), fixed so that the profile above describes the timed kernel.
@@ -374,22 +379,37 @@ def run_gpu(args, ws, rank, local):
         # roofline of the plain form: the smaller of two bounds.  HBM: per
         # update the site's byte read and written and its share of the other
         # colour's bytes (3 B) and the 6 coupling bytes each configuration
-        # streams (9 B, the couplings larger than L2).  Issue: per update 6
-        # bond tests (2 ops each), the Philox blocks of the site shared by the
-        # 64 samples of its group (3.92 pairs x 37 ops / 64), about 8/3 plane
-        # compares and the flip (lop3 + mad.wide ops, one shared issue slot)
+        # streams (9 B, the couplings larger than L2).  Issue: the kernel
+        # updates 64-lane words built in shared memory, so per update the
+        # per-lane-plane word update of the bit-sliced form / 64 (e-words 12,
+        # adder tree 16, "always" and undecided masks 16, per plane the
+        # threshold multiplexers 6 + compare 4, per pair Philox 21 + merge 2,
+        # 3.92 pairs; 20 mad.wide per Philox block) plus the layout's own
+        # work: the sign packing (9 ops per 32 bytes and lane) and the 32 x 32
+        # bit transposes (5 ops per stage, 5 stages) of the bytes read and
+        # written, about 13.5 B per update
         hbm = MEASURED.get("hbm_gbs")
         b_upd = 9.0
-        ops_upd = 12 + expected_plane_pairs() * 37 / 64 + 8 / 3 + 1
+        npp = expected_plane_pairs()
+        ops_upd = (44 + npp * (2 * 10 + 23) + npp * 20) / 64 + 13.5 * (9 + 25) / 32
         pk = _issue_peak()
         bounds = {"hbm": hbm / b_upd if hbm else None, "alu": pk * 1e3 / ops_upd if pk else None}
         binding = min((v, k) for k, v in bounds.items() if v)[1] if any(bounds.values()) else None
+        traffic = None
+        if kernel_source_hash(("common.cuh", "sweep_planes.cuh", "k_plain.cu")) == PLAIN_SOURCE_HASH:
+            upd_pass = S * R * L ** 3 // 2
+            traffic = {"dram_bytes_per_update": (PLAIN_TRAFFIC["dram_read_bytes"] + PLAIN_TRAFFIC["dram_write_bytes"])
+                       / upd_pass, **PLAIN_TRAFFIC,
+                       "what": "ncu, one colour launch; below the 9 B algorithmic figure because the two replicas "
+                               "of a tile read their shared couplings in the same wave"}
         plain = {"value": pv, "unit": UNIT, "layout": "i8 (one byte per spin)", "sweeps": nps,
-                 "kernel": "k_sweep_i8_words (4-byte words, planes shared by the 64-sample group)",
+                 "kernel": "k_sweep_i8_sliced (tiles of the 64-sample group turned into 64-lane words in shared "
+                           "memory by warp bit transposes, updated bit-sliced, written back as bytes)",
                  "speedup_bitsliced_over_plain": value / ws / pv,
                  "roofline": {"bound": binding, "bytes_per_update": b_upd, "ops_per_update": ops_upd,
                               "bound_updates_per_ns": bounds,
                               "frac": pv / bounds[binding] if binding else None,
+                              "traffic": traffic,
                               "peaks": {"hbm_gbs": hbm, "issue_tops": pk}}}
         del pl
 

@@ -455,13 +455,18 @@ ianus_status ianus_synchronize(ianus_lattice* lat);
  * 256 words per block (ianus_set_block_words), the fastest shape before the
  * lane-queue kernel.  The
  * Python autotuner (tune.py) times the shapes on the caller's lattice.
- * The plain one-byte-per-spin layout (IANUS_LAYOUT_I8) has three sweep
- * kernels: variant 1 runs one thread per update, each drawing its own
- * random planes; every other value runs a kernel in which a block draws the
+ * The plain one-byte-per-spin layout (IANUS_LAYOUT_I8) has four sweep
+ * kernels.  Variant 0 (automatic), with L = 32, 64 or 128: a block reads a
+ * tile of a 64-sample group as bytes, turns it into 64-lane words in shared
+ * memory (warp bit transposes of the sign bits), runs the bit-sliced update
+ * there and writes the tile back as bytes (the random number of sample s
+ * is bit s mod 64 of its group's plane stream, so the trajectory is the
+ * same).  Variant 1: one thread per update, each drawing its own random
+ * planes.  Other values, and variant 0 at other sides: a block draws the
  * planes of a site once for the site's 64-sample group and each update
- * compares an 8-bit prefix of its random number from shared memory: the
- * word kernel (four spins of one sample per 32-bit load) when L is a
- * multiple of 4, else the tiled kernel (one byte per thread).
+ * compares an 8-bit prefix of its random number from shared memory, in
+ * the word kernel (four spins of one sample per 32-bit load) when L is a
+ * multiple of 4, else in the tiled kernel (one byte per thread).
  * With several temperatures every variant but 1 uses the per-lane kernel
  * compiled for the geometry.  If run-time compilation is unavailable, the
  * precompiled kernel runs.  EINVAL for other values. */

@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include "lattice.h"
+#include "sweep_planes.cuh"
 
 namespace ianus {
 
@@ -1146,6 +1147,45 @@ __global__ void __launch_bounds__(256) k_measure_i8(const int8_t* __restrict__ s
     const int8_t* sp = spins + (size_t)lat * N;
     const int8_t* Jp = J + (size_t)s * D * N;
     long long e = 0, m = 0;
+    if ((L & 15) == 0) {
+      // 16 sites of a row per step: the sign bit of a +-1 byte is bit 7, a
+      // bond (i, j) is unsatisfied iff s_i J_ij s_j = -1, i.e. the three
+      // sign bits XOR to 1, so E = 2 U - D N and M = N - 2 n_-, with U and
+      // n_- counted by popcounts of sign-bit masks
+      const uint32_t qrow = (uint32_t)L / 16u, nq = N / 16u;
+      uint32_t un = 0, ng = 0;
+      for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+        const uint32_t row = q / qrow, k = q - row * qrow;
+        const uint32_t y = row % (uint32_t)L, z = row / (uint32_t)L;
+        const uint32_t base = row * (uint32_t)L + 16u * k;
+        const uint4 w = *reinterpret_cast<const uint4*>(sp + base);
+        const uint32_t nx = *reinterpret_cast<const uint32_t*>(sp + row * (uint32_t)L + (k + 1u == qrow ? 0u : 16u * (k + 1u)));
+        const uint32_t yb = ((D == 3 ? z * (uint32_t)L : 0u) + (y + 1u == (uint32_t)L ? 0u : y + 1u)) * (uint32_t)L + 16u * k;
+        const uint4 wy = *reinterpret_cast<const uint4*>(sp + yb);
+        const uint4 jx = __ldg(reinterpret_cast<const uint4*>(Jp + base));
+        const uint4 jy = __ldg(reinterpret_cast<const uint4*>(Jp + N + base));
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w}, wn[5] = {w.x, w.y, w.z, w.w, nx};
+        const uint32_t ys[4] = {wy.x, wy.y, wy.z, wy.w}, jxs[4] = {jx.x, jx.y, jx.z, jx.w}, jys[4] = {jy.x, jy.y, jy.z, jy.w};
+        uint32_t zs[4] = {0u, 0u, 0u, 0u}, jzs[4] = {0u, 0u, 0u, 0u};
+        if (D == 3) {
+          const uint32_t zb = ((z + 1u == (uint32_t)L ? 0u : z + 1u) * (uint32_t)L + y) * (uint32_t)L + 16u * k;
+          const uint4 wz = *reinterpret_cast<const uint4*>(sp + zb);
+          const uint4 jz = __ldg(reinterpret_cast<const uint4*>(Jp + 2u * N + base));
+          zs[0] = wz.x; zs[1] = wz.y; zs[2] = wz.z; zs[3] = wz.w;
+          jzs[0] = jz.x; jzs[1] = jz.y; jzs[2] = jz.z; jzs[3] = jz.w;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t right = __funnelshift_r(wn[t], wn[t + 1], 8);  // byte j: the site at x + 1
+          un += __popc((ws[t] ^ right ^ jxs[t]) & 0x80808080u);
+          un += __popc((ws[t] ^ ys[t] ^ jys[t]) & 0x80808080u);
+          if (D == 3) un += __popc((ws[t] ^ zs[t] ^ jzs[t]) & 0x80808080u);
+          ng += __popc(ws[t] & 0x80808080u);
+        }
+      }
+      e = 2ll * un;  // - D N added once per configuration below
+      m = -2ll * ng;
+    } else
     for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) {
       const uint32_t x = i % (uint32_t)L, y = (i / (uint32_t)L) % (uint32_t)L;
       const uint32_t z = D == 3 ? i / ((uint32_t)L * (uint32_t)L) : 0u;
@@ -1176,6 +1216,10 @@ __global__ void __launch_bounds__(256) k_measure_i8(const int8_t* __restrict__ s
         E += red[0][w];
         M += red[1][w];
       }
+      if ((L & 15) == 0) {
+        E -= (long long)D * N;
+        M += (long long)N;
+      }
       int64_t* a = acc + ((size_t)s * slots + sigma) * kAccStride;
       a[0] = E;
       a[1] = M;
@@ -1201,6 +1245,14 @@ __global__ void __launch_bounds__(256) k_overlap_i8(const int8_t* __restrict__ s
     if (occ) {  // Q = sum_i x_i s_i^0 s_i^1
       const int8_t* xo = occ + (size_t)s * N;
       for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += xo[i] * a0[i] * a1[i];
+    } else if ((N & 15u) == 0u) {  // 16 sites per step: s0 s1 = -1 iff the sign bits differ
+      uint32_t d = 0;
+      for (uint32_t i = 16u * threadIdx.x; i < N; i += 16u * blockDim.x) {
+        const uint4 u = *reinterpret_cast<const uint4*>(a0 + i), v = *reinterpret_cast<const uint4*>(a1 + i);
+        d += __popc((u.x ^ v.x) & 0x80808080u) + __popc((u.y ^ v.y) & 0x80808080u) +
+             __popc((u.z ^ v.z) & 0x80808080u) + __popc((u.w ^ v.w) & 0x80808080u);
+      }
+      q = -2ll * d;  // N added once below
     } else {
       for (uint32_t i = threadIdx.x; i < N; i += blockDim.x) q += a0[i] * a1[i];
     }
@@ -1210,6 +1262,7 @@ __global__ void __launch_bounds__(256) k_overlap_i8(const int8_t* __restrict__ s
     if (threadIdx.x == 0) {
       long long Q = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) Q += red[w];
+      if (!occ && (N & 15u) == 0u) Q += (long long)N;
       acc[((size_t)s * slots + (size_t)k * R) * kAccStride + 6] = Q;
     }
     __syncthreads();
@@ -1234,6 +1287,364 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
   if (g > cap) g = cap;
   if (g == 0) g = 1;
   return (unsigned)g;
+}
+
+// ---- the plain layout swept bit-sliced in shared memory ----
+//
+// The random number of sample s at (site, sweep) is bit (s mod 64) of the
+// plane stream drawn for the site and its group of 64 samples: the stream
+// the bit-sliced layout draws once per 64-lane word.  So a block takes a
+// tile of sites of one group and slot, reads the tile and its halo for the
+// group's 64 samples as full 32-byte sectors, turns them into 64-lane words
+// in shared memory (bit l = sign of sample 64 g + l), runs the bit-sliced
+// update of Sec. 3.2 on those words (one Philox block and one compare chain
+// per 64 updates), and writes the tile's rows back as bytes.  The spins stay
+// one byte each in global memory before and after every colour pass.
+//
+// Tile: kSlZ planes (3D) x kSlY rows x the L sites of a row (L a multiple
+// of 32).  Shared memory, 64-bit words; a row is stored by x parity (even x
+// at x/2, odd x at L/2 + x/2), so the active sites of a warp are adjacent:
+//   box [kSlZ + 2][kSlY + 2][L]  spins: planes z0-1..z0+kSlZ, rows y0-1..y0+kSlY
+//   jx  [kSlZ][kSlY][L]          x+ couplings of the tile's sites
+//   jy  [kSlZ][kSlY + 1][L]      y+ couplings of rows y0-1..y0+kSlY-1
+//   jz  [kSlZ + 1][kSlY][L]      z+ couplings of planes z0-1..z0+kSlZ-1
+//   tp  [kPlanes][kMaxClasses]   threshold planes of the group's 64 lanes
+// In 2D the box is one plane of kSlY + 2 rows and there is no jz.
+constexpr int kSlThreads = 256;
+constexpr uint32_t kSlZ = 2, kSlY = 8;
+
+// Rows a block reads: the spin box without its four corner rows (no site of
+// the tile has them as neighbours), then the coupling rows.
+template <int D>
+__host__ __device__ constexpr uint32_t sl_box_rows() {
+  return D == 3 ? 2 * kSlY + kSlZ * (kSlY + 2) : kSlY + 2;
+}
+template <int D>
+__host__ __device__ constexpr uint32_t sl_rows(uint32_t) {
+  return sl_box_rows<D>() + (D == 3 ? kSlZ * kSlY + kSlZ * (kSlY + 1) + (kSlZ + 1) * kSlY : kSlY + (kSlY + 1));
+}
+// Words of the tile's shared-memory arrays (the box keeps room for its
+// corner rows, unused).
+template <int D>
+__host__ __device__ constexpr uint32_t sl_smem_rows() {
+  return D == 3 ? (kSlZ + 2) * (kSlY + 2) + kSlZ * kSlY + kSlZ * (kSlY + 1) + (kSlZ + 1) * kSlY
+                : (kSlY + 2) + kSlY + (kSlY + 1);
+}
+
+__device__ __forceinline__ uint32_t sl_index(uint32_t x, uint32_t hL) { return (x & 1u) * hL + (x >> 1); }
+
+// Site (within a 32-site chunk) whose bit sits at position q of a packed
+// mask: site 4k + b at bit 8b + 7 - k (sl_pack).
+__device__ __forceinline__ uint32_t sl_site_of_bit(uint32_t q) { return 4u * (7u - (q & 7u)) + (q >> 3); }
+
+// Signs of 32 consecutive +-1 bytes (words k = 0..7 of a and b, byte b of
+// word k = site 4k + b) as one 32-bit mask.  Every bit of a +-1 byte but
+// bit 0 is its sign, so word k gives bit 7 - k of each of its bytes (word
+// 7 gives bit 1, moved down to bit 0): site 4k + b lands at bit 8b + 7 - k.
+__device__ __forceinline__ uint32_t sl_pack(const uint4& a, const uint4& b) {
+  uint32_t m = a.x & 0x80808080u;
+  m |= a.y & 0x40404040u;
+  m |= a.z & 0x20202020u;
+  m |= a.w & 0x10101010u;
+  m |= b.x & 0x08080808u;
+  m |= b.y & 0x04040404u;
+  m |= b.z & 0x02020202u;
+  m |= (b.w >> 1) & 0x01010101u;
+  return m;
+}
+
+// Signs of 16 consecutive +-1 bytes (words k = 0..3 of v, byte b of word k
+// = site 4k + b): site 4k + b at bit 8b + 7 - k (bits 4..7 of each byte).
+__device__ __forceinline__ uint32_t sl_pack16(const uint4& v) {
+  return (v.x & 0x80808080u) | (v.y & 0x40404040u) | (v.z & 0x20202020u) | (v.w & 0x10101010u);
+}
+
+// Two sl_pack16 masks of sites 0..15 (lo) and 16..31 (hi) of a chunk as one
+// 32-bit mask: byte b holds lo's bits in its low nibble, hi's in its high
+// nibble, so bit j is site 16 ((j >> 2) & 1) + 4 (3 - (j & 3)) + (j >> 3).
+__device__ __forceinline__ uint32_t sl_merge16(uint32_t lo, uint32_t hi) {
+  return ((lo >> 4) & 0x0F0F0F0Fu) | (hi & 0xF0F0F0F0u);
+}
+
+__device__ __forceinline__ uint32_t sl_site_of_bit16(uint32_t j) {
+  return 16u * ((j >> 2) & 1u) + 4u * (3u - (j & 3u)) + (j >> 3);
+}
+
+// Word k of the 32 bytes a mask packs: sign of byte b from bit 8b + 7 - k,
+// byte = +1 (0x01) or -1 (0xFF) = 1 + 0xFE sign.
+__device__ __forceinline__ uint32_t sl_unpack_word(uint32_t m, int k) {
+  return ((m >> (7 - k)) & 0x01010101u) * 0xFEu + 0x01010101u;
+}
+
+// 32 x 32 bit transpose across a warp: lane i holds row i on entry (bit j
+// = element (i, j)) and column i on return (bit j = element (j, i)).  Stage
+// s swaps bit s of the row index with bit s of the column index: the lane
+// with bit s of its index clear keeps its bits j with bit s clear and takes
+// the partner's bits with bit s clear shifted up by s; the other lane keeps
+// the bits with bit s set and takes the partner's shifted down by s.  A
+// rotation stands in for either shift: the bits it wraps around land where
+// the keep-mask discards them.  The per-lane rotations and keep-masks of the
+// five stages are constants.
+struct SlTranspose {
+  uint32_t rot[5], keep[5];
+  __device__ __forceinline__ SlTranspose() {
+    const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t s = 16u >> i;
+      const uint32_t m = i == 0 ? 0x0000FFFFu : i == 1 ? 0x00FF00FFu : i == 2 ? 0x0F0F0F0Fu : i == 3 ? 0x33333333u
+                                                                                                      : 0x55555555u;
+      const bool up = (lane & s) != 0u;
+      rot[i] = up ? 32u - s : s;  // rotate left: down by s, or up by s
+      keep[i] = up ? ~m : m;
+    }
+  }
+  __device__ __forceinline__ uint32_t operator()(uint32_t x) const {
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const uint32_t y = __shfl_xor_sync(0xffffffffu, x, 16u >> i);
+      const uint32_t yr = __funnelshift_l(y, y, rot[i]);
+      x = (x & keep[i]) | (yr & ~keep[i]);
+    }
+    return x;
+  }
+};
+
+template <int D, int ALGO, int C>
+__global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Params p) {
+  extern __shared__ uint64_t sl[];
+  constexpr uint32_t TZ = D == 3 ? kSlZ : 1u, BZ = D == 3 ? kSlZ + 2 : 1u, BY = kSlY + 2, ZO = D == 3 ? 1u : 0u;
+  const uint32_t L = (uint32_t)p.L, hL = L >> 1, N = p.N, S = (uint32_t)p.S;
+  uint64_t* box = sl;
+  uint64_t* jx = box + BZ * BY * L;
+  uint64_t* jy = jx + TZ * kSlY * L;
+  uint64_t* jz = jy + TZ * (kSlY + 1) * L;
+  uint64_t* tp = jz + (D == 3 ? (TZ + 1) * kSlY * L : 0u);
+  // grid (slots, tiles, groups): the slots of one tile and group run side by
+  // side, so the couplings they share are read from DRAM once
+  const uint32_t tiles_y = L / kSlY;
+  const uint32_t y0 = (blockIdx.y % tiles_y) * kSlY, z0 = (blockIdx.y / tiles_y) * TZ;
+  const uint32_t g = blockIdx.z;
+  const int sigma = (int)blockIdx.x;
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  const int tslot = sigma / p.R, a = sigma - tslot * p.R;
+  auto wrap = [L](uint32_t v) { return v == 0xFFFFFFFFu ? L - 1u : (v == L ? 0u : v); };  // v in [-1, L]
+  // threshold planes of the 64 lanes: warp u builds class u (plane q = bit
+  // 31 - q of each lane's threshold, plane 32 = threshold 2^32)
+  if (warp <= 2u * D) {
+    const uint32_t u = warp;
+    uint64_t T[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t s = 64u * g + 32u * (uint32_t)h + lane;
+      const int k = s < S ? p.temp_of[((size_t)s * p.R + a) * p.K + tslot] : tslot;
+      T[h] = p.thr[(size_t)k * kMaxClasses + u];
+    }
+    const uint64_t always = (uint64_t)__ballot_sync(0xffffffffu, T[0] >= kTwo32) |
+                            ((uint64_t)__ballot_sync(0xffffffffu, T[1] >= kTwo32) << 32);
+    uint64_t mine = 0;
+#pragma unroll 4
+    for (uint32_t q = 0; q < 32u; ++q) {
+      const uint32_t lo = __ballot_sync(0xffffffffu, T[0] < kTwo32 && ((T[0] >> (31u - q)) & 1ull));
+      const uint32_t hi = __ballot_sync(0xffffffffu, T[1] < kTwo32 && ((T[1] >> (31u - q)) & 1ull));
+      if (lane == q) mine = (uint64_t)lo | ((uint64_t)hi << 32);
+    }
+    tp[lane * kMaxClasses + u] = mine;
+    if (lane == 0) tp[32 * kMaxClasses + u] = always;
+  }
+  // the box and the couplings, one row (L sites) of the group's 64 samples
+  // per warp task.  A sample's row is read as P = L/16 pieces of 16 bytes
+  // by P consecutive lanes, 32/P samples per load instruction, so a load
+  // touches 32/P lines instead of 32; each lane packs its piece's 16 signs
+  // into the warp's staging row [sample][piece], and the row's words are
+  // then formed chunk by chunk: lane l reads the 32-site mask of sample
+  // 32 h + l and the warp transposes.  Warp w takes rows w, w + 8, ... of
+  // the block's row list.
+  constexpr int P = 2 * C;          // pieces of 16 sites per row
+  constexpr int SPI = 32 / P;       // samples per load instruction
+  constexpr int NI = 64 / SPI;      // load instructions per row
+  constexpr int SW = C;             // staging words (32-site masks) per sample
+  const SlTranspose tr;
+  const uint32_t n_box = sl_box_rows<D>(), n_jx = TZ * kSlY, n_jy = TZ * (kSlY + 1);
+  const uint32_t n_rows = sl_rows<D>(L);
+  const uint32_t xq = sl_site_of_bit16(lane);
+  const uint32_t dq = sl_index(xq, hL);  // chunk c adds 16 c: each 32-site chunk is 16 words of each parity
+  constexpr uint32_t kWarps = kSlThreads / 32;
+  uint32_t* stage = reinterpret_cast<uint32_t*>(tp + kPlanes * kMaxClasses) + warp * (64 * SW);
+  const uint32_t grp = lane / P, piece = lane - grp * P;
+#pragma unroll 1
+  for (uint32_t r = warp; r < n_rows; r += kWarps) {
+    uint32_t z, y, d = 0;
+    bool spin = false;
+    uint64_t* dst;
+    if (r < n_box) {
+      // 3D: rows 1..kSlY of plane 0, all rows of planes 1..kSlZ, rows
+      // 1..kSlY of plane kSlZ + 1 (the corner rows are not read)
+      uint32_t zi = 0u, yi = r;
+      if (D == 3) {
+        if (r < kSlY) {
+          yi = r + 1u;
+        } else if (r < kSlY + kSlZ * BY) {
+          zi = 1u + (r - kSlY) / BY;
+          yi = r - kSlY - (zi - 1u) * BY;
+        } else {
+          zi = kSlZ + 1u;
+          yi = r - kSlY - kSlZ * BY + 1u;
+        }
+      }
+      z = D == 3 ? wrap(z0 + zi - 1u) : 0u;
+      y = wrap(y0 + yi - 1u);
+      spin = true;
+      dst = box + (zi * BY + yi) * L;
+    } else if (r < n_box + n_jx) {
+      const uint32_t rr = r - n_box, zi = rr / kSlY, yi = rr - zi * kSlY;
+      z = z0 + zi;
+      y = y0 + yi;
+      dst = jx + rr * L;
+    } else if (r < n_box + n_jx + n_jy) {
+      const uint32_t rr = r - n_box - n_jx, zi = rr / (kSlY + 1), yi = rr - zi * (kSlY + 1);
+      z = z0 + zi;
+      y = wrap(y0 + yi - 1u);
+      d = 1;
+      dst = jy + rr * L;
+    } else {
+      const uint32_t rr = r - n_box - n_jx - n_jy, zi = rr / kSlY, yi = rr - zi * kSlY;
+      z = wrap(z0 + zi - 1u);
+      y = y0 + yi;
+      d = 2;
+      dst = jz + rr * L;
+    }
+    // lane's sample for instruction i: 64 g + SPI i + grp; consecutive
+    // samples are N bytes apart (spins) or D N (couplings)
+    const size_t stride = spin ? (size_t)N : (size_t)D * N;
+    const int8_t* base = (spin ? p.spins + ((size_t)sigma * S + 64u * g) * N : p.J + (size_t)64u * g * D * N + (size_t)d * N) +
+                         ((size_t)z * L + y) * L + 16u * piece + (size_t)grp * stride;
+    uint4 v[NI];
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      v[i] = make_uint4(0u, 0u, 0u, 0u);
+      if (64u * g + (uint32_t)(SPI * i) + grp < S) v[i] = *reinterpret_cast<const uint4*>(base + (size_t)(SPI * i) * stride);
+    }
+    // pieces 2c and 2c + 1 of a sample sit in neighbouring lanes: the even
+    // lane merges them into the chunk's 32-site mask and stages it
+#pragma unroll
+    for (int i = 0; i < NI; ++i) {
+      const uint32_t mine = sl_pack16(v[i]);
+      const uint32_t other = __shfl_xor_sync(0xffffffffu, mine, 1);
+      if ((piece & 1u) == 0u) stage[((uint32_t)(SPI * i) + grp) * SW + (piece >> 1)] = sl_merge16(mine, other);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const uint32_t lo = tr(stage[lane * SW + c]);
+      const uint32_t hi = tr(stage[(32u + lane) * SW + c]);
+      dst[dq + 16u * c] = (uint64_t)lo | ((uint64_t)hi << 32);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // the colour pass on the tile's words
+  BitsParams bp;
+  bp.keys = p.keys;
+  const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
+  const uint32_t n_act = TZ * kSlY * hL;
+#pragma unroll 1
+  for (uint32_t w = threadIdx.x; w < n_act; w += kSlThreads) {
+    const uint32_t k = w % hL, rest = w / hL, yi = rest % kSlY, zi = rest / kSlY;
+    const uint32_t y = y0 + yi, z = D == 3 ? z0 + zi : 0u;
+    const uint32_t par = (uint32_t)(p.colour ^ (int)(y + z)) & 1u;
+    const uint32_t x = 2u * k + par;
+    const uint32_t is = par * hL + k;                                        // the site (parity par)
+    const uint32_t ip = par ? (k + 1u == hL ? 0u : k + 1u) : hL + k;          // x + 1
+    const uint32_t im = par ? k : hL + (k == 0u ? hL - 1u : k - 1u);          // x - 1
+    uint64_t* row = box + ((zi + ZO) * BY + yi + 1u) * L;  // the site's row; rows y +- 1 and planes z +- 1 around it
+    const uint64_t b = row[is];
+    uint64_t e[2 * D];
+    e[0] = b ^ row[ip] ^ jx[(zi * kSlY + yi) * L + is];
+    e[1] = b ^ row[im] ^ jx[(zi * kSlY + yi) * L + im];
+    e[2] = b ^ (row + L)[is] ^ jy[(zi * (kSlY + 1) + yi + 1u) * L + is];
+    e[3] = b ^ (row - L)[is] ^ jy[(zi * (kSlY + 1) + yi) * L + is];
+    if (D == 3) {
+      e[4] = b ^ (row + BY * L)[is] ^ jz[((zi + 1u) * kSlY + yi) * L + is];
+      e[5] = b ^ (row - BY * L)[is] ^ jz[(zi * kSlY + yi) * L + is];
+    }
+    uint64_t u0, u1, u2;
+    count_unsat<D>(e, u0, u1, u2);
+    planes::LazyWord lw = planes::bits_word_start<D, ALGO>(tp, u0, u1, u2);
+    planes::bits_plane_pairs<D, ALGO>(lw, tp, bp, tk, x + L * (y + L * z), c2, 0u, 16u);
+    const uint64_t flip = ALGO == 0 ? lw.lt : ~lw.lt;
+    if (flip) row[is] = b ^ flip;
+  }
+  __syncthreads();
+  // the tile's rows back to global memory, a row of the group's 64 samples
+  // per warp task: lane q takes the word of the site whose sign lands at
+  // bit q of the 32-byte packing (sl_pack), so after the transpose lane l
+  // holds sample 32 h + l's 32 signs in the order sl_unpack_word expects
+  const uint32_t dq3 = sl_index(sl_site_of_bit(lane), hL);
+#pragma unroll 1
+  for (uint32_t r = warp; r < TZ * kSlY; r += kWarps) {
+    const uint32_t zi = r / kSlY, yi = r - zi * kSlY;
+    const uint32_t y = y0 + yi, z = D == 3 ? z0 + zi : 0u;
+    const uint64_t* src = box + ((zi + ZO) * BY + yi + 1u) * L + dq3;
+    const size_t row_off = ((size_t)z * L + y) * L;
+    const uint32_t s_0 = 64u * g + lane, s_1 = s_0 + 32u;
+    int8_t* d0 = p.spins + ((size_t)sigma * S + s_0) * N + row_off;
+    int8_t* d1 = p.spins + ((size_t)sigma * S + s_1) * N + row_off;
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
+      const uint64_t wv = src[16 * c];
+      const uint32_t m0 = tr((uint32_t)wv), m1 = tr((uint32_t)(wv >> 32));
+      if (s_0 < S) {
+        *reinterpret_cast<uint4*>(d0 + 32 * c) =
+            make_uint4(sl_unpack_word(m0, 0), sl_unpack_word(m0, 1), sl_unpack_word(m0, 2), sl_unpack_word(m0, 3));
+        *reinterpret_cast<uint4*>(d0 + 32 * c + 16) =
+            make_uint4(sl_unpack_word(m0, 4), sl_unpack_word(m0, 5), sl_unpack_word(m0, 6), sl_unpack_word(m0, 7));
+      }
+      if (s_1 < S) {
+        *reinterpret_cast<uint4*>(d1 + 32 * c) =
+            make_uint4(sl_unpack_word(m1, 0), sl_unpack_word(m1, 1), sl_unpack_word(m1, 2), sl_unpack_word(m1, 3));
+        *reinterpret_cast<uint4*>(d1 + 32 * c + 16) =
+            make_uint4(sl_unpack_word(m1, 4), sl_unpack_word(m1, 5), sl_unpack_word(m1, 6), sl_unpack_word(m1, 7));
+      }
+    }
+  }
+}
+
+size_t sl_smem_bytes(int D, uint32_t L) {
+  const uint32_t rows = D == 3 ? sl_smem_rows<3>() : sl_smem_rows<2>();
+  const size_t stage = (size_t)(kSlThreads / 32) * 64 * (L / 32) * sizeof(uint32_t);  // per warp [64][L/32] masks
+  return ((size_t)rows * L + (size_t)kPlanes * kMaxClasses) * sizeof(uint64_t) + stage;
+}
+
+// The shared-memory bit-sliced sweep takes rows of 1, 2 or 4 whole 32-site
+// chunks, read by 2, 4 or 8 lanes per sample: L = 32, 64 or 128 (3D tiles
+// of 98 L words, 2D of 27 L, plus 1 KiB L/16 of staging).
+bool i8_sliced_fits(const Lattice& lat) {
+  return (lat.D == 2 || lat.D == 3) && (lat.L == 32 || lat.L == 64 || lat.L == 128) && !lat.field &&
+         lat.rng != IANUS_RNG_WHEEL;
+}
+
+template <int D, int ALGO, int C>
+cudaError_t launch_sliced_c(Lattice& lat, const I8Params& p, dim3 grid, size_t smem) {
+  static bool ok = false;
+  if (!ok) {
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_i8_sliced<D, ALGO, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    ok = true;
+  }
+  k_sweep_i8_sliced<D, ALGO, C><<<grid, kSlThreads, smem, lat.stream>>>(p);
+  return cudaGetLastError();
+}
+
+template <int D, int ALGO>
+cudaError_t launch_sliced(Lattice& lat, const I8Params& p, dim3 grid, size_t smem) {
+  switch (lat.L / 32) {
+    case 1: return launch_sliced_c<D, ALGO, 1>(lat, p, grid, smem);
+    case 2: return launch_sliced_c<D, ALGO, 2>(lat, p, grid, smem);
+    default: return launch_sliced_c<D, ALGO, 4>(lat, p, grid, smem);
+  }
 }
 
 }  // namespace
@@ -1283,6 +1694,17 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
     else
       k_sweep_field_i8<2><<<grid, 256, 0, lat.stream>>>(fp);
     return cudaGetLastError();
+  }
+  if (lat.variant == 0 && i8_sliced_fits(lat)) {  // bit-sliced in shared memory, the automatic choice
+    const size_t smem = sl_smem_bytes(lat.D, (uint32_t)lat.L);
+    const uint32_t tiles = (uint32_t)lat.L / kSlY * (lat.D == 3 ? (uint32_t)lat.L / kSlZ : 1u);
+    const dim3 sgrid((unsigned)lat.slots, tiles, (unsigned)lat.G);
+    if (lat.D == 3) {
+      if (inv) return launch_sliced<3, 1>(lat, p, sgrid, smem);
+      return launch_sliced<3, 0>(lat, p, sgrid, smem);
+    }
+    if (inv) return launch_sliced<2, 1>(lat, p, sgrid, smem);
+    return launch_sliced<2, 0>(lat, p, sgrid, smem);
   }
   if (lat.variant != 1 && lat.L % 4 == 0) {  // the word kernel: 4-byte words, planes shared by the group
     const dim3 wgrid((lat.N / 4u + kWordThreads - 1) / kWordThreads, (unsigned)lat.G, (unsigned)lat.slots);
