@@ -1136,6 +1136,92 @@ __global__ void __launch_bounds__(256) k_measure_field_i8(const int8_t* __restri
   }
 }
 
+// One temperature, R = 1 or 2 replicas, L a multiple of 16: block per
+// sample, E and M of each replica and (R = 2) the overlap Q of the two
+// (Sec. 4.1) in one pass that reads the sample's couplings once.  16 sites
+// of a row per step: a bond (i, j) is unsatisfied iff the sign bits (bit 7)
+// of s_i, J_ij and s_j XOR to 1, so E = 2 U - D N, M = N - 2 n_- and
+// Q = N - 2 n_differ, with U, n_- and n_differ counted by popcounts of
+// sign-bit masks.
+template <int D, int R>
+__global__ void __launch_bounds__(256) k_measure_i8_k1(const int8_t* __restrict__ spins,
+                                                       const int8_t* __restrict__ J, int64_t* acc, int S, int L,
+                                                       uint32_t N, int want_q) {
+  __shared__ long long red[2 * R + 1][8];
+  const uint32_t qrow = (uint32_t)L / 16u, nq = N / 16u, uL = (uint32_t)L;
+  for (uint32_t s = blockIdx.x; s < (uint32_t)S; s += gridDim.x) {
+    const int8_t* Jp = J + (size_t)s * D * N;
+    uint32_t un[R], ng[R], df = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) un[r] = ng[r] = 0;
+    for (uint32_t q = threadIdx.x; q < nq; q += blockDim.x) {
+      const uint32_t row = q / qrow, k = q - row * qrow;
+      const uint32_t y = row % uL, z = row / uL;
+      const uint32_t base = row * uL + 16u * k;
+      const uint32_t nxo = row * uL + (k + 1u == qrow ? 0u : 16u * (k + 1u));
+      const uint32_t yb = ((D == 3 ? z * uL : 0u) + (y + 1u == uL ? 0u : y + 1u)) * uL + 16u * k;
+      const uint32_t zb = D == 3 ? ((z + 1u == uL ? 0u : z + 1u) * uL + y) * uL + 16u * k : 0u;
+      const uint4 jx = __ldg(reinterpret_cast<const uint4*>(Jp + base));
+      const uint4 jy = __ldg(reinterpret_cast<const uint4*>(Jp + N + base));
+      uint4 jz = make_uint4(0u, 0u, 0u, 0u);
+      if (D == 3) jz = __ldg(reinterpret_cast<const uint4*>(Jp + 2u * N + base));
+      const uint32_t jxs[4] = {jx.x, jx.y, jx.z, jx.w}, jys[4] = {jy.x, jy.y, jy.z, jy.w};
+      const uint32_t jzs[4] = {jz.x, jz.y, jz.z, jz.w};
+      uint32_t w0[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int8_t* sp = spins + ((size_t)r * S + s) * N;  // slot r = replica r at the one temperature
+        const uint4 w = *reinterpret_cast<const uint4*>(sp + base);
+        const uint32_t nx = *reinterpret_cast<const uint32_t*>(sp + nxo);
+        const uint4 wy = *reinterpret_cast<const uint4*>(sp + yb);
+        uint4 wz = make_uint4(0u, 0u, 0u, 0u);
+        if (D == 3) wz = *reinterpret_cast<const uint4*>(sp + zb);
+        const uint32_t ws[5] = {w.x, w.y, w.z, w.w, nx};
+        const uint32_t ys[4] = {wy.x, wy.y, wy.z, wy.w}, zs[4] = {wz.x, wz.y, wz.z, wz.w};
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const uint32_t right = __funnelshift_r(ws[t], ws[t + 1], 8);  // byte j: the site at x + 1
+          un[r] += __popc((ws[t] ^ right ^ jxs[t]) & 0x80808080u) + __popc((ws[t] ^ ys[t] ^ jys[t]) & 0x80808080u);
+          if (D == 3) un[r] += __popc((ws[t] ^ zs[t] ^ jzs[t]) & 0x80808080u);
+          ng[r] += __popc(ws[t] & 0x80808080u);
+          if (R == 2) {
+            if (r == 0) w0[t] = ws[t];
+            else df += __popc((w0[t] ^ ws[t]) & 0x80808080u);
+          }
+        }
+      }
+    }
+    long long v[2 * R + 1];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      v[2 * r] = un[r];
+      v[2 * r + 1] = ng[r];
+    }
+    v[2 * R] = df;
+#pragma unroll
+    for (int i = 0; i < 2 * R + 1; ++i)
+      for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+    const int wid = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0)
+      for (int i = 0; i < 2 * R + 1; ++i) red[i][wid] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long t[2 * R + 1];
+      for (int i = 0; i < 2 * R + 1; ++i) {
+        t[i] = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[i] += red[i][w];
+      }
+      for (int r = 0; r < R; ++r) {
+        int64_t* a = acc + ((size_t)s * R + r) * kAccStride;
+        a[0] = 2ll * t[2 * r] - (long long)D * N;
+        a[1] = (long long)N - 2ll * t[2 * r + 1];
+      }
+      if (R == 2 && want_q) acc[(size_t)s * R * kAccStride + 6] = (long long)N - 2ll * t[2 * R];
+    }
+    __syncthreads();
+  }
+}
+
 // Block per configuration: E = -sum_bonds J s s and M = sum s (Sec. 4.1).
 template <int D>
 __global__ void __launch_bounds__(256) k_measure_i8(const int8_t* __restrict__ spins,
@@ -1311,7 +1397,7 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 //   tp  [kPlanes][kMaxClasses]   threshold planes of the group's 64 lanes
 // In 2D the box is one plane of kSlY + 2 rows and there is no jz.
 constexpr int kSlThreads = 256;
-constexpr uint32_t kSlZ = 2, kSlY = 8;
+constexpr uint32_t kSlZ = 2, kSlY = 4;
 
 // Rows a block reads: the spin box without its four corner rows (no site of
 // the tile has them as neighbours), then the coupling rows.
@@ -1410,122 +1496,152 @@ struct SlTranspose {
   }
 };
 
-template <int D, int ALGO, int C>
+// Row of the compact spin box (the corner rows are not stored): 3D planes 0
+// and kSlZ + 1 hold rows 1..kSlY of the box only, planes 1..kSlZ all kSlY +
+// 2 rows; 2D one plane of kSlY + 2 rows.  own(zi, yi): the row of tile
+// site row yi (0..kSlY-1) of tile plane zi (0..kSlZ-1).
+template <int D>
+__device__ __forceinline__ uint32_t sl_own_row(uint32_t zi, uint32_t yi) {
+  return D == 3 ? kSlY + zi * (kSlY + 2) + yi + 1u : yi + 1u;
+}
+template <int D>
+__device__ __forceinline__ uint32_t sl_zm_row(uint32_t zi, uint32_t yi) {  // the same row one plane down
+  return zi == 0u ? yi : sl_own_row<D>(zi - 1u, yi);
+}
+template <int D>
+__device__ __forceinline__ uint32_t sl_zp_row(uint32_t zi, uint32_t yi) {  // the same row one plane up
+  return zi + 1u == kSlZ ? kSlY + kSlZ * (kSlY + 2) + yi : sl_own_row<D>(zi + 1u, yi);
+}
+
+// SB configuration slots (1, or 2 when the lattice has an even number) per
+// block: the slots share the group's couplings, which are converted once.
+template <int D, int ALGO, int C, int SB>
 __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Params p) {
   extern __shared__ uint64_t sl[];
-  constexpr uint32_t TZ = D == 3 ? kSlZ : 1u, BZ = D == 3 ? kSlZ + 2 : 1u, BY = kSlY + 2, ZO = D == 3 ? 1u : 0u;
+  constexpr uint32_t TZ = D == 3 ? kSlZ : 1u, BY = kSlY + 2;
+  constexpr uint32_t NB = sl_box_rows<D>();  // rows of one slot's compact box
   const uint32_t L = (uint32_t)p.L, hL = L >> 1, N = p.N, S = (uint32_t)p.S;
-  uint64_t* box = sl;
-  uint64_t* jx = box + BZ * BY * L;
-  uint64_t* jy = jx + TZ * kSlY * L;
-  uint64_t* jz = jy + TZ * (kSlY + 1) * L;
-  uint64_t* tp = jz + (D == 3 ? (TZ + 1) * kSlY * L : 0u);
-  // grid (slots, tiles, groups): the slots of one tile and group run side by
-  // side, so the couplings they share are read from DRAM once
+  uint64_t* box = sl;                        // [SB][NB][L]
+  uint64_t* jx = box + SB * NB * L;           // [TZ][kSlY][L]
+  uint64_t* jy = jx + TZ * kSlY * L;          // [TZ][kSlY + 1][L]
+  uint64_t* jz = jy + TZ * (kSlY + 1) * L;    // [TZ + 1][kSlY][L] (3D)
+  uint64_t* tp = jz + (D == 3 ? (TZ + 1) * kSlY * L : 0u);  // [SB][kPlanes][kMaxClasses]
+  // grid (slot pairs, tiles, groups): the slots of one tile and group run
+  // side by side, so the couplings they share are read from DRAM once
   const uint32_t tiles_y = L / kSlY;
   const uint32_t y0 = (blockIdx.y % tiles_y) * kSlY, z0 = (blockIdx.y / tiles_y) * TZ;
   const uint32_t g = blockIdx.z;
-  const int sigma = (int)blockIdx.x;
+  const int sigma0 = (int)blockIdx.x * SB;
   const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31u;
   const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
-  const int tslot = sigma / p.R, a = sigma - tslot * p.R;
   auto wrap = [L](uint32_t v) { return v == 0xFFFFFFFFu ? L - 1u : (v == L ? 0u : v); };  // v in [-1, L]
-  // threshold planes of the 64 lanes: warp u builds class u (plane q = bit
-  // 31 - q of each lane's threshold, plane 32 = threshold 2^32)
-  if (warp <= 2u * D) {
-    const uint32_t u = warp;
-    uint64_t T[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const uint32_t s = 64u * g + 32u * (uint32_t)h + lane;
-      const int k = s < S ? p.temp_of[((size_t)s * p.R + a) * p.K + tslot] : tslot;
-      T[h] = p.thr[(size_t)k * kMaxClasses + u];
-    }
-    const uint64_t always = (uint64_t)__ballot_sync(0xffffffffu, T[0] >= kTwo32) |
-                            ((uint64_t)__ballot_sync(0xffffffffu, T[1] >= kTwo32) << 32);
-    uint64_t mine = 0;
-#pragma unroll 4
-    for (uint32_t q = 0; q < 32u; ++q) {
-      const uint32_t lo = __ballot_sync(0xffffffffu, T[0] < kTwo32 && ((T[0] >> (31u - q)) & 1ull));
-      const uint32_t hi = __ballot_sync(0xffffffffu, T[1] < kTwo32 && ((T[1] >> (31u - q)) & 1ull));
-      if (lane == q) mine = (uint64_t)lo | ((uint64_t)hi << 32);
-    }
-    tp[lane * kMaxClasses + u] = mine;
-    if (lane == 0) tp[32 * kMaxClasses + u] = always;
-  }
-  // the box and the couplings, one row (L sites) of the group's 64 samples
-  // per warp task.  A sample's row is read as P = L/16 pieces of 16 bytes
-  // by P consecutive lanes, 32/P samples per load instruction, so a load
-  // touches 32/P lines instead of 32; each lane packs its piece's 16 signs
-  // into the warp's staging row [sample][piece], and the row's words are
-  // then formed chunk by chunk: lane l reads the 32-site mask of sample
-  // 32 h + l and the warp transposes.  Warp w takes rows w, w + 8, ... of
-  // the block's row list.
+  constexpr uint32_t kWarps = kSlThreads / 32;
+  // the boxes and the couplings, one row (L sites) of the group's 64
+  // samples per warp task.  A sample's row is read as P = L/16 pieces of 16
+  // bytes by P consecutive lanes, 32/P samples per load instruction, so a
+  // load touches 32/P lines instead of 32; each lane packs its piece's 16
+  // signs, neighbouring lanes merge their halves of a 32-site chunk into the
+  // warp's staging row [sample][chunk], and the row's words are then formed
+  // chunk by chunk: lane l reads the 32-site mask of sample 32 h + l and the
+  // warp transposes.  Warp w takes rows w, w + 8, ... of the block's list:
+  // the SB compact boxes, then the coupling rows.
   constexpr int P = 2 * C;          // pieces of 16 sites per row
   constexpr int SPI = 32 / P;       // samples per load instruction
   constexpr int NI = 64 / SPI;      // load instructions per row
   constexpr int SW = C;             // staging words (32-site masks) per sample
-  const SlTranspose tr;
-  const uint32_t n_box = sl_box_rows<D>(), n_jx = TZ * kSlY, n_jy = TZ * (kSlY + 1);
-  const uint32_t n_rows = sl_rows<D>(L);
+  constexpr uint32_t n_box = SB * NB, n_jx = TZ * kSlY, n_jy = TZ * (kSlY + 1);
+  const uint32_t n_rows = n_box + sl_rows<D>(L) - NB;
   const uint32_t xq = sl_site_of_bit16(lane);
   const uint32_t dq = sl_index(xq, hL);  // chunk c adds 16 c: each 32-site chunk is 16 words of each parity
-  constexpr uint32_t kWarps = kSlThreads / 32;
-  uint32_t* stage = reinterpret_cast<uint32_t*>(tp + kPlanes * kMaxClasses) + warp * (64 * SW);
+  uint32_t* stage = reinterpret_cast<uint32_t*>(tp + SB * kPlanes * kMaxClasses) + warp * (64 * SW);
   const uint32_t grp = lane / P, piece = lane - grp * P;
-#pragma unroll 1
-  for (uint32_t r = warp; r < n_rows; r += kWarps) {
+  // row r of the list: issue this lane's loads (v) and return the row's
+  // shared-memory words
+  uint4 v[NI];
+  auto issue = [&](uint32_t r) -> uint64_t* {
     uint32_t z, y, d = 0;
-    bool spin = false;
-    uint64_t* dst;
+    const int8_t* src0;
+    size_t stride;
     if (r < n_box) {
-      // 3D: rows 1..kSlY of plane 0, all rows of planes 1..kSlZ, rows
-      // 1..kSlY of plane kSlZ + 1 (the corner rows are not read)
-      uint32_t zi = 0u, yi = r;
+      const uint32_t as = r / NB, rb = r - as * NB;
+      // 3D: rows 1..kSlY of box plane 0, all rows of planes 1..kSlZ, rows
+      // 1..kSlY of plane kSlZ + 1
+      uint32_t zi = 0u, yi = rb;
       if (D == 3) {
-        if (r < kSlY) {
-          yi = r + 1u;
-        } else if (r < kSlY + kSlZ * BY) {
-          zi = 1u + (r - kSlY) / BY;
-          yi = r - kSlY - (zi - 1u) * BY;
+        if (rb < kSlY) {
+          yi = rb + 1u;
+        } else if (rb < kSlY + kSlZ * BY) {
+          zi = 1u + (rb - kSlY) / BY;
+          yi = rb - kSlY - (zi - 1u) * BY;
         } else {
           zi = kSlZ + 1u;
-          yi = r - kSlY - kSlZ * BY + 1u;
+          yi = rb - kSlY - kSlZ * BY + 1u;
         }
       }
       z = D == 3 ? wrap(z0 + zi - 1u) : 0u;
       y = wrap(y0 + yi - 1u);
-      spin = true;
-      dst = box + (zi * BY + yi) * L;
-    } else if (r < n_box + n_jx) {
-      const uint32_t rr = r - n_box, zi = rr / kSlY, yi = rr - zi * kSlY;
-      z = z0 + zi;
-      y = y0 + yi;
-      dst = jx + rr * L;
-    } else if (r < n_box + n_jx + n_jy) {
-      const uint32_t rr = r - n_box - n_jx, zi = rr / (kSlY + 1), yi = rr - zi * (kSlY + 1);
-      z = z0 + zi;
-      y = wrap(y0 + yi - 1u);
-      d = 1;
-      dst = jy + rr * L;
+      stride = (size_t)N;
+      src0 = p.spins + ((size_t)(sigma0 + (int)as) * S + 64u * g) * N;
     } else {
-      const uint32_t rr = r - n_box - n_jx - n_jy, zi = rr / kSlY, yi = rr - zi * kSlY;
-      z = wrap(z0 + zi - 1u);
-      y = y0 + yi;
-      d = 2;
-      dst = jz + rr * L;
+      const uint32_t rj = r - n_box;
+      if (rj < n_jx) {
+        const uint32_t zi = rj / kSlY, yi = rj - zi * kSlY;
+        z = z0 + zi;
+        y = y0 + yi;
+      } else if (rj < n_jx + n_jy) {
+        const uint32_t rr = rj - n_jx, zi = rr / (kSlY + 1), yi = rr - zi * (kSlY + 1);
+        z = z0 + zi;
+        y = wrap(y0 + yi - 1u);
+        d = 1;
+      } else {
+        const uint32_t rr = rj - n_jx - n_jy, zi = rr / kSlY, yi = rr - zi * kSlY;
+        z = wrap(z0 + zi - 1u);
+        y = y0 + yi;
+        d = 2;
+      }
+      stride = (size_t)D * N;
+      src0 = p.J + (size_t)64u * g * D * N + (size_t)d * N;
     }
-    // lane's sample for instruction i: 64 g + SPI i + grp; consecutive
-    // samples are N bytes apart (spins) or D N (couplings)
-    const size_t stride = spin ? (size_t)N : (size_t)D * N;
-    const int8_t* base = (spin ? p.spins + ((size_t)sigma * S + 64u * g) * N : p.J + (size_t)64u * g * D * N + (size_t)d * N) +
-                         ((size_t)z * L + y) * L + 16u * piece + (size_t)grp * stride;
-    uint4 v[NI];
+    // lane's sample for instruction i: 64 g + SPI i + grp
+    const int8_t* base = src0 + ((size_t)z * L + y) * L + 16u * piece + (size_t)grp * stride;
 #pragma unroll
     for (int i = 0; i < NI; ++i) {
       v[i] = make_uint4(0u, 0u, 0u, 0u);
       if (64u * g + (uint32_t)(SPI * i) + grp < S) v[i] = *reinterpret_cast<const uint4*>(base + (size_t)(SPI * i) * stride);
     }
+    return box + r * L;  // the boxes and coupling arrays follow the row list
+  };
+  // the first row's loads are in flight while the threshold planes are built
+  uint64_t* dst = warp < n_rows ? issue(warp) : nullptr;
+  const SlTranspose tr;
+  // threshold planes of the 64 lanes of each slot: one warp per (slot,
+  // class u).  Plane q is bit 31 - q of each lane's threshold (0 for a
+  // threshold of 2^32), i.e. a row of the transposed 32 x 32 bit matrix of
+  // the thresholds of 32 lanes; plane 32 marks the thresholds of 2^32.
+#pragma unroll 1
+  for (uint32_t task = warp; task < SB * (2u * D + 1u); task += kWarps) {
+    const uint32_t as = task / (2u * D + 1u), u = task - as * (2u * D + 1u);
+    const int sigma = sigma0 + (int)as, tslot = sigma / p.R, rep = sigma - tslot * p.R;
+    uint64_t T[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t s = 64u * g + 32u * (uint32_t)h + lane;
+      const int k = s < S ? p.temp_of[((size_t)s * p.R + rep) * p.K + tslot] : tslot;
+      T[h] = p.thr[(size_t)k * kMaxClasses + u];
+    }
+    const uint64_t always = (uint64_t)__ballot_sync(0xffffffffu, T[0] >= kTwo32) |
+                            ((uint64_t)__ballot_sync(0xffffffffu, T[1] >= kTwo32) << 32);
+    // after the transpose lane j holds bit j of the 32 lanes' thresholds
+    const uint32_t lo = tr(T[0] >= kTwo32 ? 0u : (uint32_t)T[0]);
+    const uint32_t hi = tr(T[1] >= kTwo32 ? 0u : (uint32_t)T[1]);
+    uint64_t* tpa = tp + as * kPlanes * kMaxClasses;
+    tpa[(31u - lane) * kMaxClasses + u] = (uint64_t)lo | ((uint64_t)hi << 32);
+    if (lane == 0) tpa[32 * kMaxClasses + u] = always;
+  }
+  // each row: its signs packed and staged, the next row's loads issued,
+  // then the staged chunks transposed into the row's words
+#pragma unroll 1
+  for (uint32_t r = warp; r < n_rows; r += kWarps) {
     // pieces 2c and 2c + 1 of a sample sit in neighbouring lanes: the even
     // lane merges them into the chunk's 32-site mask and stages it
 #pragma unroll
@@ -1535,19 +1651,20 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
       if ((piece & 1u) == 0u) stage[((uint32_t)(SPI * i) + grp) * SW + (piece >> 1)] = sl_merge16(mine, other);
     }
     __syncwarp();
+    uint64_t* const cur = dst;
+    if (r + kWarps < n_rows) dst = issue(r + kWarps);
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const uint32_t lo = tr(stage[lane * SW + c]);
       const uint32_t hi = tr(stage[(32u + lane) * SW + c]);
-      dst[dq + 16u * c] = (uint64_t)lo | ((uint64_t)hi << 32);
+      cur[dq + 16u * c] = (uint64_t)lo | ((uint64_t)hi << 32);
     }
     __syncwarp();
   }
   __syncthreads();
-  // the colour pass on the tile's words
+  // the colour pass on the tile's words, every slot of the block per word
   BitsParams bp;
   bp.keys = p.keys;
-  const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)sigma << 12) | g;
   const uint32_t n_act = TZ * kSlY * hL;
 #pragma unroll 1
   for (uint32_t w = threadIdx.x; w < n_act; w += kSlThreads) {
@@ -1558,23 +1675,39 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
     const uint32_t is = par * hL + k;                                        // the site (parity par)
     const uint32_t ip = par ? (k + 1u == hL ? 0u : k + 1u) : hL + k;          // x + 1
     const uint32_t im = par ? k : hL + (k == 0u ? hL - 1u : k - 1u);          // x - 1
-    uint64_t* row = box + ((zi + ZO) * BY + yi + 1u) * L;  // the site's row; rows y +- 1 and planes z +- 1 around it
-    const uint64_t b = row[is];
-    uint64_t e[2 * D];
-    e[0] = b ^ row[ip] ^ jx[(zi * kSlY + yi) * L + is];
-    e[1] = b ^ row[im] ^ jx[(zi * kSlY + yi) * L + im];
-    e[2] = b ^ (row + L)[is] ^ jy[(zi * (kSlY + 1) + yi + 1u) * L + is];
-    e[3] = b ^ (row - L)[is] ^ jy[(zi * (kSlY + 1) + yi) * L + is];
+    const uint32_t ro = sl_own_row<D>(zi, yi) * L, rzp = sl_zp_row<D>(zi, yi) * L, rzm = sl_zm_row<D>(zi, yi) * L;
+    uint64_t jw[2 * D];
+    jw[0] = jx[(zi * kSlY + yi) * L + is];
+    jw[1] = jx[(zi * kSlY + yi) * L + im];
+    jw[2] = jy[(zi * (kSlY + 1) + yi + 1u) * L + is];
+    jw[3] = jy[(zi * (kSlY + 1) + yi) * L + is];
     if (D == 3) {
-      e[4] = b ^ (row + BY * L)[is] ^ jz[((zi + 1u) * kSlY + yi) * L + is];
-      e[5] = b ^ (row - BY * L)[is] ^ jz[(zi * kSlY + yi) * L + is];
+      jw[4] = jz[((zi + 1u) * kSlY + yi) * L + is];
+      jw[5] = jz[(zi * kSlY + yi) * L + is];
     }
-    uint64_t u0, u1, u2;
-    count_unsat<D>(e, u0, u1, u2);
-    planes::LazyWord lw = planes::bits_word_start<D, ALGO>(tp, u0, u1, u2);
-    planes::bits_plane_pairs<D, ALGO>(lw, tp, bp, tk, x + L * (y + L * z), c2, 0u, 16u);
-    const uint64_t flip = ALGO == 0 ? lw.lt : ~lw.lt;
-    if (flip) row[is] = b ^ flip;
+    const uint32_t site = x + L * (y + L * z);
+#pragma unroll
+    for (int as = 0; as < SB; ++as) {
+      uint64_t* bx = box + (uint32_t)as * NB * L;
+      const uint64_t b = bx[ro + is];
+      uint64_t e[2 * D];
+      e[0] = b ^ bx[ro + ip] ^ jw[0];
+      e[1] = b ^ bx[ro + im] ^ jw[1];
+      e[2] = b ^ bx[ro + L + is] ^ jw[2];
+      e[3] = b ^ bx[ro - L + is] ^ jw[3];
+      if (D == 3) {
+        e[4] = b ^ bx[rzp + is] ^ jw[4];
+        e[5] = b ^ bx[rzm + is] ^ jw[5];
+      }
+      uint64_t u0, u1, u2;
+      count_unsat<D>(e, u0, u1, u2);
+      const uint64_t* tpa = tp + (uint32_t)as * kPlanes * kMaxClasses;
+      planes::LazyWord lw = planes::bits_word_start<D, ALGO>(tpa, u0, u1, u2);
+      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)(sigma0 + as) << 12) | g;
+      planes::bits_plane_pairs<D, ALGO>(lw, tpa, bp, tk, site, c2, 0u, 16u);
+      const uint64_t flip = ALGO == 0 ? lw.lt : ~lw.lt;
+      if (flip) bx[ro + is] = b ^ flip;
+    }
   }
   __syncthreads();
   // the tile's rows back to global memory, a row of the group's 64 samples
@@ -1583,14 +1716,15 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
   // holds sample 32 h + l's 32 signs in the order sl_unpack_word expects
   const uint32_t dq3 = sl_index(sl_site_of_bit(lane), hL);
 #pragma unroll 1
-  for (uint32_t r = warp; r < TZ * kSlY; r += kWarps) {
-    const uint32_t zi = r / kSlY, yi = r - zi * kSlY;
+  for (uint32_t r = warp; r < SB * TZ * kSlY; r += kWarps) {
+    const uint32_t as = r / (TZ * kSlY), ro = r - as * (TZ * kSlY), zi = ro / kSlY, yi = ro - zi * kSlY;
     const uint32_t y = y0 + yi, z = D == 3 ? z0 + zi : 0u;
-    const uint64_t* src = box + ((zi + ZO) * BY + yi + 1u) * L + dq3;
+    const uint64_t* src = box + (as * NB + sl_own_row<D>(zi, yi)) * L + dq3;
     const size_t row_off = ((size_t)z * L + y) * L;
     const uint32_t s_0 = 64u * g + lane, s_1 = s_0 + 32u;
-    int8_t* d0 = p.spins + ((size_t)sigma * S + s_0) * N + row_off;
-    int8_t* d1 = p.spins + ((size_t)sigma * S + s_1) * N + row_off;
+    const size_t sl0 = (size_t)(sigma0 + (int)as) * S;
+    int8_t* d0 = p.spins + (sl0 + s_0) * N + row_off;
+    int8_t* d1 = p.spins + (sl0 + s_1) * N + row_off;
 #pragma unroll
     for (int c = 0; c < C; ++c) {
       const uint64_t wv = src[16 * c];
@@ -1611,10 +1745,13 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
   }
 }
 
-size_t sl_smem_bytes(int D, uint32_t L) {
-  const uint32_t rows = D == 3 ? sl_smem_rows<3>() : sl_smem_rows<2>();
+// Shared memory of a block: SB compact spin boxes, the coupling rows, SB
+// threshold-plane tables and the warps' staging rows.
+size_t sl_smem_bytes(int D, uint32_t L, int SB) {
+  const uint32_t box = D == 3 ? sl_box_rows<3>() : sl_box_rows<2>();
+  const uint32_t jrows = (D == 3 ? sl_rows<3>(L) : sl_rows<2>(L)) - box;
   const size_t stage = (size_t)(kSlThreads / 32) * 64 * (L / 32) * sizeof(uint32_t);  // per warp [64][L/32] masks
-  return ((size_t)rows * L + (size_t)kPlanes * kMaxClasses) * sizeof(uint64_t) + stage;
+  return ((size_t)(SB * box + jrows) * L + (size_t)SB * kPlanes * kMaxClasses) * sizeof(uint64_t) + stage;
 }
 
 // The shared-memory bit-sliced sweep takes rows of 1, 2 or 4 whole 32-site
@@ -1625,25 +1762,34 @@ bool i8_sliced_fits(const Lattice& lat) {
          lat.rng != IANUS_RNG_WHEEL;
 }
 
-template <int D, int ALGO, int C>
+template <int D, int ALGO, int C, int SB>
 cudaError_t launch_sliced_c(Lattice& lat, const I8Params& p, dim3 grid, size_t smem) {
   static bool ok = false;
   if (!ok) {
-    cudaError_t e = cudaFuncSetAttribute(k_sweep_i8_sliced<D, ALGO, C>,
+    cudaError_t e = cudaFuncSetAttribute(k_sweep_i8_sliced<D, ALGO, C, SB>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return e;
     ok = true;
   }
-  k_sweep_i8_sliced<D, ALGO, C><<<grid, kSlThreads, smem, lat.stream>>>(p);
+  k_sweep_i8_sliced<D, ALGO, C, SB><<<grid, kSlThreads, smem, lat.stream>>>(p);
   return cudaGetLastError();
 }
 
+// Two configuration slots per block when the lattice has an even number of
+// slots, else one.
 template <int D, int ALGO>
-cudaError_t launch_sliced(Lattice& lat, const I8Params& p, dim3 grid, size_t smem) {
-  switch (lat.L / 32) {
-    case 1: return launch_sliced_c<D, ALGO, 1>(lat, p, grid, smem);
-    case 2: return launch_sliced_c<D, ALGO, 2>(lat, p, grid, smem);
-    default: return launch_sliced_c<D, ALGO, 4>(lat, p, grid, smem);
+cudaError_t launch_sliced(Lattice& lat, const I8Params& p) {
+  const int SB = lat.slots % 2 == 0 ? 2 : 1;
+  const size_t smem = sl_smem_bytes(D, (uint32_t)lat.L, SB);
+  const uint32_t tiles = (uint32_t)lat.L / kSlY * (D == 3 ? (uint32_t)lat.L / kSlZ : 1u);
+  const dim3 grid((unsigned)(lat.slots / SB), tiles, (unsigned)lat.G);
+  switch (lat.L / 32 * 2 + (SB - 1)) {
+    case 2: return launch_sliced_c<D, ALGO, 1, 1>(lat, p, grid, smem);
+    case 3: return launch_sliced_c<D, ALGO, 1, 2>(lat, p, grid, smem);
+    case 4: return launch_sliced_c<D, ALGO, 2, 1>(lat, p, grid, smem);
+    case 5: return launch_sliced_c<D, ALGO, 2, 2>(lat, p, grid, smem);
+    case 8: return launch_sliced_c<D, ALGO, 4, 1>(lat, p, grid, smem);
+    default: return launch_sliced_c<D, ALGO, 4, 2>(lat, p, grid, smem);
   }
 }
 
@@ -1696,15 +1842,8 @@ cudaError_t launch_sweep_i8(Lattice& lat, int colour, uint64_t t, int inv) {
     return cudaGetLastError();
   }
   if (lat.variant == 0 && i8_sliced_fits(lat)) {  // bit-sliced in shared memory, the automatic choice
-    const size_t smem = sl_smem_bytes(lat.D, (uint32_t)lat.L);
-    const uint32_t tiles = (uint32_t)lat.L / kSlY * (lat.D == 3 ? (uint32_t)lat.L / kSlZ : 1u);
-    const dim3 sgrid((unsigned)lat.slots, tiles, (unsigned)lat.G);
-    if (lat.D == 3) {
-      if (inv) return launch_sliced<3, 1>(lat, p, sgrid, smem);
-      return launch_sliced<3, 0>(lat, p, sgrid, smem);
-    }
-    if (inv) return launch_sliced<2, 1>(lat, p, sgrid, smem);
-    return launch_sliced<2, 0>(lat, p, sgrid, smem);
+    if (lat.D == 3) return inv ? launch_sliced<3, 1>(lat, p) : launch_sliced<3, 0>(lat, p);
+    return inv ? launch_sliced<2, 1>(lat, p) : launch_sliced<2, 0>(lat, p);
   }
   if (lat.variant != 1 && lat.L % 4 == 0) {  // the word kernel: 4-byte words, planes shared by the group
     const dim3 wgrid((lat.N / 4u + kWordThreads - 1) / kWordThreads, (unsigned)lat.G, (unsigned)lat.slots);
@@ -1737,7 +1876,19 @@ cudaError_t launch_measure_i8(Lattice& lat, int want_q) {
   else if (lat.field)
     k_measure_field_i8<2><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.hs,
                                                          lat.occ, lat.acc, lat.S, lat.slots, lat.L, lat.N);
-  else if (lat.D == 3)
+  else if (lat.K == 1 && lat.R <= 2 && lat.L % 16 == 0) {  // E, M (and Q) in one pass per sample
+    const unsigned gs = (unsigned)std::min<uint64_t>((uint64_t)lat.S, 152u * 8u);
+    const int8_t* sp = (const int8_t*)lat.spins;
+    const int8_t* J = (const int8_t*)lat.J;
+    if (lat.D == 3) {
+      if (lat.R == 2) k_measure_i8_k1<3, 2><<<gs, 256, 0, lat.stream>>>(sp, J, lat.acc, lat.S, lat.L, lat.N, want_q);
+      else k_measure_i8_k1<3, 1><<<gs, 256, 0, lat.stream>>>(sp, J, lat.acc, lat.S, lat.L, lat.N, want_q);
+    } else {
+      if (lat.R == 2) k_measure_i8_k1<2, 2><<<gs, 256, 0, lat.stream>>>(sp, J, lat.acc, lat.S, lat.L, lat.N, want_q);
+      else k_measure_i8_k1<2, 1><<<gs, 256, 0, lat.stream>>>(sp, J, lat.acc, lat.S, lat.L, lat.N, want_q);
+    }
+    return cudaGetLastError();
+  } else if (lat.D == 3)
     k_measure_i8<3><<<grid, 256, 0, lat.stream>>>((const int8_t*)lat.spins, (const int8_t*)lat.J, lat.acc,
                                                    lat.S, lat.R, lat.slots, lat.L, lat.N);
   else
