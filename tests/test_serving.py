@@ -58,3 +58,77 @@ def test_admission_respects_memory_budget(ianus):
     spans = sorted((r.admitted, r.finished) for r in results)
     for (a0, f0), (a1, _) in zip(spans, spans[1:]):
         assert a1 >= f0 - 1e-6  # the next job is admitted only after the previous one left
+
+
+class _FakeLattice:
+    def __init__(self):
+        self.closed = False
+
+    def close(self):
+        self.closed = True
+
+
+def _bare_server():
+    srv = serve.Server.__new__(serve.Server)  # host bookkeeping only, no CUDA streams
+    srv._closing = []
+    return srv
+
+
+def test_finished_job_lattice_outlives_its_running_compile():
+    """A job that finishes while a worker still compiles its kernel (reading
+    the lattice's shape) keeps its lattice open until the compile returns;
+    a compile that never started is cancelled and the lattice closes at
+    once."""
+    from concurrent.futures import Future
+
+    srv = _bare_server()
+    running = Future()
+    assert running.set_running_or_notify_cancel()  # a worker has started it
+    a = serve._Active()
+    a.lat, a.ready = _FakeLattice(), running
+    lat = a.lat
+    srv._retire(a)
+    assert not lat.closed and a.lat is None and len(srv._closing) == 1
+    srv._reap()
+    assert not lat.closed
+    running.set_result(True)
+    srv._reap()
+    assert lat.closed and srv._closing == []
+
+    pending = Future()  # queued, not started: cancelled
+    b = serve._Active()
+    b.lat, b.ready = _FakeLattice(), pending
+    lat_b = b.lat
+    srv._retire(b)
+    assert lat_b.closed and pending.cancelled() and srv._closing == []
+
+    done = Future()
+    done.set_result(False)
+    c = serve._Active()
+    c.lat, c.ready = _FakeLattice(), done
+    lat_c = c.lat
+    srv._retire(c)
+    assert lat_c.closed
+
+
+def test_drain_waits_for_every_compile():
+    import threading
+    import time
+    from concurrent.futures import ThreadPoolExecutor
+
+    srv = _bare_server()
+    gate = threading.Event()
+    with ThreadPoolExecutor(max_workers=1) as pool:
+        fut = pool.submit(gate.wait, 10.0)
+        a = serve._Active()
+        a.lat, a.ready = _FakeLattice(), fut
+        lat = a.lat
+        t0 = time.monotonic()
+        while not fut.running() and time.monotonic() - t0 < 5.0:
+            time.sleep(0.001)
+        assert fut.running()
+        srv._retire(a)
+        assert not lat.closed
+        gate.set()
+        srv._drain()
+        assert lat.closed and srv._closing == []
