@@ -522,14 +522,16 @@ def run_other_configs(args):
     # per-lane-plane kernel, 3D Metropolis: e-words 12, adder tree 16, the
     # "always" plane by a 6-multiplexer tree over the class bits (12) and the
     # need / undecided masks (4); per plane the threshold bit by 2
-    # multiplexers (4) + compare (4), per pair Philox 21 ALU + merge 2;
-    # ~3.9 plane pairs per word
-    # (and 20 mad.wide per Philox block)
-    alu_word = 44 + 3.9 * (2 * 8 + 23)
+    # multiplexers (4) + compare (4); per pair one Philox block from rounds 2
+    # on (rounds 0 and 1 split into a site key, once per word, and parts
+    # shared by the block): 16 ALU + 2 to merge the parts + 2 to merge the
+    # planes, and 16 mad.wide; the site key 1 ALU and 2 mad.wide per word,
+    # shared by its 2 replicas; ~3.9 plane pairs per word
+    alu_word = 44 + 3.9 * (2 * 8 + 20) + 1 / 2
     out["L32_pt_32temps"] = {
         "updates_per_ns": rate, "ms_per_100_sweeps": sec * 1e3 / reps,
         "mode": "bit-sliced, per-lane threshold planes, device PT swap every 10 sweeps",
-        "roofline": issue_roof(alu_word, 3.9 * 20, 64, rate),
+        "roofline": issue_roof(alu_word, 3.9 * 16 + 2 / 2, 64, rate),
     }
     if not args.no_cpu_baseline:
         import oracle
@@ -739,14 +741,14 @@ def run_other_configs(args):
     # per-lane-plane update, 3D heat bath: e-words 12, adder tree 16, the
     # "always" plane (12) and the undecided mask (4); per plane the
     # threshold bit by a 7-way multiplexer tree (6) + compare (4); per pair
-    # Philox 21 ALU + merge 2; 3.92 plane pairs per word (and 20 mad.wide
-    # per Philox block)
-    alu_word = 44 + 3.92 * (2 * 10 + 23)
+    # one Philox block from rounds 2 on (18 ALU, 16 mad.wide) + merge 2;
+    # 3.92 plane pairs per word; the site key 1 ALU and 2 mad.wide per word
+    alu_word = 44 + 3.92 * (2 * 10 + 20) + 1
     out["resident_L8_64xG_hb"] = {
         **res_out,
         "mode": "bit-sliced, k_resident_bits: one block per 64-sample group holds spins, couplings and threshold "
                 "planes in shared memory for up to 4096 sweeps per launch; heat bath T=1.0, one replica",
-        "roofline": issue_roof(alu_word, 3.92 * 20, 64, res_out["152x64"]["resident"]["updates_per_ns"]),
+        "roofline": issue_roof(alu_word, 3.92 * 16 + 2, 64, res_out["152x64"]["resident"]["updates_per_ns"]),
     }
     # device-side set-up: couplings and initial spins of the bench workload from the seed
     t0 = time.perf_counter()

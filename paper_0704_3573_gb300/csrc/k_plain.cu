@@ -1553,7 +1553,8 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
   const uint32_t n_rows = n_box + sl_rows<D>(L) - NB;
   const uint32_t xq = sl_site_of_bit16(lane);
   const uint32_t dq = sl_index(xq, hL);  // chunk c adds 16 c: each 32-site chunk is 16 words of each parity
-  uint32_t* stage = reinterpret_cast<uint32_t*>(tp + SB * kPlanes * kMaxClasses) + warp * (64 * SW);
+  uint4* su = reinterpret_cast<uint4*>(tp + SB * kPlanes * kMaxClasses);  // [SB][16] Philox parts
+  uint32_t* stage = reinterpret_cast<uint32_t*>(su + SB * 16) + warp * (64 * SW);
   const uint32_t grp = lane / P, piece = lane - grp * P;
   // row r of the list: issue this lane's loads (v) and return the row's
   // shared-memory words
@@ -1638,6 +1639,7 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
     tpa[(31u - lane) * kMaxClasses + u] = (uint64_t)lo | ((uint64_t)hi << 32);
     if (lane == 0) tpa[32 * kMaxClasses + u] = always;
   }
+  planes::plane_uniform_table(su, SB, sigma0, g, tk, p.keys);
   // each row: its signs packed and staged, the next row's loads issued,
   // then the staged chunks transposed into the row's words
 #pragma unroll 1
@@ -1663,8 +1665,6 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
   }
   __syncthreads();
   // the colour pass on the tile's words, every slot of the block per word
-  BitsParams bp;
-  bp.keys = p.keys;
   const uint32_t n_act = TZ * kSlY * hL;
 #pragma unroll 1
   for (uint32_t w = threadIdx.x; w < n_act; w += kSlThreads) {
@@ -1685,7 +1685,7 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
       jw[4] = jz[((zi + 1u) * kSlY + yi) * L + is];
       jw[5] = jz[(zi * kSlY + yi) * L + is];
     }
-    const uint32_t site = x + L * (y + L * z);
+    const planes::PlaneSiteKey sk = planes::plane_site_key(x + L * (y + L * z), tk, p.keys);
 #pragma unroll
     for (int as = 0; as < SB; ++as) {
       uint64_t* bx = box + (uint32_t)as * NB * L;
@@ -1703,8 +1703,7 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
       count_unsat<D>(e, u0, u1, u2);
       const uint64_t* tpa = tp + (uint32_t)as * kPlanes * kMaxClasses;
       planes::LazyWord lw = planes::bits_word_start<D, ALGO>(tpa, u0, u1, u2);
-      const uint32_t c2 = (TAG_SPIN << 28) | ((uint32_t)(sigma0 + as) << 12) | g;
-      planes::bits_plane_pairs<D, ALGO>(lw, tpa, bp, tk, site, c2, 0u, 16u);
+      planes::bits_plane_pairs<D, ALGO>(lw, tpa, su + 16 * as, sk, p.keys, 0u, tk, 0u, 16u);
       const uint64_t flip = ALGO == 0 ? lw.lt : ~lw.lt;
       if (flip) bx[ro + is] = b ^ flip;
     }
@@ -1746,12 +1745,14 @@ __global__ void __launch_bounds__(kSlThreads, 3) k_sweep_i8_sliced(const I8Param
 }
 
 // Shared memory of a block: SB compact spin boxes, the coupling rows, SB
-// threshold-plane tables and the warps' staging rows.
+// threshold-plane tables, SB tables of shared Philox parts and the warps'
+// staging rows.
 size_t sl_smem_bytes(int D, uint32_t L, int SB) {
   const uint32_t box = D == 3 ? sl_box_rows<3>() : sl_box_rows<2>();
   const uint32_t jrows = (D == 3 ? sl_rows<3>(L) : sl_rows<2>(L)) - box;
   const size_t stage = (size_t)(kSlThreads / 32) * 64 * (L / 32) * sizeof(uint32_t);  // per warp [64][L/32] masks
-  return ((size_t)(SB * box + jrows) * L + (size_t)SB * kPlanes * kMaxClasses) * sizeof(uint64_t) + stage;
+  return ((size_t)(SB * box + jrows) * L + (size_t)SB * kPlanes * kMaxClasses) * sizeof(uint64_t) +
+         (size_t)SB * 16 * sizeof(uint4) + stage;
 }
 
 // The shared-memory bit-sliced sweep takes rows of 1, 2 or 4 whole 32-site

@@ -57,6 +57,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_bits(const BitsPara
   uint64_t* s_sp = sm;                          // [R][N]
   uint64_t* s_J = s_sp + (size_t)R * N;         // [D][N]
   uint64_t* s_tp = s_J + (size_t)D * N;         // [R][kPlanes][kMaxClasses]
+  uint4* s_u = reinterpret_cast<uint4*>(s_tp + (size_t)R * kPlanes * kMaxClasses);  // [R][16] Philox parts
   uint64_t* g_sp = p.spins + ((size_t)g * p.slots + (size_t)tslot * R) * N;
   const uint64_t* g_J = p.J + (size_t)g * D * N;
   const uint64_t* g_tp = p.tp + ((size_t)g * p.slots + (size_t)tslot * R) * kPlanes * kMaxClasses;
@@ -69,6 +70,10 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_bits(const BitsPara
   for (uint32_t s = 0; s < nsweeps; ++s) {
     const uint64_t t = t0 + s;
     const Tick tk{(uint32_t)t, (uint32_t)(t >> 32)};
+    // this sweep's Philox parts shared by the block (the previous sweep's
+    // last barrier has passed every reader of the old ones)
+    planes::plane_uniform_table(s_u, (int)R, tslot * (int)R, (uint32_t)g, tk, p.keys);
+    __syncthreads();
 #pragma unroll 1
     for (int c = 0; c < 2; ++c) {
 #pragma unroll 1
@@ -76,6 +81,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_bits(const BitsPara
         const Nbr n = split_neighbours_t<P2>(p.geom, c, w);
         uint64_t jw[2 * D];
         bond_words<D>(s_J, N, n, jw);
+        const planes::PlaneSiteKey sk = planes::plane_site_key(n.site, tk, p.keys);
 #pragma unroll 1
         for (uint32_t a = 0; a < R; ++a) {
           uint64_t* sp = s_sp + (size_t)a * N;
@@ -83,9 +89,7 @@ __global__ void __launch_bounds__(kResThreads, 1) k_resident_bits(const BitsPara
           uint64_t b, u0, u1, u2;
           planes::bits_class_planes<D>(sp, n, jw, b, u0, u1, u2);
           planes::LazyWord lw = planes::bits_word_start<D, ALGO>(tpa, u0, u1, u2);
-          const uint32_t sigma = (uint32_t)tslot * R + a;
-          const uint32_t c2 = (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)g;
-          planes::bits_plane_pairs<D, ALGO>(lw, tpa, p, tk, n.site, c2, 0u, 16u);
+          planes::bits_plane_pairs<D, ALGO>(lw, tpa, s_u + 16u * a, sk, p.keys, 0u, tk, 0u, 16u);
           const uint64_t flip = ALGO == 0 ? lw.lt : ~lw.lt;
           if (flip) sp[n.self] = b ^ flip;
         }
@@ -226,7 +230,8 @@ cudaError_t launch_fused_t(Lattice& lat, const BitsParams& p, uint32_t nsweeps, 
 }
 
 size_t resident_bits_smem(const Lattice& lat) {
-  return ((size_t)lat.R * lat.N + (size_t)lat.D * lat.N + (size_t)lat.R * kPlanes * kMaxClasses) * sizeof(uint64_t);
+  return ((size_t)lat.R * lat.N + (size_t)lat.D * lat.N + (size_t)lat.R * kPlanes * kMaxClasses) * sizeof(uint64_t) +
+         (size_t)lat.R * 16 * sizeof(uint4);
 }
 
 size_t resident_fused_smem(const Lattice& lat) {

@@ -42,10 +42,16 @@ struct WordQueue {
   uint32_t self[kQueue], site[kQueue], a[kQueue];
 };
 
-// Shared memory of the generic kernel: R replicas' threshold planes, then
-// the warps' queues (Q).
+// Shared memory of the generic kernel: R replicas' threshold planes, their
+// Philox parts shared by the block ([R][16] uint4), then the warps' queues
+// (Q).
+// Blocks of more replicas than this compute the shared Philox parts inline
+// instead of staging them (their planes alone nearly fill shared memory).
+constexpr int kUniformMaxR = 64;
+
 __host__ __device__ inline uint64_t bits_sweep_smem(int R, bool Q = true) {
-  return (uint64_t)R * kPlanes * kMaxClasses * sizeof(uint64_t) + (Q ? kWarpsPerBlock * sizeof(WordQueue) : 0);
+  return (uint64_t)R * kPlanes * kMaxClasses * sizeof(uint64_t) + (R <= kUniformMaxR ? (uint64_t)R * 16 * 16 : 0) +
+         (Q ? kWarpsPerBlock * sizeof(WordQueue) : 0);
 }
 
 // Plane pairs before a heat-bath word can be queued.
@@ -74,18 +80,75 @@ __device__ __forceinline__ uint64_t class_select(const uint64_t* row, uint64_t u
   return mux(u2, mux(u1, row[6], c), lo);
 }
 
+// Philox rounds 0 and 1 of the plane stream, counter (site, t_lo, c2, t_hi),
+// split: the products of round 0 are M0 site and M1 c2, so after round 1
+// the state is (s1 ^ u1, s2, u2 ^ s3, u3) with s from the site and the
+// sweep's high word only (the site key, once per site and sweep) and u from
+// c2 and the sweep's low word only (once per plane pair, slot and sweep,
+// shared by every site of a block).  Rounds 2..9 then run as usual.
+struct PlaneSiteKey {
+  uint32_t s1, s2, s3;
+};
+
+__device__ __forceinline__ PlaneSiteKey plane_site_key(uint32_t site, const Tick& tk, const PhiloxKeys& K) {
+  const uint64_t p0 = (uint64_t)0xD2511F53u * site;
+  const uint32_t b = (uint32_t)(p0 >> 32) ^ tk.hi ^ K.k1[0];
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * b;
+  return PlaneSiteKey{(uint32_t)(p1 >> 32), (uint32_t)p1, (uint32_t)p0};
+}
+
+// The shared part of counter word c2 (w unused).
+__device__ __forceinline__ uint4 plane_uniform(uint32_t c2, const Tick& tk, const PhiloxKeys& K) {
+  const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+  const uint32_t a = (uint32_t)(p1 >> 32) ^ tk.lo ^ K.k0[0];
+  const uint64_t p0 = (uint64_t)0xD2511F53u * a;
+  return make_uint4((uint32_t)p1 ^ K.k0[1], (uint32_t)(p0 >> 32) ^ K.k1[1], (uint32_t)p0, 0u);
+}
+
+__device__ __forceinline__ uint4 philox10_split(const PlaneSiteKey& s, const uint4& u, const PhiloxKeys& K) {
+  uint32_t c0 = s.s1 ^ u.x, c1 = s.s2, c2 = u.y ^ s.s3, c3 = u.z;
+#pragma unroll
+  for (int r = 2; r < 10; ++r) {
+    const uint64_t p0 = (uint64_t)0xD2511F53u * c0;
+    const uint64_t p1 = (uint64_t)0xCD9E8D57u * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+    const uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return make_uint4(c0, c1, c2, c3);
+}
+
+// Shared parts of the 16 plane pairs of `slots` consecutive slots
+// sigma0.. of group g (counter word c2 = TAG_SPIN | pair | slot | group):
+// u[a * 16 + m], filled by the block's threads.
+__device__ __forceinline__ void plane_uniform_table(uint4* u, int slots, int sigma0, uint32_t g, const Tick& tk,
+                                                    const PhiloxKeys& K) {
+  for (int i = (int)threadIdx.x; i < slots * 16; i += (int)blockDim.x) {
+    const uint32_t a = (uint32_t)i >> 4, m = (uint32_t)i & 15u;
+    const uint32_t c2 = (TAG_SPIN << 28) | (m << 24) | ((uint32_t)(sigma0 + (int)a) << 12) | g;
+    u[i] = plane_uniform(c2, tk, K);
+  }
+}
+
 // Plane pairs mm0, mm0 + 1, ... (below mm_end) of one word against the
 // per-lane planes tpa, two Philox blocks at a time (two independent round
-// chains in flight); stops when every lane is decided.
+// chains in flight), from the site key and the slot's shared parts ua[16]
+// (null: computed here from the slot's counter word c2base and tk); stops
+// when every lane is decided.
 template <int D, int ALGO>
-__device__ __forceinline__ void bits_plane_pairs(LazyWord& w, const uint64_t* tpa, const BitsParams& p,
-                                                 const Tick& tk, uint32_t site, uint32_t c2, uint32_t mm0,
-                                                 uint32_t mm_end) {
+__device__ __forceinline__ void bits_plane_pairs(LazyWord& w, const uint64_t* tpa, const uint4* ua,
+                                                 const PlaneSiteKey& sk, const PhiloxKeys& keys, uint32_t c2base,
+                                                 const Tick& tk, uint32_t mm0, uint32_t mm_end) {
   uint64_t und = w.und, lt = w.lt;
 #pragma unroll 1
   for (uint32_t mm = mm0; mm < mm_end && und != 0ull; mm += 2u) {
-    const uint4 xa = philox10(site, tk.lo, c2 | (mm << 24), tk.hi, p.keys);
-    const uint4 xb = philox10(site, tk.lo, c2 | ((mm + 1u) << 24), tk.hi, p.keys);
+    const uint4 ma = ua ? ua[mm] : plane_uniform(c2base | (mm << 24), tk, keys);
+    const uint4 mb = ua ? ua[mm + 1u] : plane_uniform(c2base | ((mm + 1u) << 24), tk, keys);
+    const uint4 xa = philox10_split(sk, ma, keys);
+    const uint4 xb = philox10_split(sk, mb, keys);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const uint4& x = q < 2 ? xa : xb;
@@ -139,15 +202,19 @@ __device__ __forceinline__ void bits_class_planes(const uint64_t* sp, const Nbr&
 struct SweepCtx {
   const BitsParams* p;
   const uint64_t* tp;  // shared-memory planes of the block's replicas
+  const uint4* U;      // shared-memory Philox parts of the block's replicas, [R][16] (null above kUniformMaxR)
   uint64_t* sp0;       // spins of the block's first replica
   Tick tk;
   int g, tslot, R;
 };
 
+// Counter word c2 of replica a's plane stream without the pair (bits 24..27).
 __device__ __forceinline__ uint32_t bits_c2(const SweepCtx& c, uint32_t a) {
   const uint32_t sigma = (uint32_t)(c.tslot * c.R) + a;
   return (TAG_SPIN << 28) | (sigma << 12) | (uint32_t)c.g;
 }
+
+__device__ __forceinline__ const uint4* bits_u(const SweepCtx& c, uint32_t a) { return c.U ? c.U + 16u * a : nullptr; }
 
 // Warp-wide append of the lanes with pred set; n is warp-uniform.
 __device__ __forceinline__ void queue_push(WordQueue& q, uint32_t& n, bool pred, const LazyWord& w, uint32_t self,
@@ -191,8 +258,8 @@ __device__ __forceinline__ void queue_round(WordQueue& q, uint32_t& n, uint32_t 
   __syncwarp();
   n -= take;
   if (has) {
-    bits_plane_pairs<D, ALGO>(w, c.tp + (uint64_t)a * kPlanes * kMaxClasses, *c.p, c.tk, site, bits_c2(c, a),
-                              kPhaseA, 16u);
+    bits_plane_pairs<D, ALGO>(w, c.tp + (uint64_t)a * kPlanes * kMaxClasses, bits_u(c, a),
+                              plane_site_key(site, c.tk, c.p->keys), c.p->keys, bits_c2(c, a), c.tk, kPhaseA, 16u);
     uint64_t* sp = c.sp0 + (uint64_t)a * c.p->geom.N;
     const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
     if (flip) sp[self] ^= flip;
@@ -203,13 +270,14 @@ __device__ __forceinline__ void queue_round(WordQueue& q, uint32_t& n, uint32_t 
 // queue (Q); without the queue, all its plane pairs and its write.
 template <int D, int ALGO, bool Q>
 __device__ __forceinline__ void bits_update(WordQueue& q, uint32_t& nq, const SweepCtx& c, bool valid, const Nbr& n,
-                                            uint32_t a, uint64_t b, uint64_t u0, uint64_t u1, uint64_t u2) {
+                                            const PlaneSiteKey& sk, uint32_t a, uint64_t b, uint64_t u0, uint64_t u1,
+                                            uint64_t u2) {
   const uint64_t* tpa = c.tp + (uint64_t)a * kPlanes * kMaxClasses;
   LazyWord w;
   w.und = 0;
   if (valid) {
     w = bits_word_start<D, ALGO>(tpa, u0, u1, u2);
-    bits_plane_pairs<D, ALGO>(w, tpa, *c.p, c.tk, n.site, bits_c2(c, a), 0u, Q ? kPhaseA : 16u);
+    bits_plane_pairs<D, ALGO>(w, tpa, bits_u(c, a), sk, c.p->keys, bits_c2(c, a), c.tk, 0u, Q ? kPhaseA : 16u);
   }
   if (!Q) {
     const uint64_t flip = (ALGO == 0) ? w.lt : ~w.lt;
@@ -230,25 +298,30 @@ __device__ __forceinline__ void bits_update(WordQueue& q, uint32_t& nq, const Sw
 // word's loads are in flight together; with RT = 0 the replicas go in turn.
 template <int D, int ALGO, int RT, bool P2, bool Q>
 __device__ __forceinline__ void sweep_planes_body(const BitsParams& p, const Geom& geom) {
-  extern __shared__ uint64_t sm_tp[];  // [R][kPlanes][kMaxClasses], then the queues
+  extern __shared__ uint64_t sm_tp[];  // [R][kPlanes][kMaxClasses], [R][16] Philox parts, then the queues
   const int R = RT > 0 ? RT : p.R;
   const int gt = blockIdx.y;  // g * K + tslot
   const int g = gt / p.K, tslot = gt - g * p.K;
-  // stage this block's threshold planes
+  const Tick tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  uint4* sm_u = reinterpret_cast<uint4*>(sm_tp + (uint64_t)R * kPlanes * kMaxClasses);
+  const bool staged_u = R <= kUniformMaxR;
+  // stage this block's threshold planes and Philox parts
   {
     const uint64_t* src = p.tp + ((uint64_t)g * p.slots + (uint64_t)tslot * R) * kPlanes * kMaxClasses;
     for (int k = threadIdx.x; k < R * kPlanes * kMaxClasses; k += kPlanesBlock) sm_tp[k] = src[k];
+    if (staged_u) plane_uniform_table(sm_u, R, tslot * R, (uint32_t)g, tk, p.keys);
   }
   __syncthreads();
-  WordQueue& q = reinterpret_cast<WordQueue*>(sm_tp + (uint64_t)R * kPlanes * kMaxClasses)[threadIdx.x >> 5];
+  WordQueue& q = reinterpret_cast<WordQueue*>(sm_u + (staged_u ? (uint64_t)R * 16 : 0))[threadIdx.x >> 5];
   uint32_t nq = 0;
   const uint32_t N = geom.N;
   const uint64_t* Jg = p.J + (uint64_t)g * D * N;
   SweepCtx c;
   c.p = &p;
   c.tp = sm_tp;
+  c.U = staged_u ? sm_u : nullptr;
   c.sp0 = p.spins + ((uint64_t)g * p.slots + (uint64_t)tslot * R) * N;
-  c.tk = sweep_tick(p.t_lo, p.t_hi, p.t_dev);
+  c.tk = tk;
   c.g = g;
   c.tslot = tslot;
   c.R = R;
@@ -272,6 +345,7 @@ __device__ __forceinline__ void sweep_planes_body(const BitsParams& p, const Geo
         jw[5] = __ldg(Jg + 2u * N + n.zm);
       }
     }
+    const PlaneSiteKey sk = plane_site_key(n.site, c.tk, p.keys);  // shared by the word's replicas
     if (RT > 0) {
       uint64_t b[RT > 0 ? RT : 1], u0[RT > 0 ? RT : 1], u1[RT > 0 ? RT : 1], u2[RT > 0 ? RT : 1];
 #pragma unroll
@@ -281,13 +355,13 @@ __device__ __forceinline__ void sweep_planes_body(const BitsParams& p, const Geo
       }
 #pragma unroll
       for (int a = 0; a < RT; ++a)
-        bits_update<D, ALGO, Q>(q, nq, c, valid, n, (uint32_t)a, b[a], u0[a], u1[a], u2[a]);
+        bits_update<D, ALGO, Q>(q, nq, c, valid, n, sk, (uint32_t)a, b[a], u0[a], u1[a], u2[a]);
     } else {
 #pragma unroll 1
       for (int a = 0; a < R; ++a) {
         uint64_t b = 0, u0 = 0, u1 = 0, u2 = 0;
         if (valid) bits_class_planes<D>(c.sp0 + (uint64_t)a * N, n, jw, b, u0, u1, u2);
-        bits_update<D, ALGO, Q>(q, nq, c, valid, n, (uint32_t)a, b, u0, u1, u2);
+        bits_update<D, ALGO, Q>(q, nq, c, valid, n, sk, (uint32_t)a, b, u0, u1, u2);
       }
     }
   }
