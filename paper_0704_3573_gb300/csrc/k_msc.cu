@@ -1362,8 +1362,9 @@ cudaError_t launch_sweep_bits(Lattice& lat, int colour, uint64_t t, int inv) {
   }
   // Lane-uniform thresholds (one temperature): the kernel specialised for
   // them at run time.  Variants (ianus_set_variant): 0 = automatic (the
-  // specialised kernel for lattices of >= 2^20 site words, else the per-lane
-  // planes), 1 = per-lane planes, 2.. = a specialised kernel shape from
+  // lane-queue shape with one temperature and one or two replicas, else the
+  // per-lane planes; small lattices take the resident sweep before they get
+  // here), 1 = per-lane planes, 2.. = a specialised kernel shape from
   // kJitShapes.  A compile costs a fraction of a second and is cached.
   const int v = jit_variant_for(lat);
   if (v >= 2) {

@@ -1,10 +1,11 @@
 """Autotuner for the bit-sliced sweep: kernel variant and launch shape.
 
 For a lattice and an (algorithm, beta) it times every candidate kernel
-variant (precompiled per-lane threshold planes, or one of the shapes of the
-kernel specialised at run time: lockstep or per-warp queues, 3 or 4 blocks per
-SM) and several launch shapes (colour words per 256-thread block) on a short
-block of sweeps, and keeps the fastest.  The state is snapshotted before and
+variant (the automatic choice, which sweeps small lattices resident in shared
+memory; precompiled per-lane threshold planes; or one of the shapes of the
+kernel specialised at run time: lockstep, per-warp queues, the lane-queue
+kernel and its persistent form) and several launch shapes (colour words per
+block) on a short block of sweeps, and keeps the fastest.  The state is snapshotted before and
 restored after every trial, so tuning never changes the simulation: the
 trajectory after tune() is the one the lattice would have followed anyway.
 Choices are cached in a JSON file keyed by GPU name and lattice shape.
@@ -16,7 +17,7 @@ import json
 import os
 import tempfile
 
-VARIANTS = tuple(range(1, 28))
+VARIANTS = tuple(range(0, 28))
 BLOCK_WORDS = (0, 256, 512, 1024, 2048)
 
 
