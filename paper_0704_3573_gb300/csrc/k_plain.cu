@@ -1380,21 +1380,27 @@ inline unsigned grid_for(uint64_t total, unsigned block = 256, unsigned cap = 15
 // The random number of sample s at (site, sweep) is bit (s mod 64) of the
 // plane stream drawn for the site and its group of 64 samples: the stream
 // the bit-sliced layout draws once per 64-lane word.  So a block takes a
-// tile of sites of one group and slot, reads the tile and its halo for the
-// group's 64 samples as full 32-byte sectors, turns them into 64-lane words
-// in shared memory (bit l = sign of sample 64 g + l), runs the bit-sliced
-// update of Sec. 3.2 on those words (one Philox block and one compare chain
-// per 64 updates), and writes the tile's rows back as bytes.  The spins stay
-// one byte each in global memory before and after every colour pass.
+// tile of sites of one group and its configuration slots (two when the
+// lattice has an even number of slots, so the couplings they share are read
+// and converted once), reads the tile and its halo for the group's 64
+// samples as bytes, turns them into 64-lane words in shared memory (bit l =
+// sign of sample 64 g + l), runs the bit-sliced update of Sec. 3.2 on those
+// words (one Philox block and one compare chain per 64 updates), and writes
+// the tile's rows back as bytes.  The spins stay one byte each in global
+// memory before and after every colour pass.
 //
-// Tile: kSlZ planes (3D) x kSlY rows x the L sites of a row (L a multiple
-// of 32).  Shared memory, 64-bit words; a row is stored by x parity (even x
+// Tile: kSlZ planes (3D) x kSlY rows x the L sites of a row (L = 32, 64 or
+// 128).  Shared memory, 64-bit words; a row is stored by x parity (even x
 // at x/2, odd x at L/2 + x/2), so the active sites of a warp are adjacent:
-//   box [kSlZ + 2][kSlY + 2][L]  spins: planes z0-1..z0+kSlZ, rows y0-1..y0+kSlY
+//   box [SB][NB][L]   each slot's spins: planes z0-1 and z0+kSlZ with rows
+//                     y0..y0+kSlY-1 only (sl_zm_row, sl_zp_row), planes
+//                     z0..z0+kSlZ-1 with rows y0-1..y0+kSlY (sl_own_row)
 //   jx  [kSlZ][kSlY][L]          x+ couplings of the tile's sites
 //   jy  [kSlZ][kSlY + 1][L]      y+ couplings of rows y0-1..y0+kSlY-1
 //   jz  [kSlZ + 1][kSlY][L]      z+ couplings of planes z0-1..z0+kSlZ-1
-//   tp  [kPlanes][kMaxClasses]   threshold planes of the group's 64 lanes
+//   tp  [SB][kPlanes][kMaxClasses]  threshold planes of each slot's 64 lanes
+//   u   [SB][16] (uint4)         the slots' Philox parts shared by the block
+//   staging, per warp [64][L/32] (uint32): 32-site sign masks per sample
 // In 2D the box is one plane of kSlY + 2 rows and there is no jz.
 constexpr int kSlThreads = 256;
 constexpr uint32_t kSlZ = 2, kSlY = 4;
